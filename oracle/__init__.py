@@ -1,0 +1,213 @@
+"""FP64 CPU oracle for the k-medoids hot path (test infrastructure).
+
+Only the test suite, ``__graft_entry__.smoke()`` and the ``cpu_baseline`` /
+``--impl reference`` legs of ``bench.py`` may import this module.  It wraps
+``kmedoids_oracle.c`` (plain C, FP64) with ctypes; nothing here touches the
+CUDA library and the CUDA library never touches this.
+
+Every function follows a passage of Schubert & Rousseeuw, "Fast and Eager
+k-Medoids Clustering" (arXiv 2008.05171):
+
+* ``td``            -- Eq. (2) (TD objective), labels = lowest nearest slot.
+* ``cache``         -- the per-point cache nearest / d_n / d_s of Sec. 2.
+* ``removal_loss``  -- Delta^{-m_i} of Eq. (7).
+* ``build``         -- Alg. 1 (PAM BUILD), self term included in each gain.
+* ``eval_swaps``    -- one SWAP evaluation: brute force (Eq. (2) recomputed),
+                       PAM (Alg. 2 + Eq. (5)) or FastPAM1 (Alg. 3 + Eq. (7)).
+* ``swap_delta``    -- Delta of one (slot, candidate) swap by Eq. (5).
+* ``swap``          -- SWAP to convergence: PAM brute force / PAM cached /
+                       FastPAM1 / FastPAM2 / FasterPAM (Alg. 4).
+
+Parity unpinned: FastPAM2's additional swaps (the paper describes FastPAM2
+only in words, Sec. 3.2) beyond the invariants the tests check.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "kmedoids_oracle.c")
+_SO = os.path.join(_HERE, "liboracle.so")
+_LOCK = threading.Lock()
+_LIB = None
+
+VARIANTS = {"pam_bruteforce": 0, "pam": 1, "fastpam1": 2, "fastpam2": 3,
+            "fasterpam": 4}
+EVAL_METHODS = {"bruteforce": 0, "pam": 1, "fastpam1": 2}
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (OpenMP over candidates) in place."""
+    if force or not os.path.exists(_SO) or \
+            os.path.getmtime(_SO) < os.path.getmtime(_SRC):
+        tmp = _SO + ".tmp%d" % os.getpid()
+        subprocess.check_call(["gcc", "-O2", "-fPIC", "-shared", "-fopenmp",
+                               "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _SO)
+    return _SO
+
+
+def _lib():
+    global _LIB
+    with _LOCK:
+        if _LIB is None:
+            build()
+            lib = ctypes.CDLL(_SO)
+            P = ctypes.c_void_p
+            i64, i32, f64 = ctypes.c_int64, ctypes.c_int, ctypes.c_double
+            lib.oracle_td.restype = f64
+            lib.oracle_td.argtypes = [P, i32, i64, i64, P, i32, P]
+            lib.oracle_cache.restype = None
+            lib.oracle_cache.argtypes = [P, i32, i64, i64, P, i32, P, P, P, P]
+            lib.oracle_removal_loss.restype = None
+            lib.oracle_removal_loss.argtypes = [i64, i32, P, P, P, P]
+            lib.oracle_build.restype = i32
+            lib.oracle_build.argtypes = [P, i32, i64, i64, i32, P, P, P]
+            lib.oracle_eval_swaps.restype = None
+            lib.oracle_eval_swaps.argtypes = [P, i32, i64, i64, P, i32, i32,
+                                              P, P, P, P, P]
+            lib.oracle_swap_delta.restype = f64
+            lib.oracle_swap_delta.argtypes = [P, i32, i64, i64, P, i32, i32,
+                                              i64]
+            lib.oracle_swap.restype = i32
+            lib.oracle_swap.argtypes = [P, i32, i64, i64, i32, P, i32, i32,
+                                        f64, f64, P, P, i32, P, P, P]
+            lib.oracle_num_threads.restype = i32
+            lib.oracle_set_threads.argtypes = [i32]
+            _LIB = lib
+    return _LIB
+
+
+def _p(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _mat(D: np.ndarray, n: int | None = None):
+    """Return (array, dtype code, n, ld) for a C-contiguous (n, ld) matrix."""
+    D = np.ascontiguousarray(D)
+    if D.dtype == np.int32:
+        code = 0
+    elif D.dtype == np.float32:
+        code = 1
+    else:
+        raise TypeError("oracle matrices are int32 or float32")
+    rows, ld = D.shape
+    n = rows if n is None else n
+    if n > rows or n > ld:
+        raise ValueError("n exceeds the matrix shape")
+    return D, code, n, ld
+
+
+def _med(medoids) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(medoids, dtype=np.int32))
+
+
+def num_threads() -> int:
+    return int(_lib().oracle_num_threads())
+
+
+def set_threads(t: int) -> None:
+    _lib().oracle_set_threads(int(t))
+
+
+def td(D, medoids, n=None, return_labels=False):
+    D, code, n, ld = _mat(D, n)
+    med = _med(medoids)
+    labels = np.empty(n, dtype=np.int32)
+    v = _lib().oracle_td(_p(D), code, n, ld, _p(med), len(med), _p(labels))
+    return (v, labels) if return_labels else v
+
+
+def cache(D, medoids, n=None):
+    D, code, n, ld = _mat(D, n)
+    med = _med(medoids)
+    near = np.empty(n, np.int32)
+    sec = np.empty(n, np.int32)
+    dn = np.empty(n, np.float64)
+    ds = np.empty(n, np.float64)
+    _lib().oracle_cache(_p(D), code, n, ld, _p(med), len(med), _p(near),
+                        _p(sec), _p(dn), _p(ds))
+    return near, sec, dn, ds
+
+
+def removal_loss(near, dn, ds, k):
+    near = np.ascontiguousarray(near, np.int32)
+    dn = np.ascontiguousarray(dn, np.float64)
+    ds = np.ascontiguousarray(ds, np.float64)
+    rl = np.empty(k, np.float64)
+    _lib().oracle_removal_loss(len(near), k, _p(near), _p(dn), _p(ds), _p(rl))
+    return rl
+
+
+def pam_build(D, k, n=None):
+    """Alg. 1 (BUILD). Returns (medoids int32[k], TD, step gains float64[k])."""
+    D, code, n, ld = _mat(D, n)
+    med = np.empty(k, np.int32)
+    tdv = np.zeros(1, np.float64)
+    steps = np.empty(k, np.float64)
+    _lib().oracle_build(_p(D), code, n, ld, k, _p(med), _p(tdv), _p(steps))
+    return med, float(tdv[0]), steps
+
+
+def eval_swaps(D, medoids, method="fastpam1", n=None):
+    """One SWAP evaluation. Returns (cand_delta[n], cand_slot[n], best)
+    with best = (delta, slot, cand) the lexicographic minimum."""
+    D, code, n, ld = _mat(D, n)
+    med = _med(medoids)
+    cd = np.empty(n, np.float64)
+    cs = np.empty(n, np.int32)
+    bd = np.zeros(1, np.float64)
+    bs = np.zeros(1, np.int32)
+    bc = np.zeros(1, np.int64)
+    _lib().oracle_eval_swaps(_p(D), code, n, ld, _p(med), len(med),
+                             EVAL_METHODS[method], _p(cd), _p(cs), _p(bd),
+                             _p(bs), _p(bc))
+    return cd, cs, (float(bd[0]), int(bs[0]), int(bc[0]))
+
+
+def swap_delta(D, medoids, slot, cand, n=None):
+    D, code, n, ld = _mat(D, n)
+    med = _med(medoids)
+    return float(_lib().oracle_swap_delta(_p(D), code, n, ld, _p(med),
+                                          len(med), int(slot), int(cand)))
+
+
+def swap(D, medoids, variant="fastpam1", max_iter=1000, tol=0.0,
+         fastpam2_tol=0.0, n=None, trace_cap=None):
+    """SWAP to convergence from ``medoids``.  Returns a dict with medoids,
+    iterations, swaps, converged, visited, td_bookkept, td and the trace of
+    applied swaps (delta, slot, cand)."""
+    D, code, n, ld = _mat(D, n)
+    med = _med(medoids).copy()
+    k = len(med)
+    cap = int(trace_cap if trace_cap is not None else max(16, 4 * k + 64))
+    stats = np.zeros(4, np.int64)
+    tdv = np.zeros(2, np.float64)
+    tr_d = np.zeros(cap, np.float64)
+    tr_i = np.zeros(cap, np.int32)
+    tr_c = np.zeros(cap, np.int64)
+    _lib().oracle_swap(_p(D), code, n, ld, k, _p(med), VARIANTS[variant],
+                       int(max_iter), float(tol), float(fastpam2_tol),
+                       _p(stats), _p(tdv), cap, _p(tr_d), _p(tr_i), _p(tr_c))
+    ns = min(int(stats[1]), cap)
+    return {
+        "medoids": med, "iterations": int(stats[0]), "swaps": int(stats[1]),
+        "converged": bool(stats[2]), "visited": int(stats[3]),
+        "td_bookkept": float(tdv[0]), "td": float(tdv[1]),
+        "trace": list(zip(tr_d[:ns].tolist(), tr_i[:ns].tolist(),
+                          tr_c[:ns].tolist())),
+    }
+
+
+def run(D, k, variant="fastpam1", n=None, **kw):
+    """BUILD followed by SWAP (the paper's full PAM / FastPAM1 / FasterPAM)."""
+    med, td_build, _ = pam_build(D, k, n=n)
+    out = swap(D, med, variant=variant, n=n, **kw)
+    out["build_medoids"] = med
+    out["td_build"] = td_build
+    return out

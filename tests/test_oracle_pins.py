@@ -1,0 +1,322 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+None of these tests retypes an oracle formula: the expected values come from
+the paper's worked example (Fig. 1), from brute-force recomputation of the TD
+objective (Eq. (2)) in numpy, from enumeration of all medoid sets, or from
+invariants the paper states (Sec. 2 and 3).
+"""
+import itertools
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import bruteforce as bf
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def fig1():
+    with open(os.path.join(GOLDEN, "fig1_alternating.json")) as f:
+        g = json.load(f)
+    names = list(g["points"].keys())
+    x = np.array([g["points"][a] for a in names], np.int64)
+    n = len(x)
+    D = np.zeros((n, 8), np.int32)
+    D[:, :n] = np.abs(x[:, None] - x[None, :])
+    return g, names, D
+
+
+# ------------------------------------------------------------------ P1 --
+
+@pytest.mark.parametrize("variant", ["pam_bruteforce", "pam", "fastpam1",
+                                     "fasterpam", "fastpam2"])
+def test_fig1_worked_example(variant):
+    """Fig. 1: from medoids {B, E} SWAP makes B->A (loss 7), then E->D
+    (loss 6), then stops."""
+    g, names, D = fig1()
+    idx = {a: i for i, a in enumerate(names)}
+    start = [idx[a] for a in g["start_medoids"]]
+    out = oracle.swap(D, start, variant=variant, n=6)
+    assert out["swaps"] == len(g["swaps"])
+    med = list(start)
+    for (delta, slot, cand), sw in zip(out["trace"], g["swaps"]):
+        assert med[slot] == idx[sw["remove"]]
+        assert cand == idx[sw["add"]]
+        med[slot] = cand
+        assert oracle.td(D, med, n=6) == sw["loss_after"]
+    assert out["td"] == g["swaps"][-1]["loss_after"]
+    assert out["td_bookkept"] == out["td"]
+    assert out["converged"]
+    if variant in ("pam_bruteforce", "pam", "fastpam1"):
+        assert out["iterations"] == out["swaps"] + 1
+
+
+def test_fig1_build_then_swap():
+    """BUILD on the Fig. 1 points: first medoid is the 1-medoid (C and D tie
+    at distance sum 14, lowest index wins), then the greedy step adds A;
+    SWAP then moves C -> D and reaches the loss 6 of Fig. 1."""
+    g, names, D = fig1()
+    med, tdb, steps = oracle.pam_build(D, 2, n=6)
+    bmed, bsteps = bf.greedy_build(D[:, :6], 2)
+    assert list(med) == bmed == [names.index("C"), names.index("A")]
+    assert tdb == 7 == bf.td(D[:, :6], med)
+    out = oracle.swap(D, med, variant="fastpam1", n=6)
+    assert out["td"] == g["swaps"][-1]["loss_after"]
+    assert out["swaps"] == 1 and out["iterations"] == 2
+
+
+# ------------------------------------------------------------------ P2 --
+
+def test_eval_matches_bruteforce_integer():
+    """Per candidate, min_i Delta(i, c) and its lowest slot from the
+    FastPAM1 decomposition (Eq. (7)), from PAM's change function (Eq. (5))
+    and from full TD recomputation all equal brute force exactly."""
+    for D in bf.tiny_instances(11, 150):
+        n = D.shape[0]
+        g = np.random.default_rng(n * 7 + int(D.sum()))
+        for k in range(1 if n > 2 else 2, n):
+            if k < 2:
+                continue
+            med = list(g.choice(n, size=k, replace=False))
+            dl = bf.swap_deltas(D, med)
+            want = dl.min(axis=0)
+            wslot = dl.argmin(axis=0)
+            wbest = bf.best_swap(D, med)
+            for method in ("fastpam1", "pam", "bruteforce"):
+                cd, cs, best = oracle.eval_swaps(D, med, method=method)
+                for c in range(n):
+                    if c in med:
+                        assert cs[c] == -1
+                        continue
+                    assert cd[c] == want[c], (method, n, k, c)
+                    assert cs[c] == wslot[c], (method, n, k, c)
+                assert best == (wbest[0], wbest[1], wbest[2]), method
+
+
+def test_eval_matches_bruteforce_float():
+    for D in bf.tiny_float_instances(12, 60):
+        n = D.shape[0]
+        g = np.random.default_rng(n)
+        for k in range(2, n):
+            med = list(g.choice(n, size=k, replace=False))
+            dl = bf.swap_deltas(D, med)
+            want = dl.min(axis=0)
+            scale = bf.td(D, med) + 1.0
+            cd, cs, best = oracle.eval_swaps(D, med, method="fastpam1")
+            for c in range(n):
+                if c in med:
+                    continue
+                assert abs(cd[c] - want[c]) <= 1e-12 * scale
+                # slot: exact argmin unless an exact-arithmetic tie
+                assert dl[cs[c], c] <= want[c] + 1e-12 * scale
+
+
+def test_swap_delta_single_pair():
+    for D in bf.tiny_instances(13, 60):
+        n = D.shape[0]
+        g = np.random.default_rng(n + 3)
+        k = int(g.integers(2, n))
+        med = list(g.choice(n, size=k, replace=False))
+        dl = bf.swap_deltas(D, med)
+        for i in range(k):
+            for c in range(n):
+                if c not in med:
+                    assert oracle.swap_delta(D, med, i, c) == dl[i, c]
+
+
+def test_cache_and_removal_loss():
+    """nearest / d_n / d_s are the two smallest (distance, slot) pairs; the
+    removal loss of slot i equals TD(M - m_i) - TD(M) (the loss of removing
+    the medoid and reassigning its points to their second nearest)."""
+    for D in bf.tiny_instances(14, 80):
+        n = D.shape[0]
+        g = np.random.default_rng(n + 5)
+        k = int(g.integers(2, n + 1))
+        med = list(g.choice(n, size=k, replace=False))
+        near, sec, dn, ds = oracle.cache(D, med)
+        bn, bdn, bds = bf.cache(D, med)
+        assert (near == bn).all() and (dn == bdn).all() and (ds == bds).all()
+        rl = oracle.removal_loss(near, dn, ds, k)
+        base = bf.td(D, med)
+        for i in range(k):
+            rest = med[:i] + med[i + 1:]
+            assert rl[i] == bf.td(D, rest) - base
+
+
+# --------------------------------------------------------------- P3-P5 --
+
+def test_fastpam1_equals_pam_trajectory():
+    """FastPAM1 makes exactly the swaps of PAM (Sec. 3.1) -- checked against
+    an independent brute-force steepest descent on integer data."""
+    for D in bf.tiny_instances(21, 120, n_lo=5, n_hi=11):
+        n = D.shape[0]
+        g = np.random.default_rng(n * 13)
+        k = int(g.integers(2, min(n, 5)))
+        start = list(g.choice(n, size=k, replace=False))
+        bmed, btrace = bf.steepest(D, start)
+        for variant in ("pam_bruteforce", "pam", "fastpam1"):
+            out = oracle.swap(D, start, variant=variant)
+            assert [tuple(t) for t in out["trace"]] == \
+                [(float(d), i, c) for d, i, c in btrace], variant
+            assert list(out["medoids"]) == bmed
+            assert out["iterations"] == out["swaps"] + 1
+
+
+@pytest.mark.parametrize("variant", ["fastpam1", "fastpam2", "fasterpam"])
+def test_monotone_and_locally_optimal(variant):
+    """TD strictly decreases at every accepted swap and the final medoids
+    admit no swap with Delta < 0 (Sec. 2)."""
+    insts = bf.tiny_instances(31, 60, n_lo=5, n_hi=11)
+    insts += [np.ascontiguousarray(M) for M in
+              bf.tiny_float_instances(32, 30, n_lo=5, n_hi=11)]
+    for D in insts:
+        n = D.shape[0]
+        g = np.random.default_rng(n * 17)
+        k = int(g.integers(2, min(n, 5)))
+        start = list(g.choice(n, size=k, replace=False))
+        out = oracle.swap(D, start, variant=variant)
+        med = list(start)
+        prev = bf.td(D, med)
+        for d, i, c in out["trace"]:
+            assert d < 0
+            med[i] = c
+            cur = bf.td(D, med)
+            assert abs((cur - prev) - d) <= 1e-9 * (1 + prev)
+            assert cur < prev
+            prev = cur
+        assert list(out["medoids"]) == med
+        assert abs(out["td"] - prev) <= 1e-9 * (1 + prev)
+        assert abs(out["td_bookkept"] - out["td"]) <= 1e-9 * (1 + prev)
+        assert bf.swap_deltas(D, med).min() >= -1e-9 * (1 + prev)
+        assert out["converged"]
+
+
+def test_fasterpam_scan_rule():
+    """Alg. 4 read as a cyclic scan: after the final swap at index p the
+    scan visits the other n - 1 indices without a swap, so the positions
+    visited are (absolute index of the last swap) + n."""
+    for D in bf.tiny_instances(33, 40, n_lo=6, n_hi=11):
+        n = D.shape[0]
+        g = np.random.default_rng(n)
+        k = int(g.integers(2, 5))
+        start = list(g.choice(n, size=k, replace=False))
+        out = oracle.swap(D, start, variant="fasterpam")
+        if out["swaps"] == 0:
+            assert out["visited"] == n and out["iterations"] == 1
+        else:
+            assert out["visited"] % n == (out["trace"][-1][2] + n) % n
+            # replay the scan with brute force to confirm eagerness
+            med = list(start)
+            pos = 0
+            for d, i, c in out["trace"]:
+                while pos % n != c:  # candidates before c did not improve
+                    p = pos % n
+                    if p not in med:
+                        assert bf.swap_deltas(D, med)[:, p].min() >= 0
+                    pos += 1
+                dl = bf.swap_deltas(D, med)[:, c]
+                assert dl.min() == d and int(dl.argmin()) == i
+                med[i] = c
+                pos += 1
+
+
+def test_fastpam2_first_swap_is_fastpam1_swap():
+    for D in bf.tiny_instances(41, 60, n_lo=6, n_hi=11):
+        n = D.shape[0]
+        g = np.random.default_rng(n * 3)
+        k = int(g.integers(2, 5))
+        start = list(g.choice(n, size=k, replace=False))
+        f1 = oracle.swap(D, start, variant="fastpam1", max_iter=1)
+        f2 = oracle.swap(D, start, variant="fastpam2", max_iter=1)
+        if f1["swaps"]:
+            assert f2["trace"][0] == f1["trace"][0]
+        else:
+            assert f2["swaps"] == 0
+
+
+# ------------------------------------------------------------------ P6 --
+
+def test_build_is_greedy_td():
+    """BUILD: the first medoid is the 1-medoid of Eq. (3); each further
+    medoid is argmin_c TD(M + c) (lowest index on ties); the bookkept TD
+    equals Eq. (2) after every step."""
+    insts = bf.tiny_instances(51, 90, n_lo=3, n_hi=12)
+    for D in insts:
+        n = D.shape[0]
+        for k in range(1, n + 1):
+            med, tdb, steps = oracle.pam_build(D, k)
+            bmed, bsteps = bf.greedy_build(D, k)
+            assert list(med) == bmed
+            assert np.allclose(steps, bsteps, rtol=0, atol=0)
+            assert tdb == bf.td(D, med)
+
+
+def test_build_float_bookkeeping():
+    for D in bf.tiny_float_instances(52, 40):
+        n = D.shape[0]
+        k = max(1, n // 3)
+        med, tdb, steps = oracle.pam_build(D, k)
+        assert abs(tdb - bf.td(D, med)) <= 1e-9 * (1 + tdb)
+        bmed, _ = bf.greedy_build(D, k)
+        assert list(med) == bmed
+
+
+# ------------------------------------------------------------------ P7 --
+
+def test_degenerate_k():
+    for D in bf.tiny_instances(61, 40, n_lo=3, n_hi=9):
+        n = D.shape[0]
+        # k = n: every point is a medoid
+        med, tdb, _ = oracle.pam_build(D, n)
+        assert tdb == 0 and sorted(med) == list(range(n))
+        out = oracle.swap(D, med, variant="fastpam1")
+        assert out["swaps"] == 0 and out["td"] == 0
+        # k = 1: BUILD gives the global optimum; SWAP from any medoid
+        # reaches it (the 1-medoid, lowest index on ties)
+        med1, td1, _ = oracle.pam_build(D, 1)
+        assert td1 == bf.optimum(D, 1)
+        for v in ("fastpam1", "fasterpam", "fastpam2", "pam"):
+            out = oracle.swap(D, [n - 1], variant=v)
+            assert out["td"] == td1
+
+
+def test_local_optimum_vs_enumeration():
+    """For k = 1..3 and n <= 12: the local optimum is never below the
+    global optimum; on metric data it is within the locality gap of 5
+    (Sec. 3.2, Arya et al.)."""
+    for D in bf.tiny_instances(71, 45, n_lo=5, n_hi=12,
+                               kinds=("grid1", "grid2")):
+        n = D.shape[0]
+        for k in (1, 2, 3):
+            if k >= n:
+                continue
+            opt = bf.optimum(D, k)
+            out = oracle.run(D, k, variant="fastpam1")
+            assert out["td"] >= opt
+            assert out["td"] <= 5 * opt + 1e-9
+
+
+def test_iteration_cap_reports_not_converged():
+    D = bf.tiny_instances(81, 1, n_lo=10, n_hi=10, kinds=("grid2",))[0]
+    start = [0, 1, 2]
+    full = oracle.swap(D, start, variant="fastpam1")
+    if full["swaps"] >= 1:
+        out = oracle.swap(D, start, variant="fastpam1", max_iter=1)
+        assert not out["converged"] and out["swaps"] == 1
+
+
+def test_thread_count_does_not_change_results():
+    from paper_2008_05171_gb300 import workloads as wl
+    X = wl.gmm_points(300, 4, 6, seed="t-threads")
+    D = wl.euclidean_f32(X)
+    med, _, _ = oracle.pam_build(D, 6)
+    a = oracle.eval_swaps(D, med)
+    oracle.set_threads(1)
+    try:
+        b = oracle.eval_swaps(D, med)
+    finally:
+        oracle.set_threads(os.cpu_count() or 1)
+    assert (a[0] == b[0]).all() and (a[1] == b[1]).all() and a[2] == b[2]
