@@ -1,0 +1,381 @@
+#!/usr/bin/env python3
+"""Benchmark of the k-medoids hot path on GB300.
+
+One step = one whole run of the method on one synthetic input resident in
+HBM: PAM BUILD (k greedy steps) + the per-point cache + FastPAM1 SWAP to
+convergence (best swap per pass, cache update after each swap), i.e.
+kmedoids_run() through the C ABI.  Default workload: n=20000 points, d=16
+float32 Gaussian mixture (100 clusters, centres U[-10,10]^16, sigma=1, equal
+weights), Euclidean float32 20000x20000 matrix (1.6 GB, larger than L2),
+k=100.  ``--workload gmm_50000`` runs the n=50000, k=200 mixture (10 GB).
+
+metric: Delta-TD point evaluations per second over the whole step (every
+(candidate, point) pair BUILD and SWAP evaluate), plus the full run time
+(ms_per_step) and the SWAP iteration time.  The roofline object covers the
+kernel with the largest share of the step.  Multi-GPU: replicas only (the
+method's passes are one sequential chain; each rank runs its own instance).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+WORKLOADS = {
+    "gmm_20000": dict(n=20000, d=16, centers=100, k=100, recipe="gmm_20000_points",
+                      desc="n=20000 d=16 f32 GMM (100 clusters, centres U[-10,10]^16, "
+                           "sigma=1, equal weights), Euclidean f32 20000x20000 matrix, "
+                           "k=100, BUILD + FastPAM1 SWAP to convergence"),
+    "gmm_50000": dict(n=50000, d=32, centers=200, k=200, recipe="gmm_50000_points",
+                      desc="n=50000 d=32 f32 GMM (200 clusters, centres U[-10,10]^32, "
+                           "sigma U[0.5,2], Dirichlet(1) weights), Euclidean f32 "
+                           "50000x50000 matrix (10 GB), k=200, BUILD + FastPAM1 SWAP "
+                           "to convergence"),
+}
+
+
+def load_json(path):
+    try:
+        with open(path) as f:
+            return json.load(f)
+    except Exception:
+        return None
+
+
+def peaks():
+    p = load_json(os.path.join(ROOT, "MEASURED_PEAKS.json"))
+    if p and p.get("hbm_gbs"):
+        return float(p["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def source_hash():
+    import hashlib
+    h = hashlib.sha256()
+    for f in ("km_stream.cu", "km_device.cuh"):
+        with open(os.path.join(ROOT, "paper_2008_05171_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            import tempfile
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index),
+                 "--query-gpu=clocks.sm,clocks.max.sm,power.draw,"
+                 "clocks_event_reasons.hw_slowdown,"
+                 "clocks_event_reasons.hw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_power_cap",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown",
+                 "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[3:7]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def make_input(wl_name, device):
+    """Synthetic matrix on the device (FP64 direct differences -> FP32)."""
+    from paper_2008_05171_gb300 import workloads as wl
+    spec = WORKLOADS[wl_name]
+    X = getattr(wl, spec["recipe"])()
+    D = wl.euclidean_f32_torch(X, device)
+    return D, spec
+
+
+def evals_of(n, k, res):
+    """(candidate, point) pairs evaluated by BUILD and SWAP in one run."""
+    build = sum((n - t) * n for t in range(k))
+    swap = res["iterations"] * (n - k) * n
+    return build, swap
+
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+    import paper_2008_05171_gb300.kmedoids as km
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    D, spec = make_input(args.workload, dev)
+    n, k = spec["n"], spec["k"]
+    code = km.KM_F32
+    opts = km.options(profile=True)
+    ws = km.workspace(n, k, code, opts, device=dev)
+    torch.cuda.synchronize()
+
+    def step(profile=True):
+        return km.run(D, k, ws=ws, labels=True, profile=profile)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clocks = Clocks(local_rank)
+    clocks.start()
+    stream = torch.cuda.current_stream()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    results = []
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for i in range(args.steps):
+        ev[i][0].record(stream)
+        results.append(step())
+        ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    ck = clocks.stop()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = float(sum(step_ms))
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+
+    evals = [sum(evals_of(n, k, r)) for r in results]
+    value = world * sum(evals) / (total_ms / 1e3)
+    r0 = results[-1]
+    # kernel shares and roofline of the dominant one
+    swap_launch_ms = r0["eval_ms"] / max(1, r0["eval_launches"])
+    build_launch_ms = r0["build_eval_ms"] / max(1, r0["build_launches"])
+    swap_bytes = (n - k) * n * 4
+    build_bytes = sum((n - t) * n * 4 for t in range(k)) / k
+    peak, peak_kind = peaks()
+    kern = {
+        "swap_eval": {"launch_ms": swap_launch_ms, "bytes": swap_bytes,
+                      "share_ms": r0["eval_ms"]},
+        "build_eval": {"launch_ms": build_launch_ms, "bytes": build_bytes,
+                       "share_ms": r0["build_eval_ms"]},
+    }
+    dom = max(kern, key=lambda x: kern[x]["share_ms"])
+    prof = load_json(os.path.join(ROOT, "profiles", "traffic.json")) or {}
+    traffic = None
+    ent = prof.get(dom)
+    if ent and ent.get("source_hash") == source_hash() and \
+            ent.get("workload") == args.workload:
+        traffic = ent.get("dram_bytes_per_launch")
+
+    def roof(name):
+        kk = kern[name]
+        ach = kk["bytes"] / (kk["launch_ms"] / 1e3) / 1e9
+        return {"bound": "hbm", "achieved": round(ach, 1), "peak": peak,
+                "unit": "GB/s", "frac": round(ach / peak, 4),
+                "peak_source": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)"
+                if peak_kind == "measured" else "fallback 6.8 TB/s",
+                "kernel": "k_stream<float,%s>" % ("SWAP" if name == "swap_eval" else "BUILD"),
+                "algorithmic_bytes_per_launch": kk["bytes"],
+                "avg_launch_ms": round(kk["launch_ms"], 5)}
+
+    roofline = roof(dom)
+    roofline["traffic"] = traffic
+    other = roof("swap_eval" if dom == "build_eval" else "build_eval")
+
+    # end to end: pinned host matrix -> device, run, results -> host
+    e2e = None
+    if not args.no_e2e:
+        Dh = torch.empty(D.shape, dtype=D.dtype, pin_memory=True)
+        Dh.copy_(D)
+        Dd = torch.empty_like(D)
+        med_h = torch.empty(k, dtype=torch.int32, pin_memory=True)
+        lab_h = torch.empty(n, dtype=torch.int32, pin_memory=True)
+        torch.cuda.synchronize()
+        e_ms, e_evals = 0.0, 0
+        for i in range(max(1, min(args.steps, 3))):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            Dd.copy_(Dh, non_blocking=True)
+            r = km.run(Dd, k, ws=ws, labels=True)
+            med_h.copy_(r["medoids"], non_blocking=True)
+            lab_h.copy_(r["labels"], non_blocking=True)
+            b.record(stream)
+            torch.cuda.synchronize()
+            e_ms += a.elapsed_time(b)
+            e_evals += sum(evals_of(n, k, r))
+        e2e = {"value": world * e_evals / (e_ms / 1e3), "unit": "point-evals/s",
+               "h2d_bytes_per_step": int(D.numel() * 4),
+               "d2h_bytes_per_step": int(4 * k + 4 * n + 8 * 8)}
+        del Dh, Dd
+
+    swap_iter_ms = r0["eval_ms"] / max(1, r0["eval_launches"])
+    line = {
+        "metric": "SWAP dTD point-evals/sec + full PAM run time (k=100/200); % HBM roofline",
+        "value": value, "unit": "point-evals/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32 (FP64 dTD sums)",
+        "data": "synthetic",
+        "config": {"workload": args.workload + ": " + spec["desc"],
+                   "n": n, "k": k, "matrix_bytes": int(D.numel() * 4),
+                   "l2": "matrix larger than L2 (no flush needed)",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "full_run_ms": total_ms / args.steps,
+        "swap_iterations": r0["iterations"], "swaps": r0["swaps"],
+        "swap_iter_ms": swap_iter_ms,
+        "swap_evals_per_s": (n - k) * n / (swap_iter_ms / 1e3),
+        "td": r0["td"],
+        "kernel_ms_per_step": {"build_eval": r0["build_eval_ms"],
+                               "swap_eval": r0["eval_ms"],
+                               "build_total": r0["build_ms"],
+                               "swap_total": r0["swap_ms"]},
+        "roofline": roofline, "roofline_other": other,
+        "gpu_launches": int(sum(r["kernel_launches"] for r in results)),
+        "clocks": ck, "e2e": e2e, "wall_s": wall,
+    }
+    if rank == 0 and not args.no_cpu_baseline and world == 1:
+        line["cpu_baseline"] = cpu_baseline(D, spec, args.cpu_seconds)
+    return line
+
+
+def cpu_baseline(D, spec, budget_s):
+    """The FP64 oracle on the host cores, on a bounded sample of the same
+    workload: BUILD gains of the first steps and FastPAM1 evaluation passes
+    from the BUILD medoids, as many as fit in about budget_s seconds."""
+    import oracle
+    n, k = spec["n"], spec["k"]
+    Dh = D.cpu().numpy()
+    threads = oracle.num_threads()
+    t0 = time.perf_counter()
+    evals = 0
+    prefix = []
+    steps = 0
+    while time.perf_counter() - t0 < budget_s / 2 and steps < k:
+        g = oracle.build_gains(Dh, prefix)
+        evals += (n - len(prefix)) * n
+        prefix.append(int(np.argmin(g)))
+        steps += 1
+    passes = 0
+    chosen = set(prefix)
+    rest = [i for i in range(n) if i not in chosen][:k - len(prefix)]
+    med = np.array(prefix + rest, np.int32)
+    while time.perf_counter() - t0 < budget_s or passes == 0:
+        oracle.eval_swaps(Dh, med, method="fastpam1")
+        evals += (n - k) * n
+        passes += 1
+    dt = time.perf_counter() - t0
+    return {"value": evals / dt, "unit": "point-evals/s", "cores": threads,
+            "kind": "oracle",
+            "sample": "%d BUILD steps + %d FastPAM1 evaluation passes of the same "
+                      "n=%d k=%d matrix (FP64 C oracle, OpenMP over candidates), %.1f s"
+                      % (steps, passes, n, k, dt)}
+
+
+def run_reference(args, rank, world):
+    """The oracle as the reference arm: timed on the host cores on a bounded
+    sample of the workload per step (rank 0 only)."""
+    if rank != 0:
+        return None
+    import torch
+    spec = WORKLOADS[args.workload]
+    from paper_2008_05171_gb300 import workloads as wl
+    X = getattr(wl, spec["recipe"])()
+    dev = torch.device("cuda", 0) if torch.cuda.is_available() else torch.device("cpu")
+    if dev.type == "cuda":
+        D = wl.euclidean_f32_torch(X, dev)
+    else:
+        D = torch.from_numpy(wl.euclidean_f32(X))
+    budget = max(2.0, 60.0 / max(1, args.steps + args.warmup))
+    for _ in range(args.warmup):
+        cpu_baseline(D, spec, budget / 4)
+    vals, secs = [], []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        cb = cpu_baseline(D, spec, budget)
+        secs.append(time.perf_counter() - t0)
+        vals.append(cb["value"])
+    v = float(np.mean(vals))
+    cb["value"] = v
+    return {"impl": "reference", "metric": "SWAP dTD point-evals/sec + full PAM run time "
+            "(k=100/200); % HBM roofline", "value": v, "unit": "point-evals/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * float(np.mean(secs)), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload + ": " + spec["desc"], "n": spec["n"],
+                       "k": spec["k"]},
+            "cpu_baseline": cb,
+            "e2e": {"value": v, "unit": "point-evals/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="gmm_20000", choices=sorted(WORKLOADS))
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        if args.impl == "ours":
+            torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl" if args.impl == "ours" else "gloo")
+    if args.impl == "reference":
+        line = run_reference(args, rank, world)
+    else:
+        line = run_ours(args, rank, world, local_rank)
+    if rank == 0 and line is not None:
+        print(json.dumps(line))
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,186 @@
+/*
+ * kmedoids.h -- C ABI of the GB300 (sm_103a) k-medoids library
+ * (libkmedoids.so).
+ *
+ * The library implements the hot path of Schubert & Rousseeuw, "Fast and
+ * Eager k-Medoids Clustering: O(k) Runtime Improvement of the PAM, CLARA,
+ * and CLARANS Algorithms" (arXiv 2008.05171):
+ *
+ *   - PAM BUILD (Alg. 1), the greedy initialisation;
+ *   - the per-point cache nearest / d_n / d_s (Sec. 2) and the removal loss
+ *     Delta^{-m_i} (Eq. (7));
+ *   - the FastPAM1 SWAP evaluation (Alg. 3, Eq. (7)): Delta TD of every
+ *     (medoid slot i, non-medoid candidate c) in O(n) per candidate;
+ *   - the best swap, its application and the cache update (Alg. 3);
+ *   - FastPAM2 (Sec. 3.2) and the eager FasterPAM (Alg. 4).
+ *
+ * Data conventions (all entry points):
+ *   D       dissimilarity matrix, n rows of ld elements, row-major, DEVICE
+ *           memory owned by the caller.  d(x_o, x_c) = D[c*ld + o].  D must
+ *           be symmetric with a zero diagonal and finite entries >= 0 (the
+ *           paper's symmetric special case, Sec. 1.2); the library does not
+ *           scan D to check this.  Columns n..ld-1 are padding and never
+ *           read as distances.  The base address must be 16-byte aligned and
+ *           ld a multiple of 4 (rows are streamed with 16-byte bulk copies);
+ *           otherwise the call returns KM_E_INVALID.
+ *   dtype   KM_I32 (int32 distances; sums in int64, results exact) or
+ *           KM_F32 (float32 distances; Delta TD and TD sums in FP64).
+ *   medoids int32 point indices in SLOT order, DEVICE memory.  A swap puts
+ *           the new medoid into the removed medoid's slot.  Labels are slots.
+ *   ws      DEVICE workspace of at least kmedoids_workspace_size() bytes,
+ *           256-byte aligned, owned by the caller; the library never
+ *           allocates device memory and keeps no state between calls.
+ *   stream  a cudaStream_t (NULL = legacy default stream).  Every call
+ *           enqueues its work on this stream and synchronises it before
+ *           returning (the result struct is filled on the host).
+ *   Ties    nearest medoid = lowest slot among equal distances; per
+ *           candidate the lowest slot; the applied swap is the
+ *           lexicographic minimum of (Delta, slot, candidate); BUILD takes
+ *           the lowest point index among equal gains.
+ *
+ * Errors: every call returns a km_status and never aborts the process.
+ * Arguments are validated before any work is enqueued.  A device-side wait
+ * that exceeds its time limit returns KM_E_TIMEOUT.  kmedoids_last_error()
+ * returns a thread-local message describing the last failure.
+ */
+#ifndef KMEDOIDS_H_
+#define KMEDOIDS_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  KM_OK = 0,
+  KM_E_INVALID = 1,       /* bad argument (sizes, pointers, alignment) */
+  KM_E_WORKSPACE = 2,     /* workspace smaller than required */
+  KM_E_CUDA = 3,          /* a CUDA runtime call failed */
+  KM_E_NOT_CONVERGED = 4, /* max_iter reached; results are the best so far */
+  KM_E_TIMEOUT = 5,       /* a device-side wait gave up */
+  KM_E_NUMERIC = 6,       /* non-finite value met where a distance was due */
+  KM_E_UNSUPPORTED = 7    /* valid but outside this build's limits */
+} km_status;
+
+typedef enum { KM_I32 = 0, KM_F32 = 1 } km_dtype;
+
+typedef enum {
+  KM_FASTPAM1 = 0, /* best swap per iteration (Alg. 3); same swaps as PAM */
+  KM_FASTPAM2 = 1, /* best swap per slot, up to k swaps per iteration */
+  KM_FASTERPAM = 2 /* eager: first improving candidate in scan order (Alg. 4) */
+} km_variant;
+
+/* Options.  Zero-initialise and call km_default_options() first. */
+typedef struct km_options {
+  int32_t variant;        /* km_variant */
+  int32_t max_iter;       /* evaluation passes (FasterPAM: full scans);
+                             <= 0 means 100*k + 100 */
+  double tol;             /* a swap is applied iff Delta < -tol (default 0) */
+  double fastpam2_tol;    /* FastPAM2 applies an additional swap iff its
+                             recomputed Delta < -fastpam2_tol * |Delta*| */
+  int32_t rows_per_tile;  /* candidate rows per CTA tile; 0 = automatic */
+  int32_t profile;        /* nonzero: time kernels with CUDA events */
+  int32_t trace_capacity; /* entries available in the trace arrays */
+  int32_t reserved0;
+  /* HOST arrays (may be NULL) receiving every applied swap in order. */
+  double *trace_delta;
+  int32_t *trace_slot;
+  int32_t *trace_cand;
+  int64_t *trace_time_ns; /* device %globaltimer when the swap was applied */
+  double *build_gains;    /* HOST, k entries: BUILD step gains (step 0 = the
+                             first medoid's distance sum) */
+} km_options;
+
+/* Results, filled on the HOST before the call returns. */
+typedef struct km_result {
+  double td;            /* final TD = sum of d_n, recomputed on the device
+                           (FP64 for KM_F32, exact for KM_I32) */
+  int64_t td_i64;       /* final TD as int64 (KM_I32 only) */
+  double td_bookkept;   /* initial TD + sum of the applied Delta values */
+  double td_initial;    /* TD of the starting medoids (after BUILD) */
+  int32_t iterations;   /* evaluation passes (FasterPAM: scans started) */
+  int32_t swaps;        /* swaps applied */
+  int32_t status;       /* km_status of the call */
+  int32_t build_steps;  /* medoids chosen by BUILD */
+  int64_t visited;      /* FasterPAM: scan positions visited */
+  /* profile != 0 only (milliseconds of device time, CUDA events): */
+  double build_ms;      /* whole BUILD */
+  double swap_ms;       /* whole SWAP phase (cache init + iterations) */
+  double eval_ms;       /* sum over the SWAP evaluation kernel launches */
+  int32_t eval_launches;
+  int32_t build_launches; /* BUILD evaluation kernel launches */
+  double build_eval_ms;   /* sum over the BUILD evaluation kernel launches */
+  int64_t kernel_launches; /* kernels this call launched (all phases) */
+} km_result;
+
+/* Fill *o with the defaults (FastPAM1, tol 0, automatic tiles). */
+void km_default_options(km_options *o);
+
+/* Bytes of device workspace the calls below need for (n, k, dtype, options).
+ * Returns 0 for invalid sizes. */
+size_t kmedoids_workspace_size(int64_t n, int32_t k, int32_t dtype,
+                               const km_options *opts);
+
+/* PAM BUILD (Alg. 1): k greedy steps.  Step 0 takes the point with the
+ * smallest distance sum (the 1-medoid, Eq. (3)); each further step adds the
+ * non-medoid c minimising sum_o min(d(o,c) - d_n(o), 0), the exact TD change
+ * of adding c (the point c itself included).  Writes k medoids (slot order =
+ * order chosen) to medoids_out (DEVICE).  res->td = TD of the result. */
+km_status kmedoids_build(const void *D, int32_t dtype, int64_t n, int64_t ld,
+                         int32_t k, int32_t *medoids_out,
+                         const km_options *opts, km_result *res, void *ws,
+                         size_t ws_bytes, void *stream);
+
+/* SWAP (Alg. 3 / Sec. 3.2 / Alg. 4, by opts->variant) from the k medoids in
+ * medoids_inout (DEVICE, updated in place) until no swap has Delta < -tol
+ * or max_iter passes were made (KM_E_NOT_CONVERGED).  labels_out (DEVICE,
+ * n entries, may be NULL) receives each point's nearest slot at exit.
+ * k = 1 swaps directly to the 1-medoid (Eq. (3)); k = n does nothing. */
+km_status kmedoids_swap(const void *D, int32_t dtype, int64_t n, int64_t ld,
+                        int32_t k, int32_t *medoids_inout, int32_t *labels_out,
+                        const km_options *opts, km_result *res, void *ws,
+                        size_t ws_bytes, void *stream);
+
+/* BUILD followed by SWAP; medoids_out (DEVICE, k entries). */
+km_status kmedoids_run(const void *D, int32_t dtype, int64_t n, int64_t ld,
+                       int32_t k, int32_t *medoids_out, int32_t *labels_out,
+                       const km_options *opts, km_result *res, void *ws,
+                       size_t ws_bytes, void *stream);
+
+/* One FastPAM1 evaluation pass (Alg. 3, Eq. (7)) for the medoids given
+ * (DEVICE, k entries, unchanged): for every point c, cand_delta[c] (DEVICE
+ * double, n entries, may be NULL) = min_i Delta(i, c) and cand_slot[c]
+ * (DEVICE int32, may be NULL) = the lowest slot attaining it; medoid rows
+ * get +inf and -1.  best (HOST) receives the lexicographic minimum
+ * (Delta, slot, candidate) over all non-medoids; with k = n it is
+ * (+inf, -1, -1).  Requires 2 <= k <= n. */
+km_status kmedoids_eval_swaps(const void *D, int32_t dtype, int64_t n,
+                              int64_t ld, int32_t k, const int32_t *medoids,
+                              double *cand_delta, int32_t *cand_slot,
+                              double *best_delta, int32_t *best_slot,
+                              int32_t *best_cand, void *ws, size_t ws_bytes,
+                              void *stream);
+
+/* The per-point cache (Sec. 2) for the medoids given: near/sec (DEVICE
+ * int32, n entries) = nearest and second-nearest slot, dn/ds (DEVICE, n
+ * entries, D's dtype) = their distances; removal (DEVICE double, k
+ * entries, may be NULL) = Delta^{-m_i} of Eq. (7).  For k = 1, sec = -1 and
+ * ds = the dtype's largest value.  Requires 1 <= k <= n. */
+km_status kmedoids_cache(const void *D, int32_t dtype, int64_t n, int64_t ld,
+                         int32_t k, const int32_t *medoids, int32_t *near,
+                         int32_t *sec, void *dn, void *ds, double *removal,
+                         void *ws, size_t ws_bytes, void *stream);
+
+/* Thread-local description of the last failure ("" if none). */
+const char *kmedoids_last_error(void);
+
+/* Library version string. */
+const char *kmedoids_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* KMEDOIDS_H_ */

@@ -11,7 +11,8 @@ k-Medoids Clustering" (arXiv 2008.05171):
 * ``td``            -- Eq. (2) (TD objective), labels = lowest nearest slot.
 * ``cache``         -- the per-point cache nearest / d_n / d_s of Sec. 2.
 * ``removal_loss``  -- Delta^{-m_i} of Eq. (7).
-* ``build``         -- Alg. 1 (PAM BUILD), self term included in each gain.
+* ``pam_build``     -- Alg. 1 (PAM BUILD), self term included in each gain;
+                       ``build_gains`` one step of it given a prefix.
 * ``eval_swaps``    -- one SWAP evaluation: brute force (Eq. (2) recomputed),
                        PAM (Alg. 2 + Eq. (5)) or FastPAM1 (Alg. 3 + Eq. (7)).
 * ``swap_delta``    -- Delta of one (slot, candidate) swap by Eq. (5).
@@ -77,6 +78,8 @@ def _lib():
             lib.oracle_swap.restype = i32
             lib.oracle_swap.argtypes = [P, i32, i64, i64, i32, P, i32, i32,
                                         f64, f64, P, P, i32, P, P, P]
+            lib.oracle_build_gains.restype = None
+            lib.oracle_build_gains.argtypes = [P, i32, i64, i64, P, i32, P]
             lib.oracle_num_threads.restype = i32
             lib.oracle_set_threads.argtypes = [i32]
             _LIB = lib
@@ -152,6 +155,16 @@ def pam_build(D, k, n=None):
     steps = np.empty(k, np.float64)
     _lib().oracle_build(_p(D), code, n, ld, k, _p(med), _p(tdv), _p(steps))
     return med, float(tdv[0]), steps
+
+
+def build_gains(D, prefix, n=None):
+    """Gains of every candidate for the BUILD step after ``prefix`` (Alg. 1);
+    with an empty prefix, the distance sums of step 0.  Medoids get +inf."""
+    D, code, n, ld = _mat(D, n)
+    med = _med(prefix) if len(prefix) else np.zeros(1, np.int32)
+    g = np.empty(n, np.float64)
+    _lib().oracle_build_gains(_p(D), code, n, ld, _p(med), len(prefix), _p(g))
+    return g
 
 
 def eval_swaps(D, medoids, method="fastpam1", n=None):

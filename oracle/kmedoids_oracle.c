@@ -217,6 +217,44 @@ int oracle_build(const void *D, int dtype, int64_t n, int64_t ld, int k,
   return 0;
 }
 
+/* One BUILD step of Alg. 1 given the medoids chosen so far (t of them):
+ * gains[c] = sum_o min(d(o,c) - d_n(o), 0) for non-medoids (t > 0), or the
+ * distance sum of c (t = 0); medoids get +inf. */
+void oracle_build_gains(const void *D, int dtype, int64_t n, int64_t ld,
+                        const int32_t *med, int t, double *gains) {
+  or_mat m = mk(D, dtype, n, ld);
+  double *dnear = (double *)malloc(sizeof(double) * (size_t)n);
+  char *is_med = (char *)calloc((size_t)n, 1);
+  for (int j = 0; j < t; j++) is_med[med[j]] = 1;
+  for (int64_t o = 0; o < n; o++) {
+    double b = OR_INF;
+    for (int j = 0; j < t; j++) {
+      double v = od(&m, o, med[j]);
+      if (v < b) b = v;
+    }
+    dnear[o] = b;
+  }
+#pragma omp parallel for schedule(static)
+  for (int64_t c = 0; c < n; c++) {
+    if (is_med[c]) {
+      gains[c] = OR_INF;
+      continue;
+    }
+    double g = 0.0;
+    for (int64_t o = 0; o < n; o++) {
+      if (t == 0) {
+        g += od(&m, o, c);
+      } else {
+        double dd = od(&m, o, c) - dnear[o];
+        if (dd < 0.0) g += dd;
+      }
+    }
+    gains[c] = g;
+  }
+  free(dnear);
+  free(is_med);
+}
+
 /* ------------------------------------------------------------------------
  * One evaluation of all swaps (medoid slot i, non-medoid candidate c).
  * Outputs, per point c: cand_delta[c] = min_i Delta(i,c) and cand_slot[c] =

@@ -1,0 +1,706 @@
+// km_api.cu -- the C ABI of libkmedoids (declared in include/kmedoids.h):
+// argument checks, workspace carving and the host-side enqueue loops of
+// BUILD (Alg. 1) and SWAP (Alg. 3 FastPAM1, Sec. 3.2 FastPAM2, Alg. 4
+// FasterPAM).  All arithmetic of the method runs in the kernels of
+// km_stream.cu and km_points.cu; this file only orders launches and reads
+// the device state record between batches of passes.
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/kmedoids.h"
+#include "km_device.cuh"
+#include "km_internal.h"
+
+using namespace km;
+
+namespace {
+
+thread_local std::string g_err;
+
+km_status fail(km_status s, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return s;
+}
+
+#define KM_CUDA(call)                                                                   \
+  do {                                                                                  \
+    cudaError_t e_ = (call);                                                            \
+    if (e_ != cudaSuccess)                                                              \
+      return fail(KM_E_CUDA, "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_),    \
+                  __FILE__, __LINE__);                                                  \
+  } while (0)
+
+// a kernel launch through a launcher returning cudaError_t, counted
+#define KM_LAUNCH(ctx, call) \
+  do {                       \
+    KM_CUDA(call);           \
+    ++(ctx).launches;        \
+  } while (0)
+
+size_t al(size_t x) { return (x + 255) / 256 * 256; }
+int64_t rup(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
+
+struct WsLayout {
+  size_t st, med, is_med, near, sec, dn, ds, bdn, removal, td2, partials, slot_partials,
+      slot_best, fp2_order, win_delta, win_slot, trace, gains, cand_gain, total;
+  int64_t n_pad;
+  int k_pad;
+  int trace_cap;
+};
+
+bool make_ws(int64_t n, int k, const km_options* o, WsLayout* L) {
+  if (n <= 0 || k <= 0 || k > n || n > (int64_t)INT32_MAX - 2 * kChunk) return false;
+  const int64_t n_pad = rup(n, kChunk);
+  const int k_pad = (int)rup(k, 32);
+  const int variant = o ? o->variant : KM_FASTPAM1;
+  const int cap = (o && o->trace_capacity > 0) ? o->trace_capacity : 0;
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    size_t r = off;
+    off += al(bytes);
+    return r;
+  };
+  L->st = take(512);
+  L->med = take(4 * (size_t)k_pad);
+  L->is_med = take((size_t)n_pad);
+  L->near = take(4 * (size_t)n_pad);
+  L->sec = take(4 * (size_t)n_pad);
+  L->dn = take(4 * (size_t)n_pad);
+  L->ds = take(4 * (size_t)n_pad);
+  L->bdn = take(4 * (size_t)n_pad);
+  L->removal = take(8 * 2 * (size_t)k_pad);
+  L->td2 = take(16);
+  L->partials = take(16 * (size_t)kMaxGrid);
+  L->slot_partials = take(variant == KM_FASTPAM2 ? 16 * (size_t)kMaxGrid * k : 0);
+  L->slot_best = take(16 * (size_t)k);
+  L->fp2_order = take(4 * (size_t)k);
+  L->win_delta = take(8 * (size_t)kMaxGrid * kMaxRows);
+  L->win_slot = take(4 * (size_t)kMaxGrid * kMaxRows);
+  L->trace = take(sizeof(TraceRec) * (size_t)(cap > 0 ? cap : 1));
+  L->gains = take(8 * (size_t)k);
+  L->cand_gain = take(8 * (size_t)n_pad);
+  L->total = off;
+  L->n_pad = n_pad;
+  L->k_pad = k_pad;
+  L->trace_cap = cap;
+  return true;
+}
+
+struct Ctx {
+  const void* D;
+  int dtype;
+  int n;
+  long long ld;
+  int k;
+  unsigned char* ws;
+  WsLayout L;
+  cudaStream_t s;
+  km_options opt;
+  int sms;
+  long long launches = 0;
+  KmState* st() const { return reinterpret_cast<KmState*>(ws + L.st); }
+  template <class P>
+  P* at(size_t off) const {
+    return reinterpret_cast<P*>(ws + off);
+  }
+};
+
+km_status check_common(const void* D, int32_t dtype, int64_t n, int64_t ld, int32_t k, void* ws,
+                       size_t ws_bytes, const km_options* opts, Ctx* c) {
+  if (!D) return fail(KM_E_INVALID, "D is NULL");
+  if (dtype != KM_I32 && dtype != KM_F32) return fail(KM_E_INVALID, "unknown dtype %d", dtype);
+  if (n <= 0) return fail(KM_E_INVALID, "n must be positive (got %lld)", (long long)n);
+  if (n > (int64_t)INT32_MAX - 2 * kChunk) return fail(KM_E_INVALID, "n too large");
+  if (k < 1 || k > n) return fail(KM_E_INVALID, "need 1 <= k <= n (k=%d, n=%lld)", k, (long long)n);
+  if (ld < n) return fail(KM_E_INVALID, "ld (%lld) < n (%lld)", (long long)ld, (long long)n);
+  if (ld % 4 != 0) return fail(KM_E_INVALID, "ld (%lld) must be a multiple of 4", (long long)ld);
+  if (reinterpret_cast<uintptr_t>(D) % 16 != 0) return fail(KM_E_INVALID, "D must be 16-byte aligned");
+  if (!ws) return fail(KM_E_INVALID, "workspace is NULL");
+  if (reinterpret_cast<uintptr_t>(ws) % 256 != 0) return fail(KM_E_INVALID, "workspace must be 256-byte aligned");
+  km_options def;
+  km_default_options(&def);
+  c->opt = opts ? *opts : def;
+  if (c->opt.variant < 0 || c->opt.variant > 2) return fail(KM_E_INVALID, "unknown variant %d", c->opt.variant);
+  if (!(c->opt.tol >= 0.0)) return fail(KM_E_INVALID, "tol must be >= 0");
+  if (!(c->opt.fastpam2_tol >= 0.0)) return fail(KM_E_INVALID, "fastpam2_tol must be >= 0");
+  if (c->opt.rows_per_tile != 0 && c->opt.rows_per_tile != 1 && c->opt.rows_per_tile != 2 &&
+      c->opt.rows_per_tile != 4 && c->opt.rows_per_tile != 8 && c->opt.rows_per_tile != 16)
+    return fail(KM_E_INVALID, "rows_per_tile must be 0, 1, 2, 4, 8 or 16");
+  if (c->opt.trace_capacity < 0) return fail(KM_E_INVALID, "trace_capacity < 0");
+  if (!make_ws(n, k, &c->opt, &c->L)) return fail(KM_E_INVALID, "invalid sizes");
+  if (ws_bytes < c->L.total)
+    return fail(KM_E_WORKSPACE, "workspace too small: %zu < %zu bytes", ws_bytes, c->L.total);
+  c->D = D;
+  c->dtype = dtype;
+  c->n = (int)n;
+  c->ld = ld;
+  c->k = k;
+  c->ws = static_cast<unsigned char*>(ws);
+  c->sms = device_sm_count();
+  if (c->sms <= 0) return fail(KM_E_CUDA, "no CUDA device");
+  if (c->opt.max_iter <= 0) c->opt.max_iter = 100 * k + 100;
+  return KM_OK;
+}
+
+StreamArgs stream_args(const Ctx& c) {
+  StreamArgs a;
+  memset(&a, 0, sizeof(a));
+  a.D = c.D;
+  a.ld = c.ld;
+  a.n = c.n;
+  a.k = c.k;
+  a.k_pad = c.L.k_pad;
+  a.n_pad = (int)c.L.n_pad;
+  a.is_med = c.at<uint8_t>(c.L.is_med);
+  a.dn = c.at<void>(c.L.dn);
+  a.ds = c.at<void>(c.L.ds);
+  a.near = c.at<int32_t>(c.L.near);
+  a.bdn = c.at<void>(c.L.bdn);
+  a.removal = c.at<void>(c.L.removal);
+  a.td2 = c.at<void>(c.L.td2);
+  a.st = c.st();
+  a.partials = c.at<void>(c.L.partials);
+  a.slot_partials = c.at<void>(c.L.slot_partials);
+  a.slot_best = c.at<void>(c.L.slot_best);
+  a.fp2_order = c.at<int32_t>(c.L.fp2_order);
+  a.tol = c.opt.tol;
+  return a;
+}
+
+PointArgs point_args(const Ctx& c) {
+  PointArgs a;
+  memset(&a, 0, sizeof(a));
+  a.D = c.D;
+  a.ld = c.ld;
+  a.n = c.n;
+  a.k = c.k;
+  a.k_pad = c.L.k_pad;
+  a.n_pad = (int)c.L.n_pad;
+  a.med = c.at<int32_t>(c.L.med);
+  a.is_med = c.at<uint8_t>(c.L.is_med);
+  a.near = c.at<int32_t>(c.L.near);
+  a.sec = c.at<int32_t>(c.L.sec);
+  a.dn = c.at<void>(c.L.dn);
+  a.ds = c.at<void>(c.L.ds);
+  a.bdn = c.at<void>(c.L.bdn);
+  a.removal = c.at<void>(c.L.removal);
+  a.td2 = c.at<void>(c.L.td2);
+  a.st = c.st();
+  a.trace = c.at<void>(c.L.trace);
+  a.trace_cap = c.L.trace_cap;
+  a.partials = c.at<void>(c.L.partials);
+  a.slot_best = c.at<void>(c.L.slot_best);
+  a.fp2_order = c.at<int32_t>(c.L.fp2_order);
+  a.gains = c.at<double>(c.L.gains);
+  a.fp2_tol = c.opt.fastpam2_tol;
+  return a;
+}
+
+int grid_for(const Ctx& c, int rows) {
+  int g = c.sms;
+  const int need = (c.n + rows - 1) / rows;
+  if (g > need) g = need;
+  if (g > kMaxGrid) g = kMaxGrid;
+  if (g < 1) g = 1;
+  return g;
+}
+
+// Event pairs around kernel launches, summed after the final sync.
+struct Timer {
+  bool on = false;
+  std::vector<cudaEvent_t> ev;
+  size_t used = 0;
+  cudaStream_t s = nullptr;
+  void start(bool enable, cudaStream_t st) {
+    on = enable;
+    s = st;
+  }
+  int mark() {  // returns event index or -1
+    if (!on) return -1;
+    if (used == ev.size()) {
+      if (ev.size() >= 16384) return -1;
+      cudaEvent_t e;
+      if (cudaEventCreate(&e) != cudaSuccess) return -1;
+      ev.push_back(e);
+    }
+    cudaEventRecord(ev[used], s);
+    return (int)used++;
+  }
+  double ms(int a, int b) const {
+    if (a < 0 || b < 0) return 0.0;
+    float v = 0.f;
+    cudaEventElapsedTime(&v, ev[a], ev[b]);
+    return v;
+  }
+  ~Timer() {
+    for (auto e : ev) cudaEventDestroy(e);
+  }
+};
+
+km_status read_state(const Ctx& c, KmState* h) {
+  KM_CUDA(cudaMemcpyAsync(h, c.st(), sizeof(KmState), cudaMemcpyDeviceToHost, c.s));
+  KM_CUDA(cudaStreamSynchronize(c.s));
+  if (h->error) return fail((km_status)h->error, "device reported status %d (a wait timed out)", h->error);
+  return KM_OK;
+}
+
+km_status reset_state(const Ctx& c) {
+  KmState h;
+  memset(&h, 0, sizeof(h));
+  h.last = -1;
+  KM_CUDA(cudaMemcpyAsync(c.st(), &h, sizeof(h), cudaMemcpyHostToDevice, c.s));
+  return KM_OK;
+}
+
+// ------------------------------------------------------------------ BUILD
+km_status do_build(Ctx& c, Timer& tm, std::vector<std::pair<int, int>>& ev, km_result* res) {
+  KM_CUDA(cudaMemsetAsync(c.at<void>(c.L.is_med), 0, (size_t)c.L.n_pad, c.s));
+  StreamConfig cfg;
+  if (!stream_config(kModeBuild, c.k, 0, c.opt.rows_per_tile, &cfg))
+    return fail(KM_E_UNSUPPORTED, "no BUILD kernel configuration fits");
+  const int grid = grid_for(c, cfg.rows);
+  StreamArgs sa = stream_args(c);
+  PointArgs pa = point_args(c);
+  for (int step = 0; step < c.k; ++step) {
+    sa.build_first = (step == 0);
+    pa.build_first = (step == 0);
+    const int e0 = tm.mark();
+    KM_LAUNCH(c, launch_stream(c.dtype, kModeBuild, cfg, grid, sa, c.s));
+    const int e1 = tm.mark();
+    ev.push_back({e0, e1});
+    KM_LAUNCH(c, launch_build_commit(c.dtype, pa, c.s));
+  }
+  if (res) res->build_launches = c.k;
+  return KM_OK;
+}
+
+// ------------------------------------------------------------------- SWAP
+km_status swap_setup(Ctx& c) {
+  KM_CUDA(cudaMemsetAsync(c.at<void>(c.L.is_med), 0, (size_t)c.L.n_pad, c.s));
+  KM_CUDA(cudaMemsetAsync(c.at<void>(c.L.removal), 0, 16 * (size_t)c.L.k_pad, c.s));
+  KM_CUDA(cudaMemsetAsync(c.at<void>(c.L.td2), 0, 16, c.s));
+  PointArgs pa = point_args(c);
+  KM_LAUNCH(c, launch_mark_medoids(pa, c.s));
+  KM_LAUNCH(c, launch_cache_init(c.dtype, pa, c.s));
+  return KM_OK;
+}
+
+km_status swap_k1(Ctx& c, KmState* h) {
+  // k = 1: the best single swap is the 1-medoid (Eq. (3)); compare the
+  // distance sums of every point with the current medoid's.
+  StreamConfig cfg;
+  if (!stream_config(kModeBuild, 1, 0, c.opt.rows_per_tile, &cfg))
+    return fail(KM_E_UNSUPPORTED, "no kernel configuration fits");
+  KM_CUDA(cudaMemsetAsync(c.at<void>(c.L.is_med), 0, (size_t)c.L.n_pad, c.s));
+  StreamArgs sa = stream_args(c);
+  sa.build_first = 1;
+  sa.cand_gain = c.at<double>(c.L.cand_gain);
+  KM_LAUNCH(c, launch_stream(c.dtype, kModeBuild, cfg, grid_for(c, cfg.rows), sa, c.s));
+  int32_t m = 0;
+  KM_CUDA(cudaMemcpyAsync(&m, c.at<int32_t>(c.L.med), 4, cudaMemcpyDeviceToHost, c.s));
+  KM_CUDA(cudaStreamSynchronize(c.s));
+  double sm = 0.0;
+  KM_CUDA(cudaMemcpyAsync(&sm, c.at<double>(c.L.cand_gain) + m, 8, cudaMemcpyDeviceToHost, c.s));
+  km_status e = read_state(c, h);
+  if (e != KM_OK) return e;
+  const double best = h->build_gain_d;
+  const int cb = h->build_cand;
+  int iters = 1, swaps = 0;
+  if (cb != m && cb >= 0 && best - sm < -c.opt.tol && c.opt.max_iter >= 1) {
+    KM_CUDA(cudaMemcpyAsync(c.at<int32_t>(c.L.med), &cb, 4, cudaMemcpyHostToDevice, c.s));
+    swaps = 1;
+    iters = (c.opt.max_iter >= 2) ? 2 : 1;
+    if (c.L.trace_cap > 0) {
+      TraceRec tr;
+      memset(&tr, 0, sizeof(tr));
+      tr.d = best - sm;
+      tr.di = (long long)(best - sm);
+      tr.slot = 0;
+      tr.cand = cb;
+      KM_CUDA(cudaMemcpyAsync(c.at<TraceRec>(c.L.trace), &tr, sizeof(tr), cudaMemcpyHostToDevice, c.s));
+    }
+  }
+  KM_CUDA(cudaStreamSynchronize(c.s));
+  // fresh state + cache for labels and the exact TD
+  km_status r = reset_state(c);
+  if (r != KM_OK) return r;
+  r = swap_setup(c);
+  if (r != KM_OK) return r;
+  r = read_state(c, h);
+  if (r != KM_OK) return r;
+  h->iter = iters;
+  h->swaps = swaps;
+  h->ntrace = swaps;
+  h->done = (swaps == 0 || c.opt.max_iter >= 2) ? 1 : 0;
+  return KM_OK;
+}
+
+km_status do_swap(Ctx& c, Timer& tm, std::vector<std::pair<int, int>>& ev, KmState* h,
+                  km_result* res) {
+  km_status r = swap_setup(c);
+  if (r != KM_OK) return r;
+  if (c.k == 1) return swap_k1(c, h);
+  const int variant = c.opt.variant;
+  const int flavour = variant == KM_FASTPAM2 ? kFastPAM2 : (variant == KM_FASTERPAM ? kFasterPAM : kFastPAM1);
+  StreamConfig cfg;
+  if (!stream_config(kModeSwap, c.k, flavour, c.opt.rows_per_tile, &cfg))
+    return fail(KM_E_UNSUPPORTED, "k=%d too large for the SWAP kernel's shared memory", c.k);
+  const int grid = grid_for(c, cfg.rows);
+  StreamArgs sa = stream_args(c);
+  sa.flavour = flavour;
+  sa.win_rows = cfg.rows;
+  if (flavour == kFasterPAM) {  // per-position results of a scan window
+    sa.cand_delta = c.at<double>(c.L.win_delta);
+    sa.cand_slot = c.at<int32_t>(c.L.win_slot);
+  }
+  PointArgs pa = point_args(c);
+  const int max_iter = c.opt.max_iter;
+
+  if (variant == KM_FASTPAM1 || variant == KM_FASTERPAM) {
+    const long long pos_limit = (long long)max_iter * c.n;
+    int launched = 0, batch = 1;
+    const int max_launch = (variant == KM_FASTPAM1) ? max_iter : INT32_MAX;
+    while (true) {
+      int nb = batch;
+      if (variant == KM_FASTPAM1 && launched + nb > max_launch) nb = max_launch - launched;
+      for (int j = 0; j < nb; ++j) {
+        const int e0 = tm.mark();
+        KM_LAUNCH(c, launch_stream(c.dtype, kModeSwap, cfg, grid, sa, c.s));
+        const int e1 = tm.mark();
+        ev.push_back({e0, e1});
+        KM_LAUNCH(c, launch_apply(c.dtype, pa, c.s));
+      }
+      launched += nb;
+      r = read_state(c, h);
+      if (r != KM_OK) return r;
+      if (h->done) break;
+      if (variant == KM_FASTPAM1 && launched >= max_launch) break;
+      if (variant == KM_FASTERPAM && h->pos >= pos_limit) break;
+      batch = batch < 64 ? batch * 2 : 64;
+    }
+  } else {
+    // FastPAM2: evaluation pass, best swap, then the queued per-slot swaps
+    while (h->iter < max_iter) {
+      const int e0 = tm.mark();
+      KM_LAUNCH(c, launch_stream(c.dtype, kModeSwap, cfg, grid, sa, c.s));
+      const int e1 = tm.mark();
+      ev.push_back({e0, e1});
+      r = read_state(c, h);
+      if (r != KM_OK) return r;
+      if (h->done) break;
+      KM_LAUNCH(c, launch_apply(c.dtype, pa, c.s));
+      const int extra = h->fp2_extra;
+      for (int q = 0; q < extra; ++q) {
+        pa.fp2_index = q;
+        KM_LAUNCH(c, launch_fp2_try(c.dtype, pa, c.s));
+        KM_LAUNCH(c, launch_apply(c.dtype, pa, c.s));
+      }
+      r = read_state(c, h);
+      if (r != KM_OK) return r;
+    }
+  }
+  (void)res;
+  return KM_OK;
+}
+
+void fill_result(const Ctx& c, const KmState& h, km_result* res) {
+  if (!res) return;
+  res->iterations = h.iter;
+  res->swaps = h.swaps;
+  res->td_bookkept = (c.dtype == KM_I32) ? (double)h.td_book_i : h.td_book_d;
+}
+
+km_status finish(Ctx& c, KmState* h, int32_t* medoids_out, int32_t* labels_out, km_result* res,
+                 const Timer& tm, const std::vector<std::pair<int, int>>& ev_swap) {
+  // final exact TD of the current buffer
+  double td_d = 0.0;
+  long long td_i = 0;
+  KmState hs;
+  km_status r = read_state(c, &hs);
+  if (r != KM_OK) return r;
+  const int rb = hs.rb;
+  if (c.dtype == KM_I32)
+    KM_CUDA(cudaMemcpyAsync(&td_i, c.at<long long>(c.L.td2) + rb, 8, cudaMemcpyDeviceToHost, c.s));
+  else
+    KM_CUDA(cudaMemcpyAsync(&td_d, c.at<double>(c.L.td2) + rb, 8, cudaMemcpyDeviceToHost, c.s));
+  if (medoids_out)
+    KM_CUDA(cudaMemcpyAsync(medoids_out, c.at<int32_t>(c.L.med), 4 * (size_t)c.k,
+                            cudaMemcpyDeviceToDevice, c.s));
+  if (labels_out)
+    KM_CUDA(cudaMemcpyAsync(labels_out, c.at<int32_t>(c.L.near), 4 * (size_t)c.n,
+                            cudaMemcpyDeviceToDevice, c.s));
+  const int nt = h->ntrace < c.L.trace_cap ? h->ntrace : c.L.trace_cap;
+  std::vector<TraceRec> tr((size_t)(nt > 0 ? nt : 0));
+  if (nt > 0)
+    KM_CUDA(cudaMemcpyAsync(tr.data(), c.at<TraceRec>(c.L.trace), sizeof(TraceRec) * nt,
+                            cudaMemcpyDeviceToHost, c.s));
+  KM_CUDA(cudaStreamSynchronize(c.s));
+  for (int i = 0; i < nt; ++i) {
+    if (c.opt.trace_delta) c.opt.trace_delta[i] = (c.dtype == KM_I32) ? (double)tr[i].di : tr[i].d;
+    if (c.opt.trace_slot) c.opt.trace_slot[i] = tr[i].slot;
+    if (c.opt.trace_cand) c.opt.trace_cand[i] = tr[i].cand;
+    if (c.opt.trace_time_ns) c.opt.trace_time_ns[i] = tr[i].t_ns;
+  }
+  if (res) {
+    res->td = (c.dtype == KM_I32) ? (double)td_i : td_d;
+    res->td_i64 = (c.dtype == KM_I32) ? td_i : 0;
+    double sum = 0.0;
+    int cnt = 0;
+    for (auto& p : ev_swap) {
+      if (cnt >= h->iter) break;
+      sum += tm.ms(p.first, p.second);
+      ++cnt;
+    }
+    if (tm.on) {
+      res->eval_ms = sum;
+      res->eval_launches = cnt;
+    }
+  }
+  return KM_OK;
+}
+
+}  // namespace
+
+// ====================================================================== ABI
+extern "C" {
+
+void km_default_options(km_options* o) {
+  if (!o) return;
+  memset(o, 0, sizeof(*o));
+  o->variant = KM_FASTPAM1;
+  o->max_iter = 0;
+  o->tol = 0.0;
+  o->fastpam2_tol = 0.0;
+}
+
+size_t kmedoids_workspace_size(int64_t n, int32_t k, int32_t dtype, const km_options* opts) {
+  if (dtype != KM_I32 && dtype != KM_F32) return 0;
+  WsLayout L;
+  km_options def;
+  km_default_options(&def);
+  if (!make_ws(n, k, opts ? opts : &def, &L)) return 0;
+  return L.total;
+}
+
+const char* kmedoids_last_error(void) { return g_err.c_str(); }
+
+const char* kmedoids_version(void) { return "kmedoids-gb300 0.1 (sm_103a)"; }
+
+static km_status run_impl(bool do_b, bool do_s, const void* D, int32_t dtype, int64_t n, int64_t ld,
+                          int32_t k, int32_t* medoids_io, int32_t* labels_out,
+                          const km_options* opts, km_result* res, void* ws, size_t ws_bytes,
+                          void* stream) {
+  g_err.clear();
+  Ctx c;
+  km_status r = check_common(D, dtype, n, ld, k, ws, ws_bytes, opts, &c);
+  if (r != KM_OK) {
+    if (res) res->status = r;
+    return r;
+  }
+  if (!medoids_io) return fail(KM_E_INVALID, "medoids pointer is NULL");
+  c.s = static_cast<cudaStream_t>(stream);
+  if (res) {
+    memset(res, 0, sizeof(*res));
+  }
+  Timer tm;
+  tm.start(c.opt.profile != 0, c.s);
+  std::vector<std::pair<int, int>> ev_build, ev_swap;
+  r = reset_state(c);
+  if (r != KM_OK) return r;
+  KmState h;
+  memset(&h, 0, sizeof(h));
+
+  if (!do_b) {
+    // validate the given medoids: in range and distinct
+    std::vector<int32_t> hm((size_t)k);
+    KM_CUDA(cudaMemcpyAsync(hm.data(), medoids_io, 4 * (size_t)k, cudaMemcpyDeviceToHost, c.s));
+    KM_CUDA(cudaStreamSynchronize(c.s));
+    std::vector<char> seen((size_t)n, 0);
+    for (int j = 0; j < k; ++j) {
+      if (hm[j] < 0 || hm[j] >= n) return fail(KM_E_INVALID, "medoid %d out of range: %d", j, hm[j]);
+      if (seen[hm[j]]) return fail(KM_E_INVALID, "medoid %d repeated: %d", j, hm[j]);
+      seen[hm[j]] = 1;
+    }
+    KM_CUDA(cudaMemcpyAsync(c.at<int32_t>(c.L.med), medoids_io, 4 * (size_t)k,
+                            cudaMemcpyDeviceToDevice, c.s));
+  }
+  const int b0 = tm.mark();
+  if (do_b) {
+    r = do_build(c, tm, ev_build, res);
+    if (r != KM_OK) return r;
+  }
+  const int b1 = tm.mark();
+  KmState hb;
+  r = read_state(c, &hb);
+  if (r != KM_OK) {
+    if (res) res->status = r;
+    return r;
+  }
+  if (res && do_b) {
+    res->build_steps = hb.build_step;
+    if (c.opt.build_gains) {
+      KM_CUDA(cudaMemcpyAsync(c.opt.build_gains, c.at<double>(c.L.gains), 8 * (size_t)k,
+                              cudaMemcpyDeviceToHost, c.s));
+      KM_CUDA(cudaStreamSynchronize(c.s));
+    }
+  }
+  km_status conv = KM_OK;
+  if (do_s) {
+    r = reset_state(c);
+    if (r != KM_OK) return r;
+    const int s0 = tm.mark();
+    r = do_swap(c, tm, ev_swap, &h, res);
+    const int s1 = tm.mark();
+    if (r != KM_OK) {
+      if (res) res->status = r;
+      return r;
+    }
+    KmState h2;
+    r = read_state(c, &h2);
+    if (r != KM_OK) return r;
+    if (c.k == 1) {
+      h2.iter = h.iter;
+      h2.swaps = h.swaps;
+      h2.ntrace = h.ntrace;
+      h2.done = h.done;
+    }
+    h = h2;
+    if (!h.done) conv = KM_E_NOT_CONVERGED;
+    if (res) {
+      res->iterations = h.iter;
+      res->swaps = h.swaps;
+      if (c.opt.variant == KM_FASTERPAM && c.k > 1) {
+        res->visited = h.pos;
+        res->iterations = (int)((h.pos + c.n - 1) / c.n);
+      }
+      if (tm.on) res->swap_ms = tm.ms(s0, s1);
+    }
+  } else {
+    // BUILD only: the cache of the result gives labels and the exact TD
+    r = reset_state(c);
+    if (r != KM_OK) return r;
+    r = swap_setup(c);
+    if (r != KM_OK) return r;
+    r = read_state(c, &h);
+    if (r != KM_OK) return r;
+    h.iter = 0;
+    h.swaps = 0;
+    h.ntrace = 0;
+  }
+  r = finish(c, &h, medoids_io, labels_out, res, tm, ev_swap);
+  if (r != KM_OK) return r;
+  if (res) {
+    // initial TD: bookkept TD of BUILD, or the cache's exact TD of the start
+    KmState hf;
+    r = read_state(c, &hf);
+    if (r != KM_OK) return r;
+    res->td_bookkept = (c.dtype == KM_I32) ? (double)hf.td_book_i : hf.td_book_d;
+    if (do_b) res->td_initial = (c.dtype == KM_I32) ? (double)hb.td_book_i : hb.td_book_d;
+    if (tm.on) {
+      res->build_ms = tm.ms(b0, b1);
+      double s = 0.0;
+      for (auto& p : ev_build) s += tm.ms(p.first, p.second);
+      res->build_eval_ms = s;
+    }
+    res->status = conv;
+    res->kernel_launches = c.launches;
+  }
+  if (conv != KM_OK) fail(conv, "max_iter (%d) reached before convergence", c.opt.max_iter);
+  return conv;
+}
+
+km_status kmedoids_build(const void* D, int32_t dtype, int64_t n, int64_t ld, int32_t k,
+                         int32_t* medoids_out, const km_options* opts, km_result* res, void* ws,
+                         size_t ws_bytes, void* stream) {
+  return run_impl(true, false, D, dtype, n, ld, k, medoids_out, nullptr, opts, res, ws, ws_bytes,
+                  stream);
+}
+
+km_status kmedoids_swap(const void* D, int32_t dtype, int64_t n, int64_t ld, int32_t k,
+                        int32_t* medoids_inout, int32_t* labels_out, const km_options* opts,
+                        km_result* res, void* ws, size_t ws_bytes, void* stream) {
+  return run_impl(false, true, D, dtype, n, ld, k, medoids_inout, labels_out, opts, res, ws,
+                  ws_bytes, stream);
+}
+
+km_status kmedoids_run(const void* D, int32_t dtype, int64_t n, int64_t ld, int32_t k,
+                       int32_t* medoids_out, int32_t* labels_out, const km_options* opts,
+                       km_result* res, void* ws, size_t ws_bytes, void* stream) {
+  return run_impl(true, true, D, dtype, n, ld, k, medoids_out, labels_out, opts, res, ws, ws_bytes,
+                  stream);
+}
+
+km_status kmedoids_eval_swaps(const void* D, int32_t dtype, int64_t n, int64_t ld, int32_t k,
+                              const int32_t* medoids, double* cand_delta, int32_t* cand_slot,
+                              double* best_delta, int32_t* best_slot, int32_t* best_cand,
+                              void* ws, size_t ws_bytes, void* stream) {
+  g_err.clear();
+  Ctx c;
+  km_status r = check_common(D, dtype, n, ld, k, ws, ws_bytes, nullptr, &c);
+  if (r != KM_OK) return r;
+  if (k < 2) return fail(KM_E_INVALID, "kmedoids_eval_swaps needs k >= 2");
+  if (!medoids) return fail(KM_E_INVALID, "medoids is NULL");
+  c.s = static_cast<cudaStream_t>(stream);
+  r = reset_state(c);
+  if (r != KM_OK) return r;
+  KM_CUDA(cudaMemcpyAsync(c.at<int32_t>(c.L.med), medoids, 4 * (size_t)k, cudaMemcpyDeviceToDevice, c.s));
+  r = swap_setup(c);
+  if (r != KM_OK) return r;
+  StreamConfig cfg;
+  if (!stream_config(kModeSwap, k, kEvalOnly, 0, &cfg))
+    return fail(KM_E_UNSUPPORTED, "k=%d too large for the SWAP kernel", k);
+  StreamArgs sa = stream_args(c);
+  sa.flavour = kEvalOnly;
+  sa.cand_delta = cand_delta;
+  sa.cand_slot = cand_slot;
+  KM_LAUNCH(c, launch_stream(dtype, kModeSwap, cfg, grid_for(c, cfg.rows), sa, c.s));
+  PointArgs pa = point_args(c);
+  pa.cand_delta = cand_delta;
+  pa.cand_slot = cand_slot;
+  KM_LAUNCH(c, launch_fill_medoid_rows(pa, c.s));
+  KmState h;
+  r = read_state(c, &h);
+  if (r != KM_OK) return r;
+  if (best_delta) *best_delta = (h.best_cand < 0) ? __builtin_inf()
+                                                  : (dtype == KM_I32 ? (double)h.best_i : h.best_d);
+  if (best_slot) *best_slot = h.best_slot;
+  if (best_cand) *best_cand = h.best_cand;
+  return KM_OK;
+}
+
+km_status kmedoids_cache(const void* D, int32_t dtype, int64_t n, int64_t ld, int32_t k,
+                         const int32_t* medoids, int32_t* near, int32_t* sec, void* dn, void* ds,
+                         double* removal, void* ws, size_t ws_bytes, void* stream) {
+  g_err.clear();
+  Ctx c;
+  km_status r = check_common(D, dtype, n, ld, k, ws, ws_bytes, nullptr, &c);
+  if (r != KM_OK) return r;
+  if (!medoids) return fail(KM_E_INVALID, "medoids is NULL");
+  c.s = static_cast<cudaStream_t>(stream);
+  r = reset_state(c);
+  if (r != KM_OK) return r;
+  KM_CUDA(cudaMemcpyAsync(c.at<int32_t>(c.L.med), medoids, 4 * (size_t)k, cudaMemcpyDeviceToDevice, c.s));
+  r = swap_setup(c);
+  if (r != KM_OK) return r;
+  if (near) KM_CUDA(cudaMemcpyAsync(near, c.at<int32_t>(c.L.near), 4 * (size_t)n, cudaMemcpyDeviceToDevice, c.s));
+  if (sec) KM_CUDA(cudaMemcpyAsync(sec, c.at<int32_t>(c.L.sec), 4 * (size_t)n, cudaMemcpyDeviceToDevice, c.s));
+  if (dn) KM_CUDA(cudaMemcpyAsync(dn, c.at<void>(c.L.dn), 4 * (size_t)n, cudaMemcpyDeviceToDevice, c.s));
+  if (ds) KM_CUDA(cudaMemcpyAsync(ds, c.at<void>(c.L.ds), 4 * (size_t)n, cudaMemcpyDeviceToDevice, c.s));
+  if (removal) {
+    PointArgs pa = point_args(c);
+    pa.out_double = removal;
+    KM_LAUNCH(c, launch_removal_to_double(dtype, pa, c.s));
+  }
+  KmState h;
+  return read_state(c, &h);
+}
+
+}  // extern "C"

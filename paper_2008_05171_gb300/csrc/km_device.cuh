@@ -1,0 +1,245 @@
+// km_device.cuh -- device-side building blocks shared by the kernels of
+// libkmedoids: launch geometry, the device state record, reduction keys, and
+// thin inline-PTX wrappers for mbarriers and 1-D bulk (TMA) copies.
+#pragma once
+
+#include <cstdint>
+#include <climits>
+#include <cuda_runtime.h>
+
+namespace km {
+
+// ---------------------------------------------------------------- geometry
+constexpr int kChunk = 1024;                   // matrix columns per stage
+constexpr int kConsWarps = 8;                  // consumer warps per CTA
+constexpr int kConsThreads = kConsWarps * 32;  // each owns 4 columns
+constexpr int kThreads = kConsThreads + 32;    // + one producer warp
+constexpr int kMaxGrid = 1024;                 // workspace bound on CTAs
+constexpr int kMaxRows = 16;                   // largest candidate tile
+constexpr unsigned long long kWaitLimitNs = 4000000000ull;  // 4 s
+
+static_assert(kConsThreads * 4 == kChunk, "4 columns per consumer thread");
+
+// Status codes written by kernels (same values as km_status).
+constexpr int kErrTimeout = 5;
+
+// ---------------------------------------------------------- device state
+// One record per call, in the workspace.  Kernels read it to pick buffers
+// and write the decisions of each pass, so a whole SWAP loop can be enqueued
+// without the host looking at intermediate results.
+struct KmState {
+  int iter;          // evaluation passes completed
+  int swaps;         // swaps applied
+  int done;          // 1: converged / nothing left to do
+  int error;         // km_status of a device-detected failure, 0 if none
+  unsigned ticket;   // last-block-done counter of the running kernel
+  int rb;            // which removal-loss / TD buffer is current (0/1)
+  int accept;        // 1: a swap (best_*) is pending for the apply kernel
+  int build_step;    // BUILD steps committed
+  double best_d;     // pending / best swap: Delta (float data)
+  long long best_i;  // pending / best swap: Delta (integer data)
+  int best_slot;
+  int best_cand;
+  double build_gain_d;      // BUILD: best gain of the current step
+  long long build_gain_i;
+  int build_cand;
+  int ntrace;               // swaps recorded in the trace
+  double td_book_d;         // bookkept TD (initial + applied deltas)
+  long long td_book_i;
+  double build_td_d;        // exact TD after the last BUILD commit
+  long long build_td_i;
+  long long pos;            // FasterPAM: absolute scan position
+  long long last;           // FasterPAM: absolute position of last swap
+  int fp2_extra;            // FastPAM2: additional slots queued this pass
+  int pad0;
+  double fp2_dstar;         // FastPAM2: |Delta*| of the pass
+  long long fp2_dstar_i;
+};
+
+// Trace record of an applied swap.
+struct TraceRec {
+  double d;
+  long long di;
+  int slot;
+  int cand;
+  long long t_ns;
+};
+
+// Reduction key: lexicographic (delta, slot, cand).  For BUILD the slot is
+// unused (0) and cand is the point index.
+template <class A>
+struct Key {
+  A d;
+  int slot;
+  int cand;
+};
+
+// Load a key written by another CTA of the running kernel (L2, not L1).
+template <class A>
+__device__ __forceinline__ Key<A> ld_cg_key(const Key<A>* p) {
+  Key<A> r;
+  r.d = __ldcg(&p->d);
+  r.slot = __ldcg(&p->slot);
+  r.cand = __ldcg(&p->cand);
+  return r;
+}
+
+template <class A>
+__device__ __forceinline__ bool key_less(const Key<A>& a, const Key<A>& b) {
+  if (a.d != b.d) return a.d < b.d;
+  if (a.slot != b.slot) return a.slot < b.slot;
+  return a.cand < b.cand;
+}
+
+// --------------------------------------------------------- type traits
+template <class T>
+struct Tr;
+
+template <>
+struct Tr<float> {
+  using A = double;  // accumulator / Delta type
+  __device__ __forceinline__ static float low() { return -__int_as_float(0x7f800000); }
+  __device__ __forceinline__ static float high() { return __int_as_float(0x7f800000); }
+  __device__ __forceinline__ static double a_high() { return __longlong_as_double(0x7ff0000000000000ll); }
+};
+
+template <>
+struct Tr<int32_t> {
+  using A = long long;
+  __device__ __forceinline__ static int32_t low() { return INT_MIN; }
+  __device__ __forceinline__ static int32_t high() { return INT_MAX; }
+  __device__ __forceinline__ static long long a_high() { return LLONG_MAX; }
+};
+
+__device__ __forceinline__ double to_double(double v) { return v; }
+__device__ __forceinline__ double to_double(long long v) { return (double)v; }
+
+// Delta contributions: exact FP64 differences of two FP32 values, or exact
+// int64 differences of two int32 values.
+__device__ __forceinline__ double dif(float a, float b) { return (double)a - (double)b; }
+__device__ __forceinline__ long long dif(int32_t a, int32_t b) { return (long long)a - (long long)b; }
+
+__device__ __forceinline__ void atomic_add_acc(double* p, double v) { atomicAdd(p, v); }
+__device__ __forceinline__ void atomic_add_acc(long long* p, long long v) {
+  atomicAdd(reinterpret_cast<unsigned long long*>(p), static_cast<unsigned long long>(v));
+}
+
+template <class A>
+__device__ __forceinline__ A shfl_down_a(A v, int o) { return __shfl_down_sync(0xffffffffu, v, o); }
+
+template <class A>
+__device__ __forceinline__ Key<A> shfl_key(const Key<A>& k, int src) {
+  Key<A> r;
+  r.d = __shfl_sync(0xffffffffu, k.d, src);
+  r.slot = __shfl_sync(0xffffffffu, k.slot, src);
+  r.cand = __shfl_sync(0xffffffffu, k.cand, src);
+  return r;
+}
+
+// Warp-wide lexicographic minimum; the result is valid in every lane.
+template <class A>
+__device__ __forceinline__ Key<A> warp_min_key(Key<A> k) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    Key<A> other;
+    other.d = __shfl_xor_sync(0xffffffffu, k.d, o);
+    other.slot = __shfl_xor_sync(0xffffffffu, k.slot, o);
+    other.cand = __shfl_xor_sync(0xffffffffu, k.cand, o);
+    if (key_less(other, k)) k = other;
+  }
+  return k;
+}
+
+template <class A>
+__device__ __forceinline__ A warp_sum(A v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// ------------------------------------------------------------- timers
+__device__ __forceinline__ unsigned long long globaltimer() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// ------------------------------------------------------- mbarrier / TMA
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
+               : "memory");
+}
+
+__device__ __forceinline__ void fence_barrier_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Wait for the phase with the given parity to complete.  Gives up after
+// kWaitLimitNs (returns false) or as soon as *abort becomes nonzero.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const unsigned long long t0 = globaltimer();
+  while (true) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if (*abort) return false;
+    if (globaltimer() - t0 > kWaitLimitNs) return false;
+  }
+}
+
+// 1-D bulk copy global -> shared, completion signalled on *bar (tx bytes).
+// Both addresses 16-byte aligned, bytes a multiple of 16.
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// Barrier among the consumer warps only (the producer warp runs its own
+// loop), built on an mbarrier with one arrival per warp so that the wait is
+// bounded like every other wait.  `phase` is the calling thread's copy of
+// the barrier phase.  Returns false when the wait gave up.
+__device__ __forceinline__ bool cons_sync(uint64_t* bar, uint32_t& phase, volatile int* abort) {
+  __syncwarp();
+  if ((threadIdx.x & 31) == 0) mbar_arrive(bar);
+  const bool ok = mbar_wait(bar, phase, abort);
+  phase ^= 1u;
+  __syncwarp();
+  return ok;
+}
+
+__device__ __forceinline__ float4 lds4(const float* p) { return *reinterpret_cast<const float4*>(p); }
+__device__ __forceinline__ int4 lds4(const int32_t* p) { return *reinterpret_cast<const int4*>(p); }
+
+}  // namespace km

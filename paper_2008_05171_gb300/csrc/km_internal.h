@@ -1,0 +1,111 @@
+// km_internal.h -- host-side interface between the C-ABI layer (km_api.cu)
+// and the kernel translation units.  Not installed; not part of the ABI.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace km {
+
+struct KmState;
+
+// Streaming-kernel modes.
+enum StreamMode { kModeSwap = 0, kModeBuild = 1 };
+
+// SWAP pass flavours (what the last CTA decides after the pass).
+enum SwapFlavour {
+  kFastPAM1 = 0,  // best swap; accept iff Delta < -tol, else done
+  kFastPAM2 = 1,  // as FastPAM1 + per-slot best swaps queued for later
+  kFasterPAM = 2, // window of the cyclic scan; first improving candidate
+  kEvalOnly = 3   // evaluation only: best key written, no decision
+};
+
+struct StreamArgs {
+  const void* D;
+  long long ld;
+  int n;
+  int k;
+  int k_pad;
+  int n_pad;
+  const uint8_t* is_med;
+  // SWAP per-point cache (n_pad entries, padding holds sentinels)
+  const void* dn;
+  const void* ds;
+  const int32_t* near;
+  // BUILD nearest distance (n_pad entries)
+  const void* bdn;
+  int build_first;
+  // removal loss [2][k_pad] and exact TD [2] (accumulator type)
+  void* removal;
+  void* td2;
+  KmState* st;
+  void* partials;       // Key[kMaxGrid]
+  void* slot_partials;  // Key[kMaxGrid][k]   (FastPAM2)
+  void* slot_best;      // Key[k]             (FastPAM2)
+  int32_t* fp2_order;   // [k]                (FastPAM2)
+  double* cand_delta;   // per-candidate outputs (index = output index)
+  int32_t* cand_slot;
+  double* cand_gain;    // BUILD per-candidate gains
+  int flavour;          // SwapFlavour
+  int win_rows;         // FasterPAM: positions per CTA
+  double tol;
+};
+
+struct PointArgs {
+  const void* D;
+  long long ld;
+  int n;
+  int k;
+  int k_pad;
+  int n_pad;
+  int32_t* med;
+  uint8_t* is_med;
+  int32_t* near;
+  int32_t* sec;
+  void* dn;
+  void* ds;
+  void* bdn;
+  void* removal;  // [2][k_pad]
+  void* td2;      // [2]
+  KmState* st;
+  void* trace;    // TraceRec[trace_cap]
+  int trace_cap;
+  int build_first;
+  int fp2_index;  // FastPAM2 extra-swap index
+  double fp2_tol;
+  const void* slot_best;      // Key[k] (FastPAM2)
+  const int32_t* fp2_order;   // [k]    (FastPAM2)
+  double* gains;              // BUILD gains per step [k]
+  const double* cand_in;      // per-candidate values (k = 1 path)
+  double* cand_delta;         // fill kernel outputs
+  int32_t* cand_slot;
+  double* out_double;         // accumulator -> double conversion target
+  void* partials; // Key[kMaxGrid] scratch for grid reductions
+  int use_rb;     // cache init: write into buffer st->rb (0) or the given
+};
+
+// Launch configuration chosen for a (mode, k) pair.
+struct StreamConfig {
+  int rows;       // candidate rows per tile (R)
+  int stages;     // ring depth (S)
+  size_t smem;    // dynamic shared memory bytes
+};
+
+// Returns false if no configuration fits (k too large).
+bool stream_config(int mode, int k, int flavour, int forced_rows, StreamConfig* cfg);
+
+cudaError_t launch_stream(int dtype, int mode, const StreamConfig& cfg, int grid,
+                          const StreamArgs& a, cudaStream_t s);
+
+cudaError_t launch_cache_init(int dtype, const PointArgs& a, cudaStream_t s);
+cudaError_t launch_apply(int dtype, const PointArgs& a, cudaStream_t s);
+cudaError_t launch_build_commit(int dtype, const PointArgs& a, cudaStream_t s);
+cudaError_t launch_fp2_try(int dtype, const PointArgs& a, cudaStream_t s);
+cudaError_t launch_mark_medoids(const PointArgs& a, cudaStream_t s);
+cudaError_t launch_fill_medoid_rows(const PointArgs& a, cudaStream_t s);
+cudaError_t launch_removal_to_double(int dtype, const PointArgs& a, cudaStream_t s);
+
+int device_sm_count();
+
+}  // namespace km

@@ -1,0 +1,408 @@
+// km_points.cu -- per-point kernels of the SWAP and BUILD loops:
+//
+//   k_cache_init      nearest / second-nearest slot and distance of every
+//                     point (Sec. 2), the removal loss Delta^{-m_i} (Eq. (7))
+//                     and the exact TD (Eq. (2)) for the current medoids.
+//   k_apply           performs the pending swap (Alg. 3 "swap roles"): the
+//                     new medoid takes the slot of the removed one; the cache
+//                     is updated incrementally (points whose nearest or
+//                     second nearest was the removed slot rescan all k
+//                     medoids), and the removal loss / TD of the next pass
+//                     are accumulated on the way.
+//   k_build_commit    adds the chosen BUILD medoid and updates d_n (Alg. 1).
+//   k_fp2_try         FastPAM2: exact Delta of one queued per-slot swap
+//                     against the current cache, by Eq. (5).
+//
+// One thread per point; d(x_o, x_m) is read as D[m*ld + o] so a warp reads
+// 32 consecutive elements of a medoid row.  Grid-wide results use a
+// last-block-done ticket in the device state.
+#include <type_traits>
+
+#include "km_device.cuh"
+#include "km_internal.h"
+
+namespace km {
+
+constexpr int kPtThreads = 256;
+
+template <class A>
+__device__ __forceinline__ A block_sum(A v, A* scratch) {
+  v = warp_sum(v);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (l == 0) scratch[w] = v;
+  __syncthreads();
+  A r = A(0);
+  if (threadIdx.x == 0)
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) r += scratch[i];
+  __syncthreads();
+  return r;  // valid in thread 0
+}
+
+// top-2 insertion under the lexicographic (distance, slot) order, with
+// slots offered in ascending order (strict comparisons keep the lowest slot)
+template <class T>
+__device__ __forceinline__ void top2_push(T v, int j, int& n1, T& d1, int& n2, T& d2) {
+  if (n1 < 0 || v < d1) {
+    n2 = n1;
+    d2 = d1;
+    n1 = j;
+    d1 = v;
+  } else if (n2 < 0 || v < d2) {
+    n2 = j;
+    d2 = v;
+  }
+}
+
+// ------------------------------------------------------------ cache init
+template <class T>
+__global__ void __launch_bounds__(kPtThreads) k_cache_init(const PointArgs a) {
+  using A = typename Tr<T>::A;
+  extern __shared__ __align__(16) unsigned char sm[];
+  A* sacc = reinterpret_cast<A*>(sm);
+  A* scratch = sacc + a.k;
+  __shared__ int is_last;
+  KmState* st = a.st;
+  const int k = a.k, n = a.n;
+  const int rb = st->rb;
+  for (int i = threadIdx.x; i < k; i += blockDim.x) sacc[i] = A(0);
+  __syncthreads();
+  const int o = blockIdx.x * blockDim.x + threadIdx.x;
+  const T* D = static_cast<const T*>(a.D);
+  T* dn = static_cast<T*>(a.dn);
+  T* ds = static_cast<T*>(a.ds);
+  A tdl = A(0);
+  if (o < n) {
+    int n1 = -1, n2 = -1;
+    T d1 = Tr<T>::high(), d2 = Tr<T>::high();
+    for (int j = 0; j < k; ++j) {
+      const T v = D[(size_t)a.med[j] * a.ld + o];
+      top2_push(v, j, n1, d1, n2, d2);
+    }
+    a.near[o] = n1;
+    a.sec[o] = n2;
+    dn[o] = d1;
+    ds[o] = (n2 < 0) ? Tr<T>::high() : d2;
+    if (n2 >= 0) atomic_add_acc(&sacc[n1], dif(d2, d1));
+    tdl = A(d1);
+  } else if (o < a.n_pad) {
+    a.near[o] = 0;
+    a.sec[o] = 0;
+    dn[o] = Tr<T>::low();  // sentinels: d < low never holds
+    ds[o] = Tr<T>::low();
+  }
+  const A bs = block_sum(tdl, scratch);
+  A* rem = static_cast<A*>(a.removal) + (size_t)rb * a.k_pad;
+  if (threadIdx.x == 0) atomic_add_acc(static_cast<A*>(a.td2) + rb, bs);
+  for (int i = threadIdx.x; i < k; i += blockDim.x)
+    if (sacc[i] != A(0)) atomic_add_acc(&rem[i], sacc[i]);
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) is_last = (atomicAdd(&st->ticket, 1u) == gridDim.x - 1);
+  __syncthreads();
+  if (is_last && threadIdx.x == 0) {
+    __threadfence();
+    const A td0 = static_cast<volatile A*>(a.td2)[rb];
+    st->td_book_d = to_double(td0);
+    st->td_book_i = (long long)td0;
+    st->ticket = 0;
+  }
+}
+
+// -------------------------------------------------------------- apply swap
+template <class T>
+__global__ void __launch_bounds__(kPtThreads) k_apply(const PointArgs a) {
+  using A = typename Tr<T>::A;
+  extern __shared__ __align__(16) unsigned char sm[];
+  A* sacc = reinterpret_cast<A*>(sm);
+  A* scratch = sacc + a.k;
+  __shared__ int is_last;
+  KmState* st = a.st;
+  if (st->error || !st->accept) return;  // uniform for the launch
+  const int k = a.k, n = a.n;
+  const int i_s = st->best_slot, c_s = st->best_cand;
+  const int rb = st->rb;
+  for (int i = threadIdx.x; i < k; i += blockDim.x) sacc[i] = A(0);
+  __syncthreads();
+  const int o = blockIdx.x * blockDim.x + threadIdx.x;
+  const T* D = static_cast<const T*>(a.D);
+  T* dn = static_cast<T*>(a.dn);
+  T* ds = static_cast<T*>(a.ds);
+  A tdl = A(0);
+  if (o < n) {
+    int n1 = a.near[o], n2 = a.sec[o];
+    T d1 = dn[o], d2 = ds[o];
+    if (n1 == i_s || n2 == i_s) {
+      // the removed medoid was nearest or second: rescan every slot
+      n1 = -1;
+      n2 = -1;
+      d1 = Tr<T>::high();
+      d2 = Tr<T>::high();
+      for (int j = 0; j < k; ++j) {
+        const int m = (j == i_s) ? c_s : a.med[j];
+        top2_push(D[(size_t)m * a.ld + o], j, n1, d1, n2, d2);
+      }
+    } else {
+      // only the new medoid enters: top-2 of {nearest, second, new}
+      const T dc = D[(size_t)c_s * a.ld + o];
+      if (dc < d1 || (dc == d1 && i_s < n1)) {
+        n2 = n1;
+        d2 = d1;
+        n1 = i_s;
+        d1 = dc;
+      } else if (dc < d2 || (dc == d2 && i_s < n2)) {
+        n2 = i_s;
+        d2 = dc;
+      }
+    }
+    a.near[o] = n1;
+    a.sec[o] = n2;
+    dn[o] = d1;
+    ds[o] = d2;
+    atomic_add_acc(&sacc[n1], dif(d2, d1));
+    tdl = A(d1);
+  }
+  const A bs = block_sum(tdl, scratch);
+  A* rem = static_cast<A*>(a.removal) + (size_t)(rb ^ 1) * a.k_pad;
+  if (threadIdx.x == 0) atomic_add_acc(static_cast<A*>(a.td2) + (rb ^ 1), bs);
+  for (int i = threadIdx.x; i < k; i += blockDim.x)
+    if (sacc[i] != A(0)) atomic_add_acc(&rem[i], sacc[i]);
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) is_last = (atomicAdd(&st->ticket, 1u) == gridDim.x - 1);
+  __syncthreads();
+  if (is_last && threadIdx.x == 0) {
+    __threadfence();
+    const int old = a.med[i_s];
+    a.med[i_s] = c_s;
+    a.is_med[old] = 0;
+    a.is_med[c_s] = 1;
+    const int nt = st->ntrace;
+    if (nt < a.trace_cap) {
+      TraceRec* tr = static_cast<TraceRec*>(a.trace) + nt;
+      tr->d = st->best_d;
+      tr->di = st->best_i;
+      tr->slot = i_s;
+      tr->cand = c_s;
+      tr->t_ns = (long long)globaltimer();
+    }
+    st->ntrace = nt + 1;
+    st->swaps += 1;
+    st->td_book_d += st->best_d;
+    st->td_book_i += st->best_i;
+    st->accept = 0;
+    st->rb = rb ^ 1;
+    st->ticket = 0;
+  }
+}
+
+// ------------------------------------------------------------ BUILD commit
+template <class T>
+__global__ void __launch_bounds__(kPtThreads) k_build_commit(const PointArgs a) {
+  using A = typename Tr<T>::A;
+  __shared__ A scratch[kPtThreads / 32];
+  KmState* st = a.st;
+  if (st->error) return;
+  const int n = a.n;
+  const int c = st->build_cand;
+  const int o = blockIdx.x * blockDim.x + threadIdx.x;
+  const T* D = static_cast<const T*>(a.D);
+  T* bdn = static_cast<T*>(a.bdn);
+  A local = A(0);
+  if (c >= 0 && c < n) {
+    if (o < n) {
+      const T v = D[(size_t)c * a.ld + o];
+      T cur = v;
+      if (!a.build_first) {
+        const T prev = bdn[o];
+        if (!(v < prev)) cur = prev;
+      }
+      bdn[o] = cur;
+      local = A(cur);
+    } else if (o < a.n_pad) {
+      bdn[o] = Tr<T>::low();  // padding: never above a distance
+    }
+  }
+  const A bs = block_sum(local, scratch);
+  if (threadIdx.x == 0) {
+    if (std::is_same<A, double>::value)
+      atomicAdd(&st->build_td_d, to_double(bs));
+    else
+      atomicAdd(reinterpret_cast<unsigned long long*>(&st->build_td_i),
+                static_cast<unsigned long long>((long long)bs));
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0 && c >= 0 && c < n) {
+    const int step = st->build_step;
+    a.med[step] = c;
+    a.is_med[c] = 1;
+    if (a.gains) a.gains[step] = st->build_gain_d;
+    if (a.build_first) {
+      st->td_book_d = st->build_gain_d;
+      st->td_book_i = st->build_gain_i;
+    } else {
+      st->td_book_d += st->build_gain_d;
+      st->td_book_i += st->build_gain_i;
+    }
+    st->build_step = step + 1;
+  }
+}
+
+// ----------------------------------------------- FastPAM2 additional swap
+template <class T>
+__global__ void __launch_bounds__(kPtThreads) k_fp2_try(const PointArgs a) {
+  using A = typename Tr<T>::A;
+  __shared__ A scratch[kPtThreads / 32];
+  __shared__ int is_last;
+  KmState* st = a.st;
+  // The apply kernel that follows accumulates the next removal loss and TD
+  // into buffer rb^1; clear it here as the evaluation pass does.
+  const int rb = st->rb;
+  if (blockIdx.x == 0) {
+    A* rnext = static_cast<A*>(a.removal) + (size_t)(rb ^ 1) * a.k_pad;
+    for (int i = threadIdx.x; i < a.k; i += blockDim.x) rnext[i] = A(0);
+    if (threadIdx.x == 0) static_cast<A*>(a.td2)[rb ^ 1] = A(0);
+  }
+  if (st->error || st->done) return;
+  if (a.fp2_index >= st->fp2_extra) return;
+  const int i = a.fp2_order[a.fp2_index];
+  const Key<A> sb = static_cast<const Key<A>*>(a.slot_best)[i];
+  const int c = sb.cand;
+  if (a.is_med[c]) {  // already a medoid after an earlier swap
+    if (blockIdx.x == 0 && threadIdx.x == 0) st->accept = 0;
+    return;
+  }
+  const int n = a.n;
+  const int o = blockIdx.x * blockDim.x + threadIdx.x;
+  const T* D = static_cast<const T*>(a.D);
+  const T* dn = static_cast<const T*>(a.dn);
+  const T* ds = static_cast<const T*>(a.ds);
+  A v = A(0);
+  if (o < n) {
+    const T doc = D[(size_t)c * a.ld + o];
+    const T d1 = dn[o], d2 = ds[o];
+    if (a.near[o] != i) {
+      if (doc < d1) v = dif(doc, d1);          // (c)
+    } else {
+      v = (doc < d2) ? dif(doc, d1) : dif(d2, d1);  // (b1) / (b2)
+    }
+  }
+  const A bs = block_sum(v, scratch);
+  A* parts = static_cast<A*>(a.partials);
+  if (threadIdx.x == 0) {
+    parts[blockIdx.x] = bs;
+    __threadfence();
+    is_last = (atomicAdd(&st->ticket, 1u) == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (is_last && threadIdx.x == 0) {
+    __threadfence();
+    A tot = A(0);
+    for (int g = 0; g < (int)gridDim.x; ++g) tot += static_cast<volatile A*>(parts)[g];
+    const double thr = -a.fp2_tol * st->fp2_dstar;
+    if (to_double(tot) < thr) {
+      st->accept = 1;
+      st->best_d = to_double(tot);
+      st->best_i = (long long)tot;
+      st->best_slot = i;
+      st->best_cand = c;
+    } else {
+      st->accept = 0;
+    }
+    st->ticket = 0;
+  }
+}
+
+// ------------------------------------------------------------- small ones
+__global__ void k_mark_medoids(const PointArgs a) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j < a.k) a.is_med[a.med[j]] = 1;
+}
+
+__global__ void k_fill_medoid_rows(const PointArgs a) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c < a.n && a.is_med[c]) {
+    if (a.cand_delta) a.cand_delta[c] = __longlong_as_double(0x7ff0000000000000ll);
+    if (a.cand_slot) a.cand_slot[c] = -1;
+  }
+}
+
+template <class A>
+__global__ void k_removal_to_double(const PointArgs a) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int rb = a.st->rb;
+  if (i < a.k) a.out_double[i] = to_double(static_cast<const A*>(a.removal)[(size_t)rb * a.k_pad + i]);
+}
+
+// ------------------------------------------------------------- launchers
+static inline int blocks_for(int n) { return (n + kPtThreads - 1) / kPtThreads; }
+
+cudaError_t launch_cache_init(int dtype, const PointArgs& a, cudaStream_t s) {
+  const int grid = blocks_for(a.n_pad);
+  const size_t smem = 8 * (size_t)a.k + 8 * (kPtThreads / 32);
+  if (dtype == 0) {
+    cudaFuncSetAttribute(k_cache_init<int32_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_cache_init<int32_t><<<grid, kPtThreads, smem, s>>>(a);
+  } else {
+    cudaFuncSetAttribute(k_cache_init<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_cache_init<float><<<grid, kPtThreads, smem, s>>>(a);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_apply(int dtype, const PointArgs& a, cudaStream_t s) {
+  const int grid = blocks_for(a.n);
+  const size_t smem = 8 * (size_t)a.k + 8 * (kPtThreads / 32);
+  if (dtype == 0) {
+    cudaFuncSetAttribute(k_apply<int32_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_apply<int32_t><<<grid, kPtThreads, smem, s>>>(a);
+  } else {
+    cudaFuncSetAttribute(k_apply<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_apply<float><<<grid, kPtThreads, smem, s>>>(a);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_build_commit(int dtype, const PointArgs& a, cudaStream_t s) {
+  const int grid = blocks_for(a.n_pad);
+  if (dtype == 0)
+    k_build_commit<int32_t><<<grid, kPtThreads, 0, s>>>(a);
+  else
+    k_build_commit<float><<<grid, kPtThreads, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fp2_try(int dtype, const PointArgs& a, cudaStream_t s) {
+  const int grid = blocks_for(a.n);
+  if (grid > kMaxGrid) return cudaErrorInvalidConfiguration;
+  if (dtype == 0)
+    k_fp2_try<int32_t><<<grid, kPtThreads, 0, s>>>(a);
+  else
+    k_fp2_try<float><<<grid, kPtThreads, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_mark_medoids(const PointArgs& a, cudaStream_t s) {
+  k_mark_medoids<<<(a.k + 255) / 256, 256, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fill_medoid_rows(const PointArgs& a, cudaStream_t s) {
+  k_fill_medoid_rows<<<blocks_for(a.n), kPtThreads, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_removal_to_double(int dtype, const PointArgs& a, cudaStream_t s) {
+  if (dtype == 0)
+    k_removal_to_double<long long><<<(a.k + 255) / 256, 256, 0, s>>>(a);
+  else
+    k_removal_to_double<double><<<(a.k + 255) / 256, 256, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+int device_sm_count() {
+  int dev = 0, v = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+  if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+  return v;
+}
+
+}  // namespace km

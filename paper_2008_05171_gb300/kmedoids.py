@@ -1,0 +1,305 @@
+"""Python binding of libkmedoids (include/kmedoids.h), argument marshalling only.
+
+Every function here takes torch CUDA tensors, passes their device pointers,
+sizes and the current CUDA stream to the C ABI of the same name, and turns
+the result struct into a dict.  All of the method's arithmetic runs in the
+library's kernels; there is no CPU fallback: if ``libkmedoids.so`` has not
+been built, or no CUDA device is present, the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libkmedoids.so")
+
+KM_I32, KM_F32 = 0, 1
+VARIANTS = {"fastpam1": 0, "fastpam2": 1, "fasterpam": 2}
+STATUS = {0: "KM_OK", 1: "KM_E_INVALID", 2: "KM_E_WORKSPACE", 3: "KM_E_CUDA",
+          4: "KM_E_NOT_CONVERGED", 5: "KM_E_TIMEOUT", 6: "KM_E_NUMERIC",
+          7: "KM_E_UNSUPPORTED"}
+EXPORTS = ["km_default_options", "kmedoids_workspace_size", "kmedoids_build",
+           "kmedoids_swap", "kmedoids_run", "kmedoids_eval_swaps",
+           "kmedoids_cache", "kmedoids_last_error", "kmedoids_version"]
+
+
+class KmError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__("%s: %s" % (STATUS.get(status, status), msg))
+        self.status = status
+
+
+class km_options(ctypes.Structure):
+    _fields_ = [("variant", ctypes.c_int32), ("max_iter", ctypes.c_int32),
+                ("tol", ctypes.c_double), ("fastpam2_tol", ctypes.c_double),
+                ("rows_per_tile", ctypes.c_int32), ("profile", ctypes.c_int32),
+                ("trace_capacity", ctypes.c_int32),
+                ("reserved0", ctypes.c_int32),
+                ("trace_delta", ctypes.POINTER(ctypes.c_double)),
+                ("trace_slot", ctypes.POINTER(ctypes.c_int32)),
+                ("trace_cand", ctypes.POINTER(ctypes.c_int32)),
+                ("trace_time_ns", ctypes.POINTER(ctypes.c_int64)),
+                ("build_gains", ctypes.POINTER(ctypes.c_double))]
+
+
+class km_result(ctypes.Structure):
+    _fields_ = [("td", ctypes.c_double), ("td_i64", ctypes.c_int64),
+                ("td_bookkept", ctypes.c_double),
+                ("td_initial", ctypes.c_double),
+                ("iterations", ctypes.c_int32), ("swaps", ctypes.c_int32),
+                ("status", ctypes.c_int32), ("build_steps", ctypes.c_int32),
+                ("visited", ctypes.c_int64), ("build_ms", ctypes.c_double),
+                ("swap_ms", ctypes.c_double), ("eval_ms", ctypes.c_double),
+                ("eval_launches", ctypes.c_int32),
+                ("build_launches", ctypes.c_int32),
+                ("build_eval_ms", ctypes.c_double),
+                ("kernel_launches", ctypes.c_int64)]
+
+
+_LOCK = threading.Lock()
+_LIB = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libkmedoids.so (raises if it has not been built)."""
+    global _LIB
+    with _LOCK:
+        if _LIB is not None:
+            return _LIB
+        if not os.path.exists(path):
+            raise RuntimeError(
+                "libkmedoids.so not found at %s: build it first "
+                "(python -c 'import __graft_entry__ as g; g.build()')" % path)
+        lib = ctypes.CDLL(path)
+        P, i32, i64, sz = (ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64,
+                           ctypes.c_size_t)
+        opt_p = ctypes.POINTER(km_options)
+        res_p = ctypes.POINTER(km_result)
+        lib.km_default_options.argtypes = [opt_p]
+        lib.km_default_options.restype = None
+        lib.kmedoids_workspace_size.argtypes = [i64, i32, i32, opt_p]
+        lib.kmedoids_workspace_size.restype = sz
+        for name in ("kmedoids_swap", "kmedoids_run"):
+            f = getattr(lib, name)
+            f.argtypes = [P, i32, i64, i64, i32, P, P, opt_p, res_p, P, sz, P]
+            f.restype = i32
+        lib.kmedoids_build.argtypes = [P, i32, i64, i64, i32, P, opt_p, res_p,
+                                       P, sz, P]
+        lib.kmedoids_build.restype = i32
+        lib.kmedoids_eval_swaps.argtypes = [P, i32, i64, i64, i32, P, P, P,
+                                            P, P, P, P, sz, P]
+        lib.kmedoids_eval_swaps.restype = i32
+        lib.kmedoids_cache.argtypes = [P, i32, i64, i64, i32, P, P, P, P, P,
+                                       P, P, sz, P]
+        lib.kmedoids_cache.restype = i32
+        lib.kmedoids_last_error.restype = ctypes.c_char_p
+        lib.kmedoids_version.restype = ctypes.c_char_p
+        _LIB = lib
+    return _LIB
+
+
+def _check(status: int):
+    if status != 0:
+        raise KmError(status, load().kmedoids_last_error().decode())
+
+
+def _torch():
+    import torch
+    if not torch.cuda.is_available():
+        raise RuntimeError("libkmedoids needs a CUDA device; none is present")
+    return torch
+
+
+def _dtype_code(D) -> int:
+    torch = _torch()
+    if D.dtype == torch.int32:
+        return KM_I32
+    if D.dtype == torch.float32:
+        return KM_F32
+    raise TypeError("D must be int32 or float32 (got %s)" % D.dtype)
+
+
+def _matrix(D, n):
+    if D.dim() != 2 or not D.is_cuda or D.stride(1) != 1:
+        raise ValueError("D must be a 2-D CUDA tensor with unit column stride")
+    n = D.shape[0] if n is None else int(n)
+    return n, D.stride(0)
+
+
+def _stream():
+    return ctypes.c_void_p(_torch().cuda.current_stream().cuda_stream)
+
+
+def options(variant="fastpam1", max_iter=0, tol=0.0, fastpam2_tol=0.0,
+            rows_per_tile=0, profile=False, trace=0):
+    o = km_options()
+    load().km_default_options(ctypes.byref(o))
+    o.variant = VARIANTS[variant] if isinstance(variant, str) else int(variant)
+    o.max_iter = int(max_iter)
+    o.tol = float(tol)
+    o.fastpam2_tol = float(fastpam2_tol)
+    o.rows_per_tile = int(rows_per_tile)
+    o.profile = 1 if profile else 0
+    o.trace_capacity = int(trace)
+    return o
+
+
+def workspace_size(n, k, dtype_code, opts=None) -> int:
+    return int(load().kmedoids_workspace_size(
+        int(n), int(k), int(dtype_code),
+        ctypes.byref(opts) if opts is not None else None))
+
+
+def workspace(n, k, dtype_code, opts=None, device=None):
+    """Allocate a device workspace (caller-owned torch tensor)."""
+    torch = _torch()
+    nbytes = workspace_size(n, k, dtype_code, opts)
+    if nbytes == 0:
+        raise KmError(1, "invalid sizes for a workspace")
+    return torch.empty(nbytes, dtype=torch.uint8, device=device or "cuda")
+
+
+def _result(res: km_result, o: km_options, k: int) -> dict:
+    out = {f: getattr(res, f) for f, _ in km_result._fields_}
+    return out
+
+
+class _Trace:
+    def __init__(self, o: km_options, cap: int, k: int, want_gains: bool):
+        import numpy as np
+        self.np = np
+        self.d = np.zeros(max(cap, 1), np.float64)
+        self.s = np.zeros(max(cap, 1), np.int32)
+        self.c = np.zeros(max(cap, 1), np.int32)
+        self.t = np.zeros(max(cap, 1), np.int64)
+        self.g = np.zeros(max(k, 1), np.float64)
+        if cap > 0:
+            o.trace_delta = self.d.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+            o.trace_slot = self.s.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+            o.trace_cand = self.c.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+            o.trace_time_ns = self.t.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))
+        if want_gains:
+            o.build_gains = self.g.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+    def items(self, nswaps: int):
+        m = min(nswaps, len(self.d))
+        return [(float(self.d[i]), int(self.s[i]), int(self.c[i]))
+                for i in range(m)]
+
+
+def _call(fn_name, D, k, medoids, labels, n, ws, opts_kw, want_gains):
+    torch = _torch()
+    lib = load()
+    n, ld = _matrix(D, n)
+    code = _dtype_code(D)
+    o = options(**opts_kw)
+    tr = _Trace(o, o.trace_capacity, k, want_gains)
+    if ws is None:
+        ws = workspace(n, k, code, o, device=D.device)
+    res = km_result()
+    fn = getattr(lib, fn_name)
+    if fn_name == "kmedoids_build":
+        st = fn(ctypes.c_void_p(D.data_ptr()), code, n, ld, k,
+                ctypes.c_void_p(medoids.data_ptr()), ctypes.byref(o),
+                ctypes.byref(res), ctypes.c_void_p(ws.data_ptr()),
+                ws.numel(), _stream())
+    else:
+        st = fn(ctypes.c_void_p(D.data_ptr()), code, n, ld, k,
+                ctypes.c_void_p(medoids.data_ptr()),
+                ctypes.c_void_p(labels.data_ptr() if labels is not None else 0),
+                ctypes.byref(o), ctypes.byref(res),
+                ctypes.c_void_p(ws.data_ptr()), ws.numel(), _stream())
+    if st not in (0, 4):
+        _check(st)
+    out = _result(res, o, k)
+    out["status_name"] = STATUS.get(st, st)
+    out["converged"] = st == 0
+    out["medoids"] = medoids
+    out["labels"] = labels
+    out["trace"] = tr.items(res.swaps) if o.trace_capacity > 0 else []
+    out["trace_time_ns"] = tr.t[:min(res.swaps, o.trace_capacity)].copy() \
+        if o.trace_capacity > 0 else None
+    if want_gains:
+        out["build_gains"] = tr.g[:k].copy()
+    return out
+
+
+def run(D, k, n=None, labels=True, ws=None, **kw):
+    """BUILD + SWAP (kmedoids_run).  kw: variant, max_iter, tol,
+    fastpam2_tol, rows_per_tile, profile, trace."""
+    torch = _torch()
+    n_ = D.shape[0] if n is None else n
+    med = torch.empty(k, dtype=torch.int32, device=D.device)
+    lab = torch.empty(n_, dtype=torch.int32, device=D.device) if labels else None
+    return _call("kmedoids_run", D, k, med, lab, n, ws, kw, True)
+
+
+def build(D, k, n=None, ws=None, **kw):
+    """PAM BUILD (kmedoids_build)."""
+    torch = _torch()
+    med = torch.empty(k, dtype=torch.int32, device=D.device)
+    return _call("kmedoids_build", D, k, med, None, n, ws, kw, True)
+
+
+def swap(D, medoids, n=None, labels=True, ws=None, **kw):
+    """SWAP from the given medoids (kmedoids_swap); medoids are copied."""
+    torch = _torch()
+    med = torch.as_tensor(medoids, dtype=torch.int32).to(D.device).clone()
+    n_ = D.shape[0] if n is None else n
+    lab = torch.empty(n_, dtype=torch.int32, device=D.device) if labels else None
+    return _call("kmedoids_swap", D, med.numel(), med, lab, n, ws, kw, False)
+
+
+def eval_swaps(D, medoids, n=None, ws=None):
+    """One FastPAM1 evaluation (kmedoids_eval_swaps): per-candidate best
+    Delta and slot tensors, and the best (Delta, slot, candidate)."""
+    torch = _torch()
+    lib = load()
+    n, ld = _matrix(D, n)
+    code = _dtype_code(D)
+    med = torch.as_tensor(medoids, dtype=torch.int32).to(D.device).contiguous()
+    k = med.numel()
+    if ws is None:
+        ws = workspace(n, k, code, None, device=D.device)
+    cd = torch.empty(n, dtype=torch.float64, device=D.device)
+    cs = torch.empty(n, dtype=torch.int32, device=D.device)
+    bd = ctypes.c_double()
+    bs = ctypes.c_int32()
+    bc = ctypes.c_int32()
+    _check(lib.kmedoids_eval_swaps(
+        ctypes.c_void_p(D.data_ptr()), code, n, ld, k,
+        ctypes.c_void_p(med.data_ptr()), ctypes.c_void_p(cd.data_ptr()),
+        ctypes.c_void_p(cs.data_ptr()), ctypes.byref(bd), ctypes.byref(bs),
+        ctypes.byref(bc), ctypes.c_void_p(ws.data_ptr()), ws.numel(),
+        _stream()))
+    return cd, cs, (bd.value, bs.value, bc.value)
+
+
+def cache(D, medoids, n=None, ws=None):
+    """Per-point cache (kmedoids_cache): near, sec, dn, ds, removal loss."""
+    torch = _torch()
+    lib = load()
+    n, ld = _matrix(D, n)
+    code = _dtype_code(D)
+    med = torch.as_tensor(medoids, dtype=torch.int32).to(D.device).contiguous()
+    k = med.numel()
+    if ws is None:
+        ws = workspace(n, k, code, None, device=D.device)
+    near = torch.empty(n, dtype=torch.int32, device=D.device)
+    sec = torch.empty(n, dtype=torch.int32, device=D.device)
+    dn = torch.empty(n, dtype=D.dtype, device=D.device)
+    ds = torch.empty(n, dtype=D.dtype, device=D.device)
+    rl = torch.empty(k, dtype=torch.float64, device=D.device)
+    _check(lib.kmedoids_cache(
+        ctypes.c_void_p(D.data_ptr()), code, n, ld, k,
+        ctypes.c_void_p(med.data_ptr()), ctypes.c_void_p(near.data_ptr()),
+        ctypes.c_void_p(sec.data_ptr()), ctypes.c_void_p(dn.data_ptr()),
+        ctypes.c_void_p(ds.data_ptr()), ctypes.c_void_p(rl.data_ptr()),
+        ctypes.c_void_p(ws.data_ptr()), ws.numel(), _stream()))
+    return near, sec, dn, ds, rl
+
+
+def version() -> str:
+    return load().kmedoids_version().decode()

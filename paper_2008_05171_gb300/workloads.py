@@ -33,10 +33,12 @@ import numpy as np
 SEED_BASE = 1000
 
 
-def rng_for(tag: int | str, extra: int = 0) -> np.random.Generator:
-    """numpy PCG64 stream for workload ``tag`` (int config index or name)."""
-    if isinstance(tag, str):
-        tag = sum((i + 1) * ord(ch) for i, ch in enumerate(tag)) % 997
+def rng_for(tag, extra: int = 0) -> np.random.Generator:
+    """numpy PCG64 stream for workload ``tag`` (an int index, or any value
+    whose repr names the input)."""
+    if not isinstance(tag, (int, np.integer)):
+        txt = repr(tag)
+        tag = sum((i + 1) * ord(ch) for i, ch in enumerate(txt)) % 99991
     return np.random.Generator(np.random.PCG64(SEED_BASE + int(tag) +
                                                1_000_003 * int(extra)))
 

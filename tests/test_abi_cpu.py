@@ -1,0 +1,85 @@
+"""Host-side checks of the C-ABI library that need no GPU: it loads, it
+exports every function include/kmedoids.h declares, the workspace size is
+sane, and argument validation returns a status (no launch happens)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "kmedoids.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2008_05171_gb300 import build as b
+    b.build()
+    import paper_2008_05171_gb300.kmedoids as km
+    return km.load()
+
+
+def declared_functions():
+    txt = open(HEADER).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    names = re.findall(r"^[A-Za-z_][\w\s\*]*?\b(km\w*|kmedoids\w*)\s*\(",
+                       txt, flags=re.M)
+    return sorted(set(names))
+
+
+def test_exports_every_declared_symbol(lib):
+    names = declared_functions()
+    assert "kmedoids_run" in names and len(names) >= 8
+    for name in names:
+        assert hasattr(lib, name), name
+    import paper_2008_05171_gb300.kmedoids as km
+    assert sorted(km.EXPORTS) == names
+
+
+def test_workspace_size(lib):
+    import paper_2008_05171_gb300.kmedoids as km
+    a = km.workspace_size(1000, 10, km.KM_I32)
+    b = km.workspace_size(20000, 100, km.KM_F32)
+    assert 0 < a < b
+    assert km.workspace_size(10, 11, km.KM_F32) == 0  # k > n
+    assert km.workspace_size(0, 1, km.KM_F32) == 0
+    assert km.workspace_size(10, 2, 7) == 0           # unknown dtype
+    o = km.options(variant="fastpam2")
+    assert km.workspace_size(20000, 100, km.KM_F32, o) > b
+    o = km.options(trace=1000)
+    assert km.workspace_size(20000, 100, km.KM_F32, o) > b
+
+
+def test_invalid_arguments_return_status(lib):
+    import paper_2008_05171_gb300.kmedoids as km
+    o = km.options()
+    res = km.km_result()
+    P = ctypes.c_void_p
+    buf = (ctypes.c_char * 4096)()
+    fake = ctypes.addressof(buf) + (256 - ctypes.addressof(buf) % 256) % 256
+    cases = [
+        (None, 1, 100, 100, 10, 1),      # D NULL
+        (fake, 5, 100, 100, 10, 1),      # dtype
+        (fake, 1, 100, 100, 0, 1),       # k = 0
+        (fake, 1, 100, 100, 101, 1),     # k > n
+        (fake, 1, 100, 99, 10, 1),       # ld < n
+        (fake, 1, 100, 102, 10, 1),      # ld not a multiple of 4
+        (fake + 4, 1, 100, 100, 10, 1),  # misaligned D
+        (fake, 1, 100, 100, 10, 2),      # workspace too small
+    ]
+    for D, dt, n, ld, k, want in cases:
+        st = lib.kmedoids_run(P(D), dt, n, ld, k, P(fake), None,
+                              ctypes.byref(o), ctypes.byref(res), P(fake), 64,
+                              None)
+        assert st == want, (D, dt, n, ld, k, st)
+        assert lib.kmedoids_last_error()
+    bad = km.options(variant=9)
+    st = lib.kmedoids_run(P(fake), 1, 100, 100, 10, P(fake), None,
+                          ctypes.byref(bad), ctypes.byref(res), P(fake), 1 << 30,
+                          None)
+    assert st == 1
+
+
+def test_version(lib):
+    import paper_2008_05171_gb300.kmedoids as km
+    assert "sm_103a" in km.version()

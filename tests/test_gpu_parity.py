@@ -1,0 +1,324 @@
+"""Parity of the CUDA path (through the C ABI) against the FP64 oracle.
+
+Integer dissimilarities: bit-exact medoids, labels, TD, BUILD gains, swap
+trajectories and per-candidate Delta values.  Float dissimilarities: the
+tolerance the method allows -- TD within 1e-6 relative, per-candidate Delta
+within 1e-9 * TD (the GPU sums the same FP64 terms in another order), and
+every accepted swap replayed by the oracle from the same pre-swap state.
+Sizes span several 1024-column chunks and candidate tiles with ragged
+tails, padded row strides, and the degenerate k = 1, 2, n cases.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2008_05171_gb300 import workloads as wl
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():  # pragma: no cover - CPU containers
+    pytest.skip("needs a CUDA device", allow_module_level=True)
+
+import paper_2008_05171_gb300.kmedoids as km  # noqa: E402
+
+
+def dev(Dh):
+    return torch.from_numpy(np.ascontiguousarray(Dh)).cuda()
+
+
+def int_instance(n, seed, hi=1000, dim=2, ld=None):
+    X = wl.int_coords(n, dim, hi, seed=seed)
+    return wl.manhattan_int32(X, ld=ld)
+
+
+def float_instance(n, d, centers, seed, ld=None):
+    X = wl.gmm_points(n, d, centers, seed=seed)
+    return wl.euclidean_f32(X, ld=ld)
+
+
+def rand_medoids(n, k, seed):
+    return np.random.default_rng(seed).choice(n, size=k, replace=False)
+
+
+INT_CASES = [(5, 2, None), (37, 3, 40), (300, 7, None), (1000, 10, None),
+             (2100, 20, 2112), (2500, 40, None)]
+
+
+# ------------------------------------------------------------------ cache
+
+@pytest.mark.parametrize("n,k,ld", INT_CASES)
+def test_cache_int(n, k, ld):
+    Dh = int_instance(n, ("cache", n), ld=ld)
+    med = rand_medoids(n, k, n)
+    near, sec, dn, ds, rl = km.cache(dev(Dh), med)
+    onear, osec, odn, ods = oracle.cache(Dh, med)
+    assert (near.cpu().numpy() == onear).all()
+    assert (sec.cpu().numpy() == osec).all()
+    assert (dn.cpu().numpy() == odn).all()
+    assert (ds.cpu().numpy() == ods).all()
+    orl = oracle.removal_loss(onear, odn, ods, k)
+    assert (rl.cpu().numpy() == orl).all()
+
+
+def test_cache_float_and_k1():
+    Dh = float_instance(1500, 8, 12, "cache-f")
+    med = rand_medoids(1500, 12, 5)
+    near, sec, dn, ds, rl = km.cache(dev(Dh), med)
+    onear, osec, odn, ods = oracle.cache(Dh, med)
+    assert (near.cpu().numpy() == onear).all()
+    assert (dn.cpu().numpy().astype(np.float64) == odn).all()
+    assert (ds.cpu().numpy().astype(np.float64) == ods).all()
+    orl = oracle.removal_loss(onear, odn, ods, 12)
+    assert np.allclose(rl.cpu().numpy(), orl, rtol=1e-12, atol=1e-9)
+    near, sec, dn, ds, rl = km.cache(dev(Dh), [7])
+    assert (near.cpu().numpy() == 0).all() and (sec.cpu().numpy() == -1).all()
+    assert (dn.cpu().numpy() == Dh[:, 7]).all()
+
+
+# ------------------------------------------------------------- evaluation
+
+@pytest.mark.parametrize("n,k,ld", INT_CASES)
+def test_eval_int_exact(n, k, ld):
+    Dh = int_instance(n, ("eval", n), ld=ld)
+    med = rand_medoids(n, k, n + 1)
+    cd, cs, best = km.eval_swaps(dev(Dh), med)
+    ocd, ocs, obest = oracle.eval_swaps(Dh, med, method="fastpam1")
+    cd = cd.cpu().numpy()
+    cs = cs.cpu().numpy()
+    assert (cs == ocs).all()
+    assert (cd == ocd).all()
+    assert best == obest
+
+
+@pytest.mark.parametrize("n,d,c,k", [(700, 4, 8, 8), (3000, 16, 30, 30),
+                                     (2049, 8, 20, 64)])
+def test_eval_float(n, d, c, k):
+    Dh = float_instance(n, d, c, ("evalf", n))
+    med = rand_medoids(n, k, n)
+    cd, cs, best = km.eval_swaps(dev(Dh), med)
+    ocd, ocs, obest = oracle.eval_swaps(Dh, med, method="fastpam1")
+    cd = cd.cpu().numpy()
+    cs = cs.cpu().numpy()
+    tdv = oracle.td(Dh, med)
+    tol = 1e-9 * tdv
+    nm = ocs >= 0
+    assert (cs[~nm] == -1).all()
+    assert np.max(np.abs(cd[nm] - ocd[nm])) <= tol
+    # the slot chosen is optimal up to the tolerance (exact ties may differ)
+    for c_ in np.nonzero(nm & (cs != ocs))[0]:
+        dl = oracle.swap_delta(Dh, med, cs[c_], c_)
+        assert dl <= ocd[c_] + tol
+    assert abs(best[0] - obest[0]) <= tol
+
+
+# ----------------------------------------------------------------- BUILD
+
+@pytest.mark.parametrize("n,k,ld", INT_CASES + [(1000, 1000, None)])
+def test_build_int_exact(n, k, ld):
+    Dh = int_instance(n, ("build", n), ld=ld)
+    out = km.build(dev(Dh), k)
+    omed, otd, ogains = oracle.pam_build(Dh, k)
+    assert out["medoids"].cpu().numpy().tolist() == omed.tolist()
+    assert out["td_i64"] == int(otd)
+    assert out["build_gains"].tolist() == ogains.tolist()
+    assert out["build_steps"] == k
+
+
+def test_build_float():
+    Dh = float_instance(2600, 16, 25, "build-f")
+    k = 25
+    out = km.build(dev(Dh), k)
+    med = out["medoids"].cpu().numpy()
+    tdv = oracle.td(Dh, med)
+    assert abs(out["td"] - tdv) <= 1e-9 * tdv
+    # replay each step: the GPU's choice is the oracle's best up to 1e-6*TD
+    gains = out["build_gains"]
+    for t in range(k):
+        g = oracle.build_gains(Dh, med[:t])
+        best = g.min()
+        scale = abs(g[med[t]]) if t == 0 else tdv
+        assert g[med[t]] <= best + 1e-6 * scale
+        assert abs(gains[t] - g[med[t]]) <= 1e-6 * scale
+        if g[med[t]] != best:
+            second = np.partition(g, 1)[1]
+            assert second - best <= 1e-6 * scale  # only near-ties may differ
+
+
+# ------------------------------------------------------------ full runs
+
+def assert_same_run(out, ref):
+    assert out["medoids"].cpu().numpy().tolist() == ref["medoids"].tolist()
+    assert out["td_i64"] == int(ref["td"])
+    assert out["swaps"] == ref["swaps"]
+    assert out["iterations"] == ref["iterations"]
+    assert [(int(d), i, c) for d, i, c in out["trace"]] == \
+        [(int(d), i, c) for d, i, c in ref["trace"]]
+
+
+@pytest.mark.parametrize("variant", ["fastpam1", "fasterpam", "fastpam2"])
+@pytest.mark.parametrize("n,k,ld", INT_CASES)
+def test_swap_int_exact(variant, n, k, ld):
+    Dh = int_instance(n, ("swap", n), ld=ld)
+    start = rand_medoids(n, k, n + 7)
+    out = km.swap(dev(Dh), start, variant=variant, trace=100000)
+    ref = oracle.swap(Dh, start, variant=variant, trace_cap=100000)
+    assert_same_run(out, ref)
+    if variant == "fasterpam":
+        assert out["visited"] == ref["visited"]
+    lab = out["labels"].cpu().numpy()
+    _, olab = oracle.td(Dh, ref["medoids"], return_labels=True)
+    assert (lab == olab).all()
+
+
+def test_run_manhattan_1000_exact():
+    """Integer workload: n=1000 Manhattan int32, k=10, BUILD + FastPAM1."""
+    Dh, k = wl.manhattan_1000()
+    out = km.run(dev(Dh), k, trace=1000)
+    ref = oracle.run(Dh, k, variant="fastpam1")
+    assert_same_run(out, ref)
+    assert out["build_gains"].tolist() == oracle.pam_build(Dh, k)[2].tolist()
+    for v in ("fasterpam", "fastpam2"):
+        o2 = km.run(dev(Dh), k, variant=v, trace=1000)
+        r2 = oracle.run(Dh, k, variant=v)
+        assert_same_run(o2, r2)
+
+
+def replay_float(Dh, start, out, sample=None, kind="fastpam1"):
+    """Every accepted swap: |Delta_gpu - Delta_oracle| <= 1e-9 * TD and
+    Delta_oracle < 0; for FastPAM1 it is within 1e-6 * TD of the oracle's
+    best swap of that state, for FasterPAM within 1e-6 * TD of the best slot
+    for that candidate (Alg. 4 swaps each candidate with its best slot)."""
+    med = np.array(start, np.int32)
+    trace = out["trace"]
+    idx = range(len(trace)) if sample is None else sample
+    for j, (d, i, c) in enumerate(trace):
+        if j in idx:
+            tdv = oracle.td(Dh, med)
+            dor = oracle.swap_delta(Dh, med, i, c)
+            assert abs(d - dor) <= 1e-9 * tdv, (j, d, dor)
+            assert dor < 1e-9 * tdv
+            if kind in ("fastpam1", "fasterpam"):
+                cd, _, best = oracle.eval_swaps(Dh, med)
+                ref = best[0] if kind == "fastpam1" else cd[c]
+                assert dor <= ref + 1e-6 * tdv
+        med[i] = c
+    assert med.tolist() == out["medoids"].cpu().numpy().tolist()
+    return med
+
+
+@pytest.mark.parametrize("variant", ["fastpam1", "fasterpam", "fastpam2"])
+def test_swap_float(variant):
+    Dh = float_instance(2500, 16, 20, ("swapf", variant))
+    start = rand_medoids(2500, 20, 3)
+    out = km.swap(dev(Dh), start, variant=variant, trace=100000)
+    kind = "fastpam1" if variant == "fastpam1" else (
+        "fasterpam" if variant == "fasterpam" else "fastpam2")
+    med = replay_float(Dh, start, out, kind=kind)
+    tdv = oracle.td(Dh, med)
+    assert abs(out["td"] - tdv) <= 1e-9 * tdv
+    assert abs(out["td_bookkept"] - tdv) <= 1e-9 * tdv
+    _, _, best = oracle.eval_swaps(Dh, med)
+    assert best[0] >= -1e-9 * tdv  # locally optimal
+    ref = oracle.swap(Dh, start, variant=variant)
+    if variant == "fastpam1":
+        assert abs(out["td"] - ref["td"]) <= 1e-6 * ref["td"]
+
+
+def test_run_float_gmm():
+    Dh = float_instance(4000, 16, 40, "runf")
+    k = 40
+    out = km.run(dev(Dh), k, trace=10000)
+    ref = oracle.run(Dh, k, variant="fastpam1")
+    assert abs(out["td"] - ref["td"]) <= 1e-6 * ref["td"]
+    if out["medoids"].cpu().numpy().tolist() != ref["medoids"].tolist():
+        # divergence is allowed only through near-ties
+        replay_float(Dh, ref["build_medoids"], out)
+
+
+# --------------------------------------------------------- degenerate k
+
+@pytest.mark.parametrize("dtype", ["int", "float"])
+def test_k_equals_one(dtype):
+    Dh = int_instance(900, "k1") if dtype == "int" else \
+        float_instance(900, 4, 3, "k1f")
+    for v in ("fastpam1", "fasterpam", "fastpam2"):
+        out = km.swap(dev(Dh), [899], variant=v, trace=10)
+        ref = oracle.swap(Dh, [899], variant=v)
+        assert out["medoids"].cpu().numpy().tolist() == ref["medoids"].tolist()
+        assert out["iterations"] == ref["iterations"]
+        assert out["swaps"] == ref["swaps"]
+        assert abs(out["td"] - ref["td"]) <= 1e-6 * ref["td"]
+    out = km.run(dev(Dh), 1)
+    omed, otd, _ = oracle.pam_build(Dh, 1)
+    assert out["medoids"].cpu().numpy().tolist() == omed.tolist()
+    assert out["swaps"] == 0
+
+
+def test_k_equals_n_and_tiny():
+    Dh = int_instance(6, "kn")
+    out = km.run(dev(Dh), 6)
+    assert out["td_i64"] == 0 and out["swaps"] == 0
+    assert sorted(out["medoids"].cpu().numpy().tolist()) == list(range(6))
+    for n in (2, 3, 4):
+        Dh = int_instance(n, ("tiny", n))
+        for k in range(1, n + 1):
+            out = km.run(dev(Dh), k, trace=64)
+            ref = oracle.run(Dh, k, variant="fastpam1")
+            assert out["medoids"].cpu().numpy().tolist() == ref["medoids"].tolist()
+            assert out["td_i64"] == int(ref["td"])
+
+
+def test_all_distances_equal():
+    Dh = np.zeros((64, 64), np.int32)
+    out = km.run(dev(Dh), 5, trace=64)
+    ref = oracle.run(Dh, 5, variant="fastpam1")
+    assert out["medoids"].cpu().numpy().tolist() == ref["medoids"].tolist()
+    assert out["td_i64"] == 0 and out["swaps"] == 0
+
+
+def test_duplicates_and_ties():
+    X = np.repeat(wl.int_coords(150, 2, 8, seed="dup"), 3, axis=0)
+    Dh = wl.manhattan_int32(X)
+    for v in ("fastpam1", "fasterpam", "fastpam2"):
+        out = km.run(dev(Dh), 12, variant=v, trace=10000)
+        ref = oracle.run(Dh, 12, variant=v)
+        assert_same_run(out, ref)
+
+
+def test_max_iter_not_converged():
+    Dh = int_instance(800, "cap")
+    start = rand_medoids(800, 10, 1)
+    full = oracle.swap(Dh, start, variant="fastpam1")
+    assert full["swaps"] >= 2
+    out = km.swap(dev(Dh), start, max_iter=1, trace=10)
+    assert out["status_name"] == "KM_E_NOT_CONVERGED"
+    assert out["swaps"] == 1 and out["iterations"] == 1
+    assert out["trace"][0][1:] == full["trace"][0][1:]
+
+
+def test_invalid_medoids_and_workspace():
+    Dh = int_instance(100, "inv")
+    D = dev(Dh)
+    with pytest.raises(km.KmError):
+        km.swap(D, [1, 1, 2])
+    with pytest.raises(km.KmError):
+        km.swap(D, [1, 200])
+    ws = torch.empty(1024, dtype=torch.uint8, device="cuda")
+    with pytest.raises(km.KmError) as e:
+        km.run(D, 5, ws=ws)
+    assert e.value.status == 2
+
+
+def test_stream_and_workspace_reuse():
+    Dh = int_instance(1200, "reuse")
+    D = dev(Dh)
+    code = km.KM_I32
+    ws = km.workspace(1200, 9, code, km.options(trace=100))
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        a = km.run(D, 9, ws=ws, trace=100)
+        b = km.run(D, 9, ws=ws, trace=100)
+    s.synchronize()
+    assert a["medoids"].cpu().tolist() == b["medoids"].cpu().tolist()
+    assert a["td_i64"] == b["td_i64"]

@@ -320,3 +320,19 @@ def test_thread_count_does_not_change_results():
     finally:
         oracle.set_threads(os.cpu_count() or 1)
     assert (a[0] == b[0]).all() and (a[1] == b[1]).all() and a[2] == b[2]
+
+
+def test_build_gains_step_matches_build():
+    for D in bf.tiny_instances(91, 30, n_lo=4, n_hi=12):
+        n = D.shape[0]
+        k = max(1, n // 2)
+        med, _, steps = oracle.pam_build(D, k)
+        for t in range(k):
+            g = oracle.build_gains(D, med[:t])
+            assert int(np.argmin(g)) == med[t] and g[med[t]] == steps[t]
+            base = bf.td(D, list(med[:t])) if t else 0.0
+            for c in range(n):
+                if c in med[:t]:
+                    assert g[c] == np.inf
+                elif t:
+                    assert g[c] == bf.td(D, list(med[:t]) + [c]) - base
