@@ -173,6 +173,29 @@ km_status kmedoids_cache(const void *D, int32_t dtype, int64_t n, int64_t ld,
                          int32_t *sec, void *dn, void *ds, double *removal,
                          void *ws, size_t ws_bytes, void *stream);
 
+/* kmedoids_eval_swaps without a caller-provided workspace, for callers that
+ * cannot allocate device memory when they evaluate swaps (a frozen memory
+ * pool, a plugin that must not use the host application's allocator, a
+ * real-time loop that cannot risk a blocking allocation).  The paper has no
+ * counterpart: this is a deployment interface of this library.
+ * Same arguments and results as kmedoids_eval_swaps, without ws/ws_bytes.
+ * Scratch: a fixed 2 MiB array in device memory that is part of the
+ * library image; every GPU that loads the library holds it until the
+ * process exits.  Limits: n <= 32768 and k <= 512 (larger sizes return
+ * KM_E_UNSUPPORTED with a message; nothing is launched).  Allocates nothing
+ * (no cudaMalloc, cudaFree or allocating library routine).  The first call
+ * on a device looks up the array's device address (cudaGetSymbolAddress)
+ * with that device current; make that first call before any stream capture
+ * on the device.  All calls share the one array: the call clears what must
+ * start at zero, but calls that overlap on the GPU (other streams, other
+ * host threads) race on it and must be serialised by the caller. */
+km_status kmedoids_eval_swaps_static(const void *D, int32_t dtype, int64_t n,
+                                     int64_t ld, int32_t k,
+                                     const int32_t *medoids,
+                                     double *cand_delta, int32_t *cand_slot,
+                                     double *best_delta, int32_t *best_slot,
+                                     int32_t *best_cand, void *stream);
+
 /* Thread-local description of the last failure ("" if none). */
 const char *kmedoids_last_error(void);
 

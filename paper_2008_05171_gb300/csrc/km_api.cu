@@ -469,6 +469,8 @@ km_status finish(Ctx& c, KmState* h, int32_t* medoids_out, int32_t* labels_out, 
 
 }  // namespace
 
+void km::set_last_error(const char* msg) { g_err = msg ? msg : ""; }
+
 // ====================================================================== ABI
 extern "C" {
 

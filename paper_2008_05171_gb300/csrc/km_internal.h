@@ -108,4 +108,7 @@ cudaError_t launch_removal_to_double(int dtype, const PointArgs& a, cudaStream_t
 
 int device_sm_count();
 
+// Replace the thread-local message returned by kmedoids_last_error().
+void set_last_error(const char* msg);
+
 }  // namespace km

@@ -22,7 +22,8 @@ STATUS = {0: "KM_OK", 1: "KM_E_INVALID", 2: "KM_E_WORKSPACE", 3: "KM_E_CUDA",
           7: "KM_E_UNSUPPORTED"}
 EXPORTS = ["km_default_options", "kmedoids_workspace_size", "kmedoids_build",
            "kmedoids_swap", "kmedoids_run", "kmedoids_eval_swaps",
-           "kmedoids_cache", "kmedoids_last_error", "kmedoids_version"]
+           "kmedoids_cache", "kmedoids_last_error", "kmedoids_version",
+           "kmedoids_eval_swaps_static"]
 
 
 class KmError(RuntimeError):
@@ -94,6 +95,9 @@ def load(path: str = LIB_PATH):
         lib.kmedoids_cache.argtypes = [P, i32, i64, i64, i32, P, P, P, P, P,
                                        P, P, sz, P]
         lib.kmedoids_cache.restype = i32
+        lib.kmedoids_eval_swaps_static.argtypes = [P, i32, i64, i64, i32, P,
+                                                   P, P, P, P, P, P]
+        lib.kmedoids_eval_swaps_static.restype = i32
         lib.kmedoids_last_error.restype = ctypes.c_char_p
         lib.kmedoids_version.restype = ctypes.c_char_p
         _LIB = lib
@@ -274,6 +278,29 @@ def eval_swaps(D, medoids, n=None, ws=None):
         ctypes.c_void_p(cs.data_ptr()), ctypes.byref(bd), ctypes.byref(bs),
         ctypes.byref(bc), ctypes.c_void_p(ws.data_ptr()), ws.numel(),
         _stream()))
+    return cd, cs, (bd.value, bs.value, bc.value)
+
+
+def eval_swaps_static(D, medoids, n=None):
+    """kmedoids_eval_swaps_static: the same evaluation pass with the
+    library's fixed device scratch instead of a workspace (for callers that
+    cannot allocate device memory; n <= 32768, k <= 512)."""
+    torch = _torch()
+    lib = load()
+    n, ld = _matrix(D, n)
+    code = _dtype_code(D)
+    med = torch.as_tensor(medoids, dtype=torch.int32).to(D.device).contiguous()
+    k = med.numel()
+    cd = torch.empty(n, dtype=torch.float64, device=D.device)
+    cs = torch.empty(n, dtype=torch.int32, device=D.device)
+    bd = ctypes.c_double()
+    bs = ctypes.c_int32()
+    bc = ctypes.c_int32()
+    _check(lib.kmedoids_eval_swaps_static(
+        ctypes.c_void_p(D.data_ptr()), code, n, ld, k,
+        ctypes.c_void_p(med.data_ptr()), ctypes.c_void_p(cd.data_ptr()),
+        ctypes.c_void_p(cs.data_ptr()), ctypes.byref(bd), ctypes.byref(bs),
+        ctypes.byref(bc), _stream()))
     return cd, cs, (bd.value, bs.value, bc.value)
 
 
