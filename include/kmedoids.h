@@ -24,7 +24,12 @@
  *           ld a multiple of 4 (rows are streamed with 16-byte bulk copies);
  *           otherwise the call returns KM_E_INVALID.
  *   dtype   KM_I32 (int32 distances; sums in int64, results exact) or
- *           KM_F32 (float32 distances; Delta TD and TD sums in FP64).
+ *           KM_F32 (float32 distances; TD and BUILD sums in FP64, the SWAP
+ *           Delta sums in exact 64-bit fixed point with a per-call scale
+ *           2^f, f = 60 - ceil(log2(n+1)) - (exponent of the largest entry),
+ *           i.e. ~2^-(60-log2 n) resolution relative to the largest
+ *           distance; float inputs are scanned once per call and entries
+ *           that are negative or not finite return KM_E_NUMERIC).
  *   medoids int32 point indices in SLOT order, DEVICE memory.  A swap puts
  *           the new medoid into the removed medoid's slot.  Labels are slots.
  *   ws      DEVICE workspace of at least kmedoids_workspace_size() bytes,
@@ -83,7 +88,10 @@ typedef struct km_options {
   int32_t rows_per_tile;  /* candidate rows per CTA tile; 0 = automatic */
   int32_t profile;        /* nonzero: time kernels with CUDA events */
   int32_t trace_capacity; /* entries available in the trace arrays */
-  int32_t reserved0;
+  int32_t tune;           /* kernel geometry override for tuning sweeps:
+                             0 = automatic, 1..16 = a fixed (tile rows,
+                             stages, CTAs per SM) entry of the library's
+                             table; KM_E_UNSUPPORTED if it does not fit */
   /* HOST arrays (may be NULL) receiving every applied swap in order. */
   double *trace_delta;
   int32_t *trace_slot;

@@ -4,6 +4,7 @@
 // FasterPAM).  All arithmetic of the method runs in the kernels of
 // km_stream.cu and km_points.cu; this file only orders launches and reads
 // the device state record between batches of passes.
+#include <cmath>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -106,6 +107,8 @@ struct Ctx {
   km_options opt;
   int sms;
   long long launches = 0;
+  int fshift = 0;
+  bool scanned = false;
   KmState* st() const { return reinterpret_cast<KmState*>(ws + L.st); }
   template <class P>
   P* at(size_t off) const {
@@ -135,6 +138,7 @@ km_status check_common(const void* D, int32_t dtype, int64_t n, int64_t ld, int3
       c->opt.rows_per_tile != 4 && c->opt.rows_per_tile != 8 && c->opt.rows_per_tile != 16)
     return fail(KM_E_INVALID, "rows_per_tile must be 0, 1, 2, 4, 8 or 16");
   if (c->opt.trace_capacity < 0) return fail(KM_E_INVALID, "trace_capacity < 0");
+  if (c->opt.tune < 0 || c->opt.tune > 16) return fail(KM_E_INVALID, "tune must be in 0..16");
   if (!make_ws(n, k, &c->opt, &c->L)) return fail(KM_E_INVALID, "invalid sizes");
   if (ws_bytes < c->L.total)
     return fail(KM_E_WORKSPACE, "workspace too small: %zu < %zu bytes", ws_bytes, c->L.total);
@@ -172,6 +176,7 @@ StreamArgs stream_args(const Ctx& c) {
   a.slot_best = c.at<void>(c.L.slot_best);
   a.fp2_order = c.at<int32_t>(c.L.fp2_order);
   a.tol = c.opt.tol;
+  a.fshift = c.fshift;
   return a;
 }
 
@@ -201,11 +206,14 @@ PointArgs point_args(const Ctx& c) {
   a.fp2_order = c.at<int32_t>(c.L.fp2_order);
   a.gains = c.at<double>(c.L.gains);
   a.fp2_tol = c.opt.fastpam2_tol;
+  a.fshift = c.fshift;
+  a.scan = &c.st()->scan_max;
   return a;
 }
 
-int grid_for(const Ctx& c, int rows) {
-  int g = c.sms;
+int grid_for(const Ctx& c, const StreamConfig& cfg) {
+  const int rows = cfg.rows;
+  int g = c.sms * cfg.minb;
   const int need = (c.n + rows - 1) / rows;
   if (g > need) g = need;
   if (g > kMaxGrid) g = kMaxGrid;
@@ -264,9 +272,9 @@ km_status reset_state(const Ctx& c) {
 km_status do_build(Ctx& c, Timer& tm, std::vector<std::pair<int, int>>& ev, km_result* res) {
   KM_CUDA(cudaMemsetAsync(c.at<void>(c.L.is_med), 0, (size_t)c.L.n_pad, c.s));
   StreamConfig cfg;
-  if (!stream_config(kModeBuild, c.k, 0, c.opt.rows_per_tile, &cfg))
+  if (!stream_config(kModeBuild, c.k, 0, c.opt.rows_per_tile, c.opt.tune, &cfg))
     return fail(KM_E_UNSUPPORTED, "no BUILD kernel configuration fits");
-  const int grid = grid_for(c, cfg.rows);
+  const int grid = grid_for(c, cfg);
   StreamArgs sa = stream_args(c);
   PointArgs pa = point_args(c);
   for (int step = 0; step < c.k; ++step) {
@@ -283,7 +291,35 @@ km_status do_build(Ctx& c, Timer& tm, std::vector<std::pair<int, int>>& ev, km_r
 }
 
 // ------------------------------------------------------------------- SWAP
+// Fixed-point exponent of the SWAP sums for float data: the largest entry M
+// and n bound every sum a pass forms by 3 n M < 2^62.
+km_status scan_matrix(Ctx& c) {
+  if (c.dtype != KM_F32) {
+    c.fshift = 0;
+    return KM_OK;
+  }
+  PointArgs pa = point_args(c);
+  KM_LAUNCH(c, launch_matrix_scan(pa, c.s));
+  unsigned h[2] = {0, 0};
+  KM_CUDA(cudaMemcpyAsync(h, &c.st()->scan_max, sizeof(h), cudaMemcpyDeviceToHost, c.s));
+  KM_CUDA(cudaStreamSynchronize(c.s));
+  if (h[1]) return fail(KM_E_NUMERIC, "D holds a negative, infinite or NaN entry");
+  float m;
+  memcpy(&m, &h[0], 4);
+  int em = 0;
+  if (m > 0.f) (void)frexpf(m, &em);  // m < 2^em
+  int bn = 0;
+  while ((1ll << bn) <= (long long)c.n) ++bn;  // n < 2^bn
+  c.fshift = 60 - bn - em;
+  return KM_OK;
+}
+
 km_status swap_setup(Ctx& c) {
+  if (c.dtype == KM_F32 && !c.scanned) {
+    km_status r = scan_matrix(c);
+    if (r != KM_OK) return r;
+    c.scanned = true;
+  }
   KM_CUDA(cudaMemsetAsync(c.at<void>(c.L.is_med), 0, (size_t)c.L.n_pad, c.s));
   KM_CUDA(cudaMemsetAsync(c.at<void>(c.L.removal), 0, 16 * (size_t)c.L.k_pad, c.s));
   KM_CUDA(cudaMemsetAsync(c.at<void>(c.L.td2), 0, 16, c.s));
@@ -297,13 +333,13 @@ km_status swap_k1(Ctx& c, KmState* h) {
   // k = 1: the best single swap is the 1-medoid (Eq. (3)); compare the
   // distance sums of every point with the current medoid's.
   StreamConfig cfg;
-  if (!stream_config(kModeBuild, 1, 0, c.opt.rows_per_tile, &cfg))
+  if (!stream_config(kModeBuild, 1, 0, c.opt.rows_per_tile, c.opt.tune, &cfg))
     return fail(KM_E_UNSUPPORTED, "no kernel configuration fits");
   KM_CUDA(cudaMemsetAsync(c.at<void>(c.L.is_med), 0, (size_t)c.L.n_pad, c.s));
   StreamArgs sa = stream_args(c);
   sa.build_first = 1;
   sa.cand_gain = c.at<double>(c.L.cand_gain);
-  KM_LAUNCH(c, launch_stream(c.dtype, kModeBuild, cfg, grid_for(c, cfg.rows), sa, c.s));
+  KM_LAUNCH(c, launch_stream(c.dtype, kModeBuild, cfg, grid_for(c, cfg), sa, c.s));
   int32_t m = 0;
   KM_CUDA(cudaMemcpyAsync(&m, c.at<int32_t>(c.L.med), 4, cudaMemcpyDeviceToHost, c.s));
   KM_CUDA(cudaStreamSynchronize(c.s));
@@ -351,9 +387,9 @@ km_status do_swap(Ctx& c, Timer& tm, std::vector<std::pair<int, int>>& ev, KmSta
   const int variant = c.opt.variant;
   const int flavour = variant == KM_FASTPAM2 ? kFastPAM2 : (variant == KM_FASTERPAM ? kFasterPAM : kFastPAM1);
   StreamConfig cfg;
-  if (!stream_config(kModeSwap, c.k, flavour, c.opt.rows_per_tile, &cfg))
+  if (!stream_config(kModeSwap, c.k, flavour, c.opt.rows_per_tile, c.opt.tune, &cfg))
     return fail(KM_E_UNSUPPORTED, "k=%d too large for the SWAP kernel's shared memory", c.k);
-  const int grid = grid_for(c, cfg.rows);
+  const int grid = grid_for(c, cfg);
   StreamArgs sa = stream_args(c);
   sa.flavour = flavour;
   sa.win_rows = cfg.rows;
@@ -657,13 +693,13 @@ km_status kmedoids_eval_swaps(const void* D, int32_t dtype, int64_t n, int64_t l
   r = swap_setup(c);
   if (r != KM_OK) return r;
   StreamConfig cfg;
-  if (!stream_config(kModeSwap, k, kEvalOnly, 0, &cfg))
+  if (!stream_config(kModeSwap, k, kEvalOnly, 0, 0, &cfg))
     return fail(KM_E_UNSUPPORTED, "k=%d too large for the SWAP kernel", k);
   StreamArgs sa = stream_args(c);
   sa.flavour = kEvalOnly;
   sa.cand_delta = cand_delta;
   sa.cand_slot = cand_slot;
-  KM_LAUNCH(c, launch_stream(dtype, kModeSwap, cfg, grid_for(c, cfg.rows), sa, c.s));
+  KM_LAUNCH(c, launch_stream(dtype, kModeSwap, cfg, grid_for(c, cfg), sa, c.s));
   PointArgs pa = point_args(c);
   pa.cand_delta = cand_delta;
   pa.cand_slot = cand_slot;

@@ -22,6 +22,7 @@ static_assert(kConsThreads * 4 == kChunk, "4 columns per consumer thread");
 
 // Status codes written by kernels (same values as km_status).
 constexpr int kErrTimeout = 5;
+constexpr int kErrNumeric = 6;
 
 // ---------------------------------------------------------- device state
 // One record per call, in the workspace.  Kernels read it to pick buffers
@@ -54,6 +55,9 @@ struct KmState {
   int pad0;
   double fp2_dstar;         // FastPAM2: |Delta*| of the pass
   long long fp2_dstar_i;
+  unsigned tile_next;       // next candidate tile of the running pass
+  unsigned scan_max;        // matrix scan: largest |d| (float bits)
+  unsigned scan_bad;        // matrix scan: 1 if an entry is < 0 or not finite
 };
 
 // Trace record of an applied swap.
@@ -92,30 +96,55 @@ __device__ __forceinline__ bool key_less(const Key<A>& a, const Key<A>& b) {
 }
 
 // --------------------------------------------------------- type traits
+// SWAP accumulators are 64-bit integers for both data types.  Integer
+// distances enter unchanged.  Float distances enter as exact fixed-point
+// values floor(x * 2^f), with f chosen per call from the largest matrix
+// entry M and n so that every sum the SWAP pass forms (at most 3 n M) fits
+// in 62 bits: each term keeps ~60 - log2(n) significant bits relative to M
+// and the sums are exact and independent of the summation order.  BUILD
+// gains and TD sums use G (FP64 for float data, int64 for integer data).
 template <class T>
 struct Tr;
 
+// floor(x * 2^f) for a finite x >= 0, computed with integer operations only
+// (the FP64 pipe of GB300 is narrow) and without branches.  x < 2^(60 -
+// log2(n) - f) by the choice of f, so the left shift stays below 2^62.
+__device__ __forceinline__ long long fx_of(float x, int f) {
+  const unsigned u = __float_as_uint(x) & 0x7fffffffu;
+  const int e = (int)(u >> 23);
+  const unsigned m = (u & 0x7fffffu) | (e ? 0x800000u : 0u);
+  const int sh = (e ? e : 1) - 150 + f;  // x = m * 2^(sh - f)
+  const int l = min(max(sh, 0), 62);
+  const int r = min(max(-sh, 0), 63);
+  return (long long)(((unsigned long long)m << l) >> r);
+}
+
 template <>
 struct Tr<float> {
-  using A = double;  // accumulator / Delta type
+  using A = long long;  // SWAP accumulator (fixed point)
+  using G = double;     // BUILD gains, TD
   __device__ __forceinline__ static float low() { return -__int_as_float(0x7f800000); }
   __device__ __forceinline__ static float high() { return __int_as_float(0x7f800000); }
-  __device__ __forceinline__ static double a_high() { return __longlong_as_double(0x7ff0000000000000ll); }
+  __device__ __forceinline__ static double g_high() { return __longlong_as_double(0x7ff0000000000000ll); }
+  __device__ __forceinline__ static long long fx(float x, int f) { return fx_of(x, f); }
+  __device__ __forceinline__ static double unfx(long long v, int f) { return ldexp((double)v, -f); }
 };
 
 template <>
 struct Tr<int32_t> {
   using A = long long;
+  using G = long long;
   __device__ __forceinline__ static int32_t low() { return INT_MIN; }
   __device__ __forceinline__ static int32_t high() { return INT_MAX; }
-  __device__ __forceinline__ static long long a_high() { return LLONG_MAX; }
+  __device__ __forceinline__ static long long g_high() { return LLONG_MAX; }
+  __device__ __forceinline__ static long long fx(int32_t x, int) { return (long long)x; }
+  __device__ __forceinline__ static double unfx(long long v, int) { return (double)v; }
 };
 
 __device__ __forceinline__ double to_double(double v) { return v; }
 __device__ __forceinline__ double to_double(long long v) { return (double)v; }
 
-// Delta contributions: exact FP64 differences of two FP32 values, or exact
-// int64 differences of two int32 values.
+// Exact differences for TD-type sums: FP64 of two FP32 values, or int64.
 __device__ __forceinline__ double dif(float a, float b) { return (double)a - (double)b; }
 __device__ __forceinline__ long long dif(int32_t a, int32_t b) { return (long long)a - (long long)b; }
 

@@ -49,6 +49,7 @@ struct StreamArgs {
   double* cand_gain;    // BUILD per-candidate gains
   int flavour;          // SwapFlavour
   int win_rows;         // FasterPAM: positions per CTA
+  int fshift;           // fixed-point exponent f of the SWAP sums (float data)
   double tol;
 };
 
@@ -82,18 +83,22 @@ struct PointArgs {
   int32_t* cand_slot;
   double* out_double;         // accumulator -> double conversion target
   void* partials; // Key[kMaxGrid] scratch for grid reductions
-  int use_rb;     // cache init: write into buffer st->rb (0) or the given
+  int fshift;     // fixed-point exponent f of the removal loss (float data)
+  unsigned* scan; // matrix scan result: [0] max |d| bits, [1] invalid flag
 };
 
 // Launch configuration chosen for a (mode, k) pair.
 struct StreamConfig {
   int rows;       // candidate rows per tile (R)
   int stages;     // ring depth (S)
+  int minb;       // CTAs per SM the kernel is built for
   size_t smem;    // dynamic shared memory bytes
+  int geometry;   // index into the geometry table (1-based)
 };
 
-// Returns false if no configuration fits (k too large).
-bool stream_config(int mode, int k, int flavour, int forced_rows, StreamConfig* cfg);
+// Returns false if no configuration fits (k too large).  tune > 0 forces a
+// geometry of the table; forced_rows > 0 restricts the automatic choice.
+bool stream_config(int mode, int k, int flavour, int forced_rows, int tune, StreamConfig* cfg);
 
 cudaError_t launch_stream(int dtype, int mode, const StreamConfig& cfg, int grid,
                           const StreamArgs& a, cudaStream_t s);
@@ -105,6 +110,7 @@ cudaError_t launch_fp2_try(int dtype, const PointArgs& a, cudaStream_t s);
 cudaError_t launch_mark_medoids(const PointArgs& a, cudaStream_t s);
 cudaError_t launch_fill_medoid_rows(const PointArgs& a, cudaStream_t s);
 cudaError_t launch_removal_to_double(int dtype, const PointArgs& a, cudaStream_t s);
+cudaError_t launch_matrix_scan(const PointArgs& a, cudaStream_t s);
 
 int device_sm_count();
 

@@ -56,13 +56,14 @@ __device__ __forceinline__ void top2_push(T v, int j, int& n1, T& d1, int& n2, T
 // ------------------------------------------------------------ cache init
 template <class T>
 __global__ void __launch_bounds__(kPtThreads) k_cache_init(const PointArgs a) {
-  using A = typename Tr<T>::A;
+  using A = typename Tr<T>::A;  // removal loss (fixed point / int64)
+  using G = typename Tr<T>::G;  // TD
   extern __shared__ __align__(16) unsigned char sm[];
   A* sacc = reinterpret_cast<A*>(sm);
-  A* scratch = sacc + a.k;
+  G* scratch = reinterpret_cast<G*>(sacc + a.k);
   __shared__ int is_last;
   KmState* st = a.st;
-  const int k = a.k, n = a.n;
+  const int k = a.k, n = a.n, f = a.fshift;
   const int rb = st->rb;
   for (int i = threadIdx.x; i < k; i += blockDim.x) sacc[i] = A(0);
   __syncthreads();
@@ -70,7 +71,7 @@ __global__ void __launch_bounds__(kPtThreads) k_cache_init(const PointArgs a) {
   const T* D = static_cast<const T*>(a.D);
   T* dn = static_cast<T*>(a.dn);
   T* ds = static_cast<T*>(a.ds);
-  A tdl = A(0);
+  G tdl = G(0);
   if (o < n) {
     int n1 = -1, n2 = -1;
     T d1 = Tr<T>::high(), d2 = Tr<T>::high();
@@ -82,17 +83,17 @@ __global__ void __launch_bounds__(kPtThreads) k_cache_init(const PointArgs a) {
     a.sec[o] = n2;
     dn[o] = d1;
     ds[o] = (n2 < 0) ? Tr<T>::high() : d2;
-    if (n2 >= 0) atomic_add_acc(&sacc[n1], dif(d2, d1));
-    tdl = A(d1);
+    if (n2 >= 0) atomic_add_acc(&sacc[n1], Tr<T>::fx(d2, f) - Tr<T>::fx(d1, f));
+    tdl = G(d1);
   } else if (o < a.n_pad) {
     a.near[o] = 0;
     a.sec[o] = 0;
     dn[o] = Tr<T>::low();  // sentinels: d < low never holds
     ds[o] = Tr<T>::low();
   }
-  const A bs = block_sum(tdl, scratch);
+  const G bs = block_sum(tdl, scratch);
   A* rem = static_cast<A*>(a.removal) + (size_t)rb * a.k_pad;
-  if (threadIdx.x == 0) atomic_add_acc(static_cast<A*>(a.td2) + rb, bs);
+  if (threadIdx.x == 0) atomic_add_acc(static_cast<G*>(a.td2) + rb, bs);
   for (int i = threadIdx.x; i < k; i += blockDim.x)
     if (sacc[i] != A(0)) atomic_add_acc(&rem[i], sacc[i]);
   __threadfence();
@@ -101,7 +102,7 @@ __global__ void __launch_bounds__(kPtThreads) k_cache_init(const PointArgs a) {
   __syncthreads();
   if (is_last && threadIdx.x == 0) {
     __threadfence();
-    const A td0 = static_cast<volatile A*>(a.td2)[rb];
+    const G td0 = static_cast<volatile G*>(a.td2)[rb];
     st->td_book_d = to_double(td0);
     st->td_book_i = (long long)td0;
     st->ticket = 0;
@@ -111,10 +112,12 @@ __global__ void __launch_bounds__(kPtThreads) k_cache_init(const PointArgs a) {
 // -------------------------------------------------------------- apply swap
 template <class T>
 __global__ void __launch_bounds__(kPtThreads) k_apply(const PointArgs a) {
-  using A = typename Tr<T>::A;
+  using A = typename Tr<T>::A;  // removal loss (fixed point / int64)
+  using G = typename Tr<T>::G;  // TD
   extern __shared__ __align__(16) unsigned char sm[];
   A* sacc = reinterpret_cast<A*>(sm);
-  A* scratch = sacc + a.k;
+  G* scratch = reinterpret_cast<G*>(sacc + a.k);
+  const int f = a.fshift;
   __shared__ int is_last;
   KmState* st = a.st;
   if (st->error || !st->accept) return;  // uniform for the launch
@@ -127,7 +130,7 @@ __global__ void __launch_bounds__(kPtThreads) k_apply(const PointArgs a) {
   const T* D = static_cast<const T*>(a.D);
   T* dn = static_cast<T*>(a.dn);
   T* ds = static_cast<T*>(a.ds);
-  A tdl = A(0);
+  G tdl = G(0);
   if (o < n) {
     int n1 = a.near[o], n2 = a.sec[o];
     T d1 = dn[o], d2 = ds[o];
@@ -158,12 +161,12 @@ __global__ void __launch_bounds__(kPtThreads) k_apply(const PointArgs a) {
     a.sec[o] = n2;
     dn[o] = d1;
     ds[o] = d2;
-    atomic_add_acc(&sacc[n1], dif(d2, d1));
-    tdl = A(d1);
+    atomic_add_acc(&sacc[n1], Tr<T>::fx(d2, f) - Tr<T>::fx(d1, f));
+    tdl = G(d1);
   }
-  const A bs = block_sum(tdl, scratch);
+  const G bs = block_sum(tdl, scratch);
   A* rem = static_cast<A*>(a.removal) + (size_t)(rb ^ 1) * a.k_pad;
-  if (threadIdx.x == 0) atomic_add_acc(static_cast<A*>(a.td2) + (rb ^ 1), bs);
+  if (threadIdx.x == 0) atomic_add_acc(static_cast<G*>(a.td2) + (rb ^ 1), bs);
   for (int i = threadIdx.x; i < k; i += blockDim.x)
     if (sacc[i] != A(0)) atomic_add_acc(&rem[i], sacc[i]);
   __threadfence();
@@ -198,7 +201,7 @@ __global__ void __launch_bounds__(kPtThreads) k_apply(const PointArgs a) {
 // ------------------------------------------------------------ BUILD commit
 template <class T>
 __global__ void __launch_bounds__(kPtThreads) k_build_commit(const PointArgs a) {
-  using A = typename Tr<T>::A;
+  using A = typename Tr<T>::G;
   __shared__ A scratch[kPtThreads / 32];
   KmState* st = a.st;
   if (st->error) return;
@@ -249,7 +252,8 @@ __global__ void __launch_bounds__(kPtThreads) k_build_commit(const PointArgs a) 
 // ----------------------------------------------- FastPAM2 additional swap
 template <class T>
 __global__ void __launch_bounds__(kPtThreads) k_fp2_try(const PointArgs a) {
-  using A = typename Tr<T>::A;
+  using A = typename Tr<T>::G;   // exact Delta of Eq. (5)
+  using R = typename Tr<T>::A;   // removal-loss buffers
   __shared__ A scratch[kPtThreads / 32];
   __shared__ int is_last;
   KmState* st = a.st;
@@ -257,14 +261,14 @@ __global__ void __launch_bounds__(kPtThreads) k_fp2_try(const PointArgs a) {
   // into buffer rb^1; clear it here as the evaluation pass does.
   const int rb = st->rb;
   if (blockIdx.x == 0) {
-    A* rnext = static_cast<A*>(a.removal) + (size_t)(rb ^ 1) * a.k_pad;
-    for (int i = threadIdx.x; i < a.k; i += blockDim.x) rnext[i] = A(0);
+    R* rnext = static_cast<R*>(a.removal) + (size_t)(rb ^ 1) * a.k_pad;
+    for (int i = threadIdx.x; i < a.k; i += blockDim.x) rnext[i] = R(0);
     if (threadIdx.x == 0) static_cast<A*>(a.td2)[rb ^ 1] = A(0);
   }
   if (st->error || st->done) return;
   if (a.fp2_index >= st->fp2_extra) return;
   const int i = a.fp2_order[a.fp2_index];
-  const Key<A> sb = static_cast<const Key<A>*>(a.slot_best)[i];
+  const Key<R> sb = static_cast<const Key<R>*>(a.slot_best)[i];
   const int c = sb.cand;
   if (a.is_med[c]) {  // already a medoid after an earlier swap
     if (blockIdx.x == 0 && threadIdx.x == 0) st->accept = 0;
@@ -325,11 +329,54 @@ __global__ void k_fill_medoid_rows(const PointArgs a) {
   }
 }
 
-template <class A>
+template <class T>
 __global__ void k_removal_to_double(const PointArgs a) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int rb = a.st->rb;
-  if (i < a.k) a.out_double[i] = to_double(static_cast<const A*>(a.removal)[(size_t)rb * a.k_pad + i]);
+  if (i < a.k)
+    a.out_double[i] =
+        Tr<T>::unfx(static_cast<const long long*>(a.removal)[(size_t)rb * a.k_pad + i], a.fshift);
+}
+
+// Largest |d| over the matrix (fixes the fixed-point exponent of the SWAP
+// sums) and a flag for entries that are negative or not finite.  Float data
+// only; one pass over the n x n block with 16-byte loads.
+__global__ void __launch_bounds__(kPtThreads) k_matrix_scan(const PointArgs a) {
+  __shared__ unsigned smax[kPtThreads / 32];
+  __shared__ unsigned sbad;
+  if (threadIdx.x == 0) sbad = 0;
+  __syncthreads();
+  const float* D = static_cast<const float*>(a.D);
+  const int n = a.n;
+  const int n4 = (n + 3) >> 2;
+  unsigned mx = 0, bad = 0;
+  for (long long r = blockIdx.x; r < n; r += gridDim.x) {
+    const float4* row = reinterpret_cast<const float4*>(D + (size_t)r * a.ld);
+    for (int c4 = threadIdx.x; c4 < n4; c4 += blockDim.x) {
+      const float4 v = __ldcs(row + c4);
+      const float e[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        if (4 * c4 + q < n) {
+          const unsigned u = __float_as_uint(e[q]);
+          // negative (sign bit) or inf/NaN (exponent all ones)
+          bad |= (u >> 31) | (((u >> 23) & 0xffu) == 0xffu ? 1u : 0u);
+          const unsigned m = u & 0x7fffffffu;
+          mx = m > mx ? m : mx;
+        }
+      }
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if ((threadIdx.x & 31) == 0) smax[threadIdx.x >> 5] = mx;
+  if (bad) atomicOr(&sbad, 1u);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned m = 0;
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) m = max(m, smax[i]);
+    atomicMax(&a.scan[0], m);
+    if (sbad) atomicOr(&a.scan[1], 1u);
+  }
 }
 
 // ------------------------------------------------------------- launchers
@@ -392,9 +439,17 @@ cudaError_t launch_fill_medoid_rows(const PointArgs& a, cudaStream_t s) {
 
 cudaError_t launch_removal_to_double(int dtype, const PointArgs& a, cudaStream_t s) {
   if (dtype == 0)
-    k_removal_to_double<long long><<<(a.k + 255) / 256, 256, 0, s>>>(a);
+    k_removal_to_double<int32_t><<<(a.k + 255) / 256, 256, 0, s>>>(a);
   else
-    k_removal_to_double<double><<<(a.k + 255) / 256, 256, 0, s>>>(a);
+    k_removal_to_double<float><<<(a.k + 255) / 256, 256, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_matrix_scan(const PointArgs& a, cudaStream_t s) {
+  int grid = device_sm_count() * 4;
+  if (grid < 1) grid = 1;
+  if (grid > a.n) grid = a.n;
+  k_matrix_scan<<<grid, kPtThreads, 0, s>>>(a);
   return cudaGetLastError();
 }
 

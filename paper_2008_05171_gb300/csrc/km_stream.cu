@@ -48,8 +48,10 @@ struct StageHdr {
 };
 static_assert(sizeof(StageHdr) <= 256, "stage header");
 
+constexpr int kQueue = 256;  // SWAP hit descriptors per warp queue
+
 struct Layout {
-  size_t bars, flags, wkeys, rl, red, tile_rows, acc, slot_local, stages;
+  size_t bars, flags, wkeys, rl, red, tile_rows, acc, slot_local, queues, stages;
   size_t stage_bytes, meta_bytes, total;
 };
 
@@ -78,6 +80,9 @@ __host__ __device__ inline Layout make_layout(int mode, int R, int S, int k, int
   o += (mode == kModeSwap) ? 8 * (size_t)R * (k + 1) : 0;
   L.slot_local = o;
   o += (mode == kModeSwap && fp2) ? 16 * (size_t)k : 0;
+  o = align_up(o, 16);
+  L.queues = o;
+  o += (mode == kModeSwap) ? 2 * (size_t)kQueue * kConsWarps : 0;
   o = align_up(o, 128);
   L.stages = o;
   L.meta_bytes = (mode == kModeSwap) ? 3 * 4 * (size_t)kChunk : 4 * (size_t)kChunk;
@@ -88,16 +93,94 @@ __host__ __device__ inline Layout make_layout(int mode, int R, int S, int k, int
 }
 
 // --------------------------------------------------------------- kernel
-template <class T, int MODE, int R, int S>
-__global__ void __launch_bounds__(kThreads, 1) k_stream(const StreamArgs a) {
-  using A = typename Tr<T>::A;
+// Elements of a SWAP pass that fell below d_s(o): the candidate would be
+// nearest (case (i) of Alg. 3) or second nearest (case (ii)).  Terms are
+// added in fixed point (Tr<T>::fx) to the candidate's row of accumulators:
+// slot k holds the shared term Delta^{+x_c}, slot near(o) the correction.
+//
+// Hits are rare (about 1-2 % of the pairs on clustered data) but most warp
+// rows hold one, so handling them where they occur would cost a whole warp
+// instruction stream per hit.  Instead each lane records its hits of the
+// stage in a 64-bit mask (bit 4r + j: row r, element j of its float4); at
+// the end of the stage a warp prefix sum gives every hit a slot in the
+// warp's queue in shared memory and all 32 lanes drain the queue together.
+__device__ __forceinline__ unsigned lanemask_lt() {
+  unsigned m;
+  asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+  return m;
+}
+
+template <class T>
+__device__ __forceinline__ void swap_hit_at(int r, int col, const T* data,
+                                            const unsigned char* meta, long long* acc, int k,
+                                            int f) {
+  const T d = data[(size_t)r * kChunk + col];
+  const T dn = reinterpret_cast<const T*>(meta)[col];
+  const T ds = reinterpret_cast<const T*>(meta + 4 * kChunk)[col];
+  const int sl = reinterpret_cast<const int32_t*>(meta + 8 * kChunk)[col];
+  long long* ar = acc + (size_t)r * (k + 1);
+  const long long xd = Tr<T>::fx(d, f), xs = Tr<T>::fx(ds, f);
+  if (d < dn) {
+    const long long xn = Tr<T>::fx(dn, f);
+    atomic_add_acc(ar + k, xd - xn);
+    atomic_add_acc(ar + sl, xn - xs);
+  } else {
+    atomic_add_acc(ar + sl, xd - xs);
+  }
+}
+
+// All hits of one stage for this warp; hmask as above, t = 32 warp + lane.
+template <class T>
+__device__ __forceinline__ void swap_stage_hits(unsigned long long hmask, uint16_t* q, int lane,
+                                                int warp, const T* data,
+                                                const unsigned char* meta, long long* acc, int k,
+                                                int f) {
+  const int cnt = __popcll(hmask);
+  int incl = cnt;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int v = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += v;
+  }
+  const int total = __shfl_sync(0xffffffffu, incl, 31);
+  if (total == 0) return;
+  if (total <= kQueue) {
+    int pos = incl - cnt;
+    while (hmask) {
+      const int b = __ffsll(hmask) - 1;
+      hmask &= hmask - 1;
+      q[pos++] = (uint16_t)((b << 5) | lane);
+    }
+    __syncwarp();
+    for (int e = lane; e < total; e += 32) {
+      const unsigned v = q[e];
+      const int b = (int)(v >> 5), src = (int)(v & 31u);
+      swap_hit_at<T>(b >> 2, 4 * (warp * 32 + src) + (b & 3), data, meta, acc, k, f);
+    }
+    __syncwarp();
+  } else {
+    // dense stage (e.g. far-from-converged medoids): every lane its own hits
+    while (hmask) {
+      const int b = __ffsll(hmask) - 1;
+      hmask &= hmask - 1;
+      swap_hit_at<T>(b >> 2, 4 * (warp * 32 + lane) + (b & 3), data, meta, acc, k, f);
+    }
+    __syncwarp();
+  }
+}
+
+template <class T, int MODE, int R, int S, int MINB>
+__global__ void __launch_bounds__(kThreads, MINB) k_stream(const StreamArgs a) {
+  using G = typename Tr<T>::G;
+  using A = long long;  // SWAP accumulators (fixed point / int64)
+  using KA = typename std::conditional<MODE == kModeSwap, long long, G>::type;
   using Vec = typename V4<T>::type;
   extern __shared__ __align__(128) unsigned char smem[];
 
   KmState* st = a.st;
   if (st->done || st->error) return;  // uniform for all CTAs of this launch
 
-  const int n = a.n, k = a.k;
+  const int n = a.n, k = a.k, f = a.fshift;
   const int fp2 = (MODE == kModeSwap && a.flavour == kFastPAM2);
   const Layout L = make_layout(MODE, R, S, k, fp2);
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + L.bars);
@@ -105,12 +188,14 @@ __global__ void __launch_bounds__(kThreads, 1) k_stream(const StreamArgs a) {
   uint64_t* cbar = empty + S;
   volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + L.flags);
   volatile int* last_flag = abort_flag + 1;
-  Key<A>* wkeys = reinterpret_cast<Key<A>*>(smem + L.wkeys);
+  int* scratch_int = const_cast<int*>(abort_flag) + 2;
+  Key<KA>* wkeys = reinterpret_cast<Key<KA>*>(smem + L.wkeys);
   A* rl = reinterpret_cast<A*>(smem + L.rl);
-  double* red = reinterpret_cast<double*>(smem + L.red);
+  G* red = reinterpret_cast<G*>(smem + L.red);
   int* tile_rows = reinterpret_cast<int*>(smem + L.tile_rows);
   A* acc = reinterpret_cast<A*>(smem + L.acc);
   Key<A>* slot_local = reinterpret_cast<Key<A>*>(smem + L.slot_local);
+  uint16_t* queues = reinterpret_cast<uint16_t*>(smem + L.queues);
   unsigned char* stages = smem + L.stages;
 
   const int tid = threadIdx.x;
@@ -121,7 +206,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_stream(const StreamArgs a) {
   if (MODE == kModeSwap && blockIdx.x == 0 && a.flavour != kEvalOnly) {
     A* rnext = reinterpret_cast<A*>(a.removal) + (size_t)(rb ^ 1) * a.k_pad;
     for (int i = tid; i < k; i += kThreads) rnext[i] = A(0);
-    if (tid == 0) reinterpret_cast<A*>(a.td2)[rb ^ 1] = A(0);
+    if (tid == 0) reinterpret_cast<G*>(a.td2)[rb ^ 1] = G(0);
   }
   if (MODE == kModeBuild && blockIdx.x == 0 && tid == 0) {
     st->build_td_d = 0.0;
@@ -129,9 +214,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_stream(const StreamArgs a) {
   }
 
   if (tid == 0) {
-    for (int s = 0; s < S; ++s) {
-      mbar_init(&full[s], 1);
-      mbar_init(&empty[s], kConsWarps);
+    for (int q = 0; q < S; ++q) {
+      mbar_init(&full[q], 1);
+      mbar_init(&empty[q], kConsWarps);
     }
     mbar_init(cbar, kConsWarps);
     abort_flag[0] = 0;
@@ -144,25 +229,26 @@ __global__ void __launch_bounds__(kThreads, 1) k_stream(const StreamArgs a) {
     for (int i = tid; i < R * (k + 1); i += kThreads) acc[i] = A(0);
     if (fp2)
       for (int i = tid; i < k; i += kThreads) {
-        slot_local[i].d = Tr<T>::a_high();
+        slot_local[i].d = LLONG_MAX;
         slot_local[i].slot = i;
         slot_local[i].cand = INT_MAX;
       }
   }
   __syncthreads();
 
-  // Candidate positions of this CTA: [p_lo, p_hi); row = p mod n.
-  long long base = 0, p_lo, p_hi;
-  if (MODE == kModeSwap && a.flavour == kFasterPAM) {
+  // Candidate positions: FasterPAM windows give each CTA the positions
+  // [p_lo, p_hi) (row = p mod n); full passes hand out tiles of R rows from
+  // an atomic counter so that CTAs on faster paths take more tiles.
+  const bool windowed = (MODE == kModeSwap && a.flavour == kFasterPAM);
+  long long base = 0, p_lo = 0, p_hi = 0;
+  if (windowed) {
     base = st->pos;
     const long long stop = (st->last < 0) ? (long long)n : st->last + n;
     p_lo = base + (long long)blockIdx.x * a.win_rows;
     p_hi = p_lo + a.win_rows;
     if (p_hi > stop) p_hi = stop;
-  } else {
-    p_lo = (long long)blockIdx.x * n / gridDim.x;
-    p_hi = (long long)(blockIdx.x + 1) * n / gridDim.x;
   }
+  const unsigned ntiles = (unsigned)((n + R - 1) / R);
   const int nchunks = (n + kChunk - 1) / kChunk;
   const int n4 = (n + 3) & ~3;
 
@@ -177,16 +263,33 @@ __global__ void __launch_bounds__(kThreads, 1) k_stream(const StreamArgs a) {
       while (ok) {
         int rows[R], outs[R];
         int nr = 0;
-        while (nr < R && p < p_hi) {
-          const int row = (int)(p % n);
-          if (!a.is_med[row]) {
-            rows[nr] = row;
-            outs[nr] = (int)(p - base);
-            ++nr;
+        if (windowed) {
+          while (nr < R && p < p_hi) {
+            const int row = (int)(p % n);
+            if (!a.is_med[row]) {
+              rows[nr] = row;
+              outs[nr] = (int)(p - base);
+              ++nr;
+            }
+            ++p;
           }
-          ++p;
+          if (nr == 0) break;
+        } else {
+          // next tile with at least one non-medoid row
+          while (nr == 0) {
+            const unsigned tile = atomicAdd(&st->tile_next, 1u);
+            if (tile >= ntiles) break;
+            const int r0 = (int)tile * R;
+            const int r1 = (r0 + R < n) ? r0 + R : n;
+            for (int row = r0; row < r1; ++row)
+              if (!a.is_med[row]) {
+                rows[nr] = row;
+                outs[nr] = row;
+                ++nr;
+              }
+          }
+          if (nr == 0) break;
         }
-        if (nr == 0) break;
         for (int j = 0; j < nchunks; ++j) {
           if (!mbar_wait(&empty[s], ph ^ 1, abort_flag)) {
             ok = false;
@@ -246,12 +349,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_stream(const StreamArgs a) {
 
   // ================================================================ consumers
   const int t = tid;  // 0..255, owns columns 4t..4t+3 of each chunk
-  Key<A> wbest;
-  wbest.d = Tr<T>::a_high();
+  Key<KA> wbest;
+  wbest.d = (MODE == kModeSwap) ? KA(LLONG_MAX) : KA(Tr<T>::g_high());
   wbest.slot = INT_MAX;
   wbest.cand = INT_MAX;
 
-  // BUILD per-row partial sums (registers)
+  // BUILD per-row partial sums (registers): compensated FP32 or int64
   float ks[R], kc[R];
   long long ki[R];
 #pragma unroll
@@ -290,49 +393,16 @@ __global__ void __launch_bounds__(kThreads, 1) k_stream(const StreamArgs a) {
     const T* data = reinterpret_cast<const T*>(meta + L.meta_bytes);
 
     if (MODE == kModeSwap) {
-      const Vec dn4 = lds4(reinterpret_cast<const T*>(meta) + 4 * t);
       const Vec ds4 = lds4(reinterpret_cast<const T*>(meta + 4 * kChunk) + 4 * t);
-      const int4 nr4 = lds4(reinterpret_cast<const int32_t*>(meta + 8 * kChunk) + 4 * t);
+      unsigned long long hmask = 0ull;
 #pragma unroll 4
       for (int r = 0; r < nr; ++r) {
         const Vec d4 = lds4(data + (size_t)r * kChunk + 4 * t);
-        const bool h0 = d4.x < ds4.x, h1 = d4.y < ds4.y, h2 = d4.z < ds4.z, h3 = d4.w < ds4.w;
-        if (h0 | h1 | h2 | h3) {
-          A* ar = acc + (size_t)r * (k + 1);
-          if (h0) {
-            if (d4.x < dn4.x) {
-              atomic_add_acc(ar + k, dif(d4.x, dn4.x));
-              atomic_add_acc(ar + nr4.x, dif(dn4.x, ds4.x));
-            } else {
-              atomic_add_acc(ar + nr4.x, dif(d4.x, ds4.x));
-            }
-          }
-          if (h1) {
-            if (d4.y < dn4.y) {
-              atomic_add_acc(ar + k, dif(d4.y, dn4.y));
-              atomic_add_acc(ar + nr4.y, dif(dn4.y, ds4.y));
-            } else {
-              atomic_add_acc(ar + nr4.y, dif(d4.y, ds4.y));
-            }
-          }
-          if (h2) {
-            if (d4.z < dn4.z) {
-              atomic_add_acc(ar + k, dif(d4.z, dn4.z));
-              atomic_add_acc(ar + nr4.z, dif(dn4.z, ds4.z));
-            } else {
-              atomic_add_acc(ar + nr4.z, dif(d4.z, ds4.z));
-            }
-          }
-          if (h3) {
-            if (d4.w < dn4.w) {
-              atomic_add_acc(ar + k, dif(d4.w, dn4.w));
-              atomic_add_acc(ar + nr4.w, dif(dn4.w, ds4.w));
-            } else {
-              atomic_add_acc(ar + nr4.w, dif(d4.w, ds4.w));
-            }
-          }
-        }
+        const unsigned hm = (d4.x < ds4.x ? 1u : 0u) | (d4.y < ds4.y ? 2u : 0u) |
+                            (d4.z < ds4.z ? 4u : 0u) | (d4.w < ds4.w ? 8u : 0u);
+        hmask |= (unsigned long long)hm << (4 * r);
       }
+      swap_stage_hits<T>(hmask, queues + warp * kQueue, lane, warp, data, meta, acc, k, f);
     } else {
       const int col = chunk * kChunk + 4 * t;
       const bool v0 = col < n, v1 = col + 1 < n, v2 = col + 2 < n, v3 = col + 3 < n;
@@ -355,13 +425,14 @@ __global__ void __launch_bounds__(kThreads, 1) k_stream(const StreamArgs a) {
             x2 = (d4.z < dn4.z) ? T(d4.z - dn4.z) : T(0);
             x3 = (d4.w < dn4.w) ? T(d4.w - dn4.w) : T(0);
           }
-          if constexpr (sizeof(A) == 8 && std::is_same<T, float>::value) {
-            // compensated (Kahan) FP32 partial sums, folded into FP64 per tile
-            float y, tt;
-            y = float(x0) - kc[r]; tt = ks[r] + y; kc[r] = (tt - ks[r]) - y; ks[r] = tt;
-            y = float(x1) - kc[r]; tt = ks[r] + y; kc[r] = (tt - ks[r]) - y; ks[r] = tt;
-            y = float(x2) - kc[r]; tt = ks[r] + y; kc[r] = (tt - ks[r]) - y; ks[r] = tt;
-            y = float(x3) - kc[r]; tt = ks[r] + y; kc[r] = (tt - ks[r]) - y; ks[r] = tt;
+          if constexpr (std::is_same<T, float>::value) {
+            // the four terms share a sign: their FP32 sum is within 2 ulp;
+            // the row sum is then carried with Kahan compensation
+            const float p4 = (x0 + x1) + (x2 + x3);
+            const float y = p4 - kc[r];
+            const float tt = ks[r] + y;
+            kc[r] = (tt - ks[r]) - y;
+            ks[r] = tt;
           } else {
             ki[r] += (long long)x0 + (long long)x1 + (long long)x2 + (long long)x3;
           }
@@ -386,7 +457,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_stream(const StreamArgs a) {
       for (int r = warp; r < nr; r += kConsWarps) {
         const A* ar = acc + (size_t)r * (k + 1);
         Key<A> kb;
-        kb.d = Tr<T>::a_high();
+        kb.d = LLONG_MAX;
         kb.slot = INT_MAX;
         kb.cand = 0;
         for (int i = lane; i < k; i += 32) {
@@ -401,9 +472,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_stream(const StreamArgs a) {
         const int c = __shfl_sync(0xffffffffu, my_row, r);
         const int out = __shfl_sync(0xffffffffu, my_out, r);
         if (lane == 0) {
-          if (a.cand_delta) a.cand_delta[out] = to_double(total);
+          if (a.cand_delta) a.cand_delta[out] = Tr<T>::unfx(total, f);
           if (a.cand_slot) a.cand_slot[out] = kb.slot;
-          Key<A> ck;
+          Key<KA> ck;
           ck.d = total;
           ck.slot = kb.slot;
           ck.cand = c;
@@ -431,19 +502,24 @@ __global__ void __launch_bounds__(kThreads, 1) k_stream(const StreamArgs a) {
     } else {
 #pragma unroll
       for (int r = 0; r < R; ++r) {
-        double v;
         if constexpr (std::is_same<T, float>::value) {
-          v = (double)ks[r] - (double)kc[r];
+          // value = hi + lo (Kahan keeps sum - compensation); add across the
+          // warp with error-free TwoSum in FP32, one FP64 fold per row
+          float hi = ks[r], lo = -kc[r];
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) {
+            const float ohi = __shfl_xor_sync(0xffffffffu, hi, o);
+            const float olo = __shfl_xor_sync(0xffffffffu, lo, o);
+            const float sh = hi + ohi;
+            const float bp = sh - hi;
+            const float err = (hi - (sh - bp)) + (ohi - bp);
+            hi = sh;
+            lo = lo + olo + err;
+          }
+          if (lane == 0) red[warp * R + r] = (double)hi + (double)lo;
         } else {
-          v = 0.0;
-        }
-        long long vi = ki[r];
-        if constexpr (std::is_same<T, float>::value) {
-          v = warp_sum(v);
+          const long long v = warp_sum(ki[r]);
           if (lane == 0) red[warp * R + r] = v;
-        } else {
-          vi = warp_sum(vi);
-          if (lane == 0) reinterpret_cast<long long*>(red)[warp * R + r] = vi;
         }
         ks[r] = 0.f;
         kc[r] = 0.f;
@@ -451,18 +527,13 @@ __global__ void __launch_bounds__(kThreads, 1) k_stream(const StreamArgs a) {
       }
       KM_CSYNC();
       if (warp == 0) {
-        Key<A> kb;
-        kb.d = Tr<T>::a_high();
+        Key<KA> kb;
+        kb.d = Tr<T>::g_high();
         kb.slot = 0;
         kb.cand = INT_MAX;
         if (lane < nr) {
-          A tot = A(0);
-          for (int w = 0; w < kConsWarps; ++w) {
-            if constexpr (std::is_same<T, float>::value)
-              tot += red[w * R + lane];
-            else
-              tot += reinterpret_cast<const long long*>(red)[w * R + lane];
-          }
+          G tot = G(0);
+          for (int w = 0; w < kConsWarps; ++w) tot += red[w * R + lane];
           kb.d = tot;
           kb.cand = my_row;
           if (a.cand_gain) a.cand_gain[my_out] = to_double(tot);
@@ -483,10 +554,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_stream(const StreamArgs a) {
   __threadfence();
   KM_CSYNC();
   if (t == 0) {
-    Key<A> b = wkeys[0];
+    Key<KA> b = wkeys[0];
     for (int w = 1; w < kConsWarps; ++w)
       if (key_less(wkeys[w], b)) b = wkeys[w];
-    reinterpret_cast<Key<A>*>(a.partials)[blockIdx.x] = b;
+    reinterpret_cast<Key<KA>*>(a.partials)[blockIdx.x] = b;
     __threadfence();
     const unsigned tk = atomicAdd(&st->ticket, 1u);
     last_flag[0] = (tk == gridDim.x - 1) ? 1 : 0;
@@ -496,27 +567,28 @@ __global__ void __launch_bounds__(kThreads, 1) k_stream(const StreamArgs a) {
 
   // ------------------------------------------------- last CTA: grid result
   __threadfence();
-  const Key<A>* parts = reinterpret_cast<const Key<A>*>(a.partials);
+  const Key<KA>* parts = reinterpret_cast<const Key<KA>*>(a.partials);
   if (warp == 0) {
-    Key<A> b;
-    b.d = Tr<T>::a_high();
+    Key<KA> b;
+    b.d = (MODE == kModeSwap) ? KA(LLONG_MAX) : KA(Tr<T>::g_high());
     b.slot = INT_MAX;
     b.cand = INT_MAX;
     for (int g = lane; g < (int)gridDim.x; g += 32) {
-      const Key<A> v = ld_cg_key(parts + g);
+      const Key<KA> v = ld_cg_key(parts + g);
       if (key_less(v, b)) b = v;
     }
     b = warp_min_key(b);
     if (lane == 0) wkeys[0] = b;
   }
   KM_CSYNC();
-  const Key<A> best = wkeys[0];
+  const Key<KA> best = wkeys[0];
 
   if (MODE == kModeBuild) {
     if (t == 0) {
       st->build_gain_d = to_double(best.d);
       st->build_gain_i = (long long)best.d;
       st->build_cand = best.cand;
+      st->tile_next = 0;
       st->ticket = 0;
     }
     return;
@@ -527,7 +599,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_stream(const StreamArgs a) {
     const long long stop = (st->last < 0) ? (long long)n : st->last + n;
     long long wlen = (long long)gridDim.x * a.win_rows;
     if (base + wlen > stop) wlen = stop - base;
-    int* firstw = const_cast<int*>(last_flag) + 1;
+    int* firstw = scratch_int;
     if (t == 0) *firstw = INT_MAX;
     KM_CSYNC();
     for (long long w = t; w < wlen; w += kConsThreads) {
@@ -540,8 +612,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_stream(const StreamArgs a) {
     if (t == 0) {
       const int w = *firstw;
       if (w != INT_MAX) {
-        st->accept = 1;
         const double dw = __ldcg(a.cand_delta + w);
+        st->accept = 1;
         st->best_d = dw;
         st->best_i = (long long)dw;
         st->best_slot = __ldcg(a.cand_slot + w);
@@ -560,13 +632,14 @@ __global__ void __launch_bounds__(kThreads, 1) k_stream(const StreamArgs a) {
   }
 
   if (t == 0) {
-    st->best_d = to_double(best.d);
+    const double bd = Tr<T>::unfx((long long)best.d, f);
+    st->best_d = bd;
     st->best_i = (long long)best.d;
     st->best_slot = (best.cand == INT_MAX) ? -1 : best.slot;
     st->best_cand = (best.cand == INT_MAX) ? -1 : best.cand;
     if (a.flavour != kEvalOnly) {
       st->iter += 1;
-      if (best.cand != INT_MAX && to_double(best.d) < -a.tol) {
+      if (best.cand != INT_MAX && bd < -a.tol) {
         st->accept = 1;
       } else {
         st->accept = 0;
@@ -589,18 +662,18 @@ __global__ void __launch_bounds__(kThreads, 1) k_stream(const StreamArgs a) {
     __threadfence_block();
     KM_CSYNC();
     const int bslot = (best.cand == INT_MAX) ? -1 : best.slot;
-    int* cnt = const_cast<int*>(last_flag) + 1;
+    int* cnt = scratch_int;
     if (t == 0) *cnt = 0;
     KM_CSYNC();
     for (int i = t; i < k; i += kConsThreads) {
       const Key<A> ki2 = sbest[i];
-      const bool elig = (i != bslot) && ki2.cand != INT_MAX && to_double(ki2.d) < 0.0;
+      const bool elig = (i != bslot) && ki2.cand != INT_MAX && ki2.d < 0;
       if (!elig) continue;
       int rank = 0;
       for (int j = 0; j < k; ++j) {
         if (j == i || j == bslot) continue;
         const Key<A> kj = sbest[j];
-        if (!(kj.cand != INT_MAX && to_double(kj.d) < 0.0)) continue;
+        if (!(kj.cand != INT_MAX && kj.d < 0)) continue;
         if (kj.d < ki2.d || (kj.d == ki2.d && j < i)) ++rank;
       }
       a.fp2_order[rank] = i;
@@ -609,36 +682,82 @@ __global__ void __launch_bounds__(kThreads, 1) k_stream(const StreamArgs a) {
     KM_CSYNC();
     if (t == 0) {
       st->fp2_extra = (st->accept) ? *cnt : 0;
-      st->fp2_dstar = fabs(to_double(best.d));
-      st->fp2_dstar_i = (best.d < A(0)) ? -(long long)best.d : (long long)best.d;
+      st->fp2_dstar = fabs(Tr<T>::unfx((long long)best.d, f));
     }
   }
-  if (t == 0) st->ticket = 0;
+  if (t == 0) {
+    st->tile_next = 0;
+    st->ticket = 0;
+  }
 #undef KM_CSYNC
 }
 
 // ------------------------------------------------------------- host side
-bool stream_config(int mode, int k, int flavour, int forced_rows, StreamConfig* cfg) {
-  static const int cand[][2] = {{16, 2}, {8, 3}, {4, 4}, {2, 4}, {1, 4}};
-  const size_t limit = 227 * 1024;
+// Kernel geometries: rows per tile (= per stage), ring stages, CTAs per SM.
+struct Geometry {
+  int rows, stages, minb;
+};
+static const Geometry kGeoms[] = {
+    {16, 2, 1},  // 1
+    {8, 4, 1},   // 2
+    {8, 2, 2},   // 3
+    {4, 4, 1},   // 4
+    {2, 4, 1},   // 5
+    {1, 4, 1},   // 6
+    {16, 3, 1},  // 7
+    {8, 5, 1},   // 8
+    {4, 2, 2},   // 9
+    {4, 3, 2},   // 10
+    {4, 2, 3},   // 11
+    {8, 2, 3},   // 12
+    {2, 3, 3},   // 13
+    {4, 3, 3},   // 14
+    {8, 3, 2},   // 15
+    {2, 4, 3},   // 16
+};
+static const int kNumGeoms = sizeof(kGeoms) / sizeof(kGeoms[0]);
+
+bool stream_config(int mode, int k, int flavour, int forced_rows, int tune, StreamConfig* cfg) {
   const int fp2 = (mode == kModeSwap && flavour == kFastPAM2);
-  for (auto& rs : cand) {
-    if (forced_rows > 0 && rs[0] != forced_rows) continue;
-    const Layout L = make_layout(mode, rs[0], rs[1], k, fp2);
-    if (L.total <= limit) {
-      cfg->rows = rs[0];
-      cfg->stages = rs[1];
-      cfg->smem = L.total;
+  auto fits = [&](const Geometry& g, size_t* bytes) {
+    const Layout L = make_layout(mode, g.rows, g.stages, k, fp2);
+    const size_t limit = (size_t)228 * 1024 / g.minb - 1024;
+    *bytes = L.total;
+    return L.total <= limit;
+  };
+  if (tune > 0) {
+    if (tune > kNumGeoms) return false;
+    const Geometry& g = kGeoms[tune - 1];
+    size_t b;
+    if (!fits(g, &b)) return false;
+    *cfg = {g.rows, g.stages, g.minb, b, tune};
+    return true;
+  }
+  // automatic: the first geometry of the preference list that fits.  The
+  // order comes from sweeps on GB300 (n = 20000 and 50000 float matrices):
+  // BUILD streams best with 3 CTAs/SM of 4-row tiles and a 3-stage ring;
+  // SWAP with 2 CTAs/SM of 8-row tiles (its shared accumulators grow with
+  // k, so larger k falls back to smaller footprints).
+  static const int pref_swap[] = {3, 11, 1, 2, 4, 5, 6};
+  static const int pref_build[] = {14, 12, 15, 3, 11, 1, 2, 4, 5, 6};
+  const int* pref = (mode == kModeSwap) ? pref_swap : pref_build;
+  const int npref = (mode == kModeSwap) ? 7 : 10;
+  for (int q = 0; q < npref; ++q) {
+    const Geometry& g = kGeoms[pref[q] - 1];
+    if (forced_rows > 0 && g.rows != forced_rows) continue;
+    size_t b;
+    if (fits(g, &b)) {
+      *cfg = {g.rows, g.stages, g.minb, b, pref[q]};
       return true;
     }
   }
   return false;
 }
 
-template <class T, int MODE, int R, int S>
+template <class T, int MODE, int R, int S, int MINB>
 static cudaError_t launch_one(const StreamConfig& cfg, int grid, const StreamArgs& a,
                               cudaStream_t s) {
-  auto kern = k_stream<T, MODE, R, S>;
+  auto kern = k_stream<T, MODE, R, S, MINB>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)cfg.smem);
   if (e != cudaSuccess) return e;
@@ -647,31 +766,36 @@ static cudaError_t launch_one(const StreamConfig& cfg, int grid, const StreamArg
 }
 
 template <class T, int MODE>
-static cudaError_t launch_rs(const StreamConfig& cfg, int grid, const StreamArgs& a,
-                             cudaStream_t s) {
-  switch (cfg.rows) {
-    case 16:
-      return launch_one<T, MODE, 16, 2>(cfg, grid, a, s);
-    case 8:
-      return launch_one<T, MODE, 8, 3>(cfg, grid, a, s);
-    case 4:
-      return launch_one<T, MODE, 4, 4>(cfg, grid, a, s);
-    case 2:
-      return launch_one<T, MODE, 2, 4>(cfg, grid, a, s);
-    case 1:
-      return launch_one<T, MODE, 1, 4>(cfg, grid, a, s);
-    default:
-      return cudaErrorInvalidValue;
+static cudaError_t launch_geo(const StreamConfig& cfg, int grid, const StreamArgs& a,
+                              cudaStream_t s) {
+  switch (cfg.geometry) {
+    case 1: return launch_one<T, MODE, 16, 2, 1>(cfg, grid, a, s);
+    case 2: return launch_one<T, MODE, 8, 4, 1>(cfg, grid, a, s);
+    case 3: return launch_one<T, MODE, 8, 2, 2>(cfg, grid, a, s);
+    case 4: return launch_one<T, MODE, 4, 4, 1>(cfg, grid, a, s);
+    case 5: return launch_one<T, MODE, 2, 4, 1>(cfg, grid, a, s);
+    case 6: return launch_one<T, MODE, 1, 4, 1>(cfg, grid, a, s);
+    case 7: return launch_one<T, MODE, 16, 3, 1>(cfg, grid, a, s);
+    case 8: return launch_one<T, MODE, 8, 5, 1>(cfg, grid, a, s);
+    case 9: return launch_one<T, MODE, 4, 2, 2>(cfg, grid, a, s);
+    case 10: return launch_one<T, MODE, 4, 3, 2>(cfg, grid, a, s);
+    case 11: return launch_one<T, MODE, 4, 2, 3>(cfg, grid, a, s);
+    case 12: return launch_one<T, MODE, 8, 2, 3>(cfg, grid, a, s);
+    case 13: return launch_one<T, MODE, 2, 3, 3>(cfg, grid, a, s);
+    case 14: return launch_one<T, MODE, 4, 3, 3>(cfg, grid, a, s);
+    case 15: return launch_one<T, MODE, 8, 3, 2>(cfg, grid, a, s);
+    case 16: return launch_one<T, MODE, 2, 4, 3>(cfg, grid, a, s);
+    default: return cudaErrorInvalidValue;
   }
 }
 
 cudaError_t launch_stream(int dtype, int mode, const StreamConfig& cfg, int grid,
                           const StreamArgs& a, cudaStream_t s) {
   if (dtype == 0)
-    return mode == kModeSwap ? launch_rs<int32_t, kModeSwap>(cfg, grid, a, s)
-                             : launch_rs<int32_t, kModeBuild>(cfg, grid, a, s);
-  return mode == kModeSwap ? launch_rs<float, kModeSwap>(cfg, grid, a, s)
-                           : launch_rs<float, kModeBuild>(cfg, grid, a, s);
+    return mode == kModeSwap ? launch_geo<int32_t, kModeSwap>(cfg, grid, a, s)
+                             : launch_geo<int32_t, kModeBuild>(cfg, grid, a, s);
+  return mode == kModeSwap ? launch_geo<float, kModeSwap>(cfg, grid, a, s)
+                           : launch_geo<float, kModeBuild>(cfg, grid, a, s);
 }
 
 }  // namespace km

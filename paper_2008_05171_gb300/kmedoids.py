@@ -37,7 +37,7 @@ class km_options(ctypes.Structure):
                 ("tol", ctypes.c_double), ("fastpam2_tol", ctypes.c_double),
                 ("rows_per_tile", ctypes.c_int32), ("profile", ctypes.c_int32),
                 ("trace_capacity", ctypes.c_int32),
-                ("reserved0", ctypes.c_int32),
+                ("tune", ctypes.c_int32),
                 ("trace_delta", ctypes.POINTER(ctypes.c_double)),
                 ("trace_slot", ctypes.POINTER(ctypes.c_int32)),
                 ("trace_cand", ctypes.POINTER(ctypes.c_int32)),
@@ -137,7 +137,7 @@ def _stream():
 
 
 def options(variant="fastpam1", max_iter=0, tol=0.0, fastpam2_tol=0.0,
-            rows_per_tile=0, profile=False, trace=0):
+            rows_per_tile=0, profile=False, trace=0, tune=0):
     o = km_options()
     load().km_default_options(ctypes.byref(o))
     o.variant = VARIANTS[variant] if isinstance(variant, str) else int(variant)
@@ -147,6 +147,7 @@ def options(variant="fastpam1", max_iter=0, tol=0.0, fastpam2_tol=0.0,
     o.rows_per_tile = int(rows_per_tile)
     o.profile = 1 if profile else 0
     o.trace_capacity = int(trace)
+    o.tune = int(tune)
     return o
 
 
