@@ -181,6 +181,18 @@ km_status kmedoids_cache(const void *D, int32_t dtype, int64_t n, int64_t ld,
                          int32_t *sec, void *dn, void *ds, double *removal,
                          void *ws, size_t ws_bytes, void *stream);
 
+/* Tensor-core Gram product G = X X^T of bf16 feature vectors (tcgen05 MMA,
+ * FP32 accumulation), the dot products behind the on-the-fly distances
+ * d(o,c)^2 = |x_o|^2 + |x_c|^2 - 2 x_o.x_c (Sec. 4.9 notes that recomputing
+ * distances instead of storing the matrix is the memory-saving option).
+ * X: n rows of ldx bf16 elements (DEVICE, 16-byte aligned, ldx % 8 == 0),
+ * d = 16, 32, ..., 256 features.  G: n x n FP32 (DEVICE, row stride ldg).
+ * ws (DEVICE, 256-byte aligned) >= 256 + roundup(n,128) * d * 2 bytes holds
+ * the operands rearranged for the tensor cores.  n <= 2^20. */
+km_status kmedoids_gram_bf16(const void *X, int64_t n, int32_t d, int64_t ldx,
+                             float *G, int64_t ldg, void *ws, size_t ws_bytes,
+                             void *stream);
+
 /* kmedoids_eval_swaps without a caller-provided workspace, for callers that
  * cannot allocate device memory when they evaluate swaps (a frozen memory
  * pool, a plugin that must not use the host application's allocator, a

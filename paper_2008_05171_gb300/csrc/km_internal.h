@@ -114,6 +114,11 @@ cudaError_t launch_matrix_scan(const PointArgs& a, cudaStream_t s);
 
 int device_sm_count();
 
+cudaError_t launch_prearrange(const void* X, long long ldx, int n, int d, int n_pad, void* Xp,
+                              cudaStream_t s);
+cudaError_t launch_row_norms(const void* X, long long ldx, int n, int d, int n_pad, float* norms,
+                             cudaStream_t s);
+
 // Replace the thread-local message returned by kmedoids_last_error().
 void set_last_error(const char* msg);
 

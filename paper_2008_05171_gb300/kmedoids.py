@@ -23,7 +23,7 @@ STATUS = {0: "KM_OK", 1: "KM_E_INVALID", 2: "KM_E_WORKSPACE", 3: "KM_E_CUDA",
 EXPORTS = ["km_default_options", "kmedoids_workspace_size", "kmedoids_build",
            "kmedoids_swap", "kmedoids_run", "kmedoids_eval_swaps",
            "kmedoids_cache", "kmedoids_last_error", "kmedoids_version",
-           "kmedoids_eval_swaps_static"]
+           "kmedoids_eval_swaps_static", "kmedoids_gram_bf16"]
 
 
 class KmError(RuntimeError):
@@ -98,6 +98,8 @@ def load(path: str = LIB_PATH):
         lib.kmedoids_eval_swaps_static.argtypes = [P, i32, i64, i64, i32, P,
                                                    P, P, P, P, P, P]
         lib.kmedoids_eval_swaps_static.restype = i32
+        lib.kmedoids_gram_bf16.argtypes = [P, i64, i32, i64, P, i64, P, sz, P]
+        lib.kmedoids_gram_bf16.restype = i32
         lib.kmedoids_last_error.restype = ctypes.c_char_p
         lib.kmedoids_version.restype = ctypes.c_char_p
         _LIB = lib
@@ -327,6 +329,23 @@ def cache(D, medoids, n=None, ws=None):
         ctypes.c_void_p(ds.data_ptr()), ctypes.c_void_p(rl.data_ptr()),
         ctypes.c_void_p(ws.data_ptr()), ws.numel(), _stream()))
     return near, sec, dn, ds, rl
+
+
+def gram_bf16(X):
+    """kmedoids_gram_bf16: G = X X^T (FP32) of a bf16 CUDA tensor X (n x d)."""
+    torch = _torch()
+    lib = load()
+    if X.dtype != torch.bfloat16 or X.dim() != 2 or X.stride(1) != 1:
+        raise ValueError("X must be a 2-D bf16 CUDA tensor with unit column stride")
+    n, d = X.shape
+    n_pad = (n + 127) // 128 * 128
+    ws = torch.empty(256 + n_pad * d * 2, dtype=torch.uint8, device=X.device)
+    G = torch.empty((n, n), dtype=torch.float32, device=X.device)
+    _check(lib.kmedoids_gram_bf16(
+        ctypes.c_void_p(X.data_ptr()), n, d, X.stride(0),
+        ctypes.c_void_p(G.data_ptr()), n, ctypes.c_void_p(ws.data_ptr()),
+        ws.numel(), _stream()))
+    return G
 
 
 def version() -> str:
