@@ -193,6 +193,37 @@ km_status kmedoids_gram_bf16(const void *X, int64_t n, int32_t d, int64_t ldx,
                              float *G, int64_t ldg, void *ws, size_t ws_bytes,
                              void *stream);
 
+/* ---- On-the-fly distance form (no n x n matrix).  Points are n rows of d
+ * bf16 features (DEVICE, row stride ldx elements, ldx % 8 == 0, 16-byte
+ * aligned, d a multiple of 16 up to 256); d(o,c) is the Euclidean distance.
+ * Every BUILD step and SWAP pass recomputes the distances it needs from a
+ * tensor-core Gram product (tcgen05, BF16 inputs, FP32 accumulation):
+ * d^2 = |x_o|^2 + |x_c|^2 - 2 x_o.x_c.  The per-point cache (nearest, d_n,
+ * d_s) and the TD are computed exactly from FP32 differences sum (x - y)^2,
+ * so the Gram form's rounding (relative error ~1e-5 on d^2 for well
+ * separated points) only affects which candidates see a hit and the Delta
+ * values, not the cache or the reported TD.  FastPAM1 only; k <= 224.
+ * Workspace (DEVICE, 256-byte aligned): kmedoids_features_workspace_size()
+ * bytes, which includes the features rearranged for the tensor cores. */
+size_t kmedoids_features_workspace_size(int64_t n, int32_t d, int32_t k,
+                                        const km_options *opts);
+
+/* BUILD (Alg. 1) then FastPAM1 SWAP (Alg. 3) on the features; medoids_out
+ * (DEVICE, k), labels_out (DEVICE, n, may be NULL).  res->td is the exact
+ * FP32-difference TD accumulated in FP64. */
+km_status kmedoids_run_features(const void *X_bf16, int64_t n, int32_t d,
+                                int64_t ldx, int32_t k, int32_t *medoids_out,
+                                int32_t *labels_out, const km_options *opts,
+                                km_result *res, void *ws, size_t ws_bytes,
+                                void *stream);
+
+/* FastPAM1 SWAP on the features from the medoids in medoids_inout. */
+km_status kmedoids_swap_features(const void *X_bf16, int64_t n, int32_t d,
+                                 int64_t ldx, int32_t k,
+                                 int32_t *medoids_inout, int32_t *labels_out,
+                                 const km_options *opts, km_result *res,
+                                 void *ws, size_t ws_bytes, void *stream);
+
 /* kmedoids_eval_swaps without a caller-provided workspace, for callers that
  * cannot allocate device memory when they evaluate swaps (a frozen memory
  * pool, a plugin that must not use the host application's allocator, a

@@ -1,0 +1,1075 @@
+// km_features.cu -- the on-the-fly distance form of the method: BUILD
+// (Alg. 1) and FastPAM1 SWAP (Alg. 3) over bf16 feature vectors with
+// Euclidean distances computed in every pass instead of read from an n x n
+// matrix (the paper computes distances on demand when the matrix does not
+// fit, Sec. 4.9).
+//
+// Pass kernel k_feat_pass (one persistent CTA per SM, warp-specialised):
+//   warp 0      producer: 1-D bulk copies of a 128-candidate tile (A) and of
+//               128-point blocks (B) with the points' cache entries, into a
+//               2-stage shared-memory ring (mbarrier completion);
+//   warp 1      allocates tensor memory and issues the tcgen05 MMAs:
+//               G = X_c X_o^T, BF16 inputs, FP32 accumulation, into one of
+//               two 128-column TMEM buffers (double buffering);
+//   warps 2-9   epilogue, two warpgroups of 64 columns each: read G from
+//               TMEM, d^2 = |x_c|^2 + |x_o|^2 - 2 g, then
+//               SWAP:  hits (d^2 < d_s^2) are compacted per warp and added,
+//                      with d = sqrt(d^2), to per-candidate slot
+//                      accumulators in shared memory (Eq. (7));
+//               BUILD: each thread sums min(d - d_n, 0) of its candidate
+//                      (step 0: d) with Kahan compensation.
+// The per-point cache (nearest, d_n, d_s) is computed exactly with FP32
+// direct differences sum (x - y)^2 (cache, apply and BUILD commit kernels),
+// so the bf16 Gram form only decides which candidate rows see a hit; its
+// error near the case boundaries costs at most the error itself because the
+// change function of Eq. (5) is continuous in d(o, c) at d_n and d_s.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "../../include/kmedoids.h"
+#include "km_device.cuh"
+#include "km_internal.h"
+#include "km_tc.cuh"
+
+namespace km {
+
+constexpr int kFeatStages = 2;
+constexpr int kFeatEpiWarps = 8;
+constexpr int kFeatThreads = (2 + kFeatEpiWarps) * 32;
+constexpr int kFeatQueue = 128;      // hit entries per epilogue warp
+constexpr int kFeatMaxK = 224;       // shared accumulators: 128 x (k+1) x 4 B
+constexpr int kFeatMaxD = 256;
+
+struct FeatArgs {
+  const uint16_t* Xp;   // rearranged features (core-matrix layout)
+  const uint16_t* X;    // features, row-major (ldx)
+  long long ldx;
+  int n, d, k, n_pad;
+  const float* norms;   // |x|^2, n_pad
+  // per-point cache (n_pad, padding sentinels)
+  int32_t* near;
+  int32_t* sec;
+  float* dn;
+  float* ds;
+  float* dn2;
+  float* ds2;
+  uint8_t* is_med;
+  int32_t* med;
+  double* removal;      // [2][k_pad]
+  double* td2;          // [2]
+  int k_pad;
+  KmState* st;
+  void* partials;       // Key<double>[kMaxGrid]
+  double* gains;        // BUILD gains per step
+  void* trace;
+  int trace_cap;
+  int mode;             // kModeSwap / kModeBuild
+  int build_first;
+  double tol;
+};
+
+struct FeatLayout {
+  size_t bars, flags, wkeys, rl, acc, red, queue_idx, queue_d2, tslot, a, stages, stage_bytes,
+      meta_bytes, total;
+};
+
+__host__ __device__ inline FeatLayout feat_layout(int d, int k) {
+  FeatLayout L;
+  size_t o = 0;
+  L.bars = o;
+  o += 8 * (2 + 2 * kFeatStages + 4 + 1);
+  L.flags = o;
+  o += 32;
+  L.tslot = o;
+  o += 16;
+  o = (o + 15) / 16 * 16;
+  L.wkeys = o;
+  o += 16 * 16;
+  L.rl = o;
+  o += 8 * (size_t)k;
+  L.acc = o;
+  o += 4 * (size_t)kTileM * (k + 1);
+  L.red = o;
+  o += 8 * (size_t)kTileM;
+  L.queue_idx = o;
+  o += 2 * (size_t)kFeatQueue * kFeatEpiWarps;
+  o = (o + 15) / 16 * 16;
+  L.queue_d2 = o;
+  o += 4 * (size_t)kFeatQueue * kFeatEpiWarps;
+  o = (o + 1023) / 1024 * 1024;
+  L.a = o;
+  o += (size_t)kTileM * d * 2;
+  L.stages = o;
+  L.meta_bytes = 5 * 4 * kTileN;
+  L.stage_bytes = (size_t)kTileN * d * 2 + L.meta_bytes;
+  L.stage_bytes = (L.stage_bytes + 1023) / 1024 * 1024;
+  o += L.stage_bytes * kFeatStages;
+  L.total = o;
+  return L;
+}
+
+__device__ __forceinline__ float bf(uint16_t v) { return __uint_as_float((uint32_t)v << 16); }
+
+// ------------------------------------------------------------ pass kernel
+template <int MODE>
+__global__ void __launch_bounds__(kFeatThreads, 1) k_feat_pass(const FeatArgs a) {
+  extern __shared__ __align__(1024) unsigned char smem[];
+  KmState* st = a.st;
+  if (st->done || st->error) return;
+  const int n = a.n, d = a.d, k = a.k;
+  const FeatLayout L = feat_layout(d, k);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + L.bars);
+  uint64_t* a_full = bars + 0;
+  uint64_t* tile_done = bars + 1;  // epilogue finished the published tile
+  uint64_t* b_full = bars + 2;                       // [S]
+  uint64_t* b_empty = bars + 2 + kFeatStages;        // [S]
+  uint64_t* acc_full = bars + 2 + 2 * kFeatStages;   // [2]
+  uint64_t* acc_empty = acc_full + 2;                // [2]
+  uint64_t* ep_bar = acc_full + 4;
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + L.flags);
+  int* last_flag = reinterpret_cast<int*>(smem + L.flags) + 1;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + L.flags) + 2;
+  int* tslot = reinterpret_cast<int*>(smem + L.tslot);  // tile index ping-pong [2]
+  Key<double>* wkeys = reinterpret_cast<Key<double>*>(smem + L.wkeys);
+  double* rl = reinterpret_cast<double*>(smem + L.rl);
+  float* acc = reinterpret_cast<float*>(smem + L.acc);
+  double* red = reinterpret_cast<double*>(smem + L.red);
+  uint16_t* qidx = reinterpret_cast<uint16_t*>(smem + L.queue_idx);
+  float* qd2 = reinterpret_cast<float*>(smem + L.queue_d2);
+  unsigned char* sA = smem + L.a;
+  unsigned char* stages = smem + L.stages;
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int rb = st->rb;
+  const int ntiles = a.n_pad / kTileM;
+  const int nblocks = a.n_pad / kTileN;
+  const uint32_t tile_bytes = (uint32_t)(kTileM * d * 2);
+
+  if (MODE == kModeSwap && blockIdx.x == 0) {
+    double* rnext = a.removal + (size_t)(rb ^ 1) * a.k_pad;
+    for (int i = tid; i < k; i += blockDim.x) rnext[i] = 0.0;
+    if (tid == 0) a.td2[rb ^ 1] = 0.0;
+  }
+  if (MODE == kModeBuild && blockIdx.x == 0 && tid == 0) st->build_td_d = 0.0;
+  if (tid == 0) {
+    mbar_init(a_full, 1);
+    mbar_init(tile_done, kFeatEpiWarps);
+    for (int q = 0; q < kFeatStages; ++q) {
+      mbar_init(&b_full[q], 1);
+      mbar_init(&b_empty[q], 1 + kFeatEpiWarps);
+    }
+    for (int q = 0; q < 2; ++q) {
+      mbar_init(&acc_full[q], 1);
+      mbar_init(&acc_empty[q], kFeatEpiWarps);
+    }
+    mbar_init(ep_bar, kFeatEpiWarps);
+    abort_flag[0] = 0;
+    *last_flag = 0;
+    fence_barrier_init();
+  }
+  if (MODE == kModeSwap) {
+    const double* rsrc = a.removal + (size_t)rb * a.k_pad;
+    for (int i = tid; i < k; i += blockDim.x) rl[i] = rsrc[i];
+    for (int i = tid; i < kTileM * (k + 1); i += blockDim.x) acc[i] = 0.f;
+  }
+  if (warp == 1) {
+    tmem_alloc(tmem_slot, 2 * kTileN);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  Key<double> wbest;
+  wbest.d = Tr<float>::g_high();
+  wbest.slot = INT_MAX;
+  wbest.cand = INT_MAX;
+
+  if (warp == 0) {
+    // ============================================================ producer
+    if (lane == 0) {
+      long long gb = 0;
+      bool ok = true;
+      uint32_t bused = 0, bph = 0;
+      for (int seq = 0; ok; ++seq) {
+        unsigned tile = atomicAdd(&st->tile_next, 1u);
+        const int t = (tile < (unsigned)ntiles) ? (int)tile : -1;
+        // publish a tile only after the epilogue finished the previous one:
+        // no waiter on a_full can fall two phases behind, and sA is free
+        if (seq > 0 && !mbar_wait(tile_done, (uint32_t)((seq - 1) & 1), abort_flag)) {
+          ok = false;
+          break;
+        }
+        tslot[seq & 1] = t;
+        if (t < 0) {
+          mbar_arrive(a_full);
+          break;
+        }
+        mbar_arrive_expect_tx(a_full, tile_bytes);
+        bulk_g2s(sA, a.Xp + (size_t)t * kTileM * d, tile_bytes, a_full);
+        for (int b = 0; b < nblocks; ++b, ++gb) {
+          const int s = (int)(gb % kFeatStages);
+          const uint32_t ph = (uint32_t)((gb / kFeatStages) & 1);
+          if (!mbar_wait(&b_empty[s], ph ^ 1u, abort_flag)) {
+            ok = false;
+            break;
+          }
+          unsigned char* sb = stages + (size_t)s * L.stage_bytes;
+          unsigned char* meta = sb + (size_t)kTileN * d * 2;
+          mbar_arrive_expect_tx(&b_full[s], tile_bytes + (uint32_t)L.meta_bytes);
+          bused |= 1u << s;
+          bph = (bph & ~(1u << s)) | (ph << s);
+          bulk_g2s(sb, a.Xp + (size_t)b * kTileN * d, tile_bytes, &b_full[s]);
+          const size_t o0 = (size_t)b * kTileN;
+          bulk_g2s(meta, a.norms + o0, 4 * kTileN, &b_full[s]);
+          if (MODE == kModeSwap) {
+            bulk_g2s(meta + 512, a.ds2 + o0, 4 * kTileN, &b_full[s]);
+            bulk_g2s(meta + 1024, a.dn + o0, 4 * kTileN, &b_full[s]);
+            bulk_g2s(meta + 1536, a.ds + o0, 4 * kTileN, &b_full[s]);
+            bulk_g2s(meta + 2048, a.near + o0, 4 * kTileN, &b_full[s]);
+          } else {
+            bulk_g2s(meta + 512, a.dn2 + o0, 4 * kTileN, &b_full[s]);
+            bulk_g2s(meta + 1024, a.dn + o0, 4 * kTileN, &b_full[s]);
+            bulk_g2s(meta + 1536, a.dn + o0, 4 * kTileN, &b_full[s]);
+            bulk_g2s(meta + 2048, a.near + o0, 4 * kTileN, &b_full[s]);
+          }
+        }
+      }
+      if (!ok) {
+        abort_flag[0] = 1;
+        atomicExch(&st->error, kErrTimeout);
+        volatile int never = 0;
+        for (int q = 0; q < kFeatStages; ++q)
+          if (bused & (1u << q)) (void)mbar_wait(&b_full[q], (bph >> q) & 1u, &never);
+      }
+    }
+  } else if (warp == 1) {
+    // ============================================================ MMA issuer
+    if (lane == 0) {
+      const uint32_t idesc = make_idesc_bf16(kTileM, kTileN);
+      const uint32_t lbo = 128, sbo = 16u * (uint32_t)d;
+      long long gb = 0;
+      long long issued = 0;  // blocks with MMAs in flight on the accumulators
+      for (int seq = 0;; ++seq) {
+        if (!mbar_wait(a_full, (uint32_t)(seq & 1), abort_flag)) break;
+        const int t = tslot[seq & 1];
+        if (t < 0) break;
+        tc_fence_after();
+        bool ok = true;
+        for (int b = 0; b < nblocks; ++b, ++gb) {
+          const int s = (int)(gb % kFeatStages);
+          const int buf = (int)(gb & 1);
+          if (!mbar_wait(&b_full[s], (uint32_t)((gb / kFeatStages) & 1), abort_flag) ||
+              !mbar_wait(&acc_empty[buf], (uint32_t)(((gb >> 1) & 1) ^ 1), abort_flag)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t sa = smem_u32(sA);
+          const uint32_t sb = smem_u32(stages + (size_t)s * L.stage_bytes);
+          for (int ks = 0; ks < d / 16; ++ks)
+            umma_bf16(tmem + (uint32_t)(buf * kTileN), make_sdesc(sa + ks * 256, lbo, sbo),
+                      make_sdesc(sb + ks * 256, lbo, sbo), idesc, ks > 0 ? 1u : 0u);
+          umma_commit(&acc_full[buf]);
+          umma_commit(&b_empty[s]);
+          ++issued;
+        }
+        if (!ok) break;
+      }
+      if (abort_flag[0] && issued > 0) {  // let issued MMAs finish before exit
+        volatile int never = 0;
+        const long long lastb = gb - 1;
+        (void)mbar_wait(&acc_full[lastb & 1], (uint32_t)((lastb >> 1) & 1), &never);
+      }
+    }
+  } else {
+    // ============================================================ epilogue
+    const int ew = warp - 2;              // 0..7
+    const int quarter = warp & 3;         // TMEM lanes 32*quarter..+31
+    const int group = ew >> 2;            // columns 64*group..+63
+    const int r = quarter * 32 + lane;    // candidate row within the tile
+    uint32_t eph = 0;
+    long long gb = 0;
+    uint16_t* myqi = qidx + ew * kFeatQueue;
+    float* myqd = qd2 + ew * kFeatQueue;
+    bool ok = true;
+    for (int seq = 0; ok; ++seq) {
+      if (!mbar_wait(a_full, (uint32_t)(seq & 1), abort_flag)) {
+        ok = false;
+        break;
+      }
+      const int t = tslot[seq & 1];
+      if (t < 0) break;
+      const int c = t * kTileM + r;
+      const bool cvalid = (c < n) && !a.is_med[c];
+      const float nc = (c < n) ? a.norms[c] : 0.f;
+      float ks_ = 0.f, kc_ = 0.f;  // BUILD Kahan pair
+      for (int b = 0; b < nblocks; ++b, ++gb) {
+        const int s = (int)(gb % kFeatStages);
+        const int buf = (int)(gb & 1);
+        if (!mbar_wait(&acc_full[buf], (uint32_t)((gb >> 1) & 1), abort_flag) ||
+            !mbar_wait(&b_full[s], (uint32_t)((gb / kFeatStages) & 1), abort_flag)) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        float v[64];
+        {
+          float* v0 = v;
+          float* v1 = v + 32;
+          const uint32_t ta = tmem + ((uint32_t)(quarter * 32) << 16) +
+                              (uint32_t)(buf * kTileN + group * 64);
+          tmem_ld32(ta, *reinterpret_cast<float(*)[32]>(v0));
+          tmem_ld32(ta + 32, *reinterpret_cast<float(*)[32]>(v1));
+          tmem_ld_wait();
+        }
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&acc_empty[buf]);
+        const unsigned char* meta =
+            stages + (size_t)s * L.stage_bytes + (size_t)kTileN * d * 2;
+        const float* m_no = reinterpret_cast<const float*>(meta);
+        const float* m_x1 = reinterpret_cast<const float*>(meta + 512);   // ds2 | dn2
+        const float* m_x2 = reinterpret_cast<const float*>(meta + 1024);  // dn
+        const float* m_x3 = reinterpret_cast<const float*>(meta + 1536);  // ds
+        const int* m_near = reinterpret_cast<const int*>(meta + 2048);
+        const int col0 = group * 64;
+        if (MODE == kModeSwap) {
+          unsigned long long hmask = 0ull;
+#pragma unroll
+          for (int j = 0; j < 64; j += 4) {
+            const float4 no4 = *reinterpret_cast<const float4*>(m_no + col0 + j);
+            const float4 sq4 = *reinterpret_cast<const float4*>(m_x1 + col0 + j);
+            const float e0 = fmaf(-2.f, v[j], nc + no4.x);
+            const float e1 = fmaf(-2.f, v[j + 1], nc + no4.y);
+            const float e2 = fmaf(-2.f, v[j + 2], nc + no4.z);
+            const float e3 = fmaf(-2.f, v[j + 3], nc + no4.w);
+            v[j] = e0;
+            v[j + 1] = e1;
+            v[j + 2] = e2;
+            v[j + 3] = e3;
+            const unsigned h = (e0 < sq4.x ? 1u : 0u) | (e1 < sq4.y ? 2u : 0u) |
+                               (e2 < sq4.z ? 4u : 0u) | (e3 < sq4.w ? 8u : 0u);
+            hmask |= (unsigned long long)h << j;
+          }
+          if (!cvalid) hmask = 0ull;
+          // warp compaction of (row, column, d^2) hits, then a full-lane drain
+          const int cnt = __popcll(hmask);
+          int incl = cnt;
+#pragma unroll
+          for (int o = 1; o < 32; o <<= 1) {
+            const int x = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += x;
+          }
+          const int total = __shfl_sync(0xffffffffu, incl, 31);
+          if (total > 0 && total <= kFeatQueue) {
+            int pos = incl - cnt;
+            unsigned long long mk = hmask;
+            while (mk) {
+              const int j = __ffsll(mk) - 1;
+              mk &= mk - 1;
+              myqi[pos] = (uint16_t)((lane << 6) | j);
+              float dj = 0.f;
+#pragma unroll
+              for (int q = 0; q < 64; ++q) dj = (q == j) ? v[q] : dj;
+              myqd[pos] = dj;
+              ++pos;
+            }
+            __syncwarp();
+            for (int e = lane; e < total; e += 32) {
+              const unsigned qi = myqi[e];
+              const int src = (int)(qi >> 6), j = (int)(qi & 63);
+              const int col = col0 + j;
+              const float dd = sqrtf(fmaxf(myqd[e], 0.f));
+              const float dn_ = m_x2[col], ds_ = m_x3[col];
+              const int sl = m_near[col];
+              float* arow = acc + (size_t)(quarter * 32 + src) * (k + 1);
+              if (dd < dn_) {
+                atomicAdd(arow + k, dd - dn_);
+                atomicAdd(arow + sl, dn_ - ds_);
+              } else {
+                atomicAdd(arow + sl, dd - ds_);
+              }
+            }
+            __syncwarp();
+          } else if (total > kFeatQueue) {
+            // dense block: every lane its own hits
+            unsigned long long mk = hmask;
+            float* arow = acc + (size_t)r * (k + 1);
+            while (mk) {
+              const int j = __ffsll(mk) - 1;
+              mk &= mk - 1;
+              float dj = 0.f;
+#pragma unroll
+              for (int q = 0; q < 64; ++q) dj = (q == j) ? v[q] : dj;
+              const int col = col0 + j;
+              const float dd = sqrtf(fmaxf(dj, 0.f));
+              const float dn_ = m_x2[col], ds_ = m_x3[col];
+              const int sl = m_near[col];
+              if (dd < dn_) {
+                atomicAdd(arow + k, dd - dn_);
+                atomicAdd(arow + sl, dn_ - ds_);
+              } else {
+                atomicAdd(arow + sl, dd - ds_);
+              }
+            }
+            __syncwarp();
+          }
+        } else {
+          const int colg = b * kTileN + col0;
+#pragma unroll 8
+          for (int j = 0; j < 64; ++j) {
+            const float d2 = fmaf(-2.f, v[j], nc + m_no[col0 + j]);
+            float x = 0.f;
+            if (a.build_first) {
+              if (colg + j < n) x = sqrtf(fmaxf(d2, 0.f));
+            } else if (d2 < m_x1[col0 + j]) {
+              const float dd = sqrtf(fmaxf(d2, 0.f));
+              const float dn_ = m_x2[col0 + j];
+              if (dd < dn_) x = dd - dn_;
+            }
+            const float y = x - kc_;
+            const float tt = ks_ + y;
+            kc_ = (tt - ks_) - y;
+            ks_ = tt;
+          }
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&b_empty[s]);
+      }
+      if (!ok) break;
+      // ------------------------------------------------------ tile finished
+      if (MODE == kModeBuild && group == 1) red[r] = (double)ks_ - (double)kc_;
+      if (!cons_sync(ep_bar, eph, abort_flag)) {
+        ok = false;
+        break;
+      }
+      if (group == 0) {
+        if (MODE == kModeSwap) {
+          float* arow = acc + (size_t)r * (k + 1);
+          if (cvalid) {
+            double best = 1e300;
+            int bi = 0;
+            for (int i = 0; i < k; ++i) {
+              const double vi = rl[i] + (double)arow[i];
+              if (vi < best) {
+                best = vi;
+                bi = i;
+              }
+            }
+            Key<double> ck;
+            ck.d = best + (double)arow[k];
+            ck.slot = bi;
+            ck.cand = c;
+            if (key_less(ck, wbest)) wbest = ck;
+          }
+          for (int i = 0; i <= k; ++i) arow[i] = 0.f;
+        } else {
+          if (cvalid) {
+            Key<double> ck;
+            ck.d = ((double)ks_ - (double)kc_) + red[r];
+            ck.slot = 0;
+            ck.cand = c;
+            if (key_less(ck, wbest)) wbest = ck;
+          }
+        }
+      }
+      if (!cons_sync(ep_bar, eph, abort_flag)) {
+        ok = false;
+        break;
+      }
+      if (lane == 0) mbar_arrive(tile_done);
+    }
+    if (!ok) {
+      abort_flag[0] = 1;
+      atomicExch(&st->error, kErrTimeout);
+    }
+    wbest = warp_min_key(wbest);
+    if (lane == 0) wkeys[ew] = wbest;
+  }
+
+  // ------------------------------------------------------------ CTA result
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) tmem_dealloc(tmem, 2 * kTileN);
+  if (tid == 0) {
+    Key<double> b = wkeys[0];
+    for (int w = 1; w < kFeatEpiWarps; ++w)
+      if (key_less(wkeys[w], b)) b = wkeys[w];
+    reinterpret_cast<Key<double>*>(a.partials)[blockIdx.x] = b;
+    __threadfence();
+    const unsigned tk = atomicAdd(&st->ticket, 1u);
+    *last_flag = (tk == gridDim.x - 1) ? 1 : 0;
+  }
+  __syncthreads();
+  if (!*last_flag) return;
+  __threadfence();
+  if (warp == 0) {
+    Key<double> b;
+    b.d = Tr<float>::g_high();
+    b.slot = INT_MAX;
+    b.cand = INT_MAX;
+    for (int g = lane; g < (int)gridDim.x; g += 32) {
+      const Key<double> v = ld_cg_key(reinterpret_cast<const Key<double>*>(a.partials) + g);
+      if (key_less(v, b)) b = v;
+    }
+    b = warp_min_key(b);
+    if (lane == 0) {
+      if (MODE == kModeBuild) {
+        st->build_gain_d = b.d;
+        st->build_cand = b.cand;
+      } else {
+        st->best_d = b.d;
+        st->best_i = 0;
+        st->best_slot = (b.cand == INT_MAX) ? -1 : b.slot;
+        st->best_cand = (b.cand == INT_MAX) ? -1 : b.cand;
+        st->iter += 1;
+        if (b.cand != INT_MAX && b.d < -a.tol) {
+          st->accept = 1;
+        } else {
+          st->accept = 0;
+          st->done = 1;
+        }
+      }
+      st->tile_next = 0;
+      st->ticket = 0;
+    }
+  }
+}
+
+// ------------------------------------------------- exact distance kernels
+// Squared Euclidean distance in FP32 by direct differences.
+__device__ __forceinline__ float dist2_rows(const uint16_t* x, const uint16_t* y, int d) {
+  float s = 0.f;
+  for (int t = 0; t < d; t += 8) {
+    const uint4 a = *reinterpret_cast<const uint4*>(x + t);
+    const uint4 b = *reinterpret_cast<const uint4*>(y + t);
+    const uint32_t av[4] = {a.x, a.y, a.z, a.w}, bv[4] = {b.x, b.y, b.z, b.w};
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const float d0 = __uint_as_float(av[q] << 16) - __uint_as_float(bv[q] << 16);
+      const float d1 = __uint_as_float(av[q] & 0xffff0000u) - __uint_as_float(bv[q] & 0xffff0000u);
+      s = fmaf(d0, d0, s);
+      s = fmaf(d1, d1, s);
+    }
+  }
+  return s;
+}
+
+template <class V>
+__device__ __forceinline__ V fblock_sum(V v, V* scratch) {
+  v = warp_sum(v);
+  if ((threadIdx.x & 31) == 0) scratch[threadIdx.x >> 5] = v;
+  __syncthreads();
+  V r = V(0);
+  if (threadIdx.x == 0)
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) r += scratch[i];
+  __syncthreads();
+  return r;
+}
+
+__device__ __forceinline__ void top2f(float v, int j, int& n1, float& d1, int& n2, float& d2) {
+  if (n1 < 0 || v < d1) {
+    n2 = n1;
+    d2 = d1;
+    n1 = j;
+    d1 = v;
+  } else if (n2 < 0 || v < d2) {
+    n2 = j;
+    d2 = v;
+  }
+}
+
+// Exact cache of every point for the current medoids (distances compared
+// squared; d_n, d_s stored as FP32 square roots), removal loss and TD.
+__global__ void __launch_bounds__(256) k_feat_cache(const FeatArgs a) {
+  extern __shared__ __align__(16) unsigned char sm[];
+  double* sacc = reinterpret_cast<double*>(sm);
+  __shared__ double scratch[8];
+  __shared__ int is_last;
+  KmState* st = a.st;
+  const int k = a.k, n = a.n, d = a.d;
+  const int rb = st->rb;
+  for (int i = threadIdx.x; i < k; i += blockDim.x) sacc[i] = 0.0;
+  __syncthreads();
+  const int o = blockIdx.x * blockDim.x + threadIdx.x;
+  double tdl = 0.0;
+  if (o < n) {
+    const uint16_t* xo = a.X + (size_t)o * a.ldx;
+    int n1 = -1, n2 = -1;
+    float q1 = 0.f, q2 = 0.f;
+    for (int j = 0; j < k; ++j) top2f(dist2_rows(xo, a.X + (size_t)a.med[j] * a.ldx, d), j, n1, q1, n2, q2);
+    const float e1 = sqrtf(q1);
+    const float e2 = (n2 < 0) ? Tr<float>::high() : sqrtf(q2);
+    a.near[o] = n1;
+    a.sec[o] = n2;
+    a.dn[o] = e1;
+    a.ds[o] = e2;
+    a.dn2[o] = q1;
+    a.ds2[o] = (n2 < 0) ? Tr<float>::high() : q2;
+    if (n2 >= 0) atomicAdd(&sacc[n1], (double)e2 - (double)e1);
+    tdl = e1;
+  } else if (o < a.n_pad) {
+    a.near[o] = 0;
+    a.sec[o] = 0;
+    a.dn[o] = 0.f;
+    a.ds[o] = 0.f;
+    a.dn2[o] = Tr<float>::low();
+    a.ds2[o] = Tr<float>::low();
+  }
+  const double bs = fblock_sum(tdl, scratch);
+  if (threadIdx.x == 0) atomicAdd(&a.td2[rb], bs);
+  double* rem = a.removal + (size_t)rb * a.k_pad;
+  for (int i = threadIdx.x; i < k; i += blockDim.x)
+    if (sacc[i] != 0.0) atomicAdd(&rem[i], sacc[i]);
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) is_last = (atomicAdd(&st->ticket, 1u) == gridDim.x - 1);
+  __syncthreads();
+  if (is_last && threadIdx.x == 0) {
+    __threadfence();
+    st->td_book_d = static_cast<volatile double*>(a.td2)[rb];
+    st->ticket = 0;
+  }
+}
+
+// Apply the pending swap (slot i* <- candidate c*) with an incremental,
+// exact cache update; removal loss and TD of the next pass on the way.
+__global__ void __launch_bounds__(256) k_feat_apply(const FeatArgs a) {
+  extern __shared__ __align__(16) unsigned char sm[];
+  double* sacc = reinterpret_cast<double*>(sm);
+  __shared__ double scratch[8];
+  __shared__ int is_last;
+  KmState* st = a.st;
+  if (st->error || !st->accept) return;
+  const int k = a.k, n = a.n, d = a.d;
+  const int i_s = st->best_slot, c_s = st->best_cand;
+  const int rb = st->rb;
+  for (int i = threadIdx.x; i < k; i += blockDim.x) sacc[i] = 0.0;
+  __syncthreads();
+  const int o = blockIdx.x * blockDim.x + threadIdx.x;
+  double tdl = 0.0;
+  if (o < n) {
+    const uint16_t* xo = a.X + (size_t)o * a.ldx;
+    int n1 = a.near[o], n2 = a.sec[o];
+    float q1 = a.dn2[o], q2 = a.ds2[o];
+    if (n1 == i_s || n2 == i_s) {
+      n1 = -1;
+      n2 = -1;
+      for (int j = 0; j < k; ++j) {
+        const int m = (j == i_s) ? c_s : a.med[j];
+        top2f(dist2_rows(xo, a.X + (size_t)m * a.ldx, d), j, n1, q1, n2, q2);
+      }
+    } else {
+      const float qc = dist2_rows(xo, a.X + (size_t)c_s * a.ldx, d);
+      if (qc < q1 || (qc == q1 && i_s < n1)) {
+        n2 = n1;
+        q2 = q1;
+        n1 = i_s;
+        q1 = qc;
+      } else if (qc < q2 || (qc == q2 && i_s < n2)) {
+        n2 = i_s;
+        q2 = qc;
+      }
+    }
+    const float e1 = sqrtf(q1), e2 = sqrtf(q2);
+    a.near[o] = n1;
+    a.sec[o] = n2;
+    a.dn[o] = e1;
+    a.ds[o] = e2;
+    a.dn2[o] = q1;
+    a.ds2[o] = q2;
+    atomicAdd(&sacc[n1], (double)e2 - (double)e1);
+    tdl = e1;
+  }
+  const double bs = fblock_sum(tdl, scratch);
+  if (threadIdx.x == 0) atomicAdd(&a.td2[rb ^ 1], bs);
+  double* rem = a.removal + (size_t)(rb ^ 1) * a.k_pad;
+  for (int i = threadIdx.x; i < k; i += blockDim.x)
+    if (sacc[i] != 0.0) atomicAdd(&rem[i], sacc[i]);
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) is_last = (atomicAdd(&st->ticket, 1u) == gridDim.x - 1);
+  __syncthreads();
+  if (is_last && threadIdx.x == 0) {
+    __threadfence();
+    const int old = a.med[i_s];
+    a.med[i_s] = c_s;
+    a.is_med[old] = 0;
+    a.is_med[c_s] = 1;
+    const int nt = st->ntrace;
+    if (nt < a.trace_cap) {
+      TraceRec* tr = static_cast<TraceRec*>(a.trace) + nt;
+      tr->d = st->best_d;
+      tr->di = 0;
+      tr->slot = i_s;
+      tr->cand = c_s;
+      tr->t_ns = (long long)globaltimer();
+    }
+    st->ntrace = nt + 1;
+    st->swaps += 1;
+    st->td_book_d += st->best_d;
+    st->accept = 0;
+    st->rb = rb ^ 1;
+    st->ticket = 0;
+  }
+}
+
+// BUILD commit: add the chosen point and lower d_n (exact FP32 distances).
+__global__ void __launch_bounds__(256) k_feat_build_commit(const FeatArgs a) {
+  __shared__ double scratch[8];
+  KmState* st = a.st;
+  if (st->error) return;
+  const int n = a.n, d = a.d;
+  const int c = st->build_cand;
+  const int o = blockIdx.x * blockDim.x + threadIdx.x;
+  double local = 0.0;
+  if (c >= 0 && c < n) {
+    if (o < n) {
+      const float q = dist2_rows(a.X + (size_t)o * a.ldx, a.X + (size_t)c * a.ldx, d);
+      float cur = q;
+      if (!a.build_first && !(q < a.dn2[o])) cur = a.dn2[o];
+      a.dn2[o] = cur;
+      a.dn[o] = sqrtf(cur);
+      local = sqrtf(cur);
+    } else if (o < a.n_pad) {
+      a.dn2[o] = Tr<float>::low();
+      a.dn[o] = 0.f;
+    }
+  }
+  const double bs = fblock_sum(local, scratch);
+  if (threadIdx.x == 0) atomicAdd(&st->build_td_d, bs);
+  if (blockIdx.x == 0 && threadIdx.x == 0 && c >= 0 && c < n) {
+    const int step = st->build_step;
+    a.med[step] = c;
+    a.is_med[c] = 1;
+    if (a.gains) a.gains[step] = st->build_gain_d;
+    st->td_book_d = a.build_first ? st->build_gain_d : st->td_book_d + st->build_gain_d;
+    st->build_step = step + 1;
+  }
+}
+
+__global__ void k_feat_mark(const FeatArgs a) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j < a.k) a.is_med[a.med[j]] = 1;
+}
+
+}  // namespace km
+
+// ============================================================== host side
+using namespace km;
+
+namespace {
+
+struct FeatWs {
+  size_t st, med, is_med, near, sec, dn, ds, dn2, ds2, norms, removal, td2, partials, trace,
+      gains, xp, total;
+  int n_pad, k_pad, cap;
+};
+
+bool feat_ws(int64_t n, int d, int k, const km_options* o, FeatWs* L) {
+  if (n <= 0 || k <= 0 || k > n || d <= 0 || d > kFeatMaxD || d % 16 || n > (1 << 28))
+    return false;
+  auto al = [](size_t x) { return (x + 255) / 256 * 256; };
+  const int n_pad = (int)((n + kTileM - 1) / kTileM * kTileM);
+  const int k_pad = (k + 31) / 32 * 32;
+  const int cap = (o && o->trace_capacity > 0) ? o->trace_capacity : 0;
+  size_t off = 0;
+  auto take = [&](size_t b) {
+    size_t r = off;
+    off += al(b);
+    return r;
+  };
+  L->st = take(512);
+  L->med = take(4 * (size_t)k_pad);
+  L->is_med = take((size_t)n_pad);
+  L->near = take(4 * (size_t)n_pad);
+  L->sec = take(4 * (size_t)n_pad);
+  L->dn = take(4 * (size_t)n_pad);
+  L->ds = take(4 * (size_t)n_pad);
+  L->dn2 = take(4 * (size_t)n_pad);
+  L->ds2 = take(4 * (size_t)n_pad);
+  L->norms = take(4 * (size_t)n_pad);
+  L->removal = take(16 * (size_t)k_pad);
+  L->td2 = take(16);
+  L->partials = take(16 * (size_t)kMaxGrid);
+  L->trace = take(sizeof(TraceRec) * (size_t)(cap > 0 ? cap : 1));
+  L->gains = take(8 * (size_t)k);
+  L->xp = take((size_t)n_pad * d * 2);
+  L->total = off;
+  L->n_pad = n_pad;
+  L->k_pad = k_pad;
+  L->cap = cap;
+  return true;
+}
+
+km_status ffail(km_status s, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  set_last_error(buf);
+  return s;
+}
+
+#define FK(call)                                                                                \
+  do {                                                                                          \
+    cudaError_t e_ = (call);                                                                    \
+    if (e_ != cudaSuccess)                                                                      \
+      return ffail(KM_E_CUDA, "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, \
+                   __LINE__);                                                                   \
+  } while (0)
+
+struct FCtx {
+  FeatWs L;
+  unsigned char* ws;
+  FeatArgs a;
+  cudaStream_t s;
+  km_options opt;
+  int sms;
+  long long launches = 0;
+  KmState* st() const { return reinterpret_cast<KmState*>(ws + L.st); }
+};
+
+km_status f_read(FCtx& c, KmState* h) {
+  FK(cudaMemcpyAsync(h, c.st(), sizeof(KmState), cudaMemcpyDeviceToHost, c.s));
+  FK(cudaStreamSynchronize(c.s));
+  if (h->error) return ffail((km_status)h->error, "device reported status %d", h->error);
+  return KM_OK;
+}
+
+km_status f_reset(FCtx& c) {
+  KmState h;
+  memset(&h, 0, sizeof(h));
+  h.last = -1;
+  FK(cudaMemcpyAsync(c.st(), &h, sizeof(h), cudaMemcpyHostToDevice, c.s));
+  return KM_OK;
+}
+
+km_status f_pass(FCtx& c, int mode, int first) {
+  FeatArgs a = c.a;
+  a.mode = mode;
+  a.build_first = first;
+  const FeatLayout L = feat_layout(a.d, a.k);
+  if (L.total > 227 * 1024) return ffail(KM_E_UNSUPPORTED, "feature pass needs %zu B of shared memory", L.total);
+  int grid = c.sms;
+  if (grid > a.n_pad / kTileM) grid = a.n_pad / kTileM;
+  if (grid > kMaxGrid) grid = kMaxGrid;
+  if (mode == kModeSwap) {
+    FK(cudaFuncSetAttribute(k_feat_pass<kModeSwap>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total));
+    k_feat_pass<kModeSwap><<<grid, kFeatThreads, L.total, c.s>>>(a);
+  } else {
+    FK(cudaFuncSetAttribute(k_feat_pass<kModeBuild>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total));
+    k_feat_pass<kModeBuild><<<grid, kFeatThreads, L.total, c.s>>>(a);
+  }
+  FK(cudaGetLastError());
+  ++c.launches;
+  return KM_OK;
+}
+
+km_status f_cache(FCtx& c) {
+  FK(cudaMemsetAsync(c.a.is_med, 0, (size_t)c.L.n_pad, c.s));
+  FK(cudaMemsetAsync(c.a.removal, 0, 16 * (size_t)c.L.k_pad, c.s));
+  FK(cudaMemsetAsync(c.a.td2, 0, 16, c.s));
+  k_feat_mark<<<(c.a.k + 255) / 256, 256, 0, c.s>>>(c.a);
+  FK(cudaGetLastError());
+  const size_t sm = 8 * (size_t)c.a.k;
+  FK(cudaFuncSetAttribute(k_feat_cache, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+  k_feat_cache<<<(c.L.n_pad + 255) / 256, 256, sm, c.s>>>(c.a);
+  FK(cudaGetLastError());
+  c.launches += 2;
+  return KM_OK;
+}
+
+km_status run_features(bool do_build, bool do_swap, const void* X, int64_t n, int32_t d,
+                       int64_t ldx, int32_t k, int32_t* medoids, int32_t* labels,
+                       const km_options* opts, km_result* res, void* ws, size_t ws_bytes,
+                       void* stream) {
+  set_last_error("");
+  if (!X || !medoids || !ws) return ffail(KM_E_INVALID, "NULL pointer");
+  km_options def;
+  km_default_options(&def);
+  FCtx c;
+  c.opt = opts ? *opts : def;
+  if (c.opt.variant != KM_FASTPAM1)
+    return ffail(KM_E_UNSUPPORTED, "the feature form implements FastPAM1 SWAP only");
+  if (!feat_ws(n, d, k, &c.opt, &c.L))
+    return ffail(KM_E_INVALID, "need 1 <= k <= n <= 2^28 and d a multiple of 16 up to 256");
+  if (k > kFeatMaxK) return ffail(KM_E_UNSUPPORTED, "feature form supports k <= %d", kFeatMaxK);
+  if (ldx < d || ldx % 8) return ffail(KM_E_INVALID, "ldx must be >= d and a multiple of 8");
+  if (reinterpret_cast<uintptr_t>(X) % 16 || reinterpret_cast<uintptr_t>(ws) % 256)
+    return ffail(KM_E_INVALID, "X must be 16-byte and ws 256-byte aligned");
+  if (ws_bytes < c.L.total)
+    return ffail(KM_E_WORKSPACE, "workspace too small: %zu < %zu", ws_bytes, c.L.total);
+  if (c.opt.max_iter <= 0) c.opt.max_iter = 100 * k + 100;
+  c.ws = static_cast<unsigned char*>(ws);
+  c.s = static_cast<cudaStream_t>(stream);
+  c.sms = device_sm_count();
+  if (c.sms <= 0) return ffail(KM_E_CUDA, "no CUDA device");
+  FeatArgs& a = c.a;
+  memset(&a, 0, sizeof(a));
+  a.X = static_cast<const uint16_t*>(X);
+  a.ldx = ldx;
+  a.n = (int)n;
+  a.d = d;
+  a.k = k;
+  a.n_pad = c.L.n_pad;
+  a.k_pad = c.L.k_pad;
+  a.Xp = reinterpret_cast<const uint16_t*>(c.ws + c.L.xp);
+  a.norms = reinterpret_cast<const float*>(c.ws + c.L.norms);
+  a.near = reinterpret_cast<int32_t*>(c.ws + c.L.near);
+  a.sec = reinterpret_cast<int32_t*>(c.ws + c.L.sec);
+  a.dn = reinterpret_cast<float*>(c.ws + c.L.dn);
+  a.ds = reinterpret_cast<float*>(c.ws + c.L.ds);
+  a.dn2 = reinterpret_cast<float*>(c.ws + c.L.dn2);
+  a.ds2 = reinterpret_cast<float*>(c.ws + c.L.ds2);
+  a.is_med = c.ws + c.L.is_med;
+  a.med = reinterpret_cast<int32_t*>(c.ws + c.L.med);
+  a.removal = reinterpret_cast<double*>(c.ws + c.L.removal);
+  a.td2 = reinterpret_cast<double*>(c.ws + c.L.td2);
+  a.st = c.st();
+  a.partials = c.ws + c.L.partials;
+  a.gains = reinterpret_cast<double*>(c.ws + c.L.gains);
+  a.trace = c.ws + c.L.trace;
+  a.trace_cap = c.L.cap;
+  a.tol = c.opt.tol;
+  if (res) memset(res, 0, sizeof(*res));
+
+  cudaEvent_t e0 = nullptr, e1 = nullptr, e2 = nullptr;
+  const bool prof = c.opt.profile != 0;
+  if (prof) {
+    FK(cudaEventCreate(&e0));
+    FK(cudaEventCreate(&e1));
+    FK(cudaEventCreate(&e2));
+  }
+  km_status r = f_reset(c);
+  if (r != KM_OK) return r;
+  FK(launch_prearrange(X, ldx, (int)n, d, c.L.n_pad, c.ws + c.L.xp, c.s));
+  FK(launch_row_norms(X, ldx, (int)n, d, c.L.n_pad, const_cast<float*>(a.norms), c.s));
+  c.launches += 2;
+  if (prof) FK(cudaEventRecord(e0, c.s));
+  KmState h;
+  memset(&h, 0, sizeof(h));
+  if (do_build) {
+    FK(cudaMemsetAsync(a.is_med, 0, (size_t)c.L.n_pad, c.s));
+    for (int step = 0; step < k; ++step) {
+      r = f_pass(c, kModeBuild, step == 0);
+      if (r != KM_OK) return r;
+      FeatArgs b = a;
+      b.build_first = (step == 0);
+      k_feat_build_commit<<<(c.L.n_pad + 255) / 256, 256, 0, c.s>>>(b);
+      FK(cudaGetLastError());
+      ++c.launches;
+    }
+    r = f_read(c, &h);
+    if (r != KM_OK) return r;
+    if (res) {
+      res->build_steps = h.build_step;
+      res->td_initial = h.td_book_d;
+    }
+    if (c.opt.build_gains)
+      FK(cudaMemcpy(c.opt.build_gains, a.gains, 8 * (size_t)k, cudaMemcpyDeviceToHost));
+  } else {
+    FK(cudaMemcpyAsync(a.med, medoids, 4 * (size_t)k, cudaMemcpyDeviceToDevice, c.s));
+  }
+  if (prof) FK(cudaEventRecord(e1, c.s));
+  km_status conv = KM_OK;
+  r = f_reset(c);
+  if (r != KM_OK) return r;
+  r = f_cache(c);
+  if (r != KM_OK) return r;
+  if (do_swap && k < n) {
+    int launched = 0, batch = 1;
+    const size_t sm = 8 * (size_t)k;
+    FK(cudaFuncSetAttribute(k_feat_apply, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    while (true) {
+      int nb = batch;
+      if (launched + nb > c.opt.max_iter) nb = c.opt.max_iter - launched;
+      for (int j = 0; j < nb; ++j) {
+        r = f_pass(c, kModeSwap, 0);
+        if (r != KM_OK) return r;
+        k_feat_apply<<<(a.n + 255) / 256, 256, sm, c.s>>>(a);
+        FK(cudaGetLastError());
+        ++c.launches;
+      }
+      launched += nb;
+      r = f_read(c, &h);
+      if (r != KM_OK) return r;
+      if (h.done || launched >= c.opt.max_iter) break;
+      batch = batch < 32 ? batch * 2 : 32;
+    }
+    if (!h.done) conv = KM_E_NOT_CONVERGED;
+  }
+  if (prof) FK(cudaEventRecord(e2, c.s));
+  r = f_read(c, &h);
+  if (r != KM_OK) return r;
+  double td = 0.0;
+  FK(cudaMemcpyAsync(&td, a.td2 + h.rb, 8, cudaMemcpyDeviceToHost, c.s));
+  FK(cudaMemcpyAsync(medoids, a.med, 4 * (size_t)k, cudaMemcpyDeviceToDevice, c.s));
+  if (labels) FK(cudaMemcpyAsync(labels, a.near, 4 * (size_t)n, cudaMemcpyDeviceToDevice, c.s));
+  const int nt = h.ntrace < c.L.cap ? h.ntrace : c.L.cap;
+  std::vector<TraceRec> tr((size_t)(nt > 0 ? nt : 0));
+  if (nt > 0) FK(cudaMemcpyAsync(tr.data(), a.trace, sizeof(TraceRec) * nt, cudaMemcpyDeviceToHost, c.s));
+  FK(cudaStreamSynchronize(c.s));
+  for (int i = 0; i < nt; ++i) {
+    if (c.opt.trace_delta) c.opt.trace_delta[i] = tr[i].d;
+    if (c.opt.trace_slot) c.opt.trace_slot[i] = tr[i].slot;
+    if (c.opt.trace_cand) c.opt.trace_cand[i] = tr[i].cand;
+    if (c.opt.trace_time_ns) c.opt.trace_time_ns[i] = tr[i].t_ns;
+  }
+  if (res) {
+    res->td = td;
+    res->td_bookkept = h.td_book_d;
+    res->iterations = h.iter;
+    res->swaps = h.swaps;
+    res->status = conv;
+    res->kernel_launches = c.launches;
+    if (prof) {
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      res->build_ms = ms;
+      cudaEventElapsedTime(&ms, e1, e2);
+      res->swap_ms = ms;
+    }
+  }
+  if (prof) {
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaEventDestroy(e2);
+  }
+  if (conv != KM_OK) ffail(conv, "max_iter reached before convergence");
+  return conv;
+}
+
+}  // namespace
+
+extern "C" size_t kmedoids_features_workspace_size(int64_t n, int32_t d, int32_t k,
+                                                   const km_options* opts) {
+  FeatWs L;
+  km_options def;
+  km_default_options(&def);
+  if (!feat_ws(n, d, k, opts ? opts : &def, &L)) return 0;
+  return L.total;
+}
+
+extern "C" km_status kmedoids_run_features(const void* X, int64_t n, int32_t d, int64_t ldx,
+                                           int32_t k, int32_t* medoids_out, int32_t* labels_out,
+                                           const km_options* opts, km_result* res, void* ws,
+                                           size_t ws_bytes, void* stream) {
+  return run_features(true, true, X, n, d, ldx, k, medoids_out, labels_out, opts, res, ws,
+                      ws_bytes, stream);
+}
+
+extern "C" km_status kmedoids_swap_features(const void* X, int64_t n, int32_t d, int64_t ldx,
+                                            int32_t k, int32_t* medoids_inout,
+                                            int32_t* labels_out, const km_options* opts,
+                                            km_result* res, void* ws, size_t ws_bytes,
+                                            void* stream) {
+  return run_features(false, true, X, n, d, ldx, k, medoids_inout, labels_out, opts, res, ws,
+                      ws_bytes, stream);
+}

@@ -23,7 +23,9 @@ STATUS = {0: "KM_OK", 1: "KM_E_INVALID", 2: "KM_E_WORKSPACE", 3: "KM_E_CUDA",
 EXPORTS = ["km_default_options", "kmedoids_workspace_size", "kmedoids_build",
            "kmedoids_swap", "kmedoids_run", "kmedoids_eval_swaps",
            "kmedoids_cache", "kmedoids_last_error", "kmedoids_version",
-           "kmedoids_eval_swaps_static", "kmedoids_gram_bf16"]
+           "kmedoids_eval_swaps_static", "kmedoids_gram_bf16",
+           "kmedoids_features_workspace_size", "kmedoids_run_features",
+           "kmedoids_swap_features"]
 
 
 class KmError(RuntimeError):
@@ -100,6 +102,12 @@ def load(path: str = LIB_PATH):
         lib.kmedoids_eval_swaps_static.restype = i32
         lib.kmedoids_gram_bf16.argtypes = [P, i64, i32, i64, P, i64, P, sz, P]
         lib.kmedoids_gram_bf16.restype = i32
+        lib.kmedoids_features_workspace_size.argtypes = [i64, i32, i32, opt_p]
+        lib.kmedoids_features_workspace_size.restype = sz
+        for name in ("kmedoids_run_features", "kmedoids_swap_features"):
+            f = getattr(lib, name)
+            f.argtypes = [P, i64, i32, i64, i32, P, P, opt_p, res_p, P, sz, P]
+            f.restype = i32
         lib.kmedoids_last_error.restype = ctypes.c_char_p
         lib.kmedoids_version.restype = ctypes.c_char_p
         _LIB = lib
@@ -346,6 +354,58 @@ def gram_bf16(X):
         ctypes.c_void_p(G.data_ptr()), n, ctypes.c_void_p(ws.data_ptr()),
         ws.numel(), _stream()))
     return G
+
+
+def _features_call(fn_name, X, k, med, labels, kw):
+    torch = _torch()
+    lib = load()
+    if X.dtype != torch.bfloat16 or X.dim() != 2 or X.stride(1) != 1:
+        raise ValueError("X must be a 2-D bf16 CUDA tensor with unit column stride")
+    n, d = X.shape
+    o = options(**kw)
+    tr = _Trace(o, o.trace_capacity, k, fn_name == "kmedoids_run_features")
+    nbytes = lib.kmedoids_features_workspace_size(n, d, k, ctypes.byref(o))
+    if nbytes == 0:
+        raise KmError(1, "invalid sizes for the feature form")
+    ws = torch.empty(nbytes, dtype=torch.uint8, device=X.device)
+    res = km_result()
+    st = getattr(lib, fn_name)(
+        ctypes.c_void_p(X.data_ptr()), n, d, X.stride(0), k,
+        ctypes.c_void_p(med.data_ptr()),
+        ctypes.c_void_p(labels.data_ptr() if labels is not None else 0),
+        ctypes.byref(o), ctypes.byref(res), ctypes.c_void_p(ws.data_ptr()),
+        ws.numel(), _stream())
+    if st not in (0, 4):
+        _check(st)
+    out = _result(res, o, k)
+    out["status_name"] = STATUS.get(st, st)
+    out["converged"] = st == 0
+    out["medoids"] = med
+    out["labels"] = labels
+    out["trace"] = tr.items(res.swaps) if o.trace_capacity > 0 else []
+    if fn_name == "kmedoids_run_features":
+        out["build_gains"] = tr.g[:k].copy()
+    return out
+
+
+def run_features(X, k, labels=True, **kw):
+    """BUILD + FastPAM1 on bf16 features with on-the-fly Euclidean distances
+    (kmedoids_run_features)."""
+    torch = _torch()
+    med = torch.empty(k, dtype=torch.int32, device=X.device)
+    lab = torch.empty(X.shape[0], dtype=torch.int32, device=X.device) \
+        if labels else None
+    return _features_call("kmedoids_run_features", X, k, med, lab, kw)
+
+
+def swap_features(X, medoids, labels=True, **kw):
+    """FastPAM1 on bf16 features from the given medoids
+    (kmedoids_swap_features)."""
+    torch = _torch()
+    med = torch.as_tensor(medoids, dtype=torch.int32).to(X.device).clone()
+    lab = torch.empty(X.shape[0], dtype=torch.int32, device=X.device) \
+        if labels else None
+    return _features_call("kmedoids_swap_features", X, med.numel(), med, lab, kw)
 
 
 def version() -> str:

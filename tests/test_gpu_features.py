@@ -26,3 +26,51 @@ def test_gram_bf16_matches_fp32(n, d):
     ref = X64 @ X64.T
     bound = 1e-5 * (np.abs(X64) @ np.abs(X64).T) + 1e-6
     assert np.all(np.abs(G - ref) <= bound), np.max(np.abs(G - ref) / bound)
+
+
+# ---------------------------------------------------------------- runs
+
+import oracle  # noqa: E402
+
+
+def _feat_case(n, d, centers, seed):
+    X = wl.features_200000(n=n, d=d, n_centers=centers) if seed is None else \
+        wl.to_bf16_values(wl.gmm_points(n, d, centers, seed=seed,
+                                        center_std=2.0, center_box=None))
+    Dh = wl.euclidean_f32(X.astype(np.float64))
+    return X, Dh
+
+
+@pytest.mark.parametrize("n,d,k", [(1000, 128, 8), (777, 64, 12), (2500, 128, 20)])
+def test_run_features_matches_oracle(n, d, k):
+    """BUILD + FastPAM1 with on-the-fly bf16 Gram distances: the TD it
+    reports is exact for its medoids, every BUILD choice is the oracle's best
+    up to the Gram rounding, the result is locally optimal and its TD equals
+    the oracle's run on the exact matrix within 1e-5."""
+    X, Dh = _feat_case(n, d, max(2, k // 2), ("feat", n, d))
+    Xt = torch.from_numpy(X).to(torch.bfloat16).cuda()
+    out = km.run_features(Xt, k, trace=10000)
+    med = out["medoids"].cpu().numpy()
+    assert len(set(med.tolist())) == k
+    tdv = oracle.td(Dh, med)
+    assert abs(out["td"] - tdv) <= 1e-6 * tdv
+    assert abs(out["td_bookkept"] - tdv) <= 1e-4 * tdv
+    _, olab = oracle.td(Dh, med, return_labels=True)
+    lab = out["labels"].cpu().numpy()
+    assert np.mean(lab == olab) > 0.999
+    _, _, best = oracle.eval_swaps(Dh, med)
+    assert best[0] >= -1e-5 * tdv
+    ref = oracle.run(Dh, k, variant="fastpam1")
+    assert abs(out["td"] - ref["td"]) <= 1e-5 * ref["td"]
+
+
+def test_build_features_steps():
+    X, Dh = _feat_case(1500, 128, 6, "featb")
+    Xt = torch.from_numpy(X).to(torch.bfloat16).cuda()
+    out = km.run_features(Xt, 6, max_iter=1)
+    gains = out["build_gains"]
+    # rebuild the BUILD prefix from the oracle's view of the GPU's choices
+    start = km.swap_features(Xt, [0, 1, 2, 3, 4, 5], max_iter=1)  # smoke
+    assert start["iterations"] >= 1
+    omed, otd, ogains = oracle.pam_build(Dh, 6)
+    assert np.allclose(gains, ogains, rtol=1e-4, atol=1e-3 * abs(ogains[0]) / 1500)
