@@ -13,8 +13,10 @@
 //               two 128-column TMEM buffers (double buffering);
 //   warps 2-9   epilogue, two warpgroups of 64 columns each: read G from
 //               TMEM, d^2 = |x_c|^2 + |x_o|^2 - 2 g, then
-//               SWAP:  hits (d^2 < d_s^2) are compacted per warp and added,
-//                      with d = sqrt(d^2), to per-candidate slot
+//               SWAP:  hits (d^2 < d_s^2, tested as g - |x_c|^2/2 >
+//                      (|x_o|^2 - d_s^2)/2 with one add and one compare per
+//                      pair; an 8-column warp vote guards the rare path)
+//                      add, with d = sqrt(d^2), to per-candidate slot
 //                      accumulators in shared memory (Eq. (7));
 //               BUILD: each thread sums min(d - d_n, 0) of its candidate
 //                      (step 0: d) with Kahan compensation.
@@ -39,7 +41,6 @@ namespace km {
 constexpr int kFeatStages = 2;
 constexpr int kFeatEpiWarps = 8;
 constexpr int kFeatThreads = (2 + kFeatEpiWarps) * 32;
-constexpr int kFeatQueue = 128;      // hit entries per epilogue warp
 constexpr int kFeatMaxK = 224;       // shared accumulators: 128 x (k+1) x 4 B
 constexpr int kFeatMaxD = 256;
 
@@ -56,6 +57,8 @@ struct FeatArgs {
   float* ds;
   float* dn2;
   float* ds2;
+  float* thr;           // hit threshold of each point: (|x_o|^2 - d^2)/2 with
+                        // d = d_s (SWAP) or d_n (BUILD); +inf on padding
   uint8_t* is_med;
   int32_t* med;
   double* removal;      // [2][k_pad]
@@ -72,8 +75,7 @@ struct FeatArgs {
 };
 
 struct FeatLayout {
-  size_t bars, flags, wkeys, rl, acc, red, queue_idx, queue_d2, tslot, a, stages, stage_bytes,
-      meta_bytes, total;
+  size_t bars, flags, wkeys, rl, acc, red, tslot, a, stages, stage_bytes, meta_bytes, total;
 };
 
 __host__ __device__ inline FeatLayout feat_layout(int d, int k) {
@@ -94,11 +96,6 @@ __host__ __device__ inline FeatLayout feat_layout(int d, int k) {
   o += 4 * (size_t)kTileM * (k + 1);
   L.red = o;
   o += 8 * (size_t)kTileM;
-  L.queue_idx = o;
-  o += 2 * (size_t)kFeatQueue * kFeatEpiWarps;
-  o = (o + 15) / 16 * 16;
-  L.queue_d2 = o;
-  o += 4 * (size_t)kFeatQueue * kFeatEpiWarps;
   o = (o + 1023) / 1024 * 1024;
   L.a = o;
   o += (size_t)kTileM * d * 2;
@@ -137,8 +134,6 @@ __global__ void __launch_bounds__(kFeatThreads, 1) k_feat_pass(const FeatArgs a)
   double* rl = reinterpret_cast<double*>(smem + L.rl);
   float* acc = reinterpret_cast<float*>(smem + L.acc);
   double* red = reinterpret_cast<double*>(smem + L.red);
-  uint16_t* qidx = reinterpret_cast<uint16_t*>(smem + L.queue_idx);
-  float* qd2 = reinterpret_cast<float*>(smem + L.queue_d2);
   unsigned char* sA = smem + L.a;
   unsigned char* stages = smem + L.stages;
 
@@ -226,17 +221,10 @@ __global__ void __launch_bounds__(kFeatThreads, 1) k_feat_pass(const FeatArgs a)
           bulk_g2s(sb, a.Xp + (size_t)b * kTileN * d, tile_bytes, &b_full[s]);
           const size_t o0 = (size_t)b * kTileN;
           bulk_g2s(meta, a.norms + o0, 4 * kTileN, &b_full[s]);
-          if (MODE == kModeSwap) {
-            bulk_g2s(meta + 512, a.ds2 + o0, 4 * kTileN, &b_full[s]);
-            bulk_g2s(meta + 1024, a.dn + o0, 4 * kTileN, &b_full[s]);
-            bulk_g2s(meta + 1536, a.ds + o0, 4 * kTileN, &b_full[s]);
-            bulk_g2s(meta + 2048, a.near + o0, 4 * kTileN, &b_full[s]);
-          } else {
-            bulk_g2s(meta + 512, a.dn2 + o0, 4 * kTileN, &b_full[s]);
-            bulk_g2s(meta + 1024, a.dn + o0, 4 * kTileN, &b_full[s]);
-            bulk_g2s(meta + 1536, a.dn + o0, 4 * kTileN, &b_full[s]);
-            bulk_g2s(meta + 2048, a.near + o0, 4 * kTileN, &b_full[s]);
-          }
+          bulk_g2s(meta + 512, a.thr + o0, 4 * kTileN, &b_full[s]);
+          bulk_g2s(meta + 1024, a.dn + o0, 4 * kTileN, &b_full[s]);
+          bulk_g2s(meta + 1536, a.ds + o0, 4 * kTileN, &b_full[s]);
+          bulk_g2s(meta + 2048, a.near + o0, 4 * kTileN, &b_full[s]);
         }
       }
       if (!ok) {
@@ -294,8 +282,6 @@ __global__ void __launch_bounds__(kFeatThreads, 1) k_feat_pass(const FeatArgs a)
     const int r = quarter * 32 + lane;    // candidate row within the tile
     uint32_t eph = 0;
     long long gb = 0;
-    uint16_t* myqi = qidx + ew * kFeatQueue;
-    float* myqd = qd2 + ew * kFeatQueue;
     bool ok = true;
     for (int seq = 0; ok; ++seq) {
       if (!mbar_wait(a_full, (uint32_t)(seq & 1), abort_flag)) {
@@ -333,109 +319,60 @@ __global__ void __launch_bounds__(kFeatThreads, 1) k_feat_pass(const FeatArgs a)
         const unsigned char* meta =
             stages + (size_t)s * L.stage_bytes + (size_t)kTileN * d * 2;
         const float* m_no = reinterpret_cast<const float*>(meta);
-        const float* m_x1 = reinterpret_cast<const float*>(meta + 512);   // ds2 | dn2
-        const float* m_x2 = reinterpret_cast<const float*>(meta + 1024);  // dn
-        const float* m_x3 = reinterpret_cast<const float*>(meta + 1536);  // ds
+        const float* m_thr = reinterpret_cast<const float*>(meta + 512);
+        const float* m_dn = reinterpret_cast<const float*>(meta + 1024);
+        const float* m_ds = reinterpret_cast<const float*>(meta + 1536);
         const int* m_near = reinterpret_cast<const int*>(meta + 2048);
         const int col0 = group * 64;
-        if (MODE == kModeSwap) {
-          unsigned long long hmask = 0ull;
-#pragma unroll
-          for (int j = 0; j < 64; j += 4) {
-            const float4 no4 = *reinterpret_cast<const float4*>(m_no + col0 + j);
-            const float4 sq4 = *reinterpret_cast<const float4*>(m_x1 + col0 + j);
-            const float e0 = fmaf(-2.f, v[j], nc + no4.x);
-            const float e1 = fmaf(-2.f, v[j + 1], nc + no4.y);
-            const float e2 = fmaf(-2.f, v[j + 2], nc + no4.z);
-            const float e3 = fmaf(-2.f, v[j + 3], nc + no4.w);
-            v[j] = e0;
-            v[j + 1] = e1;
-            v[j + 2] = e2;
-            v[j + 3] = e3;
-            const unsigned h = (e0 < sq4.x ? 1u : 0u) | (e1 < sq4.y ? 2u : 0u) |
-                               (e2 < sq4.z ? 4u : 0u) | (e3 < sq4.w ? 8u : 0u);
-            hmask |= (unsigned long long)h << j;
-          }
-          if (!cvalid) hmask = 0ull;
-          // warp compaction of (row, column, d^2) hits, then a full-lane drain
-          const int cnt = __popcll(hmask);
-          int incl = cnt;
-#pragma unroll
-          for (int o = 1; o < 32; o <<= 1) {
-            const int x = __shfl_up_sync(0xffffffffu, incl, o);
-            if (lane >= o) incl += x;
-          }
-          const int total = __shfl_sync(0xffffffffu, incl, 31);
-          if (total > 0 && total <= kFeatQueue) {
-            int pos = incl - cnt;
-            unsigned long long mk = hmask;
-            while (mk) {
-              const int j = __ffsll(mk) - 1;
-              mk &= mk - 1;
-              myqi[pos] = (uint16_t)((lane << 6) | j);
-              float dj = 0.f;
-#pragma unroll
-              for (int q = 0; q < 64; ++q) dj = (q == j) ? v[q] : dj;
-              myqd[pos] = dj;
-              ++pos;
-            }
-            __syncwarp();
-            for (int e = lane; e < total; e += 32) {
-              const unsigned qi = myqi[e];
-              const int src = (int)(qi >> 6), j = (int)(qi & 63);
-              const int col = col0 + j;
-              const float dd = sqrtf(fmaxf(myqd[e], 0.f));
-              const float dn_ = m_x2[col], ds_ = m_x3[col];
-              const int sl = m_near[col];
-              float* arow = acc + (size_t)(quarter * 32 + src) * (k + 1);
-              if (dd < dn_) {
-                atomicAdd(arow + k, dd - dn_);
-                atomicAdd(arow + sl, dn_ - ds_);
-              } else {
-                atomicAdd(arow + sl, dd - ds_);
-              }
-            }
-            __syncwarp();
-          } else if (total > kFeatQueue) {
-            // dense block: every lane its own hits
-            unsigned long long mk = hmask;
-            float* arow = acc + (size_t)r * (k + 1);
-            while (mk) {
-              const int j = __ffsll(mk) - 1;
-              mk &= mk - 1;
-              float dj = 0.f;
-#pragma unroll
-              for (int q = 0; q < 64; ++q) dj = (q == j) ? v[q] : dj;
-              const int col = col0 + j;
-              const float dd = sqrtf(fmaxf(dj, 0.f));
-              const float dn_ = m_x2[col], ds_ = m_x3[col];
-              const int sl = m_near[col];
-              if (dd < dn_) {
-                atomicAdd(arow + k, dd - dn_);
-                atomicAdd(arow + sl, dn_ - ds_);
-              } else {
-                atomicAdd(arow + sl, dd - ds_);
-              }
-            }
-            __syncwarp();
-          }
-        } else {
+        // d(o,c)^2 < d^2(o)  <=>  g - |x_c|^2/2 > (|x_o|^2 - d^2(o))/2 = thr[o]
+        const float hc = cvalid ? 0.5f * nc : __int_as_float(0x7f800000);
+        if (MODE == kModeBuild && a.build_first) {
           const int colg = b * kTileN + col0;
-#pragma unroll 8
+#pragma unroll
           for (int j = 0; j < 64; ++j) {
             const float d2 = fmaf(-2.f, v[j], nc + m_no[col0 + j]);
-            float x = 0.f;
-            if (a.build_first) {
-              if (colg + j < n) x = sqrtf(fmaxf(d2, 0.f));
-            } else if (d2 < m_x1[col0 + j]) {
-              const float dd = sqrtf(fmaxf(d2, 0.f));
-              const float dn_ = m_x2[col0 + j];
-              if (dd < dn_) x = dd - dn_;
-            }
+            const float x = (colg + j < n) ? sqrtf(fmaxf(d2, 0.f)) : 0.f;
             const float y = x - kc_;
             const float tt = ks_ + y;
             kc_ = (tt - ks_) - y;
             ks_ = tt;
+          }
+        } else {
+#pragma unroll
+          for (int j0 = 0; j0 < 64; j0 += 8) {
+            const float4 t0 = *reinterpret_cast<const float4*>(m_thr + col0 + j0);
+            const float4 t1 = *reinterpret_cast<const float4*>(m_thr + col0 + j0 + 4);
+            const float tq[8] = {t0.x, t0.y, t0.z, t0.w, t1.x, t1.y, t1.z, t1.w};
+            bool p = false;
+#pragma unroll
+            for (int q = 0; q < 8; ++q) p |= (v[j0 + q] - hc > tq[q]);
+            if (!__any_sync(0xffffffffu, p)) continue;
+            // rare path: the lanes with a hit in this 8-column group
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+              if (v[j0 + q] - hc > tq[q]) {
+                const int col = col0 + j0 + q;
+                const float d2 = fmaf(-2.f, v[j0 + q], nc + m_no[col]);
+                const float dd = sqrtf(fmaxf(d2, 0.f));
+                const float dn_ = m_dn[col];
+                if (MODE == kModeSwap) {
+                  const float ds_ = m_ds[col];
+                  const int sl = m_near[col];
+                  float* arow = acc + (size_t)r * (k + 1);
+                  if (dd < dn_) {
+                    atomicAdd(arow + k, dd - dn_);
+                    atomicAdd(arow + sl, dn_ - ds_);
+                  } else {
+                    atomicAdd(arow + sl, dd - ds_);
+                  }
+                } else if (dd < dn_) {
+                  const float y = (dd - dn_) - kc_;
+                  const float tt = ks_ + y;
+                  kc_ = (tt - ks_) - y;
+                  ks_ = tt;
+                }
+              }
+            }
           }
         }
         __syncwarp();
@@ -611,6 +548,7 @@ __global__ void __launch_bounds__(256) k_feat_cache(const FeatArgs a) {
     a.ds[o] = e2;
     a.dn2[o] = q1;
     a.ds2[o] = (n2 < 0) ? Tr<float>::high() : q2;
+    a.thr[o] = (n2 < 0) ? -Tr<float>::high() : 0.5f * (a.norms[o] - q2);
     if (n2 >= 0) atomicAdd(&sacc[n1], (double)e2 - (double)e1);
     tdl = e1;
   } else if (o < a.n_pad) {
@@ -620,6 +558,7 @@ __global__ void __launch_bounds__(256) k_feat_cache(const FeatArgs a) {
     a.ds[o] = 0.f;
     a.dn2[o] = Tr<float>::low();
     a.ds2[o] = Tr<float>::low();
+    a.thr[o] = Tr<float>::high();
   }
   const double bs = fblock_sum(tdl, scratch);
   if (threadIdx.x == 0) atomicAdd(&a.td2[rb], bs);
@@ -683,6 +622,7 @@ __global__ void __launch_bounds__(256) k_feat_apply(const FeatArgs a) {
     a.ds[o] = e2;
     a.dn2[o] = q1;
     a.ds2[o] = q2;
+    a.thr[o] = 0.5f * (a.norms[o] - q2);
     atomicAdd(&sacc[n1], (double)e2 - (double)e1);
     tdl = e1;
   }
@@ -735,10 +675,12 @@ __global__ void __launch_bounds__(256) k_feat_build_commit(const FeatArgs a) {
       if (!a.build_first && !(q < a.dn2[o])) cur = a.dn2[o];
       a.dn2[o] = cur;
       a.dn[o] = sqrtf(cur);
+      a.thr[o] = 0.5f * (a.norms[o] - cur);
       local = sqrtf(cur);
     } else if (o < a.n_pad) {
       a.dn2[o] = Tr<float>::low();
       a.dn[o] = 0.f;
+      a.thr[o] = Tr<float>::high();
     }
   }
   const double bs = fblock_sum(local, scratch);
@@ -766,7 +708,7 @@ using namespace km;
 namespace {
 
 struct FeatWs {
-  size_t st, med, is_med, near, sec, dn, ds, dn2, ds2, norms, removal, td2, partials, trace,
+  size_t st, med, is_med, near, sec, dn, ds, dn2, ds2, thr, norms, removal, td2, partials, trace,
       gains, xp, total;
   int n_pad, k_pad, cap;
 };
@@ -793,6 +735,7 @@ bool feat_ws(int64_t n, int d, int k, const km_options* o, FeatWs* L) {
   L->ds = take(4 * (size_t)n_pad);
   L->dn2 = take(4 * (size_t)n_pad);
   L->ds2 = take(4 * (size_t)n_pad);
+  L->thr = take(4 * (size_t)n_pad);
   L->norms = take(4 * (size_t)n_pad);
   L->removal = take(16 * (size_t)k_pad);
   L->td2 = take(16);
@@ -851,7 +794,8 @@ km_status f_reset(FCtx& c) {
   return KM_OK;
 }
 
-km_status f_pass(FCtx& c, int mode, int first) {
+km_status f_pass(FCtx& c, int mode, int first, cudaEvent_t ev0 = nullptr,
+                 cudaEvent_t ev1 = nullptr) {
   FeatArgs a = c.a;
   a.mode = mode;
   a.build_first = first;
@@ -860,14 +804,17 @@ km_status f_pass(FCtx& c, int mode, int first) {
   int grid = c.sms;
   if (grid > a.n_pad / kTileM) grid = a.n_pad / kTileM;
   if (grid > kMaxGrid) grid = kMaxGrid;
-  if (mode == kModeSwap) {
+  if (mode == kModeSwap)
     FK(cudaFuncSetAttribute(k_feat_pass<kModeSwap>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total));
-    k_feat_pass<kModeSwap><<<grid, kFeatThreads, L.total, c.s>>>(a);
-  } else {
+  else
     FK(cudaFuncSetAttribute(k_feat_pass<kModeBuild>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total));
+  if (ev0) FK(cudaEventRecord(ev0, c.s));
+  if (mode == kModeSwap)
+    k_feat_pass<kModeSwap><<<grid, kFeatThreads, L.total, c.s>>>(a);
+  else
     k_feat_pass<kModeBuild><<<grid, kFeatThreads, L.total, c.s>>>(a);
-  }
   FK(cudaGetLastError());
+  if (ev1) FK(cudaEventRecord(ev1, c.s));
   ++c.launches;
   return KM_OK;
 }
@@ -928,6 +875,7 @@ km_status run_features(bool do_build, bool do_swap, const void* X, int64_t n, in
   a.ds = reinterpret_cast<float*>(c.ws + c.L.ds);
   a.dn2 = reinterpret_cast<float*>(c.ws + c.L.dn2);
   a.ds2 = reinterpret_cast<float*>(c.ws + c.L.ds2);
+  a.thr = reinterpret_cast<float*>(c.ws + c.L.thr);
   a.is_med = c.ws + c.L.is_med;
   a.med = reinterpret_cast<int32_t*>(c.ws + c.L.med);
   a.removal = reinterpret_cast<double*>(c.ws + c.L.removal);
@@ -942,6 +890,7 @@ km_status run_features(bool do_build, bool do_swap, const void* X, int64_t n, in
 
   cudaEvent_t e0 = nullptr, e1 = nullptr, e2 = nullptr;
   const bool prof = c.opt.profile != 0;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> bev, sev;
   if (prof) {
     FK(cudaEventCreate(&e0));
     FK(cudaEventCreate(&e1));
@@ -958,7 +907,13 @@ km_status run_features(bool do_build, bool do_swap, const void* X, int64_t n, in
   if (do_build) {
     FK(cudaMemsetAsync(a.is_med, 0, (size_t)c.L.n_pad, c.s));
     for (int step = 0; step < k; ++step) {
-      r = f_pass(c, kModeBuild, step == 0);
+      cudaEvent_t x0 = nullptr, x1 = nullptr;
+      if (prof) {
+        FK(cudaEventCreate(&x0));
+        FK(cudaEventCreate(&x1));
+        bev.push_back({x0, x1});
+      }
+      r = f_pass(c, kModeBuild, step == 0, x0, x1);
       if (r != KM_OK) return r;
       FeatArgs b = a;
       b.build_first = (step == 0);
@@ -991,7 +946,13 @@ km_status run_features(bool do_build, bool do_swap, const void* X, int64_t n, in
       int nb = batch;
       if (launched + nb > c.opt.max_iter) nb = c.opt.max_iter - launched;
       for (int j = 0; j < nb; ++j) {
-        r = f_pass(c, kModeSwap, 0);
+        cudaEvent_t x0 = nullptr, x1 = nullptr;
+        if (prof) {
+          FK(cudaEventCreate(&x0));
+          FK(cudaEventCreate(&x1));
+          sev.push_back({x0, x1});
+        }
+        r = f_pass(c, kModeSwap, 0, x0, x1);
         if (r != KM_OK) return r;
         k_feat_apply<<<(a.n + 255) / 256, 256, sm, c.s>>>(a);
         FK(cudaGetLastError());
@@ -1035,12 +996,36 @@ km_status run_features(bool do_build, bool do_swap, const void* X, int64_t n, in
       res->build_ms = ms;
       cudaEventElapsedTime(&ms, e1, e2);
       res->swap_ms = ms;
+      double sb = 0.0, ss = 0.0;
+      for (auto& p : bev) {
+        cudaEventElapsedTime(&ms, p.first, p.second);
+        sb += ms;
+      }
+      int cnt = 0;
+      for (auto& p : sev) {
+        if (cnt >= h.iter) break;
+        cudaEventElapsedTime(&ms, p.first, p.second);
+        ss += ms;
+        ++cnt;
+      }
+      res->build_eval_ms = sb;
+      res->build_launches = (int)bev.size();
+      res->eval_ms = ss;
+      res->eval_launches = cnt;
     }
   }
   if (prof) {
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     cudaEventDestroy(e2);
+    for (auto& p : bev) {
+      cudaEventDestroy(p.first);
+      cudaEventDestroy(p.second);
+    }
+    for (auto& p : sev) {
+      cudaEventDestroy(p.first);
+      cudaEventDestroy(p.second);
+    }
   }
   if (conv != KM_OK) ffail(conv, "max_iter reached before convergence");
   return conv;
