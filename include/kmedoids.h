@@ -121,6 +121,8 @@ typedef struct km_result {
   int32_t build_launches; /* BUILD evaluation kernel launches */
   double build_eval_ms;   /* sum over the BUILD evaluation kernel launches */
   int64_t kernel_launches; /* kernels this call launched (all phases) */
+  int32_t best_sample;     /* kmedoids_clara: index of the winning sample */
+  int32_t reserved1;
 } km_result;
 
 /* Fill *o with the defaults (FastPAM1, tol 0, automatic tiles). */
@@ -223,6 +225,63 @@ km_status kmedoids_swap_features(const void *X_bf16, int64_t n, int32_t d,
                                  int32_t *medoids_inout, int32_t *labels_out,
                                  const km_options *opts, km_result *res,
                                  void *ws, size_t ws_bytes, void *stream);
+
+/* ---- Batched form: many independent PAM instances in one persistent launch.
+ * Instance i's matrix lives in a float32 arena (DEVICE) at element offset
+ * inst[i].offset: n rows of ld elements (ld % 4 == 0, offset % 4 == 0,
+ * arena 16-byte aligned), symmetric with a zero diagonal.  Each instance
+ * runs BUILD (Alg. 1) then FastPAM1 SWAP (Alg. 3) to convergence on one
+ * CTA, instances taken largest first; limits n <= 4096, k <= 128.  Results
+ * per instance: k medoids at medoids_out[inst[i].medoid_offset ...] and a
+ * km_batch_result (exact TD of the result in FP64, passes, swaps, status). */
+typedef struct km_instance {
+  int64_t offset;        /* first element of the instance's matrix */
+  int32_t n, ld, k;
+  int32_t medoid_offset; /* where its k medoids are written */
+} km_instance;
+
+typedef struct km_batch_result {
+  double td;
+  int32_t iterations, swaps, status, pad;
+} km_batch_result;
+
+size_t kmedoids_batched_workspace_size(int32_t count);
+
+/* Fill the arena with Euclidean matrices of float32 points (FP64
+ * differences, one rounding to float32): instance i uses the n_i points
+ * starting at row point_offsets[i] (DEVICE int64) of points (DEVICE,
+ * dim floats per point). */
+km_status kmedoids_batched_distances(const float *points, int32_t dim,
+                                     const int64_t *point_offsets,
+                                     const km_instance *inst, int32_t count,
+                                     float *arena, void *stream);
+
+/* inst (DEVICE, count entries), medoids_out / results (DEVICE).  opts:
+ * max_iter, tol; tune 1 = 8 warps per CTA, otherwise 16. */
+km_status kmedoids_run_batched(const float *arena, const km_instance *inst,
+                               int32_t count, int32_t *medoids_out,
+                               km_batch_result *results,
+                               const km_options *opts, void *ws,
+                               size_t ws_bytes, void *stream);
+
+/* ---- CLARA (Sec. 2.2; FastCLARA, Sec. 3.3).  X: n points of d float32
+ * features (DEVICE, row-major).  sample_idx (DEVICE, samples x
+ * sample_size int32): the caller's subsamples (the paper suggests
+ * sample_size = 80 + 4k).  Each sample's Euclidean matrix is built in FP64
+ * and rounded to float32, solved by BUILD + FastPAM1 (batched form), and
+ * every point is assigned to the sample's medoids (FP32 differences, FP64
+ * TD).  The sample with the least TD wins (lowest index on ties):
+ * medoids_out (DEVICE, k point indices), labels_out (DEVICE, n, may be
+ * NULL), sample_td_host (HOST, samples, may be NULL); res->td = best TD,
+ * res->best_sample its index. */
+size_t kmedoids_clara_workspace_size(int32_t k, int32_t samples,
+                                     int32_t sample_size);
+km_status kmedoids_clara(const float *X, int64_t n, int32_t d, int32_t k,
+                         int32_t samples, int32_t sample_size,
+                         const int32_t *sample_idx, int32_t *medoids_out,
+                         int32_t *labels_out, double *sample_td_host,
+                         km_result *res, void *ws, size_t ws_bytes,
+                         void *stream);
 
 /* kmedoids_eval_swaps without a caller-provided workspace, for callers that
  * cannot allocate device memory when they evaluate swaps (a frozen memory

@@ -18,6 +18,8 @@ k-Medoids Clustering" (arXiv 2008.05171):
 * ``swap_delta``    -- Delta of one (slot, candidate) swap by Eq. (5).
 * ``swap``          -- SWAP to convergence: PAM brute force / PAM cached /
                        FastPAM1 / FastPAM2 / FasterPAM (Alg. 4).
+* ``clara``         -- CLARA (Sec. 2.2, FastCLARA of Sec. 3.3) on given
+                       samples; ``euclid_f32`` the FP64 -> float32 matrix.
 
 Parity unpinned: FastPAM2's additional swaps (the paper describes FastPAM2
 only in words, Sec. 3.2) beyond the invariants the tests check.
@@ -80,6 +82,11 @@ def _lib():
                                         f64, f64, P, P, i32, P, P, P]
             lib.oracle_build_gains.restype = None
             lib.oracle_build_gains.argtypes = [P, i32, i64, i64, P, i32, P]
+            lib.oracle_euclid_f32.restype = None
+            lib.oracle_euclid_f32.argtypes = [P, i64, i32, P, i64, P]
+            lib.oracle_clara.restype = i32
+            lib.oracle_clara.argtypes = [P, i64, i32, i32, i32, i32, P, P, P,
+                                         P, P]
             lib.oracle_num_threads.restype = i32
             lib.oracle_set_threads.argtypes = [i32]
             _LIB = lib
@@ -215,6 +222,36 @@ def swap(D, medoids, variant="fastpam1", max_iter=1000, tol=0.0,
         "trace": list(zip(tr_d[:ns].tolist(), tr_i[:ns].tolist(),
                           tr_c[:ns].tolist())),
     }
+
+
+def euclid_f32(X, idx=None, ld=None):
+    """Euclidean matrix of float32 points computed in FP64, rounded once to
+    float32 (rows padded to ld with zeros)."""
+    X = np.ascontiguousarray(X, np.float32)
+    m = X.shape[0] if idx is None else len(idx)
+    ld = (m + 3) // 4 * 4 if ld is None else ld
+    D = np.empty((m, ld), np.float32)
+    ix = None if idx is None else np.ascontiguousarray(idx, np.int64)
+    _lib().oracle_euclid_f32(_p(X), m, X.shape[1],
+                             _p(ix) if ix is not None else None, ld, _p(D))
+    return D
+
+
+def clara(X, k, sample_idx):
+    """CLARA (Sec. 2.2 / 3.3): PAM (BUILD + FastPAM1) on each given sample,
+    full-data TD of each, best sample kept.  Returns (medoids, labels,
+    sample_tds, best_sample)."""
+    X = np.ascontiguousarray(X, np.float32)
+    S = np.ascontiguousarray(sample_idx, np.int32)
+    samples, s = S.shape
+    n, d = X.shape
+    med = np.empty(k, np.int32)
+    lab = np.empty(n, np.int32)
+    tds = np.empty(samples, np.float64)
+    best = np.zeros(1, np.int32)
+    _lib().oracle_clara(_p(X), n, d, k, samples, s, _p(S), _p(med), _p(lab),
+                        _p(tds), _p(best))
+    return med, lab, tds, int(best[0])
 
 
 def run(D, k, variant="fastpam1", n=None, **kw):

@@ -665,3 +665,110 @@ int oracle_swap(const void *D, int dtype, int64_t n, int64_t ld, int k,
   td[1] = oracle_td(D, dtype, n, ld, med, k, NULL);
   return 0;
 }
+
+/* ------------------------------------------------------------------------
+ * Euclidean dissimilarity matrix of m float32 points in FP64, rounded once
+ * to float32: D[i*ld + j] = sqrt(sum_t (x_it - x_jt)^2) (zero diagonal,
+ * symmetric by construction).  Used for CLARA samples and batch instances.
+ * ---------------------------------------------------------------------- */
+void oracle_euclid_f32(const float *X, int64_t m, int d, const int64_t *idx,
+                       int64_t ld, float *D) {
+  for (int64_t i = 0; i < m; i++) {
+    const float *xi = X + (idx ? idx[i] : i) * (int64_t)d;
+    for (int64_t j = 0; j < m; j++) {
+      const float *xj = X + (idx ? idx[j] : j) * (int64_t)d;
+      double s = 0.0;
+      for (int t = 0; t < d; t++) {
+        double df = (double)xi[t] - (double)xj[t];
+        s += df * df;
+      }
+      D[i * ld + j] = (float)sqrt(s);
+    }
+    for (int64_t j = m; j < ld; j++) D[i * ld + j] = 0.0f;
+  }
+}
+
+/* ------------------------------------------------------------------------
+ * CLARA (Sec. 2.2 "Variants and Extensions of PAM", Sec. 3.3 FastCLARA):
+ * for each of `samples` subsamples of s points (indices given, drawn by the
+ * caller), run PAM -- BUILD then FastPAM1 -- on the subsample's matrix,
+ * assign every point of the full data set to its nearest medoid, and keep
+ * the medoids with the least TD on the full data (lowest sample index on
+ * ties).  Distances are Euclidean in FP64 from float32 coordinates.
+ * Outputs: medoids (global indices, k), labels (n, may be NULL), the TD of
+ * every sample (samples) and the index of the best sample.
+ * ---------------------------------------------------------------------- */
+int oracle_clara(const float *X, int64_t n, int d, int k, int samples, int s,
+                 const int32_t *sample_idx, int32_t *medoids, int32_t *labels,
+                 double *sample_td, int32_t *best_sample) {
+  int64_t ld = (s + 3) / 4 * 4;
+  float *D = (float *)malloc(sizeof(float) * (size_t)s * (size_t)ld);
+  int64_t *idx = (int64_t *)malloc(sizeof(int64_t) * (size_t)s);
+  int32_t *med = (int32_t *)malloc(sizeof(int32_t) * (size_t)k);
+  int32_t *bestmed = (int32_t *)malloc(sizeof(int32_t) * (size_t)k);
+  double best_td = OR_INF;
+  int best = -1;
+  for (int q = 0; q < samples; q++) {
+    for (int i = 0; i < s; i++) idx[i] = sample_idx[(int64_t)q * s + i];
+    oracle_euclid_f32(X, s, d, idx, ld, D);
+    double tdb;
+    oracle_build(D, 1, s, ld, k, med, &tdb, NULL);
+    int64_t stats[4];
+    double tds[2];
+    oracle_swap(D, 1, s, ld, k, med, 2, 100 * k + 100, 0.0, 0.0, stats, tds, 0,
+                NULL, NULL, NULL);
+    /* full-data TD of this sample's medoids (global indices) */
+    double td = 0.0;
+#pragma omp parallel for reduction(+ : td) schedule(static)
+    for (int64_t o = 0; o < n; o++) {
+      double b = OR_INF;
+      for (int j = 0; j < k; j++) {
+        const float *xm = X + (int64_t)idx[med[j]] * d;
+        const float *xo = X + o * (int64_t)d;
+        double sq = 0.0;
+        for (int t = 0; t < d; t++) {
+          double df = (double)xo[t] - (double)xm[t];
+          sq += df * df;
+        }
+        double v = sqrt(sq);
+        if (v < b) b = v;
+      }
+      td += b;
+    }
+    if (sample_td) sample_td[q] = td;
+    if (td < best_td) {
+      best_td = td;
+      best = q;
+      for (int j = 0; j < k; j++) bestmed[j] = (int32_t)idx[med[j]];
+    }
+  }
+  for (int j = 0; j < k; j++) medoids[j] = bestmed[j];
+  if (labels) {
+#pragma omp parallel for schedule(static)
+    for (int64_t o = 0; o < n; o++) {
+      double b = OR_INF;
+      int lab = -1;
+      for (int j = 0; j < k; j++) {
+        const float *xm = X + (int64_t)bestmed[j] * d;
+        const float *xo = X + o * (int64_t)d;
+        double sq = 0.0;
+        for (int t = 0; t < d; t++) {
+          double df = (double)xo[t] - (double)xm[t];
+          sq += df * df;
+        }
+        double v = sqrt(sq);
+        if (v < b) {
+          b = v;
+          lab = j;
+        }
+      }
+      labels[o] = lab;
+    }
+  }
+  if (best_sample) *best_sample = best;
+  free(D);
+  free(idx);
+  free(med);
+  free(bestmed);
+  return 0;
+}

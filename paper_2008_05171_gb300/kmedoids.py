@@ -25,7 +25,9 @@ EXPORTS = ["km_default_options", "kmedoids_workspace_size", "kmedoids_build",
            "kmedoids_cache", "kmedoids_last_error", "kmedoids_version",
            "kmedoids_eval_swaps_static", "kmedoids_gram_bf16",
            "kmedoids_features_workspace_size", "kmedoids_run_features",
-           "kmedoids_swap_features"]
+           "kmedoids_swap_features", "kmedoids_batched_workspace_size",
+           "kmedoids_batched_distances", "kmedoids_run_batched",
+           "kmedoids_clara_workspace_size", "kmedoids_clara"]
 
 
 class KmError(RuntimeError):
@@ -58,7 +60,8 @@ class km_result(ctypes.Structure):
                 ("eval_launches", ctypes.c_int32),
                 ("build_launches", ctypes.c_int32),
                 ("build_eval_ms", ctypes.c_double),
-                ("kernel_launches", ctypes.c_int64)]
+                ("kernel_launches", ctypes.c_int64),
+                ("best_sample", ctypes.c_int32), ("reserved1", ctypes.c_int32)]
 
 
 _LOCK = threading.Lock()
@@ -108,6 +111,17 @@ def load(path: str = LIB_PATH):
             f = getattr(lib, name)
             f.argtypes = [P, i64, i32, i64, i32, P, P, opt_p, res_p, P, sz, P]
             f.restype = i32
+        lib.kmedoids_batched_workspace_size.argtypes = [i32]
+        lib.kmedoids_batched_workspace_size.restype = sz
+        lib.kmedoids_batched_distances.argtypes = [P, i32, P, P, i32, P, P]
+        lib.kmedoids_batched_distances.restype = i32
+        lib.kmedoids_run_batched.argtypes = [P, P, i32, P, P, opt_p, P, sz, P]
+        lib.kmedoids_run_batched.restype = i32
+        lib.kmedoids_clara_workspace_size.argtypes = [i32, i32, i32]
+        lib.kmedoids_clara_workspace_size.restype = sz
+        lib.kmedoids_clara.argtypes = [P, i64, i32, i32, i32, i32, P, P, P, P,
+                                       res_p, P, sz, P]
+        lib.kmedoids_clara.restype = i32
         lib.kmedoids_last_error.restype = ctypes.c_char_p
         lib.kmedoids_version.restype = ctypes.c_char_p
         _LIB = lib
@@ -406,6 +420,82 @@ def swap_features(X, medoids, labels=True, **kw):
     lab = torch.empty(X.shape[0], dtype=torch.int32, device=X.device) \
         if labels else None
     return _features_call("kmedoids_swap_features", X, med.numel(), med, lab, kw)
+
+
+INSTANCE_DTYPE = [("offset", "<i8"), ("n", "<i4"), ("ld", "<i4"), ("k", "<i4"),
+                  ("medoid_offset", "<i4")]
+BATCH_RESULT_DTYPE = [("td", "<f8"), ("iterations", "<i4"), ("swaps", "<i4"),
+                      ("status", "<i4"), ("pad", "<i4")]
+
+
+def batch_layout(sizes):
+    """Descriptor table for instances of (n, k): arena offsets with row
+    stride ld = roundup(n, 4), concatenated medoid offsets.  Returns
+    (numpy structured array, arena elements, total medoids)."""
+    import numpy as np
+    inst = np.zeros(len(sizes), dtype=INSTANCE_DTYPE)
+    off = 0
+    moff = 0
+    for i, (n, k) in enumerate(sizes):
+        ld = (n + 3) // 4 * 4
+        inst[i] = (off, n, ld, k, moff)
+        off += n * ld
+        moff += k
+    return inst, off, moff
+
+
+def batched_distances(points, point_offsets, inst_dev, arena):
+    """kmedoids_batched_distances: fill the arena from float32 points."""
+    torch = _torch()
+    lib = load()
+    offs = torch.as_tensor(point_offsets, dtype=torch.int64).to(points.device)
+    _check(lib.kmedoids_batched_distances(
+        ctypes.c_void_p(points.data_ptr()), points.shape[1],
+        ctypes.c_void_p(offs.data_ptr()), ctypes.c_void_p(inst_dev.data_ptr()),
+        inst_dev.numel() // 24, ctypes.c_void_p(arena.data_ptr()), _stream()))
+
+
+def run_batched(arena, inst_dev, total_medoids, **kw):
+    """kmedoids_run_batched.  inst_dev: uint8 CUDA tensor holding the
+    descriptor table.  Returns (medoids tensor, results uint8 tensor)."""
+    torch = _torch()
+    lib = load()
+    count = inst_dev.numel() // 24
+    med = torch.empty(total_medoids, dtype=torch.int32, device=arena.device)
+    res = torch.empty(count * 24, dtype=torch.uint8, device=arena.device)
+    ws = torch.empty(lib.kmedoids_batched_workspace_size(count),
+                     dtype=torch.uint8, device=arena.device)
+    o = options(**kw)
+    _check(lib.kmedoids_run_batched(
+        ctypes.c_void_p(arena.data_ptr()), ctypes.c_void_p(inst_dev.data_ptr()),
+        count, ctypes.c_void_p(med.data_ptr()), ctypes.c_void_p(res.data_ptr()),
+        ctypes.byref(o), ctypes.c_void_p(ws.data_ptr()), ws.numel(), _stream()))
+    return med, res
+
+
+def clara(X, k, sample_idx):
+    """kmedoids_clara: X float32 CUDA (n x d), sample_idx int32 CUDA
+    (samples x sample_size).  Returns a dict with medoids, labels,
+    sample_td (list), best_sample, td."""
+    import numpy as np
+    torch = _torch()
+    lib = load()
+    n, d = X.shape
+    samples, s = sample_idx.shape
+    ws = torch.empty(lib.kmedoids_clara_workspace_size(k, samples, s),
+                     dtype=torch.uint8, device=X.device)
+    med = torch.empty(k, dtype=torch.int32, device=X.device)
+    lab = torch.empty(n, dtype=torch.int32, device=X.device)
+    tds = np.zeros(samples, np.float64)
+    res = km_result()
+    _check(lib.kmedoids_clara(
+        ctypes.c_void_p(X.data_ptr()), n, d, k, samples, s,
+        ctypes.c_void_p(sample_idx.data_ptr()), ctypes.c_void_p(med.data_ptr()),
+        ctypes.c_void_p(lab.data_ptr()),
+        tds.ctypes.data_as(ctypes.c_void_p), ctypes.byref(res),
+        ctypes.c_void_p(ws.data_ptr()), ws.numel(), _stream()))
+    return {"medoids": med, "labels": lab, "sample_td": tds.tolist(),
+            "best_sample": res.best_sample, "td": res.td}
 
 
 def version() -> str:

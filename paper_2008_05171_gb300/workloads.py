@@ -188,5 +188,25 @@ def batched_instance_points(i: int, n: int, d: int = 8) -> np.ndarray:
     return uniform_points(n, d, seed=5, extra=i + 1)
 
 
+def batched_points(specs, d: int = 8, seed=5):
+    """float32 points of every instance, concatenated, and the first row of
+    each instance (uniform in [0,1)^d)."""
+    parts = [uniform_points(n, d, seed=seed, extra=i + 1).astype(np.float32)
+             for i, (n, _) in enumerate(specs)]
+    offs = np.cumsum([0] + [p.shape[0] for p in parts])[:-1].astype(np.int64)
+    return np.concatenate(parts, axis=0), offs
+
+
 def clara_points(n: int = 1_000_000, d: int = 32, n_centers: int = 100):
-    return gmm_points(n, d, n_centers, seed=6, center_box=10.0, sigma=1.0)
+    """float32 points of the 100-cluster mixture (centres U[-10,10]^d,
+    sigma = 1, equal weights)."""
+    return gmm_points(n, d, n_centers, seed=6, center_box=10.0,
+                      sigma=1.0).astype(np.float32)
+
+
+def clara_samples(n: int, samples: int, size: int, seed=7) -> np.ndarray:
+    """CLARA subsamples: `samples` rows of `size` distinct point indices,
+    each drawn uniformly without replacement and sorted (int32)."""
+    g = rng_for(seed)
+    return np.stack([np.sort(g.choice(n, size=size, replace=False))
+                     for _ in range(samples)]).astype(np.int32)

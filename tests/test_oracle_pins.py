@@ -336,3 +336,37 @@ def test_build_gains_step_matches_build():
                     assert g[c] == np.inf
                 elif t:
                     assert g[c] == bf.td(D, list(med[:t]) + [c]) - base
+
+
+# ------------------------------------------------------------------ CLARA
+
+def test_clara_single_full_sample_is_pam():
+    """CLARA with one 'sample' holding every point is PAM on the full data
+    (Sec. 2.2): same medoids and TD as BUILD + FastPAM1."""
+    from paper_2008_05171_gb300 import workloads as wl
+    X = wl.gmm_points(150, 3, 4, seed="clara-pin").astype(np.float32)
+    D = oracle.euclid_f32(X)
+    S = np.arange(150, dtype=np.int32)[None, :]
+    med, lab, tds, best = oracle.clara(X, 4, S)
+    ref = oracle.run(D, 4, variant="fastpam1")
+    assert best == 0
+    assert med.tolist() == ref["medoids"].tolist()
+    assert abs(tds[0] - ref["td"]) <= 1e-5 * ref["td"]
+
+
+def test_clara_best_sample_has_least_full_td():
+    from paper_2008_05171_gb300 import workloads as wl
+    X = wl.gmm_points(400, 2, 5, seed="clara-pin2").astype(np.float32)
+    D = oracle.euclid_f32(X)
+    S = wl.clara_samples(400, 5, 30, seed="clara-pin2")
+    med, lab, tds, best = oracle.clara(X, 5, S)
+    assert best == int(np.argmin(tds))
+    full = bf.td(D, med)
+    assert abs(full - tds[best]) <= 1e-5 * full
+    # each sample's TD is the TD of PAM on that sample, assigned to all data
+    for q in range(5):
+        Dq = oracle.euclid_f32(X, idx=S[q])
+        r = oracle.run(Dq, 5, variant="fastpam1")
+        gm = S[q][r["medoids"]]
+        assert abs(bf.td(D, gm) - tds[q]) <= 1e-5 * tds[q]
+    assert (lab == np.argmin(D[:, :400][:, med], axis=1)).all()
