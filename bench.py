@@ -39,6 +39,12 @@ WORKLOADS = {
                                  "(centres N(0,4I), sigma=1), Euclidean distances on the fly "
                                  "from a tcgen05 BF16 Gram with FP32 accumulation (no n x n "
                                  "matrix), exact FP32 cache, k=200, BUILD + FastPAM1 SWAP"),
+    "batched_512": dict(n=0, d=8, centers=0, k=0, recipe="batched",
+                        desc="512 independent PAM instances (n ~ U[200,4000], d=8 float32 "
+                             "uniform in [0,1)^8, k ~ U[5,50], Euclidean matrices in one "
+                             "11.5 GB arena) in one persistent launch, plus CLARA on "
+                             "n=1e6 d=32 float32 (100-cluster mixture), k=100, 10 samples "
+                             "of 80+4k=480 points"),
     "gmm_50000": dict(n=50000, d=32, centers=200, k=200, recipe="gmm_50000_points",
                       desc="n=50000 d=32 f32 GMM (200 clusters, centres U[-10,10]^32, "
                            "sigma U[0.5,2], Dirichlet(1) weights), Euclidean f32 "
@@ -252,11 +258,86 @@ def run_features(args, rank, world, local_rank):
     return line
 
 
+def run_batched(args, rank, world, local_rank):
+    """Batched instances + CLARA: kmedoids_run_batched and kmedoids_clara."""
+    import torch
+    import paper_2008_05171_gb300.kmedoids as km
+    from paper_2008_05171_gb300 import workloads as wl
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    specs = wl.batched_specs(512)
+    P, offs = wl.batched_points(specs, d=8)
+    inst, arena_len, nmed = km.batch_layout(specs)
+    inst_dev = torch.from_numpy(inst.view(np.uint8).copy()).to(dev)
+    arena = torch.empty(arena_len, dtype=torch.float32, device=dev)
+    km.batched_distances(torch.from_numpy(P).to(dev), offs, inst_dev, arena)
+    kc, samples = 100, 10
+    Xc = torch.from_numpy(wl.clara_points()).to(dev)
+    Sc = torch.from_numpy(wl.clara_samples(Xc.shape[0], samples, 80 + 4 * kc)).to(dev)
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+
+    def step():
+        a, b, c = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        a.record(stream)
+        med, res = km.run_batched(arena, inst_dev, nmed)
+        b.record(stream)
+        cl = km.clara(Xc, kc, Sc)
+        c.record(stream)
+        torch.cuda.synchronize()
+        r = np.frombuffer(res.cpu().numpy().tobytes(), dtype=km.BATCH_RESULT_DTYPE)
+        return r, cl, a.elapsed_time(b), b.elapsed_time(c)
+
+    for _ in range(args.warmup):
+        step()
+    clocks = Clocks(local_rank)
+    clocks.start()
+    outs = [step() for _ in range(args.steps)]
+    ck = clocks.stop()
+    bt = [o[2] for o in outs]
+    ct = [o[3] for o in outs]
+    total_ms = float(sum(bt) + sum(ct))
+    r = outs[-1][0]
+    ev_b = 0
+    bytes_b = 0
+    for (n, k), it in zip(specs, r["iterations"]):
+        ev_b += sum((n - t) * n for t in range(k)) + int(it) * (n - k) * n
+        bytes_b += 4 * (sum((n - t) * n for t in range(k)) + int(it) * (n - k) * n)
+    ev_c = Xc.shape[0] * kc * samples
+    value = world * args.steps * (ev_b + ev_c) / (total_ms / 1e3)
+    b_ms = float(np.mean(bt))
+    peak, pk = peaks()
+    ach = bytes_b / (b_ms / 1e3) / 1e9
+    line = {
+        "metric": "SWAP dTD point-evals/sec + full PAM run time (k=100/200); % HBM roofline",
+        "value": value, "unit": "point-evals/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32 (fixed-point dTD, FP64 TD)",
+        "data": "synthetic",
+        "config": {"workload": args.workload + ": " + WORKLOADS[args.workload]["desc"],
+                   "instances": len(specs), "arena_bytes": int(arena_len * 4),
+                   "l2": "arena 11.5 GB > L2",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "batched_ms": b_ms, "clara_ms": float(np.mean(ct)),
+        "instances_per_s": len(specs) / (b_ms / 1e3),
+        "batched_swaps": int(r["swaps"].sum()), "batched_passes": int(r["iterations"].sum()),
+        "clara_td": outs[-1][1]["td"], "clara_best_sample": outs[-1][1]["best_sample"],
+        "roofline": {"bound": "hbm", "achieved": round(ach, 1), "peak": peak, "unit": "GB/s",
+                     "frac": round(ach / peak, 4), "kernel": "k_batch_pam<16>",
+                     "algorithmic_bytes_per_launch": bytes_b, "avg_launch_ms": round(b_ms, 3),
+                     "peak_source": pk, "traffic": None},
+        "clocks": ck, "e2e": None,
+    }
+    return line
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
     import paper_2008_05171_gb300.kmedoids as km
     if args.workload.startswith("features"):
         return run_features(args, rank, world, local_rank)
+    if args.workload.startswith("batched"):
+        return run_batched(args, rank, world, local_rank)
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
     D, spec = make_input(args.workload, dev)
@@ -431,6 +512,35 @@ def run_reference(args, rank, world):
     import torch
     spec = WORKLOADS[args.workload]
     from paper_2008_05171_gb300 import workloads as wl
+    if args.workload.startswith("batched"):
+        # the oracle on the first instances of the batch (bounded sample)
+        import oracle
+        specs = wl.batched_specs(512)[:6]
+        P, offs = wl.batched_points(specs, d=8)
+        vals, secs = [], []
+        for _ in range(args.warmup + args.steps):
+            t0 = time.perf_counter()
+            ev = 0
+            for (n, k), o in zip(specs, offs):
+                D = oracle.euclid_f32(P[o:o + n])
+                r = oracle.run(D, k, variant="fastpam1")
+                ev += sum((n - t) * n for t in range(k)) + r["iterations"] * (n - k) * n
+            dt = time.perf_counter() - t0
+            vals.append(ev / dt)
+            secs.append(dt)
+        v = float(np.mean(vals[args.warmup:]))
+        cb = {"value": v, "unit": "point-evals/s", "cores": oracle.num_threads(),
+              "kind": "oracle", "sample": "BUILD + FastPAM1 on the first 6 of the 512 "
+              "instances (FP64 C oracle)"}
+        return {"impl": "reference", "metric": "SWAP dTD point-evals/sec + full PAM run time "
+                "(k=100/200); % HBM roofline", "value": v, "unit": "point-evals/s",
+                "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": 1e3 * float(np.mean(secs[args.warmup:])),
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f64", "data": "synthetic",
+                "config": {"workload": args.workload}, "cpu_baseline": cb,
+                "e2e": {"value": v, "unit": "point-evals/s", "h2d_bytes_per_step": 0,
+                        "d2h_bytes_per_step": 0}}
     X = getattr(wl, spec["recipe"])()
     if args.workload.startswith("features"):
         # no n x n matrix exists in this form: time the oracle on a subsample
