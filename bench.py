@@ -305,6 +305,52 @@ def run_batched(args, rank, world, local_rank):
         bytes_b += 4 * (sum((n - t) * n for t in range(k)) + int(it) * (n - k) * n)
     ev_c = Xc.shape[0] * kc * samples
     value = world * args.steps * (ev_b + ev_c) / (total_ms / 1e3)
+    # kernels per step: ordering + persistent PAM, and CLARA's own count
+    launches = args.steps * (2 + int(outs[-1][1]["kernel_launches"]))
+    e2e = None
+    if not args.no_e2e:
+        # the public calls from host data: points, offsets and descriptors
+        # in, distances + batched PAM, CLARA from host features, results out
+        Ph = torch.from_numpy(P).pin_memory()
+        Oh = torch.from_numpy(np.asarray(offs, dtype=np.int64)).pin_memory()
+        Ih = torch.from_numpy(inst.view(np.uint8).copy()).pin_memory()
+        Xh = Xc.cpu().pin_memory()
+        Sh = Sc.cpu().pin_memory()
+        med_h = torch.empty(nmed, dtype=torch.int32).pin_memory()
+        res_h = torch.empty(len(specs) * 24, dtype=torch.uint8).pin_memory()
+        cmed_h = torch.empty(kc, dtype=torch.int32).pin_memory()
+        lab_h = torch.empty(Xc.shape[0], dtype=torch.int32).pin_memory()
+
+        def e2e_step():
+            P_d = Ph.to(dev, non_blocking=True)
+            O_d = Oh.to(dev, non_blocking=True)
+            I_d = Ih.to(dev, non_blocking=True)
+            km.batched_distances(P_d, O_d, I_d, arena)
+            m, r = km.run_batched(arena, I_d, nmed)
+            med_h.copy_(m, non_blocking=True)
+            res_h.copy_(r, non_blocking=True)
+            X_d = Xh.to(dev, non_blocking=True)
+            S_d = Sh.to(dev, non_blocking=True)
+            cl = km.clara(X_d, kc, S_d)
+            cmed_h.copy_(cl["medoids"], non_blocking=True)
+            lab_h.copy_(cl["labels"], non_blocking=True)
+
+        e2e_step()
+        torch.cuda.synchronize()
+        ea, eb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ea.record(stream)
+        for _ in range(args.steps):
+            e2e_step()
+        eb.record(stream)
+        torch.cuda.synchronize()
+        e_ms = ea.elapsed_time(eb)
+        h2d = (Ph.numel() * 4 + Oh.numel() * 8 + Ih.numel() + Xh.numel() * 4 + Sh.numel() * 4)
+        d2h = med_h.numel() * 4 + res_h.numel() + cmed_h.numel() * 4 + lab_h.numel() * 4
+        e2e = {"value": world * args.steps * (ev_b + ev_c) / (e_ms / 1e3), "unit": "point-evals/s",
+               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+               "ms_per_step": e_ms / args.steps,
+               "includes": "host->device copies of points and features, the batched "
+                           "distance matrices, batched PAM, CLARA, results back"}
     b_ms = float(np.mean(bt))
     peak, pk = peaks()
     ach = bytes_b / (b_ms / 1e3) / 1e9
@@ -326,7 +372,7 @@ def run_batched(args, rank, world, local_rank):
                      "frac": round(ach / peak, 4), "kernel": "k_batch_pam<16>",
                      "algorithmic_bytes_per_launch": bytes_b, "avg_launch_ms": round(b_ms, 3),
                      "peak_source": pk, "traffic": None},
-        "clocks": ck, "e2e": None,
+        "clocks": ck, "e2e": e2e, "gpu_launches": launches,
     }
     return line
 

@@ -256,8 +256,15 @@ km_status kmedoids_batched_distances(const float *points, int32_t dim,
                                      const km_instance *inst, int32_t count,
                                      float *arena, void *stream);
 
-/* inst (DEVICE, count entries), medoids_out / results (DEVICE).  opts:
- * max_iter, tol; tune 1 = 8 warps per CTA, otherwise 16. */
+/* inst (DEVICE, count entries, 1 <= count <= 65536), medoids_out / results
+ * (DEVICE).  opts: max_iter, tol; tune 1 = 8 warps per CTA, otherwise 16.
+ * Asynchronous: the call only enqueues work on the stream (a zeroing copy,
+ * a kernel ordering the instances largest first, and the persistent PAM
+ * kernel) and never reads device memory on the host, so it can be captured
+ * in a CUDA graph.  Instances are validated on the device: one violating
+ * the limits above gets status KM_E_INVALID in its result and the others
+ * still run.  Host-side failures (NULL pointers, alignment, count,
+ * workspace) are returned before anything is enqueued. */
 km_status kmedoids_run_batched(const float *arena, const km_instance *inst,
                                int32_t count, int32_t *medoids_out,
                                km_batch_result *results,

@@ -30,6 +30,7 @@ namespace km {
 
 constexpr int kBatchMaxN = 4096;
 constexpr int kBatchMaxK = 128;
+constexpr int kBatchMaxCount = 1 << 16;
 
 struct BatchArgs {
   const float* arena;
@@ -85,16 +86,50 @@ __global__ void k_batch_dist(const DistArgs a) {
   }
 }
 
+// Processing order, largest work first (n^2 (k + 1), the BUILD plus SWAP
+// passes' scale): the rank of instance i is the number of instances with
+// more work, or equal work and a lower index, i.e. a stable sort by counting.
+__device__ __forceinline__ double batch_work(const km_instance& a) {
+  return (double)a.n * (double)a.n * (double)(a.k + 1);
+}
+
+__global__ void __launch_bounds__(256) k_batch_order(const km_instance* inst, int count,
+                                                     int32_t* order) {
+  __shared__ double w[256];
+  for (int i0 = blockIdx.x * blockDim.x; i0 < count; i0 += gridDim.x * blockDim.x) {
+    const int i = i0 + threadIdx.x;
+    const double wi = (i < count) ? batch_work(inst[i]) : 0.0;
+    int r = 0;
+    for (int j0 = 0; j0 < count; j0 += 256) {
+      __syncthreads();
+      if (j0 + threadIdx.x < count) w[threadIdx.x] = batch_work(inst[j0 + threadIdx.x]);
+      __syncthreads();
+      const int m = min(256, count - j0);
+      for (int t = 0; t < m; ++t) {
+        const double wj = w[t];
+        r += (wj > wi || (wj == wi && j0 + t < i)) ? 1 : 0;
+      }
+    }
+    if (i < count) order[r] = i;
+  }
+}
+
+// Per-warp cp.async ring: every warp streams its own candidate rows through
+// kRingStages stages of 512 columns (32 lanes x 4 float4), so each SM keeps
+// up to WARPS x (kRingStages - 1) x 2 KB of row data in flight.
+constexpr int kRingStages = 4;
+constexpr int kRingFloats = 512;
+
 template <int WARPS>
 struct BatchSmem {
+  float ring[WARPS][kRingStages][kRingFloats];
   float dn[kBatchMaxN];
   float ds[kBatchMaxN];
   uint8_t near[kBatchMaxN];
-  uint8_t sec[kBatchMaxN];
   uint8_t is_med[kBatchMaxN];
   int32_t med[kBatchMaxK];
   long long rl[kBatchMaxK];
-  long long acc[WARPS][kBatchMaxK + 1];
+  long long acc[WARPS][kBatchMaxK];
   double wd[WARPS];
   long long wl[WARPS];
   int wslot[WARPS];
@@ -129,6 +164,91 @@ __device__ __forceinline__ double warp_sum_pair(float hi, float lo) {
   return (double)hi + (double)lo;
 }
 
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;" ::: "memory");
+}
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// Streams the warp's candidate rows c = warp, warp + WARPS, ... (medoid rows
+// skipped) through the warp's ring.  on_chunk(c, o, v, stage) receives the
+// lane's entries row[o + 128 u + 4 lane + t] as v[u].t (entries at or beyond
+// n are stale and must be masked by the caller) and a pointer to the stage;
+// on_row_end(c) runs once per row.  Both are warp-uniform.  Each lane reads
+// back only the 16-byte pieces it copied itself, so cp.async.wait_group is the
+// only synchronisation; it completes when the lane's own copies land.
+template <int WARPS, class Chunk, class RowEnd>
+__device__ __forceinline__ void stream_rows(BatchSmem<WARPS>& S, const float* D, int n, int ld,
+                                            int warp, int lane, Chunk&& on_chunk,
+                                            RowEnd&& on_row_end) {
+  float(*ring)[kRingFloats] = S.ring[warp];
+  int ic = warp;
+  while (ic < n && S.is_med[ic]) ic += WARPS;
+  int io = 0;
+  int cc = ic, co = 0;
+  auto issue = [&](int slot) {
+    if (ic < n) {
+      const float* row = D + (size_t)ic * ld;
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int p = io + 128 * u + 4 * lane;
+        if (p < n) cp_async16(&ring[slot][128 * u + 4 * lane], row + p);
+      }
+      io += kRingFloats;
+      if (io >= n) {
+        io = 0;
+        ic += WARPS;
+        while (ic < n && S.is_med[ic]) ic += WARPS;
+      }
+    }
+    cp_async_commit();
+  };
+#pragma unroll
+  for (int s = 0; s < kRingStages - 1; ++s) issue(s);
+  int slot = 0;
+  while (cc < n) {
+    issue(slot == 0 ? kRingStages - 1 : slot - 1);
+    cp_async_wait<kRingStages - 1>();
+    const float* stage = ring[slot];
+    float4 v[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) v[u] = *reinterpret_cast<const float4*>(stage + 128 * u + 4 * lane);
+    on_chunk(cc, co, v, stage);
+    co += kRingFloats;
+    if (co >= n) {
+      on_row_end(cc);
+      co = 0;
+      cc += WARPS;
+      while (cc < n && S.is_med[cc]) cc += WARPS;
+    }
+    slot = (slot + 1 == kRingStages) ? 0 : slot + 1;
+  }
+  cp_async_wait<0>();
+}
+
+// floor(x * 2^f) for finite x >= 0 with 2^f = s1 * s2 (each a normal power
+// of two): scaling by powers of two is exact in FP32 unless the value drops
+// below the normal range, where both the rounded and the exact value floor
+// to 0, and x * 2^f < 2^62 by the choice of f.  So the round-down
+// conversion gives the same value as the integer-only fx_of, in three
+// instructions.
+__device__ __forceinline__ long long fx_scaled(float x, float s1, float s2) {
+  return __float2ll_rd((x * s1) * s2);
+}
+
+// 2^e as a float for -126 <= e <= 127.
+__device__ __forceinline__ float pow2f(int e) { return __int_as_float((e + 127) << 23); }
+
+__device__ __forceinline__ float f4get(const float4& v, int t) {
+  return t == 0 ? v.x : t == 1 ? v.y : t == 2 ? v.z : v.w;
+}
+
 template <int WARPS>
 __global__ void __launch_bounds__(WARPS * 32, 1) k_batch_pam(const BatchArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -153,7 +273,8 @@ __global__ void __launch_bounds__(WARPS * 32, 1) k_batch_pam(const BatchArgs a) 
     res.swaps = 0;
     res.status = 0;
     res.pad = 0;
-    if (n < 1 || n > kBatchMaxN || k < 1 || k > kBatchMaxK || k > n || ld < n || (ld & 3)) {
+    if (n < 1 || n > kBatchMaxN || k < 1 || k > kBatchMaxK || k > n || ld < n || (ld & 3) ||
+        (in.offset & 3) || in.offset < 0) {
       if (tid == 0) {
         res.status = KM_E_INVALID;
         a.out[q] = res;
@@ -161,7 +282,18 @@ __global__ void __launch_bounds__(WARPS * 32, 1) k_batch_pam(const BatchArgs a) 
       __syncthreads();
       continue;
     }
-    for (int o = tid; o < n; o += NT) S.is_med[o] = 0;
+    // d_n and d_s of the columns past n up to the ring's 512-column stride
+    // hold -inf, so `d < d_n` and `d < d_s` never hold there and the stream
+    // loops need no column bounds checks after BUILD step 0
+    const int npad = (n + kRingFloats - 1) / kRingFloats * kRingFloats;
+    for (int o = tid; o < npad; o += NT) {
+      if (o < n) {
+        S.is_med[o] = 0;
+      } else {
+        S.dn[o] = -__int_as_float(0x7f800000);
+        S.ds[o] = -__int_as_float(0x7f800000);
+      }
+    }
     __syncthreads();
 
     // ------------------------------------------------------------- BUILD
@@ -169,33 +301,49 @@ __global__ void __launch_bounds__(WARPS * 32, 1) k_batch_pam(const BatchArgs a) 
     for (int step = 0; step < k; ++step) {
       double bd = 1e300;
       int bc = INT_MAX;
-      for (int c = warp; c < n; c += WARPS) {
-        if (S.is_med[c]) continue;
-        const float* row = D + (size_t)c * ld;
-        float hs = 0.f, hc = 0.f;
-        for (int o = lane * 4; o < n; o += 128) {
-          const float4 v = *reinterpret_cast<const float4*>(row + o);
-          const float e[4] = {v.x, v.y, v.z, v.w};
+      float hs = 0.f, hc = 0.f, hs2 = 0.f, hc2 = 0.f;  // two compensated chains
+      stream_rows<WARPS>(
+          S, D, n, ld, warp, lane,
+          [&](int, int o, const float4(&v)[4], const float*) {
+            if (step == 0) {
 #pragma unroll
-          for (int t = 0; t < 4; ++t) {
-            if (o + t < n) {
-              float x;
-              if (step == 0) {
-                x = e[t];
-                mloc = max(mloc, __float_as_uint(e[t]) & 0x7fffffffu);
-              } else {
-                x = (e[t] < S.dn[o + t]) ? e[t] - S.dn[o + t] : 0.f;
+              for (int u = 0; u < 4; ++u) {
+                const int p0 = o + 128 * u + 4 * lane;
+#pragma unroll
+                for (int t = 0; t < 4; ++t) {
+                  if (p0 + t < n) {
+                    const float e = f4get(v[u], t);
+                    mloc = max(mloc, __float_as_uint(e) & 0x7fffffffu);
+                    kahan_add(hs, hc, e);
+                  }
+                }
               }
-              kahan_add(hs, hc, x);
+            } else {
+#pragma unroll
+              for (int u = 0; u < 4; ++u) {
+                const int p0 = o + 128 * u + 4 * lane;  // < npad <= kBatchMaxN
+                const float4 d4 = *reinterpret_cast<const float4*>(&S.dn[p0]);
+                // min(e - d_n, 0): e - d_n is negative exactly when e < d_n
+                // (and +inf on the -inf padding, giving 0)
+                kahan_add(hs, hc, fminf(v[u].x - d4.x, 0.f));
+                kahan_add(hs2, hc2, fminf(v[u].y - d4.y, 0.f));
+                kahan_add(hs, hc, fminf(v[u].z - d4.z, 0.f));
+                kahan_add(hs2, hc2, fminf(v[u].w - d4.w, 0.f));
+              }
             }
-          }
-        }
-        const double g = warp_sum_pair(hs, -hc);
-        if (g < bd) {  // rows visited in ascending order: keeps the lowest c
-          bd = g;
-          bc = c;
-        }
-      }
+          },
+          [&](int c) {
+            // fold the two chains with TwoSum, then across the warp
+            const float sh = hs + hs2;
+            const float bp = sh - hs;
+            const float err = (hs - (sh - bp)) + (hs2 - bp);
+            const double g = warp_sum_pair(sh, err - hc - hc2);
+            hs = hc = hs2 = hc2 = 0.f;
+            if (g < bd) {  // rows visited in ascending order: keeps the lowest c
+              bd = g;
+              bc = c;
+            }
+          });
       if (lane == 0) {
         S.wd[warp] = bd;
         S.wcand[warp] = bc;
@@ -239,28 +387,40 @@ __global__ void __launch_bounds__(WARPS * 32, 1) k_batch_pam(const BatchArgs a) 
     int bn = 0;
     while ((1ll << bn) <= (long long)n) ++bn;
     const int f = 60 - bn - em;
+    // 2^f split in two normal factors: -81 <= f <= 209 for finite data
+    const float fs1 = pow2f(f / 2), fs2 = pow2f(f - f / 2);
 
     // --------------------------------------------- cache, removal loss, TD
+    // nearest slot, d_n and d_s of every point from the k medoid rows (read
+    // column-wise, eight rows in flight); lowest slot among equal distances
     auto cache_all = [&]() {
       for (int i = tid; i < k; i += NT) S.rl[i] = 0;
       __syncthreads();
       for (int o = tid; o < n; o += NT) {
         int n1 = -1, n2 = -1;
         float d1 = 0.f, d2 = 0.f;
-        for (int j = 0; j < k; ++j) {
-          const float v = D[(size_t)S.med[j] * ld + o];
-          if (n1 < 0 || v < d1) {
-            n2 = n1;
-            d2 = d1;
-            n1 = j;
-            d1 = v;
-          } else if (n2 < 0 || v < d2) {
-            n2 = j;
-            d2 = v;
+        for (int j0 = 0; j0 < k; j0 += 8) {
+          float v8[8];
+#pragma unroll
+          for (int u = 0; u < 8; ++u)
+            v8[u] = (j0 + u < k) ? D[(size_t)S.med[j0 + u] * ld + o] : 0.f;
+#pragma unroll
+          for (int u = 0; u < 8; ++u) {
+            if (j0 + u < k) {
+              const float v = v8[u];
+              if (n1 < 0 || v < d1) {
+                n2 = n1;
+                d2 = d1;
+                n1 = j0 + u;
+                d1 = v;
+              } else if (n2 < 0 || v < d2) {
+                n2 = j0 + u;
+                d2 = v;
+              }
+            }
           }
         }
         S.near[o] = (uint8_t)n1;
-        S.sec[o] = (uint8_t)(n2 < 0 ? 0 : n2);
         S.dn[o] = d1;
         S.ds[o] = (n2 < 0) ? __int_as_float(0x7f800000) : d2;
         if (n2 >= 0) atomic_add_acc(&S.rl[n1], fx_of(d2, f) - fx_of(d1, f));
@@ -277,59 +437,73 @@ __global__ void __launch_bounds__(WARPS * 32, 1) k_batch_pam(const BatchArgs a) 
         long long wbest = LLONG_MAX;
         int wslot = INT_MAX, wcand = INT_MAX;
         if (k >= 2) {
-          for (int c = warp; c < n; c += WARPS) {
-            if (S.is_med[c]) continue;
-            long long* ar = S.acc[warp];
-            for (int i = lane; i <= k; i += 32) ar[i] = 0;
-            __syncwarp();
-            const float* row = D + (size_t)c * ld;
-            for (int o = lane * 4; o < n; o += 128) {
-              const float4 v = *reinterpret_cast<const float4*>(row + o);
-              const float e[4] = {v.x, v.y, v.z, v.w};
+          long long* ar = S.acc[warp];
+          for (int i = lane; i < k; i += 32) ar[i] = 0;
+          __syncwarp();
+          long long lp = 0;  // this lane's part of the shared accumulator
+          stream_rows<WARPS>(
+              S, D, n, ld, warp, lane,
+              [&](int, int o, const float4(&v)[4], const float* stage) {
+                // fast path: one d < d_s test per entry; hits in a lane mask
+                unsigned mask = 0;
 #pragma unroll
-              for (int t = 0; t < 4; ++t) {
-                const int p = o + t;
-                if (p < n && e[t] < S.ds[p]) {
+                for (int u = 0; u < 4; ++u) {
+                  const int p0 = o + 128 * u + 4 * lane;  // < npad <= kBatchMaxN
+                  const float4 s4 = *reinterpret_cast<const float4*>(&S.ds[p0]);
+#pragma unroll
+                  for (int t = 0; t < 4; ++t)
+                    if (f4get(v[u], t) < f4get(s4, t)) mask |= 1u << (4 * u + t);
+                }
+                // each lane walks its own hits (Eq. (7) cases)
+                while (mask) {
+                  const int b = __ffs(mask) - 1;
+                  mask &= mask - 1;
+                  const int col = 128 * (b >> 2) + 4 * lane + (b & 3);
+                  const int p = o + col;
+                  const float e = stage[col];
                   const float dnp = S.dn[p], dsp = S.ds[p];
                   const int sl = S.near[p];
-                  const long long xd = fx_of(e[t], f), xs = fx_of(dsp, f);
-                  if (e[t] < dnp) {
-                    const long long xn = fx_of(dnp, f);
-                    atomic_add_acc(&ar[k], xd - xn);
+                  const long long xd = fx_scaled(e, fs1, fs2), xs = fx_scaled(dsp, fs1, fs2);
+                  if (e < dnp) {
+                    const long long xn = fx_scaled(dnp, fs1, fs2);
+                    lp += xd - xn;
                     atomic_add_acc(&ar[sl], xn - xs);
                   } else {
                     atomic_add_acc(&ar[sl], xd - xs);
                   }
                 }
-              }
-            }
-            __syncwarp();
-            long long bv = LLONG_MAX;
-            int bi = INT_MAX;
-            for (int i = lane; i < k; i += 32) {
-              const long long v = S.rl[i] + ar[i];
-              if (v < bv) {
-                bv = v;
-                bi = i;
-              }
-            }
+              },
+              [&](int c) {
+                __syncwarp();
+                long long bv = LLONG_MAX;
+                int bi = INT_MAX;
+                for (int i = lane; i < k; i += 32) {
+                  const long long v = S.rl[i] + ar[i];
+                  if (v < bv) {
+                    bv = v;
+                    bi = i;
+                  }
+                }
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-              const long long ov = __shfl_xor_sync(0xffffffffu, bv, o);
-              const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-              if (ov < bv || (ov == bv && oi < bi)) {
-                bv = ov;
-                bi = oi;
-              }
-            }
-            const long long tot = bv + ar[k];
-            if (tot < wbest || (tot == wbest && (bi < wslot || (bi == wslot && c < wcand)))) {
-              wbest = tot;
-              wslot = bi;
-              wcand = c;
-            }
-            __syncwarp();
-          }
+                for (int o = 16; o > 0; o >>= 1) {
+                  const long long ov = __shfl_xor_sync(0xffffffffu, bv, o);
+                  const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+                  if (ov < bv || (ov == bv && oi < bi)) {
+                    bv = ov;
+                    bi = oi;
+                  }
+                }
+                const long long tot = bv + warp_sum(lp);
+                lp = 0;
+                if (tot < wbest || (tot == wbest && (bi < wslot || (bi == wslot && c < wcand)))) {
+                  wbest = tot;
+                  wslot = bi;
+                  wcand = c;
+                }
+                __syncwarp();
+                for (int i = lane; i < k; i += 32) ar[i] = 0;
+                __syncwarp();
+              });
         } else {
           // k = 1: the best single swap is the 1-medoid (Eq. (3))
           for (int c = warp; c < n; c += WARPS) {
@@ -410,65 +584,91 @@ __global__ void __launch_bounds__(WARPS * 32, 1) k_batch_pam(const BatchArgs a) 
   }
 }
 
-// CLARA assignment: for each point and each sample, the nearest of the
-// sample's k medoids (FP32 direct differences), summed per sample in FP64.
-__global__ void __launch_bounds__(256) k_clara_assign(const float* X, long long n, int d,
-                                                      const int32_t* med, int k, int samples,
-                                                      double* sample_td) {
-  extern __shared__ float sm[];  // medoid coordinates of one sample, k x d
-  __shared__ double red[8];
-  for (int q = 0; q < samples; ++q) {
-    for (int e = threadIdx.x; e < k * d; e += blockDim.x)
-      sm[e] = X[(long long)med[q * k + e / d] * d + e % d];
-    __syncthreads();
-    double part = 0.0;
-    for (long long o = blockIdx.x * (long long)blockDim.x + threadIdx.x; o < n;
-         o += (long long)gridDim.x * blockDim.x) {
-      const float* xo = X + o * d;
-      float best = __int_as_float(0x7f800000);
-      for (int j = 0; j < k; ++j) {
-        float s2 = 0.f;
-        for (int t = 0; t < d; ++t) {
-          const float df = xo[t] - sm[j * d + t];
-          s2 = fmaf(df, df, s2);
-        }
-        best = fminf(best, s2);
-      }
-      part += (double)sqrtf(best);
-    }
-    part = warp_sum(part);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = part;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      double t = 0.0;
-      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
-      atomicAdd(&sample_td[q], t);
-    }
-    __syncthreads();
-  }
+// CLARA: medoid j of sample q is position smed[q k + j] of that sample;
+// replace it by the point index sample_idx[q s + position].
+__global__ void k_clara_map(int32_t* smed, const int32_t* sample_idx, int samples, int k, int s) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < samples * k) smed[e] = sample_idx[(long long)(e / k) * s + smed[e]];
 }
 
-// Labels of every point for the chosen medoids (lowest slot on ties).
-__global__ void k_clara_labels(const float* X, long long n, int d, const int32_t* med, int k,
-                               int32_t* labels) {
+// CLARA assignment: every point against the k medoids of each of nq samples
+// (FP32 direct differences, lowest slot on ties), sqrt of the least squared
+// distance summed per sample in FP64.  The medoid coordinates of all nq
+// samples sit in shared memory with rows padded to DP4 float4 (zeros), the
+// point in registers (zero-padded the same way).  With labels != NULL (one
+// sample) the nearest slot of every point is written as well.
+// DP4 = 0: any d, the point read from global memory (rows padded to dp4).
+template <int DP4>
+__global__ void __launch_bounds__(256) k_clara_assign(const float* X, long long n, int d, int dp4,
+                                                      const int32_t* med, int k, int nq,
+                                                      double* sample_td, int32_t* labels) {
+  extern __shared__ float4 sm4[];  // [nq * k][dp4] medoid rows, then [nq][256] FP64 sums
+  if (DP4 > 0) dp4 = DP4;
+  double* part = reinterpret_cast<double*>(sm4 + (size_t)nq * k * dp4);
+  for (int e = threadIdx.x; e < nq * k * dp4 * 4; e += blockDim.x) {
+    const int r = e / (dp4 * 4), t = e % (dp4 * 4);
+    reinterpret_cast<float*>(sm4)[e] = (t < d) ? X[(long long)med[r] * d + t] : 0.f;
+  }
+  for (int q = 0; q < nq; ++q) part[q * 256 + threadIdx.x] = 0.0;
+  __syncthreads();
   for (long long o = blockIdx.x * (long long)blockDim.x + threadIdx.x; o < n;
        o += (long long)gridDim.x * blockDim.x) {
+    constexpr int R = DP4 > 0 ? DP4 : 1;
+    float4 x[R];
     const float* xo = X + o * d;
-    float best = 0.f;
-    int lab = -1;
-    for (int j = 0; j < k; ++j) {
-      const float* xm = X + (long long)med[j] * d;
-      float s2 = 0.f;
-      for (int t = 0; t < d; ++t) {
-        const float df = xo[t] - xm[t];
-        s2 = fmaf(df, df, s2);
-      }
-      if (lab < 0 || s2 < best) {
-        best = s2;
-        lab = j;
-      }
+#pragma unroll
+    for (int t4 = 0; t4 < DP4; ++t4) {
+      const int t = 4 * t4;
+      x[t4].x = (t < d) ? xo[t] : 0.f;
+      x[t4].y = (t + 1 < d) ? xo[t + 1] : 0.f;
+      x[t4].z = (t + 2 < d) ? xo[t + 2] : 0.f;
+      x[t4].w = (t + 3 < d) ? xo[t + 3] : 0.f;
     }
-    labels[o] = lab;
+    for (int q = 0; q < nq; ++q) {
+      const float4* mq = sm4 + (size_t)q * k * dp4;
+      float best = __int_as_float(0x7f800000);
+      int lab = 0;
+      for (int j = 0; j < k; ++j) {
+        float s2 = 0.f;
+        if (DP4 == 0) {
+          const float* mr = reinterpret_cast<const float*>(mq + j * dp4);
+          for (int t = 0; t < d; ++t) {
+            const float df = xo[t] - mr[t];
+            s2 = fmaf(df, df, s2);
+          }
+        }
+#pragma unroll
+        for (int t4 = 0; t4 < DP4; ++t4) {
+          const float4 m = mq[j * DP4 + t4];
+          float df = x[t4].x - m.x;
+          s2 = fmaf(df, df, s2);
+          df = x[t4].y - m.y;
+          s2 = fmaf(df, df, s2);
+          df = x[t4].z - m.z;
+          s2 = fmaf(df, df, s2);
+          df = x[t4].w - m.w;
+          s2 = fmaf(df, df, s2);
+        }
+        if (s2 < best) {
+          best = s2;
+          lab = j;
+        }
+      }
+      part[q * 256 + threadIdx.x] += (double)sqrtf(best);
+      if (labels) labels[o] = lab;
+    }
+  }
+  __syncthreads();
+  for (int q = 0; q < nq; ++q) {
+    double v = part[q * 256 + threadIdx.x];
+    v = warp_sum(v);
+    if ((threadIdx.x & 31) == 0) part[q * 256 + threadIdx.x] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < nq) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += part[threadIdx.x * 256 + 32 * w];
+    atomicAdd(&sample_td[threadIdx.x], t);
   }
 }
 
@@ -520,6 +720,27 @@ cudaError_t launch_batch_cfg(int cfg, const BatchArgs& a, int sms, cudaStream_t 
 
 size_t al256(size_t x) { return (x + 255) / 256 * 256; }
 
+template <int DP4>
+cudaError_t launch_assign_t(const float* X, long long n, int d, int dp4, const int32_t* med, int k,
+                            int nq, double* td, int32_t* labels, int grid, cudaStream_t s) {
+  const size_t sm = 16 * (size_t)nq * k * dp4 + 8 * 256 * (size_t)nq;
+  cudaError_t e = cudaFuncSetAttribute(k_clara_assign<DP4>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
+  k_clara_assign<DP4><<<grid, 256, sm, s>>>(X, n, d, dp4, med, k, nq, td, labels);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_clara_assign(const float* X, long long n, int d, int dp4, const int32_t* med,
+                                int k, int nq, double* td, int32_t* labels, int grid,
+                                cudaStream_t s) {
+  if (dp4 <= 2) return launch_assign_t<2>(X, n, d, 2, med, k, nq, td, labels, grid, s);
+  if (dp4 <= 4) return launch_assign_t<4>(X, n, d, 4, med, k, nq, td, labels, grid, s);
+  if (dp4 <= 8) return launch_assign_t<8>(X, n, d, 8, med, k, nq, td, labels, grid, s);
+  if (dp4 <= 16) return launch_assign_t<16>(X, n, d, 16, med, k, nq, td, labels, grid, s);
+  return launch_assign_t<0>(X, n, d, dp4, med, k, nq, td, labels, grid, s);
+}
+
 }  // namespace
 
 extern "C" size_t kmedoids_batched_workspace_size(int32_t count) {
@@ -533,7 +754,8 @@ extern "C" km_status kmedoids_run_batched(const float* arena, const km_instance*
                                           void* ws, size_t ws_bytes, void* stream) {
   set_last_error("");
   if (!arena || !inst || !medoids_out || !results || !ws) return bfail(KM_E_INVALID, "NULL pointer");
-  if (count <= 0) return bfail(KM_E_INVALID, "count must be positive");
+  if (count <= 0 || count > kBatchMaxCount)
+    return bfail(KM_E_INVALID, "count must be in [1, %d]", kBatchMaxCount);
   if (reinterpret_cast<uintptr_t>(arena) % 16 || reinterpret_cast<uintptr_t>(ws) % 256)
     return bfail(KM_E_INVALID, "arena must be 16-byte and ws 256-byte aligned");
   if (ws_bytes < kmedoids_batched_workspace_size(count))
@@ -542,27 +764,12 @@ extern "C" km_status kmedoids_run_batched(const float* arena, const km_instance*
   km_default_options(&def);
   const km_options o = opts ? *opts : def;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  // order instances by work (n^2 (k + 1)), largest first
-  std::vector<km_instance> h((size_t)count);
-  BK(cudaMemcpyAsync(h.data(), inst, sizeof(km_instance) * count, cudaMemcpyDeviceToHost, s));
-  BK(cudaStreamSynchronize(s));
-  std::vector<int32_t> ord((size_t)count);
-  for (int i = 0; i < count; ++i) {
-    ord[i] = i;
-    if (h[i].n < 1 || h[i].n > kBatchMaxN || h[i].k < 1 || h[i].k > kBatchMaxK || h[i].k > h[i].n ||
-        h[i].ld < h[i].n || h[i].ld % 4 || h[i].offset % 4 || h[i].offset < 0)
-      return bfail(KM_E_INVALID, "instance %d: need 1 <= k <= n <= %d, k <= %d, ld >= n, ld and "
-                   "offset multiples of 4", i, kBatchMaxN, kBatchMaxK);
-  }
-  std::stable_sort(ord.begin(), ord.end(), [&](int x, int y) {
-    const double wx = (double)h[x].n * h[x].n * (h[x].k + 1), wy = (double)h[y].n * h[y].n * (h[y].k + 1);
-    return wx > wy;
-  });
   unsigned char* w = static_cast<unsigned char*>(ws);
   unsigned* queue = reinterpret_cast<unsigned*>(w);
   int32_t* order = reinterpret_cast<int32_t*>(w + al256(256));
   BK(cudaMemsetAsync(queue, 0, 256, s));
-  BK(cudaMemcpyAsync(order, ord.data(), 4 * (size_t)count, cudaMemcpyHostToDevice, s));
+  k_batch_order<<<(count + 255) / 256, 256, 0, s>>>(inst, count, order);
+  BK(cudaGetLastError());
   BatchArgs a;
   memset(&a, 0, sizeof(a));
   a.arena = arena;
@@ -578,7 +785,6 @@ extern "C" km_status kmedoids_run_batched(const float* arena, const km_instance*
   // tune: 0 automatic (16 warps per CTA), 1 = 8 warps, 2 = 16 warps
   const int cfg = (o.tune == 1) ? 0 : 1;
   BK(launch_batch_cfg(cfg, a, sms, s));
-  BK(cudaStreamSynchronize(s));
   return KM_OK;
 }
 
@@ -611,7 +817,7 @@ extern "C" size_t kmedoids_clara_workspace_size(int32_t k, int32_t samples, int3
   return al256(kmedoids_batched_workspace_size(samples)) +
          al256(sizeof(km_instance) * (size_t)samples) +
          al256(sizeof(km_batch_result) * (size_t)samples) + al256(4 * (size_t)samples * k) +
-         al256(8 * (size_t)samples) + al256(4 * (size_t)samples * sample_size * ld);
+         al256(8 * ((size_t)samples + 1)) + al256(4 * (size_t)samples * sample_size * ld);
 }
 
 extern "C" km_status kmedoids_clara(const float* X, int64_t n, int32_t d, int32_t k,
@@ -640,7 +846,7 @@ extern "C" km_status kmedoids_clara(const float* X, int64_t n, int32_t d, int32_
   km_instance* inst = reinterpret_cast<km_instance*>(take(sizeof(km_instance) * samples));
   km_batch_result* bres = reinterpret_cast<km_batch_result*>(take(sizeof(km_batch_result) * samples));
   int32_t* smed = reinterpret_cast<int32_t*>(take(4 * (size_t)samples * k));
-  double* std_ = reinterpret_cast<double*>(take(8 * (size_t)samples));
+  double* std_ = reinterpret_cast<double*>(take(8 * ((size_t)samples + 1)));
   float* arena = reinterpret_cast<float*>(take(4 * (size_t)samples * sample_size * ld));
   std::vector<km_instance> hi((size_t)samples);
   for (int q = 0; q < samples; ++q) {
@@ -667,21 +873,22 @@ extern "C" km_status kmedoids_clara(const float* X, int64_t n, int32_t d, int32_
   km_status r = kmedoids_run_batched(arena, inst, samples, smed, bres, &o, bws,
                                      kmedoids_batched_workspace_size(samples), stream);
   if (r != KM_OK) return r;
-  // map sample-local medoids to point indices (device gather on the host path)
-  std::vector<int32_t> hm((size_t)samples * k), hs((size_t)samples * sample_size);
-  BK(cudaMemcpyAsync(hm.data(), smed, 4 * hm.size(), cudaMemcpyDeviceToHost, s));
-  BK(cudaMemcpyAsync(hs.data(), sample_idx, 4 * hs.size(), cudaMemcpyDeviceToHost, s));
-  BK(cudaStreamSynchronize(s));
-  for (int q = 0; q < samples; ++q)
-    for (int j = 0; j < k; ++j) hm[(size_t)q * k + j] = hs[(size_t)q * sample_size + hm[(size_t)q * k + j]];
-  BK(cudaMemcpyAsync(smed, hm.data(), 4 * hm.size(), cudaMemcpyHostToDevice, s));
-  BK(cudaMemsetAsync(std_, 0, 8 * (size_t)samples, s));
-  const size_t sm = 4 * (size_t)k * d;
-  if (sm > 200 * 1024) return bfail(KM_E_UNSUPPORTED, "k * d too large for the assignment kernel");
-  BK(cudaFuncSetAttribute(k_clara_assign, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-  int grid = device_sm_count() * 4;
-  k_clara_assign<<<grid, 256, sm, s>>>(X, n, d, smed, k, samples, std_);
+  // sample-local medoid positions -> point indices
+  k_clara_map<<<(samples * k + 255) / 256, 256, 0, s>>>(smed, sample_idx, samples, k, sample_size);
   BK(cudaGetLastError());
+  BK(cudaMemsetAsync(std_, 0, 8 * (size_t)samples, s));
+  const int dp4 = (d + 3) / 4;
+  const size_t per_sample = 16 * (size_t)k * dp4 + 8 * 256;
+  const size_t smem_cap = 200 * 1024;
+  if (per_sample > smem_cap) return bfail(KM_E_UNSUPPORTED, "k * d too large for the assignment kernel");
+  const int group = (int)std::min<size_t>((size_t)samples, smem_cap / per_sample);
+  const int agrid = device_sm_count() * 8;
+  int64_t launches = 4;  // distances, order, PAM, medoid map
+  for (int q0 = 0; q0 < samples; q0 += group) {
+    const int nq = std::min(group, samples - q0);
+    BK(launch_clara_assign(X, n, d, dp4, smed + (size_t)q0 * k, k, nq, std_ + q0, nullptr, agrid, s));
+    ++launches;
+  }
   std::vector<double> tds((size_t)samples);
   BK(cudaMemcpyAsync(tds.data(), std_, 8 * (size_t)samples, cudaMemcpyDeviceToHost, s));
   BK(cudaStreamSynchronize(s));
@@ -690,9 +897,10 @@ extern "C" km_status kmedoids_clara(const float* X, int64_t n, int32_t d, int32_
     if (tds[q] < tds[best]) best = q;
   BK(cudaMemcpyAsync(medoids_out, smed + (size_t)best * k, 4 * (size_t)k, cudaMemcpyDeviceToDevice, s));
   if (labels_out) {
-    k_clara_labels<<<device_sm_count() * 4, 256, 0, s>>>(X, n, d, smed + (size_t)best * k, k,
-                                                         labels_out);
-    BK(cudaGetLastError());
+    // labels of the chosen medoids; the TD this pass adds lands in a scratch slot
+    BK(launch_clara_assign(X, n, d, dp4, smed + (size_t)best * k, k, 1, std_ + samples, labels_out,
+                           agrid, s));
+    ++launches;
   }
   BK(cudaStreamSynchronize(s));
   if (sample_td_host)
@@ -702,6 +910,7 @@ extern "C" km_status kmedoids_clara(const float* X, int64_t n, int32_t d, int32_
     res->td = tds[best];
     res->best_sample = best;
     res->status = KM_OK;
+    res->kernel_launches = launches;
   }
   return KM_OK;
 }

@@ -5,21 +5,26 @@
 // fit, Sec. 4.9).
 //
 // Pass kernel k_feat_pass (one persistent CTA per SM, warp-specialised):
-//   warp 0      producer: 1-D bulk copies of a 128-candidate tile (A) and of
-//               128-point blocks (B) with the points' cache entries, into a
-//               2-stage shared-memory ring (mbarrier completion);
+//   warp 0      producer: 1-D bulk copies of a 128-candidate tile (A), of
+//               128-point blocks (B) into a ring of as many stages as shared
+//               memory holds (freed by the MMA's completion), and of the
+//               blocks' cache entries into a separate 4-stage ring (freed
+//               by the epilogue), all with mbarrier completion;
 //   warp 1      allocates tensor memory and issues the tcgen05 MMAs:
 //               G = X_c X_o^T, BF16 inputs, FP32 accumulation, into one of
-//               two 128-column TMEM buffers (double buffering);
+//               four 128-column TMEM accumulators;
 //   warps 2-9   epilogue, two warpgroups of 64 columns each: read G from
-//               TMEM, d^2 = |x_c|^2 + |x_o|^2 - 2 g, then
-//               SWAP:  hits (d^2 < d_s^2, tested as g - |x_c|^2/2 >
-//                      (|x_o|^2 - d_s^2)/2 with one add and one compare per
-//                      pair; an 8-column warp vote guards the rare path)
-//                      add, with d = sqrt(d^2), to per-candidate slot
-//                      accumulators in shared memory (Eq. (7));
-//               BUILD: each thread sums min(d - d_n, 0) of its candidate
-//                      (step 0: d) with Kahan compensation.
+//               TMEM and test every pair against its point's threshold,
+//               d(o,c)^2 < d^2(o)  <=>  g - |x_c|^2/2 > (|x_o|^2 - d^2(o))/2,
+//               one add and one compare per pair into a 16-bit lane mask;
+//               the pairs that pass (rare) are walked lane by lane (or, in
+//               a group where some lane has many, with predication) and
+//               take d = sqrt(|x_c|^2 + |x_o|^2 - 2 g):
+//               SWAP:  Eq. (7) per-slot terms into per-candidate slot
+//                      accumulators in shared memory, the shared term into
+//                      a compensated register sum;
+//               BUILD: min(d - d_n, 0) summed with Kahan compensation
+//                      (step 0: every d).
 // The per-point cache (nearest, d_n, d_s) is computed exactly with FP32
 // direct differences sum (x - y)^2 (cache, apply and BUILD commit kernels),
 // so the bf16 Gram form only decides which candidate rows see a hit; its
@@ -38,10 +43,9 @@
 
 namespace km {
 
-constexpr int kFeatStages = 2;
 constexpr int kFeatEpiWarps = 8;
 constexpr int kFeatThreads = (2 + kFeatEpiWarps) * 32;
-constexpr int kFeatMaxK = 224;       // shared accumulators: 128 x (k+1) x 4 B
+constexpr int kFeatMaxK = 224;       // shared accumulators: 128 x k x 4 B
 constexpr int kFeatMaxD = 256;
 
 struct FeatArgs {
@@ -74,15 +78,20 @@ struct FeatArgs {
   double tol;
 };
 
+constexpr int kFeatAccBufs = 4;     // TMEM accumulators of kTileN columns
+constexpr int kFeatMetaStages = 4;  // ring of per-block point caches
+constexpr int kFeatMaxBStages = 4;  // ring of point blocks (as many as fit)
+
 struct FeatLayout {
-  size_t bars, flags, wkeys, rl, acc, red, tslot, a, stages, stage_bytes, meta_bytes, total;
+  size_t bars, flags, wkeys, rl, acc, red, tslot, meta, a, stages, stage_bytes, meta_bytes, total;
+  int bst;  // point-block stages
 };
 
 __host__ __device__ inline FeatLayout feat_layout(int d, int k) {
   FeatLayout L;
   size_t o = 0;
   L.bars = o;
-  o += 8 * (2 + 2 * kFeatStages + 4 + 1);
+  o += 8 * (2 + 2 * kFeatMaxBStages + 2 * kFeatMetaStages + 2 * kFeatAccBufs + 1);
   L.flags = o;
   o += 32;
   L.tslot = o;
@@ -93,22 +102,48 @@ __host__ __device__ inline FeatLayout feat_layout(int d, int k) {
   L.rl = o;
   o += 8 * (size_t)k;
   L.acc = o;
-  o += 4 * (size_t)kTileM * (k + 1);
+  o += 4 * (size_t)kTileM * k;
   L.red = o;
   o += 8 * (size_t)kTileM;
+  o = (o + 127) / 128 * 128;
+  L.meta = o;
+  L.meta_bytes = 5 * 4 * kTileN;
+  o += L.meta_bytes * kFeatMetaStages;
   o = (o + 1023) / 1024 * 1024;
   L.a = o;
   o += (size_t)kTileM * d * 2;
   L.stages = o;
-  L.meta_bytes = 5 * 4 * kTileN;
-  L.stage_bytes = (size_t)kTileN * d * 2 + L.meta_bytes;
-  L.stage_bytes = (L.stage_bytes + 1023) / 1024 * 1024;
-  o += L.stage_bytes * kFeatStages;
+  L.stage_bytes = (size_t)kTileN * d * 2;
+  const size_t cap = 227 * 1024;
+  int bst = (o < cap) ? (int)((cap - o) / L.stage_bytes) : 0;
+  if (bst > kFeatMaxBStages) bst = kFeatMaxBStages;
+  if (bst < 1) bst = 1;  // then total > cap: the host rejects the shape
+  L.bst = bst;
+  o += L.stage_bytes * bst;
   L.total = o;
   return L;
 }
 
 __device__ __forceinline__ float bf(uint16_t v) { return __uint_as_float((uint32_t)v << 16); }
+
+// v[j] for a lane-dependent j in [0, 16): a select tree over registers.
+__device__ __forceinline__ float sel16(const float* v, int j) {
+  const bool b0 = j & 1, b1 = j & 2, b2 = j & 4, b3 = j & 8;
+  const float a0 = b0 ? v[1] : v[0], a1 = b0 ? v[3] : v[2];
+  const float a2 = b0 ? v[5] : v[4], a3 = b0 ? v[7] : v[6];
+  const float a4 = b0 ? v[9] : v[8], a5 = b0 ? v[11] : v[10];
+  const float a6 = b0 ? v[13] : v[12], a7 = b0 ? v[15] : v[14];
+  const float c0 = b1 ? a1 : a0, c1 = b1 ? a3 : a2, c2 = b1 ? a5 : a4, c3 = b1 ? a7 : a6;
+  const float e0 = b2 ? c1 : c0, e1 = b2 ? c3 : c2;
+  return b3 ? e1 : e0;
+}
+
+__device__ __forceinline__ void kahan_addf(float& s, float& c, float x) {
+  const float y = x - c;
+  const float t = s + y;
+  c = (t - s) - y;
+  s = t;
+}
 
 // ------------------------------------------------------------ pass kernel
 template <int MODE>
@@ -118,14 +153,17 @@ __global__ void __launch_bounds__(kFeatThreads, 1) k_feat_pass(const FeatArgs a)
   if (st->done || st->error) return;
   const int n = a.n, d = a.d, k = a.k;
   const FeatLayout L = feat_layout(d, k);
+  const int bst = L.bst;
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + L.bars);
   uint64_t* a_full = bars + 0;
-  uint64_t* tile_done = bars + 1;  // epilogue finished the published tile
-  uint64_t* b_full = bars + 2;                       // [S]
-  uint64_t* b_empty = bars + 2 + kFeatStages;        // [S]
-  uint64_t* acc_full = bars + 2 + 2 * kFeatStages;   // [2]
-  uint64_t* acc_empty = acc_full + 2;                // [2]
-  uint64_t* ep_bar = acc_full + 4;
+  uint64_t* tile_done = bars + 1;                       // epilogue finished the published tile
+  uint64_t* b_full = bars + 2;                          // [kFeatMaxBStages]
+  uint64_t* b_empty = b_full + kFeatMaxBStages;         // [kFeatMaxBStages], MMA commit
+  uint64_t* m_full = b_empty + kFeatMaxBStages;         // [kFeatMetaStages]
+  uint64_t* m_empty = m_full + kFeatMetaStages;         // [kFeatMetaStages], epilogue
+  uint64_t* acc_full = m_empty + kFeatMetaStages;       // [kFeatAccBufs]
+  uint64_t* acc_empty = acc_full + kFeatAccBufs;        // [kFeatAccBufs]
+  uint64_t* ep_bar = acc_empty + kFeatAccBufs;
   volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + L.flags);
   int* last_flag = reinterpret_cast<int*>(smem + L.flags) + 1;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + L.flags) + 2;
@@ -134,6 +172,7 @@ __global__ void __launch_bounds__(kFeatThreads, 1) k_feat_pass(const FeatArgs a)
   double* rl = reinterpret_cast<double*>(smem + L.rl);
   float* acc = reinterpret_cast<float*>(smem + L.acc);
   double* red = reinterpret_cast<double*>(smem + L.red);
+  unsigned char* metas = smem + L.meta;
   unsigned char* sA = smem + L.a;
   unsigned char* stages = smem + L.stages;
 
@@ -152,11 +191,15 @@ __global__ void __launch_bounds__(kFeatThreads, 1) k_feat_pass(const FeatArgs a)
   if (tid == 0) {
     mbar_init(a_full, 1);
     mbar_init(tile_done, kFeatEpiWarps);
-    for (int q = 0; q < kFeatStages; ++q) {
+    for (int q = 0; q < kFeatMaxBStages; ++q) {
       mbar_init(&b_full[q], 1);
-      mbar_init(&b_empty[q], 1 + kFeatEpiWarps);
+      mbar_init(&b_empty[q], 1);
     }
-    for (int q = 0; q < 2; ++q) {
+    for (int q = 0; q < kFeatMetaStages; ++q) {
+      mbar_init(&m_full[q], 1);
+      mbar_init(&m_empty[q], kFeatEpiWarps);
+    }
+    for (int q = 0; q < kFeatAccBufs; ++q) {
       mbar_init(&acc_full[q], 1);
       mbar_init(&acc_empty[q], kFeatEpiWarps);
     }
@@ -168,10 +211,10 @@ __global__ void __launch_bounds__(kFeatThreads, 1) k_feat_pass(const FeatArgs a)
   if (MODE == kModeSwap) {
     const double* rsrc = a.removal + (size_t)rb * a.k_pad;
     for (int i = tid; i < k; i += blockDim.x) rl[i] = rsrc[i];
-    for (int i = tid; i < kTileM * (k + 1); i += blockDim.x) acc[i] = 0.f;
+    for (int i = tid; i < kTileM * k; i += blockDim.x) acc[i] = 0.f;
   }
   if (warp == 1) {
-    tmem_alloc(tmem_slot, 2 * kTileN);
+    tmem_alloc(tmem_slot, kFeatAccBufs * kTileN);
     tmem_relinquish();
   }
   tc_fence_before();
@@ -189,7 +232,7 @@ __global__ void __launch_bounds__(kFeatThreads, 1) k_feat_pass(const FeatArgs a)
     if (lane == 0) {
       long long gb = 0;
       bool ok = true;
-      uint32_t bused = 0, bph = 0;
+      uint32_t bused = 0, bph = 0, mused = 0, mph = 0;
       for (int seq = 0; ok; ++seq) {
         unsigned tile = atomicAdd(&st->tile_next, 1u);
         const int t = (tile < (unsigned)ntiles) ? (int)tile : -1;
@@ -207,32 +250,44 @@ __global__ void __launch_bounds__(kFeatThreads, 1) k_feat_pass(const FeatArgs a)
         mbar_arrive_expect_tx(a_full, tile_bytes);
         bulk_g2s(sA, a.Xp + (size_t)t * kTileM * d, tile_bytes, a_full);
         for (int b = 0; b < nblocks; ++b, ++gb) {
-          const int s = (int)(gb % kFeatStages);
-          const uint32_t ph = (uint32_t)((gb / kFeatStages) & 1);
+          const int s = (int)(gb % bst);
+          const uint32_t ph = (uint32_t)((gb / bst) & 1);
           if (!mbar_wait(&b_empty[s], ph ^ 1u, abort_flag)) {
             ok = false;
             break;
           }
-          unsigned char* sb = stages + (size_t)s * L.stage_bytes;
-          unsigned char* meta = sb + (size_t)kTileN * d * 2;
-          mbar_arrive_expect_tx(&b_full[s], tile_bytes + (uint32_t)L.meta_bytes);
+          mbar_arrive_expect_tx(&b_full[s], tile_bytes);
           bused |= 1u << s;
           bph = (bph & ~(1u << s)) | (ph << s);
-          bulk_g2s(sb, a.Xp + (size_t)b * kTileN * d, tile_bytes, &b_full[s]);
+          bulk_g2s(stages + (size_t)s * L.stage_bytes, a.Xp + (size_t)b * kTileN * d, tile_bytes,
+                   &b_full[s]);
+          const int ms = (int)(gb % kFeatMetaStages);
+          const uint32_t mp = (uint32_t)((gb / kFeatMetaStages) & 1);
+          if (!mbar_wait(&m_empty[ms], mp ^ 1u, abort_flag)) {
+            ok = false;
+            break;
+          }
+          unsigned char* meta = metas + (size_t)ms * L.meta_bytes;
+          mbar_arrive_expect_tx(&m_full[ms], (uint32_t)L.meta_bytes);
+          mused |= 1u << ms;
+          mph = (mph & ~(1u << ms)) | (mp << ms);
           const size_t o0 = (size_t)b * kTileN;
-          bulk_g2s(meta, a.norms + o0, 4 * kTileN, &b_full[s]);
-          bulk_g2s(meta + 512, a.thr + o0, 4 * kTileN, &b_full[s]);
-          bulk_g2s(meta + 1024, a.dn + o0, 4 * kTileN, &b_full[s]);
-          bulk_g2s(meta + 1536, a.ds + o0, 4 * kTileN, &b_full[s]);
-          bulk_g2s(meta + 2048, a.near + o0, 4 * kTileN, &b_full[s]);
+          bulk_g2s(meta, a.norms + o0, 4 * kTileN, &m_full[ms]);
+          bulk_g2s(meta + 512, a.thr + o0, 4 * kTileN, &m_full[ms]);
+          bulk_g2s(meta + 1024, a.dn + o0, 4 * kTileN, &m_full[ms]);
+          bulk_g2s(meta + 1536, a.ds + o0, 4 * kTileN, &m_full[ms]);
+          bulk_g2s(meta + 2048, a.near + o0, 4 * kTileN, &m_full[ms]);
         }
       }
       if (!ok) {
         abort_flag[0] = 1;
         atomicExch(&st->error, kErrTimeout);
+        // wait (bounded) for this thread's own copies still in flight
         volatile int never = 0;
-        for (int q = 0; q < kFeatStages; ++q)
+        for (int q = 0; q < kFeatMaxBStages; ++q)
           if (bused & (1u << q)) (void)mbar_wait(&b_full[q], (bph >> q) & 1u, &never);
+        for (int q = 0; q < kFeatMetaStages; ++q)
+          if (mused & (1u << q)) (void)mbar_wait(&m_full[q], (mph >> q) & 1u, &never);
       }
     }
   } else if (warp == 1) {
@@ -249,10 +304,10 @@ __global__ void __launch_bounds__(kFeatThreads, 1) k_feat_pass(const FeatArgs a)
         tc_fence_after();
         bool ok = true;
         for (int b = 0; b < nblocks; ++b, ++gb) {
-          const int s = (int)(gb % kFeatStages);
-          const int buf = (int)(gb & 1);
-          if (!mbar_wait(&b_full[s], (uint32_t)((gb / kFeatStages) & 1), abort_flag) ||
-              !mbar_wait(&acc_empty[buf], (uint32_t)(((gb >> 1) & 1) ^ 1), abort_flag)) {
+          const int s = (int)(gb % bst);
+          const int buf = (int)(gb % kFeatAccBufs);
+          if (!mbar_wait(&b_full[s], (uint32_t)((gb / bst) & 1), abort_flag) ||
+              !mbar_wait(&acc_empty[buf], (uint32_t)(((gb / kFeatAccBufs) & 1) ^ 1), abort_flag)) {
             ok = false;
             break;
           }
@@ -271,7 +326,8 @@ __global__ void __launch_bounds__(kFeatThreads, 1) k_feat_pass(const FeatArgs a)
       if (abort_flag[0] && issued > 0) {  // let issued MMAs finish before exit
         volatile int never = 0;
         const long long lastb = gb - 1;
-        (void)mbar_wait(&acc_full[lastb & 1], (uint32_t)((lastb >> 1) & 1), &never);
+        (void)mbar_wait(&acc_full[lastb % kFeatAccBufs],
+                        (uint32_t)((lastb / kFeatAccBufs) & 1), &never);
       }
     }
   } else {
@@ -280,6 +336,8 @@ __global__ void __launch_bounds__(kFeatThreads, 1) k_feat_pass(const FeatArgs a)
     const int quarter = warp & 3;         // TMEM lanes 32*quarter..+31
     const int group = ew >> 2;            // columns 64*group..+63
     const int r = quarter * 32 + lane;    // candidate row within the tile
+    const int col0 = group * 64;
+    float* arow = acc + (size_t)r * k;
     uint32_t eph = 0;
     long long gb = 0;
     bool ok = true;
@@ -293,101 +351,102 @@ __global__ void __launch_bounds__(kFeatThreads, 1) k_feat_pass(const FeatArgs a)
       const int c = t * kTileM + r;
       const bool cvalid = (c < n) && !a.is_med[c];
       const float nc = (c < n) ? a.norms[c] : 0.f;
-      float ks_ = 0.f, kc_ = 0.f;  // BUILD Kahan pair
+      // d(o,c)^2 < d^2(o)  <=>  g - |x_c|^2/2 > (|x_o|^2 - d^2(o))/2 = thr[o]
+      const float hc = cvalid ? 0.5f * nc : __int_as_float(0x7f800000);
+      float ks_ = 0.f, kc_ = 0.f;  // Kahan pair: BUILD gain or SWAP shared term
       for (int b = 0; b < nblocks; ++b, ++gb) {
-        const int s = (int)(gb % kFeatStages);
-        const int buf = (int)(gb & 1);
-        if (!mbar_wait(&acc_full[buf], (uint32_t)((gb >> 1) & 1), abort_flag) ||
-            !mbar_wait(&b_full[s], (uint32_t)((gb / kFeatStages) & 1), abort_flag)) {
+        const int buf = (int)(gb % kFeatAccBufs);
+        const int ms = (int)(gb % kFeatMetaStages);
+        if (!mbar_wait(&acc_full[buf], (uint32_t)((gb / kFeatAccBufs) & 1), abort_flag) ||
+            !mbar_wait(&m_full[ms], (uint32_t)((gb / kFeatMetaStages) & 1), abort_flag)) {
           ok = false;
           break;
         }
         tc_fence_after();
         float v[64];
         {
-          float* v0 = v;
-          float* v1 = v + 32;
           const uint32_t ta = tmem + ((uint32_t)(quarter * 32) << 16) +
-                              (uint32_t)(buf * kTileN + group * 64);
-          tmem_ld32(ta, *reinterpret_cast<float(*)[32]>(v0));
-          tmem_ld32(ta + 32, *reinterpret_cast<float(*)[32]>(v1));
+                              (uint32_t)(buf * kTileN + col0);
+          tmem_ld32(ta, *reinterpret_cast<float(*)[32]>(v));
+          tmem_ld32(ta + 32, *reinterpret_cast<float(*)[32]>(v + 32));
           tmem_ld_wait();
         }
         tc_fence_before();
         __syncwarp();
         if (lane == 0) mbar_arrive(&acc_empty[buf]);
-        const unsigned char* meta =
-            stages + (size_t)s * L.stage_bytes + (size_t)kTileN * d * 2;
+        const unsigned char* meta = metas + (size_t)ms * L.meta_bytes;
         const float* m_no = reinterpret_cast<const float*>(meta);
         const float* m_thr = reinterpret_cast<const float*>(meta + 512);
         const float* m_dn = reinterpret_cast<const float*>(meta + 1024);
         const float* m_ds = reinterpret_cast<const float*>(meta + 1536);
         const int* m_near = reinterpret_cast<const int*>(meta + 2048);
-        const int col0 = group * 64;
-        // d(o,c)^2 < d^2(o)  <=>  g - |x_c|^2/2 > (|x_o|^2 - d^2(o))/2 = thr[o]
-        const float hc = cvalid ? 0.5f * nc : __int_as_float(0x7f800000);
+        // one pair (o = column col, candidate c = this thread's row) that
+        // passed the threshold test; exact case split on d = sqrt(d^2)
+        auto hit = [&](int col, float g) {
+          const float d2 = fmaf(-2.f, g, nc + m_no[col]);
+          const float dd = sqrtf(fmaxf(d2, 0.f));
+          const float dn_ = m_dn[col];
+          if (MODE == kModeSwap) {
+            const float ds_ = m_ds[col];
+            const int sl = m_near[col];
+            const bool inner = dd < dn_;
+            atomicAdd(arow + sl, inner ? dn_ - ds_ : dd - ds_);  // Eq. (7) per-slot term
+            if (inner) kahan_addf(ks_, kc_, dd - dn_);           // shared term
+          } else if (dd < dn_) {
+            kahan_addf(ks_, kc_, dd - dn_);
+          }
+        };
         if (MODE == kModeBuild && a.build_first) {
           const int colg = b * kTileN + col0;
 #pragma unroll
           for (int j = 0; j < 64; ++j) {
             const float d2 = fmaf(-2.f, v[j], nc + m_no[col0 + j]);
-            const float x = (colg + j < n) ? sqrtf(fmaxf(d2, 0.f)) : 0.f;
-            const float y = x - kc_;
-            const float tt = ks_ + y;
-            kc_ = (tt - ks_) - y;
-            ks_ = tt;
+            kahan_addf(ks_, kc_, (colg + j < n) ? sqrtf(fmaxf(d2, 0.f)) : 0.f);
           }
         } else {
 #pragma unroll
-          for (int j0 = 0; j0 < 64; j0 += 8) {
-            const float4 t0 = *reinterpret_cast<const float4*>(m_thr + col0 + j0);
-            const float4 t1 = *reinterpret_cast<const float4*>(m_thr + col0 + j0 + 4);
-            const float tq[8] = {t0.x, t0.y, t0.z, t0.w, t1.x, t1.y, t1.z, t1.w};
-            bool p = false;
+          for (int g16 = 0; g16 < 4; ++g16) {
+            // fast path: one add and one compare per pair into a lane mask
+            unsigned mask = 0;
 #pragma unroll
-            for (int q = 0; q < 8; ++q) p |= (v[j0 + q] - hc > tq[q]);
-            if (!__any_sync(0xffffffffu, p)) continue;
-            // rare path: the lanes with a hit in this 8-column group
+            for (int q = 0; q < 16; q += 4) {
+              const float4 t4 = *reinterpret_cast<const float4*>(m_thr + col0 + g16 * 16 + q);
+              mask |= (v[g16 * 16 + q + 0] - hc > t4.x) ? (1u << (q + 0)) : 0u;
+              mask |= (v[g16 * 16 + q + 1] - hc > t4.y) ? (1u << (q + 1)) : 0u;
+              mask |= (v[g16 * 16 + q + 2] - hc > t4.z) ? (1u << (q + 2)) : 0u;
+              mask |= (v[g16 * 16 + q + 3] - hc > t4.w) ? (1u << (q + 3)) : 0u;
+            }
+            const unsigned most = __reduce_max_sync(0xffffffffu, (unsigned)__popc(mask));
+            if (most == 0) continue;
+            const int cb = col0 + g16 * 16;
+            if (most > 4) {
+              // dense group: every column, predicated on its bit
 #pragma unroll
-            for (int q = 0; q < 8; ++q) {
-              if (v[j0 + q] - hc > tq[q]) {
-                const int col = col0 + j0 + q;
-                const float d2 = fmaf(-2.f, v[j0 + q], nc + m_no[col]);
-                const float dd = sqrtf(fmaxf(d2, 0.f));
-                const float dn_ = m_dn[col];
-                if (MODE == kModeSwap) {
-                  const float ds_ = m_ds[col];
-                  const int sl = m_near[col];
-                  float* arow = acc + (size_t)r * (k + 1);
-                  if (dd < dn_) {
-                    atomicAdd(arow + k, dd - dn_);
-                    atomicAdd(arow + sl, dn_ - ds_);
-                  } else {
-                    atomicAdd(arow + sl, dd - ds_);
-                  }
-                } else if (dd < dn_) {
-                  const float y = (dd - dn_) - kc_;
-                  const float tt = ks_ + y;
-                  kc_ = (tt - ks_) - y;
-                  ks_ = tt;
-                }
+              for (int j = 0; j < 16; ++j)
+                if ((mask >> j) & 1u) hit(cb + j, v[g16 * 16 + j]);
+            } else {
+              // sparse group: each lane walks its own hits
+              while (mask) {
+                const int j = __ffs(mask) - 1;
+                mask &= mask - 1;
+                hit(cb + j, sel16(v + g16 * 16, j));
               }
             }
           }
         }
         __syncwarp();
-        if (lane == 0) mbar_arrive(&b_empty[s]);
+        if (lane == 0) mbar_arrive(&m_empty[ms]);
       }
       if (!ok) break;
       // ------------------------------------------------------ tile finished
-      if (MODE == kModeBuild && group == 1) red[r] = (double)ks_ - (double)kc_;
+      if (group == 1) red[r] = (double)ks_ - (double)kc_;
       if (!cons_sync(ep_bar, eph, abort_flag)) {
         ok = false;
         break;
       }
       if (group == 0) {
+        const double shared_part = ((double)ks_ - (double)kc_) + red[r];
         if (MODE == kModeSwap) {
-          float* arow = acc + (size_t)r * (k + 1);
           if (cvalid) {
             double best = 1e300;
             int bi = 0;
@@ -399,16 +458,16 @@ __global__ void __launch_bounds__(kFeatThreads, 1) k_feat_pass(const FeatArgs a)
               }
             }
             Key<double> ck;
-            ck.d = best + (double)arow[k];
+            ck.d = best + shared_part;
             ck.slot = bi;
             ck.cand = c;
             if (key_less(ck, wbest)) wbest = ck;
           }
-          for (int i = 0; i <= k; ++i) arow[i] = 0.f;
+          for (int i = 0; i < k; ++i) arow[i] = 0.f;
         } else {
           if (cvalid) {
             Key<double> ck;
-            ck.d = ((double)ks_ - (double)kc_) + red[r];
+            ck.d = shared_part;
             ck.slot = 0;
             ck.cand = c;
             if (key_less(ck, wbest)) wbest = ck;
@@ -432,7 +491,7 @@ __global__ void __launch_bounds__(kFeatThreads, 1) k_feat_pass(const FeatArgs a)
   // ------------------------------------------------------------ CTA result
   tc_fence_before();
   __syncthreads();
-  if (warp == 1) tmem_dealloc(tmem, 2 * kTileN);
+  if (warp == 1) tmem_dealloc(tmem, kFeatAccBufs * kTileN);
   if (tid == 0) {
     Key<double> b = wkeys[0];
     for (int w = 1; w < kFeatEpiWarps; ++w)

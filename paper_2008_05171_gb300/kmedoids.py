@@ -495,7 +495,8 @@ def clara(X, k, sample_idx):
         tds.ctypes.data_as(ctypes.c_void_p), ctypes.byref(res),
         ctypes.c_void_p(ws.data_ptr()), ws.numel(), _stream()))
     return {"medoids": med, "labels": lab, "sample_td": tds.tolist(),
-            "best_sample": res.best_sample, "td": res.td}
+            "best_sample": res.best_sample, "td": res.td,
+            "kernel_launches": res.kernel_launches}
 
 
 def version() -> str:

@@ -71,3 +71,76 @@ def test_clara_matches_oracle():
     lab = out["labels"].cpu().numpy()
     assert np.mean(lab == olab) > 0.999
     assert abs(out["td"] - otds[obest]) <= 1e-6 * otds[obest]
+
+
+def _run_specs(specs, seed, **kw):
+    P, offs = wl.batched_points(specs, d=8, seed=seed)
+    inst, arena_len, nmed = km.batch_layout(specs)
+    inst_dev = torch.from_numpy(inst.view(np.uint8).copy()).cuda()
+    arena = torch.zeros(arena_len, dtype=torch.float32, device="cuda")
+    km.batched_distances(torch.from_numpy(P).cuda(), offs, inst_dev, arena)
+    med, res = km.run_batched(arena, inst_dev, nmed, **kw)
+    med = med.cpu().numpy()
+    res = np.frombuffer(res.cpu().numpy().tobytes(), dtype=km.BATCH_RESULT_DTYPE)
+    return P, offs, inst, med, res
+
+
+def test_batched_long_rows_and_ragged_tails():
+    """Rows of several 512-column ring stages with ragged last stages, up to
+    the n = 4096 and k = 128 limits."""
+    specs = [(4096, 128), (4093, 9), (1025, 40), (1537, 2), (513, 3), (2048, 1)]
+    P, offs, inst, med, res = _run_specs(specs, "batched-long")
+    for i, (n, k) in enumerate(specs):
+        mo = int(inst[i]["medoid_offset"])
+        ref = oracle.run(oracle.euclid_f32(P[offs[i]:offs[i] + n]), k, variant="fastpam1")
+        assert res[i]["status"] == 0, i
+        assert med[mo:mo + k].tolist() == ref["medoids"].tolist(), (i, n, k)
+        assert abs(res[i]["td"] - ref["td"]) <= 1e-9 * max(1.0, ref["td"]), i
+        if k < n:
+            assert res[i]["swaps"] == ref["swaps"], i
+            assert res[i]["iterations"] == ref["iterations"], i
+
+
+def test_batched_invalid_instance_reported_per_instance():
+    """An instance outside the limits gets KM_E_INVALID in its own result;
+    the other instances are solved."""
+    specs = [(300, 5), (200, 4), (250, 6)]
+    P, offs = wl.batched_points(specs, d=8, seed="batched-invalid")
+    inst, arena_len, nmed = km.batch_layout(specs)
+    inst[1]["k"] = 300  # k > n
+    inst_dev = torch.from_numpy(inst.view(np.uint8).copy()).cuda()
+    arena = torch.zeros(arena_len, dtype=torch.float32, device="cuda")
+    km.batched_distances(torch.from_numpy(P).cuda(), offs, inst_dev, arena)
+    med, res = km.run_batched(arena, inst_dev, nmed + 300)
+    res = np.frombuffer(res.cpu().numpy().tobytes(), dtype=km.BATCH_RESULT_DTYPE)
+    assert res[1]["status"] == 1
+    assert res[0]["status"] == 0 and res[2]["status"] == 0
+    med = med.cpu().numpy()
+    for i in (0, 2):
+        n, k = specs[i]
+        mo = int(inst[i]["medoid_offset"])
+        ref = oracle.run(oracle.euclid_f32(P[offs[i]:offs[i] + n]), k, variant="fastpam1")
+        assert med[mo:mo + k].tolist() == ref["medoids"].tolist(), i
+
+
+def test_batched_graph_capture_replays():
+    """kmedoids_run_batched enqueues only device work, so it can be captured
+    in a CUDA graph; replays give the eager result."""
+    specs = [(700, 12), (1100, 20), (300, 4), (64, 64)]
+    P, offs = wl.batched_points(specs, d=8, seed="batched-graph")
+    inst, arena_len, nmed = km.batch_layout(specs)
+    inst_dev = torch.from_numpy(inst.view(np.uint8).copy()).cuda()
+    arena = torch.zeros(arena_len, dtype=torch.float32, device="cuda")
+    km.batched_distances(torch.from_numpy(P).cuda(), offs, inst_dev, arena)
+    med0, res0 = km.run_batched(arena, inst_dev, nmed)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        med1, res1 = km.run_batched(arena, inst_dev, nmed)
+    for _ in range(2):
+        med1.fill_(-1)
+        res1.fill_(0)
+        g.replay()
+        torch.cuda.synchronize()
+        assert torch.equal(med0, med1)
+        assert torch.equal(res0, res1)

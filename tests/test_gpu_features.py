@@ -74,3 +74,23 @@ def test_build_features_steps():
     assert start["iterations"] >= 1
     omed, otd, ogains = oracle.pam_build(Dh, 6)
     assert np.allclose(gains, ogains, rtol=1e-4, atol=1e-3 * abs(ogains[0]) / 1500)
+
+
+def test_run_features_many_tiles_per_cta():
+    """n = 20000 gives 157 candidate tiles, more than there are SMs, so CTAs
+    take several tiles each through the dynamic tile counter (and the tile
+    hand-over between producer and epilogue); the run must equal the
+    oracle's BUILD + FastPAM1 on the exact FP32 matrix within 1e-5 and its
+    reported TD must be exact for its medoids."""
+    n, d, k = 20000, 32, 16
+    X = wl.to_bf16_values(wl.gmm_points(n, d, 12, seed="feat-many", center_std=2.0,
+                                        center_box=None))
+    Xt = torch.from_numpy(X).to(torch.bfloat16).cuda()
+    out = km.run_features(Xt, k)
+    med = out["medoids"].cpu().numpy()
+    assert len(set(med.tolist())) == k
+    D = wl.euclidean_f32_torch(X, torch.device("cuda", 0)).cpu().numpy()
+    tdv = oracle.td(D, med)
+    assert abs(out["td"] - tdv) <= 1e-6 * tdv
+    ref = oracle.run(D, k, variant="fastpam1")
+    assert abs(out["td"] - ref["td"]) <= 1e-5 * ref["td"]
