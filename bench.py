@@ -266,6 +266,8 @@ def run_batched(args, rank, world, local_rank):
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
     specs = wl.batched_specs(512)
+    if args.instances:
+        specs = specs[:args.instances]
     P, offs = wl.batched_points(specs, d=8)
     inst, arena_len, nmed = km.batch_layout(specs)
     inst_dev = torch.from_numpy(inst.view(np.uint8).copy()).to(dev)
@@ -355,15 +357,12 @@ def run_batched(args, rank, world, local_rank):
     peak, pk = peaks()
     ach = bytes_b / (b_ms / 1e3) / 1e9
     line = {
-        "metric": "SWAP dTD point-evals/sec + full PAM run time (k=100/200); % HBM roofline",
+        "metric": BATCHED_METRIC,
         "value": value, "unit": "point-evals/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32 (fixed-point dTD, FP64 TD)",
         "data": "synthetic",
-        "config": {"workload": args.workload + ": " + WORKLOADS[args.workload]["desc"],
-                   "instances": len(specs), "arena_bytes": int(arena_len * 4),
-                   "l2": "arena 11.5 GB > L2",
-                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "config": batched_config(args, specs, arena_len, world),
         "batched_ms": b_ms, "clara_ms": float(np.mean(ct)),
         "instances_per_s": len(specs) / (b_ms / 1e3),
         "batched_swaps": int(r["swaps"].sum()), "batched_passes": int(r["iterations"].sum()),
@@ -374,6 +373,10 @@ def run_batched(args, rank, world, local_rank):
                      "peak_source": pk, "traffic": None},
         "clocks": ck, "e2e": e2e, "gpu_launches": launches,
     }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cb = oracle_batched(specs, args.cpu_seconds)
+        cb.pop("seconds")
+        line["cpu_baseline"] = cb
     return line
 
 
@@ -550,6 +553,42 @@ def cpu_baseline(D, spec, budget_s):
                       % (steps, passes, n, k, dt)}
 
 
+BATCHED_METRIC = "SWAP dTD point-evals/sec + full PAM run time (k=100/200); % HBM roofline"
+
+
+def batched_config(args, specs, arena_len, world):
+    if arena_len is None:
+        arena_len = sum(n * ((n + 3) // 4 * 4) for n, _ in specs)
+    return {"workload": args.workload + ": " + WORKLOADS[args.workload]["desc"],
+            "instances": len(specs), "arena_bytes": int(arena_len * 4),
+            "l2": "arena %.1f GB > L2 (129 MB): no flush needed" % (arena_len * 4 / 1e9),
+            "parallelism": "replicas" if world > 1 else "single GPU"}
+
+
+def oracle_batched(specs, budget_s):
+    """The FP64 oracle's BUILD + FastPAM1 on the batch's instances in order
+    until about budget_s seconds of solver time (matrix construction not
+    timed, as on the GPU side where the arena is built before the step)."""
+    import oracle
+    from paper_2008_05171_gb300 import workloads as wl
+    head = specs[:64]
+    P, offs = wl.batched_points(head, d=8)
+    ev, el, done = 0, 0.0, 0
+    for (n, k), o in zip(head, offs):
+        D = oracle.euclid_f32(P[o:o + n])
+        t0 = time.perf_counter()
+        r = oracle.run(D, k, variant="fastpam1")
+        el += time.perf_counter() - t0
+        ev += sum((n - t) * n for t in range(k)) + r["iterations"] * (n - k) * n
+        done += 1
+        if el >= budget_s:
+            break
+    return {"value": ev / el, "unit": "point-evals/s", "cores": oracle.num_threads(),
+            "kind": "oracle", "seconds": el,
+            "sample": "BUILD + FastPAM1 on the first %d of the %d instances (FP64 C oracle, "
+                      "OpenMP over candidates), %.1f s of solver time" % (done, len(specs), el)}
+
+
 def run_reference(args, rank, world):
     """The oracle as the reference arm: timed on the host cores on a bounded
     sample of the workload per step (rank 0 only)."""
@@ -560,31 +599,21 @@ def run_reference(args, rank, world):
     from paper_2008_05171_gb300 import workloads as wl
     if args.workload.startswith("batched"):
         # the oracle on the first instances of the batch (bounded sample)
-        import oracle
-        specs = wl.batched_specs(512)[:6]
-        P, offs = wl.batched_points(specs, d=8)
-        vals, secs = [], []
+        vals, secs, cb = [], [], None
         for _ in range(args.warmup + args.steps):
-            t0 = time.perf_counter()
-            ev = 0
-            for (n, k), o in zip(specs, offs):
-                D = oracle.euclid_f32(P[o:o + n])
-                r = oracle.run(D, k, variant="fastpam1")
-                ev += sum((n - t) * n for t in range(k)) + r["iterations"] * (n - k) * n
-            dt = time.perf_counter() - t0
-            vals.append(ev / dt)
-            secs.append(dt)
+            cb = oracle_batched(wl.batched_specs(512), 8.0)
+            vals.append(cb["value"])
+            secs.append(cb["seconds"])
         v = float(np.mean(vals[args.warmup:]))
-        cb = {"value": v, "unit": "point-evals/s", "cores": oracle.num_threads(),
-              "kind": "oracle", "sample": "BUILD + FastPAM1 on the first 6 of the 512 "
-              "instances (FP64 C oracle)"}
-        return {"impl": "reference", "metric": "SWAP dTD point-evals/sec + full PAM run time "
-                "(k=100/200); % HBM roofline", "value": v, "unit": "point-evals/s",
+        cb = dict(cb, value=v)
+        cb.pop("seconds")
+        return {"impl": "reference", "metric": BATCHED_METRIC, "value": v, "unit": "point-evals/s",
                 "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
                 "ms_per_step": 1e3 * float(np.mean(secs[args.warmup:])),
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                 "dtype": "f64", "data": "synthetic",
-                "config": {"workload": args.workload}, "cpu_baseline": cb,
+                "config": batched_config(args, wl.batched_specs(512), None, world),
+                "cpu_baseline": cb,
                 "e2e": {"value": v, "unit": "point-evals/s", "h2d_bytes_per_step": 0,
                         "d2h_bytes_per_step": 0}}
     X = getattr(wl, spec["recipe"])()
@@ -630,7 +659,20 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    # smaller cases of the same recipes, for profiler captures only
+    ap.add_argument("--n", type=int, default=None, help="features_*: number of points")
+    ap.add_argument("--k", type=int, default=None, help="features_*: number of medoids")
+    ap.add_argument("--instances", type=int, default=None,
+                    help="batched_*: first INSTANCES instances of the batch")
     args = ap.parse_args()
+    spec = WORKLOADS[args.workload]
+    if args.workload.startswith("features") and (args.n or args.k):
+        n, k = args.n or spec["n"], args.k or spec["k"]
+        WORKLOADS[args.workload] = dict(spec, n=n, k=k, desc=spec["desc"] +
+                                        " [reduced to n=%d k=%d for profiling]" % (n, k))
+    if args.workload.startswith("batched") and args.instances:
+        WORKLOADS[args.workload] = dict(spec, desc=spec["desc"] +
+                                        " [first %d instances, for profiling]" % args.instances)
     if args.warmup < 3:
         args.warmup = 3
     world = int(os.environ.get("WORLD_SIZE", "1"))

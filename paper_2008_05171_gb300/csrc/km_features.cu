@@ -13,7 +13,7 @@
 //   warp 1      allocates tensor memory and issues the tcgen05 MMAs:
 //               G = X_c X_o^T, BF16 inputs, FP32 accumulation, into one of
 //               four 128-column TMEM accumulators;
-//   warps 2-9   epilogue, two warpgroups of 64 columns each: read G from
+//   warps 2-17  epilogue, four warpgroups of 32 columns each: read G from
 //               TMEM and test every pair against its point's threshold,
 //               d(o,c)^2 < d^2(o)  <=>  g - |x_c|^2/2 > (|x_o|^2 - d^2(o))/2,
 //               one add and one compare per pair into a 16-bit lane mask;
@@ -43,7 +43,7 @@
 
 namespace km {
 
-constexpr int kFeatEpiWarps = 8;
+constexpr int kFeatEpiWarps = 16;
 constexpr int kFeatThreads = (2 + kFeatEpiWarps) * 32;
 constexpr int kFeatMaxK = 224;       // shared accumulators: 128 x k x 4 B
 constexpr int kFeatMaxD = 256;
@@ -104,7 +104,7 @@ __host__ __device__ inline FeatLayout feat_layout(int d, int k) {
   L.acc = o;
   o += 4 * (size_t)kTileM * k;
   L.red = o;
-  o += 8 * (size_t)kTileM;
+  o += 8 * (size_t)kTileM * (kFeatEpiWarps / 4 - 1);
   o = (o + 127) / 128 * 128;
   L.meta = o;
   L.meta_bytes = 5 * 4 * kTileN;
@@ -332,11 +332,11 @@ __global__ void __launch_bounds__(kFeatThreads, 1) k_feat_pass(const FeatArgs a)
     }
   } else {
     // ============================================================ epilogue
-    const int ew = warp - 2;              // 0..7
+    const int ew = warp - 2;              // 0..15
     const int quarter = warp & 3;         // TMEM lanes 32*quarter..+31
-    const int group = ew >> 2;            // columns 64*group..+63
+    const int group = ew >> 2;            // columns 32*group..+31
     const int r = quarter * 32 + lane;    // candidate row within the tile
-    const int col0 = group * 64;
+    const int col0 = group * 32;
     float* arow = acc + (size_t)r * k;
     uint32_t eph = 0;
     long long gb = 0;
@@ -363,14 +363,9 @@ __global__ void __launch_bounds__(kFeatThreads, 1) k_feat_pass(const FeatArgs a)
           break;
         }
         tc_fence_after();
-        float v[64];
-        {
-          const uint32_t ta = tmem + ((uint32_t)(quarter * 32) << 16) +
-                              (uint32_t)(buf * kTileN + col0);
-          tmem_ld32(ta, *reinterpret_cast<float(*)[32]>(v));
-          tmem_ld32(ta + 32, *reinterpret_cast<float(*)[32]>(v + 32));
-          tmem_ld_wait();
-        }
+        float v[32];
+        tmem_ld32(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(buf * kTileN + col0), v);
+        tmem_ld_wait();
         tc_fence_before();
         __syncwarp();
         if (lane == 0) mbar_arrive(&acc_empty[buf]);
@@ -399,13 +394,13 @@ __global__ void __launch_bounds__(kFeatThreads, 1) k_feat_pass(const FeatArgs a)
         if (MODE == kModeBuild && a.build_first) {
           const int colg = b * kTileN + col0;
 #pragma unroll
-          for (int j = 0; j < 64; ++j) {
+          for (int j = 0; j < 32; ++j) {
             const float d2 = fmaf(-2.f, v[j], nc + m_no[col0 + j]);
             kahan_addf(ks_, kc_, (colg + j < n) ? sqrtf(fmaxf(d2, 0.f)) : 0.f);
           }
         } else {
 #pragma unroll
-          for (int g16 = 0; g16 < 4; ++g16) {
+          for (int g16 = 0; g16 < 2; ++g16) {
             // fast path: one add and one compare per pair into a lane mask
             unsigned mask = 0;
 #pragma unroll
@@ -439,13 +434,14 @@ __global__ void __launch_bounds__(kFeatThreads, 1) k_feat_pass(const FeatArgs a)
       }
       if (!ok) break;
       // ------------------------------------------------------ tile finished
-      if (group == 1) red[r] = (double)ks_ - (double)kc_;
+      if (group > 0) red[(group - 1) * kTileM + r] = (double)ks_ - (double)kc_;
       if (!cons_sync(ep_bar, eph, abort_flag)) {
         ok = false;
         break;
       }
       if (group == 0) {
-        const double shared_part = ((double)ks_ - (double)kc_) + red[r];
+        double shared_part = (double)ks_ - (double)kc_;
+        for (int g = 0; g < kFeatEpiWarps / 4 - 1; ++g) shared_part += red[g * kTileM + r];
         if (MODE == kModeSwap) {
           if (cvalid) {
             double best = 1e300;
