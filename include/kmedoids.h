@@ -88,10 +88,20 @@ typedef struct km_options {
   int32_t rows_per_tile;  /* candidate rows per CTA tile; 0 = automatic */
   int32_t profile;        /* nonzero: time kernels with CUDA events */
   int32_t trace_capacity; /* entries available in the trace arrays */
-  int32_t tune;           /* kernel geometry override for tuning sweeps:
-                             0 = automatic, 1..16 = a fixed (tile rows,
-                             stages, CTAs per SM) entry of the library's
-                             table; KM_E_UNSUPPORTED if it does not fit */
+  int32_t tune;           /* matrix-form kernel geometry (tile rows, ring
+                             stages, CTAs per SM):
+                             0 = automatic (the library's preference
+                               order, measured on GB300 at n = 20000 and
+                               50000);
+                             -1 = measured: the first call for a given
+                               (device, dtype, BUILD/SWAP, variant, n, k)
+                               times one pass of every table entry that
+                               fits on the caller's matrix and keeps the
+                               fastest for the rest of the process (costs
+                               three passes per entry once; results do not
+                               depend on the geometry);
+                             1..16 = a fixed table entry;
+                             KM_E_UNSUPPORTED if it does not fit */
   /* HOST arrays (may be NULL) receiving every applied swap in order. */
   double *trace_delta;
   int32_t *trace_slot;
@@ -122,7 +132,8 @@ typedef struct km_result {
   double build_eval_ms;   /* sum over the BUILD evaluation kernel launches */
   int64_t kernel_launches; /* kernels this call launched (all phases) */
   int32_t best_sample;     /* kmedoids_clara: index of the winning sample */
-  int32_t reserved1;
+  int16_t swap_geometry;   /* geometry table entries (1..16) the SWAP and */
+  int16_t build_geometry;  /* BUILD passes ran with; 0 = not run */
 } km_result;
 
 /* Fill *o with the defaults (FastPAM1, tol 0, automatic tiles). */

@@ -8,7 +8,10 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include "../../include/kmedoids.h"
@@ -109,6 +112,7 @@ struct Ctx {
   long long launches = 0;
   int fshift = 0;
   bool scanned = false;
+  int swap_geom = 0, build_geom = 0;  // geometry table entries used
   KmState* st() const { return reinterpret_cast<KmState*>(ws + L.st); }
   template <class P>
   P* at(size_t off) const {
@@ -138,7 +142,7 @@ km_status check_common(const void* D, int32_t dtype, int64_t n, int64_t ld, int3
       c->opt.rows_per_tile != 4 && c->opt.rows_per_tile != 8 && c->opt.rows_per_tile != 16)
     return fail(KM_E_INVALID, "rows_per_tile must be 0, 1, 2, 4, 8 or 16");
   if (c->opt.trace_capacity < 0) return fail(KM_E_INVALID, "trace_capacity < 0");
-  if (c->opt.tune < 0 || c->opt.tune > 16) return fail(KM_E_INVALID, "tune must be in 0..16");
+  if (c->opt.tune < -1 || c->opt.tune > 16) return fail(KM_E_INVALID, "tune must be in -1..16");
   if (!make_ws(n, k, &c->opt, &c->L)) return fail(KM_E_INVALID, "invalid sizes");
   if (ws_bytes < c->L.total)
     return fail(KM_E_WORKSPACE, "workspace too small: %zu < %zu bytes", ws_bytes, c->L.total);
@@ -268,14 +272,87 @@ km_status reset_state(const Ctx& c) {
   return KM_OK;
 }
 
+// ------------------------------------------------------------- autotuning
+// tune = -1: the first call for a (device, dtype, mode, variant, n, k) times
+// one pass of every geometry of the table that fits, on the caller's own
+// matrix and state, and keeps the fastest for the rest of the process.  The
+// state record is restored before every timed pass, so the passes leave no
+// trace; results do not depend on the geometry (exact sums, total orders).
+std::mutex g_tune_mu;
+std::map<std::tuple<int, int, int, int, int, int>, int> g_tune;
+
+km_status config_for(Ctx& c, int mode, int flavour, const StreamArgs& sa, StreamConfig* cfg) {
+  const char* what = (mode == kModeSwap) ? "SWAP" : "BUILD";
+  if (c.opt.tune >= 0) {
+    if (!stream_config(mode, c.k, flavour, c.opt.rows_per_tile, c.opt.tune, cfg))
+      return fail(KM_E_UNSUPPORTED, "no %s kernel configuration fits (k=%d, tune=%d)", what, c.k,
+                  c.opt.tune);
+    return KM_OK;
+  }
+  int dev = 0;
+  KM_CUDA(cudaGetDevice(&dev));
+  const auto key = std::make_tuple(dev, c.dtype, mode, flavour, c.n, c.k * 64 + c.opt.rows_per_tile);
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune.find(key);
+    if (it != g_tune.end() && stream_config(mode, c.k, flavour, 0, it->second, cfg)) return KM_OK;
+  }
+  KmState saved;
+  km_status r = read_state(c, &saved);
+  if (r != KM_OK) return r;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  KM_CUDA(cudaEventCreate(&e0));
+  KM_CUDA(cudaEventCreate(&e1));
+  int best = 0;
+  float best_ms = 0.f;
+  for (int g = 1; g <= 16; ++g) {
+    StreamConfig cg;
+    if (!stream_config(mode, c.k, flavour, 0, g, &cg)) continue;
+    if (c.opt.rows_per_tile > 0 && cg.rows != c.opt.rows_per_tile) continue;
+    StreamArgs a = sa;
+    a.win_rows = cg.rows;
+    const int grid = grid_for(c, cg);
+    float tmin = 0.f;
+    for (int rep = 0; rep < 3; ++rep) {  // one warm-up, then the faster of two
+      KM_CUDA(cudaMemcpyAsync(c.st(), &saved, sizeof(saved), cudaMemcpyHostToDevice, c.s));
+      KM_CUDA(cudaEventRecord(e0, c.s));
+      KM_LAUNCH(c, launch_stream(c.dtype, mode, cg, grid, a, c.s));
+      KM_CUDA(cudaEventRecord(e1, c.s));
+      KmState chk;
+      r = read_state(c, &chk);  // synchronises; reports a device timeout
+      if (r != KM_OK) break;
+      float ms = 0.f;
+      KM_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+      if (rep == 1 || (rep == 2 && ms < tmin)) tmin = ms;
+    }
+    if (r != KM_OK) break;
+    if (best == 0 || tmin < best_ms) {
+      best = g;
+      best_ms = tmin;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (r != KM_OK) return r;
+  KM_CUDA(cudaMemcpyAsync(c.st(), &saved, sizeof(saved), cudaMemcpyHostToDevice, c.s));
+  KM_CUDA(cudaStreamSynchronize(c.s));
+  if (best == 0 || !stream_config(mode, c.k, flavour, 0, best, cfg))
+    return fail(KM_E_UNSUPPORTED, "no %s kernel configuration fits (k=%d)", what, c.k);
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tune[key] = best;
+  return KM_OK;
+}
+
 // ------------------------------------------------------------------ BUILD
 km_status do_build(Ctx& c, Timer& tm, std::vector<std::pair<int, int>>& ev, km_result* res) {
   KM_CUDA(cudaMemsetAsync(c.at<void>(c.L.is_med), 0, (size_t)c.L.n_pad, c.s));
-  StreamConfig cfg;
-  if (!stream_config(kModeBuild, c.k, 0, c.opt.rows_per_tile, c.opt.tune, &cfg))
-    return fail(KM_E_UNSUPPORTED, "no BUILD kernel configuration fits");
-  const int grid = grid_for(c, cfg);
   StreamArgs sa = stream_args(c);
+  sa.build_first = 1;
+  StreamConfig cfg;
+  km_status r = config_for(c, kModeBuild, 0, sa, &cfg);
+  if (r != KM_OK) return r;
+  c.build_geom = cfg.geometry;
+  const int grid = grid_for(c, cfg);
   PointArgs pa = point_args(c);
   for (int step = 0; step < c.k; ++step) {
     sa.build_first = (step == 0);
@@ -386,17 +463,18 @@ km_status do_swap(Ctx& c, Timer& tm, std::vector<std::pair<int, int>>& ev, KmSta
   if (c.k == 1) return swap_k1(c, h);
   const int variant = c.opt.variant;
   const int flavour = variant == KM_FASTPAM2 ? kFastPAM2 : (variant == KM_FASTERPAM ? kFasterPAM : kFastPAM1);
-  StreamConfig cfg;
-  if (!stream_config(kModeSwap, c.k, flavour, c.opt.rows_per_tile, c.opt.tune, &cfg))
-    return fail(KM_E_UNSUPPORTED, "k=%d too large for the SWAP kernel's shared memory", c.k);
-  const int grid = grid_for(c, cfg);
   StreamArgs sa = stream_args(c);
   sa.flavour = flavour;
-  sa.win_rows = cfg.rows;
   if (flavour == kFasterPAM) {  // per-position results of a scan window
     sa.cand_delta = c.at<double>(c.L.win_delta);
     sa.cand_slot = c.at<int32_t>(c.L.win_slot);
   }
+  StreamConfig cfg;
+  r = config_for(c, kModeSwap, flavour, sa, &cfg);
+  if (r != KM_OK) return r;
+  c.swap_geom = cfg.geometry;
+  sa.win_rows = cfg.rows;
+  const int grid = grid_for(c, cfg);
   PointArgs pa = point_args(c);
   const int max_iter = c.opt.max_iter;
 
@@ -445,13 +523,6 @@ km_status do_swap(Ctx& c, Timer& tm, std::vector<std::pair<int, int>>& ev, KmSta
   }
   (void)res;
   return KM_OK;
-}
-
-void fill_result(const Ctx& c, const KmState& h, km_result* res) {
-  if (!res) return;
-  res->iterations = h.iter;
-  res->swaps = h.swaps;
-  res->td_bookkept = (c.dtype == KM_I32) ? (double)h.td_book_i : h.td_book_d;
 }
 
 km_status finish(Ctx& c, KmState* h, int32_t* medoids_out, int32_t* labels_out, km_result* res,
@@ -650,6 +721,8 @@ static km_status run_impl(bool do_b, bool do_s, const void* D, int32_t dtype, in
     }
     res->status = conv;
     res->kernel_launches = c.launches;
+    res->swap_geometry = (int16_t)c.swap_geom;
+    res->build_geometry = (int16_t)c.build_geom;
   }
   if (conv != KM_OK) fail(conv, "max_iter (%d) reached before convergence", c.opt.max_iter);
   return conv;

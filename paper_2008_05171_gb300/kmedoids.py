@@ -61,7 +61,8 @@ class km_result(ctypes.Structure):
                 ("build_launches", ctypes.c_int32),
                 ("build_eval_ms", ctypes.c_double),
                 ("kernel_launches", ctypes.c_int64),
-                ("best_sample", ctypes.c_int32), ("reserved1", ctypes.c_int32)]
+                ("best_sample", ctypes.c_int32), ("swap_geometry", ctypes.c_int16),
+                ("build_geometry", ctypes.c_int16)]
 
 
 _LOCK = threading.Lock()

@@ -73,11 +73,11 @@ def test_invalid_arguments_return_status(lib):
                               None)
         assert st == want, (D, dt, n, ld, k, st)
         assert lib.kmedoids_last_error()
-    bad = km.options(variant=9)
-    st = lib.kmedoids_run(P(fake), 1, 100, 100, 10, P(fake), None,
-                          ctypes.byref(bad), ctypes.byref(res), P(fake), 1 << 30,
-                          None)
-    assert st == 1
+    for bad in (km.options(variant=9), km.options(tune=-2), km.options(tune=17)):
+        st = lib.kmedoids_run(P(fake), 1, 100, 100, 10, P(fake), None,
+                              ctypes.byref(bad), ctypes.byref(res), P(fake), 1 << 30,
+                              None)
+        assert st == 1
 
 
 def test_version(lib):

@@ -322,3 +322,22 @@ def test_stream_and_workspace_reuse():
     s.synchronize()
     assert a["medoids"].cpu().tolist() == b["medoids"].cpu().tolist()
     assert a["td_i64"] == b["td_i64"]
+
+
+@pytest.mark.parametrize("variant", ["fastpam1", "fasterpam", "fastpam2"])
+def test_measured_geometry_same_result(variant):
+    """tune = -1 times every geometry that fits on the first call for a shape
+    and keeps the fastest; the result equals the automatic choice's (exact
+    sums, total orders), the chosen entries are reported, and a second call
+    reuses them."""
+    Dh = int_instance(3000, ("tune", variant))
+    D = dev(Dh)
+    a = km.run(D, 12, variant=variant)
+    b = km.run(D, 12, variant=variant, tune=-1)
+    c = km.run(D, 12, variant=variant, tune=-1)
+    for r in (b, c):
+        assert r["medoids"].cpu().tolist() == a["medoids"].cpu().tolist()
+        assert r["td_i64"] == a["td_i64"] and r["swaps"] == a["swaps"]
+        assert 1 <= r["swap_geometry"] <= 16 and 1 <= r["build_geometry"] <= 16
+    assert (b["swap_geometry"], b["build_geometry"]) == (c["swap_geometry"], c["build_geometry"])
+    assert c["kernel_launches"] < b["kernel_launches"]  # no timing passes the second time
