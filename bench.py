@@ -76,10 +76,10 @@ def tensor_peak():
     return 1700.0, "fallback sustained"
 
 
-def source_hash():
+def source_hash(files=("km_stream.cu", "km_device.cuh")):
     import hashlib
     h = hashlib.sha256()
-    for f in ("km_stream.cu", "km_device.cuh"):
+    for f in files:
         with open(os.path.join(ROOT, "paper_2008_05171_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -356,6 +356,13 @@ def run_batched(args, rank, world, local_rank):
     b_ms = float(np.mean(bt))
     peak, pk = peaks()
     ach = bytes_b / (b_ms / 1e3) / 1e9
+    # DRAM traffic per launch: the ratio of DRAM bytes to algorithmic bytes
+    # from one ncu capture of a smaller batch (traffic is proportional to the
+    # rows streamed), applied to this launch; null once the kernel changed
+    traffic = None
+    ent = (load_json(os.path.join(ROOT, "profiles", "traffic.json")) or {}).get("batch_pam")
+    if ent and ent.get("source_hash") == source_hash(("km_batched.cu", "km_device.cuh")):
+        traffic = round(ent["dram_bytes_per_algorithmic_byte"] * bytes_b)
     line = {
         "metric": BATCHED_METRIC,
         "value": value, "unit": "point-evals/s", "n_gpus": world, "steps": args.steps,
@@ -370,7 +377,7 @@ def run_batched(args, rank, world, local_rank):
         "roofline": {"bound": "hbm", "achieved": round(ach, 1), "peak": peak, "unit": "GB/s",
                      "frac": round(ach / peak, 4), "kernel": "k_batch_pam<16>",
                      "algorithmic_bytes_per_launch": bytes_b, "avg_launch_ms": round(b_ms, 3),
-                     "peak_source": pk, "traffic": None},
+                     "peak_source": pk, "traffic": traffic},
         "clocks": ck, "e2e": e2e, "gpu_launches": launches,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -399,7 +406,7 @@ def run_ours(args, rank, world, local_rank):
     # tune=-1: the first (warm-up) call times every kernel geometry that fits
     # on this matrix and the library keeps the fastest for the timed steps
     def step(profile=True):
-        return km.run(D, k, ws=ws, labels=True, profile=profile, tune=-1)
+        return km.run(D, k, ws=ws, labels=True, profile=profile, tune=args.tune)
 
     for _ in range(args.warmup):
         step()
@@ -480,7 +487,7 @@ def run_ours(args, rank, world, local_rank):
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             a.record(stream)
             Dd.copy_(Dh, non_blocking=True)
-            r = km.run(Dd, k, ws=ws, labels=True, tune=-1)
+            r = km.run(Dd, k, ws=ws, labels=True, tune=args.tune)
             med_h.copy_(r["medoids"], non_blocking=True)
             lab_h.copy_(r["labels"], non_blocking=True)
             b.record(stream)
@@ -505,7 +512,9 @@ def run_ours(args, rank, world, local_rank):
                    "n": n, "k": k, "matrix_bytes": int(D.numel() * 4),
                    "geometry": {"swap": int(r0["swap_geometry"]),
                                 "build": int(r0["build_geometry"]),
-                                "picked_by": "measured on the first call (tune=-1)"},
+                                "picked_by": {-1: "measured on the first call (tune=-1)",
+                                              0: "preference order (tune=0)"}.get(
+                                                  args.tune, "fixed (tune=%d)" % args.tune)},
                    "l2": "matrix larger than L2 (no flush needed)",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "full_run_ms": total_ms / args.steps,
@@ -556,7 +565,36 @@ def cpu_baseline(D, spec, budget_s):
             "kind": "oracle",
             "sample": "%d BUILD steps + %d FastPAM1 evaluation passes of the same "
                       "n=%d k=%d matrix (FP64 C oracle, OpenMP over candidates), %.1f s"
-                      % (steps, passes, n, k, dt)}
+                      % (steps, passes, n, k, dt),
+            "pam_vs_fastpam1": pam_vs_fastpam1(Dh, med, threads)}
+
+
+def pam_vs_fastpam1(Dh, med, threads, n_sub=4000):
+    """One SWAP evaluation pass of original PAM (Eq. (5): every (medoid,
+    candidate) pair summed over all points) and of FastPAM1 (Eq. (7)) with
+    the oracle on the first n_sub points and the first medoids among them:
+    the same-host speedup the paper quotes for the O(k) improvement.  Also
+    FastPAM1 on one thread."""
+    import oracle
+    Ds = np.ascontiguousarray(Dh[:n_sub, :n_sub])
+    k = len(med)
+    sub = [int(m) for m in med if m < n_sub][:k]
+    sub += [i for i in range(n_sub) if i not in set(sub)][:k - len(sub)]
+    sub = np.array(sub, np.int32)
+    out = {"n": n_sub, "k": k, "threads": threads}
+    for name, method in (("pam_pass_s", "pam"), ("fastpam1_pass_s", "fastpam1")):
+        t0 = time.perf_counter()
+        oracle.eval_swaps(Ds, sub, method=method)
+        out[name] = time.perf_counter() - t0
+    oracle.set_threads(1)
+    try:
+        t0 = time.perf_counter()
+        oracle.eval_swaps(Ds, sub, method="fastpam1")
+        out["fastpam1_pass_1thread_s"] = time.perf_counter() - t0
+    finally:
+        oracle.set_threads(threads)
+    out["speedup_pam_over_fastpam1"] = out["pam_pass_s"] / out["fastpam1_pass_s"]
+    return out
 
 
 BATCHED_METRIC = "SWAP dTD point-evals/sec + full PAM run time (k=100/200); % HBM roofline"
@@ -670,6 +708,9 @@ def main():
     ap.add_argument("--k", type=int, default=None, help="features_*: number of medoids")
     ap.add_argument("--instances", type=int, default=None,
                     help="batched_*: first INSTANCES instances of the batch")
+    ap.add_argument("--tune", type=int, default=-1,
+                    help="matrix workloads: kernel geometry (-1 measured on the first "
+                         "call, 0 the library's preference order, 1..16 fixed)")
     args = ap.parse_args()
     spec = WORKLOADS[args.workload]
     if args.workload.startswith("features") and (args.n or args.k):

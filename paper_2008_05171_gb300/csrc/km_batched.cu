@@ -16,6 +16,7 @@
 // assigned to each sample's medoids (FP32 direct differences, FP64 TD sum)
 // and the sample with the least TD wins (lowest index on ties).
 #include <algorithm>
+#include <cstddef>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -116,15 +117,18 @@ __global__ void __launch_bounds__(256) k_batch_order(const km_instance* inst, in
 
 // Per-warp cp.async ring: every warp streams its own candidate rows through
 // kRingStages stages of 512 columns (32 lanes x 4 float4), so each SM keeps
-// up to WARPS x (kRingStages - 1) x 2 KB of row data in flight.
+// up to WARPS x (kRingStages - 1) x 2 KB of row data in flight.  (One 1-D
+// bulk copy per stage issued by lane 0, with an mbarrier per stage, measured
+// 14 % slower on GB300 than these per-lane 16-byte copies.)
 constexpr int kRingStages = 4;
 constexpr int kRingFloats = 512;
 
+// dn, ds and the ring are read as float4: keep them 16-byte aligned.
 template <int WARPS>
 struct BatchSmem {
-  float ring[WARPS][kRingStages][kRingFloats];
-  float dn[kBatchMaxN];
-  float ds[kBatchMaxN];
+  alignas(16) float ring[WARPS][kRingStages][kRingFloats];
+  alignas(16) float dn[kBatchMaxN];
+  alignas(16) float ds[kBatchMaxN];
   uint8_t near[kBatchMaxN];
   uint8_t is_med[kBatchMaxN];
   int32_t med[kBatchMaxK];
@@ -141,6 +145,10 @@ struct BatchSmem {
   double dstar;
   long long dstar_i;
 };
+
+static_assert(offsetof(BatchSmem<16>, dn) % 16 == 0 && offsetof(BatchSmem<16>, ds) % 16 == 0 &&
+                  offsetof(BatchSmem<8>, dn) % 16 == 0 && offsetof(BatchSmem<8>, ds) % 16 == 0,
+              "float4 reads of d_n / d_s need 16-byte alignment");
 
 __device__ __forceinline__ void kahan_add(float& s, float& c, float x) {
   const float y = x - c;

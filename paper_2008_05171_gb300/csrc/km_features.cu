@@ -16,7 +16,8 @@
 //   warps 2-17  epilogue, four warpgroups of 32 columns each: read G from
 //               TMEM and test every pair against its point's threshold,
 //               d(o,c)^2 < d^2(o)  <=>  g - |x_c|^2/2 > (|x_o|^2 - d^2(o))/2,
-//               one add and one compare per pair into a 16-bit lane mask;
+//               as the sign of (thr + |x_c|^2/2) - g funnel-shifted into a
+//               16-bit lane mask (two adds and one shift per pair);
 //               the pairs that pass (rare) are walked lane by lane (or, in
 //               a group where some lane has many, with predication) and
 //               take d = sqrt(|x_c|^2 + |x_o|^2 - 2 g):
@@ -401,15 +402,18 @@ __global__ void __launch_bounds__(kFeatThreads, 1) k_feat_pass(const FeatArgs a)
         } else {
 #pragma unroll
           for (int g16 = 0; g16 < 2; ++g16) {
-            // fast path: one add and one compare per pair into a lane mask
+            // fast path: bit j of the lane mask is the sign of
+            // (thr[o] + |x_c|^2/2) - g for column j (set: a hit), shifted in
+            // from column 15 down to 0 with one funnel shift per pair
             unsigned mask = 0;
 #pragma unroll
-            for (int q = 0; q < 16; q += 4) {
+            for (int q = 12; q >= 0; q -= 4) {
               const float4 t4 = *reinterpret_cast<const float4*>(m_thr + col0 + g16 * 16 + q);
-              mask |= (v[g16 * 16 + q + 0] - hc > t4.x) ? (1u << (q + 0)) : 0u;
-              mask |= (v[g16 * 16 + q + 1] - hc > t4.y) ? (1u << (q + 1)) : 0u;
-              mask |= (v[g16 * 16 + q + 2] - hc > t4.z) ? (1u << (q + 2)) : 0u;
-              mask |= (v[g16 * 16 + q + 3] - hc > t4.w) ? (1u << (q + 3)) : 0u;
+              const float* vq = v + g16 * 16 + q;
+              mask = __funnelshift_l(__float_as_uint((t4.w + hc) - vq[3]), mask, 1);
+              mask = __funnelshift_l(__float_as_uint((t4.z + hc) - vq[2]), mask, 1);
+              mask = __funnelshift_l(__float_as_uint((t4.y + hc) - vq[1]), mask, 1);
+              mask = __funnelshift_l(__float_as_uint((t4.x + hc) - vq[0]), mask, 1);
             }
             const unsigned most = __reduce_max_sync(0xffffffffu, (unsigned)__popc(mask));
             if (most == 0) continue;
