@@ -85,6 +85,22 @@ def source_hash(files=("km_stream.cu", "km_device.cuh")):
     return h.hexdigest()[:16]
 
 
+def max_over_ranks(ms, world, device):
+    """Slowest rank's time: the timed region ends when every rank is done."""
+    if world <= 1:
+        return float(ms)
+    import torch
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world):
+    if world > 1:
+        import torch
+        torch.distributed.barrier()
+
+
 class Clocks:
     """nvidia-smi sampling during the timed region."""
 
@@ -175,8 +191,7 @@ def run_features(args, rank, world, local_rank):
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
-    if world > 1:
-        torch.distributed.barrier()
+    barrier(world)
     clocks = Clocks(local_rank)
     clocks.start()
     stream = torch.cuda.current_stream()
@@ -190,11 +205,7 @@ def run_features(args, rank, world, local_rank):
         ev[i][1].record(stream)
     torch.cuda.synchronize()
     ck = clocks.stop()
-    total_ms = float(sum(a.elapsed_time(b) for a, b in ev))
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in ev), world, dev)
     evals = [sum(evals_of(n, k, r)) for r in results]
     value = world * sum(evals) / (total_ms / 1e3)
     r0 = results[-1]
@@ -292,13 +303,15 @@ def run_batched(args, rank, world, local_rank):
 
     for _ in range(args.warmup):
         step()
+    torch.cuda.synchronize()
+    barrier(world)
     clocks = Clocks(local_rank)
     clocks.start()
     outs = [step() for _ in range(args.steps)]
     ck = clocks.stop()
     bt = [o[2] for o in outs]
     ct = [o[3] for o in outs]
-    total_ms = float(sum(bt) + sum(ct))
+    total_ms = max_over_ranks(sum(bt) + sum(ct), world, dev)
     r = outs[-1][0]
     ev_b = 0
     bytes_b = 0
@@ -411,8 +424,7 @@ def run_ours(args, rank, world, local_rank):
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
-    if world > 1:
-        torch.distributed.barrier()
+    barrier(world)
     clocks = Clocks(local_rank)
     clocks.start()
     stream = torch.cuda.current_stream()
@@ -429,11 +441,7 @@ def run_ours(args, rank, world, local_rank):
     wall = time.perf_counter() - t0
     ck = clocks.stop()
     step_ms = [a.elapsed_time(b) for a, b in ev]
-    total_ms = float(sum(step_ms))
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(sum(step_ms), world, dev)
 
     evals = [sum(evals_of(n, k, r)) for r in results]
     value = world * sum(evals) / (total_ms / 1e3)
@@ -645,7 +653,7 @@ def run_reference(args, rank, world):
         # the oracle on the first instances of the batch (bounded sample)
         vals, secs, cb = [], [], None
         for _ in range(args.warmup + args.steps):
-            cb = oracle_batched(wl.batched_specs(512), 8.0)
+            cb = oracle_batched(wl.batched_specs(512), min(8.0, args.cpu_seconds))
             vals.append(cb["value"])
             secs.append(cb["seconds"])
         v = float(np.mean(vals[args.warmup:]))
