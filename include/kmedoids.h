@@ -196,7 +196,7 @@ km_status kmedoids_cache(const void *D, int32_t dtype, int64_t n, int64_t ld,
 
 /* Tensor-core Gram product G = X X^T of bf16 feature vectors (tcgen05 MMA,
  * FP32 accumulation), the dot products behind the on-the-fly distances
- * d(o,c)^2 = |x_o|^2 + |x_c|^2 - 2 x_o.x_c (Sec. 4.9 notes that recomputing
+ * d(o,c)^2 = |x_o|^2 + |x_c|^2 - 2 x_o.x_c (Sec. 4.8 notes that recomputing
  * distances instead of storing the matrix is the memory-saving option).
  * X: n rows of ldx bf16 elements (DEVICE, 16-byte aligned, ldx % 8 == 0),
  * d = 16, 32, ..., 256 features.  G: n x n FP32 (DEVICE, row stride ldg).
@@ -282,7 +282,23 @@ km_status kmedoids_run_batched(const float *arena, const km_instance *inst,
                                const km_options *opts, void *ws,
                                size_t ws_bytes, void *stream);
 
-/* ---- CLARA (Sec. 2.2; FastCLARA, Sec. 3.3).  X: n points of d float32
+/* kmedoids_run_batched without BUILD: every instance starts from the k
+ * medoids the caller wrote at medoids_inout[inst[i].medoid_offset ...]
+ * (DEVICE) and runs FastPAM1 SWAP to convergence, the result replacing them.
+ * For restarts from random starts (the paper recommends uniform random
+ * initialisation with several restarts once swapping is cheap, Sec. 4.3
+ * and Sec. 6): several instances may share one matrix (same offset), one
+ * per starting set; the caller keeps the result with the least TD.
+ * Starting medoids out of range or repeated give that instance
+ * KM_E_INVALID.  Same limits, workspace and asynchrony as
+ * kmedoids_run_batched. */
+km_status kmedoids_swap_batched(const float *arena, const km_instance *inst,
+                                int32_t count, int32_t *medoids_inout,
+                                km_batch_result *results,
+                                const km_options *opts, void *ws,
+                                size_t ws_bytes, void *stream);
+
+/* ---- CLARA (Sec. 2.1; FastCLARA, Sec. 3.4).  X: n points of d float32
  * features (DEVICE, row-major).  sample_idx (DEVICE, samples x
  * sample_size int32): the caller's subsamples (the paper suggests
  * sample_size = 80 + 4k).  Each sample's Euclidean matrix is built in FP64

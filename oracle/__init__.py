@@ -18,7 +18,7 @@ k-Medoids Clustering" (arXiv 2008.05171):
 * ``swap_delta``    -- Delta of one (slot, candidate) swap by Eq. (5).
 * ``swap``          -- SWAP to convergence: PAM brute force / PAM cached /
                        FastPAM1 / FastPAM2 / FasterPAM (Alg. 4).
-* ``clara``         -- CLARA (Sec. 2.2, FastCLARA of Sec. 3.3) on given
+* ``clara``         -- CLARA (Sec. 2.1, FastCLARA of Sec. 3.4) on given
                        samples; ``euclid_f32`` the FP64 -> float32 matrix.
 
 Parity unpinned: FastPAM2's additional swaps (the paper describes FastPAM2
@@ -238,7 +238,7 @@ def euclid_f32(X, idx=None, ld=None):
 
 
 def clara(X, k, sample_idx):
-    """CLARA (Sec. 2.2 / 3.3): PAM (BUILD + FastPAM1) on each given sample,
+    """CLARA (Sec. 2.1 / 3.4): PAM (BUILD + FastPAM1) on each given sample,
     full-data TD of each, best sample kept.  Returns (medoids, labels,
     sample_tds, best_sample)."""
     X = np.ascontiguousarray(X, np.float32)

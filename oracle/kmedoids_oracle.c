@@ -689,7 +689,7 @@ void oracle_euclid_f32(const float *X, int64_t m, int d, const int64_t *idx,
 }
 
 /* ------------------------------------------------------------------------
- * CLARA (Sec. 2.2 "Variants and Extensions of PAM", Sec. 3.3 FastCLARA):
+ * CLARA (Sec. 2.1 "Variants and Extensions of PAM", Sec. 3.4 FastCLARA):
  * for each of `samples` subsamples of s points (indices given, drawn by the
  * caller), run PAM -- BUILD then FastPAM1 -- on the subsample's matrix,
  * assign every point of the full data set to its nearest medoid, and keep

@@ -1,10 +1,10 @@
 // km_batched.cu -- many independent PAM instances in one persistent launch,
-// and CLARA (Sec. 2.2; FastCLARA, Sec. 3.3) on top of it.
+// and CLARA (Sec. 2.1; FastCLARA, Sec. 3.4) on top of it.
 //
-// k_batch_pam: each CTA takes instances from an atomic queue (the host
-// orders them largest first) and runs the whole method on one instance:
-// BUILD (Alg. 1), the exact per-point cache, and FastPAM1 SWAP (Alg. 3,
-// Eq. (7)) to convergence, with every per-point quantity in shared memory
+// k_batch_pam: each CTA takes instances from an atomic queue (ordered
+// largest first) and runs the whole method on one instance: BUILD (Alg. 1)
+// or the caller's starting medoids (restarts from random starts), the exact
+// per-point cache, and FastPAM1 SWAP (Alg. 3, Eq. (7)) to convergence, with every per-point quantity in shared memory
 // and one warp per candidate row.  Float sums of the SWAP pass use the same
 // exact 64-bit fixed point as the single-instance kernels (scale from the
 // instance's largest entry, found during BUILD step 0).  Instances need
@@ -44,6 +44,7 @@ struct BatchArgs {
   int* error;
   int max_iter;
   double tol;
+  int start_given;           // 1: start from the medoids in `medoids` (no BUILD)
 };
 
 // Euclidean matrix of m points (FP64 differences, one rounding to FP32):
@@ -304,9 +305,51 @@ __global__ void __launch_bounds__(WARPS * 32, 1) k_batch_pam(const BatchArgs a) 
     }
     __syncthreads();
 
-    // ------------------------------------------------------------- BUILD
     unsigned mloc = 0;
-    for (int step = 0; step < k; ++step) {
+    if (a.start_given) {
+      // the largest entry over the whole matrix (fixed-point scale of the
+      // SWAP sums), streamed with no row marked as a medoid yet
+      stream_rows<WARPS>(
+          S, D, n, ld, warp, lane,
+          [&](int, int o, const float4(&v)[4], const float*) {
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+              const int p0 = o + 128 * u + 4 * lane;
+#pragma unroll
+              for (int t = 0; t < 4; ++t)
+                if (p0 + t < n) mloc = max(mloc, __float_as_uint(f4get(v[u], t)) & 0x7fffffffu);
+            }
+          },
+          [&](int) {});
+      for (int o = 16; o > 0; o >>= 1) mloc = max(mloc, __shfl_xor_sync(0xffffffffu, mloc, o));
+      if (lane == 0) S.wmax[warp] = mloc;
+      // the caller's starting medoids must be in range and distinct
+      if (tid == 0) {
+        int bad = 0;
+        for (int j = 0; j < k && !bad; ++j) {
+          const int m = a.medoids[in.medoid_offset + j];
+          if (m < 0 || m >= n || S.is_med[m]) {
+            bad = 1;
+          } else {
+            S.is_med[m] = 1;
+            S.med[j] = m;
+          }
+        }
+        S.cstar = bad;
+      }
+      __syncthreads();
+      if (S.cstar) {
+        if (tid == 0) {
+          res.status = KM_E_INVALID;
+          a.out[q] = res;
+        }
+        __syncthreads();
+        continue;
+      }
+    }
+
+    // ------------------------------------------------------------- BUILD
+    for (int step = 0; step < (a.start_given ? 0 : k); ++step) {
       double bd = 1e300;
       int bc = INT_MAX;
       float hs = 0.f, hc = 0.f, hs2 = 0.f, hc2 = 0.f;  // two compensated chains
@@ -757,10 +800,9 @@ extern "C" size_t kmedoids_batched_workspace_size(int32_t count) {
   return al256(256) + al256(4 * (size_t)count);
 }
 
-extern "C" km_status kmedoids_run_batched(const float* arena, const km_instance* inst,
-                                          int32_t count, int32_t* medoids_out,
-                                          km_batch_result* results, const km_options* opts,
-                                          void* ws, size_t ws_bytes, void* stream) {
+static km_status batched_impl(bool start_given, const float* arena, const km_instance* inst,
+                              int32_t count, int32_t* medoids_out, km_batch_result* results,
+                              const km_options* opts, void* ws, size_t ws_bytes, void* stream) {
   set_last_error("");
   if (!arena || !inst || !medoids_out || !results || !ws) return bfail(KM_E_INVALID, "NULL pointer");
   if (count <= 0 || count > kBatchMaxCount)
@@ -790,11 +832,27 @@ extern "C" km_status kmedoids_run_batched(const float* arena, const km_instance*
   a.queue = queue;
   a.max_iter = o.max_iter > 0 ? o.max_iter : 10000;
   a.tol = o.tol;
+  a.start_given = start_given ? 1 : 0;
   const int sms = device_sm_count();
   // tune: 0 automatic (16 warps per CTA), 1 = 8 warps, 2 = 16 warps
   const int cfg = (o.tune == 1) ? 0 : 1;
   BK(launch_batch_cfg(cfg, a, sms, s));
   return KM_OK;
+}
+
+extern "C" km_status kmedoids_run_batched(const float* arena, const km_instance* inst,
+                                          int32_t count, int32_t* medoids_out,
+                                          km_batch_result* results, const km_options* opts,
+                                          void* ws, size_t ws_bytes, void* stream) {
+  return batched_impl(false, arena, inst, count, medoids_out, results, opts, ws, ws_bytes, stream);
+}
+
+extern "C" km_status kmedoids_swap_batched(const float* arena, const km_instance* inst,
+                                           int32_t count, int32_t* medoids_inout,
+                                           km_batch_result* results, const km_options* opts,
+                                           void* ws, size_t ws_bytes, void* stream) {
+  return batched_impl(true, arena, inst, count, medoids_inout, results, opts, ws, ws_bytes,
+                      stream);
 }
 
 extern "C" km_status kmedoids_batched_distances(const float* points, int32_t dim,

@@ -2,7 +2,7 @@
 // (Alg. 1) and FastPAM1 SWAP (Alg. 3) over bf16 feature vectors with
 // Euclidean distances computed in every pass instead of read from an n x n
 // matrix (the paper computes distances on demand when the matrix does not
-// fit, Sec. 4.9).
+// fit, Sec. 4.8).
 //
 // Pass kernel k_feat_pass (one persistent CTA per SM, warp-specialised):
 //   warp 0      producer: 1-D bulk copies of a 128-candidate tile (A), of

@@ -27,7 +27,7 @@ EXPORTS = ["km_default_options", "kmedoids_workspace_size", "kmedoids_build",
            "kmedoids_features_workspace_size", "kmedoids_run_features",
            "kmedoids_swap_features", "kmedoids_batched_workspace_size",
            "kmedoids_batched_distances", "kmedoids_run_batched",
-           "kmedoids_clara_workspace_size", "kmedoids_clara"]
+           "kmedoids_swap_batched", "kmedoids_clara_workspace_size", "kmedoids_clara"]
 
 
 class KmError(RuntimeError):
@@ -116,8 +116,9 @@ def load(path: str = LIB_PATH):
         lib.kmedoids_batched_workspace_size.restype = sz
         lib.kmedoids_batched_distances.argtypes = [P, i32, P, P, i32, P, P]
         lib.kmedoids_batched_distances.restype = i32
-        lib.kmedoids_run_batched.argtypes = [P, P, i32, P, P, opt_p, P, sz, P]
-        lib.kmedoids_run_batched.restype = i32
+        for f in (lib.kmedoids_run_batched, lib.kmedoids_swap_batched):
+            f.argtypes = [P, P, i32, P, P, opt_p, P, sz, P]
+            f.restype = i32
         lib.kmedoids_clara_workspace_size.argtypes = [i32, i32, i32]
         lib.kmedoids_clara_workspace_size.restype = sz
         lib.kmedoids_clara.argtypes = [P, i64, i32, i32, i32, i32, P, P, P, P,
@@ -472,6 +473,24 @@ def run_batched(arena, inst_dev, total_medoids, **kw):
         count, ctypes.c_void_p(med.data_ptr()), ctypes.c_void_p(res.data_ptr()),
         ctypes.byref(o), ctypes.c_void_p(ws.data_ptr()), ws.numel(), _stream()))
     return med, res
+
+
+def swap_batched(arena, inst_dev, medoids, **kw):
+    """kmedoids_swap_batched: medoids (int32 CUDA tensor, every instance's k
+    starting medoids at its medoid_offset) is updated in place.  Returns
+    (medoids, results uint8 tensor)."""
+    torch = _torch()
+    lib = load()
+    count = inst_dev.numel() // 24
+    res = torch.empty(count * 24, dtype=torch.uint8, device=arena.device)
+    ws = torch.empty(lib.kmedoids_batched_workspace_size(count),
+                     dtype=torch.uint8, device=arena.device)
+    o = options(**kw)
+    _check(lib.kmedoids_swap_batched(
+        ctypes.c_void_p(arena.data_ptr()), ctypes.c_void_p(inst_dev.data_ptr()),
+        count, ctypes.c_void_p(medoids.data_ptr()), ctypes.c_void_p(res.data_ptr()),
+        ctypes.byref(o), ctypes.c_void_p(ws.data_ptr()), ws.numel(), _stream()))
+    return medoids, res
 
 
 def clara(X, k, sample_idx):

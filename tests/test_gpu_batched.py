@@ -144,3 +144,62 @@ def test_batched_graph_capture_replays():
         torch.cuda.synchronize()
         assert torch.equal(med0, med1)
         assert torch.equal(res0, res1)
+
+
+def test_restarts_from_random_starts_match_oracle():
+    """kmedoids_swap_batched: several uniform random starting sets on the
+    same matrices (instances sharing one arena offset), each FastPAM1 to
+    convergence: every run equals the oracle's FastPAM1 from the same start
+    (medoids, swaps, passes; TD within 1e-9), and the best-of-restarts pick
+    is the oracle's."""
+    specs = [(900, 12), (2600, 30), (515, 5)]
+    P, offs = wl.batched_points(specs, d=8, seed="restarts")
+    inst1, arena_len, _ = km.batch_layout(specs)
+    arena = torch.zeros(arena_len, dtype=torch.float32, device="cuda")
+    km.batched_distances(torch.from_numpy(P).cuda(), offs,
+                         torch.from_numpy(inst1.view(np.uint8).copy()).cuda(), arena)
+    R = 6
+    g = np.random.default_rng(77)
+    rows, starts, moff = [], [], 0
+    for i, (n, k) in enumerate(specs):
+        for r in range(R):
+            rows.append((int(inst1[i]["offset"]), n, int(inst1[i]["ld"]), k, moff))
+            starts.append(np.sort(g.choice(n, size=k, replace=False)).astype(np.int32))
+            moff += k
+    inst = np.array(rows, dtype=km.INSTANCE_DTYPE)
+    med = torch.from_numpy(np.concatenate(starts)).cuda()
+    inst_dev = torch.from_numpy(inst.view(np.uint8).copy()).cuda()
+    med, res = km.swap_batched(arena, inst_dev, med)
+    med = med.cpu().numpy()
+    res = np.frombuffer(res.cpu().numpy().tobytes(), dtype=km.BATCH_RESULT_DTYPE)
+    for i, (n, k) in enumerate(specs):
+        Do = oracle.euclid_f32(P[offs[i]:offs[i] + n])
+        tds = []
+        for r in range(R):
+            j = i * R + r
+            ref = oracle.swap(Do, starts[j], variant="fastpam1")
+            mo = int(inst[j]["medoid_offset"])
+            assert res[j]["status"] == 0
+            assert med[mo:mo + k].tolist() == ref["medoids"].tolist(), (i, r)
+            assert res[j]["swaps"] == ref["swaps"] and res[j]["iterations"] == ref["iterations"]
+            assert abs(res[j]["td"] - ref["td"]) <= 1e-9 * ref["td"]
+            tds.append(ref["td"])
+        gpu_best = int(np.argmin([res[i * R + r]["td"] for r in range(R)]))
+        assert gpu_best == int(np.argmin(tds))
+
+
+def test_swap_batched_rejects_bad_starts():
+    specs = [(300, 4), (300, 4)]
+    P, offs = wl.batched_points(specs, d=8, seed="bad-starts")
+    inst, arena_len, nmed = km.batch_layout(specs)
+    inst_dev = torch.from_numpy(inst.view(np.uint8).copy()).cuda()
+    arena = torch.zeros(arena_len, dtype=torch.float32, device="cuda")
+    km.batched_distances(torch.from_numpy(P).cuda(), offs, inst_dev, arena)
+    med = torch.tensor([1, 2, 3, 4, 7, 7, 8, 9], dtype=torch.int32, device="cuda")  # repeat
+    med, res = km.swap_batched(arena, inst_dev, med)
+    res = np.frombuffer(res.cpu().numpy().tobytes(), dtype=km.BATCH_RESULT_DTYPE)
+    assert res[0]["status"] == 0 and res[1]["status"] == 1
+    med2 = torch.tensor([1, 2, 3, 4, 5, 6, 7, 300], dtype=torch.int32, device="cuda")  # range
+    _, res2 = km.swap_batched(arena, inst_dev, med2)
+    res2 = np.frombuffer(res2.cpu().numpy().tobytes(), dtype=km.BATCH_RESULT_DTYPE)
+    assert res2[1]["status"] == 1

@@ -342,7 +342,7 @@ def test_build_gains_step_matches_build():
 
 def test_clara_single_full_sample_is_pam():
     """CLARA with one 'sample' holding every point is PAM on the full data
-    (Sec. 2.2): same medoids and TD as BUILD + FastPAM1."""
+    (Sec. 2.1): same medoids and TD as BUILD + FastPAM1."""
     from paper_2008_05171_gb300 import workloads as wl
     X = wl.gmm_points(150, 3, 4, seed="clara-pin").astype(np.float32)
     D = oracle.euclid_f32(X)
