@@ -258,16 +258,18 @@ typedef struct km_batch_result {
 
 size_t kmedoids_batched_workspace_size(int32_t count);
 
-/* Fill the arena with Euclidean matrices of float32 points (FP64
- * differences, one rounding to float32): instance i uses the n_i points
- * starting at row point_offsets[i] (DEVICE int64) of points (DEVICE,
- * dim floats per point). */
+/* Fill the arena with Euclidean matrices of float32 points: FP64
+ * differences, squares accumulated with fused multiply-adds in coordinate
+ * order, FP64 square root, one rounding to float32 (padding columns zero).
+ * Instance i uses the n_i points starting at row point_offsets[i] (DEVICE
+ * int64) of points (DEVICE, dim floats per point).  count <= 65535,
+ * dim <= 864 (else KM_E_UNSUPPORTED).  Synchronises the stream. */
 km_status kmedoids_batched_distances(const float *points, int32_t dim,
                                      const int64_t *point_offsets,
                                      const km_instance *inst, int32_t count,
                                      float *arena, void *stream);
 
-/* inst (DEVICE, count entries, 1 <= count <= 65536), medoids_out / results
+/* inst (DEVICE, count entries, 1 <= count <= 65535), medoids_out / results
  * (DEVICE).  opts: max_iter, tol; tune 1 = 8 warps per CTA, otherwise 16.
  * Asynchronous: the call only enqueues work on the stream (a zeroing copy,
  * a kernel ordering the instances largest first, and the persistent PAM

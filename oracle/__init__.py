@@ -49,8 +49,10 @@ def build(force: bool = False) -> str:
     if force or not os.path.exists(_SO) or \
             os.path.getmtime(_SO) < os.path.getmtime(_SRC):
         tmp = _SO + ".tmp%d" % os.getpid()
-        subprocess.check_call(["gcc", "-O2", "-fPIC", "-shared", "-fopenmp",
-                               "-o", tmp, _SRC, "-lm"])
+        # -ffp-contract=off: no fused multiply-add unless the source asks for
+        # one, so the results do not depend on the host architecture
+        subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fPIC", "-shared",
+                               "-fopenmp", "-o", tmp, _SRC, "-lm"])
         os.replace(tmp, _SO)
     return _SO
 

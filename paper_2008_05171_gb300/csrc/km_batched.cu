@@ -31,7 +31,8 @@ namespace km {
 
 constexpr int kBatchMaxN = 4096;
 constexpr int kBatchMaxK = 128;
-constexpr int kBatchMaxCount = 1 << 16;
+constexpr int kBatchMaxCount = 65535;  // also the grid height of the distance kernel
+constexpr int kDistMaxDim = 864;       // 64 staged points + the tile fit in shared memory
 
 struct BatchArgs {
   const float* arena;
@@ -47,9 +48,11 @@ struct BatchArgs {
   int start_given;           // 1: start from the medoids in `medoids` (no BUILD)
 };
 
-// Euclidean matrix of m points (FP64 differences, one rounding to FP32):
-// instance/sample q has points P[idx[q][i]] (idx may be NULL: consecutive
-// points from point_off[q]) and writes rows of ld elements at D + d_off[q].
+// Euclidean matrix of m points: FP64 differences, squares accumulated with
+// fused multiply-adds in coordinate order, FP64 square root, one rounding to
+// FP32.  Instance/sample q has points P[idx[q][i]] (idx may be NULL:
+// consecutive points from point_off[q]) and writes rows of ld elements at
+// D + d_off[q] (zeros in the padding columns).
 struct DistArgs {
   const float* P;
   int dim;
@@ -61,32 +64,72 @@ struct DistArgs {
   int count;
 };
 
-__global__ void k_batch_dist(const DistArgs a) {
-  // grid.y = instance, grid.x x block = rows; one thread per row entry
+__device__ __forceinline__ double dist_fp64(const float* xi, const float* xj, int dim) {
+  double sq = 0.0;
+  for (int t = 0; t < dim; ++t) {
+    const double df = (double)xi[t] - (double)xj[t];
+    sq = __fma_rn(df, df, sq);
+  }
+  return sqrt(sq);
+}
+
+// 32 x 32 tiles of the upper triangle, each written with its mirror image:
+// d(j, i) squares the negated differences of d(i, j), so the recipe gives
+// bitwise-symmetric values and half the FP64 work suffices.  The 64 points
+// of a tile are staged in shared memory (row stride dim | 1 words, so the
+// 32 lanes reading 32 different points hit distinct banks).
+__global__ void __launch_bounds__(256) k_batch_dist(const DistArgs a) {
+  extern __shared__ float xsm[];  // [64][stride]
+  __shared__ float tile[32][33];
   const int q = blockIdx.y;
   if (q >= a.count) return;
   const km_instance in = a.inst[q];
   float* D = a.D + in.offset;
-  const int m = in.n;
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < (long long)m * in.ld;
-       e += (long long)gridDim.x * blockDim.x) {
-    const int i = (int)(e / in.ld), j = (int)(e % in.ld);
-    float v = 0.f;
-    if (j < m) {
-      const long long pi = a.idx ? a.idx[(long long)q * a.s + i] : a.point_off[q] + i;
-      const long long pj = a.idx ? a.idx[(long long)q * a.s + j] : a.point_off[q] + j;
-      const float* xi = a.P + pi * a.dim;
-      const float* xj = a.P + pj * a.dim;
-      double sq = 0.0;
-      for (int t = 0; t < a.dim; ++t) {
-        const double df = (double)xi[t] - (double)xj[t];
-        sq += df * df;
+  const int m = in.n, dim = a.dim, stride = dim | 1;
+  const int T = (m + 31) / 32;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8 threads
+  for (long long L = blockIdx.x; L < (long long)T * T; L += gridDim.x) {
+    const int ti = (int)(L / T), tj = (int)(L % T);
+    if (tj < ti) continue;  // the block's uniform choice
+    __syncthreads();        // the previous tile's reads of xsm / tile are done
+    for (int e = threadIdx.x; e < 64 * dim; e += blockDim.x) {
+      const int r = e / dim, t = e % dim;
+      const int gi = (r < 32) ? ti * 32 + r : tj * 32 + (r - 32);
+      float v = 0.f;
+      if (gi < m) {
+        const long long pt = a.idx ? a.idx[(long long)q * a.s + gi] : a.point_off[q] + gi;
+        v = a.P[pt * dim + t];
       }
-      v = (float)sqrt(sq);
+      xsm[r * stride + t] = v;
     }
-    D[(size_t)i * in.ld + j] = v;
+    __syncthreads();
+    const float* xj = xsm + (32 + tx) * stride;
+    const int j = tj * 32 + tx;
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      const int ii = ty + 8 * r, i = ti * 32 + ii;
+      const float v = (float)dist_fp64(xsm + ii * stride, xj, dim);
+      if (i < m && j < m) D[(size_t)i * in.ld + j] = v;
+      tile[ii][tx] = v;
+    }
+    if (ti != tj) {
+      __syncthreads();
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        const int jj = ty + 8 * r;
+        const int i2 = ti * 32 + tx, j2 = tj * 32 + jj;
+        if (i2 < m && j2 < m) D[(size_t)j2 * in.ld + i2] = tile[tx][jj];
+      }
+    }
   }
+  const int pad = in.ld - m;
+  if (pad > 0)
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < (long long)m * pad;
+         e += (long long)gridDim.x * blockDim.x)
+      D[(size_t)(e / pad) * in.ld + m + (int)(e % pad)] = 0.f;
 }
+
+size_t dist_smem(int dim) { return 4 * (size_t)64 * (size_t)(dim | 1); }
 
 // Processing order, largest work first (n^2 (k + 1), the BUILD plus SWAP
 // passes' scale): the rank of instance i is the number of instances with
@@ -242,13 +285,20 @@ __device__ __forceinline__ void stream_rows(BatchSmem<WARPS>& S, const float* D,
 }
 
 // floor(x * 2^f) for finite x >= 0 with 2^f = s1 * s2 (each a normal power
-// of two): scaling by powers of two is exact in FP32 unless the value drops
-// below the normal range, where both the rounded and the exact value floor
-// to 0, and x * 2^f < 2^62 by the choice of f.  So the round-down
-// conversion gives the same value as the integer-only fx_of, in three
-// instructions.
+// of two), equal to the integer-only fx_of.  y = x * 2^f is exact in FP32
+// (power-of-two scaling; below the normal range both the rounded and the
+// exact value floor to 0) and y < 2^62 by the choice of f.  The 64-bit
+// result is assembled from two 32-bit conversions (a 64-bit conversion runs
+// on GB300's narrow FP64 pipe): hi = floor(y / 2^32) (exact scaling; hi is
+// either below 2^24 or y / 2^32 itself, so it converts back to FP32
+// exactly), r = y - hi * 2^32 in one fused operation (exact: r < 2^32 and a
+// multiple of y's unit in the last place), lo = floor(r).
 __device__ __forceinline__ long long fx_scaled(float x, float s1, float s2) {
-  return __float2ll_rd((x * s1) * s2);
+  const float y = (x * s1) * s2;
+  const unsigned hi = __float2uint_rz(y * 0x1p-32f);
+  const float r = __fmaf_rn(-(float)hi, 0x1p32f, y);
+  const unsigned lo = __float2uint_rd(r);
+  return (long long)(((unsigned long long)hi << 32) | lo);
 }
 
 // 2^e as a float for -126 <= e <= 127.
@@ -474,7 +524,7 @@ __global__ void __launch_bounds__(WARPS * 32, 1) k_batch_pam(const BatchArgs a) 
         S.near[o] = (uint8_t)n1;
         S.dn[o] = d1;
         S.ds[o] = (n2 < 0) ? __int_as_float(0x7f800000) : d2;
-        if (n2 >= 0) atomic_add_acc(&S.rl[n1], fx_of(d2, f) - fx_of(d1, f));
+        if (n2 >= 0) atomic_add_shared64(&S.rl[n1], fx_of(d2, f) - fx_of(d1, f));
       }
       __syncthreads();
     };
@@ -519,9 +569,9 @@ __global__ void __launch_bounds__(WARPS * 32, 1) k_batch_pam(const BatchArgs a) 
                   if (e < dnp) {
                     const long long xn = fx_scaled(dnp, fs1, fs2);
                     lp += xd - xn;
-                    atomic_add_acc(&ar[sl], xn - xs);
+                    atomic_add_shared64(&ar[sl], xn - xs);
                   } else {
-                    atomic_add_acc(&ar[sl], xd - xs);
+                    atomic_add_shared64(&ar[sl], xd - xs);
                   }
                 }
               },
@@ -862,6 +912,8 @@ extern "C" km_status kmedoids_batched_distances(const float* points, int32_t dim
   set_last_error("");
   if (!points || !point_offsets || !inst || !arena || count <= 0 || dim <= 0)
     return bfail(KM_E_INVALID, "invalid arguments");
+  if (count > kBatchMaxCount || dim > kDistMaxDim)
+    return bfail(KM_E_UNSUPPORTED, "need count <= %d and dim <= %d", kBatchMaxCount, kDistMaxDim);
   DistArgs a;
   memset(&a, 0, sizeof(a));
   a.P = points;
@@ -872,7 +924,9 @@ extern "C" km_status kmedoids_batched_distances(const float* points, int32_t dim
   a.count = count;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   dim3 grid(64, count);
-  k_batch_dist<<<grid, 256, 0, s>>>(a);
+  const size_t sm = dist_smem(dim);
+  BK(cudaFuncSetAttribute(k_batch_dist, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+  k_batch_dist<<<grid, 256, sm, s>>>(a);
   BK(cudaGetLastError());
   BK(cudaStreamSynchronize(s));
   return KM_OK;
@@ -894,10 +948,10 @@ extern "C" km_status kmedoids_clara(const float* X, int64_t n, int32_t d, int32_
                                     km_result* res, void* ws, size_t ws_bytes, void* stream) {
   set_last_error("");
   if (!X || !sample_idx || !medoids_out || !ws) return bfail(KM_E_INVALID, "NULL pointer");
-  if (n <= 0 || d <= 0 || k <= 0 || samples <= 0 || sample_size < k || sample_size > n ||
-      sample_size > kBatchMaxN || k > kBatchMaxK)
-    return bfail(KM_E_INVALID, "need 1 <= k <= sample_size <= min(n, %d), k <= %d, samples >= 1",
-                 kBatchMaxN, kBatchMaxK);
+  if (n <= 0 || d <= 0 || d > kDistMaxDim || k <= 0 || samples <= 0 || samples > kBatchMaxCount ||
+      sample_size < k || sample_size > n || sample_size > kBatchMaxN || k > kBatchMaxK)
+    return bfail(KM_E_INVALID, "need 1 <= k <= sample_size <= min(n, %d), k <= %d, "
+                 "1 <= samples <= %d, d <= %d", kBatchMaxN, kBatchMaxK, kBatchMaxCount, kDistMaxDim);
   if (ws_bytes < kmedoids_clara_workspace_size(k, samples, sample_size))
     return bfail(KM_E_WORKSPACE, "workspace too small");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -933,7 +987,9 @@ extern "C" km_status kmedoids_clara(const float* X, int64_t n, int32_t d, int32_
   da.inst = inst;
   da.D = arena;
   da.count = samples;
-  k_batch_dist<<<dim3(64, samples), 256, 0, s>>>(da);
+  const size_t dsm = dist_smem(d);
+  BK(cudaFuncSetAttribute(k_batch_dist, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dsm));
+  k_batch_dist<<<dim3(64, samples), 256, dsm, s>>>(da);
   BK(cudaGetLastError());
   km_options o;
   km_default_options(&o);

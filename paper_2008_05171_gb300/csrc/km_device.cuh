@@ -153,6 +153,22 @@ __device__ __forceinline__ void atomic_add_acc(long long* p, long long v) {
   atomicAdd(reinterpret_cast<unsigned long long*>(p), static_cast<unsigned long long>(v));
 }
 
+// v added to a 64-bit accumulator in SHARED memory with native 32-bit atomics
+// (the 64-bit shared atomic add measured slower on GB300): the low word takes
+// v's low half and reports whether this addition wrapped it, the high word
+// then takes v's high half plus that carry.  Every thread accounts for
+// exactly its own carry, so the sum is exact modulo 2^64.  p is 8-byte
+// aligned (little-endian words).
+__device__ __forceinline__ void atomic_add_shared64(long long* p, long long v) {
+  unsigned* w = reinterpret_cast<unsigned*>(p);
+  const unsigned lo = (unsigned)v;
+  const unsigned hi = (unsigned)((unsigned long long)v >> 32);
+  const unsigned old = atomicAdd(w, lo);
+  const unsigned up = hi + ((old + lo < old) ? 1u : 0u);
+  if (up) atomicAdd(w + 1, up);
+}
+__device__ __forceinline__ void atomic_add_shared64(double* p, double v) { atomicAdd(p, v); }
+
 template <class A>
 __device__ __forceinline__ A shfl_down_a(A v, int o) { return __shfl_down_sync(0xffffffffu, v, o); }
 

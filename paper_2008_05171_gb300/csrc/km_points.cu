@@ -83,7 +83,7 @@ __global__ void __launch_bounds__(kPtThreads) k_cache_init(const PointArgs a) {
     a.sec[o] = n2;
     dn[o] = d1;
     ds[o] = (n2 < 0) ? Tr<T>::high() : d2;
-    if (n2 >= 0) atomic_add_acc(&sacc[n1], Tr<T>::fx(d2, f) - Tr<T>::fx(d1, f));
+    if (n2 >= 0) atomic_add_shared64(&sacc[n1], Tr<T>::fx(d2, f) - Tr<T>::fx(d1, f));
     tdl = G(d1);
   } else if (o < a.n_pad) {
     a.near[o] = 0;
@@ -161,7 +161,7 @@ __global__ void __launch_bounds__(kPtThreads) k_apply(const PointArgs a) {
     a.sec[o] = n2;
     dn[o] = d1;
     ds[o] = d2;
-    atomic_add_acc(&sacc[n1], Tr<T>::fx(d2, f) - Tr<T>::fx(d1, f));
+    atomic_add_shared64(&sacc[n1], Tr<T>::fx(d2, f) - Tr<T>::fx(d1, f));
     tdl = G(d1);
   }
   const G bs = block_sum(tdl, scratch);

@@ -122,10 +122,10 @@ __device__ __forceinline__ void swap_hit_at(int r, int col, const T* data,
   const long long xd = Tr<T>::fx(d, f), xs = Tr<T>::fx(ds, f);
   if (d < dn) {
     const long long xn = Tr<T>::fx(dn, f);
-    atomic_add_acc(ar + k, xd - xn);
-    atomic_add_acc(ar + sl, xn - xs);
+    atomic_add_shared64(ar + k, xd - xn);
+    atomic_add_shared64(ar + sl, xn - xs);
   } else {
-    atomic_add_acc(ar + sl, xd - xs);
+    atomic_add_shared64(ar + sl, xd - xs);
   }
 }
 
