@@ -18,6 +18,7 @@ k-Medoids Clustering" (arXiv 2008.05171):
 * ``swap_delta``    -- Delta of one (slot, candidate) swap by Eq. (5).
 * ``swap``          -- SWAP to convergence: PAM brute force / PAM cached /
                        FastPAM1 / FastPAM2 / FasterPAM (Alg. 4).
+* ``clarans``       -- FastCLARANS (Sec. 3.4) over given candidate draws.
 * ``clara``         -- CLARA (Sec. 2.1, FastCLARA of Sec. 3.4) on given
                        samples; ``euclid_f32`` the FP64 -> float32 matrix.
 
@@ -84,6 +85,9 @@ def _lib():
                                         f64, f64, P, P, i32, P, P, P]
             lib.oracle_build_gains.restype = None
             lib.oracle_build_gains.argtypes = [P, i32, i64, i64, P, i32, P]
+            lib.oracle_clarans.restype = i32
+            lib.oracle_clarans.argtypes = [P, i32, i64, i64, i32, P, P, i64, i64,
+                                           f64, P, P, i32, P, P, P]
             lib.oracle_euclid_f32.restype = None
             lib.oracle_euclid_f32.argtypes = [P, i64, i32, P, i64, P]
             lib.oracle_clara.restype = i32
@@ -223,6 +227,35 @@ def swap(D, medoids, variant="fastpam1", max_iter=1000, tol=0.0,
         "td_bookkept": float(tdv[0]), "td": float(tdv[1]),
         "trace": list(zip(tr_d[:ns].tolist(), tr_i[:ns].tolist(),
                           tr_c[:ns].tolist())),
+    }
+
+
+def clarans(D, medoids, cand, maxneighbor, tol=0.0, n=None, trace_cap=None):
+    """FastCLARANS (Sec. 3.4) from ``medoids`` over the given candidate draws
+    ``cand``, stopping after ``maxneighbor`` consecutive failed draws.
+    Returns a dict with medoids, consumed (draws used), swaps, stopped,
+    evaluated, td_bookkept, td and the trace (delta, slot, cand)."""
+    D, code, n, ld = _mat(D, n)
+    med = _med(medoids).copy()
+    k = len(med)
+    cand = np.ascontiguousarray(cand, np.int32)
+    cap = int(trace_cap if trace_cap is not None else max(16, 4 * k + 64))
+    stats = np.zeros(4, np.int64)
+    tdv = np.zeros(2, np.float64)
+    tr_d = np.zeros(cap, np.float64)
+    tr_i = np.zeros(cap, np.int32)
+    tr_c = np.zeros(cap, np.int64)
+    rc = _lib().oracle_clarans(_p(D), code, n, ld, k, _p(med), _p(cand), len(cand),
+                               int(maxneighbor), float(tol), _p(stats), _p(tdv), cap,
+                               _p(tr_d), _p(tr_i), _p(tr_c))
+    if rc != 0:
+        raise ValueError("oracle_clarans: need 2 <= k < n, maxneighbor >= 1")
+    ns = min(int(stats[1]), cap)
+    return {
+        "medoids": med, "consumed": int(stats[0]), "swaps": int(stats[1]),
+        "stopped": bool(stats[2]), "evaluated": int(stats[3]),
+        "td_bookkept": float(tdv[0]), "td": float(tdv[1]),
+        "trace": list(zip(tr_d[:ns].tolist(), tr_i[:ns].tolist(), tr_c[:ns].tolist())),
     }
 
 

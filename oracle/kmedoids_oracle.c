@@ -667,6 +667,75 @@ int oracle_swap(const void *D, int dtype, int64_t n, int64_t ld, int k,
 }
 
 /* ------------------------------------------------------------------------
+ * FastCLARANS (Sec. 3.4): CLARANS's randomized search with the FastPAM1
+ * evaluation.  CLARANS draws a random (medoid, non-medoid) pair, swaps if
+ * that lowers TD and stops after a fixed number of consecutive failed
+ * draws; FastCLARANS draws only the non-medoid and evaluates it against all
+ * k medoids at once.  The draws are given: cand[0..len) (a draw that is a
+ * medoid at its turn is skipped and not counted).  Each draw c: Delta =
+ * min over slots of Eq. (7) (lowest slot on ties); if Delta < -tol the swap
+ * is applied at once (the new medoid takes the slot) and the failure count
+ * restarts at 0, else it grows by one; the search stops when it reaches
+ * maxneighbor or the draws run out.  Needs 2 <= k < n.
+ * stats[0] = draws consumed (medoids included), stats[1] = swaps,
+ * stats[2] = 1 if stopped by maxneighbor, stats[3] = draws evaluated.
+ * td and the trace as in oracle_swap.  Returns 0, or -1 on invalid input.
+ * ---------------------------------------------------------------------- */
+int oracle_clarans(const void *D, int dtype, int64_t n, int64_t ld, int k,
+                   int32_t *med, const int32_t *cand, int64_t len,
+                   int64_t maxneighbor, double tol, int64_t *stats, double *td,
+                   int trace_cap, double *tr_d, int32_t *tr_i, int64_t *tr_c) {
+  if (k < 2 || k >= n || len < 0 || maxneighbor < 1) return -1;
+  or_mat m = mk(D, dtype, n, ld);
+  double *acc = (double *)malloc(sizeof(double) * (size_t)k);
+  int32_t *near = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
+  double *dn = (double *)malloc(sizeof(double) * (size_t)n);
+  double *ds = (double *)malloc(sizeof(double) * (size_t)n);
+  double *rl = (double *)malloc(sizeof(double) * (size_t)k);
+  char *is_med = (char *)calloc((size_t)n, 1);
+  for (int j = 0; j < k; j++) is_med[med[j]] = 1;
+  oracle_cache(D, dtype, n, ld, med, k, near, NULL, dn, ds);
+  oracle_removal_loss(n, k, near, dn, ds, rl);
+  double tdb = oracle_td(D, dtype, n, ld, med, k, NULL);
+  int64_t fails = 0, pos = 0, evaluated = 0, swaps = 0, ntr = 0;
+  int stopped = 0;
+  while (pos < len) {
+    const int64_t c = cand[pos++];
+    if (c < 0 || c >= n || is_med[c]) continue;
+    evaluated++;
+    int slot;
+    const double d = fastpam1_candidate(&m, k, near, dn, ds, rl, c, acc, &slot);
+    if (d < -tol) {
+      apply_trace(&ntr, trace_cap, tr_d, tr_i, tr_c, d, slot, c);
+      is_med[med[slot]] = 0;
+      med[slot] = (int32_t)c;
+      is_med[c] = 1;
+      swaps++;
+      tdb += d;
+      fails = 0;
+      oracle_cache(D, dtype, n, ld, med, k, near, NULL, dn, ds);
+      oracle_removal_loss(n, k, near, dn, ds, rl);
+    } else if (++fails >= maxneighbor) {
+      stopped = 1;
+      break;
+    }
+  }
+  stats[0] = pos;
+  stats[1] = swaps;
+  stats[2] = stopped;
+  stats[3] = evaluated;
+  td[0] = tdb;
+  td[1] = oracle_td(D, dtype, n, ld, med, k, NULL);
+  free(acc);
+  free(near);
+  free(dn);
+  free(ds);
+  free(rl);
+  free(is_med);
+  return 0;
+}
+
+/* ------------------------------------------------------------------------
  * Euclidean dissimilarity matrix of m float32 points in FP64, rounded once
  * to float32: D[i*ld + j] = sqrt(sum_t (x_it - x_jt)^2) (zero diagonal,
  * symmetric by construction).  The recipe is fixed to the operation: FP64

@@ -370,3 +370,80 @@ def test_clara_best_sample_has_least_full_td():
         gm = S[q][r["medoids"]]
         assert abs(bf.td(D, gm) - tds[q]) <= 1e-5 * tds[q]
     assert (lab == np.argmin(D[:, :400][:, med], axis=1)).all()
+
+
+# --------------------------------------------------------- FastCLARANS --
+
+def _clarans_bruteforce(D, med, cand, maxneighbor):
+    """CLARANS over the given draws with every (slot, draw) Delta recomputed
+    from the TD objective (Eq. (2)): for a non-medoid draw c, the best slot
+    is the lowest one with the least TD after putting c there."""
+    med = list(int(m) for m in med)
+    fails, pos, trace = 0, 0, []
+    while pos < len(cand):
+        c = int(cand[pos])
+        pos += 1
+        if c in med:
+            continue
+        base = bf.td(D, med)
+        best, bi = None, -1
+        for i in range(len(med)):
+            trial = med.copy()
+            trial[i] = c
+            d = bf.td(D, trial) - base
+            if best is None or d < best:
+                best, bi = d, i
+        if best < 0:
+            med[bi] = c
+            trace.append((best, bi, c))
+            fails = 0
+        else:
+            fails += 1
+            if fails >= maxneighbor:
+                return med, pos, trace, True
+    return med, pos, trace, False
+
+
+def test_clarans_matches_bruteforce_replay():
+    """FastCLARANS (Sec. 3.4) evaluates a draw against all k medoids with
+    Eq. (7); each decision must equal the brute-force TD recomputation over
+    all slots, on tiny integer matrices rich in ties, random starts, draw
+    streams with repeats and medoids, and every stopping count."""
+    g = np.random.default_rng(31)
+    for D in bf.tiny_instances(131, 90, n_lo=4, n_hi=10):
+        n = D.shape[0]
+        k = int(g.integers(2, n))
+        med = g.choice(n, size=k, replace=False).astype(np.int32)
+        cand = g.integers(0, n, size=3 * n).astype(np.int32)
+        mn = int(g.integers(1, n + 1))
+        ref_med, ref_pos, ref_tr, ref_stop = _clarans_bruteforce(D, med, cand, mn)
+        out = oracle.clarans(D, med, cand, mn)
+        assert out["medoids"].tolist() == ref_med
+        assert out["consumed"] == ref_pos and out["stopped"] == ref_stop
+        assert [(round(d), i, c) for d, i, c in out["trace"]] == \
+            [(round(d), i, c) for d, i, c in ref_tr]
+        assert out["td"] == bf.td(D, ref_med)
+
+
+def test_clarans_on_cyclic_draws_is_fasterpam():
+    """With the draws 0, 1, ..., n-1 repeated and maxneighbor = n - k (every
+    non-medoid failed once since the last swap), the randomized search
+    makes exactly FasterPAM's scan (Alg. 4): same swaps in the same order."""
+    g = np.random.default_rng(5)
+    for t, D in enumerate(bf.tiny_instances(77, 20, n_lo=8, n_hi=10) +
+                          [bf.tiny_float_instances(78, 1, 10, 10)[0]]):
+        n = D.shape[0]
+        k = 3 if n > 4 else 2
+        start = g.choice(n, size=k, replace=False).astype(np.int32)
+        ref = oracle.swap(D, start, variant="fasterpam", trace_cap=1000)
+        cyc = np.tile(np.arange(n, dtype=np.int32), 50)
+        out = oracle.clarans(D, start, cyc, n - k, trace_cap=1000)
+        assert out["stopped"]
+        assert out["medoids"].tolist() == ref["medoids"].tolist()
+        assert [(i, c) for _, i, c in out["trace"]] == [(i, c) for _, i, c in ref["trace"]]
+    # the worked example of Fig. 1: from {B, E} the swaps B->A, E->D
+    gj, names, D = fig1()
+    start = np.array([names.index("B"), names.index("E")], np.int32)
+    out = oracle.clarans(D, start, np.tile(np.arange(6, dtype=np.int32), 10), 4)
+    assert sorted(names[m] for m in out["medoids"]) == ["A", "D"]
+    assert [names[c] for _, _, c in out["trace"]] == ["A", "D"]
