@@ -45,6 +45,11 @@ WORKLOADS = {
                              "11.5 GB arena) in one persistent launch, plus CLARA on "
                              "n=1e6 d=32 float32 (100-cluster mixture), k=100, 10 samples "
                              "of 80+4k=480 points"),
+    "clarans_20000": dict(n=20000, d=16, centers=100, k=100, recipe="gmm_20000_points",
+                          desc="FastCLARANS (Sec. 3.4) on the gmm_20000 matrix (n=20000 d=16 "
+                               "f32 GMM, 100 clusters): k=100, a uniform random start, "
+                               "uniform random candidate draws with replacement, stop after "
+                               "maxneighbor = 2.5% of n-k = 497 consecutive failed draws"),
     "gmm_50000": dict(n=50000, d=32, centers=200, k=200, recipe="gmm_50000_points",
                       desc="n=50000 d=32 f32 GMM (200 clusters, centres U[-10,10]^32, "
                            "sigma U[0.5,2], Dirichlet(1) weights), Euclidean f32 "
@@ -400,9 +405,85 @@ def run_batched(args, rank, world, local_rank):
     return line
 
 
+def run_clarans(args, rank, world, local_rank):
+    """FastCLARANS from a fixed random start over fixed random draws."""
+    import torch
+    import paper_2008_05171_gb300.kmedoids as km
+    from paper_2008_05171_gb300 import workloads as wl
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    D, spec = make_input(args.workload, dev)
+    n, k = spec["n"], spec["k"]
+    mn = int(0.025 * (n - k))
+    g = wl.rng_for(("clarans", n, k))
+    start = np.sort(g.choice(n, size=k, replace=False)).astype(np.int32)
+    draws = torch.from_numpy(g.integers(0, n, size=400_000).astype(np.int32)).to(dev)
+    ws = km.workspace(n, k, km.KM_F32, km.options(profile=True), device=dev)
+    torch.cuda.synchronize()
+
+    def step():
+        return km.swap(D, start, ws=ws, variant="fastclarans", draws=draws, maxneighbor=mn,
+                       profile=True, tune=args.tune)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    barrier(world)
+    clocks = Clocks(local_rank)
+    clocks.start()
+    stream = torch.cuda.current_stream()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    results = []
+    for i in range(args.steps):
+        ev[i][0].record(stream)
+        results.append(step())
+        ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    ck = clocks.stop()
+    total_ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in ev), world, dev)
+    r0 = results[-1]
+    evals = sum(int(r["iterations"]) * n for r in results)  # draws evaluated x points
+    value = world * evals / (total_ms / 1e3)
+    rows, _, minb = km.geometry_info(r0["swap_geometry"])
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    grid = min(sms * minb, (n + rows - 1) // rows, 1024)
+    win_bytes = grid * rows * n * 4  # rows one window streams (medoid rows skipped: < 1 %)
+    launch_ms = r0["eval_ms"] / max(1, r0["eval_launches"])
+    peak, pk = peaks()
+    ach = win_bytes / (launch_ms / 1e3) / 1e9
+    line = {
+        "metric": "SWAP dTD point-evals/sec + full PAM run time (k=100/200); % HBM roofline",
+        "value": value, "unit": "point-evals/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32 (exact 64-bit fixed-point dTD sums, FP64 TD)", "data": "synthetic",
+        "config": {"workload": args.workload + ": " + spec["desc"], "n": n, "k": k,
+                   "maxneighbor": mn, "draws_available": int(draws.numel()),
+                   "l2": "matrix larger than L2 (no flush needed)",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "draws_consumed": int(r0["visited"]), "draws_evaluated": int(r0["iterations"]),
+        "swaps": int(r0["swaps"]), "windows": int(r0["eval_launches"]),
+        "stopped_by_maxneighbor": bool(r0["converged"]), "td": r0["td"],
+        "roofline": {"bound": "hbm", "achieved": round(ach, 1), "peak": peak, "unit": "GB/s",
+                     "frac": round(ach / peak, 4), "kernel": "k_stream<float,SWAP> FastCLARANS window",
+                     "algorithmic_bytes_per_launch": win_bytes, "avg_launch_ms": round(launch_ms, 5),
+                     "peak_source": pk, "traffic": None},
+        "gpu_launches": int(sum(r["kernel_launches"] for r in results)),
+        "clocks": ck, "e2e": None,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cb = oracle_clarans_sample(D.cpu().numpy(), n, k, args.cpu_seconds)
+        cb.pop("seconds")
+        line["cpu_baseline"] = cb
+    return line
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
     import paper_2008_05171_gb300.kmedoids as km
+    if args.workload.startswith("clarans"):
+        return run_clarans(args, rank, world, local_rank)
     if args.workload.startswith("features"):
         return run_features(args, rank, world, local_rank)
     if args.workload.startswith("batched"):
@@ -641,6 +722,31 @@ def oracle_batched(specs, budget_s):
                       "OpenMP over candidates), %.1f s of solver time" % (done, len(specs), el)}
 
 
+def oracle_clarans_sample(Dh, n, k, budget_s):
+    """The oracle's FastCLARANS from the workload's start over a prefix of
+    its draws, the prefix doubled until one run takes about budget_s / 3
+    (the oracle evaluates draws one after another on one core)."""
+    import oracle
+    from paper_2008_05171_gb300 import workloads as wl
+    mn = int(0.025 * (n - k))
+    g = wl.rng_for(("clarans", n, k))
+    start = np.sort(g.choice(n, size=k, replace=False)).astype(np.int32)
+    draws = g.integers(0, n, size=400_000).astype(np.int32)
+    length = 64
+    while True:
+        t0 = time.perf_counter()
+        r = oracle.clarans(Dh, start, draws[:length], mn)
+        dt = time.perf_counter() - t0
+        if dt >= budget_s / 3 or r["stopped"] or length >= len(draws):
+            break
+        length *= 2
+    return {"value": r["evaluated"] * n / dt, "unit": "point-evals/s", "cores": 1,
+            "kind": "oracle", "seconds": dt,
+            "sample": "FastCLARANS of the FP64 C oracle (one core) from the same start over "
+                      "the first %d of the same draws: %d evaluated, %d swaps, %.1f s"
+                      % (length, r["evaluated"], r["swaps"], dt)}
+
+
 def run_reference(args, rank, world):
     """The oracle as the reference arm: timed on the host cores on a bounded
     sample of the workload per step (rank 0 only)."""
@@ -669,6 +775,28 @@ def run_reference(args, rank, world):
                 "e2e": {"value": v, "unit": "point-evals/s", "h2d_bytes_per_step": 0,
                         "d2h_bytes_per_step": 0}}
     X = getattr(wl, spec["recipe"])()
+    if args.workload.startswith("clarans"):
+        dev = torch.device("cuda", 0) if torch.cuda.is_available() else torch.device("cpu")
+        Dh = (wl.euclidean_f32_torch(X, dev) if dev.type == "cuda"
+              else torch.from_numpy(wl.euclidean_f32(X))).cpu().numpy()
+        vals, secs, cb = [], [], None
+        for _ in range(args.warmup + args.steps):
+            cb = oracle_clarans_sample(Dh, spec["n"], spec["k"], min(8.0, args.cpu_seconds))
+            vals.append(cb["value"])
+            secs.append(cb.pop("seconds"))
+        v = float(np.mean(vals[args.warmup:]))
+        cb["value"] = v
+        return {"impl": "reference", "metric": "SWAP dTD point-evals/sec + full PAM run time "
+                "(k=100/200); % HBM roofline", "value": v, "unit": "point-evals/s",
+                "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": 1e3 * float(np.mean(secs[args.warmup:])),
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f64", "data": "synthetic",
+                "config": {"workload": args.workload + ": " + spec["desc"], "n": spec["n"],
+                           "k": spec["k"]},
+                "cpu_baseline": cb,
+                "e2e": {"value": v, "unit": "point-evals/s", "h2d_bytes_per_step": 0,
+                        "d2h_bytes_per_step": 0}}
     if args.workload.startswith("features"):
         # no n x n matrix exists in this form: time the oracle on a subsample
         spec = dict(spec, n=8000)

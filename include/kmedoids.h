@@ -74,7 +74,12 @@ typedef enum { KM_I32 = 0, KM_F32 = 1 } km_dtype;
 typedef enum {
   KM_FASTPAM1 = 0, /* best swap per iteration (Alg. 3); same swaps as PAM */
   KM_FASTPAM2 = 1, /* best swap per slot, up to k swaps per iteration */
-  KM_FASTERPAM = 2 /* eager: first improving candidate in scan order (Alg. 4) */
+  KM_FASTERPAM = 2, /* eager: first improving candidate in scan order (Alg. 4) */
+  KM_FASTCLARANS = 3 /* randomized search (Sec. 3.4): the caller's candidate
+                        draws (opts->draws) in order, each evaluated against
+                        all k medoids with Eq. (7) and swapped at once if it
+                        improves; stops after opts->maxneighbor consecutive
+                        failed draws.  Needs 2 <= k < n. */
 } km_variant;
 
 /* Options.  Zero-initialise and call km_default_options() first. */
@@ -109,6 +114,13 @@ typedef struct km_options {
   int64_t *trace_time_ns; /* device %globaltimer when the swap was applied */
   double *build_gains;    /* HOST, k entries: BUILD step gains (step 0 = the
                              first medoid's distance sum) */
+  /* KM_FASTCLARANS only: */
+  const int32_t *draws;   /* DEVICE, draws_len point indices (the random
+                             non-medoid picks; a draw that is a medoid at
+                             its turn, or out of range, is skipped) */
+  int64_t draws_len;
+  int64_t maxneighbor;    /* consecutive failed draws that end the search
+                             (the paper samples 2.5 % of n - k) */
 } km_options;
 
 /* Results, filled on the HOST before the call returns. */
@@ -118,11 +130,14 @@ typedef struct km_result {
   int64_t td_i64;       /* final TD as int64 (KM_I32 only) */
   double td_bookkept;   /* initial TD + sum of the applied Delta values */
   double td_initial;    /* TD of the starting medoids (after BUILD) */
-  int32_t iterations;   /* evaluation passes (FasterPAM: scans started) */
+  int32_t iterations;   /* evaluation passes (FasterPAM: scans started;
+                           FastCLARANS: draws evaluated) */
   int32_t swaps;        /* swaps applied */
   int32_t status;       /* km_status of the call */
   int32_t build_steps;  /* medoids chosen by BUILD */
-  int64_t visited;      /* FasterPAM: scan positions visited */
+  int64_t visited;      /* FasterPAM: scan positions visited; FastCLARANS:
+                           draws consumed (KM_E_NOT_CONVERGED if the draws
+                           ran out before maxneighbor consecutive failures) */
   /* profile != 0 only (milliseconds of device time, CUDA events): */
   double build_ms;      /* whole BUILD */
   double swap_ms;       /* whole SWAP phase (cache init + iterations) */
@@ -135,6 +150,15 @@ typedef struct km_result {
   int16_t swap_geometry;   /* geometry table entries (1..16) the SWAP and */
   int16_t build_geometry;  /* BUILD passes ran with; 0 = not run */
 } km_result;
+
+/* Parameters of a matrix-form geometry table entry (1..16, as reported in
+ * km_result.swap_geometry / build_geometry and accepted by opts->tune):
+ * candidate rows per tile, shared-memory ring stages, CTAs per SM.  A pass
+ * launches min(SMs x ctas_per_sm, ceil(n / rows), 1024) CTAs; a FasterPAM
+ * or FastCLARANS window covers that many times rows positions.  Returns 0,
+ * or 1 for an unknown entry (outputs untouched; NULL outputs skipped). */
+int kmedoids_geometry_info(int32_t geometry, int32_t *rows, int32_t *stages,
+                           int32_t *ctas_per_sm);
 
 /* Fill *o with the defaults (FastPAM1, tol 0, automatic tiles). */
 void km_default_options(km_options *o);

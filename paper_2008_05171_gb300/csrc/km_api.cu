@@ -135,7 +135,11 @@ km_status check_common(const void* D, int32_t dtype, int64_t n, int64_t ld, int3
   km_options def;
   km_default_options(&def);
   c->opt = opts ? *opts : def;
-  if (c->opt.variant < 0 || c->opt.variant > 2) return fail(KM_E_INVALID, "unknown variant %d", c->opt.variant);
+  if (c->opt.variant < 0 || c->opt.variant > 3) return fail(KM_E_INVALID, "unknown variant %d", c->opt.variant);
+  if (c->opt.variant == KM_FASTCLARANS &&
+      (!c->opt.draws || c->opt.draws_len < 1 || c->opt.maxneighbor < 1 || k < 2 || k >= n))
+    return fail(KM_E_INVALID, "FastCLARANS needs draws, draws_len >= 1, maxneighbor >= 1 and "
+                "2 <= k < n");
   if (!(c->opt.tol >= 0.0)) return fail(KM_E_INVALID, "tol must be >= 0");
   if (!(c->opt.fastpam2_tol >= 0.0)) return fail(KM_E_INVALID, "fastpam2_tol must be >= 0");
   if (c->opt.rows_per_tile != 0 && c->opt.rows_per_tile != 1 && c->opt.rows_per_tile != 2 &&
@@ -462,12 +466,20 @@ km_status do_swap(Ctx& c, Timer& tm, std::vector<std::pair<int, int>>& ev, KmSta
   if (r != KM_OK) return r;
   if (c.k == 1) return swap_k1(c, h);
   const int variant = c.opt.variant;
-  const int flavour = variant == KM_FASTPAM2 ? kFastPAM2 : (variant == KM_FASTERPAM ? kFasterPAM : kFastPAM1);
+  const int flavour = variant == KM_FASTPAM2     ? kFastPAM2
+                      : variant == KM_FASTERPAM   ? kFasterPAM
+                      : variant == KM_FASTCLARANS ? kCLARANS
+                                                  : kFastPAM1;
   StreamArgs sa = stream_args(c);
   sa.flavour = flavour;
-  if (flavour == kFasterPAM) {  // per-position results of a scan window
+  if (flavour == kFasterPAM || flavour == kCLARANS) {  // per-position window results
     sa.cand_delta = c.at<double>(c.L.win_delta);
     sa.cand_slot = c.at<int32_t>(c.L.win_slot);
+  }
+  if (flavour == kCLARANS) {
+    sa.draws = c.opt.draws;
+    sa.draws_len = c.opt.draws_len;
+    sa.maxneighbor = c.opt.maxneighbor;
   }
   StreamConfig cfg;
   r = config_for(c, kModeSwap, flavour, sa, &cfg);
@@ -478,7 +490,7 @@ km_status do_swap(Ctx& c, Timer& tm, std::vector<std::pair<int, int>>& ev, KmSta
   PointArgs pa = point_args(c);
   const int max_iter = c.opt.max_iter;
 
-  if (variant == KM_FASTPAM1 || variant == KM_FASTERPAM) {
+  if (variant == KM_FASTPAM1 || variant == KM_FASTERPAM || variant == KM_FASTCLARANS) {
     const long long pos_limit = (long long)max_iter * c.n;
     int launched = 0, batch = 1;
     const int max_launch = (variant == KM_FASTPAM1) ? max_iter : INT32_MAX;
@@ -683,12 +695,17 @@ static km_status run_impl(bool do_b, bool do_s, const void* D, int32_t dtype, in
     }
     h = h2;
     if (!h.done) conv = KM_E_NOT_CONVERGED;
+    if (c.opt.variant == KM_FASTCLARANS && h.fails < c.opt.maxneighbor) conv = KM_E_NOT_CONVERGED;
     if (res) {
       res->iterations = h.iter;
       res->swaps = h.swaps;
       if (c.opt.variant == KM_FASTERPAM && c.k > 1) {
         res->visited = h.pos;
         res->iterations = (int)((h.pos + c.n - 1) / c.n);
+      }
+      if (c.opt.variant == KM_FASTCLARANS) {
+        res->visited = h.pos;
+        res->iterations = (int)h.evaluated;
       }
       if (tm.on) res->swap_ms = tm.ms(s0, s1);
     }
@@ -724,7 +741,13 @@ static km_status run_impl(bool do_b, bool do_s, const void* D, int32_t dtype, in
     res->swap_geometry = (int16_t)c.swap_geom;
     res->build_geometry = (int16_t)c.build_geom;
   }
-  if (conv != KM_OK) fail(conv, "max_iter (%d) reached before convergence", c.opt.max_iter);
+  if (conv != KM_OK) {
+    if (c.opt.variant == KM_FASTCLARANS)
+      fail(conv, "the %lld draws ran out before %lld consecutive failures",
+           (long long)c.opt.draws_len, (long long)c.opt.maxneighbor);
+    else
+      fail(conv, "max_iter (%d) reached before convergence", c.opt.max_iter);
+  }
   return conv;
 }
 

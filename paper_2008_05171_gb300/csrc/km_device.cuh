@@ -58,6 +58,8 @@ struct KmState {
   unsigned tile_next;       // next candidate tile of the running pass
   unsigned scan_max;        // matrix scan: largest |d| (float bits)
   unsigned scan_bad;        // matrix scan: 1 if an entry is < 0 or not finite
+  long long fails;          // FastCLARANS: consecutive failed draws
+  long long evaluated;      // FastCLARANS: draws evaluated
 };
 
 // Trace record of an applied swap.

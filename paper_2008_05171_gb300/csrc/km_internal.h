@@ -18,7 +18,9 @@ enum SwapFlavour {
   kFastPAM1 = 0,  // best swap; accept iff Delta < -tol, else done
   kFastPAM2 = 1,  // as FastPAM1 + per-slot best swaps queued for later
   kFasterPAM = 2, // window of the cyclic scan; first improving candidate
-  kEvalOnly = 3   // evaluation only: best key written, no decision
+  kEvalOnly = 3,  // evaluation only: best key written, no decision
+  kCLARANS = 4    // window of the caller's draws; first improving draw,
+                  // stop after maxneighbor consecutive failed draws
 };
 
 struct StreamArgs {
@@ -48,7 +50,10 @@ struct StreamArgs {
   int32_t* cand_slot;
   double* cand_gain;    // BUILD per-candidate gains
   int flavour;          // SwapFlavour
-  int win_rows;         // FasterPAM: positions per CTA
+  int win_rows;         // FasterPAM / FastCLARANS: positions per CTA
+  const int32_t* draws; // FastCLARANS: candidate draws (DEVICE)
+  long long draws_len;
+  long long maxneighbor;
   int fshift;           // fixed-point exponent f of the SWAP sums (float data)
   double tol;
 };

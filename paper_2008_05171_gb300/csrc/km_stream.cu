@@ -239,11 +239,13 @@ __global__ void __launch_bounds__(kThreads, MINB) k_stream(const StreamArgs a) {
   // Candidate positions: FasterPAM windows give each CTA the positions
   // [p_lo, p_hi) (row = p mod n); full passes hand out tiles of R rows from
   // an atomic counter so that CTAs on faster paths take more tiles.
-  const bool windowed = (MODE == kModeSwap && a.flavour == kFasterPAM);
+  const bool clarans = (MODE == kModeSwap && a.flavour == kCLARANS);
+  const bool windowed = (MODE == kModeSwap && (a.flavour == kFasterPAM || clarans));
   long long base = 0, p_lo = 0, p_hi = 0;
   if (windowed) {
     base = st->pos;
-    const long long stop = (st->last < 0) ? (long long)n : st->last + n;
+    const long long stop =
+        clarans ? a.draws_len : ((st->last < 0) ? (long long)n : st->last + n);
     p_lo = base + (long long)blockIdx.x * a.win_rows;
     p_hi = p_lo + a.win_rows;
     if (p_hi > stop) p_hi = stop;
@@ -265,8 +267,8 @@ __global__ void __launch_bounds__(kThreads, MINB) k_stream(const StreamArgs a) {
         int nr = 0;
         if (windowed) {
           while (nr < R && p < p_hi) {
-            const int row = (int)(p % n);
-            if (!a.is_med[row]) {
+            const int row = clarans ? a.draws[p] : (int)(p % n);
+            if (row >= 0 && row < n && !a.is_med[row]) {
               rows[nr] = row;
               outs[nr] = (int)(p - base);
               ++nr;
@@ -594,6 +596,73 @@ __global__ void __launch_bounds__(kThreads, MINB) k_stream(const StreamArgs a) {
     return;
   }
 
+  if (clarans) {
+    // FastCLARANS: the first improving draw of the window, in draw order,
+    // unless maxneighbor consecutive draws fail before it (Sec. 3.4)
+    const long long stop = a.draws_len;
+    long long wlen = (long long)gridDim.x * a.win_rows;
+    if (base + wlen > stop) wlen = stop - base;
+    int* firstw = scratch_int;
+    int* nfail = scratch_int + 1;
+    if (t == 0) {
+      *firstw = INT_MAX;
+      *nfail = 0;
+    }
+    KM_CSYNC();
+    for (long long w = t; w < wlen; w += kConsThreads) {
+      const int row = a.draws[base + w];
+      if (row < 0 || row >= n || a.is_med[row]) continue;
+      if (__ldcg(a.cand_slot + w) >= 0 && __ldcg(a.cand_delta + w) < -a.tol)
+        atomicMin(firstw, (int)w);
+    }
+    KM_CSYNC();
+    const int fw = *firstw;
+    int cnt = 0;  // evaluated draws before the first improving one
+    for (long long w = t; w < wlen && w < fw; w += kConsThreads) {
+      const int row = a.draws[base + w];
+      if (row >= 0 && row < n && !a.is_med[row]) ++cnt;
+    }
+    if (cnt) atomicAdd(nfail, cnt);
+    KM_CSYNC();
+    if (t == 0) {
+      const long long F = *nfail;
+      if (st->fails + F >= a.maxneighbor) {
+        // stop at the draw that makes the failure count reach maxneighbor
+        const long long need = a.maxneighbor - st->fails;
+        long long seen = 0, w = 0;
+        for (; w < wlen; ++w) {
+          const int row = a.draws[base + w];
+          if (row >= 0 && row < n && !a.is_med[row] && ++seen == need) break;
+        }
+        st->accept = 0;
+        st->done = 1;
+        st->fails = a.maxneighbor;
+        st->evaluated += need;
+        st->pos = base + w + 1;
+      } else if (fw != INT_MAX) {
+        const double dw = __ldcg(a.cand_delta + fw);
+        st->accept = 1;
+        st->best_d = dw;
+        st->best_i = (long long)dw;
+        st->best_slot = __ldcg(a.cand_slot + fw);
+        st->best_cand = a.draws[base + fw];
+        st->fails = 0;
+        st->evaluated += F + 1;
+        st->last = base + fw;
+        st->pos = base + fw + 1;
+      } else {
+        st->accept = 0;
+        st->fails += F;
+        st->evaluated += F;
+        st->pos = base + wlen;
+        if (st->pos >= stop) st->done = 1;
+      }
+      st->iter += 1;
+      st->ticket = 0;
+    }
+    return;
+  }
+
   if (a.flavour == kFasterPAM) {
     // first improving candidate of the window, in scan order
     const long long stop = (st->last < 0) ? (long long)n : st->last + n;
@@ -799,3 +868,13 @@ cudaError_t launch_stream(int dtype, int mode, const StreamConfig& cfg, int grid
 }
 
 }  // namespace km
+
+extern "C" int kmedoids_geometry_info(int32_t geometry, int32_t* rows, int32_t* stages,
+                                      int32_t* ctas_per_sm) {
+  if (geometry < 1 || geometry > km::kNumGeoms) return 1;
+  const km::Geometry& g = km::kGeoms[geometry - 1];
+  if (rows) *rows = g.rows;
+  if (stages) *stages = g.stages;
+  if (ctas_per_sm) *ctas_per_sm = g.minb;
+  return 0;
+}

@@ -16,7 +16,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libkmedoids.so")
 
 KM_I32, KM_F32 = 0, 1
-VARIANTS = {"fastpam1": 0, "fastpam2": 1, "fasterpam": 2}
+VARIANTS = {"fastpam1": 0, "fastpam2": 1, "fasterpam": 2, "fastclarans": 3}
 STATUS = {0: "KM_OK", 1: "KM_E_INVALID", 2: "KM_E_WORKSPACE", 3: "KM_E_CUDA",
           4: "KM_E_NOT_CONVERGED", 5: "KM_E_TIMEOUT", 6: "KM_E_NUMERIC",
           7: "KM_E_UNSUPPORTED"}
@@ -27,7 +27,8 @@ EXPORTS = ["km_default_options", "kmedoids_workspace_size", "kmedoids_build",
            "kmedoids_features_workspace_size", "kmedoids_run_features",
            "kmedoids_swap_features", "kmedoids_batched_workspace_size",
            "kmedoids_batched_distances", "kmedoids_run_batched",
-           "kmedoids_swap_batched", "kmedoids_clara_workspace_size", "kmedoids_clara"]
+           "kmedoids_swap_batched", "kmedoids_clara_workspace_size", "kmedoids_clara",
+           "kmedoids_geometry_info"]
 
 
 class KmError(RuntimeError):
@@ -46,7 +47,9 @@ class km_options(ctypes.Structure):
                 ("trace_slot", ctypes.POINTER(ctypes.c_int32)),
                 ("trace_cand", ctypes.POINTER(ctypes.c_int32)),
                 ("trace_time_ns", ctypes.POINTER(ctypes.c_int64)),
-                ("build_gains", ctypes.POINTER(ctypes.c_double))]
+                ("build_gains", ctypes.POINTER(ctypes.c_double)),
+                ("draws", ctypes.c_void_p), ("draws_len", ctypes.c_int64),
+                ("maxneighbor", ctypes.c_int64)]
 
 
 class km_result(ctypes.Structure):
@@ -124,6 +127,8 @@ def load(path: str = LIB_PATH):
         lib.kmedoids_clara.argtypes = [P, i64, i32, i32, i32, i32, P, P, P, P,
                                        res_p, P, sz, P]
         lib.kmedoids_clara.restype = i32
+        lib.kmedoids_geometry_info.argtypes = [i32, P, P, P]
+        lib.kmedoids_geometry_info.restype = ctypes.c_int
         lib.kmedoids_last_error.restype = ctypes.c_char_p
         lib.kmedoids_version.restype = ctypes.c_char_p
         _LIB = lib
@@ -163,9 +168,16 @@ def _stream():
 
 
 def options(variant="fastpam1", max_iter=0, tol=0.0, fastpam2_tol=0.0,
-            rows_per_tile=0, profile=False, trace=0, tune=0):
+            rows_per_tile=0, profile=False, trace=0, tune=0, draws=None,
+            maxneighbor=0):
+    """km_options.  draws: int32 CUDA tensor of candidate draws (FastCLARANS);
+    the caller keeps it alive for the call."""
     o = km_options()
     load().km_default_options(ctypes.byref(o))
+    if draws is not None:
+        o.draws = ctypes.c_void_p(draws.data_ptr())
+        o.draws_len = int(draws.numel())
+    o.maxneighbor = int(maxneighbor)
     o.variant = VARIANTS[variant] if isinstance(variant, str) else int(variant)
     o.max_iter = int(max_iter)
     o.tol = float(tol)
@@ -517,6 +529,15 @@ def clara(X, k, sample_idx):
     return {"medoids": med, "labels": lab, "sample_td": tds.tolist(),
             "best_sample": res.best_sample, "td": res.td,
             "kernel_launches": res.kernel_launches}
+
+
+def geometry_info(geometry):
+    """(rows, stages, ctas_per_sm) of a matrix-form geometry table entry."""
+    r, st, m = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+    if load().kmedoids_geometry_info(int(geometry), ctypes.byref(r), ctypes.byref(st),
+                                     ctypes.byref(m)):
+        raise KmError(1, "unknown geometry %d" % geometry)
+    return r.value, st.value, m.value
 
 
 def version() -> str:
