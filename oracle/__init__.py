@@ -19,6 +19,8 @@ k-Medoids Clustering" (arXiv 2008.05171):
 * ``swap``          -- SWAP to convergence: PAM brute force / PAM cached /
                        FastPAM1 / FastPAM2 / FasterPAM (Alg. 4).
 * ``clarans``       -- FastCLARANS (Sec. 3.4) over given candidate draws.
+* ``init_weighted`` -- distance-weighted initialisation (Sec. 2.3 / 3.3) from
+                       given uniform numbers.
 * ``clara``         -- CLARA (Sec. 2.1, FastCLARA of Sec. 3.4) on given
                        samples; ``euclid_f32`` the FP64 -> float32 matrix.
 
@@ -85,6 +87,10 @@ def _lib():
                                         f64, f64, P, P, i32, P, P, P]
             lib.oracle_build_gains.restype = None
             lib.oracle_build_gains.argtypes = [P, i32, i64, i64, P, i32, P]
+            lib.oracle_init_weighted.restype = i32
+            lib.oracle_init_weighted.argtypes = [P, i32, i64, i64, i32, P, P]
+            lib.oracle_fixed_shift.restype = i32
+            lib.oracle_fixed_shift.argtypes = [P, i32, i64, i64]
             lib.oracle_clarans.restype = i32
             lib.oracle_clarans.argtypes = [P, i32, i64, i64, i32, P, P, i64, i64,
                                            f64, P, P, i32, P, P, P]
@@ -228,6 +234,25 @@ def swap(D, medoids, variant="fastpam1", max_iter=1000, tol=0.0,
         "trace": list(zip(tr_d[:ns].tolist(), tr_i[:ns].tolist(),
                           tr_c[:ns].tolist())),
     }
+
+
+def init_weighted(D, k, u, n=None):
+    """Distance-weighted initialisation (Sec. 2.3 / 3.3) driven by the given
+    uniform numbers u (k values in [0, 1)): k distinct medoids in draw
+    order."""
+    D, code, n, ld = _mat(D, n)
+    u = np.ascontiguousarray(u, np.float64)
+    assert len(u) >= k
+    med = np.empty(k, np.int32)
+    if _lib().oracle_init_weighted(_p(D), code, n, ld, int(k), _p(u), _p(med)) != 0:
+        raise ValueError("oracle_init_weighted: need 1 <= k <= n")
+    return med
+
+
+def fixed_shift(D, n=None):
+    """The fixed-point exponent f of the SWAP sums for this matrix."""
+    D, code, n, ld = _mat(D, n)
+    return int(_lib().oracle_fixed_shift(_p(D), code, n, ld))
 
 
 def clarans(D, medoids, cand, maxneighbor, tol=0.0, n=None, trace_cap=None):

@@ -667,6 +667,87 @@ int oracle_swap(const void *D, int dtype, int64_t n, int64_t ld, int k,
 }
 
 /* ------------------------------------------------------------------------
+ * Distance-weighted initialisation (Sec. 2.3 and 3.3: the k-means++ seeding
+ * with distances instead of squared distances): the first medoid is drawn
+ * uniformly, every further one with probability proportional to its
+ * distance to the nearest medoid drawn so far.  The uniform numbers are
+ * given: u[0..k), each in [0, 1).  Draw 0 picks floor(u_0 n).  Draw t >= 1
+ * uses the weights w_o = floor(d_n(o) 2^f) -- exact 64-bit fixed point with
+ * f = 60 - ceil(log2(n+1)) - e(M) as for the SWAP sums (M the largest
+ * entry; integer data: w_o = d_n(o)) -- their total W, the threshold
+ * T = floor(u_t W) evaluated in FP64 (clamped to W - 1), and picks the
+ * lowest o whose running sum of weights exceeds T.  A drawn medoid has
+ * d_n = 0, so no point is drawn twice; if W = 0 the lowest-index point
+ * not yet drawn is taken.  Returns 0, or -1 on invalid input.
+ * ---------------------------------------------------------------------- */
+static int64_t fx_weight(const or_mat *m, double x, int f) {
+  if (m->dtype == 0) return (int64_t)x;
+  return (int64_t)floor(ldexp(x, f)); /* x * 2^f is exact in FP64 */
+}
+
+int oracle_fixed_shift(const void *D, int dtype, int64_t n, int64_t ld) {
+  if (dtype == 0) return 0;
+  const float *F = (const float *)D;
+  float mx = 0.0f;
+  for (int64_t i = 0; i < n; i++)
+    for (int64_t j = 0; j < n; j++)
+      if (F[i * ld + j] > mx) mx = F[i * ld + j];
+  int em = 0;
+  if (mx > 0.0f) (void)frexpf(mx, &em); /* mx < 2^em */
+  int bn = 0;
+  while ((1ll << bn) <= (long long)n) bn++; /* n < 2^bn */
+  return 60 - bn - em;
+}
+
+int oracle_init_weighted(const void *D, int dtype, int64_t n, int64_t ld, int k,
+                         const double *u, int32_t *med) {
+  if (k < 1 || k > n || n < 1) return -1;
+  or_mat m = mk(D, dtype, n, ld);
+  const int f = oracle_fixed_shift(D, dtype, n, ld);
+  double *dn = (double *)malloc(sizeof(double) * (size_t)n);
+  char *drawn = (char *)calloc((size_t)n, 1);
+  int64_t c = (int64_t)floor(u[0] * (double)n);
+  if (c > n - 1) c = n - 1;
+  if (c < 0) c = 0;
+  med[0] = (int32_t)c;
+  drawn[c] = 1;
+  for (int64_t o = 0; o < n; o++) dn[o] = od(&m, o, c);
+  for (int t = 1; t < k; t++) {
+    int64_t W = 0;
+    for (int64_t o = 0; o < n; o++) W += fx_weight(&m, dn[o], f);
+    int64_t pick = -1;
+    if (W > 0) {
+      int64_t T = (int64_t)floor(u[t] * (double)W);
+      if (T > W - 1) T = W - 1;
+      if (T < 0) T = 0;
+      int64_t run = 0;
+      for (int64_t o = 0; o < n; o++) {
+        run += fx_weight(&m, dn[o], f);
+        if (run > T) {
+          pick = o;
+          break;
+        }
+      }
+    } else {
+      for (int64_t o = 0; o < n; o++)
+        if (!drawn[o]) {
+          pick = o;
+          break;
+        }
+    }
+    med[t] = (int32_t)pick;
+    drawn[pick] = 1;
+    for (int64_t o = 0; o < n; o++) {
+      const double v = od(&m, o, pick);
+      if (v < dn[o]) dn[o] = v;
+    }
+  }
+  free(dn);
+  free(drawn);
+  return 0;
+}
+
+/* ------------------------------------------------------------------------
  * FastCLARANS (Sec. 3.4): CLARANS's randomized search with the FastPAM1
  * evaluation.  CLARANS draws a random (medoid, non-medoid) pair, swaps if
  * that lowers TD and stops after a fixed number of consecutive failed

@@ -447,3 +447,59 @@ def test_clarans_on_cyclic_draws_is_fasterpam():
     out = oracle.clarans(D, start, np.tile(np.arange(6, dtype=np.int32), 10), 4)
     assert sorted(names[m] for m in out["medoids"]) == ["A", "D"]
     assert [names[c] for _, _, c in out["trace"]] == ["A", "D"]
+
+
+# ------------------------------------------- distance-weighted initialisation --
+
+def test_init_weighted_picks_by_the_weight_intervals():
+    """Draw t picks the point whose interval of the running weight sum holds
+    u_t W, weights = distances to the nearest medoid drawn so far (the
+    k-means++ seeding with linear distances, Sec. 2.3 / 3.3): with u_1 at
+    the middle of point o's interval the second medoid is o, for every o
+    with positive weight, on integer matrices (weights = distances)."""
+    for D in bf.tiny_instances(401, 12, n_lo=6, n_hi=10, kinds=("grid2", "sym")):
+        n = D.shape[0]
+        A = bf.sq(D)
+        first = 2
+        w = A[:, first].copy()                 # distances to the first medoid
+        W = w.sum()
+        if W == 0:
+            continue
+        prefix = np.cumsum(w) - w
+        for o in range(n):
+            if w[o] == 0:
+                continue
+            u1 = (prefix[o] + 0.5 * w[o]) / W
+            med = oracle.init_weighted(D, 2, [(first + 0.5) / n, u1])
+            assert med.tolist() == [first, o]
+
+
+def test_init_weighted_frequencies_follow_distances():
+    """Over many uniform u_1 the second medoid is o with frequency close to
+    d(o, m_1) / sum_p d(p, m_1) (chi-square, fixed seed)."""
+    D = bf.tiny_instances(402, 1, n_lo=9, n_hi=9, kinds=("grid2",))[0]
+    A = bf.sq(D)
+    first = 0
+    g = np.random.default_rng(3)
+    counts = np.zeros(A.shape[0])
+    for u1 in g.random(4000):
+        counts[oracle.init_weighted(D, 2, [0.0, u1])[1]] += 1
+    p = A[:, first] / A[:, first].sum()
+    m = p > 0
+    chi2 = (((counts[m] - 4000 * p[m]) ** 2) / (4000 * p[m])).sum()
+    assert counts[~m].sum() == 0 and chi2 < 30.0   # ~ 8 degrees of freedom
+
+
+def test_init_weighted_distinct_and_degenerate():
+    g = np.random.default_rng(9)
+    for D in bf.tiny_instances(403, 20, n_lo=4, n_hi=10):
+        n = D.shape[0]
+        u = g.random(n)
+        med = oracle.init_weighted(D, n, u)
+        assert sorted(med.tolist()) == list(range(n))          # k = n: every point once
+        assert med[0] == int(np.floor(u[0] * n))              # draw 0 is uniform
+    Z = np.zeros((6, 8), np.int32)                            # all points coincide
+    assert oracle.init_weighted(Z, 4, [0.5, 0.9, 0.1, 0.3]).tolist() == [3, 0, 1, 2]
+    F = bf.tiny_float_instances(404, 1, 8, 8)[0]
+    med = oracle.init_weighted(F, 3, [0.99999, 0.5, 0.5])
+    assert med[0] == 7 and len(set(med.tolist())) == 3
