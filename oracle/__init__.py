@@ -21,6 +21,8 @@ k-Medoids Clustering" (arXiv 2008.05171):
 * ``clarans``       -- FastCLARANS (Sec. 3.4) over given candidate draws.
 * ``init_weighted`` -- distance-weighted initialisation (Sec. 2.3 / 3.3) from
                        given uniform numbers.
+* ``init_lab``      -- LAB, BUILD on a fresh subsample per medoid (Sec. 3.3),
+                       from given subsample ranks.
 * ``clara``         -- CLARA (Sec. 2.1, FastCLARA of Sec. 3.4) on given
                        samples; ``euclid_f32`` the FP64 -> float32 matrix.
 
@@ -89,6 +91,8 @@ def _lib():
             lib.oracle_build_gains.argtypes = [P, i32, i64, i64, P, i32, P]
             lib.oracle_init_weighted.restype = i32
             lib.oracle_init_weighted.argtypes = [P, i32, i64, i64, i32, P, P]
+            lib.oracle_init_lab.restype = i32
+            lib.oracle_init_lab.argtypes = [P, i32, i64, i64, i32, i32, P, P, P]
             lib.oracle_fixed_shift.restype = i32
             lib.oracle_fixed_shift.argtypes = [P, i32, i64, i64]
             lib.oracle_clarans.restype = i32
@@ -247,6 +251,31 @@ def init_weighted(D, k, u, n=None):
     if _lib().oracle_init_weighted(_p(D), code, n, ld, int(k), _p(u), _p(med)) != 0:
         raise ValueError("oracle_init_weighted: need 1 <= k <= n")
     return med
+
+
+def lab_sample_size(n):
+    """LAB's subsample size 10 + ceil(sqrt(n)) (Sec. 3.3)."""
+    r = int(np.floor(np.sqrt(n)))
+    while r * r < n:
+        r += 1
+    return 10 + r
+
+
+def init_lab(D, k, ranks, n=None, gains=False):
+    """LAB, Linear Approximative BUILD (Sec. 3.3): before each of the k
+    choices, BUILD's gain over a subsample only.  ``ranks`` (k x s) name the
+    subsample of step t as ranks among the n - t non-medoids in index order.
+    Returns the k medoids in choice order (and each step's gain)."""
+    D, code, n, ld = _mat(D, n)
+    ranks = np.ascontiguousarray(ranks, np.int32)
+    assert ranks.ndim == 2 and ranks.shape[0] >= k
+    s = ranks.shape[1]
+    med = np.empty(k, np.int32)
+    g = np.empty(k, np.float64)
+    if _lib().oracle_init_lab(_p(D), code, n, ld, int(k), int(s), _p(ranks), _p(med),
+                              _p(g)) != 0:
+        raise ValueError("oracle_init_lab: invalid sizes or ranks")
+    return (med, g) if gains else med
 
 
 def fixed_shift(D, n=None):

@@ -748,6 +748,105 @@ int oracle_init_weighted(const void *D, int dtype, int64_t n, int64_t ld, int k,
 }
 
 /* ------------------------------------------------------------------------
+ * LAB, Linear Approximative BUILD (Sec. 3.3): BUILD restricted to a fresh
+ * random subsample before each medoid is chosen.  Step t (t = 0..k-1) takes
+ * a subsample S_t of s points from the n - t points that are not medoids
+ * yet; the candidate c in S_t with the least
+ *     gain(c) = sum_{o in S_t} min(d(o,c) - d_n(o), 0)
+ * (the change of the subsample's TD when c is added; d_n(o) = distance to
+ * the nearest medoid chosen so far; o = c included, as in BUILD) becomes
+ * the next medoid.  Step 0 has no medoid yet: gain(c) = sum_{o in S_t}
+ * d(o,c), the subsample's 1-medoid.  Lowest point index on equal gains.
+ *
+ * The subsamples are given as ranks: rank[t*s + j] in [0, n - t), distinct
+ * within a step, names the rank-th non-medoid in ascending point index at
+ * step t; a negative rank is an unused entry (a smaller subsample), and a
+ * step needs at least one used entry.  Gains are summed in the exact fixed point of the SWAP sums
+ * (distances enter as floor(x 2^f); integer data unchanged), so the choice
+ * does not depend on the summation order.  gains_out (may be NULL) gets
+ * each step's least gain as a double (fixed point scaled back by 2^-f).
+ * Returns 0, or -1 on invalid input (bad sizes, a rank out of range or
+ * repeated within its step).
+ * ---------------------------------------------------------------------- */
+int oracle_init_lab(const void *D, int dtype, int64_t n, int64_t ld, int k,
+                    int s, const int32_t *rank, int32_t *med,
+                    double *gains_out) {
+  if (k < 1 || k > n || n < 1 || s < 1) return -1;
+  or_mat m = mk(D, dtype, n, ld);
+  const int f = oracle_fixed_shift(D, dtype, n, ld);
+  double *dn = (double *)malloc(sizeof(double) * (size_t)n);
+  char *is_med = (char *)calloc((size_t)n, 1);
+  int64_t *pts = (int64_t *)malloc(sizeof(int64_t) * (size_t)s);
+  char *used = (char *)calloc((size_t)n, 1);
+  int rc = 0;
+  for (int64_t o = 0; o < n; o++) dn[o] = OR_INF;
+  for (int t = 0; t < k && rc == 0; t++) {
+    /* the subsample: rank r -> the r-th non-medoid in index order */
+    int cnt = 0;
+    for (int j = 0; j < s; j++) {
+      const int64_t r = rank[(size_t)t * s + j];
+      if (r < 0) continue; /* unused entry: a smaller subsample */
+      if (r >= n - t) {
+        rc = -1;
+        break;
+      }
+      int64_t seen = -1, p = -1;
+      for (int64_t o = 0; o < n; o++) {
+        if (!is_med[o]) seen++;
+        if (seen == r) {
+          p = o;
+          break;
+        }
+      }
+      if (used[p]) {
+        rc = -1;
+        break;
+      }
+      used[p] = 1;
+      pts[cnt++] = p;
+    }
+    for (int j = 0; j < cnt; j++) used[pts[j]] = 0;
+    if (rc != 0) break;
+    if (cnt == 0) {
+      rc = -1; /* an empty subsample */
+      break;
+    }
+    int64_t best = 0, pick = -1;
+    for (int a = 0; a < cnt; a++) {
+      const int64_t c = pts[a];
+      int64_t g = 0;
+      for (int b = 0; b < cnt; b++) {
+        const int64_t o = pts[b];
+        const int64_t dc = fx_weight(&m, od(&m, o, c), f);
+        if (t == 0) {
+          g += dc;
+        } else {
+          const int64_t v = dc - fx_weight(&m, dn[o], f);
+          if (v < 0) g += v;
+        }
+      }
+      if (pick < 0 || g < best || (g == best && c < pick)) {
+        best = g;
+        pick = c;
+      }
+    }
+    med[t] = (int32_t)pick;
+    is_med[pick] = 1;
+    if (gains_out)
+      gains_out[t] = (dtype == 0) ? (double)best : ldexp((double)best, -f);
+    for (int64_t o = 0; o < n; o++) {
+      const double v = od(&m, o, pick);
+      if (v < dn[o]) dn[o] = v;
+    }
+  }
+  free(dn);
+  free(is_med);
+  free(pts);
+  free(used);
+  return rc;
+}
+
+/* ------------------------------------------------------------------------
  * FastCLARANS (Sec. 3.4): CLARANS's randomized search with the FastPAM1
  * evaluation.  CLARANS draws a random (medoid, non-medoid) pair, swaps if
  * that lowers TD and stops after a fixed number of consecutive failed

@@ -503,3 +503,72 @@ def test_init_weighted_distinct_and_degenerate():
     F = bf.tiny_float_instances(404, 1, 8, 8)[0]
     med = oracle.init_weighted(F, 3, [0.99999, 0.5, 0.5])
     assert med[0] == 7 and len(set(med.tolist())) == 3
+
+
+def _lab_bruteforce(D, k, ranks):
+    """LAB (Sec. 3.3) from its definition: at step t the subsample is the
+    set of non-medoids at the given ranks (index order), and the next medoid
+    is the subsample point c minimising the subsample's TD with c added
+    (TD of the subsample alone at t = 0), lowest index on ties."""
+    A = bf.sq(D)
+    n = A.shape[0]
+    med = []
+    for t in range(k):
+        free = [o for o in range(n) if o not in med]
+        S = [free[r] for r in ranks[t]]
+        best, pick = None, None
+        for c in sorted(S):
+            cols = med + [c]
+            v = A[np.ix_(S, cols)].min(axis=1).sum()
+            if best is None or v < best:
+                best, pick = v, c
+        med.append(pick)
+    return med
+
+
+def test_init_lab_matches_subsample_td_bruteforce():
+    """Each LAB step is the argmin of the subsample's TD with the candidate
+    added (integer matrices rich in ties: exact)."""
+    g = np.random.default_rng(411)
+    for D in bf.tiny_instances(411, 60, n_lo=6, n_hi=12):
+        n = D.shape[0]
+        k = int(g.integers(1, n + 1))
+        s = int(g.integers(1, n - k + 2))
+        ranks = np.array([g.choice(n - t, s, replace=False) for t in range(k)])
+        assert oracle.init_lab(D, k, ranks).tolist() == _lab_bruteforce(D, k, ranks)
+
+
+def test_init_lab_full_sample_is_build():
+    """With the whole non-medoid set as every subsample (ranks 0..n-t-1,
+    the rest of the row -1 = unused), LAB is BUILD (Alg. 1): medoids and
+    gains equal the oracle's BUILD, which is pinned to greedy brute force
+    above; integer and float data."""
+    insts = bf.tiny_instances(412, 30, n_lo=5, n_hi=12) + \
+        bf.tiny_float_instances(413, 10, 5, 12)
+    for D in insts:
+        n = D.shape[0]
+        for k in sorted({1, 2, max(1, n // 2), n}):
+            ranks = np.full((k, n), -1, np.int32)
+            for t in range(k):
+                ranks[t, :n - t] = np.arange(n - t)
+            med_l, gains_l = oracle.init_lab(D, k, ranks, gains=True)
+            med_b, _, gains_b = oracle.pam_build(D, k)
+            assert med_l.tolist() == list(med_b)
+            assert np.allclose(gains_l, gains_b, rtol=0, atol=1e-9 * max(1.0, abs(gains_b[0])))
+
+
+def test_init_lab_rank_mapping_and_errors():
+    """Ranks name non-medoids in index order: with a one-point subsample
+    the step-t choice is exactly that point; out-of-range or repeated ranks
+    are rejected; LAB's subsample size is 10 + ceil(sqrt(n))."""
+    D = bf.tiny_instances(414, 1, n_lo=8, n_hi=8)[0]
+    ranks = np.array([[5], [5], [0], [4]], np.int32)
+    # step 0 picks 5; non-medoids {0..4,6,7}: rank 5 -> 6; then {0..4,7}:
+    # rank 0 -> 0; then {1..4,7}: rank 4 -> 7
+    assert oracle.init_lab(D, 4, ranks).tolist() == [5, 6, 0, 7]
+    with pytest.raises(ValueError):
+        oracle.init_lab(D, 2, np.array([[0, 0], [1, 2]], np.int32))
+    with pytest.raises(ValueError):
+        oracle.init_lab(D, 2, np.array([[0, 1], [7, 2]], np.int32))
+    assert [oracle.lab_sample_size(n) for n in (1, 2, 4, 5, 20000, 50000)] == \
+        [11, 12, 12, 13, 152, 234]
