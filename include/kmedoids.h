@@ -218,6 +218,53 @@ km_status kmedoids_cache(const void *D, int32_t dtype, int64_t n, int64_t ld,
                          int32_t *sec, void *dn, void *ds, double *removal,
                          void *ws, size_t ws_bytes, void *stream);
 
+/* Distance-weighted initialisation (Sec. 3.3; the k-means++ seeding of
+ * Sec. 2.3 with distances, not squared distances, as weights): k starting
+ * medoids for SWAP, typically FasterPAM (Sec. 4.3, Sec. 6), at O(nk) cost
+ * instead of BUILD's O(n^2 k).
+ *   u            DEVICE, k doubles in [0, 1): the caller's uniform random
+ *                numbers (any generator); draw t consumes u[t].
+ *   medoids_out  DEVICE, k int32: the draws in order (distinct points).
+ * Draw 0 is point floor(u[0] n).  Draw t >= 1 weighs every point o by its
+ * distance to the nearest medoid drawn so far, in the exact fixed point of
+ * the SWAP sums (w_o = floor(d 2^f) for KM_F32, d itself for KM_I32), and
+ * takes the lowest o whose running weight sum exceeds floor(u[t] W) (W the
+ * total weight, product in FP64); drawn points weigh 0 and are never drawn
+ * again; if W = 0 the lowest undrawn point is taken.  ws: as
+ * kmedoids_workspace_size(n, k, dtype, NULL).  KM_E_INVALID for a NULL
+ * pointer, a u[t] outside [0, 1) or the common size checks; KM_E_NUMERIC
+ * for negative or non-finite float entries.  Synchronises the stream. */
+km_status kmedoids_init_weighted(const void *D, int32_t dtype, int64_t n,
+                                 int64_t ld, int32_t k, const double *u,
+                                 int32_t *medoids_out, void *ws,
+                                 size_t ws_bytes, void *stream);
+
+/* LAB, Linear Approximative BUILD (Sec. 3.3): before each of the k choices
+ * a fresh subsample of the points that are not medoids yet is drawn, and
+ * BUILD's gain (Alg. 1) is evaluated over that subsample only; the paper
+ * uses subsamples of 10 + ceil(sqrt(n)) points.
+ *   s            entries per subsample (1 <= s <= 4096; k <= 8192).
+ *   ranks        DEVICE, k x s int32, row t = the subsample of step t as
+ *                ranks among the n - t current non-medoids in ascending
+ *                point index (rank r = the (r+1)-th smallest non-medoid),
+ *                distinct within a row; a negative entry is unused (a
+ *                smaller subsample), every row needs one used entry.
+ *   medoids_out  DEVICE, k int32: the choices in order.
+ *   gains_host   HOST, k doubles (may be NULL): each step's least gain,
+ *                sum_{o in S} min(d(o,c) - d_n(o), 0), and at step 0 the
+ *                chosen point's distance sum over its subsample.
+ * Each subsample point c is scored with that gain (its own term included,
+ * as in BUILD) in the exact fixed point of the SWAP sums; the least gain
+ * wins, lowest point index on ties.  ws: as kmedoids_workspace_size(n, k,
+ * dtype, NULL).  KM_E_INVALID for a rank outside [0, n - t), a repeated
+ * rank, an empty row, a NULL pointer or the common size checks;
+ * KM_E_UNSUPPORTED beyond the s and k limits.  Synchronises the stream. */
+km_status kmedoids_init_lab(const void *D, int32_t dtype, int64_t n,
+                            int64_t ld, int32_t k, int32_t s,
+                            const int32_t *ranks, int32_t *medoids_out,
+                            double *gains_host, void *ws, size_t ws_bytes,
+                            void *stream);
+
 /* Tensor-core Gram product G = X X^T of bf16 feature vectors (tcgen05 MMA,
  * FP32 accumulation), the dot products behind the on-the-fly distances
  * d(o,c)^2 = |x_o|^2 + |x_c|^2 - 2 x_o.x_c (Sec. 4.8 notes that recomputing

@@ -837,4 +837,108 @@ km_status kmedoids_cache(const void* D, int32_t dtype, int64_t n, int64_t ld, in
   return read_state(c, &h);
 }
 
+// Shared set-up of the two initialisations: argument checks, fixed-point
+// scale of the matrix, kernel arguments over the workspace.
+static km_status init_setup(const void* D, int32_t dtype, int64_t n, int64_t ld, int32_t k,
+                            int32_t* medoids_out, void* ws, size_t ws_bytes, void* stream, Ctx* c,
+                            InitArgs* ia) {
+  g_err.clear();
+  km_status r = check_common(D, dtype, n, ld, k, ws, ws_bytes, nullptr, c);
+  if (r != KM_OK) return r;
+  if (!medoids_out) return fail(KM_E_INVALID, "medoids_out is NULL");
+  c->s = static_cast<cudaStream_t>(stream);
+  r = reset_state(*c);
+  if (r != KM_OK) return r;
+  if (dtype == KM_F32) {
+    r = scan_matrix(*c);
+    if (r != KM_OK) return r;
+  }
+  memset(ia, 0, sizeof(*ia));
+  ia->D = D;
+  ia->ld = ld;
+  ia->n = (int)n;
+  ia->k = k;
+  ia->fshift = c->fshift;
+  ia->med = c->at<int32_t>(c->L.med);
+  ia->dn = c->at<void>(c->L.bdn);
+  ia->flags = c->at<uint8_t>(c->L.is_med);
+  ia->csum = c->at<long long>(c->L.cand_gain);  // n_pad doubles >= n/32 sums
+  ia->gains = c->at<double>(c->L.gains);
+  ia->st = c->st();
+  return KM_OK;
+}
+
+static km_status init_finish(Ctx& c, int32_t* medoids_out) {
+  KmState h;
+  KM_CUDA(cudaMemcpyAsync(&h, c.st(), sizeof(KmState), cudaMemcpyDeviceToHost, c.s));
+  KM_CUDA(cudaStreamSynchronize(c.s));
+  if (h.error) return fail(KM_E_INVALID, "an initialisation step had an empty subsample");
+  KM_CUDA(cudaMemcpyAsync(medoids_out, c.at<int32_t>(c.L.med), 4 * (size_t)c.k,
+                          cudaMemcpyDeviceToDevice, c.s));
+  KM_CUDA(cudaStreamSynchronize(c.s));
+  return KM_OK;
+}
+
+km_status kmedoids_init_weighted(const void* D, int32_t dtype, int64_t n, int64_t ld, int32_t k,
+                                 const double* u, int32_t* medoids_out, void* ws,
+                                 size_t ws_bytes, void* stream) {
+  Ctx c;
+  InitArgs ia;
+  if (!u) return fail(KM_E_INVALID, "u is NULL");
+  km_status r = init_setup(D, dtype, n, ld, k, medoids_out, ws, ws_bytes, stream, &c, &ia);
+  if (r != KM_OK) return r;
+  std::vector<double> hu((size_t)k);
+  KM_CUDA(cudaMemcpyAsync(hu.data(), u, 8 * (size_t)k, cudaMemcpyDeviceToHost, c.s));
+  KM_CUDA(cudaStreamSynchronize(c.s));
+  for (int t = 0; t < k; ++t)
+    if (!(hu[t] >= 0.0 && hu[t] < 1.0))
+      return fail(KM_E_INVALID, "u[%d] = %g is not in [0, 1)", t, hu[t]);
+  ia.u = u;
+  KM_LAUNCH(c, launch_init_weighted(dtype, ia, c.s));
+  return init_finish(c, medoids_out);
+}
+
+km_status kmedoids_init_lab(const void* D, int32_t dtype, int64_t n, int64_t ld, int32_t k,
+                            int32_t s, const int32_t* ranks, int32_t* medoids_out,
+                            double* gains_host, void* ws, size_t ws_bytes, void* stream) {
+  Ctx c;
+  InitArgs ia;
+  if (!ranks) return fail(KM_E_INVALID, "ranks is NULL");
+  if (s < 1) return fail(KM_E_INVALID, "s must be >= 1 (got %d)", s);
+  if (s > 4096 || k > 8192)
+    return fail(KM_E_UNSUPPORTED, "LAB supports s <= 4096 and k <= 8192 (s=%d, k=%d)", s, k);
+  km_status r = init_setup(D, dtype, n, ld, k, medoids_out, ws, ws_bytes, stream, &c, &ia);
+  if (r != KM_OK) return r;
+  // every step: ranks in [0, n - t) or negative (unused), distinct, >= 1 used
+  std::vector<int32_t> hr((size_t)k * s);
+  KM_CUDA(cudaMemcpyAsync(hr.data(), ranks, 4 * hr.size(), cudaMemcpyDeviceToHost, c.s));
+  KM_CUDA(cudaStreamSynchronize(c.s));
+  std::vector<int32_t> stamp((size_t)n, -1);
+  for (int t = 0; t < k; ++t) {
+    int used = 0;
+    for (int j = 0; j < s; ++j) {
+      const int32_t v = hr[(size_t)t * s + j];
+      if (v < 0) continue;
+      if ((int64_t)v >= n - t)
+        return fail(KM_E_INVALID, "LAB rank %d of step %d is outside [0, %lld)", v, t,
+                    (long long)(n - t));
+      if (stamp[v] == t) return fail(KM_E_INVALID, "LAB rank %d repeated in step %d", v, t);
+      stamp[v] = t;
+      ++used;
+    }
+    if (!used) return fail(KM_E_INVALID, "LAB step %d has an empty subsample", t);
+  }
+  ia.s = s;
+  ia.ranks = ranks;
+  KM_LAUNCH(c, launch_init_lab(dtype, ia, c.s));
+  r = init_finish(c, medoids_out);
+  if (r != KM_OK) return r;
+  if (gains_host) {
+    KM_CUDA(cudaMemcpyAsync(gains_host, c.at<double>(c.L.gains), 8 * (size_t)k,
+                            cudaMemcpyDeviceToHost, c.s));
+    KM_CUDA(cudaStreamSynchronize(c.s));
+  }
+  return KM_OK;
+}
+
 }  // extern "C"

@@ -92,6 +92,28 @@ struct PointArgs {
   unsigned* scan; // matrix scan result: [0] max |d| bits, [1] invalid flag
 };
 
+// Initialisation kernels (Sec. 3.3): distance-weighted seeding and LAB.
+struct InitArgs {
+  const void* D;
+  long long ld;
+  int n;
+  int k;
+  int s;                 // LAB: subsample entries per step
+  int fshift;            // fixed-point exponent f (float data)
+  const double* u;       // weighted: k uniform numbers (DEVICE)
+  const int32_t* ranks;  // LAB: k x s subsample ranks (DEVICE)
+  int32_t* med;          // k chosen medoids (DEVICE)
+  double* gains;         // LAB: each step's least gain (may be NULL)
+  void* dn;              // n_pad distances to the nearest chosen medoid
+  uint8_t* flags;        // n_pad drawn flags
+  long long* csum;       // weighted: ceil(n/32) chunk weight sums
+  KmState* st;
+};
+
+size_t init_lab_smem(int k, int s);
+cudaError_t launch_init_weighted(int dtype, const InitArgs& a, cudaStream_t s);
+cudaError_t launch_init_lab(int dtype, const InitArgs& a, cudaStream_t s);
+
 // Launch configuration chosen for a (mode, k) pair.
 struct StreamConfig {
   int rows;       // candidate rows per tile (R)

@@ -28,7 +28,8 @@ EXPORTS = ["km_default_options", "kmedoids_workspace_size", "kmedoids_build",
            "kmedoids_swap_features", "kmedoids_batched_workspace_size",
            "kmedoids_batched_distances", "kmedoids_run_batched",
            "kmedoids_swap_batched", "kmedoids_clara_workspace_size", "kmedoids_clara",
-           "kmedoids_geometry_info"]
+           "kmedoids_geometry_info", "kmedoids_init_weighted",
+           "kmedoids_init_lab"]
 
 
 class KmError(RuntimeError):
@@ -129,6 +130,11 @@ def load(path: str = LIB_PATH):
         lib.kmedoids_clara.restype = i32
         lib.kmedoids_geometry_info.argtypes = [i32, P, P, P]
         lib.kmedoids_geometry_info.restype = ctypes.c_int
+        lib.kmedoids_init_weighted.argtypes = [P, i32, i64, i64, i32, P, P, P, sz, P]
+        lib.kmedoids_init_weighted.restype = i32
+        lib.kmedoids_init_lab.argtypes = [P, i32, i64, i64, i32, i32, P, P, P, P, sz,
+                                          P]
+        lib.kmedoids_init_lab.restype = i32
         lib.kmedoids_last_error.restype = ctypes.c_char_p
         lib.kmedoids_version.restype = ctypes.c_char_p
         _LIB = lib
@@ -365,6 +371,49 @@ def cache(D, medoids, n=None, ws=None):
         ctypes.c_void_p(ds.data_ptr()), ctypes.c_void_p(rl.data_ptr()),
         ctypes.c_void_p(ws.data_ptr()), ws.numel(), _stream()))
     return near, sec, dn, ds, rl
+
+
+def init_weighted(D, k, u, n=None, ws=None):
+    """Distance-weighted initialisation (kmedoids_init_weighted): u holds k
+    uniform numbers in [0, 1) (array or CUDA float64 tensor).  Returns the
+    k drawn medoids (int32 CUDA tensor, draw order)."""
+    torch = _torch()
+    lib = load()
+    n, ld = _matrix(D, n)
+    code = _dtype_code(D)
+    u = torch.as_tensor(u, dtype=torch.float64).to(D.device).contiguous()
+    if ws is None:
+        ws = workspace(n, k, code, None, device=D.device)
+    med = torch.empty(k, dtype=torch.int32, device=D.device)
+    _check(lib.kmedoids_init_weighted(
+        ctypes.c_void_p(D.data_ptr()), code, n, ld, int(k),
+        ctypes.c_void_p(u.data_ptr()), ctypes.c_void_p(med.data_ptr()),
+        ctypes.c_void_p(ws.data_ptr()), ws.numel(), _stream()))
+    return med
+
+
+def init_lab(D, k, ranks, n=None, ws=None):
+    """LAB initialisation (kmedoids_init_lab): ranks (k x s, array or int32
+    CUDA tensor) name each step's subsample among the current non-medoids.
+    Returns (medoids int32 CUDA tensor, per-step gains as a numpy array)."""
+    import numpy as np
+    torch = _torch()
+    lib = load()
+    n, ld = _matrix(D, n)
+    code = _dtype_code(D)
+    r = torch.as_tensor(ranks, dtype=torch.int32).to(D.device).contiguous()
+    if r.dim() != 2:
+        raise ValueError("ranks must be k x s")
+    if ws is None:
+        ws = workspace(n, k, code, None, device=D.device)
+    med = torch.empty(k, dtype=torch.int32, device=D.device)
+    gains = np.zeros(max(int(k), 1), np.float64)
+    _check(lib.kmedoids_init_lab(
+        ctypes.c_void_p(D.data_ptr()), code, n, ld, int(k), int(r.shape[1]),
+        ctypes.c_void_p(r.data_ptr()), ctypes.c_void_p(med.data_ptr()),
+        gains.ctypes.data_as(ctypes.c_void_p), ctypes.c_void_p(ws.data_ptr()),
+        ws.numel(), _stream()))
+    return med, gains[:k]
 
 
 def gram_bf16(X):
