@@ -90,7 +90,16 @@ typedef struct km_options {
   double tol;             /* a swap is applied iff Delta < -tol (default 0) */
   double fastpam2_tol;    /* FastPAM2 applies an additional swap iff its
                              recomputed Delta < -fastpam2_tol * |Delta*| */
-  int32_t rows_per_tile;  /* candidate rows per CTA tile; 0 = automatic */
+  int32_t rows_per_tile;  /* candidate rows per CTA tile; 0 = automatic.
+                             FasterPAM / FastCLARANS: scan positions per
+                             CTA in the longest window (0 = 8); a window
+                             spans one position per CTA right after a swap
+                             and doubles, up to this, while none is found.
+                             They run as one persistent cooperative launch
+                             (one CTA of 512 threads per SM) that
+                             evaluates a window, takes the first improving
+                             position and applies it without returning to
+                             the host. */
   int32_t profile;        /* nonzero: time kernels with CUDA events */
   int32_t trace_capacity; /* entries available in the trace arrays */
   int32_t tune;           /* matrix-form kernel geometry (tile rows, ring
@@ -148,14 +157,14 @@ typedef struct km_result {
   int64_t kernel_launches; /* kernels this call launched (all phases) */
   int32_t best_sample;     /* kmedoids_clara: index of the winning sample */
   int16_t swap_geometry;   /* geometry table entries (1..16) the SWAP and */
-  int16_t build_geometry;  /* BUILD passes ran with; 0 = not run */
+  int16_t build_geometry;  /* BUILD passes ran with; 0 = not run, or (SWAP)
+                              the eager kernel of FasterPAM / FastCLARANS */
 } km_result;
 
 /* Parameters of a matrix-form geometry table entry (1..16, as reported in
  * km_result.swap_geometry / build_geometry and accepted by opts->tune):
  * candidate rows per tile, shared-memory ring stages, CTAs per SM.  A pass
- * launches min(SMs x ctas_per_sm, ceil(n / rows), 1024) CTAs; a FasterPAM
- * or FastCLARANS window covers that many times rows positions.  Returns 0,
+ * launches min(SMs x ctas_per_sm, ceil(n / rows), 1024) CTAs.  Returns 0,
  * or 1 for an unknown entry (outputs untouched; NULL outputs skipped). */
 int kmedoids_geometry_info(int32_t geometry, int32_t *rows, int32_t *stages,
                            int32_t *ctas_per_sm);

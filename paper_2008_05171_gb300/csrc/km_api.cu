@@ -481,6 +481,51 @@ km_status do_swap(Ctx& c, Timer& tm, std::vector<std::pair<int, int>>& ev, KmSta
     sa.draws_len = c.opt.draws_len;
     sa.maxneighbor = c.opt.maxneighbor;
   }
+  if (flavour == kFasterPAM || flavour == kCLARANS) {
+    // the eager variants run as one persistent cooperative launch when every
+    // CTA of its grid can be resident (the usual case)
+    const int eg = eager_grid(c.dtype, c.k);
+    const int rows = c.opt.rows_per_tile > 0 ? c.opt.rows_per_tile : 8;
+    const long long cap = (long long)kMaxGrid * kMaxRows / 2;
+    if (eg > 0 && (long long)eg * rows <= cap) {
+      EagerArgs ea;
+      memset(&ea, 0, sizeof(ea));
+      ea.D = c.D;
+      ea.ld = c.ld;
+      ea.n = c.n;
+      ea.k = c.k;
+      ea.k_pad = c.L.k_pad;
+      ea.fshift = c.fshift;
+      ea.med = c.at<int32_t>(c.L.med);
+      ea.is_med = c.at<uint8_t>(c.L.is_med);
+      ea.near = c.at<int32_t>(c.L.near);
+      ea.sec = c.at<int32_t>(c.L.sec);
+      ea.dn = c.at<void>(c.L.dn);
+      ea.ds = c.at<void>(c.L.ds);
+      ea.removal = c.at<void>(c.L.removal);
+      ea.td2 = c.at<void>(c.L.td2);
+      ea.st = c.st();
+      ea.win_delta = c.at<double>(c.L.win_delta);
+      ea.win_slot = c.at<int32_t>(c.L.win_slot);
+      ea.win_cap = cap;
+      ea.win_rows = rows;
+      ea.bar = c.st()->bar;
+      ea.trace = c.at<void>(c.L.trace);
+      ea.trace_cap = c.L.trace_cap;
+      ea.flavour = flavour;
+      ea.draws = c.opt.draws;
+      ea.draws_len = c.opt.draws_len;
+      ea.maxneighbor = c.opt.maxneighbor;
+      ea.max_pos = (long long)c.opt.max_iter * c.n;
+      ea.tol = c.opt.tol;
+      c.swap_geom = 0;
+      const int e0 = tm.mark();
+      KM_LAUNCH(c, launch_eager(c.dtype, eg, ea, c.s));
+      const int e1 = tm.mark();
+      ev.push_back({e0, e1});
+      return read_state(c, h);
+    }
+  }
   StreamConfig cfg;
   r = config_for(c, kModeSwap, flavour, sa, &cfg);
   if (r != KM_OK) return r;

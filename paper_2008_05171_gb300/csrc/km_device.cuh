@@ -60,7 +60,10 @@ struct KmState {
   unsigned scan_bad;        // matrix scan: 1 if an entry is < 0 or not finite
   long long fails;          // FastCLARANS: consecutive failed draws
   long long evaluated;      // FastCLARANS: draws evaluated
+  long long win_len;        // FasterPAM / FastCLARANS: next window length
+  unsigned bar[2];          // grid barrier of the eager kernel: count, generation
 };
+static_assert(sizeof(KmState) <= 512, "the workspaces reserve 512 bytes for the state record");
 
 // Trace record of an applied swap.
 struct TraceRec {

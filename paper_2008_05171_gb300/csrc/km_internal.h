@@ -92,6 +92,43 @@ struct PointArgs {
   unsigned* scan; // matrix scan result: [0] max |d| bits, [1] invalid flag
 };
 
+// The eager variants (FasterPAM, FastCLARANS) as one persistent cooperative
+// launch (km_eager.cu).
+struct EagerArgs {
+  const void* D;
+  long long ld;
+  int n;
+  int k;
+  int k_pad;
+  int fshift;
+  int32_t* med;
+  uint8_t* is_med;
+  int32_t* near;
+  int32_t* sec;
+  void* dn;
+  void* ds;
+  void* removal;          // [2][k_pad] fixed point / int64
+  void* td2;              // [2] exact TD
+  KmState* st;
+  double* win_delta;      // [2][win_cap] per-position Delta of a window
+  int32_t* win_slot;      // [2][win_cap] its best slot (-1: not evaluated)
+  long long win_cap;
+  int win_rows;           // largest window = grid x win_rows positions
+  unsigned* bar;          // grid barrier: arrival count, generation
+  void* trace;            // TraceRec[trace_cap]
+  int trace_cap;
+  int flavour;            // kFasterPAM or kCLARANS
+  const int32_t* draws;   // FastCLARANS draws (DEVICE)
+  long long draws_len;
+  long long maxneighbor;
+  long long max_pos;      // FasterPAM: scan positions allowed (max_iter n)
+  double tol;
+};
+
+size_t eager_smem(int k);
+int eager_grid(int dtype, int k);  // co-resident CTAs, 0 if it cannot run
+cudaError_t launch_eager(int dtype, int grid, const EagerArgs& a, cudaStream_t s);
+
 // Initialisation kernels (Sec. 3.3): distance-weighted seeding and LAB.
 struct InitArgs {
   const void* D;

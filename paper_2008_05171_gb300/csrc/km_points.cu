@@ -110,6 +110,35 @@ __global__ void __launch_bounds__(kPtThreads) k_cache_init(const PointArgs a) {
 }
 
 // -------------------------------------------------------------- apply swap
+// Lexicographic (distance, slot) order of cache entries; slot < 0 = empty.
+template <class T>
+__device__ __forceinline__ bool entry_less(T da, int sa, T db, int sb) {
+  if (sb < 0) return sa >= 0;
+  if (sa < 0) return false;
+  return da < db || (da == db && sa < sb);
+}
+
+// Merge of two top-2 lists: the two least entries of {a1, a2, b1, b2}.
+template <class T>
+__device__ __forceinline__ void top2_merge(int& n1, T& d1, int& n2, T& d2, int m1, T e1, int m2,
+                                           T e2) {
+  if (entry_less(e1, m1, d1, n1)) {
+    // e1 is the least; the second is the lesser of d1 and e2
+    if (entry_less(e2, m2, d1, n1)) {
+      n2 = m2;
+      d2 = e2;
+    } else {
+      n2 = n1;
+      d2 = d1;
+    }
+    n1 = m1;
+    d1 = e1;
+  } else if (entry_less(e1, m1, d2, n2)) {
+    n2 = m1;
+    d2 = e1;
+  }
+}
+
 template <class T>
 __global__ void __launch_bounds__(kPtThreads) k_apply(const PointArgs a) {
   using A = typename Tr<T>::A;  // removal loss (fixed point / int64)
@@ -119,12 +148,15 @@ __global__ void __launch_bounds__(kPtThreads) k_apply(const PointArgs a) {
   G* scratch = reinterpret_cast<G*>(sacc + a.k);
   const int f = a.fshift;
   __shared__ int is_last;
+  __shared__ int s_cnt;
+  __shared__ int s_list[kPtThreads];
   KmState* st = a.st;
   if (st->error || !st->accept) return;  // uniform for the launch
   const int k = a.k, n = a.n;
   const int i_s = st->best_slot, c_s = st->best_cand;
   const int rb = st->rb;
   for (int i = threadIdx.x; i < k; i += blockDim.x) sacc[i] = A(0);
+  if (threadIdx.x == 0) s_cnt = 0;
   __syncthreads();
   const int o = blockIdx.x * blockDim.x + threadIdx.x;
   const T* D = static_cast<const T*>(a.D);
@@ -135,15 +167,9 @@ __global__ void __launch_bounds__(kPtThreads) k_apply(const PointArgs a) {
     int n1 = a.near[o], n2 = a.sec[o];
     T d1 = dn[o], d2 = ds[o];
     if (n1 == i_s || n2 == i_s) {
-      // the removed medoid was nearest or second: rescan every slot
-      n1 = -1;
-      n2 = -1;
-      d1 = Tr<T>::high();
-      d2 = Tr<T>::high();
-      for (int j = 0; j < k; ++j) {
-        const int m = (j == i_s) ? c_s : a.med[j];
-        top2_push(D[(size_t)m * a.ld + o], j, n1, d1, n2, d2);
-      }
+      // the removed medoid was nearest or second: a full rescan, done below
+      // by a whole warp
+      s_list[atomicAdd(&s_cnt, 1)] = threadIdx.x;
     } else {
       // only the new medoid enters: top-2 of {nearest, second, new}
       const T dc = D[(size_t)c_s * a.ld + o];
@@ -156,13 +182,43 @@ __global__ void __launch_bounds__(kPtThreads) k_apply(const PointArgs a) {
         n2 = i_s;
         d2 = dc;
       }
+      a.near[o] = n1;
+      a.sec[o] = n2;
+      dn[o] = d1;
+      ds[o] = d2;
+      atomic_add_shared64(&sacc[n1], Tr<T>::fx(d2, f) - Tr<T>::fx(d1, f));
+      tdl = G(d1);
     }
-    a.near[o] = n1;
-    a.sec[o] = n2;
-    dn[o] = d1;
-    ds[o] = d2;
-    atomic_add_shared64(&sacc[n1], Tr<T>::fx(d2, f) - Tr<T>::fx(d1, f));
-    tdl = G(d1);
+  }
+  __syncthreads();
+  // Rescans: a warp per point, lanes over the slots (each lane keeps the
+  // top-2 of its slots, then a butterfly merge under (distance, slot)).
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int cnt = s_cnt;
+  for (int e = warp; e < cnt; e += kPtThreads / 32) {
+    const int oo = blockIdx.x * blockDim.x + s_list[e];
+    int n1 = -1, n2 = -1;
+    T d1 = Tr<T>::high(), d2 = Tr<T>::high();
+    for (int j = lane; j < k; j += 32) {
+      const int m = (j == i_s) ? c_s : a.med[j];
+      top2_push(D[(size_t)m * a.ld + oo], j, n1, d1, n2, d2);
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      const int m1 = __shfl_xor_sync(0xffffffffu, n1, off);
+      const int m2 = __shfl_xor_sync(0xffffffffu, n2, off);
+      const T e1 = __shfl_xor_sync(0xffffffffu, d1, off);
+      const T e2 = __shfl_xor_sync(0xffffffffu, d2, off);
+      top2_merge(n1, d1, n2, d2, m1, e1, m2, e2);
+    }
+    if (lane == 0) {
+      a.near[oo] = n1;
+      a.sec[oo] = n2;
+      dn[oo] = d1;
+      ds[oo] = d2;
+      atomic_add_shared64(&sacc[n1], Tr<T>::fx(d2, f) - Tr<T>::fx(d1, f));
+      tdl += G(d1);
+    }
   }
   const G bs = block_sum(tdl, scratch);
   A* rem = static_cast<A*>(a.removal) + (size_t)(rb ^ 1) * a.k_pad;

@@ -236,18 +236,25 @@ __global__ void __launch_bounds__(kThreads, MINB) k_stream(const StreamArgs a) {
   }
   __syncthreads();
 
-  // Candidate positions: FasterPAM windows give each CTA the positions
-  // [p_lo, p_hi) (row = p mod n); full passes hand out tiles of R rows from
-  // an atomic counter so that CTAs on faster paths take more tiles.
+  // Candidate positions: a FasterPAM / FastCLARANS window is the next wl
+  // scan positions (row = p mod n, or the p-th draw), dealt round-robin so
+  // that CTA b takes base + b, base + b + G, ... (G = grid size, at most R
+  // each); its length adapts on the device (see the decision below).  Full
+  // passes hand out tiles of R rows from an atomic counter so that CTAs on
+  // faster paths take more tiles.
   const bool clarans = (MODE == kModeSwap && a.flavour == kCLARANS);
   const bool windowed = (MODE == kModeSwap && (a.flavour == kFasterPAM || clarans));
-  long long base = 0, p_lo = 0, p_hi = 0;
+  const long long wmax = (long long)gridDim.x * a.win_rows;
+  long long base = 0, p_lo = 0, p_hi = 0, wl = 0;
   if (windowed) {
     base = st->pos;
     const long long stop =
         clarans ? a.draws_len : ((st->last < 0) ? (long long)n : st->last + n);
-    p_lo = base + (long long)blockIdx.x * a.win_rows;
-    p_hi = p_lo + a.win_rows;
+    wl = st->win_len;
+    if (wl <= 0) wl = gridDim.x;
+    if (wl > wmax) wl = wmax;
+    p_lo = base + (long long)blockIdx.x;
+    p_hi = base + wl;
     if (p_hi > stop) p_hi = stop;
   }
   const unsigned ntiles = (unsigned)((n + R - 1) / R);
@@ -273,7 +280,7 @@ __global__ void __launch_bounds__(kThreads, MINB) k_stream(const StreamArgs a) {
               outs[nr] = (int)(p - base);
               ++nr;
             }
-            ++p;
+            p += gridDim.x;
           }
           if (nr == 0) break;
         } else {
@@ -600,7 +607,7 @@ __global__ void __launch_bounds__(kThreads, MINB) k_stream(const StreamArgs a) {
     // FastCLARANS: the first improving draw of the window, in draw order,
     // unless maxneighbor consecutive draws fail before it (Sec. 3.4)
     const long long stop = a.draws_len;
-    long long wlen = (long long)gridDim.x * a.win_rows;
+    long long wlen = wl;
     if (base + wlen > stop) wlen = stop - base;
     int* firstw = scratch_int;
     int* nfail = scratch_int + 1;
@@ -650,12 +657,14 @@ __global__ void __launch_bounds__(kThreads, MINB) k_stream(const StreamArgs a) {
         st->evaluated += F + 1;
         st->last = base + fw;
         st->pos = base + fw + 1;
+        st->win_len = gridDim.x;
       } else {
         st->accept = 0;
         st->fails += F;
         st->evaluated += F;
         st->pos = base + wlen;
         if (st->pos >= stop) st->done = 1;
+        st->win_len = (2 * wl < wmax) ? 2 * wl : wmax;
       }
       st->iter += 1;
       st->ticket = 0;
@@ -663,10 +672,16 @@ __global__ void __launch_bounds__(kThreads, MINB) k_stream(const StreamArgs a) {
     return;
   }
 
+  // Window length of the next launch: one position per CTA after a swap
+  // (swaps are then frequent, and a window of G rows costs little more than
+  // the launch), doubled up to G R after a window without one (a converged
+  // scan then streams at full bandwidth).  The decisions do not depend on
+  // the window length: positions after the first improving one are
+  // evaluated again against the new state.
   if (a.flavour == kFasterPAM) {
     // first improving candidate of the window, in scan order
     const long long stop = (st->last < 0) ? (long long)n : st->last + n;
-    long long wlen = (long long)gridDim.x * a.win_rows;
+    long long wlen = wl;
     if (base + wlen > stop) wlen = stop - base;
     int* firstw = scratch_int;
     if (t == 0) *firstw = INT_MAX;
@@ -689,10 +704,12 @@ __global__ void __launch_bounds__(kThreads, MINB) k_stream(const StreamArgs a) {
         st->best_cand = (int)((base + w) % n);
         st->last = base + w;
         st->pos = base + w + 1;
+        st->win_len = gridDim.x;
       } else {
         st->accept = 0;
         st->pos = base + wlen;
         if (st->pos >= stop) st->done = 1;
+        st->win_len = (2 * wl < wmax) ? 2 * wl : wmax;
       }
       st->iter += 1;
       st->ticket = 0;

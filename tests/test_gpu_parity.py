@@ -338,6 +338,47 @@ def test_measured_geometry_same_result(variant):
     for r in (b, c):
         assert r["medoids"].cpu().tolist() == a["medoids"].cpu().tolist()
         assert r["td_i64"] == a["td_i64"] and r["swaps"] == a["swaps"]
-        assert 1 <= r["swap_geometry"] <= 16 and 1 <= r["build_geometry"] <= 16
+        assert 1 <= r["build_geometry"] <= 16
+        # the eager variants run in their own persistent kernel (geometry 0)
+        assert (r["swap_geometry"] == 0) if variant == "fasterpam" else \
+            (1 <= r["swap_geometry"] <= 16)
     assert (b["swap_geometry"], b["build_geometry"]) == (c["swap_geometry"], c["build_geometry"])
-    assert c["kernel_launches"] < b["kernel_launches"]  # no timing passes the second time
+    # no timing passes the second time (the eager SWAP kernel has none, and
+    # BUILD was tuned for this shape by the first parameter of this test)
+    if variant == "fasterpam":
+        assert c["kernel_launches"] <= b["kernel_launches"]
+    else:
+        assert c["kernel_launches"] < b["kernel_launches"]
+
+
+@pytest.mark.parametrize("rows", [1, 4, 16])
+def test_fasterpam_window_lengths_same_trajectory(rows):
+    """FasterPAM and FastCLARANS evaluate adaptive windows of scan positions
+    (one per CTA after a swap, doubling after a window without one); the
+    trajectory is that of the sequential scan (Alg. 4) whatever the tile
+    rows, i.e. whatever the largest window: integer data from a random
+    start with frequent swaps (k = 40), against the oracle."""
+    n, k = 2600, 40
+    Dh = int_instance(n, ("win", rows))
+    start = rand_medoids(n, k, 99)
+    out = km.swap(dev(Dh), start, variant="fasterpam", rows_per_tile=rows, trace=100000)
+    ref = oracle.swap(Dh, start, variant="fasterpam", trace_cap=100000)
+    assert_same_run(out, ref)
+    assert out["visited"] == ref["visited"]
+
+
+def test_apply_rescans_large_k():
+    """The swap's cache update rescans a point with a whole warp (lanes over
+    the slots, butterfly merge of top-2 lists): k = 150 (several slots per
+    lane), ties from duplicated points; every FastPAM1 decision and the
+    final labels equal the oracle's."""
+    n, k = 3000, 150
+    P = np.repeat(wl.int_coords(n // 2, 2, 60, seed="rescan"), 2, axis=0)
+    Dh = wl.manhattan_int32(P)
+    start = rand_medoids(n, k, 5)
+    out = km.swap(dev(Dh), start, variant="fastpam1", trace=100000)
+    ref = oracle.swap(Dh, start, variant="fastpam1", trace_cap=100000)
+    assert_same_run(out, ref)
+    # labels come from the incrementally updated cache
+    _, olab = oracle.td(Dh, ref["medoids"], return_labels=True)
+    assert (out["labels"].cpu().numpy() == olab).all()
