@@ -50,6 +50,12 @@ WORKLOADS = {
                                "f32 GMM, 100 clusters): k=100, a uniform random start, "
                                "uniform random candidate draws with replacement, stop after "
                                "maxneighbor = 2.5% of n-k = 497 consecutive failed draws"),
+    "fasterpam_20000": dict(n=20000, d=16, centers=100, k=100, recipe="gmm_20000_points",
+                            desc="the paper's recommended pipeline (Sec. 4.3, Sec. 6) on the "
+                                 "gmm_20000 matrix (n=20000 d=16 f32 GMM, 100 clusters): "
+                                 "distance-weighted initialisation (Sec. 3.3) from fixed "
+                                 "uniform numbers, then eager FasterPAM (Alg. 4) to "
+                                 "convergence, k=100"),
     "gmm_50000": dict(n=50000, d=32, centers=200, k=200, recipe="gmm_50000_points",
                       desc="n=50000 d=32 f32 GMM (200 clusters, centres U[-10,10]^32, "
                            "sigma U[0.5,2], Dirichlet(1) weights), Euclidean f32 "
@@ -405,6 +411,147 @@ def run_batched(args, rank, world, local_rank):
     return line
 
 
+def eager_roofline(r, n, kernel):
+    """The eager kernel (one persistent launch per call): the rows the
+    sequential scan evaluates, 4 B per (candidate, point) pair, over the
+    launch's CUDA-event time.  Its decisions are sequential (Alg. 4), so it
+    is bound by the latency of one window + barrier + swap per accepted
+    swap, far below HBM bandwidth; the fraction says so."""
+    peak, pk = peaks()
+    nbytes = int(r["evaluated"]) * n * 4
+    ms = float(r["eval_ms"])
+    ach = nbytes / (ms / 1e3) / 1e9
+    return {"bound": "hbm", "achieved": round(ach, 1), "peak": peak, "unit": "GB/s",
+            "frac": round(ach / peak, 4), "kernel": kernel,
+            "algorithmic_bytes_per_launch": nbytes, "avg_launch_ms": round(ms, 5),
+            "peak_source": pk, "traffic": None,
+            "note": "sequential eager decisions: one window evaluation, grid barrier and "
+                    "swap per accepted swap (latency-bound)"}
+
+
+def fasterpam_inputs(n, k):
+    from paper_2008_05171_gb300 import workloads as wl
+    return wl.rng_for(("fasterpam", n, k)).random(k)
+
+
+def replay_evaluated(start, trace, visited, n):
+    """Candidates the sequential FasterPAM scan evaluates: non-medoid
+    positions up to `visited`, applying each swap where the scan meets its
+    candidate."""
+    med = list(int(x) for x in start)
+    inset = set(med)
+    ev, sw = 0, 0
+    for p in range(visited):
+        r = p % n
+        if r in inset:
+            continue
+        ev += 1
+        if sw < len(trace) and trace[sw][2] == r:
+            inset.discard(med[trace[sw][1]])
+            med[trace[sw][1]] = r
+            inset.add(r)
+            sw += 1
+    return ev
+
+
+def oracle_fasterpam_run(Dh, n, k):
+    """The oracle's distance-weighted start + FasterPAM (one core), timed."""
+    import oracle
+    u = fasterpam_inputs(n, k)
+    t0 = time.perf_counter()
+    start = oracle.init_weighted(Dh, k, u)
+    r = oracle.swap(Dh, start, variant="fasterpam", trace_cap=100000)
+    dt = time.perf_counter() - t0
+    ev = replay_evaluated(start, r["trace"], r["visited"], n)
+    return {"value": (ev * n + k * n) / dt, "unit": "point-evals/s", "cores": 1,
+            "kind": "oracle", "seconds": dt,
+            "sample": "the whole workload: distance-weighted start + FasterPAM of the FP64 C "
+                      "oracle (one core) on the same matrix and uniform numbers: %d candidates "
+                      "evaluated, %d swaps, %.1f s" % (ev, r["swaps"], dt)}
+
+
+def run_fasterpam(args, rank, world, local_rank):
+    """Distance-weighted start + FasterPAM to convergence per step."""
+    import torch
+    import paper_2008_05171_gb300.kmedoids as km
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    D, spec = make_input(args.workload, dev)
+    n, k = spec["n"], spec["k"]
+    u = torch.from_numpy(fasterpam_inputs(n, k)).to(dev)
+    ws = km.workspace(n, k, km.KM_F32, km.options(profile=True), device=dev)
+    torch.cuda.synchronize()
+
+    def step(Dm):
+        start = km.init_weighted(Dm, k, u, ws=ws)
+        return km.swap(Dm, start, ws=ws, variant="fasterpam", profile=True)
+
+    for _ in range(args.warmup):
+        step(D)
+    torch.cuda.synchronize()
+    barrier(world)
+    clocks = Clocks(local_rank)
+    clocks.start()
+    stream = torch.cuda.current_stream()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    results = []
+    for i in range(args.steps):
+        ev[i][0].record(stream)
+        results.append(step(D))
+        ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    ck = clocks.stop()
+    total_ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in ev), world, dev)
+    r0 = results[-1]
+    evals = sum(int(r["evaluated"]) * n + k * n for r in results)
+    value = world * evals / (total_ms / 1e3)
+    e2e = None
+    if not args.no_e2e:
+        Dh = torch.empty(D.shape, dtype=D.dtype, pin_memory=True)
+        Dh.copy_(D)
+        Dd = torch.empty_like(D)
+        med_h = torch.empty(k, dtype=torch.int32, pin_memory=True)
+        lab_h = torch.empty(n, dtype=torch.int32, pin_memory=True)
+        torch.cuda.synchronize()
+        e_ms, e_ev = 0.0, 0
+        for _ in range(max(1, min(args.steps, 3))):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            Dd.copy_(Dh, non_blocking=True)
+            r = step(Dd)
+            med_h.copy_(r["medoids"], non_blocking=True)
+            lab_h.copy_(r["labels"], non_blocking=True)
+            b.record(stream)
+            torch.cuda.synchronize()
+            e_ms += a.elapsed_time(b)
+            e_ev += int(r["evaluated"]) * n + k * n
+        e2e = {"value": world * e_ev / (e_ms / 1e3), "unit": "point-evals/s",
+               "h2d_bytes_per_step": int(D.numel() * 4), "d2h_bytes_per_step": 4 * k + 4 * n}
+        del Dh, Dd
+    line = {
+        "metric": "SWAP dTD point-evals/sec + full PAM run time (k=100/200); % HBM roofline",
+        "value": value, "unit": "point-evals/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32 (exact 64-bit fixed-point dTD sums, FP64 TD)", "data": "synthetic",
+        "config": {"workload": args.workload + ": " + spec["desc"], "n": n, "k": k,
+                   "l2": "matrix larger than L2 (no flush needed)",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "full_run_ms": total_ms / args.steps, "swaps": int(r0["swaps"]),
+        "evaluated": int(r0["evaluated"]), "visited": int(r0["visited"]),
+        "scans": int(r0["iterations"]), "fasterpam_ms": float(r0["swap_ms"]), "td": r0["td"],
+        "roofline": eager_roofline(r0, n, "k_eager<float> (FasterPAM)"),
+        "gpu_launches": int(sum(r["kernel_launches"] for r in results)) + 2 * args.steps,
+        "clocks": ck, "e2e": e2e,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cb = oracle_fasterpam_run(D.cpu().numpy(), n, k)
+        cb.pop("seconds")
+        line["cpu_baseline"] = cb
+    return line
+
+
 def run_clarans(args, rank, world, local_rank):
     """FastCLARANS from a fixed random start over fixed random draws."""
     import torch
@@ -445,13 +592,6 @@ def run_clarans(args, rank, world, local_rank):
     r0 = results[-1]
     evals = sum(int(r["iterations"]) * n for r in results)  # draws evaluated x points
     value = world * evals / (total_ms / 1e3)
-    rows, _, minb = km.geometry_info(r0["swap_geometry"])
-    sms = torch.cuda.get_device_properties(dev).multi_processor_count
-    grid = min(sms * minb, (n + rows - 1) // rows, 1024)
-    win_bytes = grid * rows * n * 4  # rows one window streams (medoid rows skipped: < 1 %)
-    launch_ms = r0["eval_ms"] / max(1, r0["eval_launches"])
-    peak, pk = peaks()
-    ach = win_bytes / (launch_ms / 1e3) / 1e9
     line = {
         "metric": "SWAP dTD point-evals/sec + full PAM run time (k=100/200); % HBM roofline",
         "value": value, "unit": "point-evals/s", "n_gpus": world, "steps": args.steps,
@@ -463,12 +603,9 @@ def run_clarans(args, rank, world, local_rank):
                    "l2": "matrix larger than L2 (no flush needed)",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "draws_consumed": int(r0["visited"]), "draws_evaluated": int(r0["iterations"]),
-        "swaps": int(r0["swaps"]), "windows": int(r0["eval_launches"]),
+        "swaps": int(r0["swaps"]),
         "stopped_by_maxneighbor": bool(r0["converged"]), "td": r0["td"],
-        "roofline": {"bound": "hbm", "achieved": round(ach, 1), "peak": peak, "unit": "GB/s",
-                     "frac": round(ach / peak, 4), "kernel": "k_stream<float,SWAP> FastCLARANS window",
-                     "algorithmic_bytes_per_launch": win_bytes, "avg_launch_ms": round(launch_ms, 5),
-                     "peak_source": pk, "traffic": None},
+        "roofline": eager_roofline(r0, n, "k_eager<float> (FastCLARANS)"),
         "gpu_launches": int(sum(r["kernel_launches"] for r in results)),
         "clocks": ck, "e2e": None,
     }
@@ -484,6 +621,8 @@ def run_ours(args, rank, world, local_rank):
     import paper_2008_05171_gb300.kmedoids as km
     if args.workload.startswith("clarans"):
         return run_clarans(args, rank, world, local_rank)
+    if args.workload.startswith("fasterpam"):
+        return run_fasterpam(args, rank, world, local_rank)
     if args.workload.startswith("features"):
         return run_features(args, rank, world, local_rank)
     if args.workload.startswith("batched"):
@@ -775,6 +914,28 @@ def run_reference(args, rank, world):
                 "e2e": {"value": v, "unit": "point-evals/s", "h2d_bytes_per_step": 0,
                         "d2h_bytes_per_step": 0}}
     X = getattr(wl, spec["recipe"])()
+    if args.workload.startswith("fasterpam"):
+        dev = torch.device("cuda", 0) if torch.cuda.is_available() else torch.device("cpu")
+        Dh = (wl.euclidean_f32_torch(X, dev) if dev.type == "cuda"
+              else torch.from_numpy(wl.euclidean_f32(X))).cpu().numpy()
+        vals, secs, cb = [], [], None
+        for _ in range(args.warmup + args.steps):
+            cb = oracle_fasterpam_run(Dh, spec["n"], spec["k"])
+            vals.append(cb["value"])
+            secs.append(cb.pop("seconds"))
+        v = float(np.mean(vals[args.warmup:]))
+        cb["value"] = v
+        return {"impl": "reference", "metric": "SWAP dTD point-evals/sec + full PAM run time "
+                "(k=100/200); % HBM roofline", "value": v, "unit": "point-evals/s",
+                "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": 1e3 * float(np.mean(secs[args.warmup:])),
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f64", "data": "synthetic",
+                "config": {"workload": args.workload + ": " + spec["desc"], "n": spec["n"],
+                           "k": spec["k"]},
+                "cpu_baseline": cb,
+                "e2e": {"value": v, "unit": "point-evals/s", "h2d_bytes_per_step": 0,
+                        "d2h_bytes_per_step": 0}}
     if args.workload.startswith("clarans"):
         dev = torch.device("cuda", 0) if torch.cuda.is_available() else torch.device("cpu")
         Dh = (wl.euclidean_f32_torch(X, dev) if dev.type == "cuda"

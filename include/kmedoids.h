@@ -159,6 +159,11 @@ typedef struct km_result {
   int16_t swap_geometry;   /* geometry table entries (1..16) the SWAP and */
   int16_t build_geometry;  /* BUILD passes ran with; 0 = not run, or (SWAP)
                               the eager kernel of FasterPAM / FastCLARANS */
+  int64_t evaluated;       /* FasterPAM / FastCLARANS: candidates evaluated
+                              by the sequential scan (non-medoid positions
+                              up to each applied swap, and every position
+                              of the passes without one); each costs one
+                              pass over the n points */
 } km_result;
 
 /* Parameters of a matrix-form geometry table entry (1..16, as reported in

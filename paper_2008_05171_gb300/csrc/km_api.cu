@@ -752,6 +752,8 @@ static km_status run_impl(bool do_b, bool do_s, const void* D, int32_t dtype, in
         res->visited = h.pos;
         res->iterations = (int)h.evaluated;
       }
+      if (c.opt.variant == KM_FASTERPAM || c.opt.variant == KM_FASTCLARANS)
+        res->evaluated = h.evaluated;
       if (tm.on) res->swap_ms = tm.ms(s0, s1);
     }
   } else {

@@ -342,17 +342,19 @@ __global__ void __launch_bounds__(kEThreads, 1) k_eager(const EagerArgs a) {
     bool swap_now = false;
     int i_s = -1, c_s = -1;
     double dlt = 0.0;
-    if (clarans) {
-      // evaluated draws before the first improving one
+    // evaluated positions (draws) before the first improving one
+    long long F = 0;
+    {
       long long cnt = 0;
       for (long long w = tid; w < wlen && w < fw; w += kEThreads)
         if (__ldcg(wsl + w) >= 0) ++cnt;
       cnt = warp_sum(cnt);
       if (lane == 0) s_cntw[warp] = cnt;
       __syncthreads();
-      long long F = 0;
       for (int q = 0; q < kEWarps; ++q) F += s_cntw[q];
       __syncthreads();
+    }
+    if (clarans) {
       if (fails + F >= a.maxneighbor) {
         // stop at the draw that makes the failure count reach maxneighbor:
         // the need-th evaluated draw of the window (segments per thread,
@@ -404,10 +406,12 @@ __global__ void __launch_bounds__(kEThreads, 1) k_eager(const EagerArgs a) {
     } else {
       if (fw != INT_MAX) {
         swap_now = true;
+        evaluated += F + 1;
         last = pos + fw;
         c_s = (int)((pos + fw) % n);
         pos = pos + fw + 1;
       } else {
+        evaluated += F;
         pos += wlen;
         if (pos >= stop) done = 1;
       }

@@ -684,7 +684,11 @@ __global__ void __launch_bounds__(kThreads, MINB) k_stream(const StreamArgs a) {
     long long wlen = wl;
     if (base + wlen > stop) wlen = stop - base;
     int* firstw = scratch_int;
-    if (t == 0) *firstw = INT_MAX;
+    int* nev = scratch_int + 1;
+    if (t == 0) {
+      *firstw = INT_MAX;
+      *nev = 0;
+    }
     KM_CSYNC();
     for (long long w = t; w < wlen; w += kConsThreads) {
       const int row = (int)((base + w) % n);
@@ -693,8 +697,19 @@ __global__ void __launch_bounds__(kThreads, MINB) k_stream(const StreamArgs a) {
         atomicMin(firstw, (int)w);
     }
     KM_CSYNC();
+    {
+      // evaluated (non-medoid) positions up to and including the first
+      // improving one
+      const int fw0 = *firstw;
+      int cnt = 0;
+      for (long long w = t; w < wlen && w <= fw0; w += kConsThreads)
+        if (!a.is_med[(int)((base + w) % n)]) ++cnt;
+      if (cnt) atomicAdd(nev, cnt);
+    }
+    KM_CSYNC();
     if (t == 0) {
       const int w = *firstw;
+      st->evaluated += *nev;
       if (w != INT_MAX) {
         const double dw = __ldcg(a.cand_delta + w);
         st->accept = 1;

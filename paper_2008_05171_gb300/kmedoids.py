@@ -66,7 +66,7 @@ class km_result(ctypes.Structure):
                 ("build_eval_ms", ctypes.c_double),
                 ("kernel_launches", ctypes.c_int64),
                 ("best_sample", ctypes.c_int32), ("swap_geometry", ctypes.c_int16),
-                ("build_geometry", ctypes.c_int16)]
+                ("build_geometry", ctypes.c_int16), ("evaluated", ctypes.c_int64)]
 
 
 _LOCK = threading.Lock()

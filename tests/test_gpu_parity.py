@@ -365,6 +365,19 @@ def test_fasterpam_window_lengths_same_trajectory(rows):
     ref = oracle.swap(Dh, start, variant="fasterpam", trace_cap=100000)
     assert_same_run(out, ref)
     assert out["visited"] == ref["visited"]
+    # candidates evaluated by the sequential scan: the non-medoid positions
+    # visited, replaying the swaps where the scan meets their candidates
+    med, ev, sw, p = list(start), 0, 0, 0
+    trace = ref["trace"]
+    while p < ref["visited"]:
+        r = p % n
+        if r not in med:
+            ev += 1
+            if sw < len(trace) and trace[sw][2] == r:
+                med[trace[sw][1]] = r
+                sw += 1
+        p += 1
+    assert sw == len(trace) and out["evaluated"] == ev
 
 
 def test_apply_rescans_large_k():
