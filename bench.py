@@ -271,6 +271,14 @@ def run_features(args, rank, world, local_rank):
         "gpu_launches": int(sum(r["kernel_launches"] for r in results)),
         "clocks": ck, "e2e": e2e,
     }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        # TD error of the result: the GPU's TD (bf16 Gram decisions, exact
+        # FP32 cache, FP64 sums) against the FP64 oracle's TD of the same
+        # medoids on the exact Euclidean distances of the same features
+        import oracle
+        td_ref = oracle.td_points(np.asarray(Xh, np.float32), r0["medoids"].cpu().numpy())
+        line["td_fp64_oracle"] = td_ref
+        line["td_rel_error"] = abs(r0["td"] - td_ref) / td_ref
     if rank == 0 and not args.no_cpu_baseline and world == 1:
         ns = 8000
         Ds = torch.from_numpy(wl.euclidean_f32(Xh[:ns].astype(np.float64)))

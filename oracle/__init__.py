@@ -8,7 +8,8 @@ CUDA library and the CUDA library never touches this.
 Every function follows a passage of Schubert & Rousseeuw, "Fast and Eager
 k-Medoids Clustering" (arXiv 2008.05171):
 
-* ``td``            -- Eq. (2) (TD objective), labels = lowest nearest slot.
+* ``td``            -- Eq. (2) (TD objective), labels = lowest nearest slot;
+                       ``td_points`` the same on feature vectors (FP64).
 * ``cache``         -- the per-point cache nearest / d_n / d_s of Sec. 2.
 * ``removal_loss``  -- Delta^{-m_i} of Eq. (7).
 * ``pam_build``     -- Alg. 1 (PAM BUILD), self term included in each gain;
@@ -91,6 +92,8 @@ def _lib():
             lib.oracle_build_gains.argtypes = [P, i32, i64, i64, P, i32, P]
             lib.oracle_init_weighted.restype = i32
             lib.oracle_init_weighted.argtypes = [P, i32, i64, i64, i32, P, P]
+            lib.oracle_td_points.restype = f64
+            lib.oracle_td_points.argtypes = [P, i64, i32, P, i32, P]
             lib.oracle_init_lab.restype = i32
             lib.oracle_init_lab.argtypes = [P, i32, i64, i64, i32, i32, P, P, P]
             lib.oracle_fixed_shift.restype = i32
@@ -146,6 +149,17 @@ def td(D, medoids, n=None, return_labels=False):
     med = _med(medoids)
     labels = np.empty(n, dtype=np.int32)
     v = _lib().oracle_td(_p(D), code, n, ld, _p(med), len(med), _p(labels))
+    return (v, labels) if return_labels else v
+
+
+def td_points(X, medoids, return_labels=False):
+    """Eq. (2) for feature vectors: TD of the medoids (point indices) with
+    Euclidean distances computed directly in FP64 (no matrix)."""
+    X = np.ascontiguousarray(X, np.float32)
+    med = _med(medoids)
+    n, d = X.shape
+    labels = np.empty(n, dtype=np.int32)
+    v = _lib().oracle_td_points(_p(X), n, d, _p(med), len(med), _p(labels))
     return (v, labels) if return_labels else v
 
 

@@ -847,6 +847,40 @@ int oracle_init_lab(const void *D, int dtype, int64_t n, int64_t ld, int k,
 }
 
 /* ------------------------------------------------------------------------
+ * TD objective, Eq. (2), of medoids given as point indices of feature
+ * vectors X (n x d float32, row-major), with the Euclidean distance computed
+ * directly in FP64: TD = sum_o min_j sqrt(sum_t (x_o,t - x_m_j,t)^2).
+ * labels (may be NULL) = lowest slot attaining the minimum.  For data
+ * without a stored matrix (the on-the-fly form), this is the exact TD
+ * against which the GPU's reported TD is compared.
+ * ---------------------------------------------------------------------- */
+double oracle_td_points(const float *X, int64_t n, int d, const int32_t *med,
+                        int k, int32_t *labels) {
+  double td = 0.0;
+#pragma omp parallel for schedule(static) reduction(+ : td)
+  for (int64_t o = 0; o < n; o++) {
+    double best = OR_INF;
+    int lab = -1;
+    for (int j = 0; j < k; j++) {
+      const float *a = X + (size_t)o * d, *b = X + (size_t)med[j] * d;
+      double s = 0.0;
+      for (int t = 0; t < d; t++) {
+        const double df = (double)a[t] - (double)b[t];
+        s += df * df;
+      }
+      const double v = sqrt(s);
+      if (v < best) {
+        best = v;
+        lab = j;
+      }
+    }
+    td += best;
+    if (labels) labels[o] = lab;
+  }
+  return td;
+}
+
+/* ------------------------------------------------------------------------
  * FastCLARANS (Sec. 3.4): CLARANS's randomized search with the FastPAM1
  * evaluation.  CLARANS draws a random (medoid, non-medoid) pair, swaps if
  * that lowers TD and stops after a fixed number of consecutive failed

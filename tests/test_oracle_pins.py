@@ -572,3 +572,21 @@ def test_init_lab_rank_mapping_and_errors():
         oracle.init_lab(D, 2, np.array([[0, 1], [7, 2]], np.int32))
     assert [oracle.lab_sample_size(n) for n in (1, 2, 4, 5, 20000, 50000)] == \
         [11, 12, 12, 13, 152, 234]
+
+
+def test_td_points_is_eq2_on_the_fp64_matrix():
+    """TD of feature vectors (no matrix) = Eq. (2) by brute force with numpy
+    FP64 distances; labels = lowest nearest slot; duplicated points give
+    ties that go to the lower slot."""
+    g = np.random.default_rng(415)
+    for _ in range(20):
+        n, d = int(g.integers(5, 60)), int(g.integers(1, 9))
+        X = g.normal(size=(n, d)).astype(np.float32)
+        X[-1] = X[0]                       # a duplicate: equal distances
+        k = int(g.integers(1, n))
+        med = g.choice(n, k, replace=False)
+        A = np.sqrt(((X[:, None, :].astype(np.float64) - X[None, :, :]) ** 2).sum(-1))
+        ref = A[:, med].min(axis=1).sum()
+        v, lab = oracle.td_points(X, med, return_labels=True)
+        assert abs(v - ref) <= 1e-12 * max(1.0, ref)
+        assert (lab == np.argmin(A[:, med], axis=1)).all()
