@@ -355,7 +355,12 @@ km_status kmedoids_batched_distances(const float *points, int32_t dim,
                                      float *arena, void *stream);
 
 /* inst (DEVICE, count entries, 1 <= count <= 65535), medoids_out / results
- * (DEVICE).  opts: max_iter, tol; tune 1 = 8 warps per CTA, otherwise 16.
+ * (DEVICE).  opts: max_iter, tol; tune 1 = 8 warps per CTA, otherwise 16;
+ * variant KM_FASTPAM1 (default) or KM_FASTERPAM (Alg. 4: each CTA scans its
+ * instance cyclically in windows of one candidate row per warp and applies
+ * the first improving swap at once, with an incremental cache update; the
+ * result's iterations then count the scans started); other variants give
+ * KM_E_UNSUPPORTED.
  * Asynchronous: the call only enqueues work on the stream (a zeroing copy,
  * a kernel ordering the instances largest first, and the persistent PAM
  * kernel) and never reads device memory on the host, so it can be captured
@@ -371,7 +376,8 @@ km_status kmedoids_run_batched(const float *arena, const km_instance *inst,
 
 /* kmedoids_run_batched without BUILD: every instance starts from the k
  * medoids the caller wrote at medoids_inout[inst[i].medoid_offset ...]
- * (DEVICE) and runs FastPAM1 SWAP to convergence, the result replacing them.
+ * (DEVICE) and runs FastPAM1 (or, with opts->variant = KM_FASTERPAM,
+ * FasterPAM) SWAP to convergence, the result replacing them.
  * For restarts from random starts (the paper recommends uniform random
  * initialisation with several restarts once swapping is cheap, Sec. 4.3
  * and Sec. 6): several instances may share one matrix (same offset), one

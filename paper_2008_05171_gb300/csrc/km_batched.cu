@@ -4,8 +4,9 @@
 // k_batch_pam: each CTA takes instances from an atomic queue (ordered
 // largest first) and runs the whole method on one instance: BUILD (Alg. 1)
 // or the caller's starting medoids (restarts from random starts), the exact
-// per-point cache, and FastPAM1 SWAP (Alg. 3, Eq. (7)) to convergence, with every per-point quantity in shared memory
-// and one warp per candidate row.  Float sums of the SWAP pass use the same
+// per-point cache, and FastPAM1 SWAP (Alg. 3, Eq. (7)) or the eager
+// FasterPAM (Alg. 4) to convergence, with every per-point quantity in shared
+// memory and one warp per candidate row.  Float sums of the SWAP pass use the same
 // exact 64-bit fixed point as the single-instance kernels (scale from the
 // instance's largest entry, found during BUILD step 0).  Instances need
 // n <= 4096 and k <= 128.
@@ -46,6 +47,7 @@ struct BatchArgs {
   int max_iter;
   double tol;
   int start_given;           // 1: start from the medoids in `medoids` (no BUILD)
+  int eager;                 // 1: FasterPAM (Alg. 4) instead of FastPAM1
 };
 
 // Euclidean matrix of m points: FP64 differences, squares accumulated with
@@ -174,6 +176,7 @@ struct BatchSmem {
   alignas(16) float dn[kBatchMaxN];
   alignas(16) float ds[kBatchMaxN];
   uint8_t near[kBatchMaxN];
+  uint8_t sec[kBatchMaxN];
   uint8_t is_med[kBatchMaxN];
   int32_t med[kBatchMaxK];
   long long rl[kBatchMaxK];
@@ -280,6 +283,38 @@ __device__ __forceinline__ void stream_rows(BatchSmem<WARPS>& S, const float* D,
       while (cc < n && S.is_med[cc]) cc += WARPS;
     }
     slot = (slot + 1 == kRingStages) ? 0 : slot + 1;
+  }
+  cp_async_wait<0>();
+}
+
+// Streams one row (n entries) through the warp's ring, as stream_rows does
+// for a sequence of rows: on_chunk(o, v, stage) for column chunks o = 0,
+// 512, ...; entries at or beyond n are stale and masked by the caller.
+template <int WARPS, class Chunk>
+__device__ __forceinline__ void stream_one_row(BatchSmem<WARPS>& S, const float* row, int n,
+                                               int warp, int lane, Chunk&& on_chunk) {
+  float(*ring)[kRingFloats] = S.ring[warp];
+  const int nch = (n + kRingFloats - 1) / kRingFloats;
+  auto issue = [&](int j) {
+    if (j < nch) {
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int p = j * kRingFloats + 128 * u + 4 * lane;
+        if (p < n) cp_async16(&ring[j % kRingStages][128 * u + 4 * lane], row + p);
+      }
+    }
+    cp_async_commit();
+  };
+#pragma unroll
+  for (int j = 0; j < kRingStages - 1; ++j) issue(j);
+  for (int j = 0; j < nch; ++j) {
+    issue(j + kRingStages - 1);
+    cp_async_wait<kRingStages - 1>();
+    const float* stage = ring[j % kRingStages];
+    float4 v[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) v[u] = *reinterpret_cast<const float4*>(stage + 128 * u + 4 * lane);
+    on_chunk(j * kRingFloats, v, stage);
   }
   cp_async_wait<0>();
 }
@@ -522,6 +557,7 @@ __global__ void __launch_bounds__(WARPS * 32, 1) k_batch_pam(const BatchArgs a) 
           }
         }
         S.near[o] = (uint8_t)n1;
+        S.sec[o] = (uint8_t)(n2 < 0 ? 0 : n2);
         S.dn[o] = d1;
         S.ds[o] = (n2 < 0) ? __int_as_float(0x7f800000) : d2;
         if (n2 >= 0) atomic_add_shared64(&S.rl[n1], fx_of(d2, f) - fx_of(d1, f));
@@ -529,7 +565,188 @@ __global__ void __launch_bounds__(WARPS * 32, 1) k_batch_pam(const BatchArgs a) 
       __syncthreads();
     };
 
-    if (k < n) {
+    if (k < n && k >= 2 && a.eager) {
+      // ------------------------------------------- FasterPAM (Alg. 4)
+      // windows of WARPS scan positions, one candidate row per warp against
+      // the current medoids; the first improving position is applied at
+      // once (incremental cache update) and the next window starts after
+      // it, so the decisions are those of the sequential scan
+      cache_all();
+      long long pos = 0, last = -1;
+      bool conv = false;
+      const long long pos_limit = (long long)a.max_iter * n;
+      // acceptance Delta < -tol on the fixed-point sums: Delta 2^f < -tol 2^f
+      // (exact power-of-two scaling; evaluated once, FP64 is slow here)
+      const double inv_scale = exp2(-(double)f);
+      const double accept_below = -a.tol * exp2((double)f);
+      while (pos < pos_limit) {
+        const long long stop = (last < 0) ? (long long)n : last + n;
+        const long long wlen = min((long long)WARPS, stop - pos);
+        long long tot = LLONG_MAX;
+        int bi = -1;
+        const int c = (warp < wlen) ? (int)((pos + warp) % n) : -1;
+        if (c >= 0 && !S.is_med[c]) {
+          long long* ar = S.acc[warp];
+          for (int i = lane; i < k; i += 32) ar[i] = 0;
+          __syncwarp();
+          long long lp = 0;
+          stream_one_row<WARPS>(S, D + (size_t)c * ld, n, warp, lane,
+                                [&](int o, const float4(&v)[4], const float* stage) {
+            unsigned mask = 0;
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+              const int p0 = o + 128 * u + 4 * lane;  // < npad <= kBatchMaxN
+              const float4 s4 = *reinterpret_cast<const float4*>(&S.ds[p0]);
+#pragma unroll
+              for (int t = 0; t < 4; ++t)
+                if (f4get(v[u], t) < f4get(s4, t)) mask |= 1u << (4 * u + t);
+            }
+            while (mask) {
+              const int b = __ffs(mask) - 1;
+              mask &= mask - 1;
+              const int col = 128 * (b >> 2) + 4 * lane + (b & 3);
+              const int p = o + col;
+              const float e = stage[col];
+              const float dnp = S.dn[p], dsp = S.ds[p];
+              const int sl = S.near[p];
+              const long long xd = fx_scaled(e, fs1, fs2), xs = fx_scaled(dsp, fs1, fs2);
+              if (e < dnp) {
+                const long long xn = fx_scaled(dnp, fs1, fs2);
+                lp += xd - xn;
+                atomic_add_shared64(&ar[sl], xn - xs);
+              } else {
+                atomic_add_shared64(&ar[sl], xd - xs);
+              }
+            }
+          });
+          __syncwarp();
+          long long bv = LLONG_MAX;
+          for (int i = lane; i < k; i += 32) {
+            const long long v = S.rl[i] + ar[i];
+            if (v < bv) {
+              bv = v;
+              bi = i;
+            }
+          }
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) {
+            const long long ov = __shfl_xor_sync(0xffffffffu, bv, o);
+            const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+            if (ov < bv || (ov == bv && oi < bi)) {
+              bv = ov;
+              bi = oi;
+            }
+          }
+          tot = bv + warp_sum(lp);
+        }
+        if (lane == 0) {
+          S.wl[warp] = tot;
+          S.wslot[warp] = (c >= 0 && !S.is_med[c]) ? bi : -1;
+        }
+        __syncthreads();
+        if (tid == 0) {
+          int fw = -1;
+          for (int w = 0; w < (int)wlen; ++w)
+            if (S.wslot[w] >= 0 &&
+                (a.tol == 0.0 ? S.wl[w] < 0 : (double)S.wl[w] < accept_below)) {
+              fw = w;
+              break;
+            }
+          S.cstar = (fw >= 0) ? (int)((pos + fw) % n) : -1;
+          S.istar = (fw >= 0) ? S.wslot[fw] : -1;
+          S.dstar_i = (fw >= 0) ? S.wl[fw] : 0;
+          S.wcand[0] = fw;
+        }
+        __syncthreads();
+        const int fw = S.wcand[0];
+        if (fw < 0) {
+          pos += wlen;
+          if (pos >= stop) {
+            conv = true;
+            break;
+          }
+          continue;
+        }
+        last = pos + fw;
+        pos = last + 1;
+        // ------------------------------------------- apply (incremental)
+        const int i_s = S.istar, c_s = S.cstar;
+        const float* rowc = D + (size_t)c_s * ld;
+        __syncthreads();  // every thread has read istar / cstar
+        if (tid == 0) {
+          S.is_med[S.med[i_s]] = 0;
+          S.med[i_s] = c_s;
+          S.is_med[c_s] = 1;
+          S.dstar += (double)S.dstar_i * inv_scale;
+        }
+        for (int i = tid; i < k; i += NT) S.rl[i] = 0;
+        __syncthreads();
+        // the new medoid's distances to this thread's points, all in flight
+        // before any is used (most points need only this one)
+        constexpr int kPer = (kBatchMaxN + NT - 1) / NT;
+        float dcv[kPer];
+#pragma unroll
+        for (int u = 0; u < kPer; ++u) {
+          const int o = tid + u * NT;
+          dcv[u] = (o < n) ? rowc[o] : 0.f;
+        }
+#pragma unroll
+        for (int u = 0; u < kPer; ++u) {
+          const int o = tid + u * NT;
+          if (o >= n) break;
+          int n1 = S.near[o], n2 = S.sec[o];
+          float d1 = S.dn[o], d2 = S.ds[o];
+          if (n1 == i_s || n2 == i_s) {
+            // the removed medoid was nearest or second: rescan every slot
+            // (eight medoid rows in flight)
+            n1 = -1;
+            n2 = -1;
+            for (int j0 = 0; j0 < k; j0 += 8) {
+              float v8[8];
+#pragma unroll
+              for (int u = 0; u < 8; ++u)
+                v8[u] = (j0 + u < k) ? D[(size_t)S.med[j0 + u] * ld + o] : 0.f;
+#pragma unroll
+              for (int u = 0; u < 8; ++u) {
+                if (j0 + u < k) {
+                  const float v = v8[u];
+                  if (n1 < 0 || v < d1) {
+                    n2 = n1;
+                    d2 = d1;
+                    n1 = j0 + u;
+                    d1 = v;
+                  } else if (n2 < 0 || v < d2) {
+                    n2 = j0 + u;
+                    d2 = v;
+                  }
+                }
+              }
+            }
+          } else {
+            // only the new medoid enters: top-2 of {nearest, second, new}
+            const float dc = dcv[u];
+            if (dc < d1 || (dc == d1 && i_s < n1)) {
+              n2 = n1;
+              d2 = d1;
+              n1 = i_s;
+              d1 = dc;
+            } else if (dc < d2 || (dc == d2 && i_s < n2)) {
+              n2 = i_s;
+              d2 = dc;
+            }
+          }
+          S.near[o] = (uint8_t)n1;
+          S.sec[o] = (uint8_t)n2;
+          S.dn[o] = d1;
+          S.ds[o] = d2;
+          atomic_add_shared64(&S.rl[n1], fx_of(d2, f) - fx_of(d1, f));
+        }
+        ++res.swaps;
+        __syncthreads();
+      }
+      res.iterations = (int)((pos + n - 1) / n);
+      res.status = conv ? 0 : KM_E_NOT_CONVERGED;
+    } else if (k < n) {
       cache_all();
       int it = 0;
       bool conv = false;
@@ -883,6 +1100,10 @@ static km_status batched_impl(bool start_given, const float* arena, const km_ins
   a.max_iter = o.max_iter > 0 ? o.max_iter : 10000;
   a.tol = o.tol;
   a.start_given = start_given ? 1 : 0;
+  if (o.variant != KM_FASTPAM1 && o.variant != KM_FASTERPAM)
+    return bfail(KM_E_UNSUPPORTED, "the batched form runs FastPAM1 or FasterPAM (variant %d)",
+                 o.variant);
+  a.eager = (o.variant == KM_FASTERPAM) ? 1 : 0;
   const int sms = device_sm_count();
   // tune: 0 automatic (16 warps per CTA), 1 = 8 warps, 2 = 16 warps
   const int cfg = (o.tune == 1) ? 0 : 1;

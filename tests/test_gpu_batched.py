@@ -203,3 +203,57 @@ def test_swap_batched_rejects_bad_starts():
     _, res2 = km.swap_batched(arena, inst_dev, med2)
     res2 = np.frombuffer(res2.cpu().numpy().tobytes(), dtype=km.BATCH_RESULT_DTYPE)
     assert res2[1]["status"] == 1
+
+
+def test_batched_fasterpam_restarts_and_build_match_oracle():
+    """FasterPAM (Alg. 4) in the batched form: each CTA scans its instance
+    in windows of one row per warp and applies the first improving swap at
+    once.  From uniform random starts (several per matrix) and after BUILD,
+    every instance's medoids, swap count, scans and TD equal the oracle's
+    FasterPAM; instances span several 512-column ring stages, ragged tails
+    and k from 2 to 128."""
+    specs = [(900, 12), (2600, 30), (515, 5), (1500, 128), (40, 2)]
+    P, offs = wl.batched_points(specs, d=8, seed="fp-batched")
+    inst1, arena_len, nmed1 = km.batch_layout(specs)
+    arena = torch.zeros(arena_len, dtype=torch.float32, device="cuda")
+    inst1_dev = torch.from_numpy(inst1.view(np.uint8).copy()).cuda()
+    km.batched_distances(torch.from_numpy(P).cuda(), offs, inst1_dev, arena)
+    mats = [oracle.euclid_f32(P[offs[i]:offs[i] + n]) for i, (n, k) in enumerate(specs)]
+    # BUILD + FasterPAM
+    med_b, res_b = km.run_batched(arena, inst1_dev, nmed1, variant="fasterpam")
+    med_b = med_b.cpu().numpy()
+    res_b = np.frombuffer(res_b.cpu().numpy().tobytes(), dtype=km.BATCH_RESULT_DTYPE)
+    for i, (n, k) in enumerate(specs):
+        ref = oracle.run(mats[i], k, variant="fasterpam")
+        mo = int(inst1[i]["medoid_offset"])
+        assert res_b[i]["status"] == 0
+        assert med_b[mo:mo + k].tolist() == ref["medoids"].tolist(), i
+        assert res_b[i]["swaps"] == ref["swaps"] and res_b[i]["iterations"] == ref["iterations"]
+        assert abs(res_b[i]["td"] - ref["td"]) <= 1e-9 * ref["td"]
+    # restarts from random starts
+    R = 3
+    g = np.random.default_rng(78)
+    rows, starts, moff = [], [], 0
+    for i, (n, k) in enumerate(specs):
+        for r in range(R):
+            rows.append((int(inst1[i]["offset"]), n, int(inst1[i]["ld"]), k, moff))
+            starts.append(np.sort(g.choice(n, size=k, replace=False)).astype(np.int32))
+            moff += k
+    inst = np.array(rows, dtype=km.INSTANCE_DTYPE)
+    med = torch.from_numpy(np.concatenate(starts)).cuda()
+    inst_dev = torch.from_numpy(inst.view(np.uint8).copy()).cuda()
+    med, res = km.swap_batched(arena, inst_dev, med, variant="fasterpam")
+    med = med.cpu().numpy()
+    res = np.frombuffer(res.cpu().numpy().tobytes(), dtype=km.BATCH_RESULT_DTYPE)
+    for i, (n, k) in enumerate(specs):
+        for r in range(R):
+            j = i * R + r
+            ref = oracle.swap(mats[i], starts[j], variant="fasterpam")
+            mo = int(inst[j]["medoid_offset"])
+            assert res[j]["status"] == 0
+            assert med[mo:mo + k].tolist() == ref["medoids"].tolist(), (i, r)
+            assert res[j]["swaps"] == ref["swaps"] and res[j]["iterations"] == ref["iterations"]
+            assert abs(res[j]["td"] - ref["td"]) <= 1e-9 * ref["td"]
+    with pytest.raises(km.KmError) as e:
+        km.run_batched(arena, inst1_dev, nmed1, variant="fastpam2")
+    assert e.value.status == 7
