@@ -419,7 +419,7 @@ def run_batched(args, rank, world, local_rank):
     return line
 
 
-def eager_roofline(r, n, kernel):
+def eager_roofline(r, n, kernel, workload=None):
     """The eager kernel (one persistent launch per call): the rows the
     sequential scan evaluates, 4 B per (candidate, point) pair, over the
     launch's CUDA-event time.  Its decisions are sequential (Alg. 4), so it
@@ -429,10 +429,15 @@ def eager_roofline(r, n, kernel):
     nbytes = int(r["evaluated"]) * n * 4
     ms = float(r["eval_ms"])
     ach = nbytes / (ms / 1e3) / 1e9
+    traffic = None
+    ent = (load_json(os.path.join(ROOT, "profiles", "traffic.json")) or {}).get("eager")
+    if ent and workload and ent.get("workload") == workload and \
+            ent.get("source_hash") == source_hash(("km_eager.cu", "km_device.cuh")):
+        traffic = ent.get("dram_bytes_per_launch")
     return {"bound": "hbm", "achieved": round(ach, 1), "peak": peak, "unit": "GB/s",
             "frac": round(ach / peak, 4), "kernel": kernel,
             "algorithmic_bytes_per_launch": nbytes, "avg_launch_ms": round(ms, 5),
-            "peak_source": pk, "traffic": None,
+            "peak_source": pk, "traffic": traffic,
             "note": "sequential eager decisions: one window evaluation, grid barrier and "
                     "swap per accepted swap (latency-bound)"}
 
@@ -549,7 +554,7 @@ def run_fasterpam(args, rank, world, local_rank):
         "full_run_ms": total_ms / args.steps, "swaps": int(r0["swaps"]),
         "evaluated": int(r0["evaluated"]), "visited": int(r0["visited"]),
         "scans": int(r0["iterations"]), "fasterpam_ms": float(r0["swap_ms"]), "td": r0["td"],
-        "roofline": eager_roofline(r0, n, "k_eager<float> (FasterPAM)"),
+        "roofline": eager_roofline(r0, n, "k_eager<float> (FasterPAM)", args.workload),
         "gpu_launches": int(sum(r["kernel_launches"] for r in results)) + 2 * args.steps,
         "clocks": ck, "e2e": e2e,
     }
