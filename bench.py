@@ -56,6 +56,11 @@ WORKLOADS = {
                                  "distance-weighted initialisation (Sec. 3.3) from fixed "
                                  "uniform numbers, then eager FasterPAM (Alg. 4) to "
                                  "convergence, k=100"),
+    "u16_20000": dict(n=20000, d=2, centers=0, k=100, recipe="manhattan_u16",
+                      desc="the compressed integer form: n=20000 2-D integer points uniform in "
+                           "[0,1000)^2, exact Manhattan distances (<= 2000) stored as uint16 "
+                           "(20000x20000, 0.8 GB), k=100, BUILD + FastPAM1 SWAP to convergence; "
+                           "the same matrix as int32 timed beside it"),
     "gmm_50000": dict(n=50000, d=32, centers=200, k=200, recipe="gmm_50000_points",
                       desc="n=50000 d=32 f32 GMM (200 clusters, centres U[-10,10]^32, "
                            "sigma U[0.5,2], Dirichlet(1) weights), Euclidean f32 "
@@ -168,9 +173,19 @@ class Clocks:
 
 
 def make_input(wl_name, device):
-    """Synthetic matrix on the device (FP64 direct differences -> FP32)."""
+    """Synthetic matrix on the device (FP64 direct differences -> FP32; the
+    16-bit workload: exact integer Manhattan distances)."""
     from paper_2008_05171_gb300 import workloads as wl
+    import torch
     spec = WORKLOADS[wl_name]
+    if spec["recipe"] == "manhattan_u16":
+        n = spec["n"]
+        P = torch.from_numpy(wl.int_coords(n, 2, 1000, seed=("u16", n)).astype(np.int32)).to(device)
+        D = torch.empty((n, n), dtype=torch.int16, device=device)
+        for r0 in range(0, n, 2048):
+            r1 = min(n, r0 + 2048)
+            D[r0:r1] = (P[r0:r1, None, :] - P[None, :, :]).abs().sum(-1).to(torch.int16)
+        return D, spec
     X = getattr(wl, spec["recipe"])()
     D = wl.euclidean_f32_torch(X, device)
     return D, spec
@@ -644,7 +659,8 @@ def run_ours(args, rank, world, local_rank):
     dev = torch.device("cuda", local_rank)
     D, spec = make_input(args.workload, dev)
     n, k = spec["n"], spec["k"]
-    code = km.KM_F32
+    code = km._dtype_code(D)
+    esize = D.element_size()
     opts = km.options(profile=True)
     ws = km.workspace(n, k, code, opts, device=dev)
     torch.cuda.synchronize()
@@ -682,8 +698,8 @@ def run_ours(args, rank, world, local_rank):
     # kernel shares and roofline of the dominant one
     swap_launch_ms = r0["eval_ms"] / max(1, r0["eval_launches"])
     build_launch_ms = r0["build_eval_ms"] / max(1, r0["build_launches"])
-    swap_bytes = (n - k) * n * 4
-    build_bytes = sum((n - t) * n * 4 for t in range(k)) / k
+    swap_bytes = (n - k) * n * esize
+    build_bytes = sum((n - t) * n * esize for t in range(k)) / k
     peak, peak_kind = peaks()
     kern = {
         "swap_eval": {"launch_ms": swap_launch_ms, "bytes": swap_bytes,
@@ -694,7 +710,7 @@ def run_ours(args, rank, world, local_rank):
     dom = max(kern, key=lambda x: kern[x]["share_ms"])
     prof = load_json(os.path.join(ROOT, "profiles", "traffic.json")) or {}
     traffic = None
-    ent = prof.get(dom)
+    ent = prof.get(dom + ("_u16" if esize == 2 else ""))
     if ent and ent.get("source_hash") == source_hash() and \
             ent.get("workload") == args.workload:
         traffic = ent.get("dram_bytes_per_launch")
@@ -706,7 +722,8 @@ def run_ours(args, rank, world, local_rank):
                 "unit": "GB/s", "frac": round(ach / peak, 4),
                 "peak_source": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)"
                 if peak_kind == "measured" else "fallback 6.8 TB/s",
-                "kernel": "k_stream<float,%s>" % ("SWAP" if name == "swap_eval" else "BUILD"),
+                "kernel": "k_stream<%s,%s>" % ({4: "float", 2: "uint16"}.get(esize, "?"),
+                                               "SWAP" if name == "swap_eval" else "BUILD"),
                 "algorithmic_bytes_per_launch": kk["bytes"],
                 "avg_launch_ms": round(kk["launch_ms"], 5)}
 
@@ -736,7 +753,7 @@ def run_ours(args, rank, world, local_rank):
             e_ms += a.elapsed_time(b)
             e_evals += sum(evals_of(n, k, r))
         e2e = {"value": world * e_evals / (e_ms / 1e3), "unit": "point-evals/s",
-               "h2d_bytes_per_step": int(D.numel() * 4),
+               "h2d_bytes_per_step": int(D.numel() * esize),
                "d2h_bytes_per_step": int(4 * k + 4 * n + 8 * 8)}
         del Dh, Dd
 
@@ -747,10 +764,11 @@ def run_ours(args, rank, world, local_rank):
         "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": total_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32 (exact 64-bit fixed-point dTD sums, FP64 TD)",
+        "dtype": "f32 (exact 64-bit fixed-point dTD sums, FP64 TD)" if esize == 4 else
+                 "u16 distances (int32 compares, int64 sums)",
         "data": "synthetic",
         "config": {"workload": args.workload + ": " + spec["desc"],
-                   "n": n, "k": k, "matrix_bytes": int(D.numel() * 4),
+                   "n": n, "k": k, "matrix_bytes": int(D.numel() * esize),
                    "geometry": {"swap": int(r0["swap_geometry"]),
                                 "build": int(r0["build_geometry"]),
                                 "picked_by": {-1: "measured on the first call (tune=-1)",
@@ -771,8 +789,27 @@ def run_ours(args, rank, world, local_rank):
         "gpu_launches": int(sum(r["kernel_launches"] for r in results)),
         "clocks": ck, "e2e": e2e, "wall_s": wall,
     }
+    if esize == 2:
+        # the same matrix as int32, timed the same way (not part of value)
+        Di = D.to(torch.int32)
+        wsi = km.workspace(n, k, km.KM_I32, opts, device=dev)
+        for _ in range(2):
+            km.run(Di, k, ws=wsi, profile=True, tune=args.tune)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        ri = km.run(Di, k, ws=wsi, profile=True, tune=args.tune)
+        b.record(stream)
+        torch.cuda.synchronize()
+        line["int32_same_matrix"] = {
+            "ms_per_step": a.elapsed_time(b),
+            "swap_iter_ms": ri["eval_ms"] / max(1, ri["eval_launches"]),
+            "build_step_ms": ri["build_eval_ms"] / max(1, ri["build_launches"]),
+            "same_medoids": ri["medoids"].cpu().tolist() == r0["medoids"].cpu().tolist()}
+        del Di, wsi
     if rank == 0 and not args.no_cpu_baseline and world == 1:
-        line["cpu_baseline"] = cpu_baseline(D, spec, args.cpu_seconds)
+        line["cpu_baseline"] = cpu_baseline(D.to(torch.int32) if esize == 2 else D, spec,
+                                            args.cpu_seconds)
     return line
 
 
@@ -926,7 +963,17 @@ def run_reference(args, rank, world):
                 "cpu_baseline": cb,
                 "e2e": {"value": v, "unit": "point-evals/s", "h2d_bytes_per_step": 0,
                         "d2h_bytes_per_step": 0}}
-    X = getattr(wl, spec["recipe"])()
+    if spec["recipe"] == "manhattan_u16":
+        # the same integer matrix (the oracle reads it as int32)
+        D, _ = make_input(args.workload, torch.device("cuda", 0)) if torch.cuda.is_available() \
+            else (None, None)
+        if D is None:
+            P = wl.int_coords(spec["n"], 2, 1000, seed=("u16", spec["n"]))
+            D = torch.from_numpy(wl.manhattan_int32(P)[:, :spec["n"]].copy())
+        D = D.to(torch.int32)
+        X = None
+    else:
+        X = getattr(wl, spec["recipe"])()
     if args.workload.startswith("fasterpam"):
         dev = torch.device("cuda", 0) if torch.cuda.is_available() else torch.device("cpu")
         Dh = (wl.euclidean_f32_torch(X, dev) if dev.type == "cuda"
@@ -976,7 +1023,9 @@ def run_reference(args, rank, world):
         spec = dict(spec, n=8000)
         X = X[:8000].astype(np.float64)
     dev = torch.device("cuda", 0) if torch.cuda.is_available() else torch.device("cpu")
-    if dev.type == "cuda":
+    if X is None:
+        pass  # the integer matrix built above
+    elif dev.type == "cuda":
         D = wl.euclidean_f32_torch(X, dev)
     else:
         D = torch.from_numpy(wl.euclidean_f32(X))

@@ -21,9 +21,11 @@
  *           paper's symmetric special case, Sec. 1.2); the library does not
  *           scan D to check this.  Columns n..ld-1 are padding and never
  *           read as distances.  The base address must be 16-byte aligned and
- *           ld a multiple of 4 (rows are streamed with 16-byte bulk copies);
+ *           ld a multiple of 4 (8 for KM_U16: rows are streamed with 16-byte
+ *           bulk copies);
  *           otherwise the call returns KM_E_INVALID.
- *   dtype   KM_I32 (int32 distances; sums in int64, results exact) or
+ *   dtype   KM_I32 (int32 distances; sums in int64, results exact),
+ *           KM_U16 (uint16 distances, the compressed form; as KM_I32), or
  *           KM_F32 (float32 distances; TD and BUILD sums in FP64, the SWAP
  *           Delta sums in exact 64-bit fixed point with a per-call scale
  *           2^f, f = 60 - ceil(log2(n+1)) - (exponent of the largest entry),
@@ -69,7 +71,13 @@ typedef enum {
   KM_E_UNSUPPORTED = 7    /* valid but outside this build's limits */
 } km_status;
 
-typedef enum { KM_I32 = 0, KM_F32 = 1 } km_dtype;
+/* KM_U16: the compressed integer form -- unsigned 16-bit distances (0 ..
+ * 65535; integer dissimilarities in that range lose nothing), half the
+ * bytes of KM_I32 per matrix pass.  Widened to int32 in the kernels, sums
+ * in int64, results exact as for KM_I32; ld must be a multiple of 8, and
+ * the cache arrays kmedoids_cache returns (dn, ds) are int32.  Matrix form
+ * only. */
+typedef enum { KM_I32 = 0, KM_F32 = 1, KM_U16 = 2 } km_dtype;
 
 typedef enum {
   KM_FASTPAM1 = 0, /* best swap per iteration (Alg. 3); same swaps as PAM */
@@ -224,9 +232,10 @@ km_status kmedoids_eval_swaps(const void *D, int32_t dtype, int64_t n,
 
 /* The per-point cache (Sec. 2) for the medoids given: near/sec (DEVICE
  * int32, n entries) = nearest and second-nearest slot, dn/ds (DEVICE, n
- * entries, D's dtype) = their distances; removal (DEVICE double, k
- * entries, may be NULL) = Delta^{-m_i} of Eq. (7).  For k = 1, sec = -1 and
- * ds = the dtype's largest value.  Requires 1 <= k <= n. */
+ * entries, D's dtype; int32 for KM_U16) = their distances; removal
+ * (DEVICE double, k entries, may be NULL) = Delta^{-m_i} of Eq. (7).  For
+ * k = 1, sec = -1 and ds = the dtype's largest value.  Requires
+ * 1 <= k <= n. */
 km_status kmedoids_cache(const void *D, int32_t dtype, int64_t n, int64_t ld,
                          int32_t k, const int32_t *medoids, int32_t *near,
                          int32_t *sec, void *dn, void *ds, double *removal,

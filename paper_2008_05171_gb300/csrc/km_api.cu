@@ -114,6 +114,7 @@ struct Ctx {
   bool scanned = false;
   int swap_geom = 0, build_geom = 0;  // geometry table entries used
   KmState* st() const { return reinterpret_cast<KmState*>(ws + L.st); }
+  int esize() const { return dtype == KM_U16 ? 2 : 4; }  // bytes per matrix element
   template <class P>
   P* at(size_t off) const {
     return reinterpret_cast<P*>(ws + off);
@@ -123,12 +124,15 @@ struct Ctx {
 km_status check_common(const void* D, int32_t dtype, int64_t n, int64_t ld, int32_t k, void* ws,
                        size_t ws_bytes, const km_options* opts, Ctx* c) {
   if (!D) return fail(KM_E_INVALID, "D is NULL");
-  if (dtype != KM_I32 && dtype != KM_F32) return fail(KM_E_INVALID, "unknown dtype %d", dtype);
+  if (dtype != KM_I32 && dtype != KM_F32 && dtype != KM_U16)
+    return fail(KM_E_INVALID, "unknown dtype %d", dtype);
   if (n <= 0) return fail(KM_E_INVALID, "n must be positive (got %lld)", (long long)n);
   if (n > (int64_t)INT32_MAX - 2 * kChunk) return fail(KM_E_INVALID, "n too large");
   if (k < 1 || k > n) return fail(KM_E_INVALID, "need 1 <= k <= n (k=%d, n=%lld)", k, (long long)n);
   if (ld < n) return fail(KM_E_INVALID, "ld (%lld) < n (%lld)", (long long)ld, (long long)n);
   if (ld % 4 != 0) return fail(KM_E_INVALID, "ld (%lld) must be a multiple of 4", (long long)ld);
+  if (dtype == KM_U16 && ld % 8 != 0)
+    return fail(KM_E_INVALID, "ld (%lld) must be a multiple of 8 for KM_U16", (long long)ld);
   if (reinterpret_cast<uintptr_t>(D) % 16 != 0) return fail(KM_E_INVALID, "D must be 16-byte aligned");
   if (!ws) return fail(KM_E_INVALID, "workspace is NULL");
   if (reinterpret_cast<uintptr_t>(ws) % 256 != 0) return fail(KM_E_INVALID, "workspace must be 256-byte aligned");
@@ -288,7 +292,7 @@ std::map<std::tuple<int, int, int, int, int, int>, int> g_tune;
 km_status config_for(Ctx& c, int mode, int flavour, const StreamArgs& sa, StreamConfig* cfg) {
   const char* what = (mode == kModeSwap) ? "SWAP" : "BUILD";
   if (c.opt.tune >= 0) {
-    if (!stream_config(mode, c.k, flavour, c.opt.rows_per_tile, c.opt.tune, cfg))
+    if (!stream_config(mode, c.k, flavour, c.opt.rows_per_tile, c.opt.tune, cfg, c.esize()))
       return fail(KM_E_UNSUPPORTED, "no %s kernel configuration fits (k=%d, tune=%d)", what, c.k,
                   c.opt.tune);
     return KM_OK;
@@ -299,7 +303,7 @@ km_status config_for(Ctx& c, int mode, int flavour, const StreamArgs& sa, Stream
   {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     auto it = g_tune.find(key);
-    if (it != g_tune.end() && stream_config(mode, c.k, flavour, 0, it->second, cfg)) return KM_OK;
+    if (it != g_tune.end() && stream_config(mode, c.k, flavour, 0, it->second, cfg, c.esize())) return KM_OK;
   }
   KmState saved;
   km_status r = read_state(c, &saved);
@@ -311,7 +315,7 @@ km_status config_for(Ctx& c, int mode, int flavour, const StreamArgs& sa, Stream
   float best_ms = 0.f;
   for (int g = 1; g <= 16; ++g) {
     StreamConfig cg;
-    if (!stream_config(mode, c.k, flavour, 0, g, &cg)) continue;
+    if (!stream_config(mode, c.k, flavour, 0, g, &cg, c.esize())) continue;
     if (c.opt.rows_per_tile > 0 && cg.rows != c.opt.rows_per_tile) continue;
     StreamArgs a = sa;
     a.win_rows = cg.rows;
@@ -340,7 +344,7 @@ km_status config_for(Ctx& c, int mode, int flavour, const StreamArgs& sa, Stream
   if (r != KM_OK) return r;
   KM_CUDA(cudaMemcpyAsync(c.st(), &saved, sizeof(saved), cudaMemcpyHostToDevice, c.s));
   KM_CUDA(cudaStreamSynchronize(c.s));
-  if (best == 0 || !stream_config(mode, c.k, flavour, 0, best, cfg))
+  if (best == 0 || !stream_config(mode, c.k, flavour, 0, best, cfg, c.esize()))
     return fail(KM_E_UNSUPPORTED, "no %s kernel configuration fits (k=%d)", what, c.k);
   std::lock_guard<std::mutex> lk(g_tune_mu);
   g_tune[key] = best;
@@ -414,7 +418,7 @@ km_status swap_k1(Ctx& c, KmState* h) {
   // k = 1: the best single swap is the 1-medoid (Eq. (3)); compare the
   // distance sums of every point with the current medoid's.
   StreamConfig cfg;
-  if (!stream_config(kModeBuild, 1, 0, c.opt.rows_per_tile, c.opt.tune, &cfg))
+  if (!stream_config(kModeBuild, 1, 0, c.opt.rows_per_tile, c.opt.tune, &cfg, c.esize()))
     return fail(KM_E_UNSUPPORTED, "no kernel configuration fits");
   KM_CUDA(cudaMemsetAsync(c.at<void>(c.L.is_med), 0, (size_t)c.L.n_pad, c.s));
   StreamArgs sa = stream_args(c);
@@ -591,7 +595,7 @@ km_status finish(Ctx& c, KmState* h, int32_t* medoids_out, int32_t* labels_out, 
   km_status r = read_state(c, &hs);
   if (r != KM_OK) return r;
   const int rb = hs.rb;
-  if (c.dtype == KM_I32)
+  if (c.dtype != KM_F32)
     KM_CUDA(cudaMemcpyAsync(&td_i, c.at<long long>(c.L.td2) + rb, 8, cudaMemcpyDeviceToHost, c.s));
   else
     KM_CUDA(cudaMemcpyAsync(&td_d, c.at<double>(c.L.td2) + rb, 8, cudaMemcpyDeviceToHost, c.s));
@@ -608,14 +612,14 @@ km_status finish(Ctx& c, KmState* h, int32_t* medoids_out, int32_t* labels_out, 
                             cudaMemcpyDeviceToHost, c.s));
   KM_CUDA(cudaStreamSynchronize(c.s));
   for (int i = 0; i < nt; ++i) {
-    if (c.opt.trace_delta) c.opt.trace_delta[i] = (c.dtype == KM_I32) ? (double)tr[i].di : tr[i].d;
+    if (c.opt.trace_delta) c.opt.trace_delta[i] = (c.dtype != KM_F32) ? (double)tr[i].di : tr[i].d;
     if (c.opt.trace_slot) c.opt.trace_slot[i] = tr[i].slot;
     if (c.opt.trace_cand) c.opt.trace_cand[i] = tr[i].cand;
     if (c.opt.trace_time_ns) c.opt.trace_time_ns[i] = tr[i].t_ns;
   }
   if (res) {
-    res->td = (c.dtype == KM_I32) ? (double)td_i : td_d;
-    res->td_i64 = (c.dtype == KM_I32) ? td_i : 0;
+    res->td = (c.dtype != KM_F32) ? (double)td_i : td_d;
+    res->td_i64 = (c.dtype != KM_F32) ? td_i : 0;
     double sum = 0.0;
     int cnt = 0;
     for (auto& p : ev_swap) {
@@ -648,7 +652,7 @@ void km_default_options(km_options* o) {
 }
 
 size_t kmedoids_workspace_size(int64_t n, int32_t k, int32_t dtype, const km_options* opts) {
-  if (dtype != KM_I32 && dtype != KM_F32) return 0;
+  if (dtype != KM_I32 && dtype != KM_F32 && dtype != KM_U16) return 0;
   WsLayout L;
   km_options def;
   km_default_options(&def);
@@ -775,8 +779,8 @@ static km_status run_impl(bool do_b, bool do_s, const void* D, int32_t dtype, in
     KmState hf;
     r = read_state(c, &hf);
     if (r != KM_OK) return r;
-    res->td_bookkept = (c.dtype == KM_I32) ? (double)hf.td_book_i : hf.td_book_d;
-    if (do_b) res->td_initial = (c.dtype == KM_I32) ? (double)hb.td_book_i : hb.td_book_d;
+    res->td_bookkept = (c.dtype != KM_F32) ? (double)hf.td_book_i : hf.td_book_d;
+    if (do_b) res->td_initial = (c.dtype != KM_F32) ? (double)hb.td_book_i : hb.td_book_d;
     if (tm.on) {
       res->build_ms = tm.ms(b0, b1);
       double s = 0.0;
@@ -836,7 +840,7 @@ km_status kmedoids_eval_swaps(const void* D, int32_t dtype, int64_t n, int64_t l
   r = swap_setup(c);
   if (r != KM_OK) return r;
   StreamConfig cfg;
-  if (!stream_config(kModeSwap, k, kEvalOnly, 0, 0, &cfg))
+  if (!stream_config(kModeSwap, k, kEvalOnly, 0, 0, &cfg, c.esize()))
     return fail(KM_E_UNSUPPORTED, "k=%d too large for the SWAP kernel", k);
   StreamArgs sa = stream_args(c);
   sa.flavour = kEvalOnly;
@@ -851,7 +855,7 @@ km_status kmedoids_eval_swaps(const void* D, int32_t dtype, int64_t n, int64_t l
   r = read_state(c, &h);
   if (r != KM_OK) return r;
   if (best_delta) *best_delta = (h.best_cand < 0) ? __builtin_inf()
-                                                  : (dtype == KM_I32 ? (double)h.best_i : h.best_d);
+                                                  : (dtype != KM_F32 ? (double)h.best_i : h.best_d);
   if (best_slot) *best_slot = h.best_slot;
   if (best_cand) *best_cand = h.best_cand;
   return KM_OK;

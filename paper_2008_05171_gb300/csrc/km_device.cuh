@@ -146,6 +146,27 @@ struct Tr<int32_t> {
   __device__ __forceinline__ static double unfx(long long v, int) { return (double)v; }
 };
 
+// Value type of a stored matrix element: 16-bit unsigned distances (the
+// compressed integer form) are widened to int32, which is exact; int32 and
+// float32 elements are used as stored.
+template <class E>
+struct Val {
+  using type = E;
+};
+template <>
+struct Val<uint16_t> {
+  using type = int32_t;
+};
+
+// Four consecutive stored elements (16-byte aligned for 4-byte types,
+// 8-byte aligned for 16-bit ones) as the value vector.
+__device__ __forceinline__ float4 ld4e(const float* p) { return *reinterpret_cast<const float4*>(p); }
+__device__ __forceinline__ int4 ld4e(const int32_t* p) { return *reinterpret_cast<const int4*>(p); }
+__device__ __forceinline__ int4 ld4e(const uint16_t* p) {
+  const uint2 u = *reinterpret_cast<const uint2*>(p);
+  return make_int4((int)(u.x & 0xffffu), (int)(u.x >> 16), (int)(u.y & 0xffffu), (int)(u.y >> 16));
+}
+
 __device__ __forceinline__ double to_double(double v) { return v; }
 __device__ __forceinline__ double to_double(long long v) { return (double)v; }
 

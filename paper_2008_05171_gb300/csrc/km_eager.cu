@@ -76,7 +76,19 @@ __device__ bool grid_barrier(unsigned* count, unsigned* gen, KmState* st, int* s
   return *s_ok != 0;
 }
 
-constexpr int kEU = 8;  // 16-byte loads per thread in flight in the window loop
+constexpr int kEU = 8;  // row loads (4 elements each) per thread in flight in the window loop
+
+// Elements 4q .. 4q+3 of a matrix row, streamed (read once per window).
+__device__ __forceinline__ float4 ld_row4(const float* row, int q) {
+  return __ldcs(reinterpret_cast<const float4*>(row) + q);
+}
+__device__ __forceinline__ int4 ld_row4(const int32_t* row, int q) {
+  return __ldcs(reinterpret_cast<const int4*>(row) + q);
+}
+__device__ __forceinline__ int4 ld_row4(const uint16_t* row, int q) {
+  const uint2 u = __ldcs(reinterpret_cast<const uint2*>(row) + q);
+  return make_int4((int)(u.x & 0xffffu), (int)(u.x >> 16), (int)(u.y & 0xffffu), (int)(u.y >> 16));
+}
 
 template <class V>
 __device__ __forceinline__ auto comp4(const V& v, int j) -> decltype(v.x) {
@@ -128,8 +140,9 @@ __device__ __forceinline__ void e_push(T v, int j, int& n1, T& d1, int& n2, T& d
 // Dynamic shared memory: k + 1 64-bit accumulators (window phase) or k
 // removal-loss partials (apply phase), the medoid of every slot, and the
 // per-warp hit queues (point index, distance).
-template <class T>
+template <class E>
 __global__ void __launch_bounds__(kEThreads, 1) k_eager(const EagerArgs a) {
+  using T = typename Val<E>::type;  // 16-bit elements widen to int32
   using A = long long;
   using G = typename Tr<T>::G;
   using Vec = typename V4e<T>::type;
@@ -150,7 +163,7 @@ __global__ void __launch_bounds__(kEThreads, 1) k_eager(const EagerArgs a) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int Gn = gridDim.x;
   const bool clarans = (a.flavour == kCLARANS);
-  const T* D = static_cast<const T*>(a.D);
+  const E* D = static_cast<const E*>(a.D);
   T* dn = static_cast<T*>(a.dn);
   T* ds = static_cast<T*>(a.ds);
   A* rem = static_cast<A*>(a.removal);
@@ -197,7 +210,7 @@ __global__ void __launch_bounds__(kEThreads, 1) k_eager(const EagerArgs a) {
       }
       for (int i = tid; i <= k; i += kEThreads) e_acc[i] = 0;
       __syncthreads();
-      const Vec* r4 = reinterpret_cast<const Vec*>(D + (size_t)row * a.ld);
+      const E* rowp = D + (size_t)row * a.ld;
       const Vec* s4 = reinterpret_cast<const Vec*>(ds);
       const int n4 = (n + 3) >> 2;
       // U float4 of the row and of d_s in flight per thread before any is
@@ -216,7 +229,7 @@ __global__ void __launch_bounds__(kEThreads, 1) k_eager(const EagerArgs a) {
         for (int u = 0; u < kEU; ++u) {
           const int q = q0 + u * kEThreads;
           if (q < n4) {
-            d4[u] = __ldcs(r4 + q);
+            d4[u] = ld_row4(rowp, q);
             e4[u] = __ldcg(s4 + q);
           }
         }
@@ -442,14 +455,14 @@ __global__ void __launch_bounds__(kEThreads, 1) k_eager(const EagerArgs a) {
     __syncthreads();
     A* rn = rem + (size_t)(rb ^ 1) * a.k_pad;
     G tdl = G(0);
-    const T* rowc = D + (size_t)c_s * a.ld;
+    const E* rowc = D + (size_t)c_s * a.ld;
     // a contiguous share of the points per CTA (every CTA takes part)
     const int per = (n + Gn - 1) / Gn;
     const int lo = blockIdx.x * per, hi = min(lo + per, n);
     for (int base = lo; base < hi; base += kEThreads) {
       const int o = base + tid;
       if (o < hi) {
-        const T dc = rowc[o];  // issued with the cache loads (used unless rescanned)
+        const T dc = (T)rowc[o];  // issued with the cache loads (used unless rescanned)
         int n1 = __ldcg(a.near + o), n2 = __ldcg(a.sec + o);
         T d1 = __ldcg(dn + o), d2 = __ldcg(ds + o);
         if (n1 == i_s || n2 == i_s) {
@@ -480,7 +493,8 @@ __global__ void __launch_bounds__(kEThreads, 1) k_eager(const EagerArgs a) {
         int n1 = -1, n2 = -1;
         T d1 = Tr<T>::high(), d2 = Tr<T>::high();
 #pragma unroll 4
-        for (int j = lane; j < k; j += 32) e_push(D[(size_t)s_med[j] * a.ld + oo], j, n1, d1, n2, d2);
+        for (int j = lane; j < k; j += 32)
+          e_push((T)D[(size_t)s_med[j] * a.ld + oo], j, n1, d1, n2, d2);
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) {
           const int m1 = __shfl_xor_sync(0xffffffffu, n1, off);
@@ -570,6 +584,11 @@ int eager_grid(int dtype, int k) {
                              (int)smem);
     if (e == cudaSuccess)
       e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_eager<int32_t>, kEThreads, smem);
+  } else if (dtype == 2) {
+    e = cudaFuncSetAttribute(k_eager<uint16_t>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem);
+    if (e == cudaSuccess)
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_eager<uint16_t>, kEThreads, smem);
   } else {
     e = cudaFuncSetAttribute(k_eager<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem);
@@ -587,6 +606,9 @@ cudaError_t launch_eager(int dtype, int grid, const EagerArgs& a, cudaStream_t s
   if (dtype == 0)
     return cudaLaunchCooperativeKernel((const void*)k_eager<int32_t>, dim3(grid), dim3(kEThreads),
                                        args, smem, s);
+  if (dtype == 2)
+    return cudaLaunchCooperativeKernel((const void*)k_eager<uint16_t>, dim3(grid),
+                                       dim3(kEThreads), args, smem, s);
   return cudaLaunchCooperativeKernel((const void*)k_eager<float>, dim3(grid), dim3(kEThreads),
                                      args, smem, s);
 }

@@ -63,13 +63,14 @@ __device__ __forceinline__ long long block_excl_scan(long long v, long long* s_w
 // 32-point chunk) and each warp stores its chunks' weight sums; a block scan
 // over contiguous runs of chunk sums finds the chunk holding T, and one
 // warp scans inside it.
-template <class T>
+template <class E>
 __global__ void __launch_bounds__(kInitThreads) k_init_weighted(const InitArgs a) {
+  using T = typename Val<E>::type;  // 16-bit elements widen to int32
   __shared__ long long s_w[kInitWarps];
   __shared__ long long s_rem;
   __shared__ int s_chunk;
   __shared__ int s_pick;
-  const T* D = static_cast<const T*>(a.D);
+  const E* D = static_cast<const E*>(a.D);
   T* dn = static_cast<T*>(a.dn);
   long long* csum = a.csum;
   const int n = a.n;
@@ -90,7 +91,7 @@ __global__ void __launch_bounds__(kInitThreads) k_init_weighted(const InitArgs a
 
   for (int t = 1; t < a.k; ++t) {
     // d_n update with the previous pick's row, chunk sums of the weights
-    const T* row = D + (size_t)pick * (size_t)a.ld;
+    const E* row = D + (size_t)pick * (size_t)a.ld;
     for (int q = warp; q < nch; q += kInitWarps) {
       const int o = (q << 5) + lane;
       long long w = 0;
@@ -169,8 +170,9 @@ __global__ void __launch_bounds__(kInitThreads) k_init_weighted(const InitArgs a
 // sum_{o in S} fx(d(o,c)); the least (gain, point) wins.  Then d_n takes the
 // row of the new medoid.  Dynamic shared memory: sorted medoids (k int32),
 // subsample points (s int32), fx(d_n) of the subsample (s int64).
-template <class T>
+template <class E>
 __global__ void __launch_bounds__(kInitThreads) k_init_lab(const InitArgs a) {
+  using T = typename Val<E>::type;  // 16-bit elements widen to int32
   extern __shared__ __align__(16) unsigned char sm_raw[];
   long long* s_dn = reinterpret_cast<long long*>(sm_raw);
   int32_t* s_pts = reinterpret_cast<int32_t*>(s_dn + a.s);
@@ -178,7 +180,7 @@ __global__ void __launch_bounds__(kInitThreads) k_init_lab(const InitArgs a) {
   __shared__ long long s_g[kInitWarps];
   __shared__ int s_c[kInitWarps];
   __shared__ int s_pick;
-  const T* D = static_cast<const T*>(a.D);
+  const E* D = static_cast<const E*>(a.D);
   T* dn = static_cast<T*>(a.dn);
   const int n = a.n, s = a.s;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -207,7 +209,7 @@ __global__ void __launch_bounds__(kInitThreads) k_init_lab(const InitArgs a) {
     for (int jc = warp; jc < s; jc += kInitWarps) {
       const int c = s_pts[jc];
       if (c < 0) continue;
-      const T* row = D + (size_t)c * (size_t)a.ld;
+      const E* row = D + (size_t)c * (size_t)a.ld;
       long long g = 0;
       for (int jo = lane; jo < s; jo += 32) {
         const int o = s_pts[jo];
@@ -262,7 +264,7 @@ __global__ void __launch_bounds__(kInitThreads) k_init_lab(const InitArgs a) {
       return;
     }
     if (t + 1 < a.k) {
-      const T* row = D + (size_t)pick * (size_t)a.ld;
+      const E* row = D + (size_t)pick * (size_t)a.ld;
       for (int o = tid; o < n; o += kInitThreads) {
         const T v = row[o];
         dn[o] = (t == 0 || v < dn[o]) ? v : dn[o];
@@ -278,6 +280,8 @@ size_t init_lab_smem(int k, int s) { return (size_t)s * 12 + (size_t)k * 4; }
 cudaError_t launch_init_weighted(int dtype, const InitArgs& a, cudaStream_t st) {
   if (dtype == 0)
     k_init_weighted<int32_t><<<1, kInitThreads, 0, st>>>(a);
+  else if (dtype == 2)
+    k_init_weighted<uint16_t><<<1, kInitThreads, 0, st>>>(a);
   else
     k_init_weighted<float><<<1, kInitThreads, 0, st>>>(a);
   return cudaGetLastError();
@@ -291,6 +295,11 @@ cudaError_t launch_init_lab(int dtype, const InitArgs& a, cudaStream_t st) {
                              (int)smem);
     if (e != cudaSuccess) return e;
     k_init_lab<int32_t><<<1, kInitThreads, smem, st>>>(a);
+  } else if (dtype == 2) {
+    e = cudaFuncSetAttribute(k_init_lab<uint16_t>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem);
+    if (e != cudaSuccess) return e;
+    k_init_lab<uint16_t><<<1, kInitThreads, smem, st>>>(a);
   } else {
     e = cudaFuncSetAttribute(k_init_lab<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem);

@@ -162,7 +162,9 @@ struct StreamConfig {
 
 // Returns false if no configuration fits (k too large).  tune > 0 forces a
 // geometry of the table; forced_rows > 0 restricts the automatic choice.
-bool stream_config(int mode, int k, int flavour, int forced_rows, int tune, StreamConfig* cfg);
+// esize: bytes per stored matrix element (4, or 2 for the 16-bit form).
+bool stream_config(int mode, int k, int flavour, int forced_rows, int tune, StreamConfig* cfg,
+                   int esize = 4);
 
 cudaError_t launch_stream(int dtype, int mode, const StreamConfig& cfg, int grid,
                           const StreamArgs& a, cudaStream_t s);

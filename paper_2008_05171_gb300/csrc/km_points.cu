@@ -54,8 +54,9 @@ __device__ __forceinline__ void top2_push(T v, int j, int& n1, T& d1, int& n2, T
 }
 
 // ------------------------------------------------------------ cache init
-template <class T>
+template <class E>
 __global__ void __launch_bounds__(kPtThreads) k_cache_init(const PointArgs a) {
+  using T = typename Val<E>::type;  // 16-bit elements widen to int32
   using A = typename Tr<T>::A;  // removal loss (fixed point / int64)
   using G = typename Tr<T>::G;  // TD
   extern __shared__ __align__(16) unsigned char sm[];
@@ -68,7 +69,7 @@ __global__ void __launch_bounds__(kPtThreads) k_cache_init(const PointArgs a) {
   for (int i = threadIdx.x; i < k; i += blockDim.x) sacc[i] = A(0);
   __syncthreads();
   const int o = blockIdx.x * blockDim.x + threadIdx.x;
-  const T* D = static_cast<const T*>(a.D);
+  const E* D = static_cast<const E*>(a.D);
   T* dn = static_cast<T*>(a.dn);
   T* ds = static_cast<T*>(a.ds);
   G tdl = G(0);
@@ -139,8 +140,9 @@ __device__ __forceinline__ void top2_merge(int& n1, T& d1, int& n2, T& d2, int m
   }
 }
 
-template <class T>
+template <class E>
 __global__ void __launch_bounds__(kPtThreads) k_apply(const PointArgs a) {
+  using T = typename Val<E>::type;  // 16-bit elements widen to int32
   using A = typename Tr<T>::A;  // removal loss (fixed point / int64)
   using G = typename Tr<T>::G;  // TD
   extern __shared__ __align__(16) unsigned char sm[];
@@ -159,7 +161,7 @@ __global__ void __launch_bounds__(kPtThreads) k_apply(const PointArgs a) {
   if (threadIdx.x == 0) s_cnt = 0;
   __syncthreads();
   const int o = blockIdx.x * blockDim.x + threadIdx.x;
-  const T* D = static_cast<const T*>(a.D);
+  const E* D = static_cast<const E*>(a.D);
   T* dn = static_cast<T*>(a.dn);
   T* ds = static_cast<T*>(a.ds);
   G tdl = G(0);
@@ -201,7 +203,7 @@ __global__ void __launch_bounds__(kPtThreads) k_apply(const PointArgs a) {
     T d1 = Tr<T>::high(), d2 = Tr<T>::high();
     for (int j = lane; j < k; j += 32) {
       const int m = (j == i_s) ? c_s : a.med[j];
-      top2_push(D[(size_t)m * a.ld + oo], j, n1, d1, n2, d2);
+      top2_push((T)D[(size_t)m * a.ld + oo], j, n1, d1, n2, d2);
     }
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) {
@@ -255,8 +257,9 @@ __global__ void __launch_bounds__(kPtThreads) k_apply(const PointArgs a) {
 }
 
 // ------------------------------------------------------------ BUILD commit
-template <class T>
+template <class E>
 __global__ void __launch_bounds__(kPtThreads) k_build_commit(const PointArgs a) {
+  using T = typename Val<E>::type;  // 16-bit elements widen to int32
   using A = typename Tr<T>::G;
   __shared__ A scratch[kPtThreads / 32];
   KmState* st = a.st;
@@ -264,7 +267,7 @@ __global__ void __launch_bounds__(kPtThreads) k_build_commit(const PointArgs a) 
   const int n = a.n;
   const int c = st->build_cand;
   const int o = blockIdx.x * blockDim.x + threadIdx.x;
-  const T* D = static_cast<const T*>(a.D);
+  const E* D = static_cast<const E*>(a.D);
   T* bdn = static_cast<T*>(a.bdn);
   A local = A(0);
   if (c >= 0 && c < n) {
@@ -306,8 +309,9 @@ __global__ void __launch_bounds__(kPtThreads) k_build_commit(const PointArgs a) 
 }
 
 // ----------------------------------------------- FastPAM2 additional swap
-template <class T>
+template <class E>
 __global__ void __launch_bounds__(kPtThreads) k_fp2_try(const PointArgs a) {
+  using T = typename Val<E>::type;  // 16-bit elements widen to int32
   using A = typename Tr<T>::G;   // exact Delta of Eq. (5)
   using R = typename Tr<T>::A;   // removal-loss buffers
   __shared__ A scratch[kPtThreads / 32];
@@ -332,7 +336,7 @@ __global__ void __launch_bounds__(kPtThreads) k_fp2_try(const PointArgs a) {
   }
   const int n = a.n;
   const int o = blockIdx.x * blockDim.x + threadIdx.x;
-  const T* D = static_cast<const T*>(a.D);
+  const E* D = static_cast<const E*>(a.D);
   const T* dn = static_cast<const T*>(a.dn);
   const T* ds = static_cast<const T*>(a.ds);
   A v = A(0);
@@ -444,6 +448,9 @@ cudaError_t launch_cache_init(int dtype, const PointArgs& a, cudaStream_t s) {
   if (dtype == 0) {
     cudaFuncSetAttribute(k_cache_init<int32_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     k_cache_init<int32_t><<<grid, kPtThreads, smem, s>>>(a);
+  } else if (dtype == 2) {
+    cudaFuncSetAttribute(k_cache_init<uint16_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_cache_init<uint16_t><<<grid, kPtThreads, smem, s>>>(a);
   } else {
     cudaFuncSetAttribute(k_cache_init<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     k_cache_init<float><<<grid, kPtThreads, smem, s>>>(a);
@@ -457,6 +464,9 @@ cudaError_t launch_apply(int dtype, const PointArgs& a, cudaStream_t s) {
   if (dtype == 0) {
     cudaFuncSetAttribute(k_apply<int32_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     k_apply<int32_t><<<grid, kPtThreads, smem, s>>>(a);
+  } else if (dtype == 2) {
+    cudaFuncSetAttribute(k_apply<uint16_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_apply<uint16_t><<<grid, kPtThreads, smem, s>>>(a);
   } else {
     cudaFuncSetAttribute(k_apply<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     k_apply<float><<<grid, kPtThreads, smem, s>>>(a);
@@ -468,6 +478,8 @@ cudaError_t launch_build_commit(int dtype, const PointArgs& a, cudaStream_t s) {
   const int grid = blocks_for(a.n_pad);
   if (dtype == 0)
     k_build_commit<int32_t><<<grid, kPtThreads, 0, s>>>(a);
+  else if (dtype == 2)
+    k_build_commit<uint16_t><<<grid, kPtThreads, 0, s>>>(a);
   else
     k_build_commit<float><<<grid, kPtThreads, 0, s>>>(a);
   return cudaGetLastError();
@@ -478,6 +490,8 @@ cudaError_t launch_fp2_try(int dtype, const PointArgs& a, cudaStream_t s) {
   if (grid > kMaxGrid) return cudaErrorInvalidConfiguration;
   if (dtype == 0)
     k_fp2_try<int32_t><<<grid, kPtThreads, 0, s>>>(a);
+  else if (dtype == 2)
+    k_fp2_try<uint16_t><<<grid, kPtThreads, 0, s>>>(a);
   else
     k_fp2_try<float><<<grid, kPtThreads, 0, s>>>(a);
   return cudaGetLastError();
@@ -494,7 +508,7 @@ cudaError_t launch_fill_medoid_rows(const PointArgs& a, cudaStream_t s) {
 }
 
 cudaError_t launch_removal_to_double(int dtype, const PointArgs& a, cudaStream_t s) {
-  if (dtype == 0)
+  if (dtype == 0 || dtype == 2)
     k_removal_to_double<int32_t><<<(a.k + 255) / 256, 256, 0, s>>>(a);
   else
     k_removal_to_double<float><<<(a.k + 255) / 256, 256, 0, s>>>(a);

@@ -58,7 +58,8 @@ struct Layout {
 __host__ __device__ inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 // Offsets of the dynamic shared-memory regions (bytes).
-__host__ __device__ inline Layout make_layout(int mode, int R, int S, int k, int fp2) {
+__host__ __device__ inline Layout make_layout(int mode, int R, int S, int k, int fp2,
+                                              int esize = 4) {
   Layout L;
   size_t o = 0;
   L.bars = o;
@@ -86,7 +87,7 @@ __host__ __device__ inline Layout make_layout(int mode, int R, int S, int k, int
   o = align_up(o, 128);
   L.stages = o;
   L.meta_bytes = (mode == kModeSwap) ? 3 * 4 * (size_t)kChunk : 4 * (size_t)kChunk;
-  L.stage_bytes = 256 + L.meta_bytes + 4 * (size_t)R * kChunk;
+  L.stage_bytes = 256 + L.meta_bytes + (size_t)esize * R * kChunk;
   o += L.stage_bytes * S;
   L.total = o;
   return L;
@@ -110,11 +111,12 @@ __device__ __forceinline__ unsigned lanemask_lt() {
   return m;
 }
 
-template <class T>
-__device__ __forceinline__ void swap_hit_at(int r, int col, const T* data,
+template <class E>
+__device__ __forceinline__ void swap_hit_at(int r, int col, const E* data,
                                             const unsigned char* meta, long long* acc, int k,
                                             int f) {
-  const T d = data[(size_t)r * kChunk + col];
+  using T = typename Val<E>::type;
+  const T d = (T)data[(size_t)r * kChunk + col];
   const T dn = reinterpret_cast<const T*>(meta)[col];
   const T ds = reinterpret_cast<const T*>(meta + 4 * kChunk)[col];
   const int sl = reinterpret_cast<const int32_t*>(meta + 8 * kChunk)[col];
@@ -130,9 +132,9 @@ __device__ __forceinline__ void swap_hit_at(int r, int col, const T* data,
 }
 
 // All hits of one stage for this warp; hmask as above, t = 32 warp + lane.
-template <class T>
+template <class E>
 __device__ __forceinline__ void swap_stage_hits(unsigned long long hmask, uint16_t* q, int lane,
-                                                int warp, const T* data,
+                                                int warp, const E* data,
                                                 const unsigned char* meta, long long* acc, int k,
                                                 int f) {
   const int cnt = __popcll(hmask);
@@ -155,7 +157,7 @@ __device__ __forceinline__ void swap_stage_hits(unsigned long long hmask, uint16
     for (int e = lane; e < total; e += 32) {
       const unsigned v = q[e];
       const int b = (int)(v >> 5), src = (int)(v & 31u);
-      swap_hit_at<T>(b >> 2, 4 * (warp * 32 + src) + (b & 3), data, meta, acc, k, f);
+      swap_hit_at<E>(b >> 2, 4 * (warp * 32 + src) + (b & 3), data, meta, acc, k, f);
     }
     __syncwarp();
   } else {
@@ -163,14 +165,15 @@ __device__ __forceinline__ void swap_stage_hits(unsigned long long hmask, uint16
     while (hmask) {
       const int b = __ffsll(hmask) - 1;
       hmask &= hmask - 1;
-      swap_hit_at<T>(b >> 2, 4 * (warp * 32 + lane) + (b & 3), data, meta, acc, k, f);
+      swap_hit_at<E>(b >> 2, 4 * (warp * 32 + lane) + (b & 3), data, meta, acc, k, f);
     }
     __syncwarp();
   }
 }
 
-template <class T, int MODE, int R, int S, int MINB>
+template <class E, int MODE, int R, int S, int MINB>
 __global__ void __launch_bounds__(kThreads, MINB) k_stream(const StreamArgs a) {
+  using T = typename Val<E>::type;  // value type (16-bit elements widen to int32)
   using G = typename Tr<T>::G;
   using A = long long;  // SWAP accumulators (fixed point / int64)
   using KA = typename std::conditional<MODE == kModeSwap, long long, G>::type;
@@ -182,7 +185,7 @@ __global__ void __launch_bounds__(kThreads, MINB) k_stream(const StreamArgs a) {
 
   const int n = a.n, k = a.k, f = a.fshift;
   const int fp2 = (MODE == kModeSwap && a.flavour == kFastPAM2);
-  const Layout L = make_layout(MODE, R, S, k, fp2);
+  const Layout L = make_layout(MODE, R, S, k, fp2, (int)sizeof(E));
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + L.bars);
   uint64_t* empty = full + S;
   uint64_t* cbar = empty + S;
@@ -259,7 +262,9 @@ __global__ void __launch_bounds__(kThreads, MINB) k_stream(const StreamArgs a) {
   }
   const unsigned ntiles = (unsigned)((n + R - 1) / R);
   const int nchunks = (n + kChunk - 1) / kChunk;
-  const int n4 = (n + 3) & ~3;
+  // columns copied per row: n rounded up to whole 16-byte pieces
+  constexpr int kGran = 16 / (int)sizeof(E);
+  const int n4 = (n + kGran - 1) / kGran * kGran;
 
   // ================================================================ producer
   if (warp == kConsWarps) {
@@ -316,7 +321,7 @@ __global__ void __launch_bounds__(kThreads, MINB) k_stream(const StreamArgs a) {
           h->last = (j == nchunks - 1);
           const int col0 = j * kChunk;
           const int cols = (n4 - col0 < kChunk) ? (n4 - col0) : kChunk;
-          const uint32_t rbytes = 4u * (uint32_t)cols;
+          const uint32_t rbytes = (uint32_t)sizeof(E) * (uint32_t)cols;
           const uint32_t mbytes = (uint32_t)L.meta_bytes;
           mbar_arrive_expect_tx(&full[s], rbytes * nr + mbytes);
           used |= 1u << s;
@@ -330,10 +335,10 @@ __global__ void __launch_bounds__(kThreads, MINB) k_stream(const StreamArgs a) {
             bulk_g2s(meta, static_cast<const T*>(a.bdn) + col0, 4 * kChunk, &full[s]);
           }
           unsigned char* data = meta + L.meta_bytes;
-          const T* D = static_cast<const T*>(a.D);
+          const E* D = static_cast<const E*>(a.D);
           for (int r = 0; r < nr; ++r)
-            bulk_g2s(data + (size_t)r * 4 * kChunk, D + (size_t)rows[r] * a.ld + col0, rbytes,
-                     &full[s]);
+            bulk_g2s(data + (size_t)r * sizeof(E) * kChunk, D + (size_t)rows[r] * a.ld + col0,
+                     rbytes, &full[s]);
           if (++s == S) {
             s = 0;
             ph ^= 1;
@@ -399,19 +404,19 @@ __global__ void __launch_bounds__(kThreads, MINB) k_stream(const StreamArgs a) {
     const int my_row = (lane < nr) ? h->rows[lane] : -1;
     const int my_out = (lane < nr) ? h->outidx[lane] : -1;
     const unsigned char* meta = sb + 256;
-    const T* data = reinterpret_cast<const T*>(meta + L.meta_bytes);
+    const E* data = reinterpret_cast<const E*>(meta + L.meta_bytes);
 
     if (MODE == kModeSwap) {
       const Vec ds4 = lds4(reinterpret_cast<const T*>(meta + 4 * kChunk) + 4 * t);
       unsigned long long hmask = 0ull;
 #pragma unroll 4
       for (int r = 0; r < nr; ++r) {
-        const Vec d4 = lds4(data + (size_t)r * kChunk + 4 * t);
+        const Vec d4 = ld4e(data + (size_t)r * kChunk + 4 * t);
         const unsigned hm = (d4.x < ds4.x ? 1u : 0u) | (d4.y < ds4.y ? 2u : 0u) |
                             (d4.z < ds4.z ? 4u : 0u) | (d4.w < ds4.w ? 8u : 0u);
         hmask |= (unsigned long long)hm << (4 * r);
       }
-      swap_stage_hits<T>(hmask, queues + warp * kQueue, lane, warp, data, meta, acc, k, f);
+      swap_stage_hits<E>(hmask, queues + warp * kQueue, lane, warp, data, meta, acc, k, f);
     } else {
       const int col = chunk * kChunk + 4 * t;
       const bool v0 = col < n, v1 = col + 1 < n, v2 = col + 2 < n, v3 = col + 3 < n;
@@ -420,7 +425,7 @@ __global__ void __launch_bounds__(kThreads, MINB) k_stream(const StreamArgs a) {
 #pragma unroll
       for (int r = 0; r < R; ++r) {
         if (r < nr) {
-          const Vec d4 = lds4(data + (size_t)r * kChunk + 4 * t);
+          const Vec d4 = ld4e(data + (size_t)r * kChunk + 4 * t);
           T x0, x1, x2, x3;
           if (first) {
             x0 = v0 ? d4.x : T(0);
@@ -818,10 +823,11 @@ static const Geometry kGeoms[] = {
 };
 static const int kNumGeoms = sizeof(kGeoms) / sizeof(kGeoms[0]);
 
-bool stream_config(int mode, int k, int flavour, int forced_rows, int tune, StreamConfig* cfg) {
+bool stream_config(int mode, int k, int flavour, int forced_rows, int tune, StreamConfig* cfg,
+                   int esize) {
   const int fp2 = (mode == kModeSwap && flavour == kFastPAM2);
   auto fits = [&](const Geometry& g, size_t* bytes) {
-    const Layout L = make_layout(mode, g.rows, g.stages, k, fp2);
+    const Layout L = make_layout(mode, g.rows, g.stages, k, fp2, esize);
     const size_t limit = (size_t)228 * 1024 / g.minb - 1024;
     *bytes = L.total;
     return L.total <= limit;
@@ -855,10 +861,10 @@ bool stream_config(int mode, int k, int flavour, int forced_rows, int tune, Stre
   return false;
 }
 
-template <class T, int MODE, int R, int S, int MINB>
+template <class E, int MODE, int R, int S, int MINB>
 static cudaError_t launch_one(const StreamConfig& cfg, int grid, const StreamArgs& a,
                               cudaStream_t s) {
-  auto kern = k_stream<T, MODE, R, S, MINB>;
+  auto kern = k_stream<E, MODE, R, S, MINB>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)cfg.smem);
   if (e != cudaSuccess) return e;
@@ -895,6 +901,9 @@ cudaError_t launch_stream(int dtype, int mode, const StreamConfig& cfg, int grid
   if (dtype == 0)
     return mode == kModeSwap ? launch_geo<int32_t, kModeSwap>(cfg, grid, a, s)
                              : launch_geo<int32_t, kModeBuild>(cfg, grid, a, s);
+  if (dtype == 2)
+    return mode == kModeSwap ? launch_geo<uint16_t, kModeSwap>(cfg, grid, a, s)
+                             : launch_geo<uint16_t, kModeBuild>(cfg, grid, a, s);
   return mode == kModeSwap ? launch_geo<float, kModeSwap>(cfg, grid, a, s)
                            : launch_geo<float, kModeBuild>(cfg, grid, a, s);
 }

@@ -15,7 +15,7 @@ import threading
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libkmedoids.so")
 
-KM_I32, KM_F32 = 0, 1
+KM_I32, KM_F32, KM_U16 = 0, 1, 2
 VARIANTS = {"fastpam1": 0, "fastpam2": 1, "fasterpam": 2, "fastclarans": 3}
 STATUS = {0: "KM_OK", 1: "KM_E_INVALID", 2: "KM_E_WORKSPACE", 3: "KM_E_CUDA",
           4: "KM_E_NOT_CONVERGED", 5: "KM_E_TIMEOUT", 6: "KM_E_NUMERIC",
@@ -154,12 +154,16 @@ def _torch():
 
 
 def _dtype_code(D) -> int:
+    """int32 -> KM_I32, float32 -> KM_F32; uint16 (or int16, whose bits are
+    read as unsigned) -> KM_U16, the compressed integer form."""
     torch = _torch()
     if D.dtype == torch.int32:
         return KM_I32
     if D.dtype == torch.float32:
         return KM_F32
-    raise TypeError("D must be int32 or float32 (got %s)" % D.dtype)
+    if D.dtype == torch.int16 or D.dtype == getattr(torch, "uint16", None):
+        return KM_U16
+    raise TypeError("D must be int32, float32 or 16-bit (got %s)" % D.dtype)
 
 
 def _matrix(D, n):
@@ -361,8 +365,9 @@ def cache(D, medoids, n=None, ws=None):
         ws = workspace(n, k, code, None, device=D.device)
     near = torch.empty(n, dtype=torch.int32, device=D.device)
     sec = torch.empty(n, dtype=torch.int32, device=D.device)
-    dn = torch.empty(n, dtype=D.dtype, device=D.device)
-    ds = torch.empty(n, dtype=D.dtype, device=D.device)
+    cdt = torch.int32 if code == KM_U16 else D.dtype  # the 16-bit form caches int32
+    dn = torch.empty(n, dtype=cdt, device=D.device)
+    ds = torch.empty(n, dtype=cdt, device=D.device)
     rl = torch.empty(k, dtype=torch.float64, device=D.device)
     _check(lib.kmedoids_cache(
         ctypes.c_void_p(D.data_ptr()), code, n, ld, k,
