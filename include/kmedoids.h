@@ -68,7 +68,7 @@ typedef enum {
   KM_E_NOT_CONVERGED = 4, /* max_iter reached; results are the best so far */
   KM_E_TIMEOUT = 5,       /* a device-side wait gave up */
   KM_E_NUMERIC = 6,       /* non-finite value met where a distance was due */
-  KM_E_UNSUPPORTED = 7    /* valid but outside this build's limits */
+  KM_E_UNSUPPORTED = 7    /* valid but outside the library's limits */
 } km_status;
 
 /* KM_U16: the compressed integer form -- unsigned 16-bit distances (0 ..
@@ -138,6 +138,13 @@ typedef struct km_options {
   int64_t draws_len;
   int64_t maxneighbor;    /* consecutive failed draws that end the search
                              (the paper samples 2.5 % of n - k) */
+  int32_t check_input;    /* nonzero (kmedoids_build / _swap / _run): one
+                             extra pass over D before any other work checks
+                             the assumptions of the method -- zero
+                             diagonal and bitwise symmetry (else
+                             KM_E_INVALID) and, for KM_F32, entries finite
+                             and >= 0 (else KM_E_NUMERIC); 32 x 32 tiles of
+                             the upper triangle against their mirrors */
 } km_options;
 
 /* Results, filled on the HOST before the call returns. */

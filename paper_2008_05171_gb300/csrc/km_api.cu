@@ -353,6 +353,7 @@ km_status config_for(Ctx& c, int mode, int flavour, const StreamArgs& sa, Stream
 
 // ------------------------------------------------------------------ BUILD
 km_status do_build(Ctx& c, Timer& tm, std::vector<std::pair<int, int>>& ev, km_result* res) {
+  NvtxRange nv("kmedoids BUILD");
   KM_CUDA(cudaMemsetAsync(c.at<void>(c.L.is_med), 0, (size_t)c.L.n_pad, c.s));
   StreamArgs sa = stream_args(c);
   sa.build_first = 1;
@@ -466,6 +467,7 @@ km_status swap_k1(Ctx& c, KmState* h) {
 
 km_status do_swap(Ctx& c, Timer& tm, std::vector<std::pair<int, int>>& ev, KmState* h,
                   km_result* res) {
+  NvtxRange nv("kmedoids SWAP");
   km_status r = swap_setup(c);
   if (r != KM_OK) return r;
   if (c.k == 1) return swap_k1(c, h);
@@ -669,6 +671,7 @@ static km_status run_impl(bool do_b, bool do_s, const void* D, int32_t dtype, in
                           const km_options* opts, km_result* res, void* ws, size_t ws_bytes,
                           void* stream) {
   g_err.clear();
+  NvtxRange nv(do_b ? (do_s ? "kmedoids_run" : "kmedoids_build") : "kmedoids_swap");
   Ctx c;
   km_status r = check_common(D, dtype, n, ld, k, ws, ws_bytes, opts, &c);
   if (r != KM_OK) {
@@ -685,6 +688,15 @@ static km_status run_impl(bool do_b, bool do_s, const void* D, int32_t dtype, in
   std::vector<std::pair<int, int>> ev_build, ev_swap;
   r = reset_state(c);
   if (r != KM_OK) return r;
+  if (c.opt.check_input) {
+    KM_LAUNCH(c, launch_matrix_check(c.dtype, c.D, c.ld, c.n, &c.st()->check_flags, c.s));
+    unsigned fl = 0;
+    KM_CUDA(cudaMemcpyAsync(&fl, &c.st()->check_flags, 4, cudaMemcpyDeviceToHost, c.s));
+    KM_CUDA(cudaStreamSynchronize(c.s));
+    if (fl & 4u) return fail(KM_E_NUMERIC, "D holds a negative, infinite or NaN entry");
+    if (fl & 2u) return fail(KM_E_INVALID, "D has a nonzero diagonal entry");
+    if (fl & 1u) return fail(KM_E_INVALID, "D is not symmetric");
+  }
   KmState h;
   memset(&h, 0, sizeof(h));
 
@@ -933,6 +945,7 @@ static km_status init_finish(Ctx& c, int32_t* medoids_out) {
 km_status kmedoids_init_weighted(const void* D, int32_t dtype, int64_t n, int64_t ld, int32_t k,
                                  const double* u, int32_t* medoids_out, void* ws,
                                  size_t ws_bytes, void* stream) {
+  NvtxRange nv("kmedoids_init_weighted");
   Ctx c;
   InitArgs ia;
   if (!u) return fail(KM_E_INVALID, "u is NULL");
@@ -952,6 +965,7 @@ km_status kmedoids_init_weighted(const void* D, int32_t dtype, int64_t n, int64_
 km_status kmedoids_init_lab(const void* D, int32_t dtype, int64_t n, int64_t ld, int32_t k,
                             int32_t s, const int32_t* ranks, int32_t* medoids_out,
                             double* gains_host, void* ws, size_t ws_bytes, void* stream) {
+  NvtxRange nv("kmedoids_init_lab");
   Ctx c;
   InitArgs ia;
   if (!ranks) return fail(KM_E_INVALID, "ranks is NULL");

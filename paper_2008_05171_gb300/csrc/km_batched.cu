@@ -1070,6 +1070,7 @@ extern "C" size_t kmedoids_batched_workspace_size(int32_t count) {
 static km_status batched_impl(bool start_given, const float* arena, const km_instance* inst,
                               int32_t count, int32_t* medoids_out, km_batch_result* results,
                               const km_options* opts, void* ws, size_t ws_bytes, void* stream) {
+  NvtxRange nv(start_given ? "kmedoids_swap_batched" : "kmedoids_run_batched");
   set_last_error("");
   if (!arena || !inst || !medoids_out || !results || !ws) return bfail(KM_E_INVALID, "NULL pointer");
   if (count <= 0 || count > kBatchMaxCount)
@@ -1167,6 +1168,7 @@ extern "C" km_status kmedoids_clara(const float* X, int64_t n, int32_t d, int32_
                                     const int32_t* sample_idx, int32_t* medoids_out,
                                     int32_t* labels_out, double* sample_td_host,
                                     km_result* res, void* ws, size_t ws_bytes, void* stream) {
+  NvtxRange nv("kmedoids_clara");
   set_last_error("");
   if (!X || !sample_idx || !medoids_out || !ws) return bfail(KM_E_INVALID, "NULL pointer");
   if (n <= 0 || d <= 0 || d > kDistMaxDim || k <= 0 || samples <= 0 || samples > kBatchMaxCount ||

@@ -62,6 +62,7 @@ struct KmState {
   long long evaluated;      // FastCLARANS: draws evaluated
   long long win_len;        // FasterPAM / FastCLARANS: next window length
   unsigned bar[2];          // grid barrier of the eager kernel: count, generation
+  unsigned check_flags;     // input check: 1 asymmetric, 2 diagonal, 4 value
 };
 static_assert(sizeof(KmState) <= 512, "the workspaces reserve 512 bytes for the state record");
 

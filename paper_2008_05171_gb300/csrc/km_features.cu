@@ -1105,6 +1105,7 @@ extern "C" km_status kmedoids_run_features(const void* X, int64_t n, int32_t d, 
                                            int32_t k, int32_t* medoids_out, int32_t* labels_out,
                                            const km_options* opts, km_result* res, void* ws,
                                            size_t ws_bytes, void* stream) {
+  NvtxRange nv("kmedoids_run_features");
   return run_features(true, true, X, n, d, ldx, k, medoids_out, labels_out, opts, res, ws,
                       ws_bytes, stream);
 }
@@ -1114,6 +1115,7 @@ extern "C" km_status kmedoids_swap_features(const void* X, int64_t n, int32_t d,
                                             int32_t* labels_out, const km_options* opts,
                                             km_result* res, void* ws, size_t ws_bytes,
                                             void* stream) {
+  NvtxRange nv("kmedoids_swap_features");
   return run_features(false, true, X, n, d, ldx, k, medoids_inout, labels_out, opts, res, ws,
                       ws_bytes, stream);
 }

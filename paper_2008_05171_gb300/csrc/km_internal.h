@@ -5,8 +5,18 @@
 #include <cstddef>
 #include <cstdint>
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 namespace km {
+
+// NVTX range for the duration of a scope (phases of a call show up in
+// profilers that record NVTX; without one attached the calls do nothing).
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 struct KmState;
 
@@ -177,6 +187,10 @@ cudaError_t launch_mark_medoids(const PointArgs& a, cudaStream_t s);
 cudaError_t launch_fill_medoid_rows(const PointArgs& a, cudaStream_t s);
 cudaError_t launch_removal_to_double(int dtype, const PointArgs& a, cudaStream_t s);
 cudaError_t launch_matrix_scan(const PointArgs& a, cudaStream_t s);
+// Checks D (zero diagonal, bitwise symmetry, finite entries >= 0 for float
+// data) and ORs the findings into *flags (1, 2, 4).
+cudaError_t launch_matrix_check(int dtype, const void* D, long long ld, int n, unsigned* flags,
+                                cudaStream_t s);
 
 int device_sm_count();
 

@@ -25,6 +25,19 @@ namespace km {
 
 constexpr int kPtThreads = 256;
 
+// bitwise inequality, zero test and value test of the input check
+__device__ __forceinline__ bool memcmp_bits(float a, float b) {
+  return __float_as_uint(a) != __float_as_uint(b);
+}
+__device__ __forceinline__ bool memcmp_bits(int32_t a, int32_t b) { return a != b; }
+__device__ __forceinline__ bool memcmp_bits(uint16_t a, uint16_t b) { return a != b; }
+__device__ __forceinline__ bool is_zero(float a) { return a == 0.f; }
+__device__ __forceinline__ bool is_zero(int32_t a) { return a == 0; }
+__device__ __forceinline__ bool is_zero(uint16_t a) { return a == 0; }
+__device__ __forceinline__ bool bad_value(float a) { return !(a >= 0.f) || isinf(a); }
+__device__ __forceinline__ bool bad_value(int32_t a) { return a < 0; }
+__device__ __forceinline__ bool bad_value(uint16_t) { return false; }
+
 template <class A>
 __device__ __forceinline__ A block_sum(A v, A* scratch) {
   v = warp_sum(v);
@@ -439,6 +452,40 @@ __global__ void __launch_bounds__(kPtThreads) k_matrix_scan(const PointArgs a) {
   }
 }
 
+// Input check: 32 x 32 tiles (ti, tj) of the upper triangle, each compared
+// element by element with its mirror tile (staged in shared memory, so both
+// reads are coalesced); diagonal tiles also check d(i, i) = 0.  Float data:
+// every entry must be finite and >= 0.
+template <class E>
+__global__ void __launch_bounds__(256) k_matrix_check(const E* D, long long ld, int n,
+                                                      unsigned* flags) {
+  __shared__ E mir[32][33];
+  const int T = (n + 31) / 32;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8
+  unsigned f = 0;
+  for (long long L = blockIdx.x; L < (long long)T * T; L += gridDim.x) {
+    const int ti = (int)(L / T), tj = (int)(L % T);
+    if (tj < ti) continue;  // uniform for the block
+    __syncthreads();
+    for (int r = ty; r < 32; r += 8) {  // mirror tile: rows of tj, columns of ti
+      const int i = tj * 32 + r, j = ti * 32 + tx;
+      if (i < n && j < n) mir[r][tx] = D[(size_t)i * ld + j];
+    }
+    __syncthreads();
+    for (int r = ty; r < 32; r += 8) {
+      const int i = ti * 32 + r, j = tj * 32 + tx;
+      if (i < n && j < n) {
+        const E v = D[(size_t)i * ld + j];
+        const E w = mir[tx][r];  // d(j, i)
+        if (memcmp_bits(v, w)) f |= 1u;
+        if (i == j && !is_zero(v)) f |= 2u;
+        if (bad_value(v)) f |= 4u;
+      }
+    }
+  }
+  if (f) atomicOr(flags, f);
+}
+
 // ------------------------------------------------------------- launchers
 static inline int blocks_for(int n) { return (n + kPtThreads - 1) / kPtThreads; }
 
@@ -512,6 +559,21 @@ cudaError_t launch_removal_to_double(int dtype, const PointArgs& a, cudaStream_t
     k_removal_to_double<int32_t><<<(a.k + 255) / 256, 256, 0, s>>>(a);
   else
     k_removal_to_double<float><<<(a.k + 255) / 256, 256, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_matrix_check(int dtype, const void* D, long long ld, int n, unsigned* flags,
+                                cudaStream_t s) {
+  long long tiles = (long long)((n + 31) / 32) * ((n + 31) / 32);
+  int grid = device_sm_count() * 8;
+  if (grid < 1) grid = 1;
+  if (tiles < grid) grid = (int)tiles;
+  if (dtype == 0)
+    k_matrix_check<int32_t><<<grid, 256, 0, s>>>(static_cast<const int32_t*>(D), ld, n, flags);
+  else if (dtype == 2)
+    k_matrix_check<uint16_t><<<grid, 256, 0, s>>>(static_cast<const uint16_t*>(D), ld, n, flags);
+  else
+    k_matrix_check<float><<<grid, 256, 0, s>>>(static_cast<const float*>(D), ld, n, flags);
   return cudaGetLastError();
 }
 

@@ -50,7 +50,7 @@ class km_options(ctypes.Structure):
                 ("trace_time_ns", ctypes.POINTER(ctypes.c_int64)),
                 ("build_gains", ctypes.POINTER(ctypes.c_double)),
                 ("draws", ctypes.c_void_p), ("draws_len", ctypes.c_int64),
-                ("maxneighbor", ctypes.c_int64)]
+                ("maxneighbor", ctypes.c_int64), ("check_input", ctypes.c_int32)]
 
 
 class km_result(ctypes.Structure):
@@ -179,7 +179,7 @@ def _stream():
 
 def options(variant="fastpam1", max_iter=0, tol=0.0, fastpam2_tol=0.0,
             rows_per_tile=0, profile=False, trace=0, tune=0, draws=None,
-            maxneighbor=0):
+            maxneighbor=0, check_input=False):
     """km_options.  draws: int32 CUDA tensor of candidate draws (FastCLARANS);
     the caller keeps it alive for the call."""
     o = km_options()
@@ -188,6 +188,7 @@ def options(variant="fastpam1", max_iter=0, tol=0.0, fastpam2_tol=0.0,
         o.draws = ctypes.c_void_p(draws.data_ptr())
         o.draws_len = int(draws.numel())
     o.maxneighbor = int(maxneighbor)
+    o.check_input = 1 if check_input else 0
     o.variant = VARIANTS[variant] if isinstance(variant, str) else int(variant)
     o.max_iter = int(max_iter)
     o.tol = float(tol)

@@ -395,3 +395,40 @@ def test_apply_rescans_large_k():
     # labels come from the incrementally updated cache
     _, olab = oracle.td(Dh, ref["medoids"], return_labels=True)
     assert (out["labels"].cpu().numpy() == olab).all()
+
+
+def test_check_input_reports_broken_matrices():
+    """check_input: one extra pass over D verifies the method's assumptions
+    (zero diagonal, symmetry; finite entries >= 0 for float data) before any
+    other work; valid matrices run unchanged (int32, float32, 16-bit)."""
+    n, k = 1100, 9
+    Dh = int_instance(n, "check")
+    ref = km.run(dev(Dh), k, trace=1000)
+    ok = km.run(dev(Dh), k, trace=1000, check_input=True)
+    assert ok["medoids"].cpu().tolist() == ref["medoids"].cpu().tolist()
+    assert ok["td_i64"] == ref["td_i64"]
+    A = Dh.copy()
+    A[700, 3] += 1                                   # d(700, 3) != d(3, 700)
+    with pytest.raises(km.KmError) as e:
+        km.run(dev(A), k, check_input=True)
+    assert e.value.status == 1 and "symmetric" in str(e.value)
+    B = Dh.copy()
+    B[1099, 1099] = 5                                # last diagonal entry, ragged tile
+    with pytest.raises(km.KmError) as e:
+        km.swap(dev(B), rand_medoids(n, k, 1), check_input=True)
+    assert e.value.status == 1 and "diagonal" in str(e.value)
+    F = wl.euclidean_f32(wl.gmm_points(700, 4, 5, seed="check-f"))
+    assert km.run(dev(F), 5, check_input=True)["converged"]
+    G = F.copy()
+    G[10, 20] = G[20, 10] = np.float32(np.nan)
+    with pytest.raises(km.KmError) as e:
+        km.run(dev(G), 5, check_input=True)
+    assert e.value.status == 6
+    U = np.zeros((n, 1104), np.uint16)
+    U[:, :n] = Dh[:, :n]
+    Ud = torch.from_numpy(U.view(np.int16)).cuda()
+    assert km.run(Ud, k, n=n, check_input=True)["td_i64"] == ref["td_i64"]
+    U[5, 6] += 1
+    with pytest.raises(km.KmError) as e:
+        km.run(torch.from_numpy(U.view(np.int16)).cuda(), k, n=n, check_input=True)
+    assert e.value.status == 1
