@@ -309,10 +309,13 @@ km_status kmedoids_gram_bf16(const void *X, int64_t n, int32_t d, int64_t ldx,
 
 /* ---- On-the-fly distance form (no n x n matrix).  Points are n rows of d
  * bf16 features (DEVICE, row stride ldx elements, ldx % 8 == 0, 16-byte
- * aligned, d a multiple of 16 up to 256); d(o,c) is the Euclidean distance.
+ * aligned, d a multiple of 16 up to 240); d(o,c) is the Euclidean distance.
  * Every BUILD step and SWAP pass recomputes the distances it needs from a
  * tensor-core Gram product (tcgen05, BF16 inputs, FP32 accumulation):
- * d^2 = |x_o|^2 + |x_c|^2 - 2 x_o.x_c.  The per-point cache (nearest, d_n,
+ * d^2 = |x_o|^2 + |x_c|^2 - 2 x_o.x_c.  The pair test against each point's
+ * threshold is folded into the product: the operands carry 16 more
+ * columns holding |x_c|^2 / 2 and the point's threshold as exact sums of
+ * three bf16 pieces, so the sign of one MMA output decides a pair.  The per-point cache (nearest, d_n,
  * d_s) and the TD are computed exactly from FP32 differences sum (x - y)^2,
  * so the Gram form's rounding (relative error ~1e-5 on d^2 for well
  * separated points) only affects which candidates see a hit and the Delta

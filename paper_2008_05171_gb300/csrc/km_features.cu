@@ -13,11 +13,14 @@
 //   warp 1      allocates tensor memory and issues the tcgen05 MMAs:
 //               G = X_c X_o^T, BF16 inputs, FP32 accumulation, into one of
 //               four 128-column TMEM accumulators;
-//   warps 2-17  epilogue, four warpgroups of 32 columns each: read G from
-//               TMEM and test every pair against its point's threshold,
+//   warps 2-17  epilogue, four warpgroups of 32 columns each: read the
+//               MMA output from TMEM and test every pair against its
+//               point's threshold,
 //               d(o,c)^2 < d^2(o)  <=>  g - |x_c|^2/2 > (|x_o|^2 - d^2(o))/2,
-//               as the sign of (thr + |x_c|^2/2) - g funnel-shifted into a
-//               16-bit lane mask (two adds and one shift per pair);
+//               folded into the product itself (the operands carry
+//               |x_c|^2/2 and the threshold in 16 extra columns, see
+//               FeatArgs), so the sign bit of each output is the test,
+//               funnel-shifted into a 16-bit lane mask (one shift a pair);
 //               the pairs that pass (rare) are walked lane by lane (or, in
 //               a group where some lane has many, with predication) and
 //               take d = sqrt(|x_c|^2 + |x_o|^2 - 2 g):
@@ -37,6 +40,8 @@
 #include <cstring>
 #include <vector>
 
+#include <cuda_bf16.h>
+
 #include "../../include/kmedoids.h"
 #include "km_device.cuh"
 #include "km_internal.h"
@@ -50,7 +55,17 @@ constexpr int kFeatMaxK = 224;       // shared accumulators: 128 x k x 4 B
 constexpr int kFeatMaxD = 256;
 
 struct FeatArgs {
-  const uint16_t* Xp;   // rearranged features (core-matrix layout)
+  // Operands of the pass, n_pad rows of dk = d + 16 bf16 columns each in
+  // the tensor cores' core-matrix layout:
+  //   A (candidate role): [-x_c, h1, h2, h3, 1, 1, 1, 0...]
+  //   B (point role):     [ x_o, 1, 1, 1, t1, t2, t3, 0...]
+  // with h1 + h2 + h3 = |x_c|^2 / 2 and t1 + t2 + t3 = thr[o] exactly (three
+  // bf16 pieces of an FP32 value), so the product is
+  //   A B^T = -x_c.x_o + |x_c|^2/2 + thr[o],
+  // negative exactly when the pair passes the threshold test below.
+  const uint16_t* XpA;
+  uint16_t* XpB;        // its t columns follow every change of thr
+  int dk;
   const uint16_t* X;    // features, row-major (ldx)
   long long ldx;
   int n, d, k, n_pad;
@@ -127,6 +142,43 @@ __host__ __device__ inline FeatLayout feat_layout(int d, int k) {
 
 __device__ __forceinline__ float bf(uint16_t v) { return __uint_as_float((uint32_t)v << 16); }
 
+// Three bf16 pieces whose sum is the FP32 value v exactly (each piece takes
+// the next eight significant bits; a non-finite v goes whole into the
+// first piece).
+__device__ __forceinline__ void split3_bf16(float v, uint16_t* p) {
+  if (!(v - v == 0.f)) {  // inf or NaN
+    p[0] = (uint16_t)(__float_as_uint(v) >> 16);
+    p[1] = p[2] = 0;
+    return;
+  }
+  float r = v;
+#pragma unroll
+  for (int q = 0; q < 3; ++q) {
+    const __nv_bfloat16 h = __float2bfloat16_rn(r);
+    p[q] = __bfloat16_as_ushort(h);
+    r = r - __bfloat162float(h);  // exact: r and h agree in their leading bits
+  }
+}
+
+// Offset (bf16 elements) of the 8-column chunk kc of row o in an operand
+// buffer of dk columns (core-matrix layout: [o/8][kc][o%8][8]).
+__device__ __forceinline__ size_t chunk_off(int o, int kc, int dk) {
+  return (((size_t)(o >> 3) * (size_t)(dk >> 3) + (size_t)kc) * 8 + (size_t)(o & 7)) * 8;
+}
+
+// The B operand's extra chunk of point o: [1, 1, 1, t1, t2, t3, 0, 0].
+__device__ __forceinline__ void write_thr_cols(const FeatArgs& a, int o, float thr) {
+  uint16_t t[3];
+  split3_bf16(thr, t);
+  const uint16_t one = 0x3F80u;  // bf16 1.0
+  uint4 c;
+  c.x = (uint32_t)one | ((uint32_t)one << 16);
+  c.y = (uint32_t)one | ((uint32_t)t[0] << 16);
+  c.z = (uint32_t)t[1] | ((uint32_t)t[2] << 16);
+  c.w = 0u;
+  *reinterpret_cast<uint4*>(a.XpB + chunk_off(o, a.d >> 3, a.dk)) = c;
+}
+
 // v[j] for a lane-dependent j in [0, 16): a select tree over registers.
 __device__ __forceinline__ float sel16(const float* v, int j) {
   const bool b0 = j & 1, b1 = j & 2, b2 = j & 4, b3 = j & 8;
@@ -152,7 +204,7 @@ __global__ void __launch_bounds__(kFeatThreads, 1) k_feat_pass(const FeatArgs a)
   extern __shared__ __align__(1024) unsigned char smem[];
   KmState* st = a.st;
   if (st->done || st->error) return;
-  const int n = a.n, d = a.d, k = a.k;
+  const int n = a.n, d = a.dk, k = a.k;  // d: the operands' K dimension
   const FeatLayout L = feat_layout(d, k);
   const int bst = L.bst;
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + L.bars);
@@ -249,7 +301,7 @@ __global__ void __launch_bounds__(kFeatThreads, 1) k_feat_pass(const FeatArgs a)
           break;
         }
         mbar_arrive_expect_tx(a_full, tile_bytes);
-        bulk_g2s(sA, a.Xp + (size_t)t * kTileM * d, tile_bytes, a_full);
+        bulk_g2s(sA, a.XpA + (size_t)t * kTileM * d, tile_bytes, a_full);
         for (int b = 0; b < nblocks; ++b, ++gb) {
           const int s = (int)(gb % bst);
           const uint32_t ph = (uint32_t)((gb / bst) & 1);
@@ -260,7 +312,7 @@ __global__ void __launch_bounds__(kFeatThreads, 1) k_feat_pass(const FeatArgs a)
           mbar_arrive_expect_tx(&b_full[s], tile_bytes);
           bused |= 1u << s;
           bph = (bph & ~(1u << s)) | (ph << s);
-          bulk_g2s(stages + (size_t)s * L.stage_bytes, a.Xp + (size_t)b * kTileN * d, tile_bytes,
+          bulk_g2s(stages + (size_t)s * L.stage_bytes, a.XpB + (size_t)b * kTileN * d, tile_bytes,
                    &b_full[s]);
           const int ms = (int)(gb % kFeatMetaStages);
           const uint32_t mp = (uint32_t)((gb / kFeatMetaStages) & 1);
@@ -353,7 +405,8 @@ __global__ void __launch_bounds__(kFeatThreads, 1) k_feat_pass(const FeatArgs a)
       const bool cvalid = (c < n) && !a.is_med[c];
       const float nc = (c < n) ? a.norms[c] : 0.f;
       // d(o,c)^2 < d^2(o)  <=>  g - |x_c|^2/2 > (|x_o|^2 - d^2(o))/2 = thr[o]
-      const float hc = cvalid ? 0.5f * nc : __int_as_float(0x7f800000);
+      // <=>  v = |x_c|^2/2 + thr[o] - g < 0, and v is what the MMA produced
+      const float hc = 0.5f * nc;
       float ks_ = 0.f, kc_ = 0.f;  // Kahan pair: BUILD gain or SWAP shared term
       for (int b = 0; b < nblocks; ++b, ++gb) {
         const int buf = (int)(gb % kFeatAccBufs);
@@ -377,8 +430,10 @@ __global__ void __launch_bounds__(kFeatThreads, 1) k_feat_pass(const FeatArgs a)
         const float* m_ds = reinterpret_cast<const float*>(meta + 1536);
         const int* m_near = reinterpret_cast<const int*>(meta + 2048);
         // one pair (o = column col, candidate c = this thread's row) that
-        // passed the threshold test; exact case split on d = sqrt(d^2)
-        auto hit = [&](int col, float g) {
+        // passed the threshold test; g = x_c.x_o recovered from v, then the
+        // exact case split on d = sqrt(d^2)
+        auto hit = [&](int col, float v) {
+          const float g = (hc + m_thr[col]) - v;
           const float d2 = fmaf(-2.f, g, nc + m_no[col]);
           const float dd = sqrtf(fmaxf(d2, 0.f));
           const float dn_ = m_dn[col];
@@ -393,28 +448,25 @@ __global__ void __launch_bounds__(kFeatThreads, 1) k_feat_pass(const FeatArgs a)
           }
         };
         if (MODE == kModeBuild && a.build_first) {
+          // every pair (thr = 0 before the first BUILD step)
           const int colg = b * kTileN + col0;
 #pragma unroll
           for (int j = 0; j < 32; ++j) {
-            const float d2 = fmaf(-2.f, v[j], nc + m_no[col0 + j]);
+            const float g = (hc + m_thr[col0 + j]) - v[j];
+            const float d2 = fmaf(-2.f, g, nc + m_no[col0 + j]);
             kahan_addf(ks_, kc_, (colg + j < n) ? sqrtf(fmaxf(d2, 0.f)) : 0.f);
           }
         } else {
 #pragma unroll
           for (int g16 = 0; g16 < 2; ++g16) {
-            // fast path: bit j of the lane mask is the sign of
-            // (thr[o] + |x_c|^2/2) - g for column j (set: a hit), shifted in
-            // from column 15 down to 0 with one funnel shift per pair
+            // fast path: bit j of the lane mask is the sign of v for column
+            // j (set: a hit), shifted in from column 15 down to 0 with one
+            // funnel shift per pair; rows that are not candidates see none
             unsigned mask = 0;
 #pragma unroll
-            for (int q = 12; q >= 0; q -= 4) {
-              const float4 t4 = *reinterpret_cast<const float4*>(m_thr + col0 + g16 * 16 + q);
-              const float* vq = v + g16 * 16 + q;
-              mask = __funnelshift_l(__float_as_uint((t4.w + hc) - vq[3]), mask, 1);
-              mask = __funnelshift_l(__float_as_uint((t4.z + hc) - vq[2]), mask, 1);
-              mask = __funnelshift_l(__float_as_uint((t4.y + hc) - vq[1]), mask, 1);
-              mask = __funnelshift_l(__float_as_uint((t4.x + hc) - vq[0]), mask, 1);
-            }
+            for (int j = 15; j >= 0; --j)
+              mask = __funnelshift_l(__float_as_uint(v[g16 * 16 + j]), mask, 1);
+            if (!cvalid) mask = 0;
             const unsigned most = __reduce_max_sync(0xffffffffu, (unsigned)__popc(mask));
             if (most == 0) continue;
             const int cb = col0 + g16 * 16;
@@ -607,7 +659,10 @@ __global__ void __launch_bounds__(256) k_feat_cache(const FeatArgs a) {
     a.ds[o] = e2;
     a.dn2[o] = q1;
     a.ds2[o] = (n2 < 0) ? Tr<float>::high() : q2;
-    a.thr[o] = (n2 < 0) ? -Tr<float>::high() : 0.5f * (a.norms[o] - q2);
+    // k = 1 has no second medoid; its SWAP is a dense pass (every pair), for
+    // which any finite threshold lets the Gram entries be recovered
+    a.thr[o] = (n2 < 0) ? 0.f : 0.5f * (a.norms[o] - q2);
+    write_thr_cols(a, o, a.thr[o]);
     if (n2 >= 0) atomicAdd(&sacc[n1], (double)e2 - (double)e1);
     tdl = e1;
   } else if (o < a.n_pad) {
@@ -618,6 +673,7 @@ __global__ void __launch_bounds__(256) k_feat_cache(const FeatArgs a) {
     a.dn2[o] = Tr<float>::low();
     a.ds2[o] = Tr<float>::low();
     a.thr[o] = Tr<float>::high();
+    write_thr_cols(a, o, Tr<float>::high());
   }
   const double bs = fblock_sum(tdl, scratch);
   if (threadIdx.x == 0) atomicAdd(&a.td2[rb], bs);
@@ -682,6 +738,7 @@ __global__ void __launch_bounds__(256) k_feat_apply(const FeatArgs a) {
     a.dn2[o] = q1;
     a.ds2[o] = q2;
     a.thr[o] = 0.5f * (a.norms[o] - q2);
+    write_thr_cols(a, o, a.thr[o]);
     atomicAdd(&sacc[n1], (double)e2 - (double)e1);
     tdl = e1;
   }
@@ -735,11 +792,13 @@ __global__ void __launch_bounds__(256) k_feat_build_commit(const FeatArgs a) {
       a.dn2[o] = cur;
       a.dn[o] = sqrtf(cur);
       a.thr[o] = 0.5f * (a.norms[o] - cur);
+      write_thr_cols(a, o, a.thr[o]);
       local = sqrtf(cur);
     } else if (o < a.n_pad) {
       a.dn2[o] = Tr<float>::low();
       a.dn[o] = 0.f;
       a.thr[o] = Tr<float>::high();
+      write_thr_cols(a, o, Tr<float>::high());
     }
   }
   const double bs = fblock_sum(local, scratch);
@@ -751,6 +810,47 @@ __global__ void __launch_bounds__(256) k_feat_build_commit(const FeatArgs a) {
     if (a.gains) a.gains[step] = st->build_gain_d;
     st->td_book_d = a.build_first ? st->build_gain_d : st->td_book_d + st->build_gain_d;
     st->build_step = step + 1;
+  }
+}
+
+// Both operand buffers of the pass from the features (see FeatArgs); thr
+// starts at 0 for points (finite, so the first BUILD step can recover every
+// Gram entry) and +inf on padding rows.
+__global__ void k_feat_prearrange(const FeatArgs a) {
+  const int dc = a.d >> 3, kcs = a.dk >> 3;
+  const long long chunks = (long long)a.n_pad * kcs;
+  uint16_t* XpA = const_cast<uint16_t*>(a.XpA);
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < chunks;
+       q += (long long)gridDim.x * blockDim.x) {
+    const long long g = q / ((long long)kcs * 8);
+    const long long rem = q - g * kcs * 8;
+    const int kc = (int)(rem / 8), rr = (int)(rem % 8);
+    const int row = (int)(g * 8 + rr);
+    uint4 va = make_uint4(0, 0, 0, 0), vb = make_uint4(0, 0, 0, 0);
+    if (kc < dc) {
+      if (row < a.n) {
+        vb = *reinterpret_cast<const uint4*>(a.X + (size_t)row * a.ldx + kc * 8);
+        va = make_uint4(vb.x ^ 0x80008000u, vb.y ^ 0x80008000u, vb.z ^ 0x80008000u,
+                        vb.w ^ 0x80008000u);
+      }
+    } else if (kc == dc) {
+      const float thr0 = (row < a.n) ? 0.f : Tr<float>::high();
+      a.thr[row] = thr0;
+      uint16_t t[3];
+      split3_bf16(thr0, t);
+      const uint16_t one = 0x3F80u;
+      vb = make_uint4((uint32_t)one | ((uint32_t)one << 16), (uint32_t)one | ((uint32_t)t[0] << 16),
+                      (uint32_t)t[1] | ((uint32_t)t[2] << 16), 0u);
+      if (row < a.n) {
+        uint16_t h[3];
+        split3_bf16(0.5f * a.norms[row], h);
+        va = make_uint4((uint32_t)h[0] | ((uint32_t)h[1] << 16),
+                        (uint32_t)h[2] | ((uint32_t)one << 16),
+                        (uint32_t)one | ((uint32_t)one << 16), 0u);
+      }
+    }
+    reinterpret_cast<uint4*>(XpA)[q] = va;
+    reinterpret_cast<uint4*>(a.XpB)[q] = vb;
   }
 }
 
@@ -768,12 +868,12 @@ namespace {
 
 struct FeatWs {
   size_t st, med, is_med, near, sec, dn, ds, dn2, ds2, thr, norms, removal, td2, partials, trace,
-      gains, xp, total;
+      gains, xpa, xpb, total;
   int n_pad, k_pad, cap;
 };
 
 bool feat_ws(int64_t n, int d, int k, const km_options* o, FeatWs* L) {
-  if (n <= 0 || k <= 0 || k > n || d <= 0 || d > kFeatMaxD || d % 16 || n > (1 << 28))
+  if (n <= 0 || k <= 0 || k > n || d <= 0 || d + 16 > kFeatMaxD || d % 16 || n > (1 << 28))
     return false;
   auto al = [](size_t x) { return (x + 255) / 256 * 256; };
   const int n_pad = (int)((n + kTileM - 1) / kTileM * kTileM);
@@ -801,7 +901,8 @@ bool feat_ws(int64_t n, int d, int k, const km_options* o, FeatWs* L) {
   L->partials = take(16 * (size_t)kMaxGrid);
   L->trace = take(sizeof(TraceRec) * (size_t)(cap > 0 ? cap : 1));
   L->gains = take(8 * (size_t)k);
-  L->xp = take((size_t)n_pad * d * 2);
+  L->xpa = take((size_t)n_pad * (d + 16) * 2);
+  L->xpb = take((size_t)n_pad * (d + 16) * 2);
   L->total = off;
   L->n_pad = n_pad;
   L->k_pad = k_pad;
@@ -858,7 +959,7 @@ km_status f_pass(FCtx& c, int mode, int first, cudaEvent_t ev0 = nullptr,
   FeatArgs a = c.a;
   a.mode = mode;
   a.build_first = first;
-  const FeatLayout L = feat_layout(a.d, a.k);
+  const FeatLayout L = feat_layout(a.dk, a.k);
   if (L.total > 227 * 1024) return ffail(KM_E_UNSUPPORTED, "feature pass needs %zu B of shared memory", L.total);
   int grid = c.sms;
   if (grid > a.n_pad / kTileM) grid = a.n_pad / kTileM;
@@ -905,7 +1006,8 @@ km_status run_features(bool do_build, bool do_swap, const void* X, int64_t n, in
   if (c.opt.variant != KM_FASTPAM1)
     return ffail(KM_E_UNSUPPORTED, "the feature form implements FastPAM1 SWAP only");
   if (!feat_ws(n, d, k, &c.opt, &c.L))
-    return ffail(KM_E_INVALID, "need 1 <= k <= n <= 2^28 and d a multiple of 16 up to 256");
+    return ffail(KM_E_INVALID, "need 1 <= k <= n <= 2^28 and d a multiple of 16 up to %d",
+                 kFeatMaxD - 16);
   if (k > kFeatMaxK) return ffail(KM_E_UNSUPPORTED, "feature form supports k <= %d", kFeatMaxK);
   if (ldx < d || ldx % 8) return ffail(KM_E_INVALID, "ldx must be >= d and a multiple of 8");
   if (reinterpret_cast<uintptr_t>(X) % 16 || reinterpret_cast<uintptr_t>(ws) % 256)
@@ -926,7 +1028,9 @@ km_status run_features(bool do_build, bool do_swap, const void* X, int64_t n, in
   a.k = k;
   a.n_pad = c.L.n_pad;
   a.k_pad = c.L.k_pad;
-  a.Xp = reinterpret_cast<const uint16_t*>(c.ws + c.L.xp);
+  a.dk = d + 16;
+  a.XpA = reinterpret_cast<const uint16_t*>(c.ws + c.L.xpa);
+  a.XpB = reinterpret_cast<uint16_t*>(c.ws + c.L.xpb);
   a.norms = reinterpret_cast<const float*>(c.ws + c.L.norms);
   a.near = reinterpret_cast<int32_t*>(c.ws + c.L.near);
   a.sec = reinterpret_cast<int32_t*>(c.ws + c.L.sec);
@@ -957,8 +1061,14 @@ km_status run_features(bool do_build, bool do_swap, const void* X, int64_t n, in
   }
   km_status r = f_reset(c);
   if (r != KM_OK) return r;
-  FK(launch_prearrange(X, ldx, (int)n, d, c.L.n_pad, c.ws + c.L.xp, c.s));
   FK(launch_row_norms(X, ldx, (int)n, d, c.L.n_pad, const_cast<float*>(a.norms), c.s));
+  {
+    long long chunks = (long long)c.L.n_pad * (a.dk / 8);
+    int grid = (int)((chunks + 255) / 256);
+    if (grid > c.sms * 16) grid = c.sms * 16;
+    k_feat_prearrange<<<grid, 256, 0, c.s>>>(a);
+    FK(cudaGetLastError());
+  }
   c.launches += 2;
   if (prof) FK(cudaEventRecord(e0, c.s));
   KmState h;
@@ -997,7 +1107,49 @@ km_status run_features(bool do_build, bool do_swap, const void* X, int64_t n, in
   if (r != KM_OK) return r;
   r = f_cache(c);
   if (r != KM_OK) return r;
-  if (do_swap && k < n) {
+  if (do_swap && k == 1 && n > 1) {
+    // k = 1: the best single swap is the 1-medoid (Eq. (3)); a dense pass
+    // sums every non-medoid's distances, compared with the current TD
+    KmState h0;
+    r = f_read(c, &h0);
+    if (r != KM_OK) return r;
+    r = f_pass(c, kModeBuild, 1);
+    if (r != KM_OK) return r;
+    KmState h1;
+    r = f_read(c, &h1);
+    if (r != KM_OK) return r;
+    int iters = 1, swaps = 0;
+    if (h1.build_cand >= 0 && c.opt.max_iter >= 1 &&
+        h1.build_gain_d - h0.td_book_d < -c.opt.tol) {
+      const int cb = h1.build_cand;
+      FK(cudaMemcpyAsync(a.med, &cb, 4, cudaMemcpyHostToDevice, c.s));
+      if (c.L.cap > 0) {
+        TraceRec t;
+        memset(&t, 0, sizeof(t));
+        t.d = h1.build_gain_d - h0.td_book_d;
+        t.slot = 0;
+        t.cand = cb;
+        FK(cudaMemcpyAsync(a.trace, &t, sizeof(t), cudaMemcpyHostToDevice, c.s));
+      }
+      swaps = 1;
+      iters = (c.opt.max_iter >= 2) ? 2 : 1;
+    }
+    r = f_reset(c);
+    if (r != KM_OK) return r;
+    r = f_cache(c);
+    if (r != KM_OK) return r;
+    h = KmState();
+    r = f_read(c, &h);
+    if (r != KM_OK) return r;
+    // record the outcome in the state read back below
+    KmState hs = h;
+    hs.iter = iters;
+    hs.swaps = swaps;
+    hs.ntrace = swaps;
+    hs.done = (swaps == 0 || c.opt.max_iter >= 2) ? 1 : 0;
+    FK(cudaMemcpyAsync(c.st(), &hs, sizeof(hs), cudaMemcpyHostToDevice, c.s));
+    if (!hs.done) conv = KM_E_NOT_CONVERGED;
+  } else if (do_swap && k < n) {
     int launched = 0, batch = 1;
     const size_t sm = 8 * (size_t)k;
     FK(cudaFuncSetAttribute(k_feat_apply, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
