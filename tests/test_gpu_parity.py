@@ -432,3 +432,31 @@ def test_check_input_reports_broken_matrices():
     with pytest.raises(km.KmError) as e:
         km.run(torch.from_numpy(U.view(np.int16)).cuda(), k, n=n, check_input=True)
     assert e.value.status == 1
+
+
+@pytest.mark.parametrize("variant", ["fasterpam", "fastpam2"])
+def test_tiny_and_nearly_full_k_all_variants(variant):
+    """Every k from 1 to n on tiny matrices (fewer points than the eager
+    kernel has CTAs), k = n - 1 on a larger one, int32 and 16-bit: the
+    variant's result equals the oracle's."""
+    for n in (2, 3, 5, 9):
+        Dh = int_instance(n, ("tiny-v", n))
+        for k in range(1, n + 1):
+            start = rand_medoids(n, k, n * 10 + k)
+            out = km.swap(dev(Dh), start, variant=variant, trace=64)
+            ref = oracle.swap(Dh, start, variant=variant)
+            assert out["medoids"].cpu().tolist() == ref["medoids"].tolist(), (n, k)
+            assert out["td_i64"] == int(ref["td"])
+    n = 700
+    Dh = int_instance(n, "nearly-full")
+    start = rand_medoids(n, n - 1, 3)
+    out = km.swap(dev(Dh), start, variant=variant)
+    ref = oracle.swap(Dh, start, variant=variant)
+    assert out["medoids"].cpu().tolist() == ref["medoids"].tolist()
+    U = np.zeros((n, 704), np.uint16)
+    U[:, :n] = Dh[:, :n]
+    start = rand_medoids(n, 9, 4)
+    out = km.swap(torch.from_numpy(U.view(np.int16)).cuda(), start, n=n, variant=variant)
+    ref = oracle.swap(np.ascontiguousarray(Dh[:, :n]), start, variant=variant)
+    assert out["medoids"].cpu().tolist() == ref["medoids"].tolist()
+    assert out["td_i64"] == int(ref["td"])
