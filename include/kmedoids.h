@@ -12,7 +12,11 @@
  *   - the FastPAM1 SWAP evaluation (Alg. 3, Eq. (7)): Delta TD of every
  *     (medoid slot i, non-medoid candidate c) in O(n) per candidate;
  *   - the best swap, its application and the cache update (Alg. 3);
- *   - FastPAM2 (Sec. 3.2) and the eager FasterPAM (Alg. 4).
+ *   - FastPAM2 (Sec. 3.2), the eager FasterPAM (Alg. 4) and FastCLARANS
+ *     (Sec. 3.4);
+ *   - the distance-weighted and LAB initialisations (Sec. 3.3);
+ *   - on-the-fly distances from bf16 features on the tensor cores, many
+ *     instances in one persistent launch, and CLARA (Sec. 2.1, 3.4).
  *
  * Data conventions (all entry points):
  *   D       dissimilarity matrix, n rows of ld elements, row-major, DEVICE

@@ -1,9 +1,11 @@
-// km_api.cu -- the C ABI of libkmedoids (declared in include/kmedoids.h):
-// argument checks, workspace carving and the host-side enqueue loops of
-// BUILD (Alg. 1) and SWAP (Alg. 3 FastPAM1, Sec. 3.2 FastPAM2, Alg. 4
-// FasterPAM).  All arithmetic of the method runs in the kernels of
-// km_stream.cu and km_points.cu; this file only orders launches and reads
-// the device state record between batches of passes.
+// km_api.cu -- the C ABI of libkmedoids for the matrix form (declared in
+// include/kmedoids.h): argument checks, workspace carving and the host-side
+// enqueue loops of BUILD (Alg. 1) and SWAP (Alg. 3 FastPAM1, Sec. 3.2
+// FastPAM2, Alg. 4 FasterPAM, Sec. 3.4 FastCLARANS), plus the
+// initialisations of Sec. 3.3.  All arithmetic of the method runs in the
+// kernels of km_stream.cu, km_points.cu, km_eager.cu and km_init.cu; this
+// file only orders launches and reads the device state record between
+// batches of passes.
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>

@@ -6,16 +6,19 @@
 //   k_apply           performs the pending swap (Alg. 3 "swap roles"): the
 //                     new medoid takes the slot of the removed one; the cache
 //                     is updated incrementally (points whose nearest or
-//                     second nearest was the removed slot rescan all k
-//                     medoids), and the removal loss / TD of the next pass
-//                     are accumulated on the way.
+//                     second nearest was the removed slot are rescanned over
+//                     all k medoids by a whole warp), and the removal loss /
+//                     TD of the next pass are accumulated on the way.
 //   k_build_commit    adds the chosen BUILD medoid and updates d_n (Alg. 1).
 //   k_fp2_try         FastPAM2: exact Delta of one queued per-slot swap
 //                     against the current cache, by Eq. (5).
+//   k_matrix_scan     largest entry (fixed-point scale) and invalid values.
+//   k_matrix_check    optional input check: zero diagonal, symmetry.
 //
 // One thread per point; d(x_o, x_m) is read as D[m*ld + o] so a warp reads
-// 32 consecutive elements of a medoid row.  Grid-wide results use a
-// last-block-done ticket in the device state.
+// 32 consecutive elements of a medoid row.  The template parameter is the
+// stored element type (float, int32, or uint16 widened to int32).
+// Grid-wide results use a last-block-done ticket in the device state.
 #include <type_traits>
 
 #include "km_device.cuh"
