@@ -1082,6 +1082,9 @@ static km_status batched_impl(bool start_given, const float* arena, const km_ins
   km_options def;
   km_default_options(&def);
   const km_options o = opts ? *opts : def;
+  if (o.variant != KM_FASTPAM1 && o.variant != KM_FASTERPAM)
+    return bfail(KM_E_UNSUPPORTED, "the batched form runs FastPAM1 or FasterPAM (variant %d)",
+                 o.variant);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   unsigned char* w = static_cast<unsigned char*>(ws);
   unsigned* queue = reinterpret_cast<unsigned*>(w);
@@ -1101,9 +1104,6 @@ static km_status batched_impl(bool start_given, const float* arena, const km_ins
   a.max_iter = o.max_iter > 0 ? o.max_iter : 10000;
   a.tol = o.tol;
   a.start_given = start_given ? 1 : 0;
-  if (o.variant != KM_FASTPAM1 && o.variant != KM_FASTERPAM)
-    return bfail(KM_E_UNSUPPORTED, "the batched form runs FastPAM1 or FasterPAM (variant %d)",
-                 o.variant);
   a.eager = (o.variant == KM_FASTERPAM) ? 1 : 0;
   const int sms = device_sm_count();
   // tune: 0 automatic (16 warps per CTA), 1 = 8 warps, 2 = 16 warps

@@ -83,3 +83,32 @@ def test_invalid_arguments_return_status(lib):
 def test_version(lib):
     import paper_2008_05171_gb300.kmedoids as km
     assert "sm_103a" in km.version()
+
+
+def test_invalid_arguments_of_the_newer_entry_points(lib):
+    """16-bit stride rule, the initialisations' and the batched form's host
+    checks: each returns its status before any device work."""
+    import paper_2008_05171_gb300.kmedoids as km
+    P = ctypes.c_void_p
+    buf = (ctypes.c_char * 4096)()
+    fake = ctypes.addressof(buf) + (256 - ctypes.addressof(buf) % 256) % 256
+    o = km.options()
+    res = km.km_result()
+    # KM_U16 needs ld % 8 == 0 (16-byte rows)
+    st = lib.kmedoids_run(P(fake), km.KM_U16, 100, 100, 10, P(fake), None, ctypes.byref(o),
+                          ctypes.byref(res), P(fake), 1 << 30, None)
+    assert st == 1 and b"multiple of 8" in lib.kmedoids_last_error()
+    # distance-weighted initialisation: u NULL
+    assert lib.kmedoids_init_weighted(P(fake), 1, 100, 100, 5, None, P(fake), P(fake),
+                                      1 << 30, None) == 1
+    # LAB: subsample size out of range, NULL ranks
+    assert lib.kmedoids_init_lab(P(fake), 1, 100, 100, 5, 0, P(fake), P(fake), None,
+                                 P(fake), 1 << 30, None) == 1
+    assert lib.kmedoids_init_lab(P(fake), 1, 100, 100, 5, 5000, P(fake), P(fake), None,
+                                 P(fake), 1 << 30, None) == 7
+    assert lib.kmedoids_init_lab(P(fake), 1, 100, 100, 5, 8, None, P(fake), None,
+                                 P(fake), 1 << 30, None) == 1
+    # batched form: only FastPAM1 and FasterPAM
+    bad = km.options(variant="fastpam2")
+    assert lib.kmedoids_run_batched(P(fake), P(fake), 1, P(fake), P(fake), ctypes.byref(bad),
+                                    P(fake), 1 << 20, None) == 7
