@@ -126,7 +126,11 @@ typedef struct km_options {
                                fastest for the rest of the process (costs
                                three passes per entry once; results do not
                                depend on the geometry);
-                             1..16 = a fixed table entry;
+                             1..16 = a fixed table entry (for FasterPAM
+                               and FastCLARANS: run the windowed streaming
+                               kernel of that geometry, one launch per
+                               window, instead of the persistent eager
+                               kernel);
                              KM_E_UNSUPPORTED if it does not fit */
   /* HOST arrays (may be NULL) receiving every applied swap in order. */
   double *trace_delta;

@@ -489,9 +489,10 @@ km_status do_swap(Ctx& c, Timer& tm, std::vector<std::pair<int, int>>& ev, KmSta
     sa.draws_len = c.opt.draws_len;
     sa.maxneighbor = c.opt.maxneighbor;
   }
-  if (flavour == kFasterPAM || flavour == kCLARANS) {
+  if ((flavour == kFasterPAM || flavour == kCLARANS) && c.opt.tune <= 0) {
     // the eager variants run as one persistent cooperative launch when every
-    // CTA of its grid can be resident (the usual case)
+    // CTA of its grid can be resident (the usual case); a fixed geometry
+    // (tune > 0) selects the windowed streaming kernel instead
     const int eg = eager_grid(c.dtype, c.k);
     const int rows = c.opt.rows_per_tile > 0 ? c.opt.rows_per_tile : 8;
     const long long cap = (long long)kMaxGrid * kMaxRows / 2;

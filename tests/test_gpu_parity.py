@@ -460,3 +460,31 @@ def test_tiny_and_nearly_full_k_all_variants(variant):
     ref = oracle.swap(np.ascontiguousarray(Dh[:, :n]), start, variant=variant)
     assert out["medoids"].cpu().tolist() == ref["medoids"].tolist()
     assert out["td_i64"] == int(ref["td"])
+
+
+@pytest.mark.parametrize("variant", ["fasterpam", "fastclarans"])
+def test_windowed_streaming_path_for_the_eager_variants(variant):
+    """A fixed geometry runs FasterPAM / FastCLARANS on the windowed
+    streaming kernel (one launch per window, adaptive window length) instead
+    of the persistent eager kernel: same decisions, swaps and counts as the
+    oracle and as the eager kernel."""
+    n, k = 1900, 24
+    Dh = int_instance(n, ("windowed", variant))
+    start = rand_medoids(n, k, 21)
+    kw = {}
+    if variant == "fastclarans":
+        draws = np.random.default_rng(5).integers(0, n, size=20000).astype(np.int32)
+        kw = dict(draws=torch.from_numpy(draws).cuda(), maxneighbor=90)
+    a = km.swap(dev(Dh), start, variant=variant, tune=3, trace=100000, **kw)
+    b = km.swap(dev(Dh), start, variant=variant, trace=100000, **kw)
+    assert a["swap_geometry"] == 3 and b["swap_geometry"] == 0
+    for key in ("swaps", "td_i64", "visited", "iterations", "evaluated"):
+        assert a[key] == b[key], key
+    assert a["medoids"].cpu().tolist() == b["medoids"].cpu().tolist()
+    if variant == "fasterpam":
+        ref = oracle.swap(Dh, start, variant=variant, trace_cap=100000)
+        assert_same_run(a, ref)
+    else:
+        ref = oracle.clarans(Dh, start, draws, 90, trace_cap=100000)
+        assert a["medoids"].cpu().tolist() == ref["medoids"].tolist()
+        assert a["iterations"] == ref["evaluated"] and a["visited"] == ref["consumed"]
