@@ -27,8 +27,9 @@ k-Medoids Clustering" (arXiv 2008.05171):
 * ``clara``         -- CLARA (Sec. 2.1, FastCLARA of Sec. 3.4) on given
                        samples; ``euclid_f32`` the FP64 -> float32 matrix.
 
-Parity unpinned: FastPAM2's additional swaps (the paper describes FastPAM2
-only in words, Sec. 3.2) beyond the invariants the tests check.
+Parity unpinned: the reading of FastPAM2's additional swaps (the paper
+describes FastPAM2 only in words, Sec. 3.2, and prints no values for it).
+The tests pin the oracle to a brute-force replay of that reading.
 """
 from __future__ import annotations
 

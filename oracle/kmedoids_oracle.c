@@ -28,9 +28,11 @@
  *
  * Parity status: every function below is pinned by tests (worked example of
  * Fig. 1, brute-force TD differences, exhaustive case tables, enumeration of
- * all medoid sets on tiny inputs, invariants) except FastPAM2's additional
- * swaps and CLARA's sample quality, which are "parity unpinned" beyond the
- * invariants (the paper describes FastPAM2 only in words, Sec. 3.2).
+ * all medoid sets on tiny inputs, invariants).  FastPAM2's additional swaps
+ * are pinned to a brute-force replay of the reading stated at the function,
+ * but the reading itself is "parity unpinned": the paper describes FastPAM2
+ * only in words (Sec. 3.2) and prints no values for it.  CLARA's sample
+ * quality is "parity unpinned" beyond the invariants.
  */
 #include <math.h>
 #include <stdint.h>

@@ -10,6 +10,9 @@ CUDA path:
                     and non-medoid c (the quantity SWAP minimises, Sec. 2).
 * ``best_swap``     lexicographic minimum of (Delta, i, c).
 * ``steepest``      repeated best swap while Delta < 0 (PAM SWAP, Alg. 2).
+* ``fastpam2``      the FastPAM2 reading of Sec. 3.2 (best swap per slot,
+                    the global best first, then the other improving slots),
+                    every Delta by full TD recomputation.
 * ``greedy_build``  each step adds argmin_c TD(M + c) (BUILD, Alg. 1; the
                     first step is the 1-medoid of Eq. (3)).
 * ``optimum``       the global optimum by enumerating all C(n, k) sets.
@@ -65,6 +68,39 @@ def steepest(D, med, max_iter=1000):
             break
         trace.append((d, i, c))
         med[i] = c
+    return med, trace
+
+
+def fastpam2(D, med, fp2_tol=0.0, max_iter=1000):
+    """FastPAM2 as read from Sec. 3.2: per slot the best (Delta_i*, c_i*)
+    over all non-medoids (lowest c on ties); apply the global best (lowest
+    slot on ties); then visit the other slots with Delta_i* < 0 in
+    ascending (Delta_i*, i), skip one whose c_i* is a medoid by now, and
+    apply it iff its Delta against the current medoids, recomputed from
+    scratch, is < -fp2_tol * |Delta*|.  Returns (medoids, trace)."""
+    med = list(med)
+    trace = []
+    for _ in range(max_iter):
+        dl = swap_deltas(D, med)
+        bc = [int(np.argmin(dl[i])) for i in range(len(med))]
+        bd = [float(dl[i, bc[i]]) for i in range(len(med))]
+        bi = int(np.argmin(bd))
+        if not bd[bi] < 0:
+            break
+        dstar = bd[bi]
+        trace.append((dstar, bi, bc[bi]))
+        med[bi] = bc[bi]
+        rest = sorted((bd[i], i) for i in range(len(med))
+                      if i != bi and bd[i] < 0)
+        for _, i in rest:
+            if bc[i] in med:
+                continue
+            trial = med.copy()
+            trial[i] = bc[i]
+            d = td(D, trial) - td(D, med)
+            if d < -fp2_tol * abs(dstar):
+                trace.append((d, i, bc[i]))
+                med[i] = bc[i]
     return med, trace
 
 

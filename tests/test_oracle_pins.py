@@ -237,6 +237,30 @@ def test_fastpam2_first_swap_is_fastpam1_swap():
             assert f2["swaps"] == 0
 
 
+@pytest.mark.parametrize("fp2_tol", [0.0, 0.25, 1.0])
+def test_fastpam2_matches_bruteforce_replay(fp2_tol):
+    """Every swap FastPAM2 applies (the best one and the additional ones,
+    their order, the skip of a candidate that became a medoid, the
+    threshold) equals a replay of the Sec. 3.2 reading in which each Delta
+    is a full TD recomputation.  Integer data: the deltas are exact."""
+    cases = 0
+    for D in bf.tiny_instances(43, 240, n_lo=6, n_hi=12):
+        n = D.shape[0]
+        g = np.random.default_rng(n * 7 + cases)
+        k = int(g.integers(2, min(6, n - 1) + 1))
+        start = [int(x) for x in g.choice(n, size=k, replace=False)]
+        got = oracle.swap(D, start, variant="fastpam2", fastpam2_tol=fp2_tol)
+        med, trace = bf.fastpam2(D, start, fp2_tol=fp2_tol)
+        assert got["converged"]
+        assert [tuple(t) for t in got["trace"]] == \
+            [(float(d), i, c) for d, i, c in trace]
+        assert list(got["medoids"]) == med
+        assert got["td"] == bf.td(D, med)
+        cases += len(trace) > got["iterations"] - 1
+    if fp2_tol < 1.0:  # an extra swap rarely beats -|Delta*| itself
+        assert cases > 0  # some iteration applied an additional swap
+
+
 # ------------------------------------------------------------------ P6 --
 
 def test_build_is_greedy_td():
