@@ -192,8 +192,13 @@ def make_input(wl_name, device):
 
 
 def evals_of(n, k, res):
-    """(candidate, point) pairs evaluated by BUILD and SWAP in one run."""
-    build = sum((n - t) * n for t in range(k))
+    """Element evaluations of BUILD and SWAP in one run: BUILD streams
+    build_rows rows of n elements (the incremental BUILD: every row once for
+    the distance sums and once for the first gains, then the rows of the
+    points whose d_n dropped; the plain pass: n - t candidate rows at step
+    t), a SWAP pass n - k candidate rows."""
+    rows = int(res.get("build_rows") or 0)
+    build = rows * n if rows > 0 else sum((n - t) * n for t in range(k))
     swap = res["iterations"] * (n - k) * n
     return build, swap
 
@@ -699,7 +704,10 @@ def run_ours(args, rank, world, local_rank):
     swap_launch_ms = r0["eval_ms"] / max(1, r0["eval_launches"])
     build_launch_ms = r0["build_eval_ms"] / max(1, r0["build_launches"])
     swap_bytes = (n - k) * n * esize
-    build_bytes = sum((n - t) * n * esize for t in range(k)) / k
+    # BUILD: rows streamed by the BUILD evaluation launches (incremental
+    # update passes, or the plain pass's candidate rows), averaged per launch
+    build_bytes = evals_of(n, k, r0)[0] * esize / max(1, r0["build_launches"])
+    incremental = int(r0["build_geometry"]) == 0
     peak, peak_kind = peaks()
     kern = {
         "swap_eval": {"launch_ms": swap_launch_ms, "bytes": swap_bytes,
@@ -710,10 +718,19 @@ def run_ours(args, rank, world, local_rank):
     dom = max(kern, key=lambda x: kern[x]["share_ms"])
     prof = load_json(os.path.join(ROOT, "profiles", "traffic.json")) or {}
     traffic = None
-    ent = prof.get(dom + ("_u16" if esize == 2 else ""))
-    if ent and ent.get("source_hash") == source_hash() and \
+    key, files = dom, ("km_stream.cu", "km_device.cuh")
+    if dom == "build_eval" and incremental:
+        key, files = "build_update", ("km_build.cu", "km_device.cuh")
+    ent = prof.get(key + ("_u16" if esize == 2 else ""))
+    if ent and ent.get("source_hash") == source_hash(files) and \
             ent.get("workload") == args.workload:
         traffic = ent.get("dram_bytes_per_launch")
+
+    def kernel_name(name):
+        t = {4: "float", 2: "uint16"}.get(esize, "?")
+        if name == "build_eval" and incremental:
+            return "k_build_update<%s> (incremental BUILD)" % t
+        return "k_stream<%s,%s>" % (t, "SWAP" if name == "swap_eval" else "BUILD")
 
     def roof(name):
         kk = kern[name]
@@ -722,8 +739,7 @@ def run_ours(args, rank, world, local_rank):
                 "unit": "GB/s", "frac": round(ach / peak, 4),
                 "peak_source": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)"
                 if peak_kind == "measured" else "fallback 6.8 TB/s",
-                "kernel": "k_stream<%s,%s>" % ({4: "float", 2: "uint16"}.get(esize, "?"),
-                                               "SWAP" if name == "swap_eval" else "BUILD"),
+                "kernel": kernel_name(name),
                 "algorithmic_bytes_per_launch": kk["bytes"],
                 "avg_launch_ms": round(kk["launch_ms"], 5)}
 
@@ -785,10 +801,28 @@ def run_ours(args, rank, world, local_rank):
                                "swap_eval": r0["eval_ms"],
                                "build_total": r0["build_ms"],
                                "swap_total": r0["swap_ms"]},
+        "build": {"mode": "incremental" if incremental else "plain pass",
+                  "rows_streamed": int(r0["build_rows"]),
+                  "plain_pass_rows": sum(n - t for t in range(k))},
         "roofline": roofline, "roofline_other": other,
         "gpu_launches": int(sum(r["kernel_launches"] for r in results)),
         "clocks": ck, "e2e": e2e, "wall_s": wall,
     }
+    if incremental and not args.no_e2e:
+        # the plain BUILD (every step streams all candidate rows) on the same
+        # matrix, timed the same way (not part of value)
+        for _ in range(2):
+            km.run(D, k, ws=ws, profile=True, tune=args.tune, build_full=True)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        rf = km.run(D, k, ws=ws, profile=True, tune=args.tune, build_full=True)
+        b.record(stream)
+        torch.cuda.synchronize()
+        line["build"]["plain_pass_run"] = {
+            "ms_per_step": a.elapsed_time(b), "build_ms": rf["build_ms"],
+            "same_medoids": rf["medoids"].cpu().tolist() == r0["medoids"].cpu().tolist(),
+            "td": rf["td"]}
     if esize == 2:
         # the same matrix as int32, timed the same way (not part of value)
         Di = D.to(torch.int32)

@@ -153,6 +153,23 @@ typedef struct km_options {
                              KM_E_INVALID) and, for KM_F32, entries finite
                              and >= 0 (else KM_E_NUMERIC); 32 x 32 tiles of
                              the upper triangle against their mirrors */
+  int32_t build_full;     /* BUILD (kmedoids_build / _run):
+                             0 (default) = incremental: the gains of all
+                               candidates are kept in exact 64-bit fixed
+                               point and, after each step, updated from the
+                               matrix rows of the points whose nearest
+                               distance the new medoid lowered only (a few
+                               passes over D in total on clustered data
+                               instead of k); for KM_F32 one extra pass
+                               first finds the fixed-point scale (and
+                               rejects negative, infinite or NaN entries
+                               with KM_E_NUMERIC);
+                             nonzero = every step streams all candidate
+                               rows (the plain pass of Alg. 1, FP32 sums
+                               with compensation for KM_F32).
+                             Both choose the same medoids up to FP32
+                             rounding of the plain pass's sums (identical
+                             for integer data). */
 } km_options;
 
 /* Results, filled on the HOST before the call returns. */
@@ -187,6 +204,8 @@ typedef struct km_result {
                               up to each applied swap, and every position
                               of the passes without one); each costs one
                               pass over the n points */
+  int64_t build_rows;      /* rows of D (n elements each) the BUILD
+                              evaluation kernels streamed */
 } km_result;
 
 /* Parameters of a matrix-form geometry table entry (1..16, as reported in

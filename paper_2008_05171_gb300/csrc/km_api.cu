@@ -56,7 +56,8 @@ int64_t rup(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
 
 struct WsLayout {
   size_t st, med, is_med, near, sec, dn, ds, bdn, removal, td2, partials, slot_partials,
-      slot_best, fp2_order, win_delta, win_slot, trace, gains, cand_gain, total;
+      slot_best, fp2_order, win_delta, win_slot, trace, gains, cand_gain, blist, blvn, blvo,
+      baux, btt, bparts, total;
   int64_t n_pad;
   int k_pad;
   int trace_cap;
@@ -92,7 +93,13 @@ bool make_ws(int64_t n, int k, const km_options* o, WsLayout* L) {
   L->win_slot = take(4 * (size_t)kMaxGrid * kMaxRows);
   L->trace = take(sizeof(TraceRec) * (size_t)(cap > 0 ? cap : 1));
   L->gains = take(8 * (size_t)k);
-  L->cand_gain = take(8 * (size_t)n_pad);
+  L->cand_gain = take(8 * (size_t)n_pad);  // also the incremental BUILD's gains
+  L->blist = take(4 * (size_t)n_pad);
+  L->blvn = take(4 * (size_t)n_pad);
+  L->blvo = take(4 * (size_t)n_pad);
+  L->baux = take(sizeof(BuildAux));
+  L->btt = take(4 * (size_t)(n_pad / kChunk));
+  L->bparts = take(16 * (size_t)(n_pad / kChunk));
   L->total = off;
   L->n_pad = n_pad;
   L->k_pad = k_pad;
@@ -115,6 +122,7 @@ struct Ctx {
   int fshift = 0;
   bool scanned = false;
   int swap_geom = 0, build_geom = 0;  // geometry table entries used
+  long long build_rows = 0;           // rows the BUILD passes streamed (-1: on the device)
   KmState* st() const { return reinterpret_cast<KmState*>(ws + L.st); }
   int esize() const { return dtype == KM_U16 ? 2 : 4; }  // bytes per matrix element
   template <class P>
@@ -354,8 +362,10 @@ km_status config_for(Ctx& c, int mode, int flavour, const StreamArgs& sa, Stream
 }
 
 // ------------------------------------------------------------------ BUILD
-km_status do_build(Ctx& c, Timer& tm, std::vector<std::pair<int, int>>& ev, km_result* res) {
-  NvtxRange nv("kmedoids BUILD");
+km_status scan_matrix(Ctx& c);
+
+// The plain BUILD: every step streams all candidate rows (Alg. 1).
+km_status do_build_full(Ctx& c, Timer& tm, std::vector<std::pair<int, int>>& ev, km_result* res) {
   KM_CUDA(cudaMemsetAsync(c.at<void>(c.L.is_med), 0, (size_t)c.L.n_pad, c.s));
   StreamArgs sa = stream_args(c);
   sa.build_first = 1;
@@ -375,6 +385,69 @@ km_status do_build(Ctx& c, Timer& tm, std::vector<std::pair<int, int>>& ev, km_r
     KM_LAUNCH(c, launch_build_commit(c.dtype, pa, c.s));
   }
   if (res) res->build_launches = c.k;
+  c.build_rows = 0;
+  for (int t = 0; t < c.k; ++t) c.build_rows += c.n - t;
+  return KM_OK;
+}
+
+BuildArgs build_args(const Ctx& c) {
+  BuildArgs a;
+  memset(&a, 0, sizeof(a));
+  a.D = c.D;
+  a.ld = c.ld;
+  a.n = c.n;
+  a.n_pad = (int)c.L.n_pad;
+  a.fshift = c.fshift;
+  a.st = c.st();
+  a.aux = c.at<BuildAux>(c.L.baux);
+  a.tticket = c.at<unsigned>(c.L.btt);
+  a.partials = c.at<void>(c.L.bparts);
+  a.cgain = c.at<long long>(c.L.cand_gain);
+  a.list = c.at<int32_t>(c.L.blist);
+  a.lvn = c.at<uint32_t>(c.L.blvn);
+  a.lvo = c.at<uint32_t>(c.L.blvo);
+  a.bdn = c.at<void>(c.L.bdn);
+  a.med = c.at<int32_t>(c.L.med);
+  a.is_med = c.at<uint8_t>(c.L.is_med);
+  a.gains = c.at<double>(c.L.gains);
+  return a;
+}
+
+// BUILD with incrementally updated gains (km_build.cu): step 0 sums every
+// row, the gains after it take every row once more, and each later step
+// streams only the rows of the points whose nearest distance the new medoid
+// lowered.  Same choices as the plain pass in exact fixed point.
+km_status do_build(Ctx& c, Timer& tm, std::vector<std::pair<int, int>>& ev, km_result* res) {
+  NvtxRange nv("kmedoids BUILD");
+  if (c.opt.build_full) return do_build_full(c, tm, ev, res);
+  if (c.dtype == KM_F32 && !c.scanned) {
+    km_status r = scan_matrix(c);  // fixed-point exponent of the gains
+    if (r != KM_OK) return r;
+    c.scanned = true;
+  }
+  const size_t tiles = (size_t)(c.L.n_pad / kChunk);
+  KM_CUDA(cudaMemsetAsync(c.at<void>(c.L.is_med), 0, (size_t)c.L.n_pad, c.s));
+  KM_CUDA(cudaMemsetAsync(c.at<void>(c.L.cand_gain), 0, 8 * (size_t)c.L.n_pad, c.s));
+  KM_CUDA(cudaMemsetAsync(c.at<void>(c.L.baux), 0, sizeof(BuildAux), c.s));
+  KM_CUDA(cudaMemsetAsync(c.at<void>(c.L.btt), 0, 4 * tiles, c.s));
+  BuildArgs ba = build_args(c);
+  const int groups = build_update_groups(c.n, c.sms);
+  c.build_geom = 0;
+  int e0 = tm.mark();
+  KM_LAUNCH(c, launch_build_update(c.dtype, kBuildColsum, groups, ba, c.s));
+  ev.push_back({e0, tm.mark()});
+  for (int step = 0; step < c.k; ++step) {
+    ba.first = (step == 0);
+    KM_LAUNCH(c, launch_build_add(c.dtype, ba, c.s));
+    if (step + 1 < c.k) {
+      e0 = tm.mark();
+      KM_LAUNCH(c, launch_build_update(c.dtype, step == 0 ? kBuildFirst : kBuildStep, groups,
+                                       ba, c.s));
+      ev.push_back({e0, tm.mark()});
+    }
+  }
+  if (res) res->build_launches = c.k;
+  c.build_rows = -1;  // read back from the device after the BUILD
   return KM_OK;
 }
 
@@ -731,6 +804,14 @@ static km_status run_impl(bool do_b, bool do_s, const void* D, int32_t dtype, in
   }
   if (res && do_b) {
     res->build_steps = hb.build_step;
+    if (c.build_rows < 0) {
+      unsigned long long rows = 0;
+      KM_CUDA(cudaMemcpyAsync(&rows, &c.at<BuildAux>(c.L.baux)->rows_total, sizeof(rows),
+                              cudaMemcpyDeviceToHost, c.s));
+      KM_CUDA(cudaStreamSynchronize(c.s));
+      c.build_rows = (long long)rows;
+    }
+    res->build_rows = c.build_rows;
     if (c.opt.build_gains) {
       KM_CUDA(cudaMemcpyAsync(c.opt.build_gains, c.at<double>(c.L.gains), 8 * (size_t)k,
                               cudaMemcpyDeviceToHost, c.s));

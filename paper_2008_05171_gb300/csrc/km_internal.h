@@ -139,6 +139,45 @@ size_t eager_smem(int k);
 int eager_grid(int dtype, int k);  // co-resident CTAs, 0 if it cannot run
 cudaError_t launch_eager(int dtype, int grid, const EagerArgs& a, cudaStream_t s);
 
+// Incremental BUILD (km_build.cu): update passes and the commit of a step.
+enum BuildMode {
+  kBuildColsum = 0,  // step 0: distance sums over all rows
+  kBuildFirst = 1,   // gains after step 0: all rows, d_n from the first medoid
+  kBuildStep = 2     // later steps: the rows whose d_n dropped
+};
+
+struct BuildAux {
+  unsigned cnt;                  // listed points of the step
+  unsigned gticket;              // column tiles done (last-block ticket)
+  unsigned long long rows_total; // rows the update passes streamed
+};
+
+struct BuildArgs {
+  const void* D;
+  long long ld;
+  int n;
+  int n_pad;
+  int fshift;          // fixed-point exponent f (float data)
+  int first;           // commit of step 0
+  KmState* st;
+  BuildAux* aux;
+  unsigned* tticket;   // [tiles] CTAs of each column tile done
+  void* partials;      // Key[tiles] best non-medoid of each tile
+  long long* cgain;    // [n_pad] fixed-point gain of every candidate
+  int32_t* list;       // [n] points whose d_n dropped at the last commit
+  uint32_t* lvn;       // [n] their new d_n (stored bits)
+  uint32_t* lvo;       // [n] their old d_n (stored bits)
+  void* bdn;           // [n_pad] d_n of every point
+  int32_t* med;        // chosen medoids
+  uint8_t* is_med;
+  double* gains;       // BUILD gains per step [k] (may be NULL)
+};
+
+int build_update_groups(int n, int sms);
+cudaError_t launch_build_update(int dtype, int mode, int groups, const BuildArgs& a,
+                                cudaStream_t s);
+cudaError_t launch_build_add(int dtype, const BuildArgs& a, cudaStream_t s);
+
 // Initialisation kernels (Sec. 3.3): distance-weighted seeding and LAB.
 struct InitArgs {
   const void* D;

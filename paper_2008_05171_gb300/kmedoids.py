@@ -50,7 +50,8 @@ class km_options(ctypes.Structure):
                 ("trace_time_ns", ctypes.POINTER(ctypes.c_int64)),
                 ("build_gains", ctypes.POINTER(ctypes.c_double)),
                 ("draws", ctypes.c_void_p), ("draws_len", ctypes.c_int64),
-                ("maxneighbor", ctypes.c_int64), ("check_input", ctypes.c_int32)]
+                ("maxneighbor", ctypes.c_int64), ("check_input", ctypes.c_int32),
+                ("build_full", ctypes.c_int32)]
 
 
 class km_result(ctypes.Structure):
@@ -66,7 +67,8 @@ class km_result(ctypes.Structure):
                 ("build_eval_ms", ctypes.c_double),
                 ("kernel_launches", ctypes.c_int64),
                 ("best_sample", ctypes.c_int32), ("swap_geometry", ctypes.c_int16),
-                ("build_geometry", ctypes.c_int16), ("evaluated", ctypes.c_int64)]
+                ("build_geometry", ctypes.c_int16), ("evaluated", ctypes.c_int64),
+                ("build_rows", ctypes.c_int64)]
 
 
 _LOCK = threading.Lock()
@@ -179,9 +181,11 @@ def _stream():
 
 def options(variant="fastpam1", max_iter=0, tol=0.0, fastpam2_tol=0.0,
             rows_per_tile=0, profile=False, trace=0, tune=0, draws=None,
-            maxneighbor=0, check_input=False):
+            maxneighbor=0, check_input=False, build_full=False):
     """km_options.  draws: int32 CUDA tensor of candidate draws (FastCLARANS);
-    the caller keeps it alive for the call."""
+    the caller keeps it alive for the call.  build_full: every BUILD step
+    streams all candidate rows instead of updating the gains
+    incrementally."""
     o = km_options()
     load().km_default_options(ctypes.byref(o))
     if draws is not None:
@@ -189,6 +193,7 @@ def options(variant="fastpam1", max_iter=0, tol=0.0, fastpam2_tol=0.0,
         o.draws_len = int(draws.numel())
     o.maxneighbor = int(maxneighbor)
     o.check_input = 1 if check_input else 0
+    o.build_full = 1 if build_full else 0
     o.variant = VARIANTS[variant] if isinstance(variant, str) else int(variant)
     o.max_iter = int(max_iter)
     o.tol = float(tol)
