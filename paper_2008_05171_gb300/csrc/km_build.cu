@@ -43,8 +43,9 @@ namespace km {
 
 constexpr int kBuThreads = 256;              // 4 candidate columns each
 constexpr int kBuCols = 4 * kBuThreads;      // columns per tile (= kChunk)
-constexpr int kBuMinRows = 32;               // listed rows per CTA, at least
-constexpr int kBuUnroll = 8;                 // rows in flight per thread
+constexpr int kBuMinRows = 8;                // listed rows per CTA, at least
+// rows in flight per thread (all loads of a group are issued before its arithmetic)
+__host__ __device__ constexpr int bu_unroll(int) { return 8; }
 static_assert(kBuCols == kChunk, "a tile spans one padding unit of n");
 
 struct BuildRowEntry {  // one listed point, staged in shared memory
@@ -167,18 +168,16 @@ __global__ void __launch_bounds__(kBuThreads) k_build_update(const BuildArgs a) 
     }
     __syncthreads();
     if (!cvalid) continue;
-    int q = 0;
-    for (; q + kBuUnroll <= m; q += kBuUnroll) {
-      Vec d[kBuUnroll];
+    constexpr int U = bu_unroll(MODE);
+    for (int q = 0; q < m; q += U) {
+      // all loads of the group first (predicated), then the arithmetic
+      Vec d[U];
 #pragma unroll
-      for (int u = 0; u < kBuUnroll; ++u)
-        d[u] = ld4e(D + (size_t)rows[q + u].o * (size_t)a.ld + col);
+      for (int u = 0; u < U; ++u)
+        if (q + u < m) d[u] = ld4e(D + (size_t)rows[q + u].o * (size_t)a.ld + col);
 #pragma unroll
-      for (int u = 0; u < kBuUnroll; ++u) bu_accumulate<T, MODE>(acc, d[u], rows[q + u], f);
-    }
-    for (; q < m; ++q) {
-      const Vec dv = ld4e(D + (size_t)rows[q].o * (size_t)a.ld + col);
-      bu_accumulate<T, MODE>(acc, dv, rows[q], f);
+      for (int u = 0; u < U; ++u)
+        if (q + u < m) bu_accumulate<T, MODE>(acc, d[u], rows[q + u], f);
     }
   }
   if (cvalid && r1 > r0) {
@@ -341,7 +340,10 @@ __global__ void __launch_bounds__(kBuThreads) k_build_add(const BuildArgs a) {
 // -------------------------------------------------------------- launchers
 int build_update_groups(int n, int sms) {
   const int tiles = (n + kBuCols - 1) / kBuCols;
-  int g = (4 * sms + tiles - 1) / tiles;  // about four 256-thread CTAs per SM
+  // about 16 CTAs per SM in all: a short list then spreads over enough CTAs
+  // that each issues its (at most kBuMinRows) row loads at once; the CTAs
+  // past the list's share only take their tile ticket
+  int g = (16 * sms + tiles - 1) / tiles;
   if (g > 1024) g = 1024;
   if (g < 1) g = 1;
   return g;
