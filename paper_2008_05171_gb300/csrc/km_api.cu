@@ -438,6 +438,7 @@ km_status do_build(Ctx& c, Timer& tm, std::vector<std::pair<int, int>>& ev, km_r
   ev.push_back({e0, tm.mark()});
   for (int step = 0; step < c.k; ++step) {
     ba.first = (step == 0);
+    ba.cur = step & 1;
     KM_LAUNCH(c, launch_build_add(c.dtype, ba, c.s));
     if (step + 1 < c.k) {
       e0 = tm.mark();

@@ -130,16 +130,19 @@ __global__ void __launch_bounds__(kBuThreads) k_build_update(const BuildArgs a) 
   const int col = tile * kBuCols + 4 * tid;
 
   // rows of this CTA: a contiguous share of the list (or of 0..n-1), at
-  // least kBuMinRows of them unless the list is shorter
-  const long long cnt = (MODE == kBuildColsum) ? (long long)n : (long long)__ldcg(&aux->cnt);
+  // least kBuMinRows of them unless the list is shorter.  The groups past
+  // the list's share leave at once and take no ticket; the count they read
+  // stays unchanged during the launch (the next commit appends to the other
+  // counter, which this launch clears first).
+  const long long cnt =
+      (MODE == kBuildColsum) ? (long long)n : (long long)__ldcg(&aux->cnt[a.cur]);
   long long g_eff = (cnt + kBuMinRows - 1) / kBuMinRows;
   if (g_eff > groups) g_eff = groups;
   if (g_eff < 1) g_eff = 1;
-  long long r0 = 0, r1 = 0;
-  if (grp < g_eff) {
-    r0 = cnt * grp / g_eff;
-    r1 = cnt * (grp + 1) / g_eff;
-  }
+  if (grp >= g_eff) return;  // uniform for the CTA
+  if (tile == 0 && grp == 0 && tid == 0) aux->cnt[a.cur ^ 1] = 0u;
+  const long long r0 = cnt * grp / g_eff;
+  const long long r1 = cnt * (grp + 1) / g_eff;
 
   long long acc[4] = {0, 0, 0, 0};
   const E* D = static_cast<const E*>(a.D);
@@ -191,7 +194,7 @@ __global__ void __launch_bounds__(kBuThreads) k_build_update(const BuildArgs a) 
   __syncthreads();
   if (tid == 0) {
     const unsigned t = atomicAdd(&a.tticket[tile], 1u);
-    s_last = (t == (unsigned)groups - 1u) ? 1 : 0;
+    s_last = (t == (unsigned)g_eff - 1u) ? 1 : 0;
   }
   __syncthreads();
   if (!s_last) return;
@@ -246,7 +249,6 @@ __global__ void __launch_bounds__(kBuThreads) k_build_update(const BuildArgs a) 
       st->build_td_d = 0.0;
       st->build_td_i = 0;
       aux->rows_total += (unsigned long long)cnt;
-      aux->cnt = 0u;
       aux->gticket = 0u;
     }
   }
@@ -298,7 +300,7 @@ __global__ void __launch_bounds__(kBuThreads) k_build_add(const BuildArgs a) {
   const unsigned m = __ballot_sync(0xffffffffu, changed);
   if (m) {
     unsigned base = 0;
-    if (lane == __ffs(m) - 1) base = atomicAdd(&a.aux->cnt, (unsigned)__popc(m));
+    if (lane == __ffs(m) - 1) base = atomicAdd(&a.aux->cnt[a.cur], (unsigned)__popc(m));
     base = __shfl_sync(0xffffffffu, base, __ffs(m) - 1);
     if (changed) {
       unsigned lt;
@@ -340,10 +342,10 @@ __global__ void __launch_bounds__(kBuThreads) k_build_add(const BuildArgs a) {
 // -------------------------------------------------------------- launchers
 int build_update_groups(int n, int sms) {
   const int tiles = (n + kBuCols - 1) / kBuCols;
-  // about 16 CTAs per SM in all: a short list then spreads over enough CTAs
-  // that each issues its (at most kBuMinRows) row loads at once; the CTAs
-  // past the list's share only take their tile ticket
-  int g = (16 * sms + tiles - 1) / tiles;
+  // up to 8 CTAs per SM in all: a short list spreads over enough CTAs that
+  // each issues its (at most kBuMinRows) row loads at once; the CTAs past
+  // the list's share exit at once
+  int g = (8 * sms + tiles - 1) / tiles;
   if (g > 1024) g = 1024;
   if (g < 1) g = 1;
   return g;

@@ -147,8 +147,11 @@ enum BuildMode {
 };
 
 struct BuildAux {
-  unsigned cnt;                  // listed points of the step
+  unsigned cnt[2];               // listed points, by step parity (the update
+                                 // after the commit of step t reads cnt[t & 1]
+                                 // and clears cnt[(t & 1) ^ 1] for the next)
   unsigned gticket;              // column tiles done (last-block ticket)
+  unsigned pad;
   unsigned long long rows_total; // rows the update passes streamed
 };
 
@@ -159,6 +162,7 @@ struct BuildArgs {
   int n_pad;
   int fshift;          // fixed-point exponent f (float data)
   int first;           // commit of step 0
+  int cur;             // parity of the step whose list is written / read
   KmState* st;
   BuildAux* aux;
   unsigned* tticket;   // [tiles] CTAs of each column tile done
