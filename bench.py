@@ -9,10 +9,13 @@ float32 Gaussian mixture (100 clusters, centres U[-10,10]^16, sigma=1, equal
 weights), Euclidean float32 20000x20000 matrix (1.6 GB, larger than L2),
 k=100.  ``--workload gmm_50000`` runs the n=50000, k=200 mixture (10 GB).
 
-metric: Delta-TD point evaluations per second over the whole step (every
-(candidate, point) pair BUILD and SWAP evaluate), plus the full run time
-(ms_per_step) and the SWAP iteration time.  The roofline object covers the
-kernel with the largest share of the step.  Multi-GPU: replicas only (the
+metric: element evaluations per second over the whole step (every
+(candidate, point) pair a SWAP pass evaluates, and every (row, candidate)
+element the BUILD kernels stream: the incremental BUILD streams every row
+twice and then only the rows of the points whose nearest distance dropped),
+plus the full run time (ms_per_step) and the SWAP iteration time.  The
+roofline object covers the kernel with the largest share of the step; the
+plain BUILD pass (every candidate row each step) is timed once beside it.  Multi-GPU: replicas only (the
 method's passes are one sequential chain; each rank runs its own instance).
 """
 from __future__ import annotations

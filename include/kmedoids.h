@@ -197,8 +197,11 @@ typedef struct km_result {
   int64_t kernel_launches; /* kernels this call launched (all phases) */
   int32_t best_sample;     /* kmedoids_clara: index of the winning sample */
   int16_t swap_geometry;   /* geometry table entries (1..16) the SWAP and */
-  int16_t build_geometry;  /* BUILD passes ran with; 0 = not run, or (SWAP)
-                              the eager kernel of FasterPAM / FastCLARANS */
+  int16_t build_geometry;  /* BUILD passes ran with; 0 = not run, (SWAP)
+                              the eager kernel of FasterPAM / FastCLARANS,
+                              or (BUILD) the incremental BUILD, whose launch
+                              shape is fixed (opts->tune then applies to
+                              the SWAP passes only) */
   int64_t evaluated;       /* FasterPAM / FastCLARANS: candidates evaluated
                               by the sequential scan (non-medoid positions
                               up to each applied swap, and every position
@@ -227,8 +230,12 @@ size_t kmedoids_workspace_size(int64_t n, int32_t k, int32_t dtype,
 /* PAM BUILD (Alg. 1): k greedy steps.  Step 0 takes the point with the
  * smallest distance sum (the 1-medoid, Eq. (3)); each further step adds the
  * non-medoid c minimising sum_o min(d(o,c) - d_n(o), 0), the exact TD change
- * of adding c (the point c itself included).  Writes k medoids (slot order =
- * order chosen) to medoids_out (DEVICE).  res->td = TD of the result. */
+ * of adding c (the point c itself included; lowest index on ties).  By
+ * default the gains of all candidates are kept and updated after each step
+ * from the rows of the points whose d_n the new medoid lowered (see
+ * km_options.build_full).  Writes k medoids (slot order = order chosen) to
+ * medoids_out (DEVICE).  res->td = TD of the result; res->build_rows = rows
+ * of D the BUILD streamed. */
 km_status kmedoids_build(const void *D, int32_t dtype, int64_t n, int64_t ld,
                          int32_t k, int32_t *medoids_out,
                          const km_options *opts, km_result *res, void *ws,
