@@ -6,7 +6,11 @@
  * Eager k-Medoids Clustering: O(k) Runtime Improvement of the PAM, CLARA,
  * and CLARANS Algorithms" (arXiv 2008.05171):
  *
- *   - PAM BUILD (Alg. 1), the greedy initialisation;
+ *   - PAM BUILD (Alg. 1), the greedy initialisation, with every candidate's
+ *     gain kept exact and updated after each step from the matrix rows of
+ *     the points whose nearest distance the new medoid lowered (the same
+ *     choices as re-evaluating every candidate, a few matrix passes per
+ *     BUILD instead of k);
  *   - the per-point cache nearest / d_n / d_s (Sec. 2) and the removal loss
  *     Delta^{-m_i} (Eq. (7));
  *   - the FastPAM1 SWAP evaluation (Alg. 3, Eq. (7)): Delta TD of every
@@ -30,11 +34,13 @@
  *           otherwise the call returns KM_E_INVALID.
  *   dtype   KM_I32 (int32 distances; sums in int64, results exact),
  *           KM_U16 (uint16 distances, the compressed form; as KM_I32), or
- *           KM_F32 (float32 distances; TD and BUILD sums in FP64, the SWAP
- *           Delta sums in exact 64-bit fixed point with a per-call scale
- *           2^f, f = 60 - ceil(log2(n+1)) - (exponent of the largest entry),
- *           i.e. ~2^-(60-log2 n) resolution relative to the largest
- *           distance; float inputs are scanned once per call and entries
+ *           KM_F32 (float32 distances; TD sums in FP64, the SWAP Delta sums
+ *           and the BUILD gains in exact 64-bit fixed point with a per-call
+ *           scale 2^f, f = 60 - ceil(log2(n+1)) - (exponent of the largest
+ *           entry), i.e. ~2^-(60-log2 n) resolution relative to the largest
+ *           distance (the plain BUILD pass of km_options.build_full sums
+ *           compensated FP32 partials in FP64); float inputs are scanned
+ *           once per call and entries
  *           that are negative or not finite return KM_E_NUMERIC).
  *   medoids int32 point indices in SLOT order, DEVICE memory.  A swap puts
  *           the new medoid into the removed medoid's slot.  Labels are slots.
