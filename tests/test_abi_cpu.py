@@ -112,3 +112,46 @@ def test_invalid_arguments_of_the_newer_entry_points(lib):
     bad = km.options(variant="fastpam2")
     assert lib.kmedoids_run_batched(P(fake), P(fake), 1, P(fake), P(fake), ctypes.byref(bad),
                                     P(fake), 1 << 20, None) == 7
+
+
+def _c_struct_fields(name):
+    """Field names of `typedef struct name { ... } name;` in the header, in
+    declaration order (comments stripped; `int32_t a, b;` gives a and b)."""
+    txt = re.sub(r"/\*.*?\*/", "", open(HEADER).read(), flags=re.S)
+    body = re.search(r"typedef struct %s \{(.*?)\} %s;" % (name, name), txt, flags=re.S)
+    assert body, name
+    fields = []
+    for decl in body.group(1).split(";"):
+        decl = decl.strip()
+        if decl:  # [const] type [*]name[, [*]name ...]
+            rest = re.match(r"(?:const\s+)?\w+\s*(.*)", decl, flags=re.S).group(1)
+            fields += [x.strip().lstrip("*").strip() for x in rest.split(",")]
+    return fields
+
+
+@pytest.mark.parametrize("struct", ["km_options", "km_result"])
+def test_ctypes_structs_match_the_header(struct, tmp_path):
+    """The binding's ctypes mirrors have the header's fields in the same
+    order at the same offsets, and the same size, as a C compiler lays them
+    out (gcc on this host)."""
+    import shutil
+    import subprocess
+    import paper_2008_05171_gb300.kmedoids as km
+    cls = getattr(km, struct)
+    names = [f for f, _ in cls._fields_]
+    assert names == _c_struct_fields(struct)
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("no C compiler")
+    src = tmp_path / "layout.c"
+    src.write_text("#include <stdio.h>\n#include <stddef.h>\n#include \"kmedoids.h\"\n"
+                   "int main(void) {\n  printf(\"%%zu\\n\", sizeof(%s));\n" % struct +
+                   "".join("  printf(\"%%zu\\n\", offsetof(%s, %s));\n" % (struct, f)
+                           for f in names) + "  return 0;\n}\n")
+    exe = tmp_path / "layout"
+    subprocess.run([gcc, "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o",
+                    str(exe)], check=True, capture_output=True)
+    out = [int(x) for x in subprocess.run([str(exe)], check=True, capture_output=True,
+                                          text=True).stdout.split()]
+    assert out[0] == ctypes.sizeof(cls)
+    assert out[1:] == [getattr(cls, f).offset for f in names]
