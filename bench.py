@@ -676,7 +676,8 @@ def run_ours(args, rank, world, local_rank):
     # tune=-1: the first (warm-up) call times every kernel geometry that fits
     # on this matrix and the library keeps the fastest for the timed steps
     def step(profile=True):
-        return km.run(D, k, ws=ws, labels=True, profile=profile, tune=args.tune)
+        return km.run(D, k, ws=ws, labels=True, profile=profile, tune=args.tune,
+                      build_full=args.build_full)
 
     for _ in range(args.warmup):
         step()
@@ -764,7 +765,7 @@ def run_ours(args, rank, world, local_rank):
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             a.record(stream)
             Dd.copy_(Dh, non_blocking=True)
-            r = km.run(Dd, k, ws=ws, labels=True, tune=args.tune)
+            r = km.run(Dd, k, ws=ws, labels=True, tune=args.tune, build_full=args.build_full)
             med_h.copy_(r["medoids"], non_blocking=True)
             lab_h.copy_(r["labels"], non_blocking=True)
             b.record(stream)
@@ -831,11 +832,11 @@ def run_ours(args, rank, world, local_rank):
         Di = D.to(torch.int32)
         wsi = km.workspace(n, k, km.KM_I32, opts, device=dev)
         for _ in range(2):
-            km.run(Di, k, ws=wsi, profile=True, tune=args.tune)
+            km.run(Di, k, ws=wsi, profile=True, tune=args.tune, build_full=args.build_full)
         torch.cuda.synchronize()
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record(stream)
-        ri = km.run(Di, k, ws=wsi, profile=True, tune=args.tune)
+        ri = km.run(Di, k, ws=wsi, profile=True, tune=args.tune, build_full=args.build_full)
         b.record(stream)
         torch.cuda.synchronize()
         line["int32_same_matrix"] = {
@@ -1098,6 +1099,9 @@ def main():
     ap.add_argument("--workload", default="gmm_20000", choices=sorted(WORKLOADS))
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--build-full", action="store_true",
+                    help="matrix workloads: time the plain BUILD pass (every candidate "
+                         "row each step) instead of the incremental BUILD")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     # smaller cases of the same recipes, for profiler captures only
     ap.add_argument("--n", type=int, default=None, help="features_*: number of points")
