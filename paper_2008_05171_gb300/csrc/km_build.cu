@@ -44,8 +44,7 @@ namespace km {
 constexpr int kBuThreads = 256;              // 4 candidate columns each
 constexpr int kBuCols = 4 * kBuThreads;      // columns per tile (= kChunk)
 constexpr int kBuMinRows = 8;                // listed rows per CTA, at least
-// rows in flight per thread (all loads of a group are issued before its arithmetic)
-__host__ __device__ constexpr int bu_unroll(int) { return 8; }
+constexpr int kBuUnroll = 8;                 // row loads in flight per thread
 static_assert(kBuCols == kChunk, "a tile spans one padding unit of n");
 
 struct BuildRowEntry {  // one listed point, staged in shared memory
@@ -171,7 +170,7 @@ __global__ void __launch_bounds__(kBuThreads) k_build_update(const BuildArgs a) 
     }
     __syncthreads();
     if (!cvalid) continue;
-    constexpr int U = bu_unroll(MODE);
+    constexpr int U = kBuUnroll;
     for (int q = 0; q < m; q += U) {
       // all loads of the group first (predicated), then the arithmetic
       Vec d[U];
