@@ -168,7 +168,11 @@ def test_fastpam1_equals_pam_trajectory():
 @pytest.mark.parametrize("variant", ["fastpam1", "fastpam2", "fasterpam"])
 def test_monotone_and_locally_optimal(variant):
     """TD strictly decreases at every accepted swap and the final medoids
-    admit no swap with Delta < 0 (Sec. 2)."""
+    admit no swap with Delta < 0 (Sec. 2).  Iteration counts: steepest
+    descent makes one swap per pass and a final pass without one
+    (iterations = swaps + 1, Sec. 5); FastPAM2 applies at least the best
+    swap in every pass but the last, and every FasterPAM scan but the last
+    holds a swap (a whole scan without one ends the run, Alg. 4)."""
     insts = bf.tiny_instances(31, 60, n_lo=5, n_hi=11)
     insts += [np.ascontiguousarray(M) for M in
               bf.tiny_float_instances(32, 30, n_lo=5, n_hi=11)]
@@ -192,6 +196,10 @@ def test_monotone_and_locally_optimal(variant):
         assert abs(out["td_bookkept"] - out["td"]) <= 1e-9 * (1 + prev)
         assert bf.swap_deltas(D, med).min() >= -1e-9 * (1 + prev)
         assert out["converged"]
+        if variant == "fastpam1":
+            assert out["iterations"] == out["swaps"] + 1
+        else:
+            assert out["swaps"] >= out["iterations"] - 1 >= 0
 
 
 def test_fasterpam_scan_rule():
