@@ -954,10 +954,11 @@ int oracle_clarans(const void *D, int dtype, int64_t n, int64_t ld, int k,
 /* ------------------------------------------------------------------------
  * Euclidean dissimilarity matrix of m float32 points in FP64, rounded once
  * to float32: D[i*ld + j] = sqrt(sum_t (x_it - x_jt)^2) (zero diagonal,
- * symmetric by construction).  The recipe is fixed to the operation: FP64
- * differences, squares accumulated with fused multiply-adds in coordinate
- * order (fma, the same on every host), FP64 square root, one rounding.
- * Used for CLARA samples and batch instances.
+ * symmetric by construction).  The Euclidean distance written out: FP64
+ * differences, their squares added one coordinate after the other in plain
+ * FP64 (the oracle is built with -ffp-contract=off, so no multiply-add is
+ * fused), FP64 square root, one rounding to float32.  Used for CLARA samples
+ * and batch instances.
  * ---------------------------------------------------------------------- */
 void oracle_euclid_f32(const float *X, int64_t m, int d, const int64_t *idx,
                        int64_t ld, float *D) {
@@ -968,7 +969,7 @@ void oracle_euclid_f32(const float *X, int64_t m, int d, const int64_t *idx,
       double s = 0.0;
       for (int t = 0; t < d; t++) {
         double df = (double)xi[t] - (double)xj[t];
-        s = fma(df, df, s); /* fused, in coordinate order: the fixed recipe */
+        s += df * df;
       }
       D[i * ld + j] = (float)sqrt(s);
     }

@@ -3,8 +3,9 @@
 Integer dissimilarities: bit-exact medoids, labels, TD, BUILD gains, swap
 trajectories and per-candidate Delta values.  Float dissimilarities: the
 tolerance the method allows -- TD within 1e-6 relative, per-candidate Delta
-within 1e-9 * TD (the GPU sums the same FP64 terms in another order), and
-every accepted swap replayed by the oracle from the same pre-swap state.
+within 1e-9 * TD (the GPU sums each distance as an exact 64-bit fixed-point
+value, the oracle sums FP64 values), and every accepted swap replayed by the
+oracle from the same pre-swap state.
 Sizes span several 1024-column chunks and candidate tiles with ragged
 tails, padded row strides, and the degenerate k = 1, 2, n cases.
 """

@@ -404,6 +404,35 @@ def test_clara_best_sample_has_least_full_td():
     assert (lab == np.argmin(D[:, :400][:, med], axis=1)).all()
 
 
+def test_euclid_f32_is_the_fp64_distance_rounded_once():
+    """The batch and CLARA matrices are Euclidean distances of float32
+    points computed in FP64 and rounded once to float32: every entry lies
+    within half a float32 ulp of scipy's FP64 distance (an independent
+    routine with its own summation order), the diagonal is zero, the matrix
+    is bitwise symmetric and the row padding is zero.  A float32 sum, a
+    dropped coordinate or a missing square root fails it."""
+    from scipy.spatial.distance import cdist
+    g = np.random.default_rng(416)
+    for d in (1, 2, 3, 8, 17, 32):
+        m = int(g.integers(5, 70))
+        X = (g.normal(size=(m, d)) * g.uniform(0.01, 100.0)).astype(np.float32)
+        X[-1] = X[0]                                   # a duplicate: distance 0
+        ld = (m + 3) // 4 * 4 + 4
+        D = oracle.euclid_f32(X, ld=ld)
+        ref = cdist(X.astype(np.float64), X.astype(np.float64))
+        got = D[:, :m].astype(np.float64)
+        half_ulp = 0.5 * np.spacing(D[:, :m]).astype(np.float64)
+        assert (np.abs(got - ref) <= half_ulp * (1 + 1e-6) + 1e-300).all(), d
+        assert (np.diag(D[:, :m]) == 0).all()
+        assert (D[:, :m] == D[:, :m].T).all()
+        assert (D[:, m:] == 0).all()
+        assert D[0, m - 1] == 0 and D[m - 1, 0] == 0
+    # sample indices select rows and columns of the full matrix
+    X = g.normal(size=(40, 5)).astype(np.float32)
+    idx = np.array([3, 17, 0, 39, 8], np.int64)
+    assert (oracle.euclid_f32(X, idx=idx)[:, :5] == oracle.euclid_f32(X)[np.ix_(idx, idx)]).all()
+
+
 # --------------------------------------------------------- FastCLARANS --
 
 def _clarans_bruteforce(D, med, cand, maxneighbor):
@@ -537,6 +566,58 @@ def test_init_weighted_distinct_and_degenerate():
     assert med[0] == 7 and len(set(med.tolist())) == 3
 
 
+def _float_matrix(seed, n, d=3):
+    """A float32 Euclidean matrix (distances with full 24-bit mantissas)."""
+    g = np.random.default_rng(seed)
+    X = (g.normal(size=(n, d)) * 3.7).astype(np.float32)
+    return oracle.euclid_f32(X)
+
+
+def test_init_weighted_float_weights_follow_the_distances():
+    """On float matrices the weights of a draw are the distances to the
+    nearest medoid (Sec. 3.3): u_1 at the middle of point o's interval of
+    the exact running sum picks o, and the interval boundaries sit where
+    the exact FP64 distances put them to 2^-40 of the total weight: u_1 just
+    above the sum of the weights before o picks o, just below it picks the
+    previous point of positive weight.  The expected intervals come from
+    numpy's FP64 distances, not from the oracle's summation."""
+    import math
+    for seed, n in ((421, 9), (422, 31), (423, 64)):
+        D = _float_matrix(seed, n)
+        A = bf.sq(D)
+        first = n // 3
+        w = A[:, first].copy()
+        W = math.fsum(w)
+        pre = [math.fsum(w[:o]) for o in range(n)]
+        pos = [o for o in range(n) if w[o] > 0]
+        delta = 2.0 ** -40 * W
+        u0 = (first + 0.5) / n
+        for j, o in enumerate(pos):
+            mid = (pre[o] + 0.5 * w[o]) / W
+            assert oracle.init_weighted(D, 2, [u0, mid]).tolist() == [first, o]
+            if j > 0 and w[o] > 4 * delta:
+                above = (pre[o] + delta) / W
+                below = (pre[o] - delta) / W
+                assert oracle.init_weighted(D, 2, [u0, above])[1] == o
+                assert oracle.init_weighted(D, 2, [u0, below])[1] == pos[j - 1]
+
+
+def test_init_weighted_float_frequencies_follow_distances():
+    """Float matrix: over many uniform u_1 the second medoid is o with
+    frequency close to d(o, m_1) / sum_p d(p, m_1) (chi-square, fixed seed,
+    ~10 degrees of freedom)."""
+    D = _float_matrix(424, 11)
+    A = bf.sq(D)
+    g = np.random.default_rng(4)
+    counts = np.zeros(11)
+    for u1 in g.random(5000):
+        counts[oracle.init_weighted(D, 2, [0.0, u1])[1]] += 1
+    p = A[:, 0] / A[:, 0].sum()
+    m = p > 0
+    chi2 = (((counts[m] - 5000 * p[m]) ** 2) / (5000 * p[m])).sum()
+    assert counts[~m].sum() == 0 and chi2 < 35.0
+
+
 def _lab_bruteforce(D, k, ranks):
     """LAB (Sec. 3.3) from its definition: at step t the subsample is the
     set of non-medoids at the given ranks (index order), and the next medoid
@@ -568,6 +649,37 @@ def test_init_lab_matches_subsample_td_bruteforce():
         s = int(g.integers(1, n - k + 2))
         ranks = np.array([g.choice(n - t, s, replace=False) for t in range(k)])
         assert oracle.init_lab(D, k, ranks).tolist() == _lab_bruteforce(D, k, ranks)
+
+
+def test_init_lab_float_matches_subsample_td_bruteforce():
+    """Float matrices: each LAB step is the argmin of the subsample's TD
+    with the candidate added, computed in numpy FP64, wherever the best
+    choice beats the runner-up by more than 1e-9 of the subsample's TD; the
+    reported gain equals the FP64 TD change to 1e-12 of it."""
+    g = np.random.default_rng(425)
+    checked = 0
+    for t0 in range(40):
+        n = int(g.integers(6, 30))
+        D = _float_matrix(4250 + t0, n, d=int(g.integers(1, 6)))
+        A = bf.sq(D)
+        k = int(g.integers(1, min(n, 6) + 1))
+        s = int(g.integers(2, n - k + 2))
+        ranks = np.array([g.choice(n - t, s, replace=False) for t in range(k)])
+        med_o, gains_o = oracle.init_lab(D, k, ranks, gains=True)
+        med = []
+        for t in range(k):
+            free = [o for o in range(n) if o not in med]
+            S = [free[r] for r in ranks[t]]
+            base = A[np.ix_(S, med)].min(axis=1).sum() if med else 0.0
+            vals = sorted((A[np.ix_(S, med + [c])].min(axis=1).sum(), c) for c in S)
+            scale = max(1.0, abs(vals[0][0]))
+            assert abs(gains_o[t] - (vals[0][0] - base)) <= 1e-12 * max(1.0, abs(base), scale)
+            if len(vals) > 1 and vals[1][0] - vals[0][0] <= 1e-9 * scale:
+                break                          # a near-tie: the rest is not comparable
+            assert med_o[t] == vals[0][1], (t0, t)
+            med.append(vals[0][1])
+            checked += 1
+    assert checked > 60
 
 
 def test_init_lab_full_sample_is_build():
