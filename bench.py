@@ -4,18 +4,17 @@
 One step = one whole run of the method on one synthetic input resident in
 HBM: PAM BUILD (k greedy steps) + the per-point cache + FastPAM1 SWAP to
 convergence (best swap per pass, cache update after each swap), i.e.
-kmedoids_run() through the C ABI.  Default workload: n=20000 points, d=16
-float32 Gaussian mixture (100 clusters, centres U[-10,10]^16, sigma=1, equal
-weights), Euclidean float32 20000x20000 matrix (1.6 GB, larger than L2),
-k=100.  ``--workload gmm_50000`` runs the n=50000, k=200 mixture (10 GB).
+kmedoids_run() through the C ABI.  Default workload: n=50000 points, d=32
+float32 Gaussian mixture (200 clusters, centres U[-10,10]^32, sigma
+U[0.5,2], Dirichlet(1) weights), Euclidean float32 50000x50000 matrix
+(10 GB, larger than L2), k=200; the same figures for the n=20000, k=100
+mixture (1.6 GB) ride along in a ``k100`` block.
 
-metric: element evaluations per second over the whole step (every
-(candidate, point) pair a SWAP pass evaluates, and every (row, candidate)
-element the BUILD kernels stream: the incremental BUILD streams every row
-twice and then only the rows of the points whose nearest distance dropped),
-plus the full run time (ms_per_step) and the SWAP iteration time.  The
-roofline object covers the kernel with the largest share of the step; the
-plain BUILD pass (every candidate row each step) is timed once beside it.  Multi-GPU: replicas only (the
+metric: SWAP dTD point-evals per second -- (n-k)*n (candidate, point) pairs
+per FastPAM1 evaluation pass divided by the median pass time (CUDA events
+around every evaluation launch of the timed runs) -- plus the full run time
+(ms_per_step: BUILD + cache + every SWAP pass and swap) and the pass's
+fraction of the measured HBM bandwidth.  Multi-GPU: replicas only (the
 method's passes are one sequential chain; each rank runs its own instance).
 """
 from __future__ import annotations
@@ -31,6 +30,9 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 import numpy as np  # noqa: E402
+
+# the headline metric, worded as the method's benchmark states it
+METRIC = "SWAP \u0394TD point-evals/sec + full PAM run time at k=100/200; % HBM roofline vs FP32 path"
 
 WORKLOADS = {
     "gmm_20000": dict(n=20000, d=16, centers=100, k=100, recipe="gmm_20000_points",
@@ -278,14 +280,12 @@ def run_features(args, rank, world, local_rank):
                "d2h_bytes_per_step": int(4 * k + 4 * n)}
         del med_h, lab_h
     line = {
-        "metric": "SWAP dTD point-evals/sec + full PAM run time (k=100/200); % HBM roofline",
+        "metric": METRIC,
         "value": value, "unit": "point-evals/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "bf16 Gram / f32 (FP64 TD)",
         "data": "synthetic",
-        "config": {"workload": args.workload + ": " + spec["desc"], "n": n, "d": d, "k": k,
-                   "l2": "features (51 MB) L2-resident by design; no matrix",
-                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "config": features_config(args.workload, spec, world),
         "full_run_ms": total_ms / args.steps, "swap_iterations": r0["iterations"],
         "swaps": r0["swaps"], "swap_iter_ms": s_ms, "build_step_ms": b_ms, "td": r0["td"],
         "kernel_ms_per_step": {"build_eval": r0["build_eval_ms"], "swap_eval": r0["eval_ms"],
@@ -566,7 +566,7 @@ def run_fasterpam(args, rank, world, local_rank):
                "h2d_bytes_per_step": int(D.numel() * 4), "d2h_bytes_per_step": 4 * k + 4 * n}
         del Dh, Dd
     line = {
-        "metric": "SWAP dTD point-evals/sec + full PAM run time (k=100/200); % HBM roofline",
+        "metric": METRIC,
         "value": value, "unit": "point-evals/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
@@ -629,7 +629,7 @@ def run_clarans(args, rank, world, local_rank):
     evals = sum(int(r["iterations"]) * n for r in results)  # draws evaluated x points
     value = world * evals / (total_ms / 1e3)
     line = {
-        "metric": "SWAP dTD point-evals/sec + full PAM run time (k=100/200); % HBM roofline",
+        "metric": METRIC,
         "value": value, "unit": "point-evals/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
@@ -667,16 +667,15 @@ def run_ours(args, rank, world, local_rank):
     dev = torch.device("cuda", local_rank)
     D, spec = make_input(args.workload, dev)
     n, k = spec["n"], spec["k"]
-    code = km._dtype_code(D)
     esize = D.element_size()
-    opts = km.options(profile=True)
-    ws = km.workspace(n, k, code, opts, device=dev)
+    stream = torch.cuda.current_stream()
+    ws = km.workspace(n, k, km._dtype_code(D), km.options(profile=True), device=dev)
     torch.cuda.synchronize()
 
     # tune=-1: the first (warm-up) call times every kernel geometry that fits
     # on this matrix and the library keeps the fastest for the timed steps
-    def step(profile=True):
-        return km.run(D, k, ws=ws, labels=True, profile=profile, tune=args.tune,
+    def step():
+        return km.run(D, k, ws=ws, labels=True, profile=True, tune=args.tune,
                       build_full=args.build_full)
 
     for _ in range(args.warmup):
@@ -685,7 +684,6 @@ def run_ours(args, rank, world, local_rank):
     barrier(world)
     clocks = Clocks(local_rank)
     clocks.start()
-    stream = torch.cuda.current_stream()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(args.steps)]
     results = []
@@ -700,35 +698,37 @@ def run_ours(args, rank, world, local_rank):
     ck = clocks.stop()
     step_ms = [a.elapsed_time(b) for a, b in ev]
     total_ms = max_over_ranks(sum(step_ms), world, dev)
-
-    evals = [sum(evals_of(n, k, r)) for r in results]
-    value = world * sum(evals) / (total_ms / 1e3)
+    sw = swap_pass_figures(n, k, esize, results)
+    pass_ms = max_over_ranks(sw["median_ms"], world, dev)
+    value = world * (n - k) * n / (pass_ms / 1e3)
     r0 = results[-1]
-    # kernel shares and roofline of the dominant one
-    swap_launch_ms = r0["eval_ms"] / max(1, r0["eval_launches"])
-    build_launch_ms = r0["build_eval_ms"] / max(1, r0["build_launches"])
-    swap_bytes = (n - k) * n * esize
+
+    # roofline of the kernel with the larger share of the step
+    build_launch_ms = sum(r["build_eval_ms"] for r in results) / \
+        max(1, sum(r["build_launches"] for r in results))
     # BUILD: rows streamed by the BUILD evaluation launches (incremental
     # update passes, or the plain pass's candidate rows), averaged per launch
     build_bytes = evals_of(n, k, r0)[0] * esize / max(1, r0["build_launches"])
     incremental = int(r0["build_geometry"]) == 0
     peak, peak_kind = peaks()
     kern = {
-        "swap_eval": {"launch_ms": swap_launch_ms, "bytes": swap_bytes,
+        "swap_eval": {"launch_ms": sw["mean_ms"], "bytes": (n - k) * n * esize,
                       "share_ms": r0["eval_ms"]},
         "build_eval": {"launch_ms": build_launch_ms, "bytes": build_bytes,
                        "share_ms": r0["build_eval_ms"]},
     }
     dom = max(kern, key=lambda x: kern[x]["share_ms"])
     prof = load_json(os.path.join(ROOT, "profiles", "traffic.json")) or {}
-    traffic = None
-    key, files = dom, ("km_stream.cu", "km_device.cuh")
-    if dom == "build_eval" and incremental:
-        key, files = "build_update", ("km_build.cu", "km_device.cuh")
-    ent = prof.get(key + ("_u16" if esize == 2 else ""))
-    if ent and ent.get("source_hash") == source_hash(files) and \
-            ent.get("workload") == args.workload:
-        traffic = ent.get("dram_bytes_per_launch")
+
+    def traffic_of(name):
+        key, files = name, ("km_stream.cu", "km_device.cuh")
+        if name == "build_eval" and incremental:
+            key, files = "build_update", ("km_build.cu", "km_device.cuh")
+        ent = prof.get(key + ("_u16" if esize == 2 else ""))
+        if ent and ent.get("source_hash") == source_hash(files) and \
+                ent.get("workload") == args.workload:
+            return ent.get("dram_bytes_per_launch")
+        return None
 
     def kernel_name(name):
         t = {4: "float", 2: "uint16"}.get(esize, "?")
@@ -741,6 +741,7 @@ def run_ours(args, rank, world, local_rank):
         ach = kk["bytes"] / (kk["launch_ms"] / 1e3) / 1e9
         return {"bound": "hbm", "achieved": round(ach, 1), "peak": peak,
                 "unit": "GB/s", "frac": round(ach / peak, 4),
+                "traffic": traffic_of(name),
                 "peak_source": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)"
                 if peak_kind == "measured" else "fallback 6.8 TB/s",
                 "kernel": kernel_name(name),
@@ -748,10 +749,10 @@ def run_ours(args, rank, world, local_rank):
                 "avg_launch_ms": round(kk["launch_ms"], 5)}
 
     roofline = roof(dom)
-    roofline["traffic"] = traffic
     other = roof("swap_eval" if dom == "build_eval" else "build_eval")
 
-    # end to end: pinned host matrix -> device, run, results -> host
+    # end to end through the public call: the matrix copied from pinned host
+    # memory, the run, medoids and labels read back -- every timed step
     e2e = None
     if not args.no_e2e:
         Dh = torch.empty(D.shape, dtype=D.dtype, pin_memory=True)
@@ -761,7 +762,7 @@ def run_ours(args, rank, world, local_rank):
         lab_h = torch.empty(n, dtype=torch.int32, pin_memory=True)
         torch.cuda.synchronize()
         e_ms, e_evals = 0.0, 0
-        for i in range(max(1, min(args.steps, 3))):
+        for i in range(args.steps):
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             a.record(stream)
             Dd.copy_(Dh, non_blocking=True)
@@ -771,35 +772,35 @@ def run_ours(args, rank, world, local_rank):
             b.record(stream)
             torch.cuda.synchronize()
             e_ms += a.elapsed_time(b)
-            e_evals += sum(evals_of(n, k, r))
+            e_evals += r["iterations"] * (n - k) * n
+        e_ms = max_over_ranks(e_ms, world, dev)
         e2e = {"value": world * e_evals / (e_ms / 1e3), "unit": "point-evals/s",
+               "steps": args.steps, "ms_per_step": e_ms / args.steps,
                "h2d_bytes_per_step": int(D.numel() * esize),
-               "d2h_bytes_per_step": int(4 * k + 4 * n + 8 * 8)}
+               "d2h_bytes_per_step": int(4 * k + 4 * n),
+               "note": "SWAP point-evals of the run / (matrix H2D + BUILD + SWAP + "
+                       "medoids and labels D2H)"}
         del Dh, Dd
 
-    swap_iter_ms = r0["eval_ms"] / max(1, r0["eval_launches"])
     line = {
-        "metric": "SWAP dTD point-evals/sec + full PAM run time (k=100/200); % HBM roofline",
-        "value": value, "unit": "point-evals/s", "n_gpus": world,
+        "metric": METRIC, "value": value, "unit": "point-evals/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": total_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
         "dtype": "f32 (exact 64-bit fixed-point dTD sums, FP64 TD)" if esize == 4 else
                  "u16 distances (int32 compares, int64 sums)",
         "data": "synthetic",
-        "config": {"workload": args.workload + ": " + spec["desc"],
-                   "n": n, "k": k, "matrix_bytes": int(D.numel() * esize),
-                   "geometry": {"swap": int(r0["swap_geometry"]),
-                                "build": int(r0["build_geometry"]),
-                                "picked_by": {-1: "measured on the first call (tune=-1)",
-                                              0: "preference order (tune=0)"}.get(
-                                                  args.tune, "fixed (tune=%d)" % args.tune)},
-                   "l2": "matrix larger than L2 (no flush needed)",
-                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "config": matrix_config(args.workload, spec, world),
+        "value_definition": "(n-k)*n point-evals per FastPAM1 SWAP evaluation pass / median "
+                            "pass time (CUDA events around every evaluation launch of the "
+                            "timed runs); ms_per_step = the whole BUILD + SWAP run",
+        "swap_pass": sw,
+        "geometry": {"swap": int(r0["swap_geometry"]), "build": int(r0["build_geometry"]),
+                     "picked_by": {-1: "measured on the first call (tune=-1)",
+                                   0: "preference order (tune=0)"}.get(
+                                       args.tune, "fixed (tune=%d)" % args.tune)},
         "full_run_ms": total_ms / args.steps,
         "swap_iterations": r0["iterations"], "swaps": r0["swaps"],
-        "swap_iter_ms": swap_iter_ms,
-        "swap_evals_per_s": (n - k) * n / (swap_iter_ms / 1e3),
         "td": r0["td"],
         "kernel_ms_per_step": {"build_eval": r0["build_eval_ms"],
                                "swap_eval": r0["eval_ms"],
@@ -830,7 +831,7 @@ def run_ours(args, rank, world, local_rank):
     if esize == 2:
         # the same matrix as int32, timed the same way (not part of value)
         Di = D.to(torch.int32)
-        wsi = km.workspace(n, k, km.KM_I32, opts, device=dev)
+        wsi = km.workspace(n, k, km.KM_I32, km.options(profile=True), device=dev)
         for _ in range(2):
             km.run(Di, k, ws=wsi, profile=True, tune=args.tune, build_full=args.build_full)
         torch.cuda.synchronize()
@@ -845,44 +846,112 @@ def run_ours(args, rank, world, local_rank):
             "build_step_ms": ri["build_eval_ms"] / max(1, ri["build_launches"]),
             "same_medoids": ri["medoids"].cpu().tolist() == r0["medoids"].cpu().tolist()}
         del Di, wsi
+    cb_D = D.to(torch.int32) if esize == 2 else D
+    if args.workload == "gmm_50000" and not args.no_k100:
+        del ws
+        line["k100"] = k100_block(args, km, dev, stream, peak)
     if rank == 0 and not args.no_cpu_baseline and world == 1:
-        line["cpu_baseline"] = cpu_baseline(D.to(torch.int32) if esize == 2 else D, spec,
-                                            args.cpu_seconds)
+        line["cpu_baseline"] = cpu_baseline(cb_D, spec, args.cpu_seconds)
     return line
 
 
-def cpu_baseline(D, spec, budget_s):
-    """The FP64 oracle on the host cores, on a bounded sample of the same
-    workload: BUILD gains of the first steps and FastPAM1 evaluation passes
-    from the BUILD medoids, as many as fit in about budget_s seconds."""
+def features_config(wl_name, spec, world):
+    """The workload description of the on-the-fly form (both arms)."""
+    return {"workload": wl_name + ": " + spec["desc"], "n": spec["n"], "d": spec["d"],
+            "k": spec["k"], "l2": "features (51 MB) L2-resident by design; no matrix",
+            "parallelism": "replicas" if world > 1 else "single GPU"}
+
+
+def matrix_config(wl_name, spec, world):
+    """The workload description of a matrix workload; both arms print the
+    same dict."""
+    n = spec["n"]
+    esize = 2 if spec["recipe"] == "manhattan_u16" else 4
+    return {"workload": wl_name + ": " + spec["desc"], "n": n, "k": spec["k"],
+            "matrix_bytes": n * n * esize,
+            "l2": "matrix larger than L2 (129 MB): no flush needed",
+            "parallelism": "replicas" if world > 1 else "single GPU"}
+
+
+def swap_pass_figures(n, k, esize, results):
+    """FastPAM1 evaluation passes of the timed runs: median (over runs of
+    each run's median pass) and mean pass time, and the roofline of the
+    median pass."""
+    med = float(np.median([r["eval_ms_median"] for r in results]))
+    mean = sum(r["eval_ms"] for r in results) / max(1, sum(r["eval_launches"] for r in results))
+    peak, _ = peaks()
+    gbs = (n - k) * n * esize / (med / 1e3) / 1e9
+    return {"median_ms": med, "mean_ms": mean,
+            "passes_per_run": int(results[-1]["iterations"]),
+            "point_evals_per_pass": (n - k) * n,
+            "median_pass_gbs": round(gbs, 1), "median_pass_frac_of_hbm": round(gbs / peak, 4)}
+
+
+def k100_block(args, km, dev, stream, peak):
+    """The k = 100 case of the metric: BUILD + FastPAM1 on the n = 20000
+    mixture (1.6 GB matrix), warm-up and timed runs as for the headline."""
+    import torch
+    spec = WORKLOADS["gmm_20000"]
+    D, _ = make_input("gmm_20000", dev)
+    n, k = spec["n"], spec["k"]
+    ws = km.workspace(n, k, km.KM_F32, km.options(profile=True), device=dev)
+    for _ in range(args.warmup):
+        km.run(D, k, ws=ws, profile=True, tune=args.tune, build_full=args.build_full)
+    torch.cuda.synchronize()
+    res, ms = [], []
+    for _ in range(args.steps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        res.append(km.run(D, k, ws=ws, profile=True, tune=args.tune,
+                          build_full=args.build_full))
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms.append(a.elapsed_time(b))
+    sw = swap_pass_figures(n, k, 4, res)
+    out = {"workload": "gmm_20000: " + spec["desc"], "n": n, "k": k,
+           "swap_point_evals_per_s": (n - k) * n / (sw["median_ms"] / 1e3),
+           "swap_pass": sw, "full_run_ms": float(np.mean(ms)),
+           "build_ms": res[-1]["build_ms"], "swap_iterations": res[-1]["iterations"],
+           "td": res[-1]["td"], "swap_geometry": int(res[-1]["swap_geometry"])}
+    del D, ws
+    torch.cuda.empty_cache()
+    return out
+
+
+def oracle_medoids(n, k):
+    """The medoid set the oracle's timed passes start from: k distinct points
+    drawn uniformly (fixed seed).  A pass's cost does not depend on which
+    medoids are current beyond the share of points near them."""
+    from paper_2008_05171_gb300 import workloads as wl
+    g = wl.rng_for(("bench-oracle-medoids", n, k))
+    return np.sort(g.choice(n, size=k, replace=False)).astype(np.int32)
+
+
+def cpu_baseline(D, spec, budget_s, pam=True):
+    """The FP64 oracle on the host cores on a bounded sample of the same
+    workload: FastPAM1 evaluation passes (Eq. (7), every non-medoid candidate
+    against all n points) over the same matrix, as many as fit in about
+    budget_s seconds (at least one); the value is the metric's point-evals
+    per second of those passes."""
     import oracle
     n, k = spec["n"], spec["k"]
-    Dh = D.cpu().numpy()
+    Dh = D.cpu().numpy() if hasattr(D, "cpu") else D
     threads = oracle.num_threads()
+    med = oracle_medoids(n, k)
     t0 = time.perf_counter()
-    evals = 0
-    prefix = []
-    steps = 0
-    while time.perf_counter() - t0 < budget_s / 2 and steps < k:
-        g = oracle.build_gains(Dh, prefix)
-        evals += (n - len(prefix)) * n
-        prefix.append(int(np.argmin(g)))
-        steps += 1
     passes = 0
-    chosen = set(prefix)
-    rest = [i for i in range(n) if i not in chosen][:k - len(prefix)]
-    med = np.array(prefix + rest, np.int32)
     while time.perf_counter() - t0 < budget_s or passes == 0:
         oracle.eval_swaps(Dh, med, method="fastpam1")
-        evals += (n - k) * n
         passes += 1
     dt = time.perf_counter() - t0
-    return {"value": evals / dt, "unit": "point-evals/s", "cores": threads,
-            "kind": "oracle",
-            "sample": "%d BUILD steps + %d FastPAM1 evaluation passes of the same "
-                      "n=%d k=%d matrix (FP64 C oracle, OpenMP over candidates), %.1f s"
-                      % (steps, passes, n, k, dt),
-            "pam_vs_fastpam1": pam_vs_fastpam1(Dh, med, threads)}
+    out = {"value": passes * (n - k) * n / dt, "unit": "point-evals/s", "cores": threads,
+           "kind": "oracle", "seconds": dt,
+           "sample": "%d FastPAM1 evaluation passes ((n-k)*n point-evals each) of the same "
+                     "n=%d k=%d matrix from a fixed uniform random medoid set (FP64 C "
+                     "oracle, OpenMP over candidates), %.1f s" % (passes, n, k, dt)}
+    if pam:
+        out["pam_vs_fastpam1"] = pam_vs_fastpam1(Dh, med, threads)
+    return out
 
 
 def pam_vs_fastpam1(Dh, med, threads, n_sub=4000):
@@ -913,7 +982,7 @@ def pam_vs_fastpam1(Dh, med, threads, n_sub=4000):
     return out
 
 
-BATCHED_METRIC = "SWAP dTD point-evals/sec + full PAM run time (k=100/200); % HBM roofline"
+BATCHED_METRIC = METRIC
 
 
 def batched_config(args, specs, arena_len, world):
@@ -1023,8 +1092,7 @@ def run_reference(args, rank, world):
             secs.append(cb.pop("seconds"))
         v = float(np.mean(vals[args.warmup:]))
         cb["value"] = v
-        return {"impl": "reference", "metric": "SWAP dTD point-evals/sec + full PAM run time "
-                "(k=100/200); % HBM roofline", "value": v, "unit": "point-evals/s",
+        return {"impl": "reference", "metric": METRIC, "value": v, "unit": "point-evals/s",
                 "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
                 "ms_per_step": 1e3 * float(np.mean(secs[args.warmup:])),
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -1045,8 +1113,7 @@ def run_reference(args, rank, world):
             secs.append(cb.pop("seconds"))
         v = float(np.mean(vals[args.warmup:]))
         cb["value"] = v
-        return {"impl": "reference", "metric": "SWAP dTD point-evals/sec + full PAM run time "
-                "(k=100/200); % HBM roofline", "value": v, "unit": "point-evals/s",
+        return {"impl": "reference", "metric": METRIC, "value": v, "unit": "point-evals/s",
                 "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
                 "ms_per_step": 1e3 * float(np.mean(secs[args.warmup:])),
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -1056,9 +1123,11 @@ def run_reference(args, rank, world):
                 "cpu_baseline": cb,
                 "e2e": {"value": v, "unit": "point-evals/s", "h2d_bytes_per_step": 0,
                         "d2h_bytes_per_step": 0}}
-    if args.workload.startswith("features"):
+    feat = args.workload.startswith("features")
+    spec_s = spec
+    if feat:
         # no n x n matrix exists in this form: time the oracle on a subsample
-        spec = dict(spec, n=8000)
+        spec_s = dict(spec, n=8000)
         X = X[:8000].astype(np.float64)
     dev = torch.device("cuda", 0) if torch.cuda.is_available() else torch.device("cpu")
     if X is None:
@@ -1067,24 +1136,32 @@ def run_reference(args, rank, world):
         D = wl.euclidean_f32_torch(X, dev)
     else:
         D = torch.from_numpy(wl.euclidean_f32(X))
+    Dh = D.cpu().numpy()
+    del D
+    # each step: as many FastPAM1 evaluation passes as fit in the budget
     budget = max(2.0, 60.0 / max(1, args.steps + args.warmup))
     for _ in range(args.warmup):
-        cpu_baseline(D, spec, budget / 4)
-    vals, secs = [], []
-    for _ in range(args.steps):
-        t0 = time.perf_counter()
-        cb = cpu_baseline(D, spec, budget)
-        secs.append(time.perf_counter() - t0)
+        cpu_baseline(Dh, spec_s, budget / 4, pam=False)
+    vals, secs, evals = [], [], 0
+    for i in range(args.steps):
+        cb = cpu_baseline(Dh, spec_s, budget, pam=(i == args.steps - 1))
+        secs.append(cb.pop("seconds"))
         vals.append(cb["value"])
     v = float(np.mean(vals))
     cb["value"] = v
-    return {"impl": "reference", "metric": "SWAP dTD point-evals/sec + full PAM run time "
-            "(k=100/200); % HBM roofline", "value": v, "unit": "point-evals/s",
+    if feat:
+        cb["sample"] = "first 8000 points of the same features as an FP32 matrix; " + \
+            cb["sample"]
+        config = features_config(args.workload, spec, world)
+    else:
+        config = matrix_config(args.workload, spec, world)
+    return {"impl": "reference", "metric": METRIC, "value": v, "unit": "point-evals/s",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * float(np.mean(secs)), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": args.workload + ": " + spec["desc"], "n": spec["n"],
-                       "k": spec["k"]},
+            "config": config,
+            "value_definition": "(n-k)*n point-evals per FastPAM1 evaluation pass of the FP64 "
+                                "C oracle / pass time, on the host cores",
             "cpu_baseline": cb,
             "e2e": {"value": v, "unit": "point-evals/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
@@ -1096,9 +1173,11 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="gmm_20000", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="gmm_50000", choices=sorted(WORKLOADS))
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-k100", action="store_true",
+                    help="gmm_50000: skip the k=100 (gmm_20000) block")
     ap.add_argument("--build-full", action="store_true",
                     help="matrix workloads: time the plain BUILD pass (every candidate "
                          "row each step) instead of the incremental BUILD")

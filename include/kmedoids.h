@@ -176,6 +176,16 @@ typedef struct km_options {
                              Both choose the same medoids up to FP32
                              rounding of the plain pass's sums (identical
                              for integer data). */
+  int64_t wait_limit_ns;  /* limit of every bounded device wait of the call
+                             (pipeline stages, consumer barriers, the grid
+                             barrier of the eager kernel), in nanoseconds;
+                             0 = 4 s.  A wait that runs out makes the call
+                             return KM_E_TIMEOUT (the kernels stop, let
+                             their own copies land and release tensor
+                             memory; the workspace is then undefined, the
+                             matrix untouched).  Negative: KM_E_INVALID.
+                             A limit far below a kernel's normal wait times
+                             turns ordinary calls into timeouts. */
 } km_options;
 
 /* Results, filled on the HOST before the call returns. */
@@ -215,6 +225,8 @@ typedef struct km_result {
                               pass over the n points */
   int64_t build_rows;      /* rows of D (n elements each) the BUILD
                               evaluation kernels streamed */
+  double eval_ms_median;   /* profile != 0: median over the SWAP evaluation
+                              launches of their device time */
 } km_result;
 
 /* Parameters of a matrix-form geometry table entry (1..16, as reported in
@@ -491,6 +503,24 @@ km_status kmedoids_eval_swaps_static(const void *D, int32_t dtype, int64_t n,
                                      double *cand_delta, int32_t *cand_slot,
                                      double *best_delta, int32_t *best_slot,
                                      int32_t *best_cand, void *stream);
+
+/* Self-test of the bounded device waits (failure detection; the paper has
+ * no counterpart).  Launches a kernel whose wait can never be satisfied,
+ * built on the same wait routines the pipelined kernels use:
+ *   kind 0  an mbarrier phase that nothing completes (the stage waits of
+ *           the streaming and on-the-fly kernels);
+ *   kind 1  a consumer barrier one of whose two warps never arrives;
+ *   kind 2  the grid barrier of the eager kernel, over two CTAs of which
+ *           one never arrives.
+ * Each wait gives up after limit_ns (1 .. 10^10 ns; 0 = the default 4 s),
+ * records KM_E_TIMEOUT in the device state record at the start of ws (a
+ * DEVICE buffer of at least 512 bytes, 256-byte aligned, caller-owned) and
+ * returns; nothing is left in flight and the CUDA context stays usable.
+ * The call synchronises the stream and returns the status the device
+ * recorded: KM_E_TIMEOUT when the wait ran out as designed (with the limit
+ * in kmedoids_last_error()), KM_E_INVALID for a bad argument. */
+km_status kmedoids_wait_selftest(int32_t kind, int64_t limit_ns, void *ws,
+                                 size_t ws_bytes, void *stream);
 
 /* Thread-local description of the last failure ("" if none). */
 const char *kmedoids_last_error(void);

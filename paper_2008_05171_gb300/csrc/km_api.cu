@@ -7,6 +7,7 @@
 // file only orders launches and reads the device state record between
 // batches of passes.
 #include <cmath>
+#include <algorithm>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -161,6 +162,7 @@ km_status check_common(const void* D, int32_t dtype, int64_t n, int64_t ld, int3
     return fail(KM_E_INVALID, "rows_per_tile must be 0, 1, 2, 4, 8 or 16");
   if (c->opt.trace_capacity < 0) return fail(KM_E_INVALID, "trace_capacity < 0");
   if (c->opt.tune < -1 || c->opt.tune > 16) return fail(KM_E_INVALID, "tune must be in -1..16");
+  if (c->opt.wait_limit_ns < 0) return fail(KM_E_INVALID, "wait_limit_ns must be >= 0");
   if (!make_ws(n, k, &c->opt, &c->L)) return fail(KM_E_INVALID, "invalid sizes");
   if (ws_bytes < c->L.total)
     return fail(KM_E_WORKSPACE, "workspace too small: %zu < %zu bytes", ws_bytes, c->L.total);
@@ -278,7 +280,10 @@ struct Timer {
 km_status read_state(const Ctx& c, KmState* h) {
   KM_CUDA(cudaMemcpyAsync(h, c.st(), sizeof(KmState), cudaMemcpyDeviceToHost, c.s));
   KM_CUDA(cudaStreamSynchronize(c.s));
-  if (h->error) return fail((km_status)h->error, "device reported status %d (a wait timed out)", h->error);
+  if (h->error == KM_E_TIMEOUT)
+    return fail(KM_E_TIMEOUT, "a device wait gave up after its limit of %llu ns",
+                h->wait_ns ? h->wait_ns : kWaitLimitNs);
+  if (h->error) return fail((km_status)h->error, "device reported status %d", h->error);
   return KM_OK;
 }
 
@@ -286,6 +291,7 @@ km_status reset_state(const Ctx& c) {
   KmState h;
   memset(&h, 0, sizeof(h));
   h.last = -1;
+  h.wait_ns = (unsigned long long)c.opt.wait_limit_ns;
   KM_CUDA(cudaMemcpyAsync(c.st(), &h, sizeof(h), cudaMemcpyHostToDevice, c.s));
   return KM_OK;
 }
@@ -701,14 +707,22 @@ km_status finish(Ctx& c, KmState* h, int32_t* medoids_out, int32_t* labels_out, 
     res->td_i64 = (c.dtype != KM_F32) ? td_i : 0;
     double sum = 0.0;
     int cnt = 0;
+    std::vector<double> per;
     for (auto& p : ev_swap) {
       if (cnt >= h->iter) break;
-      sum += tm.ms(p.first, p.second);
+      const double v = tm.ms(p.first, p.second);
+      sum += v;
+      per.push_back(v);
       ++cnt;
     }
     if (tm.on) {
       res->eval_ms = sum;
       res->eval_launches = cnt;
+      if (!per.empty()) {
+        std::sort(per.begin(), per.end());
+        const size_t m = per.size() / 2;
+        res->eval_ms_median = (per.size() % 2) ? per[m] : 0.5 * (per[m - 1] + per[m]);
+      }
     }
   }
   return KM_OK;

@@ -16,7 +16,7 @@ constexpr int kConsThreads = kConsWarps * 32;  // each owns 4 columns
 constexpr int kThreads = kConsThreads + 32;    // + one producer warp
 constexpr int kMaxGrid = 1024;                 // workspace bound on CTAs
 constexpr int kMaxRows = 16;                   // largest candidate tile
-constexpr unsigned long long kWaitLimitNs = 4000000000ull;  // 4 s
+constexpr unsigned long long kWaitLimitNs = 4000000000ull;  // 4 s: the default limit
 
 static_assert(kConsThreads * 4 == kChunk, "4 columns per consumer thread");
 
@@ -63,8 +63,17 @@ struct KmState {
   long long win_len;        // FasterPAM / FastCLARANS: next window length
   unsigned bar[2];          // grid barrier of the eager kernel: count, generation
   unsigned check_flags;     // input check: 1 asymmetric, 2 diagonal, 4 value
+  unsigned pad1;
+  unsigned long long wait_ns;  // limit of every bounded wait (0: kWaitLimitNs)
 };
 static_assert(sizeof(KmState) <= 512, "the workspaces reserve 512 bytes for the state record");
+
+// The limit of the bounded waits of a call (set by the host in the state
+// record; 0 selects the default).
+__device__ __forceinline__ unsigned long long wait_limit(const KmState* st) {
+  const unsigned long long w = st->wait_ns;
+  return w ? w : kWaitLimitNs;
+}
 
 // Trace record of an applied swap.
 struct TraceRec {
@@ -277,14 +286,17 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
 }
 
 // Wait for the phase with the given parity to complete.  Gives up after
-// kWaitLimitNs (returns false) or as soon as *abort becomes nonzero.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort) {
+// limit_ns (returns false) or as soon as *abort becomes nonzero.  The waits
+// that let a CTA's own bulk copies land before it exits keep the default
+// limit: those copies complete whatever the caller's limit is.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort,
+                                          unsigned long long limit_ns = kWaitLimitNs) {
   if (mbar_try_wait(bar, parity)) return true;
   const unsigned long long t0 = globaltimer();
   while (true) {
     if (mbar_try_wait(bar, parity)) return true;
     if (*abort) return false;
-    if (globaltimer() - t0 > kWaitLimitNs) return false;
+    if (globaltimer() - t0 > limit_ns) return false;
   }
 }
 
@@ -302,13 +314,51 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
 // loop), built on an mbarrier with one arrival per warp so that the wait is
 // bounded like every other wait.  `phase` is the calling thread's copy of
 // the barrier phase.  Returns false when the wait gave up.
-__device__ __forceinline__ bool cons_sync(uint64_t* bar, uint32_t& phase, volatile int* abort) {
+__device__ __forceinline__ bool cons_sync(uint64_t* bar, uint32_t& phase, volatile int* abort,
+                                          unsigned long long limit_ns = kWaitLimitNs) {
   __syncwarp();
   if ((threadIdx.x & 31) == 0) mbar_arrive(bar);
-  const bool ok = mbar_wait(bar, phase, abort);
+  const bool ok = mbar_wait(bar, phase, abort, limit_ns);
   phase ^= 1u;
   __syncwarp();
   return ok;
+}
+
+// Grid-wide barrier over co-resident CTAs: arrival counter + generation.
+// Thread 0 of each CTA arrives; all but the last spin on the generation
+// word.  Returns false (in every thread of the CTA) when the wait exceeded
+// limit_ns -- then st->error = kErrTimeout -- or another CTA had already
+// failed.
+__device__ __forceinline__ bool grid_barrier(unsigned* count, unsigned* gen, KmState* st,
+                                             int* s_ok, unsigned long long limit_ns) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    const unsigned g = atomicAdd(gen, 0u);
+    __threadfence();
+    if (atomicAdd(count, 1u) == gridDim.x - 1) {
+      atomicExch(count, 0u);
+      __threadfence();
+      atomicAdd(gen, 1u);
+    } else {
+      const unsigned long long t0 = globaltimer();
+      while (atomicAdd(gen, 0u) == g) {
+        if (*(volatile int*)&st->error) {
+          ok = 0;
+          break;
+        }
+        if (globaltimer() - t0 > limit_ns) {
+          atomicExch(&st->error, kErrTimeout);
+          ok = 0;
+          break;
+        }
+      }
+    }
+    __threadfence();
+    *s_ok = ok;
+  }
+  __syncthreads();
+  return *s_ok != 0;
 }
 
 __device__ __forceinline__ float4 lds4(const float* p) { return *reinterpret_cast<const float4*>(p); }

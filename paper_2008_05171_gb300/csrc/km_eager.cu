@@ -43,39 +43,6 @@ struct V4e<int32_t> {
   using type = int4;
 };
 
-// Grid-wide barrier over co-resident CTAs: arrival counter + generation.
-// Returns false when the wait exceeded kWaitLimitNs or another CTA failed.
-__device__ bool grid_barrier(unsigned* count, unsigned* gen, KmState* st, int* s_ok) {
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    int ok = 1;
-    const unsigned g = atomicAdd(gen, 0u);
-    __threadfence();
-    if (atomicAdd(count, 1u) == gridDim.x - 1) {
-      atomicExch(count, 0u);
-      __threadfence();
-      atomicAdd(gen, 1u);
-    } else {
-      const unsigned long long t0 = globaltimer();
-      while (atomicAdd(gen, 0u) == g) {
-        if (*(volatile int*)&st->error) {
-          ok = 0;
-          break;
-        }
-        if (globaltimer() - t0 > kWaitLimitNs) {
-          atomicExch(&st->error, kErrTimeout);
-          ok = 0;
-          break;
-        }
-      }
-    }
-    __threadfence();
-    *s_ok = ok;
-  }
-  __syncthreads();
-  return *s_ok != 0;
-}
-
 constexpr int kEU = 8;  // row loads (4 elements each) per thread in flight in the window loop
 
 // Elements 4q .. 4q+3 of a matrix row, streamed (read once per window).
@@ -159,6 +126,7 @@ __global__ void __launch_bounds__(kEThreads, 1) k_eager(const EagerArgs a) {
 
   KmState* st = a.st;
   if (*(volatile int*)&st->done || *(volatile int*)&st->error) return;
+  const unsigned long long wlim = wait_limit(st);
   const int n = a.n, k = a.k, f = a.fshift;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int Gn = gridDim.x;
@@ -335,7 +303,7 @@ __global__ void __launch_bounds__(kEThreads, 1) k_eager(const EagerArgs a) {
       }
       __syncthreads();
     }
-    if (!grid_barrier(a.bar, a.bar + 1, st, &s_ok)) return;
+    if (!grid_barrier(a.bar, a.bar + 1, st, &s_ok, wlim)) return;
 
     // ------------------------------------------------------- decision
     // first improving position of the window (all CTAs, same result)
@@ -548,7 +516,7 @@ __global__ void __launch_bounds__(kEThreads, 1) k_eager(const EagerArgs a) {
     book_d += dlt;
     book_i += (long long)dlt;
     rb ^= 1;
-    if (!grid_barrier(a.bar, a.bar + 1, st, &s_ok)) return;
+    if (!grid_barrier(a.bar, a.bar + 1, st, &s_ok, wlim)) return;
   }
 
   if (blockIdx.x == 0 && tid == 0) {

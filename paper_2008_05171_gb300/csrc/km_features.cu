@@ -204,6 +204,7 @@ __global__ void __launch_bounds__(kFeatThreads, 1) k_feat_pass(const FeatArgs a)
   extern __shared__ __align__(1024) unsigned char smem[];
   KmState* st = a.st;
   if (st->done || st->error) return;
+  const unsigned long long wlim = wait_limit(st);
   const int n = a.n, d = a.dk, k = a.k;  // d: the operands' K dimension
   const FeatLayout L = feat_layout(d, k);
   const int bst = L.bst;
@@ -291,7 +292,7 @@ __global__ void __launch_bounds__(kFeatThreads, 1) k_feat_pass(const FeatArgs a)
         const int t = (tile < (unsigned)ntiles) ? (int)tile : -1;
         // publish a tile only after the epilogue finished the previous one:
         // no waiter on a_full can fall two phases behind, and sA is free
-        if (seq > 0 && !mbar_wait(tile_done, (uint32_t)((seq - 1) & 1), abort_flag)) {
+        if (seq > 0 && !mbar_wait(tile_done, (uint32_t)((seq - 1) & 1), abort_flag, wlim)) {
           ok = false;
           break;
         }
@@ -305,7 +306,7 @@ __global__ void __launch_bounds__(kFeatThreads, 1) k_feat_pass(const FeatArgs a)
         for (int b = 0; b < nblocks; ++b, ++gb) {
           const int s = (int)(gb % bst);
           const uint32_t ph = (uint32_t)((gb / bst) & 1);
-          if (!mbar_wait(&b_empty[s], ph ^ 1u, abort_flag)) {
+          if (!mbar_wait(&b_empty[s], ph ^ 1u, abort_flag, wlim)) {
             ok = false;
             break;
           }
@@ -316,7 +317,7 @@ __global__ void __launch_bounds__(kFeatThreads, 1) k_feat_pass(const FeatArgs a)
                    &b_full[s]);
           const int ms = (int)(gb % kFeatMetaStages);
           const uint32_t mp = (uint32_t)((gb / kFeatMetaStages) & 1);
-          if (!mbar_wait(&m_empty[ms], mp ^ 1u, abort_flag)) {
+          if (!mbar_wait(&m_empty[ms], mp ^ 1u, abort_flag, wlim)) {
             ok = false;
             break;
           }
@@ -351,7 +352,7 @@ __global__ void __launch_bounds__(kFeatThreads, 1) k_feat_pass(const FeatArgs a)
       long long gb = 0;
       long long issued = 0;  // blocks with MMAs in flight on the accumulators
       for (int seq = 0;; ++seq) {
-        if (!mbar_wait(a_full, (uint32_t)(seq & 1), abort_flag)) break;
+        if (!mbar_wait(a_full, (uint32_t)(seq & 1), abort_flag, wlim)) break;
         const int t = tslot[seq & 1];
         if (t < 0) break;
         tc_fence_after();
@@ -359,8 +360,8 @@ __global__ void __launch_bounds__(kFeatThreads, 1) k_feat_pass(const FeatArgs a)
         for (int b = 0; b < nblocks; ++b, ++gb) {
           const int s = (int)(gb % bst);
           const int buf = (int)(gb % kFeatAccBufs);
-          if (!mbar_wait(&b_full[s], (uint32_t)((gb / bst) & 1), abort_flag) ||
-              !mbar_wait(&acc_empty[buf], (uint32_t)(((gb / kFeatAccBufs) & 1) ^ 1), abort_flag)) {
+          if (!mbar_wait(&b_full[s], (uint32_t)((gb / bst) & 1), abort_flag, wlim) ||
+              !mbar_wait(&acc_empty[buf], (uint32_t)(((gb / kFeatAccBufs) & 1) ^ 1), abort_flag, wlim)) {
             ok = false;
             break;
           }
@@ -395,7 +396,7 @@ __global__ void __launch_bounds__(kFeatThreads, 1) k_feat_pass(const FeatArgs a)
     long long gb = 0;
     bool ok = true;
     for (int seq = 0; ok; ++seq) {
-      if (!mbar_wait(a_full, (uint32_t)(seq & 1), abort_flag)) {
+      if (!mbar_wait(a_full, (uint32_t)(seq & 1), abort_flag, wlim)) {
         ok = false;
         break;
       }
@@ -411,8 +412,8 @@ __global__ void __launch_bounds__(kFeatThreads, 1) k_feat_pass(const FeatArgs a)
       for (int b = 0; b < nblocks; ++b, ++gb) {
         const int buf = (int)(gb % kFeatAccBufs);
         const int ms = (int)(gb % kFeatMetaStages);
-        if (!mbar_wait(&acc_full[buf], (uint32_t)((gb / kFeatAccBufs) & 1), abort_flag) ||
-            !mbar_wait(&m_full[ms], (uint32_t)((gb / kFeatMetaStages) & 1), abort_flag)) {
+        if (!mbar_wait(&acc_full[buf], (uint32_t)((gb / kFeatAccBufs) & 1), abort_flag, wlim) ||
+            !mbar_wait(&m_full[ms], (uint32_t)((gb / kFeatMetaStages) & 1), abort_flag, wlim)) {
           ok = false;
           break;
         }
@@ -491,7 +492,7 @@ __global__ void __launch_bounds__(kFeatThreads, 1) k_feat_pass(const FeatArgs a)
       if (!ok) break;
       // ------------------------------------------------------ tile finished
       if (group > 0) red[(group - 1) * kTileM + r] = (double)ks_ - (double)kc_;
-      if (!cons_sync(ep_bar, eph, abort_flag)) {
+      if (!cons_sync(ep_bar, eph, abort_flag, wlim)) {
         ok = false;
         break;
       }
@@ -526,7 +527,7 @@ __global__ void __launch_bounds__(kFeatThreads, 1) k_feat_pass(const FeatArgs a)
           }
         }
       }
-      if (!cons_sync(ep_bar, eph, abort_flag)) {
+      if (!cons_sync(ep_bar, eph, abort_flag, wlim)) {
         ok = false;
         break;
       }
@@ -942,6 +943,9 @@ struct FCtx {
 km_status f_read(FCtx& c, KmState* h) {
   FK(cudaMemcpyAsync(h, c.st(), sizeof(KmState), cudaMemcpyDeviceToHost, c.s));
   FK(cudaStreamSynchronize(c.s));
+  if (h->error == KM_E_TIMEOUT)
+    return ffail(KM_E_TIMEOUT, "a device wait gave up after its limit of %llu ns",
+                 h->wait_ns ? h->wait_ns : kWaitLimitNs);
   if (h->error) return ffail((km_status)h->error, "device reported status %d", h->error);
   return KM_OK;
 }
@@ -950,6 +954,7 @@ km_status f_reset(FCtx& c) {
   KmState h;
   memset(&h, 0, sizeof(h));
   h.last = -1;
+  h.wait_ns = (unsigned long long)c.opt.wait_limit_ns;
   FK(cudaMemcpyAsync(c.st(), &h, sizeof(h), cudaMemcpyHostToDevice, c.s));
   return KM_OK;
 }
@@ -1014,6 +1019,7 @@ km_status run_features(bool do_build, bool do_swap, const void* X, int64_t n, in
     return ffail(KM_E_INVALID, "X must be 16-byte and ws 256-byte aligned");
   if (ws_bytes < c.L.total)
     return ffail(KM_E_WORKSPACE, "workspace too small: %zu < %zu", ws_bytes, c.L.total);
+  if (c.opt.wait_limit_ns < 0) return ffail(KM_E_INVALID, "wait_limit_ns must be >= 0");
   if (c.opt.max_iter <= 0) c.opt.max_iter = 100 * k + 100;
   c.ws = static_cast<unsigned char*>(ws);
   c.s = static_cast<cudaStream_t>(stream);

@@ -182,6 +182,7 @@ __global__ void __launch_bounds__(kThreads, MINB) k_stream(const StreamArgs a) {
 
   KmState* st = a.st;
   if (st->done || st->error) return;  // uniform for all CTAs of this launch
+  const unsigned long long wlim = wait_limit(st);
 
   const int n = a.n, k = a.k, f = a.fshift;
   const int fp2 = (MODE == kModeSwap && a.flavour == kFastPAM2);
@@ -305,7 +306,7 @@ __global__ void __launch_bounds__(kThreads, MINB) k_stream(const StreamArgs a) {
           if (nr == 0) break;
         }
         for (int j = 0; j < nchunks; ++j) {
-          if (!mbar_wait(&empty[s], ph ^ 1, abort_flag)) {
+          if (!mbar_wait(&empty[s], ph ^ 1, abort_flag, wlim)) {
             ok = false;
             break;
           }
@@ -345,7 +346,7 @@ __global__ void __launch_bounds__(kThreads, MINB) k_stream(const StreamArgs a) {
           }
         }
       }
-      if (ok && mbar_wait(&empty[s], ph ^ 1, abort_flag)) {
+      if (ok && mbar_wait(&empty[s], ph ^ 1, abort_flag, wlim)) {
         StageHdr* h = reinterpret_cast<StageHdr*>(stages + (size_t)s * L.stage_bytes);
         h->nrows = 0;
         mbar_arrive(&full[s]);
@@ -381,7 +382,7 @@ __global__ void __launch_bounds__(kThreads, MINB) k_stream(const StreamArgs a) {
   uint32_t cph = 0;  // consumer barrier phase
 #define KM_CSYNC()                              \
   do {                                          \
-    if (!cons_sync(cbar, cph, abort_flag)) {    \
+    if (!cons_sync(cbar, cph, abort_flag, wlim)) {\
       abort_flag[0] = 1;                        \
       atomicExch(&st->error, kErrTimeout);      \
       return;                                   \
@@ -390,7 +391,7 @@ __global__ void __launch_bounds__(kThreads, MINB) k_stream(const StreamArgs a) {
   int s = 0;
   uint32_t ph = 0;
   while (true) {
-    if (!mbar_wait(&full[s], ph, abort_flag)) {
+    if (!mbar_wait(&full[s], ph, abort_flag, wlim)) {
       abort_flag[0] = 1;
       atomicExch(&st->error, kErrTimeout);
       return;

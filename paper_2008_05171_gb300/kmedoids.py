@@ -29,7 +29,7 @@ EXPORTS = ["km_default_options", "kmedoids_workspace_size", "kmedoids_build",
            "kmedoids_batched_distances", "kmedoids_run_batched",
            "kmedoids_swap_batched", "kmedoids_clara_workspace_size", "kmedoids_clara",
            "kmedoids_geometry_info", "kmedoids_init_weighted",
-           "kmedoids_init_lab"]
+           "kmedoids_init_lab", "kmedoids_wait_selftest"]
 
 
 class KmError(RuntimeError):
@@ -51,7 +51,7 @@ class km_options(ctypes.Structure):
                 ("build_gains", ctypes.POINTER(ctypes.c_double)),
                 ("draws", ctypes.c_void_p), ("draws_len", ctypes.c_int64),
                 ("maxneighbor", ctypes.c_int64), ("check_input", ctypes.c_int32),
-                ("build_full", ctypes.c_int32)]
+                ("build_full", ctypes.c_int32), ("wait_limit_ns", ctypes.c_int64)]
 
 
 class km_result(ctypes.Structure):
@@ -68,7 +68,7 @@ class km_result(ctypes.Structure):
                 ("kernel_launches", ctypes.c_int64),
                 ("best_sample", ctypes.c_int32), ("swap_geometry", ctypes.c_int16),
                 ("build_geometry", ctypes.c_int16), ("evaluated", ctypes.c_int64),
-                ("build_rows", ctypes.c_int64)]
+                ("build_rows", ctypes.c_int64), ("eval_ms_median", ctypes.c_double)]
 
 
 _LOCK = threading.Lock()
@@ -137,6 +137,8 @@ def load(path: str = LIB_PATH):
         lib.kmedoids_init_lab.argtypes = [P, i32, i64, i64, i32, i32, P, P, P, P, sz,
                                           P]
         lib.kmedoids_init_lab.restype = i32
+        lib.kmedoids_wait_selftest.argtypes = [i32, i64, P, sz, P]
+        lib.kmedoids_wait_selftest.restype = i32
         lib.kmedoids_last_error.restype = ctypes.c_char_p
         lib.kmedoids_version.restype = ctypes.c_char_p
         _LIB = lib
@@ -181,13 +183,14 @@ def _stream():
 
 def options(variant="fastpam1", max_iter=0, tol=0.0, fastpam2_tol=0.0,
             rows_per_tile=0, profile=False, trace=0, tune=0, draws=None,
-            maxneighbor=0, check_input=False, build_full=False):
+            maxneighbor=0, check_input=False, build_full=False, wait_limit_ns=0):
     """km_options.  draws: int32 CUDA tensor of candidate draws (FastCLARANS);
     the caller keeps it alive for the call.  build_full: every BUILD step
     streams all candidate rows instead of updating the gains
-    incrementally."""
+    incrementally.  wait_limit_ns: limit of the device waits (0 = 4 s)."""
     o = km_options()
     load().km_default_options(ctypes.byref(o))
+    o.wait_limit_ns = int(wait_limit_ns)
     if draws is not None:
         o.draws = ctypes.c_void_p(draws.data_ptr())
         o.draws_len = int(draws.numel())
@@ -602,3 +605,16 @@ def geometry_info(geometry):
 
 def version() -> str:
     return load().kmedoids_version().decode()
+
+
+def wait_selftest(kind, limit_ns, device=None):
+    """kmedoids_wait_selftest: a kernel waits on something that never
+    happens (kind 0 an mbarrier phase, 1 a consumer barrier, 2 the grid
+    barrier) until limit_ns runs out.  Returns (status, message); the
+    expected status is KM_E_TIMEOUT (5)."""
+    torch = _torch()
+    lib = load()
+    ws = torch.zeros(512, dtype=torch.uint8, device=device or "cuda")
+    st = lib.kmedoids_wait_selftest(int(kind), int(limit_ns), ctypes.c_void_p(ws.data_ptr()),
+                                    ws.numel(), _stream())
+    return st, lib.kmedoids_last_error().decode()

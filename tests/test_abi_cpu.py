@@ -112,6 +112,21 @@ def test_invalid_arguments_of_the_newer_entry_points(lib):
     bad = km.options(variant="fastpam2")
     assert lib.kmedoids_run_batched(P(fake), P(fake), 1, P(fake), P(fake), ctypes.byref(bad),
                                     P(fake), 1 << 20, None) == 7
+    # a negative wait limit is rejected by every form that waits
+    neg = km.options(wait_limit_ns=-1)
+    assert lib.kmedoids_run(P(fake), km.KM_F32, 100, 100, 10, P(fake), None, ctypes.byref(neg),
+                            ctypes.byref(res), P(fake), 1 << 30, None) == 1
+    assert b"wait_limit_ns" in lib.kmedoids_last_error()
+    assert lib.kmedoids_run_features(P(fake), 1000, 32, 32, 10, P(fake), None,
+                                     ctypes.byref(neg), ctypes.byref(res), P(fake), 1 << 30,
+                                     None) == 1
+    # wait self-test: kind, limit and workspace checked before any launch
+    assert lib.kmedoids_wait_selftest(3, 1000, P(fake), 512, None) == 1
+    assert lib.kmedoids_wait_selftest(0, -1, P(fake), 512, None) == 1
+    assert lib.kmedoids_wait_selftest(0, 10 ** 11, P(fake), 512, None) == 1
+    assert lib.kmedoids_wait_selftest(0, 1000, P(fake), 256, None) == 1
+    assert lib.kmedoids_wait_selftest(0, 1000, P(fake + 8), 512, None) == 1
+    assert lib.kmedoids_wait_selftest(0, 1000, None, 512, None) == 1
 
 
 def _c_struct_fields(name):
