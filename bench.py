@@ -242,8 +242,9 @@ def run_features(args, rank, world, local_rank):
     torch.cuda.synchronize()
     ck = clocks.stop()
     total_ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in ev), world, dev)
-    evals = [sum(evals_of(n, k, r)) for r in results]
-    value = world * sum(evals) / (total_ms / 1e3)
+    sw = swap_pass_figures(n, k, None, results)
+    pass_ms = max_over_ranks(sw["median_ms"], world, dev)
+    value = world * (n - k) * n / (pass_ms / 1e3)
     r0 = results[-1]
     peak, pk = tensor_peak()
     flops = 2.0 * n * n * d  # Gram of all candidates x all points, one pass
@@ -275,7 +276,8 @@ def run_features(args, rank, world, local_rank):
         b.record(stream)
         torch.cuda.synchronize()
         e_ms = a.elapsed_time(b)
-        e2e = {"value": world * sum(evals_of(n, k, r)) / (e_ms / 1e3), "unit": "point-evals/s",
+        e2e = {"value": world * r["iterations"] * (n - k) * n / (e_ms / 1e3),
+               "unit": "point-evals/s", "steps": 1,
                "h2d_bytes_per_step": int(X.numel() * 2),
                "d2h_bytes_per_step": int(4 * k + 4 * n)}
         del med_h, lab_h
@@ -286,6 +288,9 @@ def run_features(args, rank, world, local_rank):
         "scaling": "weak", "vs_baseline": None, "dtype": "bf16 Gram / f32 (FP64 TD)",
         "data": "synthetic",
         "config": features_config(args.workload, spec, world),
+        "value_definition": "(n-k)*n point-evals per FastPAM1 SWAP pass / median pass time; "
+                            "ms_per_step = the whole BUILD + SWAP run",
+        "swap_pass": sw,
         "full_run_ms": total_ms / args.steps, "swap_iterations": r0["iterations"],
         "swaps": r0["swaps"], "swap_iter_ms": s_ms, "build_step_ms": b_ms, "td": r0["td"],
         "kernel_ms_per_step": {"build_eval": r0["build_eval_ms"], "swap_eval": r0["eval_ms"],
@@ -302,6 +307,8 @@ def run_features(args, rank, world, local_rank):
         td_ref = oracle.td_points(np.asarray(Xh, np.float32), r0["medoids"].cpu().numpy())
         line["td_fp64_oracle"] = td_ref
         line["td_rel_error"] = abs(r0["td"] - td_ref) / td_ref
+    if world == 1 and not args.no_matrix_compare:
+        line["fp32_matrix_path"] = matrix_path_beside(Xh, k, r0, dev, stream)
     if rank == 0 and not args.no_cpu_baseline and world == 1:
         ns = 8000
         Ds = torch.from_numpy(wl.euclidean_f32(Xh[:ns].astype(np.float64)))
@@ -855,6 +862,68 @@ def run_ours(args, rank, world, local_rank):
     return line
 
 
+def matrix_path_beside(Xh, k, rf, dev, stream):
+    """The plain FP32 matrix path on the same points: the n x n matrix of
+    FP64 direct-difference distances rounded once to FP32 (torch cdist
+    without the Gram shortcut, in row blocks; 160 GB at n = 200000), then
+    kmedoids_run (BUILD + FastPAM1) on it.  Reports whether the feature
+    form ended at the same medoids and the TD of both medoid sets on the
+    same matrix."""
+    import torch
+    import paper_2008_05171_gb300.kmedoids as km
+    n = Xh.shape[0]
+    ld = (n + 3) // 4 * 4
+    t0 = time.perf_counter()
+    X64 = torch.from_numpy(np.asarray(Xh, np.float64)).to(dev)
+    D = torch.zeros((n, ld), dtype=torch.float32, device=dev)
+    B = 2048
+    for i0 in range(0, n, B):
+        i1 = min(n, i0 + B)
+        D[i0:i1, :n] = torch.cdist(X64[i0:i1], X64, p=2.0,
+                                   compute_mode="donot_use_mm_for_euclid_dist").float()
+    # bitwise symmetric with a zero diagonal, as the matrix form assumes
+    T = 8192
+    for i0 in range(0, n, T):
+        i1 = min(n, i0 + T)
+        for j0 in range(i0, n, T):
+            j1 = min(n, j0 + T)
+            blk = D[i0:i1, j0:j1]
+            if j0 == i0:
+                up = torch.triu(blk, 1)
+                blk.copy_(up + up.T)
+            else:
+                D[j0:j1, i0:i1] = blk.T
+    del X64
+    torch.cuda.synchronize()
+    gen_s = time.perf_counter() - t0
+    ws = km.workspace(n, k, km.KM_F32, km.options(profile=True), device=dev)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    rm = km.run(D, k, n=n, ws=ws, labels=True, profile=True, tune=0)
+    b.record(stream)
+    torch.cuda.synchronize()
+    mf = rf["medoids"].cpu().numpy()
+    mm = rm["medoids"].cpu().numpy()
+    # TD of the feature form's medoids on the same FP32 matrix
+    mf_t = torch.from_numpy(mf.astype(np.int64)).to(dev)
+    td_f = 0.0
+    for i0 in range(0, n, 8192):
+        td_f += float(D[i0:i0 + 8192, :n].index_select(1, mf_t).min(dim=1).values
+                      .double().sum().item())
+    out = {"matrix_bytes": int(n) * ld * 4, "matrix_build_s": round(gen_s, 2),
+           "run_ms": a.elapsed_time(b), "swap_pass_ms": rm["eval_ms_median"],
+           "build_ms": rm["build_ms"], "swap_iterations": rm["iterations"],
+           "swaps": rm["swaps"], "td_matrix_path": rm["td"],
+           "td_feature_medoids_on_matrix": td_f,
+           "same_medoids": sorted(mf.tolist()) == sorted(mm.tolist()),
+           "same_slot_order": mf.tolist() == mm.tolist(),
+           "td_rel_diff": abs(td_f - rm["td"]) / rm["td"],
+           "medoids_differing": int(len(set(mf.tolist()) ^ set(mm.tolist())) // 2)}
+    del D, ws
+    torch.cuda.empty_cache()
+    return out
+
+
 def features_config(wl_name, spec, world):
     """The workload description of the on-the-fly form (both arms)."""
     return {"workload": wl_name + ": " + spec["desc"], "n": spec["n"], "d": spec["d"],
@@ -875,16 +944,18 @@ def matrix_config(wl_name, spec, world):
 
 def swap_pass_figures(n, k, esize, results):
     """FastPAM1 evaluation passes of the timed runs: median (over runs of
-    each run's median pass) and mean pass time, and the roofline of the
-    median pass."""
+    each run's median pass) and mean pass time, and (matrix form: esize
+    bytes per element) the HBM roofline of the median pass."""
     med = float(np.median([r["eval_ms_median"] for r in results]))
     mean = sum(r["eval_ms"] for r in results) / max(1, sum(r["eval_launches"] for r in results))
-    peak, _ = peaks()
-    gbs = (n - k) * n * esize / (med / 1e3) / 1e9
-    return {"median_ms": med, "mean_ms": mean,
-            "passes_per_run": int(results[-1]["iterations"]),
-            "point_evals_per_pass": (n - k) * n,
-            "median_pass_gbs": round(gbs, 1), "median_pass_frac_of_hbm": round(gbs / peak, 4)}
+    out = {"median_ms": med, "mean_ms": mean,
+           "passes_per_run": int(results[-1]["iterations"]),
+           "point_evals_per_pass": (n - k) * n}
+    if esize:
+        peak, _ = peaks()
+        gbs = (n - k) * n * esize / (med / 1e3) / 1e9
+        out.update(median_pass_gbs=round(gbs, 1), median_pass_frac_of_hbm=round(gbs / peak, 4))
+    return out
 
 
 def k100_block(args, km, dev, stream, peak):
@@ -1178,6 +1249,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-k100", action="store_true",
                     help="gmm_50000: skip the k=100 (gmm_20000) block")
+    ap.add_argument("--no-matrix-compare", action="store_true",
+                    help="features_*: skip the FP32 matrix path run beside the feature form")
     ap.add_argument("--build-full", action="store_true",
                     help="matrix workloads: time the plain BUILD pass (every candidate "
                          "row each step) instead of the incremental BUILD")

@@ -371,7 +371,11 @@ km_status kmedoids_gram_bf16(const void *X, int64_t n, int32_t d, int64_t ldx,
  * d_s) and the TD are computed exactly from FP32 differences sum (x - y)^2,
  * so the Gram form's rounding (relative error ~1e-5 on d^2 for well
  * separated points) only affects which candidates see a hit and the Delta
- * values, not the cache or the reported TD.  FastPAM1 only; k <= 224.
+ * values, not the cache or the reported TD.  BUILD gains, removal losses
+ * and every Delta are sums of exact 64-bit fixed-point terms round(x 2^q)
+ * (q per call: the diameter of the data's bounding box is below 2^25
+ * units), so they do not depend on the order of the GPU's additions.
+ * FastPAM1 only; k <= 224.
  * Workspace (DEVICE, 256-byte aligned): kmedoids_features_workspace_size()
  * bytes, which includes the features rearranged for the tensor cores. */
 size_t kmedoids_features_workspace_size(int64_t n, int32_t d, int32_t k,
@@ -385,6 +389,15 @@ km_status kmedoids_run_features(const void *X_bf16, int64_t n, int32_t d,
                                 int32_t *labels_out, const km_options *opts,
                                 km_result *res, void *ws, size_t ws_bytes,
                                 void *stream);
+
+/* BUILD (Alg. 1) alone on the features: medoids_out (DEVICE, k) in the
+ * order chosen; opts->build_gains receives each step's gain; labels_out
+ * (DEVICE, n, may be NULL) the nearest slot of every point. */
+km_status kmedoids_build_features(const void *X_bf16, int64_t n, int32_t d,
+                                  int64_t ldx, int32_t k, int32_t *medoids_out,
+                                  int32_t *labels_out, const km_options *opts,
+                                  km_result *res, void *ws, size_t ws_bytes,
+                                  void *stream);
 
 /* FastPAM1 SWAP on the features from the medoids in medoids_inout. */
 km_status kmedoids_swap_features(const void *X_bf16, int64_t n, int32_t d,

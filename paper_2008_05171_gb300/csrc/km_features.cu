@@ -26,14 +26,21 @@
 //               take d = sqrt(|x_c|^2 + |x_o|^2 - 2 g):
 //               SWAP:  Eq. (7) per-slot terms into per-candidate slot
 //                      accumulators in shared memory, the shared term into
-//                      a compensated register sum;
-//               BUILD: min(d - d_n, 0) summed with Kahan compensation
-//                      (step 0: every d).
+//                      a register sum;
+//               BUILD: min(d - d_n, 0) summed in a register (step 0: every
+//                      d).
+// Every sum is exact fixed point: each distance enters as round(x 2^q), with
+// q chosen per call so that the diameter of the data's bounding box is
+// below 2^25 units (half the FP32 resolution of the largest distance); the
+// per-slot accumulators are 32-bit words in shared memory whose wrap-arounds
+// are counted in a global carry table, so every sum is an exact 64-bit
+// integer, independent of the order of the atomic additions.
 // The per-point cache (nearest, d_n, d_s) is computed exactly with FP32
 // direct differences sum (x - y)^2 (cache, apply and BUILD commit kernels),
 // so the bf16 Gram form only decides which candidate rows see a hit; its
 // error near the case boundaries costs at most the error itself because the
 // change function of Eq. (5) is continuous in d(o, c) at d_n and d_s.
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -53,6 +60,8 @@ constexpr int kFeatEpiWarps = 16;
 constexpr int kFeatThreads = (2 + kFeatEpiWarps) * 32;
 constexpr int kFeatMaxK = 224;       // shared accumulators: 128 x k x 4 B
 constexpr int kFeatMaxD = 256;
+constexpr int kFeatMaxGrid = 160;    // pass CTAs (one per SM), carry table rows
+constexpr int kFeatUnitBits = 25;    // a distance below the box diameter < 2^25 units
 
 struct FeatArgs {
   // Operands of the pass, n_pad rows of dk = d + 16 bf16 columns each in
@@ -81,9 +90,13 @@ struct FeatArgs {
                         // d = d_s (SWAP) or d_n (BUILD); +inf on padding
   uint8_t* is_med;
   int32_t* med;
-  double* removal;      // [2][k_pad]
+  long long* removal;   // [2][k_pad] removal loss, fixed point (units 2^-q)
   double* td2;          // [2]
   int k_pad;
+  int fq;               // fixed-point exponent q: a distance x enters as round(x 2^q)
+  unsigned* carry;      // [kFeatMaxGrid][kTileM][k_pad] wrap-arounds of the
+                        // 32-bit per-slot accumulators (zero between tiles)
+  float* range;         // [2][d] per-dimension minimum and maximum (scale)
   KmState* st;
   void* partials;       // Key<double>[kMaxGrid]
   double* gains;        // BUILD gains per step
@@ -99,7 +112,8 @@ constexpr int kFeatMetaStages = 4;  // ring of per-block point caches
 constexpr int kFeatMaxBStages = 4;  // ring of point blocks (as many as fit)
 
 struct FeatLayout {
-  size_t bars, flags, wkeys, rl, acc, red, tslot, meta, a, stages, stage_bytes, meta_bytes, total;
+  size_t bars, flags, wkeys, rl, acc, red, tslot, rowc, meta, a, stages, stage_bytes, meta_bytes,
+      total;
   int bst;  // point-block stages
 };
 
@@ -112,6 +126,8 @@ __host__ __device__ inline FeatLayout feat_layout(int d, int k) {
   o += 32;
   L.tslot = o;
   o += 16;
+  L.rowc = o;  // per candidate row: a carry of its slot accumulators happened
+  o += kTileM;
   o = (o + 15) / 16 * 16;
   L.wkeys = o;
   o += 16 * 16;
@@ -191,11 +207,12 @@ __device__ __forceinline__ float sel16(const float* v, int j) {
   return b3 ? e1 : e0;
 }
 
-__device__ __forceinline__ void kahan_addf(float& s, float& c, float x) {
-  const float y = x - c;
-  const float t = s + y;
-  c = (t - s) - y;
-  s = t;
+// The fixed-point value of a distance x >= 0: x 2^q rounded to the nearest
+// integer (x is below the data's diameter, so the result is below 2^25;
+// clamped at 2^26 against Gram rounding).  Rounding is monotone, so every
+// case comparison of Eq. (7) keeps its sign in fixed point.
+__device__ __forceinline__ int fxq(float x, float scale) {
+  return __float2int_rn(fminf(x * scale, 67108864.f));
 }
 
 // ------------------------------------------------------------ pass kernel
@@ -223,9 +240,10 @@ __global__ void __launch_bounds__(kFeatThreads, 1) k_feat_pass(const FeatArgs a)
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + L.flags) + 2;
   int* tslot = reinterpret_cast<int*>(smem + L.tslot);  // tile index ping-pong [2]
   Key<double>* wkeys = reinterpret_cast<Key<double>*>(smem + L.wkeys);
-  double* rl = reinterpret_cast<double*>(smem + L.rl);
-  float* acc = reinterpret_cast<float*>(smem + L.acc);
-  double* red = reinterpret_cast<double*>(smem + L.red);
+  long long* rl = reinterpret_cast<long long*>(smem + L.rl);
+  unsigned* acc = reinterpret_cast<unsigned*>(smem + L.acc);
+  long long* red = reinterpret_cast<long long*>(smem + L.red);
+  volatile unsigned char* rowc = smem + L.rowc;
   unsigned char* metas = smem + L.meta;
   unsigned char* sA = smem + L.a;
   unsigned char* stages = smem + L.stages;
@@ -237,8 +255,8 @@ __global__ void __launch_bounds__(kFeatThreads, 1) k_feat_pass(const FeatArgs a)
   const uint32_t tile_bytes = (uint32_t)(kTileM * d * 2);
 
   if (MODE == kModeSwap && blockIdx.x == 0) {
-    double* rnext = a.removal + (size_t)(rb ^ 1) * a.k_pad;
-    for (int i = tid; i < k; i += blockDim.x) rnext[i] = 0.0;
+    long long* rnext = a.removal + (size_t)(rb ^ 1) * a.k_pad;
+    for (int i = tid; i < k; i += blockDim.x) rnext[i] = 0;
     if (tid == 0) a.td2[rb ^ 1] = 0.0;
   }
   if (MODE == kModeBuild && blockIdx.x == 0 && tid == 0) st->build_td_d = 0.0;
@@ -263,10 +281,11 @@ __global__ void __launch_bounds__(kFeatThreads, 1) k_feat_pass(const FeatArgs a)
     fence_barrier_init();
   }
   if (MODE == kModeSwap) {
-    const double* rsrc = a.removal + (size_t)rb * a.k_pad;
+    const long long* rsrc = a.removal + (size_t)rb * a.k_pad;
     for (int i = tid; i < k; i += blockDim.x) rl[i] = rsrc[i];
-    for (int i = tid; i < kTileM * k; i += blockDim.x) acc[i] = 0.f;
+    for (int i = tid; i < kTileM * k; i += blockDim.x) acc[i] = 0u;
   }
+  for (int i = tid; i < kTileM; i += blockDim.x) rowc[i] = 0;
   if (warp == 1) {
     tmem_alloc(tmem_slot, kFeatAccBufs * kTileN);
     tmem_relinquish();
@@ -391,7 +410,10 @@ __global__ void __launch_bounds__(kFeatThreads, 1) k_feat_pass(const FeatArgs a)
     const int group = ew >> 2;            // columns 32*group..+31
     const int r = quarter * 32 + lane;    // candidate row within the tile
     const int col0 = group * 32;
-    float* arow = acc + (size_t)r * k;
+    unsigned* arow = acc + (size_t)r * k;
+    unsigned* crow = a.carry + ((size_t)blockIdx.x * kTileM + r) * a.k_pad;
+    const float scale = __int_as_float((127 + a.fq) << 23);                 // 2^q
+    const double unit = __longlong_as_double((long long)(1023 - a.fq) << 52);  // 2^-q
     uint32_t eph = 0;
     long long gb = 0;
     bool ok = true;
@@ -408,7 +430,7 @@ __global__ void __launch_bounds__(kFeatThreads, 1) k_feat_pass(const FeatArgs a)
       // d(o,c)^2 < d^2(o)  <=>  g - |x_c|^2/2 > (|x_o|^2 - d^2(o))/2 = thr[o]
       // <=>  v = |x_c|^2/2 + thr[o] - g < 0, and v is what the MMA produced
       const float hc = 0.5f * nc;
-      float ks_ = 0.f, kc_ = 0.f;  // Kahan pair: BUILD gain or SWAP shared term
+      long long sh = 0;  // fixed point: the BUILD gain's sum or the SWAP shared term
       for (int b = 0; b < nblocks; ++b, ++gb) {
         const int buf = (int)(gb % kFeatAccBufs);
         const int ms = (int)(gb % kFeatMetaStages);
@@ -432,20 +454,31 @@ __global__ void __launch_bounds__(kFeatThreads, 1) k_feat_pass(const FeatArgs a)
         const int* m_near = reinterpret_cast<const int*>(meta + 2048);
         // one pair (o = column col, candidate c = this thread's row) that
         // passed the threshold test; g = x_c.x_o recovered from v, then the
-        // exact case split on d = sqrt(d^2)
+        // exact case split on d = sqrt(d^2).  Eq. (7) in fixed point: the
+        // slot term (d_n - d_s, or d - d_s clamped at its case boundary
+        // d = d_s where it is 0) is accumulated as its magnitude, the shared
+        // term d - d_n as the magnitude d_n - d.
         auto hit = [&](int col, float v) {
           const float g = (hc + m_thr[col]) - v;
           const float d2 = fmaf(-2.f, g, nc + m_no[col]);
           const float dd = sqrtf(fmaxf(d2, 0.f));
           const float dn_ = m_dn[col];
+          const int ddq = fxq(dd, scale), dnq = fxq(dn_, scale);
           if (MODE == kModeSwap) {
-            const float ds_ = m_ds[col];
+            const int dsq = fxq(m_ds[col], scale);
             const int sl = m_near[col];
             const bool inner = dd < dn_;
-            atomicAdd(arow + sl, inner ? dn_ - ds_ : dd - ds_);  // Eq. (7) per-slot term
-            if (inner) kahan_addf(ks_, kc_, dd - dn_);           // shared term
+            const int mag = inner ? dsq - dnq : max(dsq - ddq, 0);
+            if (mag > 0) {
+              const unsigned old = atomicAdd(arow + sl, (unsigned)mag);
+              if (old + (unsigned)mag < old) {  // this addition wrapped the word
+                atomicAdd(crow + sl, 1u);
+                rowc[r] = 1;
+              }
+            }
+            if (inner) sh += dnq - ddq;
           } else if (dd < dn_) {
-            kahan_addf(ks_, kc_, dd - dn_);
+            sh += dnq - ddq;
           }
         };
         if (MODE == kModeBuild && a.build_first) {
@@ -455,7 +488,7 @@ __global__ void __launch_bounds__(kFeatThreads, 1) k_feat_pass(const FeatArgs a)
           for (int j = 0; j < 32; ++j) {
             const float g = (hc + m_thr[col0 + j]) - v[j];
             const float d2 = fmaf(-2.f, g, nc + m_no[col0 + j]);
-            kahan_addf(ks_, kc_, (colg + j < n) ? sqrtf(fmaxf(d2, 0.f)) : 0.f);
+            sh += (colg + j < n) ? fxq(sqrtf(fmaxf(d2, 0.f)), scale) : 0;
           }
         } else {
 #pragma unroll
@@ -491,36 +524,46 @@ __global__ void __launch_bounds__(kFeatThreads, 1) k_feat_pass(const FeatArgs a)
       }
       if (!ok) break;
       // ------------------------------------------------------ tile finished
-      if (group > 0) red[(group - 1) * kTileM + r] = (double)ks_ - (double)kc_;
+      if (group > 0) red[(group - 1) * kTileM + r] = sh;
       if (!cons_sync(ep_bar, eph, abort_flag, wlim)) {
         ok = false;
         break;
       }
       if (group == 0) {
-        double shared_part = (double)ks_ - (double)kc_;
+        long long shared_part = sh;
         for (int g = 0; g < kFeatEpiWarps / 4 - 1; ++g) shared_part += red[g * kTileM + r];
         if (MODE == kModeSwap) {
+          // Delta_i = removal loss of slot i - the slot's accumulated
+          // magnitudes (32-bit word + 2^32 x its wrap count); Delta(c) =
+          // min_i Delta_i + Delta^{+c}, all exact integers
+          const bool carried = rowc[r] != 0;
           if (cvalid) {
-            double best = 1e300;
+            long long best = LLONG_MAX;
             int bi = 0;
             for (int i = 0; i < k; ++i) {
-              const double vi = rl[i] + (double)arow[i];
+              long long t = (long long)arow[i];
+              if (carried) t += (long long)__ldcg(crow + i) << 32;
+              const long long vi = rl[i] - t;
               if (vi < best) {
                 best = vi;
                 bi = i;
               }
             }
             Key<double> ck;
-            ck.d = best + shared_part;
+            ck.d = (double)(best - shared_part) * unit;
             ck.slot = bi;
             ck.cand = c;
             if (key_less(ck, wbest)) wbest = ck;
           }
-          for (int i = 0; i < k; ++i) arow[i] = 0.f;
+          for (int i = 0; i < k; ++i) arow[i] = 0u;
+          if (carried) {
+            for (int i = 0; i < k; ++i) __stcg(crow + i, 0u);
+            rowc[r] = 0;
+          }
         } else {
           if (cvalid) {
             Key<double> ck;
-            ck.d = shared_part;
+            ck.d = (double)(a.build_first ? shared_part : -shared_part) * unit;
             ck.slot = 0;
             ck.cand = c;
             if (key_less(ck, wbest)) wbest = ck;
@@ -637,13 +680,14 @@ __device__ __forceinline__ void top2f(float v, int j, int& n1, float& d1, int& n
 // squared; d_n, d_s stored as FP32 square roots), removal loss and TD.
 __global__ void __launch_bounds__(256) k_feat_cache(const FeatArgs a) {
   extern __shared__ __align__(16) unsigned char sm[];
-  double* sacc = reinterpret_cast<double*>(sm);
+  unsigned long long* sacc = reinterpret_cast<unsigned long long*>(sm);
   __shared__ double scratch[8];
   __shared__ int is_last;
   KmState* st = a.st;
   const int k = a.k, n = a.n, d = a.d;
   const int rb = st->rb;
-  for (int i = threadIdx.x; i < k; i += blockDim.x) sacc[i] = 0.0;
+  const float scale = __int_as_float((127 + a.fq) << 23);
+  for (int i = threadIdx.x; i < k; i += blockDim.x) sacc[i] = 0ull;
   __syncthreads();
   const int o = blockIdx.x * blockDim.x + threadIdx.x;
   double tdl = 0.0;
@@ -664,7 +708,7 @@ __global__ void __launch_bounds__(256) k_feat_cache(const FeatArgs a) {
     // which any finite threshold lets the Gram entries be recovered
     a.thr[o] = (n2 < 0) ? 0.f : 0.5f * (a.norms[o] - q2);
     write_thr_cols(a, o, a.thr[o]);
-    if (n2 >= 0) atomicAdd(&sacc[n1], (double)e2 - (double)e1);
+    if (n2 >= 0) atomicAdd(&sacc[n1], (unsigned long long)(fxq(e2, scale) - fxq(e1, scale)));
     tdl = e1;
   } else if (o < a.n_pad) {
     a.near[o] = 0;
@@ -678,9 +722,9 @@ __global__ void __launch_bounds__(256) k_feat_cache(const FeatArgs a) {
   }
   const double bs = fblock_sum(tdl, scratch);
   if (threadIdx.x == 0) atomicAdd(&a.td2[rb], bs);
-  double* rem = a.removal + (size_t)rb * a.k_pad;
+  unsigned long long* rem = reinterpret_cast<unsigned long long*>(a.removal + (size_t)rb * a.k_pad);
   for (int i = threadIdx.x; i < k; i += blockDim.x)
-    if (sacc[i] != 0.0) atomicAdd(&rem[i], sacc[i]);
+    if (sacc[i] != 0ull) atomicAdd(&rem[i], sacc[i]);
   __threadfence();
   __syncthreads();
   if (threadIdx.x == 0) is_last = (atomicAdd(&st->ticket, 1u) == gridDim.x - 1);
@@ -696,7 +740,7 @@ __global__ void __launch_bounds__(256) k_feat_cache(const FeatArgs a) {
 // exact cache update; removal loss and TD of the next pass on the way.
 __global__ void __launch_bounds__(256) k_feat_apply(const FeatArgs a) {
   extern __shared__ __align__(16) unsigned char sm[];
-  double* sacc = reinterpret_cast<double*>(sm);
+  unsigned long long* sacc = reinterpret_cast<unsigned long long*>(sm);
   __shared__ double scratch[8];
   __shared__ int is_last;
   KmState* st = a.st;
@@ -704,7 +748,8 @@ __global__ void __launch_bounds__(256) k_feat_apply(const FeatArgs a) {
   const int k = a.k, n = a.n, d = a.d;
   const int i_s = st->best_slot, c_s = st->best_cand;
   const int rb = st->rb;
-  for (int i = threadIdx.x; i < k; i += blockDim.x) sacc[i] = 0.0;
+  const float scale = __int_as_float((127 + a.fq) << 23);
+  for (int i = threadIdx.x; i < k; i += blockDim.x) sacc[i] = 0ull;
   __syncthreads();
   const int o = blockIdx.x * blockDim.x + threadIdx.x;
   double tdl = 0.0;
@@ -740,14 +785,15 @@ __global__ void __launch_bounds__(256) k_feat_apply(const FeatArgs a) {
     a.ds2[o] = q2;
     a.thr[o] = 0.5f * (a.norms[o] - q2);
     write_thr_cols(a, o, a.thr[o]);
-    atomicAdd(&sacc[n1], (double)e2 - (double)e1);
+    atomicAdd(&sacc[n1], (unsigned long long)(fxq(e2, scale) - fxq(e1, scale)));
     tdl = e1;
   }
   const double bs = fblock_sum(tdl, scratch);
   if (threadIdx.x == 0) atomicAdd(&a.td2[rb ^ 1], bs);
-  double* rem = a.removal + (size_t)(rb ^ 1) * a.k_pad;
+  unsigned long long* rem =
+      reinterpret_cast<unsigned long long*>(a.removal + (size_t)(rb ^ 1) * a.k_pad);
   for (int i = threadIdx.x; i < k; i += blockDim.x)
-    if (sacc[i] != 0.0) atomicAdd(&rem[i], sacc[i]);
+    if (sacc[i] != 0ull) atomicAdd(&rem[i], sacc[i]);
   __threadfence();
   __syncthreads();
   if (threadIdx.x == 0) is_last = (atomicAdd(&st->ticket, 1u) == gridDim.x - 1);
@@ -855,6 +901,28 @@ __global__ void k_feat_prearrange(const FeatArgs a) {
   }
 }
 
+// Per-dimension minimum and maximum of the features (thread t of a block
+// takes dimension t of every gridDim-th point), as order-preserving integer
+// encodings of the float values so that integer atomics combine them.
+__device__ __forceinline__ int ord_of(float v) {
+  const int b = __float_as_int(v);
+  return b >= 0 ? b : b ^ 0x7fffffff;
+}
+
+__global__ void k_feat_range(const FeatArgs a) {
+  const int t = threadIdx.x;
+  if (t >= a.d) return;
+  int lo = INT_MAX, hi = INT_MIN;
+  for (int o = blockIdx.x; o < a.n; o += gridDim.x) {
+    const int v = ord_of(bf(a.X[(size_t)o * a.ldx + t]));
+    lo = min(lo, v);
+    hi = max(hi, v);
+  }
+  int* r = reinterpret_cast<int*>(a.range);
+  atomicMin(r + t, lo);
+  atomicMax(r + a.d + t, hi);
+}
+
 __global__ void k_feat_mark(const FeatArgs a) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j < a.k) a.is_med[a.med[j]] = 1;
@@ -869,7 +937,7 @@ namespace {
 
 struct FeatWs {
   size_t st, med, is_med, near, sec, dn, ds, dn2, ds2, thr, norms, removal, td2, partials, trace,
-      gains, xpa, xpb, total;
+      gains, xpa, xpb, carry, range, total;
   int n_pad, k_pad, cap;
 };
 
@@ -904,6 +972,8 @@ bool feat_ws(int64_t n, int d, int k, const km_options* o, FeatWs* L) {
   L->gains = take(8 * (size_t)k);
   L->xpa = take((size_t)n_pad * (d + 16) * 2);
   L->xpb = take((size_t)n_pad * (d + 16) * 2);
+  L->carry = take(4 * (size_t)kFeatMaxGrid * kTileM * k_pad);
+  L->range = take(8 * (size_t)d);
   L->total = off;
   L->n_pad = n_pad;
   L->k_pad = k_pad;
@@ -968,7 +1038,7 @@ km_status f_pass(FCtx& c, int mode, int first, cudaEvent_t ev0 = nullptr,
   if (L.total > 227 * 1024) return ffail(KM_E_UNSUPPORTED, "feature pass needs %zu B of shared memory", L.total);
   int grid = c.sms;
   if (grid > a.n_pad / kTileM) grid = a.n_pad / kTileM;
-  if (grid > kMaxGrid) grid = kMaxGrid;
+  if (grid > kFeatMaxGrid) grid = kFeatMaxGrid;
   if (mode == kModeSwap)
     FK(cudaFuncSetAttribute(k_feat_pass<kModeSwap>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total));
   else
@@ -1047,7 +1117,9 @@ km_status run_features(bool do_build, bool do_swap, const void* X, int64_t n, in
   a.thr = reinterpret_cast<float*>(c.ws + c.L.thr);
   a.is_med = c.ws + c.L.is_med;
   a.med = reinterpret_cast<int32_t*>(c.ws + c.L.med);
-  a.removal = reinterpret_cast<double*>(c.ws + c.L.removal);
+  a.removal = reinterpret_cast<long long*>(c.ws + c.L.removal);
+  a.carry = reinterpret_cast<unsigned*>(c.ws + c.L.carry);
+  a.range = reinterpret_cast<float*>(c.ws + c.L.range);
   a.td2 = reinterpret_cast<double*>(c.ws + c.L.td2);
   a.st = c.st();
   a.partials = c.ws + c.L.partials;
@@ -1076,6 +1148,37 @@ km_status run_features(bool do_build, bool do_swap, const void* X, int64_t n, in
     FK(cudaGetLastError());
   }
   c.launches += 2;
+  // fixed-point scale of the sums: q such that the diameter of the data's
+  // bounding box (an upper bound of every distance) is below 2^25 units
+  FK(cudaMemsetAsync(a.carry, 0, 4 * (size_t)kFeatMaxGrid * kTileM * c.L.k_pad, c.s));
+  FK(cudaMemsetAsync(a.range, 0x7f, 4 * (size_t)d, c.s));
+  FK(cudaMemsetAsync(a.range + d, 0x80, 4 * (size_t)d, c.s));
+  k_feat_range<<<(int)(n < 2048 ? n : 2048), (d + 31) / 32 * 32, 0, c.s>>>(a);
+  FK(cudaGetLastError());
+  ++c.launches;
+  {
+    std::vector<int> rg(2 * (size_t)d);
+    FK(cudaMemcpyAsync(rg.data(), a.range, 8 * (size_t)d, cudaMemcpyDeviceToHost, c.s));
+    FK(cudaStreamSynchronize(c.s));
+    double diam2 = 0.0;
+    for (int t = 0; t < d; ++t) {
+      int lo = rg[t], hi = rg[d + t];
+      lo = lo >= 0 ? lo : lo ^ 0x7fffffff;
+      hi = hi >= 0 ? hi : hi ^ 0x7fffffff;
+      float flo, fhi;
+      memcpy(&flo, &lo, 4);
+      memcpy(&fhi, &hi, 4);
+      const double w = (double)fhi - (double)flo;
+      diam2 += w * w;
+    }
+    const double diam = std::sqrt(diam2) * (1.0 + 1.0 / 1024.0);
+    int e = -126;
+    if (diam > 0.0 && std::isfinite(diam)) (void)std::frexp(diam, &e);  // diam < 2^e
+    int q = kFeatUnitBits - e;
+    if (q > 40) q = 40;
+    if (q < -100) q = -100;
+    a.fq = q;
+  }
   if (prof) FK(cudaEventRecord(e0, c.s));
   KmState h;
   memset(&h, 0, sizeof(h));
@@ -1219,16 +1322,23 @@ km_status run_features(bool do_build, bool do_swap, const void* X, int64_t n, in
         sb += ms;
       }
       int cnt = 0;
+      std::vector<double> per;
       for (auto& p : sev) {
         if (cnt >= h.iter) break;
         cudaEventElapsedTime(&ms, p.first, p.second);
         ss += ms;
+        per.push_back(ms);
         ++cnt;
       }
       res->build_eval_ms = sb;
       res->build_launches = (int)bev.size();
       res->eval_ms = ss;
       res->eval_launches = cnt;
+      if (!per.empty()) {
+        std::sort(per.begin(), per.end());
+        const size_t m = per.size() / 2;
+        res->eval_ms_median = (per.size() % 2) ? per[m] : 0.5 * (per[m - 1] + per[m]);
+      }
     }
   }
   if (prof) {
@@ -1265,6 +1375,15 @@ extern "C" km_status kmedoids_run_features(const void* X, int64_t n, int32_t d, 
                                            size_t ws_bytes, void* stream) {
   NvtxRange nv("kmedoids_run_features");
   return run_features(true, true, X, n, d, ldx, k, medoids_out, labels_out, opts, res, ws,
+                      ws_bytes, stream);
+}
+
+extern "C" km_status kmedoids_build_features(const void* X, int64_t n, int32_t d, int64_t ldx,
+                                             int32_t k, int32_t* medoids_out, int32_t* labels_out,
+                                             const km_options* opts, km_result* res, void* ws,
+                                             size_t ws_bytes, void* stream) {
+  NvtxRange nv("kmedoids_build_features");
+  return run_features(true, false, X, n, d, ldx, k, medoids_out, labels_out, opts, res, ws,
                       ws_bytes, stream);
 }
 

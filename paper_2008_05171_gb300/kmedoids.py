@@ -29,7 +29,7 @@ EXPORTS = ["km_default_options", "kmedoids_workspace_size", "kmedoids_build",
            "kmedoids_batched_distances", "kmedoids_run_batched",
            "kmedoids_swap_batched", "kmedoids_clara_workspace_size", "kmedoids_clara",
            "kmedoids_geometry_info", "kmedoids_init_weighted",
-           "kmedoids_init_lab", "kmedoids_wait_selftest"]
+           "kmedoids_init_lab", "kmedoids_wait_selftest", "kmedoids_build_features"]
 
 
 class KmError(RuntimeError):
@@ -114,7 +114,8 @@ def load(path: str = LIB_PATH):
         lib.kmedoids_gram_bf16.restype = i32
         lib.kmedoids_features_workspace_size.argtypes = [i64, i32, i32, opt_p]
         lib.kmedoids_features_workspace_size.restype = sz
-        for name in ("kmedoids_run_features", "kmedoids_swap_features"):
+        for name in ("kmedoids_run_features", "kmedoids_swap_features",
+                     "kmedoids_build_features"):
             f = getattr(lib, name)
             f.argtypes = [P, i64, i32, i64, i32, P, P, opt_p, res_p, P, sz, P]
             f.restype = i32
@@ -454,7 +455,8 @@ def _features_call(fn_name, X, k, med, labels, kw):
         raise ValueError("X must be a 2-D bf16 CUDA tensor with unit column stride")
     n, d = X.shape
     o = options(**kw)
-    tr = _Trace(o, o.trace_capacity, k, fn_name == "kmedoids_run_features")
+    gains = fn_name in ("kmedoids_run_features", "kmedoids_build_features")
+    tr = _Trace(o, o.trace_capacity, k, gains)
     nbytes = lib.kmedoids_features_workspace_size(n, d, k, ctypes.byref(o))
     if nbytes == 0:
         raise KmError(1, "invalid sizes for the feature form")
@@ -474,7 +476,7 @@ def _features_call(fn_name, X, k, med, labels, kw):
     out["medoids"] = med
     out["labels"] = labels
     out["trace"] = tr.items(res.swaps) if o.trace_capacity > 0 else []
-    if fn_name == "kmedoids_run_features":
+    if gains:
         out["build_gains"] = tr.g[:k].copy()
     return out
 
@@ -487,6 +489,16 @@ def run_features(X, k, labels=True, **kw):
     lab = torch.empty(X.shape[0], dtype=torch.int32, device=X.device) \
         if labels else None
     return _features_call("kmedoids_run_features", X, k, med, lab, kw)
+
+
+def build_features(X, k, labels=True, **kw):
+    """BUILD alone on bf16 features (kmedoids_build_features): medoids in
+    the order chosen, build_gains the gain of each step."""
+    torch = _torch()
+    med = torch.empty(k, dtype=torch.int32, device=X.device)
+    lab = torch.empty(X.shape[0], dtype=torch.int32, device=X.device) \
+        if labels else None
+    return _features_call("kmedoids_build_features", X, k, med, lab, kw)
 
 
 def swap_features(X, medoids, labels=True, **kw):
