@@ -439,7 +439,9 @@ km_status kmedoids_batched_distances(const float *points, int32_t dim,
                                      float *arena, void *stream);
 
 /* inst (DEVICE, count entries, 1 <= count <= 65535), medoids_out / results
- * (DEVICE).  opts: max_iter, tol; tune 1 = 8 warps per CTA, otherwise 16;
+ * (DEVICE).  opts: max_iter, tol; tune 0 = geometry 1 of the persistent
+ * kernel, 1 .. 5 = that geometry (see kmedoids_batched_geometry_info and
+ * kmedoids_batched_autotune), anything else KM_E_INVALID;
  * variant KM_FASTPAM1 (default) or KM_FASTERPAM (Alg. 4: each CTA scans its
  * instance cyclically in windows of one candidate row per warp and applies
  * the first improving swap at once, with an incremental cache update; the
@@ -475,6 +477,32 @@ km_status kmedoids_swap_batched(const float *arena, const km_instance *inst,
                                 const km_options *opts, void *ws,
                                 size_t ws_bytes, void *stream);
 
+/* Geometry g (1 .. 5) of the batched form's persistent kernel: warps per
+ * CTA and cp.async ring stages of 512 columns per warp.  Returns 0, or -1
+ * for a g outside the table. */
+int32_t kmedoids_batched_geometry_info(int32_t geometry, int32_t *warps,
+                                       int32_t *stages);
+
+/* Measured choice of the batched kernel's geometry (the tile shape of the
+ * batched form: how many candidate rows a CTA streams at once and how deep
+ * each warp's ring is).  Runs kmedoids_run_batched on the caller's batch
+ * with every geometry of the table (one warm-up and one timed run each;
+ * the outputs are overwritten with identical results, since results do not
+ * depend on the geometry) and returns the fastest in *geometry_out, to be
+ * passed as opts->tune to later calls (which may then be captured in a
+ * CUDA graph).  ms_out (HOST, 5 entries, may be NULL) receives each
+ * geometry's time (-1 if it could not launch).  The choice is cached per
+ * device, variant and histogram of the instance sizes (instances counted
+ * per (floor(log2 n), floor(log2 k)) bucket): with ms_out NULL a cached
+ * choice is returned without measuring.  Reads the instance table back to
+ * the host and synchronises the stream; arguments as kmedoids_run_batched. */
+km_status kmedoids_batched_autotune(const float *arena, const km_instance *inst,
+                                    int32_t count, int32_t *medoids_out,
+                                    km_batch_result *results,
+                                    const km_options *opts, void *ws,
+                                    size_t ws_bytes, void *stream,
+                                    int32_t *geometry_out, double *ms_out);
+
 /* ---- CLARA (Sec. 2.1; FastCLARA, Sec. 3.4).  X: n points of d float32
  * features (DEVICE, row-major).  sample_idx (DEVICE, samples x
  * sample_size int32): the caller's subsamples (the paper suggests
@@ -484,7 +512,9 @@ km_status kmedoids_swap_batched(const float *arena, const km_instance *inst,
  * TD).  The sample with the least TD wins (lowest index on ties):
  * medoids_out (DEVICE, k point indices), labels_out (DEVICE, n, may be
  * NULL), sample_td_host (HOST, samples, may be NULL); res->td = best TD,
- * res->best_sample its index. */
+ * res->best_sample its index.  Limits: 1 <= k <= sample_size <= min(n,
+ * 4096), k <= 128, d <= 864, 16 k ceil(d/4) <= 200 KB.  Synchronises the
+ * stream; a sample whose PAM run failed makes the call return its status. */
 size_t kmedoids_clara_workspace_size(int32_t k, int32_t samples,
                                      int32_t sample_size);
 km_status kmedoids_clara(const float *X, int64_t n, int32_t d, int32_t k,
@@ -493,6 +523,38 @@ km_status kmedoids_clara(const float *X, int64_t n, int32_t d, int32_t k,
                          int32_t *labels_out, double *sample_td_host,
                          km_result *res, void *ws, size_t ws_bytes,
                          void *stream);
+
+/* CLARA's outcome in device memory (kmedoids_run_batched_clara). */
+typedef struct km_clara_result {
+  double td;           /* full-data TD of the winning sample's medoids */
+  int32_t best_sample; /* its index (lowest on ties) */
+  int32_t status;      /* KM_OK, or the first failing sample's status */
+} km_clara_result;
+
+/* A batch of independent instances (as kmedoids_run_batched; count may be
+ * 0) and CLARA (as kmedoids_clara) in one asynchronous enqueue: the sample
+ * matrices, ONE persistent PAM launch over the batch and the samples
+ * together (largest first; with opts->variant = KM_FASTERPAM the batch runs
+ * FasterPAM in a launch of its own and the samples BUILD + FastPAM1), the
+ * full-data assignment of every sample, the choice of the best sample and
+ * the labels, all on the device.  Nothing is read back and nothing
+ * synchronises, so the whole call can be captured in a CUDA graph and
+ * replayed.  Outputs (DEVICE): the batch's medoids and results as
+ * kmedoids_run_batched; clara_medoids_out (k point indices),
+ * clara_labels_out (n, may be NULL), sample_td (samples FP64 TDs, may be
+ * NULL), clara_result (one record).  opts: as kmedoids_run_batched (tune
+ * picks the geometry for both); count + samples <= 65535.  Workspace
+ * (DEVICE, 256-byte aligned): kmedoids_batched_clara_workspace_size(). */
+size_t kmedoids_batched_clara_workspace_size(int32_t count, int32_t k,
+                                             int32_t samples,
+                                             int32_t sample_size);
+km_status kmedoids_run_batched_clara(
+    const float *arena, const km_instance *inst, int32_t count,
+    int32_t *medoids_out, km_batch_result *results, const float *X, int64_t n,
+    int32_t d, int32_t k, int32_t samples, int32_t sample_size,
+    const int32_t *sample_idx, int32_t *clara_medoids_out,
+    int32_t *clara_labels_out, double *sample_td, km_clara_result *clara_result,
+    const km_options *opts, void *ws, size_t ws_bytes, void *stream);
 
 /* kmedoids_eval_swaps without a caller-provided workspace, for callers that
  * cannot allocate device memory when they evaluate swaps (a frozen memory

@@ -22,6 +22,8 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <vector>
 
 #include "../../include/kmedoids.h"
@@ -35,13 +37,22 @@ constexpr int kBatchMaxK = 128;
 constexpr int kBatchMaxCount = 65535;  // also the grid height of the distance kernel
 constexpr int kDistMaxDim = 864;       // 64 staged points + the tile fit in shared memory
 
+// Instances 0 .. count_a - 1 come from the first table (arena, inst,
+// medoids, out), instances count_a .. count - 1 from the second (arena2,
+// inst2, medoids2, out2; CLARA's samples when a batch and CLARA share one
+// launch).
 struct BatchArgs {
   const float* arena;
   const km_instance* inst;
-  int count;
+  int count;                 // both tables
+  int count_a;               // the first table
   const int32_t* order;      // instance processing order (largest first)
   int32_t* medoids;          // concatenated, at inst[i].medoid_offset
   km_batch_result* out;
+  const float* arena2;
+  const km_instance* inst2;
+  int32_t* medoids2;
+  km_batch_result* out2;
   unsigned* queue;           // next position in order
   int* error;
   int max_iter;
@@ -140,16 +151,24 @@ __device__ __forceinline__ double batch_work(const km_instance& a) {
   return (double)a.n * (double)a.n * (double)(a.k + 1);
 }
 
-__global__ void __launch_bounds__(256) k_batch_order(const km_instance* inst, int count,
+// Instance i of the two tables (i < count_a: the first).
+__device__ __forceinline__ km_instance inst_at(const km_instance* ia, int count_a,
+                                              const km_instance* ib, int i) {
+  return i < count_a ? ia[i] : ib[i - count_a];
+}
+
+__global__ void __launch_bounds__(256) k_batch_order(const km_instance* inst, int count_a,
+                                                     const km_instance* inst2, int count,
                                                      int32_t* order) {
   __shared__ double w[256];
   for (int i0 = blockIdx.x * blockDim.x; i0 < count; i0 += gridDim.x * blockDim.x) {
     const int i = i0 + threadIdx.x;
-    const double wi = (i < count) ? batch_work(inst[i]) : 0.0;
+    const double wi = (i < count) ? batch_work(inst_at(inst, count_a, inst2, i)) : 0.0;
     int r = 0;
     for (int j0 = 0; j0 < count; j0 += 256) {
       __syncthreads();
-      if (j0 + threadIdx.x < count) w[threadIdx.x] = batch_work(inst[j0 + threadIdx.x]);
+      if (j0 + threadIdx.x < count)
+        w[threadIdx.x] = batch_work(inst_at(inst, count_a, inst2, j0 + threadIdx.x));
       __syncthreads();
       const int m = min(256, count - j0);
       for (int t = 0; t < m; ++t) {
@@ -162,17 +181,16 @@ __global__ void __launch_bounds__(256) k_batch_order(const km_instance* inst, in
 }
 
 // Per-warp cp.async ring: every warp streams its own candidate rows through
-// kRingStages stages of 512 columns (32 lanes x 4 float4), so each SM keeps
-// up to WARPS x (kRingStages - 1) x 2 KB of row data in flight.  (One 1-D
+// STAGES stages of 512 columns (32 lanes x 4 float4), so each SM keeps up
+// to WARPS x (STAGES - 1) x 2 KB of row data in flight.  (One 1-D
 // bulk copy per stage issued by lane 0, with an mbarrier per stage, measured
 // 14 % slower on GB300 than these per-lane 16-byte copies.)
-constexpr int kRingStages = 4;
 constexpr int kRingFloats = 512;
 
 // dn, ds and the ring are read as float4: keep them 16-byte aligned.
-template <int WARPS>
+template <int WARPS, int STAGES>
 struct BatchSmem {
-  alignas(16) float ring[WARPS][kRingStages][kRingFloats];
+  alignas(16) float ring[WARPS][STAGES][kRingFloats];
   alignas(16) float dn[kBatchMaxN];
   alignas(16) float ds[kBatchMaxN];
   uint8_t near[kBatchMaxN];
@@ -193,9 +211,18 @@ struct BatchSmem {
   long long dstar_i;
 };
 
-static_assert(offsetof(BatchSmem<16>, dn) % 16 == 0 && offsetof(BatchSmem<16>, ds) % 16 == 0 &&
-                  offsetof(BatchSmem<8>, dn) % 16 == 0 && offsetof(BatchSmem<8>, ds) % 16 == 0,
-              "float4 reads of d_n / d_s need 16-byte alignment");
+// The geometries of the persistent kernel (warps per CTA, ring stages), as
+// numbered by km_options.tune for the batched form (tune 0 = entry 1).
+#define KM_BATCH_GEOMETRIES(X) X(1, 16, 4) X(2, 8, 4) X(3, 16, 3) X(4, 8, 8) X(5, 12, 5)
+constexpr int kBatchGeometries = 5;
+#define KM_BATCH_ALIGN(G, W, S)                                                          \
+  using BatchSmemG##G = BatchSmem<W, S>;                                                 \
+  static_assert(offsetof(BatchSmemG##G, dn) % 16 == 0 &&                                 \
+                    offsetof(BatchSmemG##G, ds) % 16 == 0,                               \
+                "float4 reads of d_n / d_s need 16-byte alignment");                      \
+  static_assert(sizeof(BatchSmemG##G) <= 227 * 1024, "shared memory of one CTA");
+KM_BATCH_GEOMETRIES(KM_BATCH_ALIGN)
+#undef KM_BATCH_ALIGN
 
 __device__ __forceinline__ void kahan_add(float& s, float& c, float x) {
   const float y = x - c;
@@ -238,8 +265,8 @@ __device__ __forceinline__ void cp_async_wait() {
 // on_row_end(c) runs once per row.  Both are warp-uniform.  Each lane reads
 // back only the 16-byte pieces it copied itself, so cp.async.wait_group is the
 // only synchronisation; it completes when the lane's own copies land.
-template <int WARPS, class Chunk, class RowEnd>
-__device__ __forceinline__ void stream_rows(BatchSmem<WARPS>& S, const float* D, int n, int ld,
+template <int WARPS, int STAGES, class Chunk, class RowEnd>
+__device__ __forceinline__ void stream_rows(BatchSmem<WARPS, STAGES>& S, const float* D, int n, int ld,
                                             int warp, int lane, Chunk&& on_chunk,
                                             RowEnd&& on_row_end) {
   float(*ring)[kRingFloats] = S.ring[warp];
@@ -265,11 +292,11 @@ __device__ __forceinline__ void stream_rows(BatchSmem<WARPS>& S, const float* D,
     cp_async_commit();
   };
 #pragma unroll
-  for (int s = 0; s < kRingStages - 1; ++s) issue(s);
+  for (int s = 0; s < STAGES - 1; ++s) issue(s);
   int slot = 0;
   while (cc < n) {
-    issue(slot == 0 ? kRingStages - 1 : slot - 1);
-    cp_async_wait<kRingStages - 1>();
+    issue(slot == 0 ? STAGES - 1 : slot - 1);
+    cp_async_wait<STAGES - 1>();
     const float* stage = ring[slot];
     float4 v[4];
 #pragma unroll
@@ -282,7 +309,7 @@ __device__ __forceinline__ void stream_rows(BatchSmem<WARPS>& S, const float* D,
       cc += WARPS;
       while (cc < n && S.is_med[cc]) cc += WARPS;
     }
-    slot = (slot + 1 == kRingStages) ? 0 : slot + 1;
+    slot = (slot + 1 == STAGES) ? 0 : slot + 1;
   }
   cp_async_wait<0>();
 }
@@ -290,8 +317,8 @@ __device__ __forceinline__ void stream_rows(BatchSmem<WARPS>& S, const float* D,
 // Streams one row (n entries) through the warp's ring, as stream_rows does
 // for a sequence of rows: on_chunk(o, v, stage) for column chunks o = 0,
 // 512, ...; entries at or beyond n are stale and masked by the caller.
-template <int WARPS, class Chunk>
-__device__ __forceinline__ void stream_one_row(BatchSmem<WARPS>& S, const float* row, int n,
+template <int WARPS, int STAGES, class Chunk>
+__device__ __forceinline__ void stream_one_row(BatchSmem<WARPS, STAGES>& S, const float* row, int n,
                                                int warp, int lane, Chunk&& on_chunk) {
   float(*ring)[kRingFloats] = S.ring[warp];
   const int nch = (n + kRingFloats - 1) / kRingFloats;
@@ -300,17 +327,17 @@ __device__ __forceinline__ void stream_one_row(BatchSmem<WARPS>& S, const float*
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
         const int p = j * kRingFloats + 128 * u + 4 * lane;
-        if (p < n) cp_async16(&ring[j % kRingStages][128 * u + 4 * lane], row + p);
+        if (p < n) cp_async16(&ring[j % STAGES][128 * u + 4 * lane], row + p);
       }
     }
     cp_async_commit();
   };
 #pragma unroll
-  for (int j = 0; j < kRingStages - 1; ++j) issue(j);
+  for (int j = 0; j < STAGES - 1; ++j) issue(j);
   for (int j = 0; j < nch; ++j) {
-    issue(j + kRingStages - 1);
-    cp_async_wait<kRingStages - 1>();
-    const float* stage = ring[j % kRingStages];
+    issue(j + STAGES - 1);
+    cp_async_wait<STAGES - 1>();
+    const float* stage = ring[j % STAGES];
     float4 v[4];
 #pragma unroll
     for (int u = 0; u < 4; ++u) v[u] = *reinterpret_cast<const float4*>(stage + 128 * u + 4 * lane);
@@ -343,10 +370,10 @@ __device__ __forceinline__ float f4get(const float4& v, int t) {
   return t == 0 ? v.x : t == 1 ? v.y : t == 2 ? v.z : v.w;
 }
 
-template <int WARPS>
+template <int WARPS, int STAGES>
 __global__ void __launch_bounds__(WARPS * 32, 1) k_batch_pam(const BatchArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  BatchSmem<WARPS>& S = *reinterpret_cast<BatchSmem<WARPS>*>(smem_raw);
+  BatchSmem<WARPS, STAGES>& S = *reinterpret_cast<BatchSmem<WARPS, STAGES>*>(smem_raw);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   constexpr int NT = WARPS * 32;
 
@@ -358,9 +385,12 @@ __global__ void __launch_bounds__(WARPS * 32, 1) k_batch_pam(const BatchArgs a) 
     __syncthreads();
     const int q = S.inst;
     if (q < 0) break;
-    const km_instance in = a.inst[q];
+    const bool first = q < a.count_a;
+    const km_instance in = first ? a.inst[q] : a.inst2[q - a.count_a];
     const int n = in.n, k = in.k, ld = in.ld;
-    const float* D = a.arena + in.offset;
+    const float* D = (first ? a.arena : a.arena2) + in.offset;
+    km_batch_result* outq = first ? a.out + q : a.out2 + (q - a.count_a);
+    int32_t* medq = (first ? a.medoids : a.medoids2) + in.medoid_offset;
     km_batch_result res;
     res.td = 0.0;
     res.iterations = 0;
@@ -371,7 +401,7 @@ __global__ void __launch_bounds__(WARPS * 32, 1) k_batch_pam(const BatchArgs a) 
         (in.offset & 3) || in.offset < 0) {
       if (tid == 0) {
         res.status = KM_E_INVALID;
-        a.out[q] = res;
+        *outq = res;
       }
       __syncthreads();
       continue;
@@ -394,7 +424,7 @@ __global__ void __launch_bounds__(WARPS * 32, 1) k_batch_pam(const BatchArgs a) 
     if (a.start_given) {
       // the largest entry over the whole matrix (fixed-point scale of the
       // SWAP sums), streamed with no row marked as a medoid yet
-      stream_rows<WARPS>(
+      stream_rows<WARPS, STAGES>(
           S, D, n, ld, warp, lane,
           [&](int, int o, const float4(&v)[4], const float*) {
 #pragma unroll
@@ -412,7 +442,7 @@ __global__ void __launch_bounds__(WARPS * 32, 1) k_batch_pam(const BatchArgs a) 
       if (tid == 0) {
         int bad = 0;
         for (int j = 0; j < k && !bad; ++j) {
-          const int m = a.medoids[in.medoid_offset + j];
+          const int m = medq[j];
           if (m < 0 || m >= n || S.is_med[m]) {
             bad = 1;
           } else {
@@ -426,7 +456,7 @@ __global__ void __launch_bounds__(WARPS * 32, 1) k_batch_pam(const BatchArgs a) 
       if (S.cstar) {
         if (tid == 0) {
           res.status = KM_E_INVALID;
-          a.out[q] = res;
+          *outq = res;
         }
         __syncthreads();
         continue;
@@ -438,7 +468,7 @@ __global__ void __launch_bounds__(WARPS * 32, 1) k_batch_pam(const BatchArgs a) 
       double bd = 1e300;
       int bc = INT_MAX;
       float hs = 0.f, hc = 0.f, hs2 = 0.f, hc2 = 0.f;  // two compensated chains
-      stream_rows<WARPS>(
+      stream_rows<WARPS, STAGES>(
           S, D, n, ld, warp, lane,
           [&](int, int o, const float4(&v)[4], const float*) {
             if (step == 0) {
@@ -590,7 +620,7 @@ __global__ void __launch_bounds__(WARPS * 32, 1) k_batch_pam(const BatchArgs a) 
           for (int i = lane; i < k; i += 32) ar[i] = 0;
           __syncwarp();
           long long lp = 0;
-          stream_one_row<WARPS>(S, D + (size_t)c * ld, n, warp, lane,
+          stream_one_row<WARPS, STAGES>(S, D + (size_t)c * ld, n, warp, lane,
                                 [&](int o, const float4(&v)[4], const float* stage) {
             unsigned mask = 0;
 #pragma unroll
@@ -759,7 +789,7 @@ __global__ void __launch_bounds__(WARPS * 32, 1) k_batch_pam(const BatchArgs a) 
           for (int i = lane; i < k; i += 32) ar[i] = 0;
           __syncwarp();
           long long lp = 0;  // this lane's part of the shared accumulator
-          stream_rows<WARPS>(
+          stream_rows<WARPS, STAGES>(
               S, D, n, ld, warp, lane,
               [&](int, int o, const float4(&v)[4], const float* stage) {
                 // fast path: one d < d_s test per entry; hits in a lane mask
@@ -896,11 +926,52 @@ __global__ void __launch_bounds__(WARPS * 32, 1) k_batch_pam(const BatchArgs a) 
       double t = 0.0;
       for (int w = 0; w < WARPS; ++w) t += S.wd[w];
       res.td = t;
-      a.out[q] = res;
+      *outq = res;
     }
-    for (int j = tid; j < k; j += NT) a.medoids[in.medoid_offset + j] = S.med[j];
+    for (int j = tid; j < k; j += NT) medq[j] = S.med[j];
     __syncthreads();
   }
+}
+
+// CLARA sample q as a batch instance: s rows of ld elements at q s ld in the
+// sample arena, k medoids at q k.
+__global__ void k_clara_inst(km_instance* inst, int samples, int s, int ld, int k) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q < samples) {
+    km_instance in;
+    in.offset = (int64_t)q * s * ld;
+    in.n = s;
+    in.ld = ld;
+    in.k = k;
+    in.medoid_offset = q * k;
+    inst[q] = in;
+  }
+}
+
+// CLARA's choice on the device: the sample with the least full-data TD
+// (lowest index on ties) gives the medoids; its TD, index and the first
+// failing sample status (if any) go to the result record.  One block.
+__global__ void k_clara_select(const double* sample_td, int samples, const int32_t* smed, int k,
+                               const km_batch_result* bres, int32_t* medoids_out,
+                               km_clara_result* out, double* sample_td_out) {
+  __shared__ int best;
+  if (threadIdx.x == 0) {
+    int b = 0, st = 0;
+    for (int q = 0; q < samples; ++q) {
+      if (sample_td[q] < sample_td[b]) b = q;
+      if (st == 0 && bres[q].status != 0) st = bres[q].status;
+    }
+    best = b;
+    km_clara_result r;
+    r.td = sample_td[b];
+    r.best_sample = b;
+    r.status = st;
+    *out = r;
+  }
+  __syncthreads();
+  for (int j = threadIdx.x; j < k; j += blockDim.x) medoids_out[j] = smed[(size_t)best * k + j];
+  if (sample_td_out)
+    for (int q = threadIdx.x; q < samples; q += blockDim.x) sample_td_out[q] = sample_td[q];
 }
 
 // CLARA: medoid j of sample q is position smed[q k + j] of that sample;
@@ -1016,25 +1087,43 @@ km_status bfail(km_status s, const char* fmt, ...) {
                    __LINE__);                                                                   \
   } while (0)
 
-template <int WARPS>
+template <int WARPS, int STAGES>
 cudaError_t launch_batch(const BatchArgs& a, int sms, cudaStream_t s) {
-  const size_t sm = sizeof(BatchSmem<WARPS>);
-  cudaError_t e = cudaFuncSetAttribute(k_batch_pam<WARPS>,
+  const size_t sm = sizeof(BatchSmem<WARPS, STAGES>);
+  cudaError_t e = cudaFuncSetAttribute(k_batch_pam<WARPS, STAGES>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
   int per_sm = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_pam<WARPS>, WARPS * 32, sm);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_pam<WARPS, STAGES>,
+                                                    WARPS * 32, sm);
   if (e != cudaSuccess) return e;
   if (per_sm < 1) per_sm = 1;
   int grid = sms * per_sm;
   if (grid > a.count) grid = a.count;
   if (grid < 1) grid = 1;
-  k_batch_pam<WARPS><<<grid, WARPS * 32, sm, s>>>(a);
+  k_batch_pam<WARPS, STAGES><<<grid, WARPS * 32, sm, s>>>(a);
   return cudaGetLastError();
 }
 
-cudaError_t launch_batch_cfg(int cfg, const BatchArgs& a, int sms, cudaStream_t s) {
-  return cfg == 0 ? launch_batch<8>(a, sms, s) : launch_batch<16>(a, sms, s);
+// geometry: 1 .. kBatchGeometries (KM_BATCH_GEOMETRIES)
+cudaError_t launch_batch_geometry(int geometry, const BatchArgs& a, int sms, cudaStream_t s) {
+#define KM_BATCH_CASE(G, W, S) \
+  if (geometry == G) return launch_batch<W, S>(a, sms, s);
+  KM_BATCH_GEOMETRIES(KM_BATCH_CASE)
+#undef KM_BATCH_CASE
+  return cudaErrorInvalidValue;
+}
+
+bool batch_geometry_info(int geometry, int* warps, int* stages) {
+#define KM_BATCH_INFO(G, W, S) \
+  if (geometry == G) {         \
+    *warps = W;                \
+    *stages = S;               \
+    return true;               \
+  }
+  KM_BATCH_GEOMETRIES(KM_BATCH_INFO)
+#undef KM_BATCH_INFO
+  return false;
 }
 
 size_t al256(size_t x) { return (x + 255) / 256 * 256; }
@@ -1067,49 +1156,80 @@ extern "C" size_t kmedoids_batched_workspace_size(int32_t count) {
   return al256(256) + al256(4 * (size_t)count);
 }
 
-static km_status batched_impl(bool start_given, const float* arena, const km_instance* inst,
-                              int32_t count, int32_t* medoids_out, km_batch_result* results,
-                              const km_options* opts, void* ws, size_t ws_bytes, void* stream) {
-  NvtxRange nv(start_given ? "kmedoids_swap_batched" : "kmedoids_run_batched");
-  set_last_error("");
+namespace {
+
+km_status check_batch_args(const float* arena, const km_instance* inst, int32_t count,
+                           int32_t* medoids_out, km_batch_result* results, void* ws) {
   if (!arena || !inst || !medoids_out || !results || !ws) return bfail(KM_E_INVALID, "NULL pointer");
   if (count <= 0 || count > kBatchMaxCount)
     return bfail(KM_E_INVALID, "count must be in [1, %d]", kBatchMaxCount);
   if (reinterpret_cast<uintptr_t>(arena) % 16 || reinterpret_cast<uintptr_t>(ws) % 256)
     return bfail(KM_E_INVALID, "arena must be 16-byte and ws 256-byte aligned");
-  if (ws_bytes < kmedoids_batched_workspace_size(count))
-    return bfail(KM_E_WORKSPACE, "workspace too small");
-  km_options def;
-  km_default_options(&def);
-  const km_options o = opts ? *opts : def;
-  if (o.variant != KM_FASTPAM1 && o.variant != KM_FASTERPAM)
+  return KM_OK;
+}
+
+km_status batch_options(const km_options* opts, km_options* o, int* geometry) {
+  km_default_options(o);
+  if (opts) *o = *opts;
+  if (o->variant != KM_FASTPAM1 && o->variant != KM_FASTERPAM)
     return bfail(KM_E_UNSUPPORTED, "the batched form runs FastPAM1 or FasterPAM (variant %d)",
-                 o.variant);
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
-  unsigned char* w = static_cast<unsigned char*>(ws);
-  unsigned* queue = reinterpret_cast<unsigned*>(w);
-  int32_t* order = reinterpret_cast<int32_t*>(w + al256(256));
+                 o->variant);
+  if (o->tune < 0 || o->tune > kBatchGeometries)
+    return bfail(KM_E_INVALID, "batched tune must be 0 .. %d (kmedoids_batched_autotune picks one)",
+                 kBatchGeometries);
+  *geometry = o->tune == 0 ? 1 : o->tune;
+  return KM_OK;
+}
+
+// Enqueues the ordering kernel and the persistent PAM kernel over both
+// instance tables of `a` (device work only).
+km_status enqueue_batch(BatchArgs& a, unsigned* queue, int32_t* order, const km_options& o,
+                        int geometry, bool start_given, cudaStream_t s) {
   BK(cudaMemsetAsync(queue, 0, 256, s));
-  k_batch_order<<<(count + 255) / 256, 256, 0, s>>>(inst, count, order);
+  k_batch_order<<<(a.count + 255) / 256, 256, 0, s>>>(a.inst, a.count_a, a.inst2, a.count, order);
   BK(cudaGetLastError());
-  BatchArgs a;
-  memset(&a, 0, sizeof(a));
-  a.arena = arena;
-  a.inst = inst;
-  a.count = count;
   a.order = order;
-  a.medoids = medoids_out;
-  a.out = results;
   a.queue = queue;
   a.max_iter = o.max_iter > 0 ? o.max_iter : 10000;
   a.tol = o.tol;
   a.start_given = start_given ? 1 : 0;
   a.eager = (o.variant == KM_FASTERPAM) ? 1 : 0;
-  const int sms = device_sm_count();
-  // tune: 0 automatic (16 warps per CTA), 1 = 8 warps, 2 = 16 warps
-  const int cfg = (o.tune == 1) ? 0 : 1;
-  BK(launch_batch_cfg(cfg, a, sms, s));
+  BK(launch_batch_geometry(geometry, a, device_sm_count(), s));
   return KM_OK;
+}
+
+BatchArgs batch_args(const float* arena, const km_instance* inst, int32_t count,
+                     int32_t* medoids, km_batch_result* results) {
+  BatchArgs a;
+  memset(&a, 0, sizeof(a));
+  a.arena = arena;
+  a.inst = inst;
+  a.count = count;
+  a.count_a = count;
+  a.medoids = medoids;
+  a.out = results;
+  return a;
+}
+
+}  // namespace
+
+static km_status batched_impl(bool start_given, const float* arena, const km_instance* inst,
+                              int32_t count, int32_t* medoids_out, km_batch_result* results,
+                              const km_options* opts, void* ws, size_t ws_bytes, void* stream) {
+  NvtxRange nv(start_given ? "kmedoids_swap_batched" : "kmedoids_run_batched");
+  set_last_error("");
+  km_status r = check_batch_args(arena, inst, count, medoids_out, results, ws);
+  if (r != KM_OK) return r;
+  if (ws_bytes < kmedoids_batched_workspace_size(count))
+    return bfail(KM_E_WORKSPACE, "workspace too small");
+  km_options o;
+  int geometry = 1;
+  r = batch_options(opts, &o, &geometry);
+  if (r != KM_OK) return r;
+  unsigned char* w = static_cast<unsigned char*>(ws);
+  BatchArgs a = batch_args(arena, inst, count, medoids_out, results);
+  return enqueue_batch(a, reinterpret_cast<unsigned*>(w), reinterpret_cast<int32_t*>(w + al256(256)),
+                       o, geometry, start_given, static_cast<cudaStream_t>(stream));
 }
 
 extern "C" km_status kmedoids_run_batched(const float* arena, const km_instance* inst,
@@ -1125,6 +1245,109 @@ extern "C" km_status kmedoids_swap_batched(const float* arena, const km_instance
                                            void* ws, size_t ws_bytes, void* stream) {
   return batched_impl(true, arena, inst, count, medoids_inout, results, opts, ws, ws_bytes,
                       stream);
+}
+
+extern "C" int32_t kmedoids_batched_geometry_info(int32_t geometry, int32_t* warps,
+                                                  int32_t* stages) {
+  int w = 0, st = 0;
+  if (!batch_geometry_info(geometry, &w, &st)) return -1;
+  if (warps) *warps = w;
+  if (stages) *stages = st;
+  return 0;
+}
+
+// ------------------------------------------------------------- autotuner
+// Measured choice of the persistent kernel's geometry for a batch, cached
+// per (device, variant, instance-size histogram): counts of instances per
+// (floor(log2 n), floor(log2 k)) bucket.
+namespace {
+std::mutex g_btune_mu;
+std::map<std::vector<long long>, int> g_btune;
+}  // namespace
+
+extern "C" km_status kmedoids_batched_autotune(const float* arena, const km_instance* inst,
+                                               int32_t count, int32_t* medoids_out,
+                                               km_batch_result* results, const km_options* opts,
+                                               void* ws, size_t ws_bytes, void* stream,
+                                               int32_t* geometry_out, double* ms_out) {
+  NvtxRange nv("kmedoids_batched_autotune");
+  set_last_error("");
+  km_status r = check_batch_args(arena, inst, count, medoids_out, results, ws);
+  if (r != KM_OK) return r;
+  if (!geometry_out) return bfail(KM_E_INVALID, "geometry_out is NULL");
+  if (ws_bytes < kmedoids_batched_workspace_size(count))
+    return bfail(KM_E_WORKSPACE, "workspace too small");
+  km_options o;
+  int geometry = 1;
+  r = batch_options(opts, &o, &geometry);
+  if (r != KM_OK) return r;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  std::vector<km_instance> hi((size_t)count);
+  BK(cudaMemcpyAsync(hi.data(), inst, sizeof(km_instance) * (size_t)count,
+                     cudaMemcpyDeviceToHost, s));
+  BK(cudaStreamSynchronize(s));
+  int dev = 0;
+  BK(cudaGetDevice(&dev));
+  std::vector<long long> key = {dev, o.variant};
+  std::map<std::pair<int, int>, long long> hist;
+  for (const km_instance& in : hi) {
+    const int ln = in.n > 0 ? 31 - __builtin_clz((unsigned)in.n) : -1;
+    const int lk = in.k > 0 ? 31 - __builtin_clz((unsigned)in.k) : -1;
+    hist[{ln, lk}] += 1;
+  }
+  for (auto& e : hist) {
+    key.push_back(e.first.first);
+    key.push_back(e.first.second);
+    key.push_back(e.second);
+  }
+  if (!ms_out) {
+    std::lock_guard<std::mutex> lk(g_btune_mu);
+    auto it = g_btune.find(key);
+    if (it != g_btune.end()) {
+      *geometry_out = it->second;
+      return KM_OK;
+    }
+  }
+  unsigned char* w = static_cast<unsigned char*>(ws);
+  cudaEvent_t e0, e1;
+  BK(cudaEventCreate(&e0));
+  BK(cudaEventCreate(&e1));
+  int best = 1;
+  double best_ms = 1e300;
+  for (int g = 1; g <= kBatchGeometries; ++g) {
+    double ms_g = -1.0;
+    for (int rep = 0; rep < 2; ++rep) {  // the first run warms up
+      BatchArgs a = batch_args(arena, inst, count, medoids_out, results);
+      BK(cudaEventRecord(e0, s));
+      r = enqueue_batch(a, reinterpret_cast<unsigned*>(w), reinterpret_cast<int32_t*>(w + al256(256)),
+                        o, g, false, s);
+      if (r != KM_OK) break;
+      BK(cudaEventRecord(e1, s));
+      BK(cudaStreamSynchronize(s));
+      float ms = 0.f;
+      BK(cudaEventElapsedTime(&ms, e0, e1));
+      ms_g = ms;
+    }
+    if (r != KM_OK) {
+      r = KM_OK;  // a geometry that does not launch here is skipped
+      set_last_error("");
+      ms_g = -1.0;
+    }
+    if (ms_out) ms_out[g - 1] = ms_g;
+    if (ms_g >= 0.0 && ms_g < best_ms) {
+      best_ms = ms_g;
+      best = g;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (best_ms >= 1e300) return bfail(KM_E_CUDA, "no geometry of the batched kernel launched");
+  {
+    std::lock_guard<std::mutex> lk(g_btune_mu);
+    g_btune[key] = best;
+  }
+  *geometry_out = best;
+  return KM_OK;
 }
 
 extern "C" km_status kmedoids_batched_distances(const float* points, int32_t dim,
@@ -1154,13 +1377,155 @@ extern "C" km_status kmedoids_batched_distances(const float* points, int32_t dim
   return KM_OK;
 }
 
+// ----------------------------------------------------------------- CLARA
+namespace {
+
+// Workspace of the CLARA pipeline: the batch queue and processing order
+// (count_a batch instances + the samples), the samples' descriptors,
+// results and medoids, the per-sample TDs (+ one scratch slot) and the
+// sample matrices.
+struct ClaraWs {
+  size_t queue, order, inst, bres, smed, std_, arena, total;
+};
+
+ClaraWs clara_ws(int count_a, int k, int samples, int sample_size) {
+  const int ld = (sample_size + 3) / 4 * 4;
+  ClaraWs L;
+  size_t off = 0;
+  auto take = [&](size_t b) {
+    const size_t r = off;
+    off += al256(b);
+    return r;
+  };
+  L.queue = take(256);
+  L.order = take(4 * ((size_t)count_a + samples));
+  L.inst = take(sizeof(km_instance) * (size_t)samples);
+  L.bres = take(sizeof(km_batch_result) * (size_t)samples);
+  L.smed = take(4 * (size_t)samples * k);
+  L.std_ = take(8 * ((size_t)samples + 1));
+  L.arena = take(4 * (size_t)samples * sample_size * ld);
+  L.total = off;
+  return L;
+}
+
+km_status check_clara_args(const float* X, int64_t n, int32_t d, int32_t k, int32_t samples,
+                           int32_t sample_size, const int32_t* sample_idx, int32_t* medoids_out,
+                           void* ws) {
+  if (!X || !sample_idx || !medoids_out || !ws) return bfail(KM_E_INVALID, "NULL pointer");
+  if (n <= 0 || d <= 0 || d > kDistMaxDim || k <= 0 || samples <= 0 || samples > kBatchMaxCount ||
+      sample_size < k || sample_size > n || sample_size > kBatchMaxN || k > kBatchMaxK)
+    return bfail(KM_E_INVALID, "need 1 <= k <= sample_size <= min(n, %d), k <= %d, "
+                 "1 <= samples <= %d, d <= %d", kBatchMaxN, kBatchMaxK, kBatchMaxCount, kDistMaxDim);
+  if (reinterpret_cast<uintptr_t>(ws) % 256) return bfail(KM_E_INVALID, "ws must be 256-byte aligned");
+  const int dp4 = (d + 3) / 4;
+  if (16 * (size_t)k * dp4 + 8 * 256 > 200 * 1024)
+    return bfail(KM_E_UNSUPPORTED, "k * d too large for the assignment kernel");
+  return KM_OK;
+}
+
+// The whole CLARA method, and optionally a batch of instances, as device
+// work on one stream: sample matrices, one persistent PAM launch over the
+// batch and the samples, medoid positions -> point indices, the full-data
+// assignment of every sample, the choice of the best sample and the labels
+// of its medoids.  Nothing is read back, so the sequence can be captured in
+// a CUDA graph.
+km_status enqueue_clara(const float* arena, const km_instance* inst, int32_t count,
+                        int32_t* medoids_out, km_batch_result* results, const float* X, int64_t n,
+                        int32_t d, int32_t k, int32_t samples, int32_t sample_size,
+                        const int32_t* sample_idx, int32_t* clara_medoids, int32_t* labels,
+                        double* sample_td_out, km_clara_result* clara_res, const km_options& o,
+                        int geometry, unsigned char* w, cudaStream_t s, int64_t* launches) {
+  const ClaraWs L = clara_ws(count, k, samples, sample_size);
+  const int ld = (sample_size + 3) / 4 * 4;
+  km_instance* sinst = reinterpret_cast<km_instance*>(w + L.inst);
+  km_batch_result* bres = reinterpret_cast<km_batch_result*>(w + L.bres);
+  int32_t* smed = reinterpret_cast<int32_t*>(w + L.smed);
+  double* std_ = reinterpret_cast<double*>(w + L.std_);
+  float* sarena = reinterpret_cast<float*>(w + L.arena);
+  k_clara_inst<<<(samples + 255) / 256, 256, 0, s>>>(sinst, samples, sample_size, ld, k);
+  BK(cudaGetLastError());
+  DistArgs da;
+  memset(&da, 0, sizeof(da));
+  da.P = X;
+  da.dim = d;
+  da.idx = sample_idx;
+  da.s = sample_size;
+  da.inst = sinst;
+  da.D = sarena;
+  da.count = samples;
+  const size_t dsm = dist_smem(d);
+  BK(cudaFuncSetAttribute(k_batch_dist, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dsm));
+  k_batch_dist<<<dim3(64, samples), 256, dsm, s>>>(da);
+  BK(cudaGetLastError());
+  BatchArgs a;
+  memset(&a, 0, sizeof(a));
+  a.arena = arena;
+  a.inst = inst;
+  a.count_a = count;
+  a.medoids = medoids_out;
+  a.out = results;
+  a.arena2 = sarena;
+  a.inst2 = sinst;
+  a.medoids2 = smed;
+  a.out2 = bres;
+  a.count = count + samples;
+  km_options ob = o;
+  ob.variant = KM_FASTPAM1;  // CLARA's inner method is BUILD + FastPAM1 (FastCLARA)
+  if (count > 0 && o.variant == KM_FASTERPAM) {
+    // the batch runs FasterPAM: a launch of its own, the samples FastPAM1
+    BatchArgs ab = a;
+    ab.count = count;
+    km_status r = enqueue_batch(ab, reinterpret_cast<unsigned*>(w + L.queue),
+                                reinterpret_cast<int32_t*>(w + L.order), o, geometry, false, s);
+    if (r != KM_OK) return r;
+    a.inst = sinst;
+    a.arena = sarena;
+    a.medoids = smed;
+    a.out = bres;
+    a.count_a = samples;
+    a.count = samples;
+    *launches += 2;
+  }
+  km_status r = enqueue_batch(a, reinterpret_cast<unsigned*>(w + L.queue),
+                              reinterpret_cast<int32_t*>(w + L.order), ob, geometry, false, s);
+  if (r != KM_OK) return r;
+  k_clara_map<<<(samples * k + 255) / 256, 256, 0, s>>>(smed, sample_idx, samples, k, sample_size);
+  BK(cudaGetLastError());
+  BK(cudaMemsetAsync(std_, 0, 8 * ((size_t)samples + 1), s));
+  const int dp4 = (d + 3) / 4;
+  const size_t per_sample = 16 * (size_t)k * dp4 + 8 * 256;
+  const size_t smem_cap = 200 * 1024;
+  const int group = (int)std::min<size_t>((size_t)samples, smem_cap / per_sample);
+  const int agrid = device_sm_count() * 8;
+  *launches += 5;  // descriptors, distances, order, PAM, medoid map
+  for (int q0 = 0; q0 < samples; q0 += group) {
+    const int nq = std::min(group, samples - q0);
+    BK(launch_clara_assign(X, n, d, dp4, smed + (size_t)q0 * k, k, nq, std_ + q0, nullptr, agrid, s));
+    ++*launches;
+  }
+  k_clara_select<<<1, 256, 0, s>>>(std_, samples, smed, k, bres, clara_medoids, clara_res,
+                                   sample_td_out);
+  BK(cudaGetLastError());
+  ++*launches;
+  if (labels) {
+    // labels of the chosen medoids; the TD this pass adds lands in the scratch slot
+    BK(launch_clara_assign(X, n, d, dp4, clara_medoids, k, 1, std_ + samples, labels, agrid, s));
+    ++*launches;
+  }
+  return KM_OK;
+}
+
+}  // namespace
+
 extern "C" size_t kmedoids_clara_workspace_size(int32_t k, int32_t samples, int32_t sample_size) {
   if (k <= 0 || samples <= 0 || sample_size < k) return 0;
-  const int ld = (sample_size + 3) / 4 * 4;
-  return al256(kmedoids_batched_workspace_size(samples)) +
-         al256(sizeof(km_instance) * (size_t)samples) +
-         al256(sizeof(km_batch_result) * (size_t)samples) + al256(4 * (size_t)samples * k) +
-         al256(8 * ((size_t)samples + 1)) + al256(4 * (size_t)samples * sample_size * ld);
+  return clara_ws(0, k, samples, sample_size).total + al256(sizeof(km_clara_result));
+}
+
+extern "C" size_t kmedoids_batched_clara_workspace_size(int32_t count, int32_t k, int32_t samples,
+                                                        int32_t sample_size) {
+  if (count < 0 || k <= 0 || samples <= 0 || sample_size < k) return 0;
+  return clara_ws(count, k, samples, sample_size).total;
 }
 
 extern "C" km_status kmedoids_clara(const float* X, int64_t n, int32_t d, int32_t k,
@@ -1170,93 +1535,69 @@ extern "C" km_status kmedoids_clara(const float* X, int64_t n, int32_t d, int32_
                                     km_result* res, void* ws, size_t ws_bytes, void* stream) {
   NvtxRange nv("kmedoids_clara");
   set_last_error("");
-  if (!X || !sample_idx || !medoids_out || !ws) return bfail(KM_E_INVALID, "NULL pointer");
-  if (n <= 0 || d <= 0 || d > kDistMaxDim || k <= 0 || samples <= 0 || samples > kBatchMaxCount ||
-      sample_size < k || sample_size > n || sample_size > kBatchMaxN || k > kBatchMaxK)
-    return bfail(KM_E_INVALID, "need 1 <= k <= sample_size <= min(n, %d), k <= %d, "
-                 "1 <= samples <= %d, d <= %d", kBatchMaxN, kBatchMaxK, kBatchMaxCount, kDistMaxDim);
+  km_status r = check_clara_args(X, n, d, k, samples, sample_size, sample_idx, medoids_out, ws);
+  if (r != KM_OK) return r;
   if (ws_bytes < kmedoids_clara_workspace_size(k, samples, sample_size))
     return bfail(KM_E_WORKSPACE, "workspace too small");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  const int ld = (sample_size + 3) / 4 * 4;
   unsigned char* w = static_cast<unsigned char*>(ws);
-  size_t off = 0;
-  auto take = [&](size_t b) {
-    unsigned char* p = w + off;
-    off += al256(b);
-    return p;
-  };
-  unsigned char* bws = take(kmedoids_batched_workspace_size(samples));
-  km_instance* inst = reinterpret_cast<km_instance*>(take(sizeof(km_instance) * samples));
-  km_batch_result* bres = reinterpret_cast<km_batch_result*>(take(sizeof(km_batch_result) * samples));
-  int32_t* smed = reinterpret_cast<int32_t*>(take(4 * (size_t)samples * k));
-  double* std_ = reinterpret_cast<double*>(take(8 * ((size_t)samples + 1)));
-  float* arena = reinterpret_cast<float*>(take(4 * (size_t)samples * sample_size * ld));
-  std::vector<km_instance> hi((size_t)samples);
-  for (int q = 0; q < samples; ++q) {
-    hi[q].offset = (int64_t)q * sample_size * ld;
-    hi[q].n = sample_size;
-    hi[q].ld = ld;
-    hi[q].k = k;
-    hi[q].medoid_offset = q * k;
-  }
-  BK(cudaMemcpyAsync(inst, hi.data(), sizeof(km_instance) * samples, cudaMemcpyHostToDevice, s));
-  DistArgs da;
-  memset(&da, 0, sizeof(da));
-  da.P = X;
-  da.dim = d;
-  da.idx = sample_idx;
-  da.s = sample_size;
-  da.inst = inst;
-  da.D = arena;
-  da.count = samples;
-  const size_t dsm = dist_smem(d);
-  BK(cudaFuncSetAttribute(k_batch_dist, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dsm));
-  k_batch_dist<<<dim3(64, samples), 256, dsm, s>>>(da);
-  BK(cudaGetLastError());
+  const ClaraWs L = clara_ws(0, k, samples, sample_size);
+  km_clara_result* cres = reinterpret_cast<km_clara_result*>(w + L.total);
   km_options o;
   km_default_options(&o);
-  km_status r = kmedoids_run_batched(arena, inst, samples, smed, bres, &o, bws,
-                                     kmedoids_batched_workspace_size(samples), stream);
+  int64_t launches = 0;
+  r = enqueue_clara(nullptr, nullptr, 0, nullptr, nullptr, X, n, d, k, samples, sample_size,
+                    sample_idx, medoids_out, labels_out, nullptr, cres, o, 1, w, s, &launches);
   if (r != KM_OK) return r;
-  // sample-local medoid positions -> point indices
-  k_clara_map<<<(samples * k + 255) / 256, 256, 0, s>>>(smed, sample_idx, samples, k, sample_size);
-  BK(cudaGetLastError());
-  BK(cudaMemsetAsync(std_, 0, 8 * (size_t)samples, s));
-  const int dp4 = (d + 3) / 4;
-  const size_t per_sample = 16 * (size_t)k * dp4 + 8 * 256;
-  const size_t smem_cap = 200 * 1024;
-  if (per_sample > smem_cap) return bfail(KM_E_UNSUPPORTED, "k * d too large for the assignment kernel");
-  const int group = (int)std::min<size_t>((size_t)samples, smem_cap / per_sample);
-  const int agrid = device_sm_count() * 8;
-  int64_t launches = 4;  // distances, order, PAM, medoid map
-  for (int q0 = 0; q0 < samples; q0 += group) {
-    const int nq = std::min(group, samples - q0);
-    BK(launch_clara_assign(X, n, d, dp4, smed + (size_t)q0 * k, k, nq, std_ + q0, nullptr, agrid, s));
-    ++launches;
-  }
+  km_clara_result hres;
   std::vector<double> tds((size_t)samples);
-  BK(cudaMemcpyAsync(tds.data(), std_, 8 * (size_t)samples, cudaMemcpyDeviceToHost, s));
-  BK(cudaStreamSynchronize(s));
-  int best = 0;
-  for (int q = 1; q < samples; ++q)
-    if (tds[q] < tds[best]) best = q;
-  BK(cudaMemcpyAsync(medoids_out, smed + (size_t)best * k, 4 * (size_t)k, cudaMemcpyDeviceToDevice, s));
-  if (labels_out) {
-    // labels of the chosen medoids; the TD this pass adds lands in a scratch slot
-    BK(launch_clara_assign(X, n, d, dp4, smed + (size_t)best * k, k, 1, std_ + samples, labels_out,
-                           agrid, s));
-    ++launches;
-  }
+  BK(cudaMemcpyAsync(&hres, cres, sizeof(hres), cudaMemcpyDeviceToHost, s));
+  BK(cudaMemcpyAsync(tds.data(), w + L.std_, 8 * (size_t)samples, cudaMemcpyDeviceToHost, s));
   BK(cudaStreamSynchronize(s));
   if (sample_td_host)
     for (int q = 0; q < samples; ++q) sample_td_host[q] = tds[q];
   if (res) {
     memset(res, 0, sizeof(*res));
-    res->td = tds[best];
-    res->best_sample = best;
-    res->status = KM_OK;
+    res->td = hres.td;
+    res->best_sample = hres.best_sample;
+    res->status = hres.status;
     res->kernel_launches = launches;
   }
+  if (hres.status != 0) return bfail((km_status)hres.status, "a CLARA sample failed (status %d)",
+                                     hres.status);
   return KM_OK;
+}
+
+extern "C" km_status kmedoids_run_batched_clara(
+    const float* arena, const km_instance* inst, int32_t count, int32_t* medoids_out,
+    km_batch_result* results, const float* X, int64_t n, int32_t d, int32_t k, int32_t samples,
+    int32_t sample_size, const int32_t* sample_idx, int32_t* clara_medoids_out,
+    int32_t* clara_labels_out, double* sample_td, km_clara_result* clara_result,
+    const km_options* opts, void* ws, size_t ws_bytes, void* stream) {
+  NvtxRange nv("kmedoids_run_batched_clara");
+  set_last_error("");
+  km_status r;
+  if (count > 0) {
+    r = check_batch_args(arena, inst, count, medoids_out, results, ws);
+    if (r != KM_OK) return r;
+  } else if (count < 0) {
+    return bfail(KM_E_INVALID, "count must be >= 0");
+  }
+  r = check_clara_args(X, n, d, k, samples, sample_size, sample_idx, clara_medoids_out, ws);
+  if (r != KM_OK) return r;
+  if (!clara_result) return bfail(KM_E_INVALID, "clara_result is NULL");
+  if (count + (int64_t)samples > kBatchMaxCount)
+    return bfail(KM_E_INVALID, "count + samples must be <= %d", kBatchMaxCount);
+  if (ws_bytes < kmedoids_batched_clara_workspace_size(count, k, samples, sample_size))
+    return bfail(KM_E_WORKSPACE, "workspace too small");
+  km_options o;
+  int geometry = 1;
+  r = batch_options(opts, &o, &geometry);
+  if (r != KM_OK) return r;
+  int64_t launches = 0;
+  return enqueue_clara(count > 0 ? arena : nullptr, count > 0 ? inst : nullptr, count,
+                       medoids_out, results, X, n, d, k, samples, sample_size, sample_idx,
+                       clara_medoids_out, clara_labels_out, sample_td, clara_result, o, geometry,
+                       static_cast<unsigned char*>(ws), static_cast<cudaStream_t>(stream),
+                       &launches);
 }

@@ -29,7 +29,9 @@ EXPORTS = ["km_default_options", "kmedoids_workspace_size", "kmedoids_build",
            "kmedoids_batched_distances", "kmedoids_run_batched",
            "kmedoids_swap_batched", "kmedoids_clara_workspace_size", "kmedoids_clara",
            "kmedoids_geometry_info", "kmedoids_init_weighted",
-           "kmedoids_init_lab", "kmedoids_wait_selftest", "kmedoids_build_features"]
+           "kmedoids_init_lab", "kmedoids_wait_selftest", "kmedoids_build_features",
+           "kmedoids_batched_geometry_info", "kmedoids_batched_autotune",
+           "kmedoids_batched_clara_workspace_size", "kmedoids_run_batched_clara"]
 
 
 class KmError(RuntimeError):
@@ -138,6 +140,15 @@ def load(path: str = LIB_PATH):
         lib.kmedoids_init_lab.argtypes = [P, i32, i64, i64, i32, i32, P, P, P, P, sz,
                                           P]
         lib.kmedoids_init_lab.restype = i32
+        lib.kmedoids_batched_geometry_info.argtypes = [i32, P, P]
+        lib.kmedoids_batched_geometry_info.restype = i32
+        lib.kmedoids_batched_autotune.argtypes = [P, P, i32, P, P, opt_p, P, sz, P, P, P]
+        lib.kmedoids_batched_autotune.restype = i32
+        lib.kmedoids_batched_clara_workspace_size.argtypes = [i32, i32, i32, i32]
+        lib.kmedoids_batched_clara_workspace_size.restype = sz
+        lib.kmedoids_run_batched_clara.argtypes = [P, P, i32, P, P, P, i64, i32, i32, i32, i32,
+                                                   P, P, P, P, P, opt_p, P, sz, P]
+        lib.kmedoids_run_batched_clara.restype = i32
         lib.kmedoids_wait_selftest.argtypes = [i32, i64, P, sz, P]
         lib.kmedoids_wait_selftest.restype = i32
         lib.kmedoids_last_error.restype = ctypes.c_char_p
@@ -604,6 +615,80 @@ def clara(X, k, sample_idx):
     return {"medoids": med, "labels": lab, "sample_td": tds.tolist(),
             "best_sample": res.best_sample, "td": res.td,
             "kernel_launches": res.kernel_launches}
+
+
+CLARA_RESULT_DTYPE = [("td", "<f8"), ("best_sample", "<i4"), ("status", "<i4")]
+
+
+def batched_geometry_info(geometry):
+    """(warps per CTA, ring stages) of batched geometry 1..5."""
+    w, st = ctypes.c_int32(), ctypes.c_int32()
+    if load().kmedoids_batched_geometry_info(int(geometry), ctypes.byref(w), ctypes.byref(st)):
+        raise KmError(1, "unknown batched geometry %d" % geometry)
+    return w.value, st.value
+
+
+def batched_autotune(arena, inst_dev, total_medoids, measure=True, **kw):
+    """kmedoids_batched_autotune: times every geometry of the persistent
+    kernel on this batch; returns (best geometry, per-geometry ms or None)."""
+    import numpy as np
+    torch = _torch()
+    lib = load()
+    count = inst_dev.numel() // 24
+    med = torch.empty(total_medoids, dtype=torch.int32, device=arena.device)
+    res = torch.empty(count * 24, dtype=torch.uint8, device=arena.device)
+    ws = torch.empty(lib.kmedoids_batched_workspace_size(count),
+                     dtype=torch.uint8, device=arena.device)
+    o = options(**kw)
+    g = ctypes.c_int32()
+    ms = np.full(5, -1.0)
+    _check(lib.kmedoids_batched_autotune(
+        ctypes.c_void_p(arena.data_ptr()), ctypes.c_void_p(inst_dev.data_ptr()),
+        count, ctypes.c_void_p(med.data_ptr()), ctypes.c_void_p(res.data_ptr()),
+        ctypes.byref(o), ctypes.c_void_p(ws.data_ptr()), ws.numel(), _stream(),
+        ctypes.byref(g), ms.ctypes.data_as(ctypes.c_void_p) if measure else None))
+    return g.value, (ms.tolist() if measure else None)
+
+
+class BatchedClara:
+    """Device buffers of one kmedoids_run_batched_clara configuration; call
+    enqueue() to run it on the current stream (no host synchronisation, so
+    it can be captured in a CUDA graph and replayed)."""
+
+    def __init__(self, arena, inst_dev, total_medoids, X, k, sample_idx, labels=True, **kw):
+        torch = _torch()
+        lib = load()
+        dev = X.device
+        self.count = 0 if inst_dev is None else inst_dev.numel() // 24
+        self.arena, self.inst, self.X, self.S = arena, inst_dev, X, sample_idx
+        self.k = int(k)
+        self.samples, self.s = sample_idx.shape
+        self.medoids = torch.empty(max(1, total_medoids), dtype=torch.int32, device=dev)
+        self.results = torch.empty(max(1, self.count) * 24, dtype=torch.uint8, device=dev)
+        self.clara_medoids = torch.empty(self.k, dtype=torch.int32, device=dev)
+        self.labels = torch.empty(X.shape[0], dtype=torch.int32, device=dev) if labels else None
+        self.sample_td = torch.empty(self.samples, dtype=torch.float64, device=dev)
+        self.clara_result = torch.empty(16, dtype=torch.uint8, device=dev)
+        self.ws = torch.empty(lib.kmedoids_batched_clara_workspace_size(
+            self.count, self.k, self.samples, self.s), dtype=torch.uint8, device=dev)
+        self.opts = options(**kw)
+
+    def enqueue(self):
+        lib = load()
+        n, d = self.X.shape
+        ptr = lambda t: ctypes.c_void_p(t.data_ptr() if t is not None else 0)  # noqa: E731
+        _check(lib.kmedoids_run_batched_clara(
+            ptr(self.arena), ptr(self.inst), self.count, ptr(self.medoids), ptr(self.results),
+            ptr(self.X), n, d, self.k, self.samples, self.s, ptr(self.S),
+            ptr(self.clara_medoids), ptr(self.labels), ptr(self.sample_td),
+            ptr(self.clara_result), ctypes.byref(self.opts), ptr(self.ws), self.ws.numel(),
+            _stream()))
+
+    def clara_outcome(self):
+        import numpy as np
+        r = np.frombuffer(self.clara_result.cpu().numpy().tobytes(), dtype=CLARA_RESULT_DTYPE)[0]
+        return {"td": float(r["td"]), "best_sample": int(r["best_sample"]),
+                "status": int(r["status"])}
 
 
 def geometry_info(geometry):

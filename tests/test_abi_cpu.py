@@ -112,6 +112,40 @@ def test_invalid_arguments_of_the_newer_entry_points(lib):
     bad = km.options(variant="fastpam2")
     assert lib.kmedoids_run_batched(P(fake), P(fake), 1, P(fake), P(fake), ctypes.byref(bad),
                                     P(fake), 1 << 20, None) == 7
+    # batched geometries: a table of five; tune outside it is rejected
+    w, st = ctypes.c_int32(), ctypes.c_int32()
+    assert lib.kmedoids_batched_geometry_info(1, ctypes.byref(w), ctypes.byref(st)) == 0
+    assert (w.value, st.value) == (16, 4)
+    assert lib.kmedoids_batched_geometry_info(6, None, None) == -1
+    assert lib.kmedoids_batched_geometry_info(0, None, None) == -1
+    bad_tune = km.options(tune=6)
+    assert lib.kmedoids_run_batched(P(fake), P(fake), 1, P(fake), P(fake),
+                                    ctypes.byref(bad_tune), P(fake), 1 << 20, None) == 1
+    g = ctypes.c_int32()
+    assert lib.kmedoids_batched_autotune(P(fake), P(fake), 1, P(fake), P(fake), None,
+                                         P(fake), 16, None, ctypes.byref(g), None) == 2
+    assert lib.kmedoids_batched_autotune(P(fake), P(fake), 1, P(fake), P(fake), None,
+                                         P(fake), 1 << 20, None, None, None) == 1
+    # batch + CLARA in one enqueue: host checks before any device work
+    assert lib.kmedoids_batched_clara_workspace_size(0, 5, 4, 100) > 0
+    assert lib.kmedoids_batched_clara_workspace_size(3, 5, 4, 100) >= \
+        lib.kmedoids_batched_clara_workspace_size(0, 5, 4, 100)
+    assert lib.kmedoids_batched_clara_workspace_size(0, 5, 4, 4) == 0
+    cres = ctypes.c_void_p(fake)
+    args = [None, None, 0, None, None, P(fake), 1000, 8, 5, 4, 100, P(fake), P(fake), None,
+            None, cres, None, P(fake), 1 << 30, None]
+    a = list(args)
+    a[2] = -1
+    assert lib.kmedoids_run_batched_clara(*a) == 1        # negative count
+    a = list(args)
+    a[8] = 200                                             # k > 128
+    assert lib.kmedoids_run_batched_clara(*a) == 1
+    a = list(args)
+    a[15] = None                                           # no result record
+    assert lib.kmedoids_run_batched_clara(*a) == 1
+    a = list(args)
+    a[18] = 1024                                           # workspace too small
+    assert lib.kmedoids_run_batched_clara(*a) == 2
     # a negative wait limit is rejected by every form that waits
     neg = km.options(wait_limit_ns=-1)
     assert lib.kmedoids_run(P(fake), km.KM_F32, 100, 100, 10, P(fake), None, ctypes.byref(neg),

@@ -50,7 +50,7 @@ def _instances(count, n_lo, n_hi, k_hi, seed):
     return specs
 
 
-@pytest.mark.parametrize("tune", [0, 1])
+@pytest.mark.parametrize("tune", [0, 1, 2, 3, 4, 5])
 def test_batched_matches_oracle(tune):
     specs = _instances(36, 20, 700, 30, 123)
     P, offs = wl.batched_points(specs, d=8, seed="batched-test")
@@ -279,3 +279,96 @@ def test_batched_fasterpam_restarts_and_build_match_oracle():
     with pytest.raises(km.KmError) as e:
         km.run_batched(arena, inst1_dev, nmed1, variant="fastpam2")
     assert e.value.status == 7
+
+
+def test_batched_autotune_picks_a_geometry_with_identical_results():
+    """kmedoids_batched_autotune times every geometry of the persistent
+    kernel on the batch and returns the fastest; results do not depend on
+    the geometry, and the choice is cached per instance-size histogram."""
+    specs = _instances(40, 50, 900, 25, 321)
+    P, offs = wl.batched_points(specs, d=8, seed="batched-tune")
+    inst, arena_len, nmed = km.batch_layout(specs)
+    inst_dev = torch.from_numpy(inst.view(np.uint8).copy()).cuda()
+    arena = torch.zeros(arena_len, dtype=torch.float32, device="cuda")
+    km.batched_distances(torch.from_numpy(P).cuda(), offs, inst_dev, arena)
+    g, ms = km.batched_autotune(arena, inst_dev, nmed)
+    assert 1 <= g <= 5 and ms[g - 1] == min(m for m in ms if m >= 0)
+    assert km.batched_autotune(arena, inst_dev, nmed, measure=False)[0] == g  # cached
+    ref_med, ref_res = km.run_batched(arena, inst_dev, nmed, tune=1)
+    for t in range(1, 6):
+        med, res = km.run_batched(arena, inst_dev, nmed, tune=t)
+        assert torch.equal(med, ref_med) and torch.equal(res, ref_res), t
+    with pytest.raises(km.KmError):
+        km.run_batched(arena, inst_dev, nmed, tune=6)
+
+
+def _clara_case():
+    X = wl.gmm_points(6000, 8, 10, seed="clara-test").astype(np.float32)
+    k, samples = 5, 4
+    S = wl.clara_samples(6000, samples, 80 + 4 * k, seed="clara-test")
+    return X, k, S
+
+
+def _check_clara(bc, X, k, S):
+    omed, olab, otds, obest = oracle.clara(X, k, S)
+    out = bc.clara_outcome()
+    assert out["status"] == 0 and out["best_sample"] == obest
+    assert np.allclose(bc.sample_td.cpu().numpy(), otds, rtol=1e-6, atol=0)
+    assert bc.clara_medoids.cpu().numpy().tolist() == omed.tolist()
+    assert np.mean(bc.labels.cpu().numpy() == olab) > 0.999
+    assert abs(out["td"] - otds[obest]) <= 1e-6 * otds[obest]
+
+
+def test_batch_and_clara_in_one_enqueue_captured_in_a_graph():
+    """kmedoids_run_batched_clara: the batch's instances and CLARA's samples
+    share one persistent PAM launch and the whole method (sample matrices,
+    PAM, assignment, choice, labels) is device work only.  Eager and graph
+    replays give the oracle's results for every instance and for CLARA."""
+    specs = [(700, 12), (1100, 20), (300, 4), (64, 64), (2100, 33)]
+    P, offs = wl.batched_points(specs, d=8, seed="batched-clara")
+    inst, arena_len, nmed = km.batch_layout(specs)
+    inst_dev = torch.from_numpy(inst.view(np.uint8).copy()).cuda()
+    arena = torch.zeros(arena_len, dtype=torch.float32, device="cuda")
+    km.batched_distances(torch.from_numpy(P).cuda(), offs, inst_dev, arena)
+    X, k, S = _clara_case()
+    bc = km.BatchedClara(arena, inst_dev, nmed, torch.from_numpy(X).cuda(), k,
+                         torch.from_numpy(S).cuda())
+    bc.enqueue()
+    torch.cuda.synchronize()
+    A = arena.cpu().numpy()
+
+    def check_batch():
+        med = bc.medoids.cpu().numpy()
+        res = np.frombuffer(bc.results.cpu().numpy().tobytes(), dtype=km.BATCH_RESULT_DTYPE)
+        for i, (n, kk) in enumerate(specs):
+            ref = oracle.run(_device_matrix(A, inst, i, n), kk, variant="fastpam1")
+            mo = int(inst[i]["medoid_offset"])
+            assert res[i]["status"] == 0
+            assert med[mo:mo + kk].tolist() == ref["medoids"].tolist(), i
+            assert abs(res[i]["td"] - ref["td"]) <= 1e-9 * max(1.0, ref["td"])
+
+    check_batch()
+    _check_clara(bc, X, k, S)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        bc.enqueue()
+    for _ in range(2):
+        bc.medoids.fill_(-1)
+        bc.clara_medoids.fill_(-1)
+        bc.results.fill_(0)
+        bc.sample_td.fill_(0)
+        g.replay()
+        torch.cuda.synchronize()
+        check_batch()
+        _check_clara(bc, X, k, S)
+
+
+def test_clara_alone_through_the_one_enqueue():
+    """kmedoids_run_batched_clara with no batch instances (count 0) is
+    CLARA as kmedoids_clara computes it."""
+    X, k, S = _clara_case()
+    bc = km.BatchedClara(None, None, 0, torch.from_numpy(X).cuda(), k,
+                         torch.from_numpy(S).cuda())
+    bc.enqueue()
+    torch.cuda.synchronize()
+    _check_clara(bc, X, k, S)
