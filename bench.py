@@ -565,12 +565,12 @@ def run_fasterpam(args, rank, world, local_rank):
     D, spec = make_input(args.workload, dev)
     n, k = spec["n"], spec["k"]
     u = torch.from_numpy(fasterpam_inputs(n, k)).to(dev)
-    ws = km.workspace(n, k, km.KM_F32, km.options(profile=True), device=dev)
+    ws = km.workspace(n, k, km.KM_F32, km.options(profile=True, trace=100000), device=dev)
     torch.cuda.synchronize()
 
-    def step(Dm):
+    def step(Dm, trace=0):
         start = km.init_weighted(Dm, k, u, ws=ws)
-        return km.swap(Dm, start, ws=ws, variant="fasterpam", profile=True)
+        return km.swap(Dm, start, ws=ws, variant="fasterpam", profile=True, trace=trace)
 
     for _ in range(args.warmup):
         step(D)
@@ -592,6 +592,15 @@ def run_fasterpam(args, rank, world, local_rank):
     r0 = results[-1]
     evals = sum(int(r["evaluated"]) * n + k * n for r in results)
     value = world * evals / (total_ms / 1e3)
+    # latency per accepted swap: device timestamps of consecutive swaps
+    # (one untimed traced run)
+    rt = step(D, trace=100000)
+    ts = np.asarray(rt["trace_time_ns"], dtype=np.int64)
+    gaps = np.diff(ts) / 1e3 if len(ts) > 1 else np.zeros(1)
+    per_swap = {"median_us": float(np.median(gaps)), "mean_us": float(np.mean(gaps)),
+                "p90_us": float(np.percentile(gaps, 90)), "swaps": int(rt["swaps"]),
+                "note": "intervals between the device timestamps of consecutive applied "
+                        "swaps (windows without a swap in between included)"}
     e2e = None
     if not args.no_e2e:
         Dh = torch.empty(D.shape, dtype=D.dtype, pin_memory=True)
@@ -625,6 +634,7 @@ def run_fasterpam(args, rank, world, local_rank):
                    "l2": "matrix larger than L2 (no flush needed)",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "full_run_ms": total_ms / args.steps, "swaps": int(r0["swaps"]),
+        "per_swap": per_swap,
         "evaluated": int(r0["evaluated"]), "visited": int(r0["visited"]),
         "scans": int(r0["iterations"]), "fasterpam_ms": float(r0["swap_ms"]), "td": r0["td"],
         "roofline": eager_roofline(r0, n, "k_eager<float> (FasterPAM)", args.workload),

@@ -240,7 +240,8 @@ int kmedoids_geometry_info(int32_t geometry, int32_t *rows, int32_t *stages,
 /* Fill *o with the defaults (FastPAM1, tol 0, automatic tiles). */
 void km_default_options(km_options *o);
 
-/* Bytes of device workspace the calls below need for (n, k, dtype, options).
+/* Bytes of device workspace the calls below need for (n, k, dtype, options)
+ * (the trace capacity and FastPAM2's per-slot partials depend on them).
  * Returns 0 for invalid sizes. */
 size_t kmedoids_workspace_size(int64_t n, int32_t k, int32_t dtype,
                                const km_options *opts);

@@ -324,25 +324,33 @@ __device__ __forceinline__ bool cons_sync(uint64_t* bar, uint32_t& phase, volati
   return ok;
 }
 
-// Grid-wide barrier over co-resident CTAs: arrival counter + generation.
-// Thread 0 of each CTA arrives; all but the last spin on the generation
-// word.  Returns false (in every thread of the CTA) when the wait exceeded
-// limit_ns -- then st->error = kErrTimeout -- or another CTA had already
-// failed.
-__device__ __forceinline__ bool grid_barrier(unsigned* count, unsigned* gen, KmState* st,
+// Release-ordered atomic increment and acquire-ordered load at GPU scope.
+__device__ __forceinline__ void atom_add_release_gpu(unsigned* p, unsigned v) {
+  asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// Grid-wide barrier over co-resident CTAs on a monotonic arrival counter:
+// the e-th barrier of the launch (epoch e = 0, 1, ...; every CTA counts its
+// own) completes when *count reaches (e + 1) * gridDim.x, so no reset and
+// no second word are needed.  Thread 0 of each CTA arrives with a release
+// increment and polls with acquire loads.  Returns false (in every thread
+// of the CTA) when the wait exceeded limit_ns -- then st->error =
+// kErrTimeout -- or another CTA had already failed.  *count starts at 0.
+__device__ __forceinline__ bool grid_barrier(unsigned* count, unsigned& epoch, KmState* st,
                                              int* s_ok, unsigned long long limit_ns) {
   __syncthreads();
   if (threadIdx.x == 0) {
     int ok = 1;
-    const unsigned g = atomicAdd(gen, 0u);
-    __threadfence();
-    if (atomicAdd(count, 1u) == gridDim.x - 1) {
-      atomicExch(count, 0u);
-      __threadfence();
-      atomicAdd(gen, 1u);
-    } else {
+    const unsigned target = (epoch + 1u) * gridDim.x;
+    atom_add_release_gpu(count, 1u);
+    if ((int)(ld_acquire_gpu(count) - target) < 0) {
       const unsigned long long t0 = globaltimer();
-      while (atomicAdd(gen, 0u) == g) {
+      while ((int)(ld_acquire_gpu(count) - target) < 0) {
         if (*(volatile int*)&st->error) {
           ok = 0;
           break;
@@ -354,9 +362,9 @@ __device__ __forceinline__ bool grid_barrier(unsigned* count, unsigned* gen, KmS
         }
       }
     }
-    __threadfence();
     *s_ok = ok;
   }
+  ++epoch;
   __syncthreads();
   return *s_ok != 0;
 }

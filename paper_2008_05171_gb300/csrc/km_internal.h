@@ -124,7 +124,7 @@ struct EagerArgs {
   int32_t* win_slot;      // [2][win_cap] its best slot (-1: not evaluated)
   long long win_cap;
   int win_rows;           // largest window = grid x win_rows positions
-  unsigned* bar;          // grid barrier: arrival count, generation
+  unsigned* bar;          // grid barrier: monotonic arrival count
   void* trace;            // TraceRec[trace_cap]
   int trace_cap;
   int flavour;            // kFasterPAM or kCLARANS

@@ -27,7 +27,8 @@ __global__ void k_wait_selftest(KmState* st, int kind) {
   const unsigned long long lim = wait_limit(st);
   if (kind == 2) {
     if (blockIdx.x != 0) return;
-    (void)grid_barrier(st->bar, st->bar + 1, st, &s_ok, lim);  // records the timeout
+    unsigned epoch = 0;
+    (void)grid_barrier(st->bar, epoch, st, &s_ok, lim);  // records the timeout
     return;
   }
   if (threadIdx.x == 0) {
