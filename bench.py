@@ -784,7 +784,8 @@ def run_ours(args, rank, world, local_rank):
         key, files = name, ("km_stream.cu", "km_device.cuh")
         if name == "build_eval" and incremental:
             key, files = "build_update", ("km_build.cu", "km_device.cuh")
-        ent = prof.get(key + ("_u16" if esize == 2 else ""))
+        key += "_u16" if esize == 2 else ""
+        ent = prof.get(key + "@" + args.workload) or prof.get(key)
         if ent and ent.get("source_hash") == source_hash(files) and \
                 ent.get("workload") == args.workload:
             return ent.get("dram_bytes_per_launch")
