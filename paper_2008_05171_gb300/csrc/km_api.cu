@@ -58,7 +58,7 @@ int64_t rup(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
 struct WsLayout {
   size_t st, med, is_med, near, sec, dn, ds, bdn, removal, td2, partials, slot_partials,
       slot_best, fp2_order, win_delta, win_slot, trace, gains, cand_gain, blist, blvn, blvo,
-      baux, btt, bparts, total;
+      baux, btt, bparts, blk, total;
   int64_t n_pad;
   int k_pad;
   int trace_cap;
@@ -101,6 +101,9 @@ bool make_ws(int64_t n, int k, const km_options* o, WsLayout* L) {
   L->baux = take(sizeof(BuildAux));
   L->btt = take(4 * (size_t)(n_pad / kChunk));
   L->bparts = take(16 * (size_t)(n_pad / kChunk));
+  // results gathered for one read: the final state record, the record as
+  // BUILD left it, the TD pair, the BUILD's row count and gains
+  L->blk = take(1088 + 8 * (size_t)k_pad);
   L->total = off;
   L->n_pad = n_pad;
   L->k_pad = k_pad;
@@ -124,6 +127,7 @@ struct Ctx {
   bool scanned = false;
   int swap_geom = 0, build_geom = 0;  // geometry table entries used
   long long build_rows = 0;           // rows the BUILD passes streamed (-1: on the device)
+  bool graph_loop = false;            // the SWAP loop ran as one graph
   KmState* st() const { return reinterpret_cast<KmState*>(ws + L.st); }
   int esize() const { return dtype == KM_U16 ? 2 : 4; }  // bytes per matrix element
   template <class P>
@@ -287,13 +291,18 @@ km_status read_state(const Ctx& c, KmState* h) {
   return KM_OK;
 }
 
-km_status reset_state(const Ctx& c) {
-  KmState h;
-  memset(&h, 0, sizeof(h));
-  h.last = -1;
-  h.wait_ns = (unsigned long long)c.opt.wait_limit_ns;
-  KM_CUDA(cudaMemcpyAsync(c.st(), &h, sizeof(h), cudaMemcpyHostToDevice, c.s));
+km_status reset_state(Ctx& c) {
+  // on the device: a copy from pageable host memory would synchronise
+  KM_LAUNCH(c, launch_reset_state(c.st(), (unsigned long long)c.opt.wait_limit_ns, c.s));
   return KM_OK;
+}
+
+// The message of a failure a kernel recorded in a state record.
+km_status state_error(const KmState& h) {
+  if (h.error == KM_E_TIMEOUT)
+    return fail(KM_E_TIMEOUT, "a device wait gave up after its limit of %llu ns",
+                h.wait_ns ? h.wait_ns : kWaitLimitNs);
+  return fail((km_status)h.error, "device reported status %d", h.error);
 }
 
 // ------------------------------------------------------------- autotuning
@@ -547,6 +556,111 @@ km_status swap_k1(Ctx& c, KmState* h) {
   return KM_OK;
 }
 
+// ------------------------------------------------- SWAP loop as a graph
+// FastPAM1 to convergence as one CUDA graph: a conditional WHILE node whose
+// body is the evaluation pass, the swap and k_swap_loop_cond (which sets the
+// condition from the device state record).  Built once per distinct set of
+// kernel arguments (matrix, workspace, sizes, geometry, options) and kept,
+// so a repeated call launches one graph and reads nothing back until the end.
+struct SwapGraph {
+  std::vector<unsigned char> key;
+  cudaGraph_t g = nullptr;
+  cudaGraphExec_t e = nullptr;
+};
+std::mutex g_graph_mu;
+std::vector<SwapGraph> g_graphs;  // most recently used last
+constexpr size_t kMaxGraphs = 8;
+std::map<int, cudaStream_t> g_cap_stream;  // per device, for capturing the loop bodies
+
+template <class X>
+void key_add(std::vector<unsigned char>& k, const X& x) {
+  const unsigned char* p = reinterpret_cast<const unsigned char*>(&x);
+  k.insert(k.end(), p, p + sizeof(X));
+}
+
+// Launches the loop graph on c.s; *used = false (nothing enqueued) when a
+// graph cannot be built here, so the caller runs the host-driven loop.
+km_status swap_loop_graph(Ctx& c, const StreamConfig& cfg, int grid, const StreamArgs& sa,
+                          const PointArgs& pa, bool* used) {
+  *used = false;
+  int dev = 0;
+  KM_CUDA(cudaGetDevice(&dev));
+  std::vector<unsigned char> key;
+  key_add(key, dev);
+  key_add(key, c.dtype);
+  key_add(key, cfg);
+  key_add(key, grid);
+  key_add(key, c.opt.max_iter);
+  key_add(key, sa);
+  key_add(key, pa);
+  std::lock_guard<std::mutex> lk(g_graph_mu);
+  cudaGraphExec_t exec = nullptr;
+  for (size_t i = 0; i < g_graphs.size(); ++i)
+    if (g_graphs[i].key == key) {
+      SwapGraph e = g_graphs[i];
+      g_graphs.erase(g_graphs.begin() + (long)i);
+      g_graphs.push_back(e);
+      exec = e.e;
+      break;
+    }
+  if (!exec) {
+    cudaStream_t cs = nullptr;
+    auto it = g_cap_stream.find(dev);
+    if (it != g_cap_stream.end()) {
+      cs = it->second;
+    } else {
+      if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) return KM_OK;
+      g_cap_stream[dev] = cs;
+    }
+    SwapGraph ng;
+    ng.key = key;
+    bool ok = cudaGraphCreate(&ng.g, 0) == cudaSuccess;
+    cudaGraphConditionalHandle h = 0;
+    cudaGraphNodeParams p = {cudaGraphNodeTypeConditional};
+    memset(static_cast<void*>(&p), 0, sizeof(p));  // every union byte, ctx included
+    if (ok) ok = cudaGraphConditionalHandleCreate(&h, ng.g, 1, cudaGraphCondAssignDefault) == cudaSuccess;
+    if (ok) {
+      p.type = cudaGraphNodeTypeConditional;
+      p.conditional.handle = h;
+      p.conditional.type = cudaGraphCondTypeWhile;
+      p.conditional.size = 1;
+      cudaGraphNode_t node;
+      ok = cudaGraphAddNode(&node, ng.g, nullptr, nullptr, 0, &p) == cudaSuccess;
+    }
+    if (ok) {
+      cudaGraph_t body = p.conditional.phGraph_out[0];
+      ok = cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0,
+                                         cudaStreamCaptureModeRelaxed) == cudaSuccess;
+      if (ok) {
+        bool lok = launch_stream(c.dtype, kModeSwap, cfg, grid, sa, cs) == cudaSuccess;
+        lok = lok && launch_apply(c.dtype, pa, cs) == cudaSuccess;
+        lok = lok && launch_swap_loop_cond(c.st(), (unsigned long long)h, c.opt.max_iter, cs) ==
+                         cudaSuccess;
+        cudaGraph_t out = nullptr;
+        const bool eok = cudaStreamEndCapture(cs, &out) == cudaSuccess;
+        ok = lok && eok;
+      }
+    }
+    if (ok) ok = cudaGraphInstantiate(&ng.e, ng.g, 0) == cudaSuccess;
+    if (!ok) {
+      if (ng.e) cudaGraphExecDestroy(ng.e);
+      if (ng.g) cudaGraphDestroy(ng.g);
+      (void)cudaGetLastError();  // the host-driven loop runs instead
+      return KM_OK;
+    }
+    if (g_graphs.size() >= kMaxGraphs) {
+      cudaGraphExecDestroy(g_graphs.front().e);
+      cudaGraphDestroy(g_graphs.front().g);
+      g_graphs.erase(g_graphs.begin());
+    }
+    g_graphs.push_back(ng);
+    exec = ng.e;
+  }
+  KM_CUDA(cudaGraphLaunch(exec, c.s));
+  *used = true;
+  return KM_OK;
+}
+
 km_status do_swap(Ctx& c, Timer& tm, std::vector<std::pair<int, int>>& ev, KmState* h,
                   km_result* res) {
   NvtxRange nv("kmedoids SWAP");
@@ -612,7 +726,7 @@ km_status do_swap(Ctx& c, Timer& tm, std::vector<std::pair<int, int>>& ev, KmSta
       KM_LAUNCH(c, launch_eager(c.dtype, eg, ea, c.s));
       const int e1 = tm.mark();
       ev.push_back({e0, e1});
-      return read_state(c, h);
+      return KM_OK;  // the caller reads the state once at the end
     }
   }
   StreamConfig cfg;
@@ -624,6 +738,17 @@ km_status do_swap(Ctx& c, Timer& tm, std::vector<std::pair<int, int>>& ev, KmSta
   PointArgs pa = point_args(c);
   const int max_iter = c.opt.max_iter;
 
+  if (variant == KM_FASTPAM1 && !tm.on) {
+    // the whole loop on the device, one graph launch (per-pass event timing
+    // with profile != 0 takes the host-driven loop below)
+    bool used = false;
+    km_status gr = swap_loop_graph(c, cfg, grid, sa, pa, &used);
+    if (gr != KM_OK) return gr;
+    if (used) {
+      c.graph_loop = true;
+      return KM_OK;
+    }
+  }
   if (variant == KM_FASTPAM1 || variant == KM_FASTERPAM || variant == KM_FASTCLARANS) {
     const long long pos_limit = (long long)max_iter * c.n;
     int launched = 0, batch = 1;
@@ -671,30 +796,71 @@ km_status do_swap(Ctx& c, Timer& tm, std::vector<std::pair<int, int>>& ev, KmSta
   return KM_OK;
 }
 
-km_status finish(Ctx& c, KmState* h, int32_t* medoids_out, int32_t* labels_out, km_result* res,
-                 const Timer& tm, const std::vector<std::pair<int, int>>& ev_swap) {
-  // final exact TD of the current buffer
+// ------------------------------------------------------------- results
+// Everything a call reports is gathered into the workspace's result block
+// and read with one device-to-host copy, the call's one synchronisation
+// (the trace, when one is asked for, follows in a second copy).
+constexpr size_t kBlkFinal = 0, kBlkBuild = 512, kBlkTd = 1024, kBlkRows = 1040, kBlkGains = 1088;
+
+struct Outcome {
+  KmState fin;    // the state record at the end
+  KmState bld;    // as BUILD left it
   double td_d = 0.0;
   long long td_i = 0;
-  KmState hs;
-  km_status r = read_state(c, &hs);
-  if (r != KM_OK) return r;
-  const int rb = hs.rb;
-  if (c.dtype != KM_F32)
-    KM_CUDA(cudaMemcpyAsync(&td_i, c.at<long long>(c.L.td2) + rb, 8, cudaMemcpyDeviceToHost, c.s));
-  else
-    KM_CUDA(cudaMemcpyAsync(&td_d, c.at<double>(c.L.td2) + rb, 8, cudaMemcpyDeviceToHost, c.s));
+  unsigned long long rows = 0;
+};
+
+km_status gather_and_read(Ctx& c, bool with_build, int32_t* medoids_out, int32_t* labels_out,
+                          Outcome* o) {
+  unsigned char* blk = c.ws + c.L.blk;
   if (medoids_out)
     KM_CUDA(cudaMemcpyAsync(medoids_out, c.at<int32_t>(c.L.med), 4 * (size_t)c.k,
                             cudaMemcpyDeviceToDevice, c.s));
   if (labels_out)
     KM_CUDA(cudaMemcpyAsync(labels_out, c.at<int32_t>(c.L.near), 4 * (size_t)c.n,
                             cudaMemcpyDeviceToDevice, c.s));
-  const int nt = h->ntrace < c.L.trace_cap ? h->ntrace : c.L.trace_cap;
-  std::vector<TraceRec> tr((size_t)(nt > 0 ? nt : 0));
-  if (nt > 0)
-    KM_CUDA(cudaMemcpyAsync(tr.data(), c.at<TraceRec>(c.L.trace), sizeof(TraceRec) * nt,
-                            cudaMemcpyDeviceToHost, c.s));
+  KM_CUDA(cudaMemcpyAsync(blk + kBlkFinal, c.st(), sizeof(KmState), cudaMemcpyDeviceToDevice, c.s));
+  KM_CUDA(cudaMemcpyAsync(blk + kBlkTd, c.at<void>(c.L.td2), 16, cudaMemcpyDeviceToDevice, c.s));
+  size_t bytes = kBlkTd + 16;
+  if (with_build) {
+    KM_CUDA(cudaMemcpyAsync(blk + kBlkRows, &c.at<BuildAux>(c.L.baux)->rows_total, 8,
+                            cudaMemcpyDeviceToDevice, c.s));
+    bytes = kBlkRows + 8;
+    if (c.opt.build_gains) {
+      KM_CUDA(cudaMemcpyAsync(blk + kBlkGains, c.at<double>(c.L.gains), 8 * (size_t)c.k,
+                              cudaMemcpyDeviceToDevice, c.s));
+      bytes = kBlkGains + 8 * (size_t)c.k;
+    }
+  }
+  std::vector<unsigned char> h(bytes);
+  KM_CUDA(cudaMemcpyAsync(h.data(), blk, bytes, cudaMemcpyDeviceToHost, c.s));
+  KM_CUDA(cudaStreamSynchronize(c.s));
+  memcpy(&o->fin, h.data() + kBlkFinal, sizeof(KmState));
+  memset(&o->bld, 0, sizeof(KmState));
+  if (with_build) {
+    memcpy(&o->bld, h.data() + kBlkBuild, sizeof(KmState));
+    memcpy(&o->rows, h.data() + kBlkRows, 8);
+    if (o->bld.error) return state_error(o->bld);
+  }
+  if (o->fin.error) return state_error(o->fin);
+  const int rb = o->fin.rb & 1;
+  if (c.dtype != KM_F32)
+    memcpy(&o->td_i, h.data() + kBlkTd + 8 * rb, 8);
+  else
+    memcpy(&o->td_d, h.data() + kBlkTd + 8 * rb, 8);
+  if (with_build && c.opt.build_gains)
+    memcpy(c.opt.build_gains, h.data() + kBlkGains, 8 * (size_t)c.k);
+  return KM_OK;
+}
+
+km_status copy_trace(Ctx& c, int ntrace) {
+  const int nt = ntrace < c.L.trace_cap ? ntrace : c.L.trace_cap;
+  if (nt <= 0) return KM_OK;
+  if (!c.opt.trace_delta && !c.opt.trace_slot && !c.opt.trace_cand && !c.opt.trace_time_ns)
+    return KM_OK;
+  std::vector<TraceRec> tr((size_t)nt);
+  KM_CUDA(cudaMemcpyAsync(tr.data(), c.at<TraceRec>(c.L.trace), sizeof(TraceRec) * nt,
+                          cudaMemcpyDeviceToHost, c.s));
   KM_CUDA(cudaStreamSynchronize(c.s));
   for (int i = 0; i < nt; ++i) {
     if (c.opt.trace_delta) c.opt.trace_delta[i] = (c.dtype != KM_F32) ? (double)tr[i].di : tr[i].d;
@@ -702,30 +868,27 @@ km_status finish(Ctx& c, KmState* h, int32_t* medoids_out, int32_t* labels_out, 
     if (c.opt.trace_cand) c.opt.trace_cand[i] = tr[i].cand;
     if (c.opt.trace_time_ns) c.opt.trace_time_ns[i] = tr[i].t_ns;
   }
-  if (res) {
-    res->td = (c.dtype != KM_F32) ? (double)td_i : td_d;
-    res->td_i64 = (c.dtype != KM_F32) ? td_i : 0;
-    double sum = 0.0;
-    int cnt = 0;
-    std::vector<double> per;
-    for (auto& p : ev_swap) {
-      if (cnt >= h->iter) break;
-      const double v = tm.ms(p.first, p.second);
-      sum += v;
-      per.push_back(v);
-      ++cnt;
-    }
-    if (tm.on) {
-      res->eval_ms = sum;
-      res->eval_launches = cnt;
-      if (!per.empty()) {
-        std::sort(per.begin(), per.end());
-        const size_t m = per.size() / 2;
-        res->eval_ms_median = (per.size() % 2) ? per[m] : 0.5 * (per[m - 1] + per[m]);
-      }
-    }
-  }
   return KM_OK;
+}
+
+void eval_times(const Timer& tm, const std::vector<std::pair<int, int>>& ev_swap, int passes,
+                km_result* res) {
+  if (!tm.on || !res) return;
+  double sum = 0.0;
+  std::vector<double> per;
+  for (auto& p : ev_swap) {
+    if ((int)per.size() >= passes) break;
+    const double v = tm.ms(p.first, p.second);
+    sum += v;
+    per.push_back(v);
+  }
+  res->eval_ms = sum;
+  res->eval_launches = (int)per.size();
+  if (!per.empty()) {
+    std::sort(per.begin(), per.end());
+    const size_t m = per.size() / 2;
+    res->eval_ms_median = (per.size() % 2) ? per[m] : 0.5 * (per[m - 1] + per[m]);
+  }
 }
 
 }  // namespace
@@ -811,92 +974,85 @@ static km_status run_impl(bool do_b, bool do_s, const void* D, int32_t dtype, in
     if (r != KM_OK) return r;
   }
   const int b1 = tm.mark();
-  KmState hb;
-  r = read_state(c, &hb);
-  if (r != KM_OK) {
-    if (res) res->status = r;
-    return r;
-  }
-  if (res && do_b) {
-    res->build_steps = hb.build_step;
-    if (c.build_rows < 0) {
-      unsigned long long rows = 0;
-      KM_CUDA(cudaMemcpyAsync(&rows, &c.at<BuildAux>(c.L.baux)->rows_total, sizeof(rows),
-                              cudaMemcpyDeviceToHost, c.s));
-      KM_CUDA(cudaStreamSynchronize(c.s));
-      c.build_rows = (long long)rows;
-    }
-    res->build_rows = c.build_rows;
-    if (c.opt.build_gains) {
-      KM_CUDA(cudaMemcpyAsync(c.opt.build_gains, c.at<double>(c.L.gains), 8 * (size_t)k,
-                              cudaMemcpyDeviceToHost, c.s));
-      KM_CUDA(cudaStreamSynchronize(c.s));
-    }
-  }
-  km_status conv = KM_OK;
+  KmState* st_build = reinterpret_cast<KmState*>(c.ws + c.L.blk + kBlkBuild);
+  if (do_b && do_s)  // the SWAP resets the record: keep the BUILD's
+    KM_LAUNCH(c, launch_build_handoff(c.st(), st_build, c.at<int32_t>(c.L.med), c.k, c.s));
+  int s0 = -1, s1 = -1;
   if (do_s) {
     r = reset_state(c);
     if (r != KM_OK) return r;
-    const int s0 = tm.mark();
+    s0 = tm.mark();
     r = do_swap(c, tm, ev_swap, &h, res);
-    const int s1 = tm.mark();
+    s1 = tm.mark();
     if (r != KM_OK) {
       if (res) res->status = r;
       return r;
     }
-    KmState h2;
-    r = read_state(c, &h2);
-    if (r != KM_OK) return r;
-    if (c.k == 1) {
-      h2.iter = h.iter;
-      h2.swaps = h.swaps;
-      h2.ntrace = h.ntrace;
-      h2.done = h.done;
-    }
-    h = h2;
-    if (!h.done) conv = KM_E_NOT_CONVERGED;
-    if (c.opt.variant == KM_FASTCLARANS && h.fails < c.opt.maxneighbor) conv = KM_E_NOT_CONVERGED;
-    if (res) {
-      res->iterations = h.iter;
-      res->swaps = h.swaps;
-      if (c.opt.variant == KM_FASTERPAM && c.k > 1) {
-        res->visited = h.pos;
-        res->iterations = (int)((h.pos + c.n - 1) / c.n);
-      }
-      if (c.opt.variant == KM_FASTCLARANS) {
-        res->visited = h.pos;
-        res->iterations = (int)h.evaluated;
-      }
-      if (c.opt.variant == KM_FASTERPAM || c.opt.variant == KM_FASTCLARANS)
-        res->evaluated = h.evaluated;
-      if (tm.on) res->swap_ms = tm.ms(s0, s1);
-    }
   } else {
     // BUILD only: the cache of the result gives labels and the exact TD
+    if (do_b)
+      KM_CUDA(cudaMemcpyAsync(st_build, c.st(), sizeof(KmState), cudaMemcpyDeviceToDevice, c.s));
     r = reset_state(c);
     if (r != KM_OK) return r;
     r = swap_setup(c);
     if (r != KM_OK) return r;
-    r = read_state(c, &h);
-    if (r != KM_OK) return r;
-    h.iter = 0;
-    h.swaps = 0;
-    h.ntrace = 0;
   }
-  r = finish(c, &h, medoids_io, labels_out, res, tm, ev_swap);
+  Outcome o;
+  r = gather_and_read(c, do_b, medoids_io, labels_out, &o);
+  if (r != KM_OK) {
+    if (res) res->status = r;
+    return r;
+  }
+  KmState hf = o.fin;
+  if (!do_s) {
+    hf.iter = 0;
+    hf.swaps = 0;
+    hf.ntrace = 0;
+    hf.done = 1;
+  } else if (c.k == 1) {
+    hf.iter = h.iter;
+    hf.swaps = h.swaps;
+    hf.ntrace = h.ntrace;
+    hf.done = h.done;
+  }
+  if (c.graph_loop) c.launches += 3 * (long long)o.fin.loop_guard;
+  r = copy_trace(c, hf.ntrace);
   if (r != KM_OK) return r;
+  km_status conv = KM_OK;
+  if (do_s) {
+    if (!hf.done) conv = KM_E_NOT_CONVERGED;
+    if (c.opt.variant == KM_FASTCLARANS && hf.fails < c.opt.maxneighbor) conv = KM_E_NOT_CONVERGED;
+  }
   if (res) {
-    // initial TD: bookkept TD of BUILD, or the cache's exact TD of the start
-    KmState hf;
-    r = read_state(c, &hf);
-    if (r != KM_OK) return r;
+    res->td = (c.dtype != KM_F32) ? (double)o.td_i : o.td_d;
+    res->td_i64 = (c.dtype != KM_F32) ? o.td_i : 0;
     res->td_bookkept = (c.dtype != KM_F32) ? (double)hf.td_book_i : hf.td_book_d;
-    if (do_b) res->td_initial = (c.dtype != KM_F32) ? (double)hb.td_book_i : hb.td_book_d;
+    if (do_b) {
+      res->build_steps = o.bld.build_step;
+      res->build_rows = c.build_rows < 0 ? (long long)o.rows : c.build_rows;
+      res->td_initial = (c.dtype != KM_F32) ? (double)o.bld.td_book_i : o.bld.td_book_d;
+    }
+    if (do_s) {
+      res->iterations = hf.iter;
+      res->swaps = hf.swaps;
+      if (c.opt.variant == KM_FASTERPAM && c.k > 1) {
+        res->visited = hf.pos;
+        res->iterations = (int)((hf.pos + c.n - 1) / c.n);
+      }
+      if (c.opt.variant == KM_FASTCLARANS) {
+        res->visited = hf.pos;
+        res->iterations = (int)hf.evaluated;
+      }
+      if (c.opt.variant == KM_FASTERPAM || c.opt.variant == KM_FASTCLARANS)
+        res->evaluated = hf.evaluated;
+    }
     if (tm.on) {
+      if (do_s) res->swap_ms = tm.ms(s0, s1);
+      eval_times(tm, ev_swap, hf.iter, res);
       res->build_ms = tm.ms(b0, b1);
-      double s = 0.0;
-      for (auto& p : ev_build) s += tm.ms(p.first, p.second);
-      res->build_eval_ms = s;
+      double sb = 0.0;
+      for (auto& p : ev_build) sb += tm.ms(p.first, p.second);
+      res->build_eval_ms = sb;
     }
     res->status = conv;
     res->kernel_launches = c.launches;

@@ -52,7 +52,7 @@ struct KmState {
   long long pos;            // FasterPAM: absolute scan position
   long long last;           // FasterPAM: absolute position of last swap
   int fp2_extra;            // FastPAM2: additional slots queued this pass
-  int pad0;
+  int loop_guard;           // bodies of the SWAP loop graph run so far
   double fp2_dstar;         // FastPAM2: |Delta*| of the pass
   long long fp2_dstar_i;
   unsigned tile_next;       // next candidate tile of the running pass

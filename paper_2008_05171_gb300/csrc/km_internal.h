@@ -227,6 +227,11 @@ cudaError_t launch_apply(int dtype, const PointArgs& a, cudaStream_t s);
 cudaError_t launch_build_commit(int dtype, const PointArgs& a, cudaStream_t s);
 cudaError_t launch_fp2_try(int dtype, const PointArgs& a, cudaStream_t s);
 cudaError_t launch_mark_medoids(const PointArgs& a, cudaStream_t s);
+cudaError_t launch_reset_state(KmState* st, unsigned long long wait_ns, cudaStream_t s);
+cudaError_t launch_build_handoff(KmState* st, KmState* saved, int32_t* med, int k,
+                                 cudaStream_t s);
+cudaError_t launch_swap_loop_cond(KmState* st, unsigned long long handle, int max_iter,
+                                  cudaStream_t s);
 cudaError_t launch_fill_medoid_rows(const PointArgs& a, cudaStream_t s);
 cudaError_t launch_removal_to_double(int dtype, const PointArgs& a, cudaStream_t s);
 cudaError_t launch_matrix_scan(const PointArgs& a, cudaStream_t s);

@@ -547,6 +547,61 @@ cudaError_t launch_fp2_try(int dtype, const PointArgs& a, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+// A fresh state record (every field zero, no last swap, the caller's wait
+// limit), written on the device so that resetting it does not synchronise
+// the host with the stream.
+__global__ void k_reset_state(KmState* st, unsigned long long wait_ns) {
+  unsigned* w = reinterpret_cast<unsigned*>(st);
+  for (int i = threadIdx.x; i < (int)(sizeof(KmState) / 4); i += blockDim.x) w[i] = 0u;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    st->last = -1;
+    st->wait_ns = wait_ns;
+  }
+}
+
+cudaError_t launch_reset_state(KmState* st, unsigned long long wait_ns, cudaStream_t s) {
+  k_reset_state<<<1, 128, 0, s>>>(st, wait_ns);
+  return cudaGetLastError();
+}
+
+// The BUILD -> SWAP hand-off of kmedoids_run: keeps the state record as the
+// BUILD left it (its step count, bookkept TD and any recorded failure) for
+// the one read at the end of the call, before the SWAP resets the record.
+// After a failed BUILD the medoid slots are set to 0 .. k-1 so that the SWAP
+// kernels, which run regardless, index valid rows; the call then reports the
+// BUILD's failure.
+__global__ void k_build_handoff(KmState* st, KmState* saved, int32_t* med, int k) {
+  const unsigned* w = reinterpret_cast<const unsigned*>(st);
+  unsigned* o = reinterpret_cast<unsigned*>(saved);
+  for (int i = threadIdx.x; i < (int)(sizeof(KmState) / 4); i += blockDim.x) o[i] = w[i];
+  if (st->error)
+    for (int j = threadIdx.x; j < k; j += blockDim.x) med[j] = j;
+}
+
+cudaError_t launch_build_handoff(KmState* st, KmState* saved, int32_t* med, int k,
+                                 cudaStream_t s) {
+  k_build_handoff<<<1, 128, 0, s>>>(st, saved, med, k);
+  return cudaGetLastError();
+}
+
+// The condition of the FastPAM1 SWAP loop graph, evaluated after each pass
+// and its swap: run another body while the loop has not converged, no
+// kernel reported an error and fewer than max_iter passes ran.  A guard
+// counted here alone ends the loop after max_iter bodies whatever the other
+// kernels did.
+__global__ void k_swap_loop_cond(KmState* st, cudaGraphConditionalHandle h, int max_iter) {
+  const int g = ++st->loop_guard;
+  const bool more = !st->done && !st->error && st->iter < max_iter && g < max_iter;
+  cudaGraphSetConditional(h, more ? 1u : 0u);
+}
+
+cudaError_t launch_swap_loop_cond(KmState* st, unsigned long long handle, int max_iter,
+                                  cudaStream_t s) {
+  k_swap_loop_cond<<<1, 1, 0, s>>>(st, (cudaGraphConditionalHandle)handle, max_iter);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_mark_medoids(const PointArgs& a, cudaStream_t s) {
   k_mark_medoids<<<(a.k + 255) / 256, 256, 0, s>>>(a);
   return cudaGetLastError();

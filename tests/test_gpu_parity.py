@@ -357,6 +357,73 @@ def test_max_iter_not_converged():
     assert out["trace"][0][1:] == full["trace"][0][1:]
 
 
+@pytest.mark.parametrize("kind", ["i32", "f32", "u16"])
+def test_swap_loop_graph_equals_host_driven_loop(kind):
+    """FastPAM1 without per-pass timing runs its SWAP loop as one CUDA graph
+    (a conditional WHILE node: pass, swap, device-side loop condition); with
+    profile = 1 the host drives the passes.  Both take the same swaps in the
+    same order; the launch counts show which loop ran.  A max_iter cap ends both after that many
+    passes, not converged."""
+    if kind == "f32":
+        Dh = float_instance(2500, 8, 12, "graph-f")
+    else:
+        Dh = int_instance(2500, ("graph", kind))
+    D = dev(Dh)
+    if kind == "u16":  # 16-bit entries, rows padded to 8 elements
+        U = np.zeros((2500, 2504), np.uint16)
+        U[:, :2500] = Dh
+        D = torch.from_numpy(U.view(np.int16)).cuda()
+    g = km.run(D, 14, n=2500, trace=1000)
+    h = km.run(D, 14, n=2500, trace=1000, profile=True)
+    assert g["medoids"].cpu().tolist() == h["medoids"].cpu().tolist()
+    assert g["trace"] == h["trace"] and g["td"] == h["td"]
+    assert g["iterations"] == h["iterations"] and g["swaps"] >= 1
+    # graph: pass, swap and condition per body, one body per pass; host
+    # loop: pass and swap per launch, launched in batches of 1, 2, 4, .. 64
+    # between reads of the state (the passes after convergence exit at once)
+    launched, batch = 0, 1
+    while launched < h["iterations"]:
+        launched, batch = launched + batch, min(2 * batch, 64)
+    assert g["kernel_launches"] - 3 * g["iterations"] == h["kernel_launches"] - 2 * launched
+    start = rand_medoids(2500, 14, 5)
+    for cap in (1, 2, 3):
+        a = km.swap(D, start, n=2500, max_iter=cap, trace=10)
+        b = km.swap(D, start, n=2500, max_iter=cap, trace=10, profile=True)
+        assert a["status_name"] == b["status_name"] == "KM_E_NOT_CONVERGED"
+        assert a["iterations"] == b["iterations"] == cap
+        assert a["trace"] == b["trace"] and a["swaps"] == cap
+    # a second call with the same arguments replays the cached graph
+    g2 = km.run(D, 14, n=2500, trace=1000)
+    assert g2["medoids"].cpu().tolist() == g["medoids"].cpu().tolist()
+    assert g2["kernel_launches"] == g["kernel_launches"]
+
+
+@pytest.mark.parametrize("fill", [0x00, 0xA5, 0xFF])
+def test_workspace_contents_do_not_matter(fill):
+    """Every call initialises what it reads of the caller's workspace: the
+    same BUILD, BUILD + SWAP and SWAP results (state records, counters,
+    TD, trace) from a workspace filled with any byte pattern."""
+    Dh = int_instance(1500, "dirty")
+    D = dev(Dh)
+    ref_b = oracle.pam_build(Dh, 11)
+    ref = oracle.run(Dh, 11, variant="fastpam1")
+    opts = km.options(trace=1000)
+    ws = km.workspace(1500, 11, km.KM_I32, opts)
+    for call in ("build", "run", "swap"):
+        ws.fill_(fill)
+        if call == "build":
+            out = km.build(D, 11, ws=ws, trace=1000)
+            assert out["medoids"].cpu().tolist() == ref_b[0].tolist()
+            assert out["build_steps"] == 11 and out["td_i64"] == int(ref_b[1])
+        elif call == "run":
+            out = km.run(D, 11, ws=ws, trace=1000)
+            assert_same_run(out, ref)
+            assert out["build_steps"] == 11
+        else:
+            out = km.swap(D, ref_b[0], ws=ws, trace=1000)
+            assert_same_run(out, ref)
+
+
 def test_invalid_medoids_and_workspace():
     Dh = int_instance(100, "inv")
     D = dev(Dh)
