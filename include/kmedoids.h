@@ -46,7 +46,10 @@
  *           the new medoid into the removed medoid's slot.  Labels are slots.
  *   ws      DEVICE workspace of at least kmedoids_workspace_size() bytes,
  *           256-byte aligned, owned by the caller; the library never
- *           allocates device memory and keeps no state between calls.
+ *           allocates device memory for data.  What it keeps between calls
+ *           is derived from arguments alone: the measured kernel geometry
+ *           per shape (tune = -1) and up to 8 instantiated CUDA graphs of
+ *           the FastPAM1 SWAP loop, keyed by every argument they embed.
  *   stream  a cudaStream_t (NULL = legacy default stream).  Every call
  *           enqueues its work on this stream and synchronises it before
  *           returning (the result struct is filled on the host).
@@ -579,6 +582,24 @@ km_status kmedoids_eval_swaps_static(const void *D, int32_t dtype, int64_t n,
                                      double *cand_delta, int32_t *cand_slot,
                                      double *best_delta, int32_t *best_slot,
                                      int32_t *best_cand, void *stream);
+
+/* The dissimilarity matrix from host memory into a device buffer (the
+ * input of every entry point above; the paper's method starts from the
+ * matrix, Sec. 1.2).  Copies n rows of n elements of type dtype from host
+ * (row pitch host_ld elements) to D (row pitch ld elements, DEVICE memory
+ * owned by the caller, n * ld elements); columns n .. ld-1 of D are set to
+ * zero.  host_ld >= n and ld >= n.
+ *
+ * When host is page-locked memory (cudaHostAlloc, cudaMallocHost or
+ * cudaHostRegister, one allocation holding every row read) the SMs read it
+ * directly over the CPU-GPU link with 16-byte loads where both pitches and
+ * bases allow (4- or 2-byte loads otherwise); any other host memory is
+ * copied with cudaMemcpy2DAsync.  A device address returns KM_E_INVALID.
+ * The call enqueues on stream and synchronises it, so host may be reused
+ * on return. */
+km_status kmedoids_upload_matrix(const void *host, int64_t host_ld,
+                                 int32_t dtype, int64_t n, void *D,
+                                 int64_t ld, void *stream);
 
 /* Self-test of the bounded device waits (failure detection; the paper has
  * no counterpart).  Launches a kernel whose wait can never be satisfied,

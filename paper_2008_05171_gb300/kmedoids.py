@@ -31,7 +31,8 @@ EXPORTS = ["km_default_options", "kmedoids_workspace_size", "kmedoids_build",
            "kmedoids_geometry_info", "kmedoids_init_weighted",
            "kmedoids_init_lab", "kmedoids_wait_selftest", "kmedoids_build_features",
            "kmedoids_batched_geometry_info", "kmedoids_batched_autotune",
-           "kmedoids_batched_clara_workspace_size", "kmedoids_run_batched_clara"]
+           "kmedoids_batched_clara_workspace_size", "kmedoids_run_batched_clara",
+           "kmedoids_upload_matrix"]
 
 
 class KmError(RuntimeError):
@@ -151,6 +152,8 @@ def load(path: str = LIB_PATH):
         lib.kmedoids_run_batched_clara.restype = i32
         lib.kmedoids_wait_selftest.argtypes = [i32, i64, P, sz, P]
         lib.kmedoids_wait_selftest.restype = i32
+        lib.kmedoids_upload_matrix.argtypes = [P, i64, i32, i64, P, i64, P]
+        lib.kmedoids_upload_matrix.restype = i32
         lib.kmedoids_last_error.restype = ctypes.c_char_p
         lib.kmedoids_version.restype = ctypes.c_char_p
         _LIB = lib
@@ -702,6 +705,31 @@ def geometry_info(geometry):
 
 def version() -> str:
     return load().kmedoids_version().decode()
+
+
+def upload(H, n=None, D=None, ld=None, device=None):
+    """kmedoids_upload_matrix: the n x n matrix H (a CPU tensor with unit
+    column stride, int32 / float32 / 16-bit; pinned memory is read by the
+    SMs over the CPU-GPU link) into the device tensor D (allocated with ld
+    columns when None, ld defaulting to n rounded up to the library's
+    alignment: 4 elements, 8 for 16-bit).  Columns n .. ld-1 of D are set to
+    zero.  Returns D."""
+    torch = _torch()
+    if H.dim() != 2 or H.is_cuda or H.stride(1) != 1:
+        raise ValueError("H must be a 2-D CPU tensor with unit column stride")
+    code = _dtype_code(H)
+    n = H.shape[0] if n is None else int(n)
+    if D is None:
+        a = 8 if code == KM_U16 else 4
+        ld = (n + a - 1) // a * a if ld is None else int(ld)
+        D = torch.empty((n, ld), dtype=H.dtype, device=device or "cuda")
+    if D.dim() != 2 or not D.is_cuda or D.stride(1) != 1 or D.dtype != H.dtype:
+        raise ValueError("D must be a 2-D CUDA tensor of H's dtype with unit column stride")
+    with torch.cuda.device(D.device):
+        _check(load().kmedoids_upload_matrix(
+            ctypes.c_void_p(H.data_ptr()), H.stride(0), code, n,
+            ctypes.c_void_p(D.data_ptr()), D.stride(0), _stream()))
+    return D
 
 
 def wait_selftest(kind, limit_ns, device=None):

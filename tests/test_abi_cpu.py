@@ -161,6 +161,16 @@ def test_invalid_arguments_of_the_newer_entry_points(lib):
     assert lib.kmedoids_wait_selftest(0, 1000, P(fake), 256, None) == 1
     assert lib.kmedoids_wait_selftest(0, 1000, P(fake + 8), 512, None) == 1
     assert lib.kmedoids_wait_selftest(0, 1000, None, 512, None) == 1
+    # matrix upload: dtype, pointers and sizes checked before any CUDA call
+    up = lib.kmedoids_upload_matrix
+    assert up(P(fake), 100, 7, 100, P(fake), 100, None) == 1          # dtype
+    assert up(None, 100, km.KM_F32, 100, P(fake), 100, None) == 1     # host NULL
+    assert up(P(fake), 100, km.KM_F32, 100, None, 100, None) == 1     # D NULL
+    assert up(P(fake), 100, km.KM_F32, 0, P(fake), 100, None) == 1    # n = 0
+    assert up(P(fake), 99, km.KM_F32, 100, P(fake), 100, None) == 1   # host_ld < n
+    assert up(P(fake), 100, km.KM_F32, 100, P(fake), 99, None) == 1   # ld < n
+    assert up(P(fake), 1 << 40, km.KM_F32, 1 << 30, P(fake), 1 << 40, None) == 1
+    assert b"too large" in lib.kmedoids_last_error()
 
 
 def _c_struct_fields(name):
