@@ -81,7 +81,9 @@ typedef enum {
   KM_E_NOT_CONVERGED = 4, /* max_iter reached; results are the best so far */
   KM_E_TIMEOUT = 5,       /* a device-side wait gave up */
   KM_E_NUMERIC = 6,       /* non-finite value met where a distance was due */
-  KM_E_UNSUPPORTED = 7    /* valid but outside the library's limits */
+  KM_E_UNSUPPORTED = 7,   /* valid but outside the library's limits */
+  KM_E_BOUNDS = 8         /* bounds-checking build only: a kernel met an
+                             index out of range and skipped the access */
 } km_status;
 
 /* KM_U16: the compressed integer form -- unsigned 16-bit distances (0 ..
@@ -570,12 +572,13 @@ km_status kmedoids_run_batched_clara(
  * library image; every GPU that loads the library holds it until the
  * process exits.  Limits: n <= 32768 and k <= 512 (larger sizes return
  * KM_E_UNSUPPORTED with a message; nothing is launched).  Allocates nothing
- * (no cudaMalloc, cudaFree or allocating library routine).  The first call
- * on a device looks up the array's device address (cudaGetSymbolAddress)
- * with that device current; make that first call before any stream capture
- * on the device.  All calls share the one array: the call clears what must
- * start at zero, but calls that overlap on the GPU (other streams, other
- * host threads) race on it and must be serialised by the caller. */
+ * (no cudaMalloc, cudaFree or allocating library routine).  Every call
+ * looks up the array's device address on the current device
+ * (cudaGetSymbolAddress).  Like kmedoids_eval_swaps the call synchronises
+ * the stream to return its results, so it cannot be captured in a CUDA
+ * graph.  All calls share the one array: the call clears what must start
+ * at zero, but calls that overlap on the GPU (other streams, other host
+ * threads) race on it and must be serialised by the caller. */
 km_status kmedoids_eval_swaps_static(const void *D, int32_t dtype, int64_t n,
                                      int64_t ld, int32_t k,
                                      const int32_t *medoids,
@@ -608,7 +611,13 @@ km_status kmedoids_upload_matrix(const void *host, int64_t host_ld,
  *           the streaming and on-the-fly kernels);
  *   kind 1  a consumer barrier one of whose two warps never arrives;
  *   kind 2  the grid barrier of the eager kernel, over two CTAs of which
- *           one never arrives.
+ *           one never arrives;
+ *   kind 3  not a wait: the kernels' index check (KM_INB) applied to the
+ *           index 5 and the bound 3, no memory accessed with it.  Returns
+ *           KM_E_BOUNDS, with the index, the bound and the place of the
+ *           check in kmedoids_last_error(), in the bounds-checking build
+ *           (kmedoids_bounds_checked() = 1); KM_OK in the regular build,
+ *           whose checks compile to nothing.
  * Each wait gives up after limit_ns (1 .. 10^10 ns; 0 = the default 4 s),
  * records KM_E_TIMEOUT in the device state record at the start of ws (a
  * DEVICE buffer of at least 512 bytes, 256-byte aligned, caller-owned) and
@@ -618,6 +627,15 @@ km_status kmedoids_upload_matrix(const void *host, int64_t host_ld,
  * in kmedoids_last_error()), KM_E_INVALID for a bad argument. */
 km_status kmedoids_wait_selftest(int32_t kind, int64_t limit_ns, void *ws,
                                  size_t ws_bytes, void *stream);
+
+/* 1 in the bounds-checking build of the library (libkmedoids_bounds.so,
+ * compiled with -DKM_BOUNDS_CHECK), 0 in the regular build.  In the
+ * bounds-checking build every kernel checks each index it loads from
+ * memory (medoids, nearest / second slots, candidates, BUILD list entries,
+ * initialisation picks) against the array it indexes; an index out of
+ * range is recorded (KM_E_BOUNDS, with the index, its bound and the source
+ * line in kmedoids_last_error()) and the access is skipped. */
+int32_t kmedoids_bounds_checked(void);
 
 /* Thread-local description of the last failure ("" if none). */
 const char *kmedoids_last_error(void);

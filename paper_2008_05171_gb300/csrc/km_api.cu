@@ -6,6 +6,7 @@
 // kernels of km_stream.cu, km_points.cu, km_eager.cu and km_init.cu; this
 // file only orders launches and reads the device state record between
 // batches of passes.
+#define KM_SRC_ID 10  // names this file in bounds-check reports
 #include <cmath>
 #include <algorithm>
 #include <cstdarg>
@@ -281,13 +282,12 @@ struct Timer {
   }
 };
 
+km_status state_error(const KmState& h);
+
 km_status read_state(const Ctx& c, KmState* h) {
   KM_CUDA(cudaMemcpyAsync(h, c.st(), sizeof(KmState), cudaMemcpyDeviceToHost, c.s));
   KM_CUDA(cudaStreamSynchronize(c.s));
-  if (h->error == KM_E_TIMEOUT)
-    return fail(KM_E_TIMEOUT, "a device wait gave up after its limit of %llu ns",
-                h->wait_ns ? h->wait_ns : kWaitLimitNs);
-  if (h->error) return fail((km_status)h->error, "device reported status %d", h->error);
+  if (h->error) return state_error(*h);
   return KM_OK;
 }
 
@@ -299,10 +299,9 @@ km_status reset_state(Ctx& c) {
 
 // The message of a failure a kernel recorded in a state record.
 km_status state_error(const KmState& h) {
-  if (h.error == KM_E_TIMEOUT)
-    return fail(KM_E_TIMEOUT, "a device wait gave up after its limit of %llu ns",
-                h.wait_ns ? h.wait_ns : kWaitLimitNs);
-  return fail((km_status)h.error, "device reported status %d", h.error);
+  char buf[256];
+  const int e = state_message(h, buf, sizeof(buf));
+  return fail((km_status)e, "%s", buf);
 }
 
 // ------------------------------------------------------------- autotuning
@@ -412,6 +411,7 @@ BuildArgs build_args(const Ctx& c) {
   a.ld = c.ld;
   a.n = c.n;
   a.n_pad = (int)c.L.n_pad;
+  a.k = c.k;
   a.fshift = c.fshift;
   a.st = c.st();
   a.aux = c.at<BuildAux>(c.L.baux);

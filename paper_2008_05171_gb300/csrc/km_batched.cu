@@ -16,6 +16,7 @@
 // instances of k_batch_pam, then every point of the full data set is
 // assigned to each sample's medoids (FP32 direct differences, FP64 TD sum)
 // and the sample with the least TD wins (lowest index on ties).
+#define KM_SRC_ID 6  // names this file in bounds-check reports
 #include <algorithm>
 #include <cstddef>
 #include <cmath>

@@ -34,6 +34,7 @@
 //   k_build_add      commits the chosen medoid: d_n, the exact TD, the
 //                    medoid arrays and the list U of the points whose d_n
 //                    dropped (warp-aggregated appends).
+#define KM_SRC_ID 3  // names this file in bounds-check reports
 #include <type_traits>
 
 #include "km_device.cuh"
@@ -133,8 +134,9 @@ __global__ void __launch_bounds__(kBuThreads) k_build_update(const BuildArgs a) 
   // the list's share leave at once and take no ticket; the count they read
   // stays unchanged during the launch (the next commit appends to the other
   // counter, which this launch clears first).
-  const long long cnt =
+  long long cnt =
       (MODE == kBuildColsum) ? (long long)n : (long long)__ldcg(&aux->cnt[a.cur]);
+  if (!KM_INB(st, cnt, (long long)n + 1)) cnt = 0;  // the list holds at most n points
   long long g_eff = (cnt + kBuMinRows - 1) / kBuMinRows;
   if (g_eff > groups) g_eff = groups;
   if (g_eff < 1) g_eff = 1;
@@ -161,6 +163,7 @@ __global__ void __launch_bounds__(kBuThreads) k_build_update(const BuildArgs a) 
         e.xo = 0;
       } else {
         e.o = a.list[i];
+        if (!KM_INB(st, e.o, n)) e.o = 0;  // a row that exists; the error is recorded
         e.vn = a.lvn[i];
         e.vo = a.lvo[i];
         e.xn = Tr<T>::fx(bu_from<T>(e.vn), f);
@@ -305,9 +308,11 @@ __global__ void __launch_bounds__(kBuThreads) k_build_add(const BuildArgs a) {
       unsigned lt;
       asm("mov.u32 %0, %%lanemask_lt;" : "=r"(lt));
       const unsigned idx = base + (unsigned)__popc(m & lt);
-      a.list[idx] = o;
-      a.lvn[idx] = bu_bits(v);
-      a.lvo[idx] = bu_bits(prev);
+      if (KM_INB(a.st, idx, a.n_pad)) {
+        a.list[idx] = o;
+        a.lvn[idx] = bu_bits(v);
+        a.lvo[idx] = bu_bits(prev);
+      }
     }
   }
 
@@ -322,7 +327,7 @@ __global__ void __launch_bounds__(kBuThreads) k_build_add(const BuildArgs a) {
                                                   : reinterpret_cast<G*>(&st->build_td_i),
                    bs);
   }
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
+  if (blockIdx.x == 0 && threadIdx.x == 0 && KM_INB(st, st->build_step, a.k)) {
     const int step = st->build_step;
     a.med[step] = c;
     a.is_med[c] = 1;

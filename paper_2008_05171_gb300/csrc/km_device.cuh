@@ -5,6 +5,7 @@
 
 #include <cstdint>
 #include <climits>
+#include <cstdio>
 #include <cuda_runtime.h>
 
 namespace km {
@@ -23,6 +24,7 @@ static_assert(kConsThreads * 4 == kChunk, "4 columns per consumer thread");
 // Status codes written by kernels (same values as km_status).
 constexpr int kErrTimeout = 5;
 constexpr int kErrNumeric = 6;
+constexpr int kErrBounds = 8;
 
 // ---------------------------------------------------------- device state
 // One record per call, in the workspace.  Kernels read it to pick buffers
@@ -65,8 +67,63 @@ struct KmState {
   unsigned check_flags;     // input check: 1 asymmetric, 2 diagonal, 4 value
   unsigned pad1;
   unsigned long long wait_ns;  // limit of every bounded wait (0: kWaitLimitNs)
+  long long bad_index;      // bounds-checking build: first index out of range,
+  long long bad_bound;      //   the bound it broke,
+  int bad_line;             //   the source line of the check (0: none)
+  int bad_src;              //   and the translation unit (KM_SRC_ID)
 };
 static_assert(sizeof(KmState) <= 512, "the workspaces reserve 512 bytes for the state record");
+
+// ------------------------------------------------- bounds-checking build
+// Built with -DKM_BOUNDS_CHECK, every index a kernel loads from memory (a
+// medoid, a nearest / second slot, a candidate, a list entry, a draw, a
+// descriptor offset) is checked against the array it indexes before use.
+// An index out of range records KM_E_BOUNDS with the index, its bound and
+// the place of the check in the state record, and the access is skipped
+// (the kernels then stop at their next check of st->error); nothing traps.
+// Without the flag KM_INB is the constant true and costs nothing.
+#ifndef KM_SRC_ID
+#define KM_SRC_ID 0
+#endif
+#ifdef KM_BOUNDS_CHECK
+static __device__ __noinline__ bool km_index_fault(KmState* st, long long i, long long n,
+                                                   int src, int line) {
+  if (atomicCAS(&st->bad_line, 0, line) == 0) {
+    st->bad_index = i;
+    st->bad_bound = n;
+    st->bad_src = src;
+  }
+  atomicCAS(&st->error, 0, kErrBounds);
+  return false;
+}
+#define KM_INB(st, i, n)                                                           \
+  ((unsigned long long)(long long)(i) < (unsigned long long)(long long)(n) ||     \
+   ::km::km_index_fault((st), (long long)(i), (long long)(n), KM_SRC_ID, __LINE__))
+#else
+#define KM_INB(st, i, n) true
+#endif
+
+// Host: the message of a failure a kernel recorded in a state record (a
+// wait that gave up, an index out of range, another status); returns the
+// status.
+inline int state_message(const KmState& h, char* buf, size_t len) {
+  static const char* const src[] = {"?",           "km_stream.cu",   "km_points.cu",
+                                    "km_build.cu", "km_eager.cu",    "km_features.cu",
+                                    "km_batched.cu", "km_init.cu",   "km_gram.cu",
+                                    "km_selftest.cu", "km_api.cu",   "km_noalloc.cu",
+                                    "km_upload.cu"};
+  if (h.error == kErrTimeout) {
+    snprintf(buf, len, "a device wait gave up after its limit of %llu ns",
+             h.wait_ns ? h.wait_ns : kWaitLimitNs);
+  } else if (h.error == kErrBounds) {
+    const int id = (h.bad_src >= 0 && h.bad_src < 13) ? h.bad_src : 0;
+    snprintf(buf, len, "index %lld out of range [0, %lld) at %s:%d", h.bad_index, h.bad_bound,
+             src[id], h.bad_line);
+  } else {
+    snprintf(buf, len, "device reported status %d", h.error);
+  }
+  return h.error;
+}
 
 // The limit of the bounded waits of a call (set by the host in the state
 // record; 0 selects the default).

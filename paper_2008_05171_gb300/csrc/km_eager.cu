@@ -25,6 +25,7 @@
 // Window length: G positions (one per CTA) after a swap, doubled up to G R
 // after a window without one, so a converged scan streams at full width.
 // Every barrier wait is bounded (KM_E_TIMEOUT), after which each CTA exits.
+#define KM_SRC_ID 4  // names this file in bounds-check reports
 #include <cstdint>
 
 #include "km_device.cuh"
@@ -75,7 +76,8 @@ constexpr int kEM = 2;    // queue entries per lane with loads in flight
 // d_n - d_s), else case (ii) (slot near(o) gets d - d_s); fixed point.
 template <class T>
 __device__ __forceinline__ void swap_hit_e(T d, T dno, T dso, int sl, long long* acc, int k,
-                                           int f) {
+                                           int f, KmState* st) {
+  if (!KM_INB(st, sl, k)) return;
   const long long xd = Tr<T>::fx(d, f), xs = Tr<T>::fx(dso, f);
   if (d < dno) {
     const long long xn = Tr<T>::fx(dno, f);
@@ -255,7 +257,7 @@ __global__ void __launch_bounds__(kEThreads, 1) k_eager(const EagerArgs a) {
 #pragma unroll
             for (int m = 0; m < kEM; ++m)
               if (e0 + lane + 32 * m < total)
-                swap_hit_e<T>(dd[m], dnn[m], dss[m], sl[m], e_acc, k, f);
+                swap_hit_e<T>(dd[m], dnn[m], dss[m], sl[m], e_acc, k, f, st);
           }
           __syncwarp();
         } else {
@@ -267,7 +269,7 @@ __global__ void __launch_bounds__(kEThreads, 1) k_eager(const EagerArgs a) {
               if (hm & (1u << (4 * u + j))) {
                 const int o = 4 * (q0 + u * kEThreads) + j;
                 swap_hit_e<T>(comp4(d4[u], j), __ldcg(dn + o), comp4(e4[u], j),
-                              __ldcg(a.near + o), e_acc, k, f);
+                              __ldcg(a.near + o), e_acc, k, f, st);
               }
         }
       }
@@ -455,7 +457,7 @@ __global__ void __launch_bounds__(kEThreads, 1) k_eager(const EagerArgs a) {
           a.sec[o] = n2;
           dn[o] = d1;
           ds[o] = d2;
-          atomic_add_shared64(&sacc[n1], Tr<T>::fx(d2, f) - Tr<T>::fx(d1, f));
+          if (KM_INB(st, n1, k)) atomic_add_shared64(&sacc[n1], Tr<T>::fx(d2, f) - Tr<T>::fx(d1, f));
           tdl += G(d1);
         }
       }
@@ -468,7 +470,7 @@ __global__ void __launch_bounds__(kEThreads, 1) k_eager(const EagerArgs a) {
         T d1 = Tr<T>::high(), d2 = Tr<T>::high();
 #pragma unroll 4
         for (int j = lane; j < k; j += 32)
-          e_push((T)D[(size_t)s_med[j] * a.ld + oo], j, n1, d1, n2, d2);
+          if (KM_INB(st, s_med[j], n)) e_push((T)D[(size_t)s_med[j] * a.ld + oo], j, n1, d1, n2, d2);
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) {
           const int m1 = __shfl_xor_sync(0xffffffffu, n1, off);
@@ -483,7 +485,7 @@ __global__ void __launch_bounds__(kEThreads, 1) k_eager(const EagerArgs a) {
           a.sec[oo] = n2;
           dn[oo] = d1;
           ds[oo] = d2;
-          atomic_add_shared64(&sacc[n1], Tr<T>::fx(d2, f) - Tr<T>::fx(d1, f));
+          if (KM_INB(st, n1, k)) atomic_add_shared64(&sacc[n1], Tr<T>::fx(d2, f) - Tr<T>::fx(d1, f));
           tdl += G(d1);
         }
       }
@@ -506,7 +508,7 @@ __global__ void __launch_bounds__(kEThreads, 1) k_eager(const EagerArgs a) {
       // barrier below (rescans use c_s for slot i_s)
       const int old = __ldcg(a.med + i_s);
       a.med[i_s] = c_s;
-      a.is_med[old] = 0;
+      if (KM_INB(st, old, n)) a.is_med[old] = 0;
       a.is_med[c_s] = 1;
       if (ntrace < a.trace_cap) {
         TraceRec* tr = static_cast<TraceRec*>(a.trace) + ntrace;

@@ -40,6 +40,7 @@
 // so the bf16 Gram form only decides which candidate rows see a hit; its
 // error near the case boundaries costs at most the error itself because the
 // change function of Eq. (5) is continuous in d(o, c) at d_n and d_s.
+#define KM_SRC_ID 5  // names this file in bounds-check reports
 #include <algorithm>
 #include <cmath>
 #include <cstdarg>
@@ -469,7 +470,7 @@ __global__ void __launch_bounds__(kFeatThreads, 1) k_feat_pass(const FeatArgs a)
             const int sl = m_near[col];
             const bool inner = dd < dn_;
             const int mag = inner ? dsq - dnq : max(dsq - ddq, 0);
-            if (mag > 0) {
+            if (mag > 0 && KM_INB(a.st, sl, a.k)) {
               const unsigned old = atomicAdd(arow + sl, (unsigned)mag);
               if (old + (unsigned)mag < old) {  // this addition wrapped the word
                 atomicAdd(crow + sl, 1u);
@@ -695,7 +696,9 @@ __global__ void __launch_bounds__(256) k_feat_cache(const FeatArgs a) {
     const uint16_t* xo = a.X + (size_t)o * a.ldx;
     int n1 = -1, n2 = -1;
     float q1 = 0.f, q2 = 0.f;
-    for (int j = 0; j < k; ++j) top2f(dist2_rows(xo, a.X + (size_t)a.med[j] * a.ldx, d), j, n1, q1, n2, q2);
+    for (int j = 0; j < k; ++j)
+      if (KM_INB(st, a.med[j], n))
+        top2f(dist2_rows(xo, a.X + (size_t)a.med[j] * a.ldx, d), j, n1, q1, n2, q2);
     const float e1 = sqrtf(q1);
     const float e2 = (n2 < 0) ? Tr<float>::high() : sqrtf(q2);
     a.near[o] = n1;
@@ -708,7 +711,8 @@ __global__ void __launch_bounds__(256) k_feat_cache(const FeatArgs a) {
     // which any finite threshold lets the Gram entries be recovered
     a.thr[o] = (n2 < 0) ? 0.f : 0.5f * (a.norms[o] - q2);
     write_thr_cols(a, o, a.thr[o]);
-    if (n2 >= 0) atomicAdd(&sacc[n1], (unsigned long long)(fxq(e2, scale) - fxq(e1, scale)));
+    if (n2 >= 0 && n1 >= 0)
+      atomicAdd(&sacc[n1], (unsigned long long)(fxq(e2, scale) - fxq(e1, scale)));
     tdl = e1;
   } else if (o < a.n_pad) {
     a.near[o] = 0;
@@ -747,6 +751,7 @@ __global__ void __launch_bounds__(256) k_feat_apply(const FeatArgs a) {
   if (st->error || !st->accept) return;
   const int k = a.k, n = a.n, d = a.d;
   const int i_s = st->best_slot, c_s = st->best_cand;
+  if (!KM_INB(st, i_s, k) || !KM_INB(st, c_s, n)) return;  // uniform for the launch
   const int rb = st->rb;
   const float scale = __int_as_float((127 + a.fq) << 23);
   for (int i = threadIdx.x; i < k; i += blockDim.x) sacc[i] = 0ull;
@@ -762,6 +767,7 @@ __global__ void __launch_bounds__(256) k_feat_apply(const FeatArgs a) {
       n2 = -1;
       for (int j = 0; j < k; ++j) {
         const int m = (j == i_s) ? c_s : a.med[j];
+        if (!KM_INB(st, m, n)) continue;
         top2f(dist2_rows(xo, a.X + (size_t)m * a.ldx, d), j, n1, q1, n2, q2);
       }
     } else {
@@ -785,7 +791,8 @@ __global__ void __launch_bounds__(256) k_feat_apply(const FeatArgs a) {
     a.ds2[o] = q2;
     a.thr[o] = 0.5f * (a.norms[o] - q2);
     write_thr_cols(a, o, a.thr[o]);
-    atomicAdd(&sacc[n1], (unsigned long long)(fxq(e2, scale) - fxq(e1, scale)));
+    if (KM_INB(st, n1, k))
+      atomicAdd(&sacc[n1], (unsigned long long)(fxq(e2, scale) - fxq(e1, scale)));
     tdl = e1;
   }
   const double bs = fblock_sum(tdl, scratch);
@@ -1013,10 +1020,11 @@ struct FCtx {
 km_status f_read(FCtx& c, KmState* h) {
   FK(cudaMemcpyAsync(h, c.st(), sizeof(KmState), cudaMemcpyDeviceToHost, c.s));
   FK(cudaStreamSynchronize(c.s));
-  if (h->error == KM_E_TIMEOUT)
-    return ffail(KM_E_TIMEOUT, "a device wait gave up after its limit of %llu ns",
-                 h->wait_ns ? h->wait_ns : kWaitLimitNs);
-  if (h->error) return ffail((km_status)h->error, "device reported status %d", h->error);
+  if (h->error) {
+    char buf[256];
+    const int e = state_message(*h, buf, sizeof(buf));
+    return ffail((km_status)e, "%s", buf);
+  }
   return KM_OK;
 }
 

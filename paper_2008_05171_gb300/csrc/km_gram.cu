@@ -3,6 +3,7 @@
 // tensor memory).  The Gram entry point exists to validate the MMA operand
 // layout, descriptors and TMEM read-back on their own; the fused SWAP and
 // BUILD kernels of km_features.cu use the same pieces.
+#define KM_SRC_ID 8  // names this file in bounds-check reports
 #include <cstdio>
 
 #include "../../include/kmedoids.h"

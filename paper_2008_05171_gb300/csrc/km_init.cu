@@ -13,6 +13,7 @@
 // 64-bit fixed point (distances enter as floor(x 2^f), the scale of the SWAP
 // sums; integer distances unchanged), so every choice is independent of the
 // summation order.
+#define KM_SRC_ID 7  // names this file in bounds-check reports
 #include <cstdint>
 
 #include "km_device.cuh"
@@ -154,6 +155,7 @@ __global__ void __launch_bounds__(kInitThreads) k_init_weighted(const InitArgs a
     }
     __syncthreads();
     pick = s_pick;
+    if (!KM_INB(a.st, pick, n)) pick = 0;  // a row that exists; the error is recorded
     if (tid == 0) {
       a.med[t] = pick;
       a.flags[pick] = 1;
@@ -198,6 +200,7 @@ __global__ void __launch_bounds__(kInitThreads) k_init_lab(const InitArgs a) {
           else hi = mid;
         }
         p = r + lo;
+        if (!KM_INB(a.st, p, n)) p = -1;
       }
       s_pts[j] = p;
       s_dn[j] = (p >= 0 && t > 0) ? Tr<T>::fx(dn[p], a.fshift) : 0;

@@ -20,6 +20,7 @@ struct NvtxRange {
 
 struct KmState;
 
+
 // Streaming-kernel modes.
 enum StreamMode { kModeSwap = 0, kModeBuild = 1 };
 
@@ -160,6 +161,7 @@ struct BuildArgs {
   long long ld;
   int n;
   int n_pad;
+  int k;               // medoids to choose (length of med and gains)
   int fshift;          // fixed-point exponent f (float data)
   int first;           // commit of step 0
   int cur;             // parity of the step whose list is written / read

@@ -19,6 +19,7 @@
 // 32 consecutive elements of a medoid row.  The template parameter is the
 // stored element type (float, int32, or uint16 widened to int32).
 // Grid-wide results use a last-block-done ticket in the device state.
+#define KM_SRC_ID 2  // names this file in bounds-check reports
 #include <type_traits>
 
 #include "km_device.cuh"
@@ -93,7 +94,9 @@ __global__ void __launch_bounds__(kPtThreads) k_cache_init(const PointArgs a) {
     int n1 = -1, n2 = -1;
     T d1 = Tr<T>::high(), d2 = Tr<T>::high();
     for (int j = 0; j < k; ++j) {
-      const T v = D[(size_t)a.med[j] * a.ld + o];
+      const int m = a.med[j];
+      if (!KM_INB(st, m, n)) continue;
+      const T v = D[(size_t)m * a.ld + o];
       top2_push(v, j, n1, d1, n2, d2);
     }
     a.near[o] = n1;
@@ -172,6 +175,7 @@ __global__ void __launch_bounds__(kPtThreads) k_apply(const PointArgs a) {
   if (st->error || !st->accept) return;  // uniform for the launch
   const int k = a.k, n = a.n;
   const int i_s = st->best_slot, c_s = st->best_cand;
+  if (!KM_INB(st, i_s, k) || !KM_INB(st, c_s, n)) return;  // uniform for the launch
   const int rb = st->rb;
   for (int i = threadIdx.x; i < k; i += blockDim.x) sacc[i] = A(0);
   if (threadIdx.x == 0) s_cnt = 0;
@@ -181,7 +185,7 @@ __global__ void __launch_bounds__(kPtThreads) k_apply(const PointArgs a) {
   T* dn = static_cast<T*>(a.dn);
   T* ds = static_cast<T*>(a.ds);
   G tdl = G(0);
-  if (o < n) {
+  if (o < n && KM_INB(st, a.near[o], k)) {
     int n1 = a.near[o], n2 = a.sec[o];
     T d1 = dn[o], d2 = ds[o];
     if (n1 == i_s || n2 == i_s) {
@@ -219,6 +223,7 @@ __global__ void __launch_bounds__(kPtThreads) k_apply(const PointArgs a) {
     T d1 = Tr<T>::high(), d2 = Tr<T>::high();
     for (int j = lane; j < k; j += 32) {
       const int m = (j == i_s) ? c_s : a.med[j];
+      if (!KM_INB(st, m, n)) continue;
       top2_push((T)D[(size_t)m * a.ld + oo], j, n1, d1, n2, d2);
     }
 #pragma unroll
@@ -229,7 +234,7 @@ __global__ void __launch_bounds__(kPtThreads) k_apply(const PointArgs a) {
       const T e2 = __shfl_xor_sync(0xffffffffu, d2, off);
       top2_merge(n1, d1, n2, d2, m1, e1, m2, e2);
     }
-    if (lane == 0) {
+    if (lane == 0 && n1 >= 0) {
       a.near[oo] = n1;
       a.sec[oo] = n2;
       dn[oo] = d1;
@@ -251,7 +256,7 @@ __global__ void __launch_bounds__(kPtThreads) k_apply(const PointArgs a) {
     __threadfence();
     const int old = a.med[i_s];
     a.med[i_s] = c_s;
-    a.is_med[old] = 0;
+    if (KM_INB(st, old, n)) a.is_med[old] = 0;
     a.is_med[c_s] = 1;
     const int nt = st->ntrace;
     if (nt < a.trace_cap) {
@@ -308,7 +313,8 @@ __global__ void __launch_bounds__(kPtThreads) k_build_commit(const PointArgs a) 
       atomicAdd(reinterpret_cast<unsigned long long*>(&st->build_td_i),
                 static_cast<unsigned long long>((long long)bs));
   }
-  if (blockIdx.x == 0 && threadIdx.x == 0 && c >= 0 && c < n) {
+  if (blockIdx.x == 0 && threadIdx.x == 0 && c >= 0 && c < n &&
+      KM_INB(st, st->build_step, a.k)) {
     const int step = st->build_step;
     a.med[step] = c;
     a.is_med[c] = 1;
@@ -344,8 +350,10 @@ __global__ void __launch_bounds__(kPtThreads) k_fp2_try(const PointArgs a) {
   if (st->error || st->done) return;
   if (a.fp2_index >= st->fp2_extra) return;
   const int i = a.fp2_order[a.fp2_index];
+  if (!KM_INB(st, i, a.k)) return;
   const Key<R> sb = static_cast<const Key<R>*>(a.slot_best)[i];
   const int c = sb.cand;
+  if (!KM_INB(st, c, a.n)) return;
   if (a.is_med[c]) {  // already a medoid after an earlier swap
     if (blockIdx.x == 0 && threadIdx.x == 0) st->accept = 0;
     return;
@@ -394,7 +402,7 @@ __global__ void __launch_bounds__(kPtThreads) k_fp2_try(const PointArgs a) {
 // ------------------------------------------------------------- small ones
 __global__ void k_mark_medoids(const PointArgs a) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j < a.k) a.is_med[a.med[j]] = 1;
+  if (j < a.k && KM_INB(a.st, a.med[j], a.n)) a.is_med[a.med[j]] = 1;
 }
 
 __global__ void k_fill_medoid_rows(const PointArgs a) {

@@ -4,6 +4,7 @@
 // KM_E_TIMEOUT recorded in the device state record, kernel returns -- is
 // exercised without faulting or hanging the GPU.  Nothing is in flight when
 // a wait gives up: no bulk copy, no MMA, no tensor memory.
+#define KM_SRC_ID 9  // names this file in bounds-check reports
 #include <cstdio>
 #include <cstring>
 
@@ -20,11 +21,20 @@ constexpr long long kSelftestMaxNs = 10000000000ll;  // 10 s
 //         arrival that never comes.
 // kind 1: a consumer barrier of two warps; warp 1 leaves without arriving.
 // kind 2: the grid barrier over two CTAs; CTA 1 leaves without arriving.
+// kind 3: the bounds-check recorder: the index 5 checked against the bound
+//         3 (no memory is accessed with it).
 __global__ void k_wait_selftest(KmState* st, int kind) {
   __shared__ __align__(8) uint64_t bar;
   __shared__ int never;
   __shared__ int s_ok;
   const unsigned long long lim = wait_limit(st);
+  if (kind == 3) {
+    if (threadIdx.x == 0) {
+      volatile int bad = 5;  // not a constant the compiler could fold
+      (void)KM_INB(st, bad, 3);
+    }
+    return;
+  }
   if (kind == 2) {
     if (blockIdx.x != 0) return;
     unsigned epoch = 0;
@@ -62,7 +72,7 @@ using namespace km;
 extern "C" km_status kmedoids_wait_selftest(int32_t kind, int64_t limit_ns, void* ws,
                                             size_t ws_bytes, void* stream) {
   set_last_error("");
-  if (kind < 0 || kind > 2) return st_fail(KM_E_INVALID, "kind must be 0, 1 or 2 (got %lld)", kind);
+  if (kind < 0 || kind > 3) return st_fail(KM_E_INVALID, "kind must be 0 .. 3 (got %lld)", kind);
   if (limit_ns < 0 || limit_ns > kSelftestMaxNs)
     return st_fail(KM_E_INVALID, "limit_ns must be in 0 .. 1e10 (got %lld)", (long long)limit_ns);
   if (!ws || reinterpret_cast<uintptr_t>(ws) % 256 != 0 || ws_bytes < 512)
@@ -91,9 +101,19 @@ extern "C" km_status kmedoids_wait_selftest(int32_t kind, int64_t limit_ns, void
     set_last_error(buf);
     return KM_E_CUDA;
   }
-  if (r.error == KM_E_TIMEOUT)
-    return st_fail(KM_E_TIMEOUT, "a device wait gave up after its limit of %lld ns",
-                   (long long)(r.wait_ns ? r.wait_ns : kWaitLimitNs));
-  if (r.error) return st_fail((km_status)r.error, "device reported status %lld", r.error);
+  if (r.error) {
+    char buf[256];
+    const int code = state_message(r, buf, sizeof(buf));
+    set_last_error(buf);
+    return (km_status)code;
+  }
   return KM_OK;
+}
+
+extern "C" int32_t kmedoids_bounds_checked(void) {
+#ifdef KM_BOUNDS_CHECK
+  return 1;
+#else
+  return 0;
+#endif
 }

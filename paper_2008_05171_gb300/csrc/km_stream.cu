@@ -18,6 +18,7 @@
 // stage and walk the R rows.  The SWAP per-slot accumulators live in shared
 // memory (FP64 for float data, int64 for integer data); the fast path of an
 // element is one comparison d < d_s, which fails for most (o, c) pairs.
+#define KM_SRC_ID 1  // names this file in bounds-check reports
 #include <cfloat>
 #include <type_traits>
 
@@ -114,12 +115,13 @@ __device__ __forceinline__ unsigned lanemask_lt() {
 template <class E>
 __device__ __forceinline__ void swap_hit_at(int r, int col, const E* data,
                                             const unsigned char* meta, long long* acc, int k,
-                                            int f) {
+                                            int f, KmState* st) {
   using T = typename Val<E>::type;
   const T d = (T)data[(size_t)r * kChunk + col];
   const T dn = reinterpret_cast<const T*>(meta)[col];
   const T ds = reinterpret_cast<const T*>(meta + 4 * kChunk)[col];
   const int sl = reinterpret_cast<const int32_t*>(meta + 8 * kChunk)[col];
+  if (!KM_INB(st, sl, k)) return;
   long long* ar = acc + (size_t)r * (k + 1);
   const long long xd = Tr<T>::fx(d, f), xs = Tr<T>::fx(ds, f);
   if (d < dn) {
@@ -136,7 +138,7 @@ template <class E>
 __device__ __forceinline__ void swap_stage_hits(unsigned long long hmask, uint16_t* q, int lane,
                                                 int warp, const E* data,
                                                 const unsigned char* meta, long long* acc, int k,
-                                                int f) {
+                                                int f, KmState* st) {
   const int cnt = __popcll(hmask);
   int incl = cnt;
 #pragma unroll
@@ -157,7 +159,7 @@ __device__ __forceinline__ void swap_stage_hits(unsigned long long hmask, uint16
     for (int e = lane; e < total; e += 32) {
       const unsigned v = q[e];
       const int b = (int)(v >> 5), src = (int)(v & 31u);
-      swap_hit_at<E>(b >> 2, 4 * (warp * 32 + src) + (b & 3), data, meta, acc, k, f);
+      swap_hit_at<E>(b >> 2, 4 * (warp * 32 + src) + (b & 3), data, meta, acc, k, f, st);
     }
     __syncwarp();
   } else {
@@ -165,7 +167,7 @@ __device__ __forceinline__ void swap_stage_hits(unsigned long long hmask, uint16
     while (hmask) {
       const int b = __ffsll(hmask) - 1;
       hmask &= hmask - 1;
-      swap_hit_at<E>(b >> 2, 4 * (warp * 32 + lane) + (b & 3), data, meta, acc, k, f);
+      swap_hit_at<E>(b >> 2, 4 * (warp * 32 + lane) + (b & 3), data, meta, acc, k, f, st);
     }
     __syncwarp();
   }
@@ -417,7 +419,7 @@ __global__ void __launch_bounds__(kThreads, MINB) k_stream(const StreamArgs a) {
                             (d4.z < ds4.z ? 4u : 0u) | (d4.w < ds4.w ? 8u : 0u);
         hmask |= (unsigned long long)hm << (4 * r);
       }
-      swap_stage_hits<E>(hmask, queues + warp * kQueue, lane, warp, data, meta, acc, k, f);
+      swap_stage_hits<E>(hmask, queues + warp * kQueue, lane, warp, data, meta, acc, k, f, st);
     } else {
       const int col = chunk * kChunk + 4 * t;
       const bool v0 = col < n, v1 = col + 1 < n, v2 = col + 2 < n, v3 = col + 3 < n;

@@ -8,6 +8,7 @@
 // (about 210 GB/s from Grace memory), where copy-engine transfers of the
 // same buffer took anywhere from that to a quarter of it.  Memory the device
 // cannot address (plain pageable memory) goes through cudaMemcpy2DAsync.
+#define KM_SRC_ID 12  // names this file in bounds-check reports
 #include <cstdio>
 #include <cstring>
 

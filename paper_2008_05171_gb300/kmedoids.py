@@ -13,13 +13,15 @@ import os
 import threading
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "libkmedoids.so")
+# KMEDOIDS_BOUNDS_CHECK=1 selects the bounds-checking build of the library
+LIB_PATH = os.path.join(HERE, "libkmedoids_bounds.so"
+                        if os.environ.get("KMEDOIDS_BOUNDS_CHECK") == "1" else "libkmedoids.so")
 
 KM_I32, KM_F32, KM_U16 = 0, 1, 2
 VARIANTS = {"fastpam1": 0, "fastpam2": 1, "fasterpam": 2, "fastclarans": 3}
 STATUS = {0: "KM_OK", 1: "KM_E_INVALID", 2: "KM_E_WORKSPACE", 3: "KM_E_CUDA",
           4: "KM_E_NOT_CONVERGED", 5: "KM_E_TIMEOUT", 6: "KM_E_NUMERIC",
-          7: "KM_E_UNSUPPORTED"}
+          7: "KM_E_UNSUPPORTED", 8: "KM_E_BOUNDS"}
 EXPORTS = ["km_default_options", "kmedoids_workspace_size", "kmedoids_build",
            "kmedoids_swap", "kmedoids_run", "kmedoids_eval_swaps",
            "kmedoids_cache", "kmedoids_last_error", "kmedoids_version",
@@ -32,7 +34,7 @@ EXPORTS = ["km_default_options", "kmedoids_workspace_size", "kmedoids_build",
            "kmedoids_init_lab", "kmedoids_wait_selftest", "kmedoids_build_features",
            "kmedoids_batched_geometry_info", "kmedoids_batched_autotune",
            "kmedoids_batched_clara_workspace_size", "kmedoids_run_batched_clara",
-           "kmedoids_upload_matrix"]
+           "kmedoids_upload_matrix", "kmedoids_bounds_checked"]
 
 
 class KmError(RuntimeError):
@@ -154,6 +156,8 @@ def load(path: str = LIB_PATH):
         lib.kmedoids_wait_selftest.restype = i32
         lib.kmedoids_upload_matrix.argtypes = [P, i64, i32, i64, P, i64, P]
         lib.kmedoids_upload_matrix.restype = i32
+        lib.kmedoids_bounds_checked.argtypes = []
+        lib.kmedoids_bounds_checked.restype = i32
         lib.kmedoids_last_error.restype = ctypes.c_char_p
         lib.kmedoids_version.restype = ctypes.c_char_p
         _LIB = lib

@@ -155,7 +155,8 @@ def test_invalid_arguments_of_the_newer_entry_points(lib):
                                      ctypes.byref(neg), ctypes.byref(res), P(fake), 1 << 30,
                                      None) == 1
     # wait self-test: kind, limit and workspace checked before any launch
-    assert lib.kmedoids_wait_selftest(3, 1000, P(fake), 512, None) == 1
+    assert lib.kmedoids_wait_selftest(4, 1000, P(fake), 512, None) == 1
+    assert lib.kmedoids_wait_selftest(-1, 1000, P(fake), 512, None) == 1
     assert lib.kmedoids_wait_selftest(0, -1, P(fake), 512, None) == 1
     assert lib.kmedoids_wait_selftest(0, 10 ** 11, P(fake), 512, None) == 1
     assert lib.kmedoids_wait_selftest(0, 1000, P(fake), 256, None) == 1
@@ -214,3 +215,33 @@ def test_ctypes_structs_match_the_header(struct, tmp_path):
                                           text=True).stdout.split()]
     assert out[0] == ctypes.sizeof(cls)
     assert out[1:] == [getattr(cls, f).offset for f in names]
+
+
+def test_bounds_checking_build_loads_and_exports_the_same_symbols(tmp_path):
+    """The -DKM_BOUNDS_CHECK variant (libkmedoids_bounds.so) builds, exports
+    every declared function, reports itself through kmedoids_bounds_checked
+    and validates arguments as the regular build does; the binding loads it
+    when KMEDOIDS_BOUNDS_CHECK=1."""
+    import subprocess
+    import sys
+    from paper_2008_05171_gb300 import build as b
+    path = b.build(bounds_check=True)
+    assert path.endswith("libkmedoids_bounds.so")
+    code = (
+        "import ctypes, sys\n"
+        "sys.path.insert(0, %r)\n"
+        "import paper_2008_05171_gb300.kmedoids as km\n"
+        "assert km.LIB_PATH.endswith('libkmedoids_bounds.so'), km.LIB_PATH\n"
+        "lib = km.load()\n"
+        "assert lib.kmedoids_bounds_checked() == 1\n"
+        "for name in km.EXPORTS: getattr(lib, name)\n"
+        "P = ctypes.c_void_p\n"
+        "assert lib.kmedoids_wait_selftest(4, 1000, P(1 << 20), 512, None) == 1\n"
+        "print('ok')\n" % ROOT)
+    env = dict(os.environ, KMEDOIDS_BOUNDS_CHECK="1")
+    r = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True,
+                       timeout=300)
+    assert r.returncode == 0 and r.stdout.strip() == "ok", r.stderr
+    import paper_2008_05171_gb300.kmedoids as km
+    if os.environ.get("KMEDOIDS_BOUNDS_CHECK") != "1":
+        assert km.load().kmedoids_bounds_checked() == 0
