@@ -26,6 +26,11 @@ k-Medoids Clustering" (arXiv 2008.05171):
                        from given subsample ranks.
 * ``clara``         -- CLARA (Sec. 2.1, FastCLARA of Sec. 3.4) on given
                        samples; ``euclid_f32`` the FP64 -> float32 matrix.
+* ``bi_*``          -- the bichromatic case of the Outlook (``bichromatic.c``):
+                       medoids among m locations (rows), TD over n consumers
+                       (columns); ``bi_td``, ``bi_build`` (Alg. 1, step 0 the
+                       bichromatic medoid), ``bi_eval_swaps`` (brute force or
+                       Eq. (7)), ``bi_swap`` / ``bi_run`` (FastPAM1, Alg. 3).
 
 Parity unpinned: the reading of FastPAM2's additional swaps (the paper
 describes FastPAM2 only in words, Sec. 3.2, and prints no values for it).
@@ -42,6 +47,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "kmedoids_oracle.c")
+_SRC_BI = os.path.join(_HERE, "bichromatic.c")
 _SO = os.path.join(_HERE, "liboracle.so")
 _LOCK = threading.Lock()
 _LIB = None
@@ -54,12 +60,12 @@ EVAL_METHODS = {"bruteforce": 0, "pam": 1, "fastpam1": 2}
 def build(force: bool = False) -> str:
     """Compile the oracle with gcc (OpenMP over candidates) in place."""
     if force or not os.path.exists(_SO) or \
-            os.path.getmtime(_SO) < os.path.getmtime(_SRC):
+            os.path.getmtime(_SO) < max(os.path.getmtime(_SRC), os.path.getmtime(_SRC_BI)):
         tmp = _SO + ".tmp%d" % os.getpid()
         # -ffp-contract=off: no fused multiply-add unless the source asks for
         # one, so the results do not depend on the host architecture
         subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fPIC", "-shared",
-                               "-fopenmp", "-o", tmp, _SRC, "-lm"])
+                               "-fopenmp", "-o", tmp, _SRC, _SRC_BI, "-lm"])
         os.replace(tmp, _SO)
     return _SO
 
@@ -107,6 +113,16 @@ def _lib():
             lib.oracle_clara.restype = i32
             lib.oracle_clara.argtypes = [P, i64, i32, i32, i32, i32, P, P, P,
                                          P, P]
+            lib.oracle_bi_td.restype = f64
+            lib.oracle_bi_td.argtypes = [P, i32, i64, i64, i64, P, i32, P]
+            lib.oracle_bi_build.restype = i32
+            lib.oracle_bi_build.argtypes = [P, i32, i64, i64, i64, i32, P, P, P]
+            lib.oracle_bi_eval_swaps.restype = None
+            lib.oracle_bi_eval_swaps.argtypes = [P, i32, i64, i64, i64, P, i32, i32,
+                                                 P, P, P, P, P]
+            lib.oracle_bi_swap.restype = i32
+            lib.oracle_bi_swap.argtypes = [P, i32, i64, i64, i64, i32, P, i32, f64,
+                                           P, P, i32, P, P, P]
             lib.oracle_num_threads.restype = i32
             lib.oracle_set_threads.argtypes = [i32]
             _LIB = lib
@@ -362,6 +378,89 @@ def run(D, k, variant="fastpam1", n=None, **kw):
     """BUILD followed by SWAP (the paper's full PAM / FastPAM1 / FasterPAM)."""
     med, td_build, _ = pam_build(D, k, n=n)
     out = swap(D, med, variant=variant, n=n, **kw)
+    out["build_medoids"] = med
+    out["td_build"] = td_build
+    return out
+
+
+# ------------------------------------------------------------ bichromatic
+def _bimat(D: np.ndarray, n: int | None = None):
+    """(array, dtype code, m, n, ld) of an (m locations, ld) matrix whose
+    first n columns are the consumers: d(x_c, x_l) = D[l, c]."""
+    D = np.ascontiguousarray(D)
+    if D.dtype == np.int32:
+        code = 0
+    elif D.dtype == np.float32:
+        code = 1
+    else:
+        raise TypeError("oracle matrices are int32 or float32")
+    m, ld = D.shape
+    n = ld if n is None else int(n)
+    if n > ld:
+        raise ValueError("n exceeds the row length")
+    return D, code, m, n, ld
+
+
+def bi_td(D, medoids, n=None, return_labels=False):
+    """TD over the consumers (Eq. (2)) of medoid locations ``medoids``."""
+    D, code, m, n, ld = _bimat(D, n)
+    med = _med(medoids)
+    labels = np.empty(n, np.int32)
+    v = _lib().oracle_bi_td(_p(D), code, m, n, ld, _p(med), len(med), _p(labels))
+    return (float(v), labels) if return_labels else float(v)
+
+
+def bi_build(D, k, n=None):
+    """BUILD over the locations (Alg. 1): (medoids, TD, gain per step)."""
+    D, code, m, n, ld = _bimat(D, n)
+    med = np.empty(k, np.int32)
+    tdv = np.zeros(1, np.float64)
+    steps = np.zeros(k, np.float64)
+    if _lib().oracle_bi_build(_p(D), code, m, n, ld, int(k), _p(med), _p(tdv), _p(steps)) != 0:
+        raise ValueError("oracle_bi_build: need 1 <= k <= m")
+    return med, float(tdv[0]), steps
+
+
+def bi_eval_swaps(D, medoids, method="fastpam1", n=None):
+    """Every (slot, location) swap: (cand_delta[m], cand_slot[m], (best_delta,
+    best_slot, best_location))."""
+    D, code, m, n, ld = _bimat(D, n)
+    med = _med(medoids)
+    cd = np.zeros(m, np.float64)
+    cs = np.zeros(m, np.int32)
+    bd = np.zeros(1, np.float64)
+    bs = np.zeros(1, np.int32)
+    bc = np.zeros(1, np.int64)
+    _lib().oracle_bi_eval_swaps(_p(D), code, m, n, ld, _p(med), len(med),
+                                EVAL_METHODS[method], _p(cd), _p(cs), _p(bd), _p(bs), _p(bc))
+    return cd, cs, (float(bd[0]), int(bs[0]), int(bc[0]))
+
+
+def bi_swap(D, medoids, max_iter=1000, tol=0.0, n=None, trace_cap=None):
+    """FastPAM1 SWAP to convergence over the locations (Alg. 3)."""
+    D, code, m, n, ld = _bimat(D, n)
+    med = _med(medoids).copy()
+    k = len(med)
+    cap = int(trace_cap if trace_cap is not None else max(16, 4 * k + 64))
+    stats = np.zeros(3, np.int64)
+    tdv = np.zeros(2, np.float64)
+    tr_d = np.zeros(cap, np.float64)
+    tr_i = np.zeros(cap, np.int32)
+    tr_c = np.zeros(cap, np.int64)
+    _lib().oracle_bi_swap(_p(D), code, m, n, ld, k, _p(med), int(max_iter), float(tol),
+                          _p(stats), _p(tdv), cap, _p(tr_d), _p(tr_i), _p(tr_c))
+    ns = min(int(stats[1]), cap)
+    return {
+        "medoids": med, "iterations": int(stats[0]), "swaps": int(stats[1]),
+        "converged": bool(stats[2]), "td_bookkept": float(tdv[0]), "td": float(tdv[1]),
+        "trace": list(zip(tr_d[:ns].tolist(), tr_i[:ns].tolist(), tr_c[:ns].tolist())),
+    }
+
+
+def bi_run(D, k, n=None, **kw):
+    """BUILD then FastPAM1 SWAP in the bichromatic case."""
+    med, td_build, _ = bi_build(D, k, n=n)
+    out = bi_swap(D, med, n=n, **kw)
     out["build_medoids"] = med
     out["td_build"] = td_build
     return out

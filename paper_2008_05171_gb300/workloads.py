@@ -19,6 +19,12 @@ Gaussian mixtures and uniform clouds of the sizes the workloads below name:
                       centres ~ N(0, 4I), sigma=1, equal weights.
 * batched             instances with n ~ U[200,4000], d=8 uniform [0,1)^8,
                       k ~ U[5,50]; CLARA points: n=1e6, d=32, 100 clusters.
+* ``bichromatic_*``   facility placement (the paper's Outlook): n consumers
+                      from a 2-D Gaussian mixture (households around towns),
+                      m candidate locations uniform over the same square;
+                      an m x n rectangular matrix d(consumer, location)
+                      (exact integer Manhattan, or FP64 Euclidean rounded
+                      once to FP32), rows = locations.
 
 Every distance is computed in FP64 from the coordinates by the direct
 difference formula, rounded once to FP32 (or taken exactly for the integer
@@ -138,6 +144,49 @@ def euclidean_f32_torch(X: np.ndarray, device, ld: int | None = None,
             else:
                 D[j0:j1, i0:i1] = blk.T
     return D
+
+
+def cross_manhattan_int32(L: np.ndarray, C: np.ndarray, ld: int | None = None) -> np.ndarray:
+    """Exact integer L1 distances between rows L (locations) and C
+    (consumers) as int32, shape (len(L), ld)."""
+    L = np.asarray(L, dtype=np.int64)
+    C = np.asarray(C, dtype=np.int64)
+    m, n = L.shape[0], C.shape[0]
+    ld = round_up(n, 4) if ld is None else ld
+    D = np.zeros((m, ld), dtype=np.int32)
+    for i0 in range(0, m, 512):
+        D[i0:i0 + 512, :n] = np.abs(L[i0:i0 + 512, None, :] - C[None, :, :]).sum(-1)
+    return D
+
+
+def cross_euclidean_f32(L: np.ndarray, C: np.ndarray, ld: int | None = None) -> np.ndarray:
+    """FP64 Euclidean distances between rows L and C, rounded once to FP32,
+    shape (len(L), ld)."""
+    L = np.asarray(L, dtype=np.float64)
+    C = np.asarray(C, dtype=np.float64)
+    m, n = L.shape[0], C.shape[0]
+    ld = round_up(n, 4) if ld is None else ld
+    D = np.zeros((m, ld), dtype=np.float32)
+    for i0 in range(0, m, 256):
+        diff = L[i0:i0 + 256, None, :] - C[None, :, :]
+        D[i0:i0 + 256, :n] = np.sqrt((diff * diff).sum(-1)).astype(np.float32)
+    return D
+
+
+def bichromatic_points(m: int, n: int, *, towns: int = 40, seed=11, integer: bool = False):
+    """(locations (m, 2), consumers (n, 2)): consumers from a mixture of
+    ``towns`` Gaussian clusters (centres uniform in [0, 1000)^2, sigma
+    U[10, 60]), locations uniform over the square; integer coordinates when
+    ``integer``."""
+    g = rng_for(("bichromatic", seed))
+    centres = g.uniform(0.0, 1000.0, size=(towns, 2))
+    sig = g.uniform(10.0, 60.0, size=towns)
+    z = g.integers(0, towns, size=n)
+    C = np.clip(centres[z] + sig[z, None] * g.standard_normal(size=(n, 2)), 0.0, 999.0)
+    L = g.uniform(0.0, 1000.0, size=(m, 2))
+    if integer:
+        return np.floor(L).astype(np.int64), np.floor(C).astype(np.int64)
+    return L, C
 
 
 # -------------------------------------------------------------- workloads --
