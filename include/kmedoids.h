@@ -586,6 +586,40 @@ km_status kmedoids_eval_swaps_static(const void *D, int32_t dtype, int64_t n,
                                      double *best_delta, int32_t *best_slot,
                                      int32_t *best_cand, void *stream);
 
+/* The bichromatic case (the paper's Outlook): the medoids are chosen among
+ * m possible locations and the objective sums over n consumers, TD =
+ * sum_c min_j d(x_c, m_j) (Eq. (2) over the consumers); with k = 1 the
+ * result is the bichromatic medoid argmin_l sum_c d(x_c, x_l).
+ *   D      m rows (locations) of ld elements, DEVICE, caller-owned:
+ *          d(x_c, x_l) = D[l * ld + c] for consumers c < n; entries >= 0
+ *          (float: finite); no symmetry or diagonal is assumed.  Same dtype,
+ *          alignment and ld rules as the square form (ld >= n).
+ *   k      1 <= k <= m; medoids_out[k] location indices in slot order,
+ *          labels_out[n] (may be NULL) the nearest slot of every consumer.
+ * kmedoids_run_bichromatic: BUILD (Alg. 1; the plain pass over every
+ * non-medoid location per step) then SWAP; kmedoids_swap_bichromatic: SWAP
+ * from the given locations (validated: in range, distinct).  SWAP variants
+ * as km_options.variant: FastPAM1 (Alg. 3 over the consumers), FastPAM2,
+ * FasterPAM and FastCLARANS (draws are location indices) in the windowed
+ * streaming kernel.  check_input must be 0.  The workspace comes from
+ * kmedoids_bichromatic_workspace_size; results, errors and synchronisation
+ * as kmedoids_run.  The paper leaves this case unspecified beyond the
+ * definition; every step is the square case's with candidates over the
+ * locations and points over the consumers. */
+size_t kmedoids_bichromatic_workspace_size(int64_t m, int64_t n, int32_t k,
+                                           int32_t dtype,
+                                           const km_options *opts);
+km_status kmedoids_run_bichromatic(const void *D, int32_t dtype, int64_t m,
+                                   int64_t n, int64_t ld, int32_t k,
+                                   int32_t *medoids_out, int32_t *labels_out,
+                                   const km_options *opts, km_result *res,
+                                   void *ws, size_t ws_bytes, void *stream);
+km_status kmedoids_swap_bichromatic(const void *D, int32_t dtype, int64_t m,
+                                    int64_t n, int64_t ld, int32_t k,
+                                    int32_t *medoids_inout, int32_t *labels_out,
+                                    const km_options *opts, km_result *res,
+                                    void *ws, size_t ws_bytes, void *stream);
+
 /* The dissimilarity matrix from host memory into a device buffer (the
  * input of every entry point above; the paper's method starts from the
  * matrix, Sec. 1.2).  Copies n rows of n elements of type dtype from host

@@ -60,14 +60,20 @@ struct WsLayout {
   size_t st, med, is_med, near, sec, dn, ds, bdn, removal, td2, partials, slot_partials,
       slot_best, fp2_order, win_delta, win_slot, trace, gains, cand_gain, blist, blvn, blvo,
       baux, btt, bparts, blk, total;
-  int64_t n_pad;
+  int64_t n_pad;  // points (columns), padded
+  int64_t m_pad;  // candidate rows, padded (n_pad unless bichromatic)
   int k_pad;
   int trace_cap;
 };
 
-bool make_ws(int64_t n, int k, const km_options* o, WsLayout* L) {
-  if (n <= 0 || k <= 0 || k > n || n > (int64_t)INT32_MAX - 2 * kChunk) return false;
+// m candidate rows (locations), n points (columns); m = n for the square
+// matrix.
+bool make_ws(int64_t m, int64_t n, int k, const km_options* o, WsLayout* L) {
+  if (n <= 0 || m <= 0 || k <= 0 || k > m || n > (int64_t)INT32_MAX - 2 * kChunk ||
+      m > (int64_t)INT32_MAX - 2 * kChunk)
+    return false;
   const int64_t n_pad = rup(n, kChunk);
+  const int64_t m_pad = rup(m, kChunk);
   const int k_pad = (int)rup(k, 32);
   const int variant = o ? o->variant : KM_FASTPAM1;
   const int cap = (o && o->trace_capacity > 0) ? o->trace_capacity : 0;
@@ -79,7 +85,7 @@ bool make_ws(int64_t n, int k, const km_options* o, WsLayout* L) {
   };
   L->st = take(512);
   L->med = take(4 * (size_t)k_pad);
-  L->is_med = take((size_t)n_pad);
+  L->is_med = take((size_t)m_pad);
   L->near = take(4 * (size_t)n_pad);
   L->sec = take(4 * (size_t)n_pad);
   L->dn = take(4 * (size_t)n_pad);
@@ -95,7 +101,7 @@ bool make_ws(int64_t n, int k, const km_options* o, WsLayout* L) {
   L->win_slot = take(4 * (size_t)kMaxGrid * kMaxRows);
   L->trace = take(sizeof(TraceRec) * (size_t)(cap > 0 ? cap : 1));
   L->gains = take(8 * (size_t)k);
-  L->cand_gain = take(8 * (size_t)n_pad);  // also the incremental BUILD's gains
+  L->cand_gain = take(8 * (size_t)m_pad);  // also the incremental BUILD's gains
   L->blist = take(4 * (size_t)n_pad);
   L->blvn = take(4 * (size_t)n_pad);
   L->blvo = take(4 * (size_t)n_pad);
@@ -107,6 +113,7 @@ bool make_ws(int64_t n, int k, const km_options* o, WsLayout* L) {
   L->blk = take(1088 + 8 * (size_t)k_pad);
   L->total = off;
   L->n_pad = n_pad;
+  L->m_pad = m_pad;
   L->k_pad = k_pad;
   L->trace_cap = cap;
   return true;
@@ -115,7 +122,8 @@ bool make_ws(int64_t n, int k, const km_options* o, WsLayout* L) {
 struct Ctx {
   const void* D;
   int dtype;
-  int n;
+  int n;   // points (columns)
+  int m;   // candidate rows (n unless bichromatic)
   long long ld;
   int k;
   unsigned char* ws;
@@ -137,14 +145,17 @@ struct Ctx {
   }
 };
 
-km_status check_common(const void* D, int32_t dtype, int64_t n, int64_t ld, int32_t k, void* ws,
-                       size_t ws_bytes, const km_options* opts, Ctx* c) {
+km_status check_common(const void* D, int32_t dtype, int64_t m, int64_t n, int64_t ld, int32_t k,
+                       void* ws, size_t ws_bytes, const km_options* opts, Ctx* c) {
   if (!D) return fail(KM_E_INVALID, "D is NULL");
   if (dtype != KM_I32 && dtype != KM_F32 && dtype != KM_U16)
     return fail(KM_E_INVALID, "unknown dtype %d", dtype);
   if (n <= 0) return fail(KM_E_INVALID, "n must be positive (got %lld)", (long long)n);
-  if (n > (int64_t)INT32_MAX - 2 * kChunk) return fail(KM_E_INVALID, "n too large");
-  if (k < 1 || k > n) return fail(KM_E_INVALID, "need 1 <= k <= n (k=%d, n=%lld)", k, (long long)n);
+  if (m <= 0) return fail(KM_E_INVALID, "m must be positive (got %lld)", (long long)m);
+  if (n > (int64_t)INT32_MAX - 2 * kChunk || m > (int64_t)INT32_MAX - 2 * kChunk)
+    return fail(KM_E_INVALID, "n too large");
+  if (k < 1 || k > m) return fail(KM_E_INVALID, "need 1 <= k <= %s (k=%d, %lld)", m == n ? "n" : "m",
+                                  k, (long long)m);
   if (ld < n) return fail(KM_E_INVALID, "ld (%lld) < n (%lld)", (long long)ld, (long long)n);
   if (ld % 4 != 0) return fail(KM_E_INVALID, "ld (%lld) must be a multiple of 4", (long long)ld);
   if (dtype == KM_U16 && ld % 8 != 0)
@@ -157,7 +168,7 @@ km_status check_common(const void* D, int32_t dtype, int64_t n, int64_t ld, int3
   c->opt = opts ? *opts : def;
   if (c->opt.variant < 0 || c->opt.variant > 3) return fail(KM_E_INVALID, "unknown variant %d", c->opt.variant);
   if (c->opt.variant == KM_FASTCLARANS &&
-      (!c->opt.draws || c->opt.draws_len < 1 || c->opt.maxneighbor < 1 || k < 2 || k >= n))
+      (!c->opt.draws || c->opt.draws_len < 1 || c->opt.maxneighbor < 1 || k < 2 || k >= m))
     return fail(KM_E_INVALID, "FastCLARANS needs draws, draws_len >= 1, maxneighbor >= 1 and "
                 "2 <= k < n");
   if (!(c->opt.tol >= 0.0)) return fail(KM_E_INVALID, "tol must be >= 0");
@@ -168,12 +179,13 @@ km_status check_common(const void* D, int32_t dtype, int64_t n, int64_t ld, int3
   if (c->opt.trace_capacity < 0) return fail(KM_E_INVALID, "trace_capacity < 0");
   if (c->opt.tune < -1 || c->opt.tune > 16) return fail(KM_E_INVALID, "tune must be in -1..16");
   if (c->opt.wait_limit_ns < 0) return fail(KM_E_INVALID, "wait_limit_ns must be >= 0");
-  if (!make_ws(n, k, &c->opt, &c->L)) return fail(KM_E_INVALID, "invalid sizes");
+  if (!make_ws(m, n, k, &c->opt, &c->L)) return fail(KM_E_INVALID, "invalid sizes");
   if (ws_bytes < c->L.total)
     return fail(KM_E_WORKSPACE, "workspace too small: %zu < %zu bytes", ws_bytes, c->L.total);
   c->D = D;
   c->dtype = dtype;
   c->n = (int)n;
+  c->m = (int)m;
   c->ld = ld;
   c->k = k;
   c->ws = static_cast<unsigned char*>(ws);
@@ -189,6 +201,7 @@ StreamArgs stream_args(const Ctx& c) {
   a.D = c.D;
   a.ld = c.ld;
   a.n = c.n;
+  a.m = c.m;
   a.k = c.k;
   a.k_pad = c.L.k_pad;
   a.n_pad = (int)c.L.n_pad;
@@ -215,6 +228,7 @@ PointArgs point_args(const Ctx& c) {
   a.D = c.D;
   a.ld = c.ld;
   a.n = c.n;
+  a.m = c.m;
   a.k = c.k;
   a.k_pad = c.L.k_pad;
   a.n_pad = (int)c.L.n_pad;
@@ -243,7 +257,7 @@ PointArgs point_args(const Ctx& c) {
 int grid_for(const Ctx& c, const StreamConfig& cfg) {
   const int rows = cfg.rows;
   int g = c.sms * cfg.minb;
-  const int need = (c.n + rows - 1) / rows;
+  const int need = (c.m + rows - 1) / rows;
   if (g > need) g = need;
   if (g > kMaxGrid) g = kMaxGrid;
   if (g < 1) g = 1;
@@ -311,7 +325,7 @@ km_status state_error(const KmState& h) {
 // state record is restored before every timed pass, so the passes leave no
 // trace; results do not depend on the geometry (exact sums, total orders).
 std::mutex g_tune_mu;
-std::map<std::tuple<int, int, int, int, int, int>, int> g_tune;
+std::map<std::tuple<int, int, int, int, long long, int>, int> g_tune;
 
 km_status config_for(Ctx& c, int mode, int flavour, const StreamArgs& sa, StreamConfig* cfg) {
   const char* what = (mode == kModeSwap) ? "SWAP" : "BUILD";
@@ -323,7 +337,8 @@ km_status config_for(Ctx& c, int mode, int flavour, const StreamArgs& sa, Stream
   }
   int dev = 0;
   KM_CUDA(cudaGetDevice(&dev));
-  const auto key = std::make_tuple(dev, c.dtype, mode, flavour, c.n, c.k * 64 + c.opt.rows_per_tile);
+  const auto key = std::make_tuple(dev, c.dtype, mode, flavour, (long long)c.n * (1ll << 31) + c.m,
+                                   c.k * 64 + c.opt.rows_per_tile);
   {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     auto it = g_tune.find(key);
@@ -380,7 +395,7 @@ km_status scan_matrix(Ctx& c);
 
 // The plain BUILD: every step streams all candidate rows (Alg. 1).
 km_status do_build_full(Ctx& c, Timer& tm, std::vector<std::pair<int, int>>& ev, km_result* res) {
-  KM_CUDA(cudaMemsetAsync(c.at<void>(c.L.is_med), 0, (size_t)c.L.n_pad, c.s));
+  KM_CUDA(cudaMemsetAsync(c.at<void>(c.L.is_med), 0, (size_t)c.L.m_pad, c.s));
   StreamArgs sa = stream_args(c);
   sa.build_first = 1;
   StreamConfig cfg;
@@ -400,7 +415,7 @@ km_status do_build_full(Ctx& c, Timer& tm, std::vector<std::pair<int, int>>& ev,
   }
   if (res) res->build_launches = c.k;
   c.build_rows = 0;
-  for (int t = 0; t < c.k; ++t) c.build_rows += c.n - t;
+  for (int t = 0; t < c.k; ++t) c.build_rows += c.m - t;
   return KM_OK;
 }
 
@@ -434,14 +449,16 @@ BuildArgs build_args(const Ctx& c) {
 // lowered.  Same choices as the plain pass in exact fixed point.
 km_status do_build(Ctx& c, Timer& tm, std::vector<std::pair<int, int>>& ev, km_result* res) {
   NvtxRange nv("kmedoids BUILD");
-  if (c.opt.build_full) return do_build_full(c, tm, ev, res);
+  // the incremental gains read the rows of points as candidate columns
+  // (symmetry): the bichromatic form takes the plain pass
+  if (c.opt.build_full || c.m != c.n) return do_build_full(c, tm, ev, res);
   if (c.dtype == KM_F32 && !c.scanned) {
     km_status r = scan_matrix(c);  // fixed-point exponent of the gains
     if (r != KM_OK) return r;
     c.scanned = true;
   }
   const size_t tiles = (size_t)(c.L.n_pad / kChunk);
-  KM_CUDA(cudaMemsetAsync(c.at<void>(c.L.is_med), 0, (size_t)c.L.n_pad, c.s));
+  KM_CUDA(cudaMemsetAsync(c.at<void>(c.L.is_med), 0, (size_t)c.L.m_pad, c.s));
   KM_CUDA(cudaMemsetAsync(c.at<void>(c.L.cand_gain), 0, 8 * (size_t)c.L.n_pad, c.s));
   KM_CUDA(cudaMemsetAsync(c.at<void>(c.L.baux), 0, sizeof(BuildAux), c.s));
   KM_CUDA(cudaMemsetAsync(c.at<void>(c.L.btt), 0, 4 * tiles, c.s));
@@ -497,7 +514,7 @@ km_status swap_setup(Ctx& c) {
     if (r != KM_OK) return r;
     c.scanned = true;
   }
-  KM_CUDA(cudaMemsetAsync(c.at<void>(c.L.is_med), 0, (size_t)c.L.n_pad, c.s));
+  KM_CUDA(cudaMemsetAsync(c.at<void>(c.L.is_med), 0, (size_t)c.L.m_pad, c.s));
   KM_CUDA(cudaMemsetAsync(c.at<void>(c.L.removal), 0, 16 * (size_t)c.L.k_pad, c.s));
   KM_CUDA(cudaMemsetAsync(c.at<void>(c.L.td2), 0, 16, c.s));
   PointArgs pa = point_args(c);
@@ -512,7 +529,7 @@ km_status swap_k1(Ctx& c, KmState* h) {
   StreamConfig cfg;
   if (!stream_config(kModeBuild, 1, 0, c.opt.rows_per_tile, c.opt.tune, &cfg, c.esize()))
     return fail(KM_E_UNSUPPORTED, "no kernel configuration fits");
-  KM_CUDA(cudaMemsetAsync(c.at<void>(c.L.is_med), 0, (size_t)c.L.n_pad, c.s));
+  KM_CUDA(cudaMemsetAsync(c.at<void>(c.L.is_med), 0, (size_t)c.L.m_pad, c.s));
   StreamArgs sa = stream_args(c);
   sa.build_first = 1;
   sa.cand_gain = c.at<double>(c.L.cand_gain);
@@ -683,7 +700,7 @@ km_status do_swap(Ctx& c, Timer& tm, std::vector<std::pair<int, int>>& ev, KmSta
     sa.draws_len = c.opt.draws_len;
     sa.maxneighbor = c.opt.maxneighbor;
   }
-  if ((flavour == kFasterPAM || flavour == kCLARANS) && c.opt.tune <= 0) {
+  if ((flavour == kFasterPAM || flavour == kCLARANS) && c.opt.tune <= 0 && c.m == c.n) {
     // the eager variants run as one persistent cooperative launch when every
     // CTA of its grid can be resident (the usual case); a fixed geometry
     // (tune > 0) selects the windowed streaming kernel instead
@@ -750,7 +767,7 @@ km_status do_swap(Ctx& c, Timer& tm, std::vector<std::pair<int, int>>& ev, KmSta
     }
   }
   if (variant == KM_FASTPAM1 || variant == KM_FASTERPAM || variant == KM_FASTCLARANS) {
-    const long long pos_limit = (long long)max_iter * c.n;
+    const long long pos_limit = (long long)max_iter * c.m;
     int launched = 0, batch = 1;
     const int max_launch = (variant == KM_FASTPAM1) ? max_iter : INT32_MAX;
     while (true) {
@@ -912,7 +929,7 @@ size_t kmedoids_workspace_size(int64_t n, int32_t k, int32_t dtype, const km_opt
   WsLayout L;
   km_options def;
   km_default_options(&def);
-  if (!make_ws(n, k, opts ? opts : &def, &L)) return 0;
+  if (!make_ws(n, n, k, opts ? opts : &def, &L)) return 0;
   return L.total;
 }
 
@@ -920,19 +937,22 @@ const char* kmedoids_last_error(void) { return g_err.c_str(); }
 
 const char* kmedoids_version(void) { return "kmedoids-gb300 0.1 (sm_103a)"; }
 
-static km_status run_impl(bool do_b, bool do_s, const void* D, int32_t dtype, int64_t n, int64_t ld,
+static km_status run_impl(bool do_b, bool do_s, const void* D, int32_t dtype, int64_t m, int64_t n,
+                          int64_t ld,
                           int32_t k, int32_t* medoids_io, int32_t* labels_out,
                           const km_options* opts, km_result* res, void* ws, size_t ws_bytes,
                           void* stream) {
   g_err.clear();
   NvtxRange nv(do_b ? (do_s ? "kmedoids_run" : "kmedoids_build") : "kmedoids_swap");
   Ctx c;
-  km_status r = check_common(D, dtype, n, ld, k, ws, ws_bytes, opts, &c);
+  km_status r = check_common(D, dtype, m, n, ld, k, ws, ws_bytes, opts, &c);
   if (r != KM_OK) {
     if (res) res->status = r;
     return r;
   }
   if (!medoids_io) return fail(KM_E_INVALID, "medoids pointer is NULL");
+  if (m != n && c.opt.check_input)
+    return fail(KM_E_INVALID, "check_input tests a square symmetric matrix (m = n)");
   c.s = static_cast<cudaStream_t>(stream);
   if (res) {
     memset(res, 0, sizeof(*res));
@@ -959,9 +979,9 @@ static km_status run_impl(bool do_b, bool do_s, const void* D, int32_t dtype, in
     std::vector<int32_t> hm((size_t)k);
     KM_CUDA(cudaMemcpyAsync(hm.data(), medoids_io, 4 * (size_t)k, cudaMemcpyDeviceToHost, c.s));
     KM_CUDA(cudaStreamSynchronize(c.s));
-    std::vector<char> seen((size_t)n, 0);
+    std::vector<char> seen((size_t)m, 0);
     for (int j = 0; j < k; ++j) {
-      if (hm[j] < 0 || hm[j] >= n) return fail(KM_E_INVALID, "medoid %d out of range: %d", j, hm[j]);
+      if (hm[j] < 0 || hm[j] >= m) return fail(KM_E_INVALID, "medoid %d out of range: %d", j, hm[j]);
       if (seen[hm[j]]) return fail(KM_E_INVALID, "medoid %d repeated: %d", j, hm[j]);
       seen[hm[j]] = 1;
     }
@@ -1037,7 +1057,7 @@ static km_status run_impl(bool do_b, bool do_s, const void* D, int32_t dtype, in
       res->swaps = hf.swaps;
       if (c.opt.variant == KM_FASTERPAM && c.k > 1) {
         res->visited = hf.pos;
-        res->iterations = (int)((hf.pos + c.n - 1) / c.n);
+        res->iterations = (int)((hf.pos + c.m - 1) / c.m);
       }
       if (c.opt.variant == KM_FASTCLARANS) {
         res->visited = hf.pos;
@@ -1072,22 +1092,48 @@ static km_status run_impl(bool do_b, bool do_s, const void* D, int32_t dtype, in
 km_status kmedoids_build(const void* D, int32_t dtype, int64_t n, int64_t ld, int32_t k,
                          int32_t* medoids_out, const km_options* opts, km_result* res, void* ws,
                          size_t ws_bytes, void* stream) {
-  return run_impl(true, false, D, dtype, n, ld, k, medoids_out, nullptr, opts, res, ws, ws_bytes,
+  return run_impl(true, false, D, dtype, n, n, ld, k, medoids_out, nullptr, opts, res, ws, ws_bytes,
                   stream);
 }
 
 km_status kmedoids_swap(const void* D, int32_t dtype, int64_t n, int64_t ld, int32_t k,
                         int32_t* medoids_inout, int32_t* labels_out, const km_options* opts,
                         km_result* res, void* ws, size_t ws_bytes, void* stream) {
-  return run_impl(false, true, D, dtype, n, ld, k, medoids_inout, labels_out, opts, res, ws,
+  return run_impl(false, true, D, dtype, n, n, ld, k, medoids_inout, labels_out, opts, res, ws,
                   ws_bytes, stream);
 }
 
 km_status kmedoids_run(const void* D, int32_t dtype, int64_t n, int64_t ld, int32_t k,
                        int32_t* medoids_out, int32_t* labels_out, const km_options* opts,
                        km_result* res, void* ws, size_t ws_bytes, void* stream) {
-  return run_impl(true, true, D, dtype, n, ld, k, medoids_out, labels_out, opts, res, ws, ws_bytes,
+  return run_impl(true, true, D, dtype, n, n, ld, k, medoids_out, labels_out, opts, res, ws, ws_bytes,
                   stream);
+}
+
+size_t kmedoids_bichromatic_workspace_size(int64_t m, int64_t n, int32_t k, int32_t dtype,
+                                           const km_options* opts) {
+  if (dtype != KM_I32 && dtype != KM_F32 && dtype != KM_U16) return 0;
+  WsLayout L;
+  km_options def;
+  km_default_options(&def);
+  if (!make_ws(m, n, k, opts ? opts : &def, &L)) return 0;
+  return L.total;
+}
+
+km_status kmedoids_run_bichromatic(const void* D, int32_t dtype, int64_t m, int64_t n, int64_t ld,
+                                   int32_t k, int32_t* medoids_out, int32_t* labels_out,
+                                   const km_options* opts, km_result* res, void* ws,
+                                   size_t ws_bytes, void* stream) {
+  return run_impl(true, true, D, dtype, m, n, ld, k, medoids_out, labels_out, opts, res, ws,
+                  ws_bytes, stream);
+}
+
+km_status kmedoids_swap_bichromatic(const void* D, int32_t dtype, int64_t m, int64_t n,
+                                    int64_t ld, int32_t k, int32_t* medoids_inout,
+                                    int32_t* labels_out, const km_options* opts, km_result* res,
+                                    void* ws, size_t ws_bytes, void* stream) {
+  return run_impl(false, true, D, dtype, m, n, ld, k, medoids_inout, labels_out, opts, res, ws,
+                  ws_bytes, stream);
 }
 
 km_status kmedoids_eval_swaps(const void* D, int32_t dtype, int64_t n, int64_t ld, int32_t k,
@@ -1096,7 +1142,7 @@ km_status kmedoids_eval_swaps(const void* D, int32_t dtype, int64_t n, int64_t l
                               void* ws, size_t ws_bytes, void* stream) {
   g_err.clear();
   Ctx c;
-  km_status r = check_common(D, dtype, n, ld, k, ws, ws_bytes, nullptr, &c);
+  km_status r = check_common(D, dtype, n, n, ld, k, ws, ws_bytes, nullptr, &c);
   if (r != KM_OK) return r;
   if (k < 2) return fail(KM_E_INVALID, "kmedoids_eval_swaps needs k >= 2");
   if (!medoids) return fail(KM_E_INVALID, "medoids is NULL");
@@ -1133,7 +1179,7 @@ km_status kmedoids_cache(const void* D, int32_t dtype, int64_t n, int64_t ld, in
                          double* removal, void* ws, size_t ws_bytes, void* stream) {
   g_err.clear();
   Ctx c;
-  km_status r = check_common(D, dtype, n, ld, k, ws, ws_bytes, nullptr, &c);
+  km_status r = check_common(D, dtype, n, n, ld, k, ws, ws_bytes, nullptr, &c);
   if (r != KM_OK) return r;
   if (!medoids) return fail(KM_E_INVALID, "medoids is NULL");
   c.s = static_cast<cudaStream_t>(stream);
@@ -1161,7 +1207,7 @@ static km_status init_setup(const void* D, int32_t dtype, int64_t n, int64_t ld,
                             int32_t* medoids_out, void* ws, size_t ws_bytes, void* stream, Ctx* c,
                             InitArgs* ia) {
   g_err.clear();
-  km_status r = check_common(D, dtype, n, ld, k, ws, ws_bytes, nullptr, c);
+  km_status r = check_common(D, dtype, n, n, ld, k, ws, ws_bytes, nullptr, c);
   if (r != KM_OK) return r;
   if (!medoids_out) return fail(KM_E_INVALID, "medoids_out is NULL");
   c->s = static_cast<cudaStream_t>(stream);

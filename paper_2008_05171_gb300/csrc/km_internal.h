@@ -37,7 +37,8 @@ enum SwapFlavour {
 struct StreamArgs {
   const void* D;
   long long ld;
-  int n;
+  int n;                // points (matrix columns)
+  int m;                // candidate rows: n, or the locations of the bichromatic form
   int k;
   int k_pad;
   int n_pad;
@@ -72,7 +73,8 @@ struct StreamArgs {
 struct PointArgs {
   const void* D;
   long long ld;
-  int n;
+  int n;          // points (matrix columns)
+  int m;          // candidate rows: n, or the locations of the bichromatic form
   int k;
   int k_pad;
   int n_pad;

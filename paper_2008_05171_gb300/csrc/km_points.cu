@@ -95,7 +95,7 @@ __global__ void __launch_bounds__(kPtThreads) k_cache_init(const PointArgs a) {
     T d1 = Tr<T>::high(), d2 = Tr<T>::high();
     for (int j = 0; j < k; ++j) {
       const int m = a.med[j];
-      if (!KM_INB(st, m, n)) continue;
+      if (!KM_INB(st, m, a.m)) continue;
       const T v = D[(size_t)m * a.ld + o];
       top2_push(v, j, n1, d1, n2, d2);
     }
@@ -175,7 +175,7 @@ __global__ void __launch_bounds__(kPtThreads) k_apply(const PointArgs a) {
   if (st->error || !st->accept) return;  // uniform for the launch
   const int k = a.k, n = a.n;
   const int i_s = st->best_slot, c_s = st->best_cand;
-  if (!KM_INB(st, i_s, k) || !KM_INB(st, c_s, n)) return;  // uniform for the launch
+  if (!KM_INB(st, i_s, k) || !KM_INB(st, c_s, a.m)) return;  // uniform for the launch
   const int rb = st->rb;
   for (int i = threadIdx.x; i < k; i += blockDim.x) sacc[i] = A(0);
   if (threadIdx.x == 0) s_cnt = 0;
@@ -223,7 +223,7 @@ __global__ void __launch_bounds__(kPtThreads) k_apply(const PointArgs a) {
     T d1 = Tr<T>::high(), d2 = Tr<T>::high();
     for (int j = lane; j < k; j += 32) {
       const int m = (j == i_s) ? c_s : a.med[j];
-      if (!KM_INB(st, m, n)) continue;
+      if (!KM_INB(st, m, a.m)) continue;
       top2_push((T)D[(size_t)m * a.ld + oo], j, n1, d1, n2, d2);
     }
 #pragma unroll
@@ -256,7 +256,7 @@ __global__ void __launch_bounds__(kPtThreads) k_apply(const PointArgs a) {
     __threadfence();
     const int old = a.med[i_s];
     a.med[i_s] = c_s;
-    if (KM_INB(st, old, n)) a.is_med[old] = 0;
+    if (KM_INB(st, old, a.m)) a.is_med[old] = 0;
     a.is_med[c_s] = 1;
     const int nt = st->ntrace;
     if (nt < a.trace_cap) {
@@ -291,7 +291,7 @@ __global__ void __launch_bounds__(kPtThreads) k_build_commit(const PointArgs a) 
   const E* D = static_cast<const E*>(a.D);
   T* bdn = static_cast<T*>(a.bdn);
   A local = A(0);
-  if (c >= 0 && c < n) {
+  if (c >= 0 && c < a.m) {
     if (o < n) {
       const T v = D[(size_t)c * a.ld + o];
       T cur = v;
@@ -313,7 +313,7 @@ __global__ void __launch_bounds__(kPtThreads) k_build_commit(const PointArgs a) 
       atomicAdd(reinterpret_cast<unsigned long long*>(&st->build_td_i),
                 static_cast<unsigned long long>((long long)bs));
   }
-  if (blockIdx.x == 0 && threadIdx.x == 0 && c >= 0 && c < n &&
+  if (blockIdx.x == 0 && threadIdx.x == 0 && c >= 0 && c < a.m &&
       KM_INB(st, st->build_step, a.k)) {
     const int step = st->build_step;
     a.med[step] = c;
@@ -353,7 +353,7 @@ __global__ void __launch_bounds__(kPtThreads) k_fp2_try(const PointArgs a) {
   if (!KM_INB(st, i, a.k)) return;
   const Key<R> sb = static_cast<const Key<R>*>(a.slot_best)[i];
   const int c = sb.cand;
-  if (!KM_INB(st, c, a.n)) return;
+  if (!KM_INB(st, c, a.m)) return;
   if (a.is_med[c]) {  // already a medoid after an earlier swap
     if (blockIdx.x == 0 && threadIdx.x == 0) st->accept = 0;
     return;
@@ -402,12 +402,12 @@ __global__ void __launch_bounds__(kPtThreads) k_fp2_try(const PointArgs a) {
 // ------------------------------------------------------------- small ones
 __global__ void k_mark_medoids(const PointArgs a) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j < a.k && KM_INB(a.st, a.med[j], a.n)) a.is_med[a.med[j]] = 1;
+  if (j < a.k && KM_INB(a.st, a.med[j], a.m)) a.is_med[a.med[j]] = 1;
 }
 
 __global__ void k_fill_medoid_rows(const PointArgs a) {
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
-  if (c < a.n && a.is_med[c]) {
+  if (c < a.m && a.is_med[c]) {
     if (a.cand_delta) a.cand_delta[c] = __longlong_as_double(0x7ff0000000000000ll);
     if (a.cand_slot) a.cand_slot[c] = -1;
   }
@@ -424,7 +424,8 @@ __global__ void k_removal_to_double(const PointArgs a) {
 
 // Largest |d| over the matrix (fixes the fixed-point exponent of the SWAP
 // sums) and a flag for entries that are negative or not finite.  Float data
-// only; one pass over the n x n block with 16-byte loads.
+// only; one pass over the m x n block (m = n unless bichromatic) with
+// 16-byte loads.
 __global__ void __launch_bounds__(kPtThreads) k_matrix_scan(const PointArgs a) {
   __shared__ unsigned smax[kPtThreads / 32];
   __shared__ unsigned sbad;
@@ -434,7 +435,7 @@ __global__ void __launch_bounds__(kPtThreads) k_matrix_scan(const PointArgs a) {
   const int n = a.n;
   const int n4 = (n + 3) >> 2;
   unsigned mx = 0, bad = 0;
-  for (long long r = blockIdx.x; r < n; r += gridDim.x) {
+  for (long long r = blockIdx.x; r < a.m; r += gridDim.x) {
     const float4* row = reinterpret_cast<const float4*>(D + (size_t)r * a.ld);
     for (int c4 = threadIdx.x; c4 < n4; c4 += blockDim.x) {
       const float4 v = __ldcs(row + c4);
@@ -616,7 +617,7 @@ cudaError_t launch_mark_medoids(const PointArgs& a, cudaStream_t s) {
 }
 
 cudaError_t launch_fill_medoid_rows(const PointArgs& a, cudaStream_t s) {
-  k_fill_medoid_rows<<<blocks_for(a.n), kPtThreads, 0, s>>>(a);
+  k_fill_medoid_rows<<<blocks_for(a.m), kPtThreads, 0, s>>>(a);
   return cudaGetLastError();
 }
 
@@ -646,7 +647,7 @@ cudaError_t launch_matrix_check(int dtype, const void* D, long long ld, int n, u
 cudaError_t launch_matrix_scan(const PointArgs& a, cudaStream_t s) {
   int grid = device_sm_count() * 4;
   if (grid < 1) grid = 1;
-  if (grid > a.n) grid = a.n;
+  if (grid > a.m) grid = a.m;
   k_matrix_scan<<<grid, kPtThreads, 0, s>>>(a);
   return cudaGetLastError();
 }

@@ -186,7 +186,7 @@ __global__ void __launch_bounds__(kThreads, MINB) k_stream(const StreamArgs a) {
   if (st->done || st->error) return;  // uniform for all CTAs of this launch
   const unsigned long long wlim = wait_limit(st);
 
-  const int n = a.n, k = a.k, f = a.fshift;
+  const int n = a.n, m = a.m, k = a.k, f = a.fshift;
   const int fp2 = (MODE == kModeSwap && a.flavour == kFastPAM2);
   const Layout L = make_layout(MODE, R, S, k, fp2, (int)sizeof(E));
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + L.bars);
@@ -243,7 +243,7 @@ __global__ void __launch_bounds__(kThreads, MINB) k_stream(const StreamArgs a) {
   __syncthreads();
 
   // Candidate positions: a FasterPAM / FastCLARANS window is the next wl
-  // scan positions (row = p mod n, or the p-th draw), dealt round-robin so
+  // scan positions (row = p mod m, or the p-th draw), dealt round-robin so
   // that CTA b takes base + b, base + b + G, ... (G = grid size, at most R
   // each); its length adapts on the device (see the decision below).  Full
   // passes hand out tiles of R rows from an atomic counter so that CTAs on
@@ -255,7 +255,7 @@ __global__ void __launch_bounds__(kThreads, MINB) k_stream(const StreamArgs a) {
   if (windowed) {
     base = st->pos;
     const long long stop =
-        clarans ? a.draws_len : ((st->last < 0) ? (long long)n : st->last + n);
+        clarans ? a.draws_len : ((st->last < 0) ? (long long)m : st->last + m);
     wl = st->win_len;
     if (wl <= 0) wl = gridDim.x;
     if (wl > wmax) wl = wmax;
@@ -263,7 +263,7 @@ __global__ void __launch_bounds__(kThreads, MINB) k_stream(const StreamArgs a) {
     p_hi = base + wl;
     if (p_hi > stop) p_hi = stop;
   }
-  const unsigned ntiles = (unsigned)((n + R - 1) / R);
+  const unsigned ntiles = (unsigned)((m + R - 1) / R);
   const int nchunks = (n + kChunk - 1) / kChunk;
   // columns copied per row: n rounded up to whole 16-byte pieces
   constexpr int kGran = 16 / (int)sizeof(E);
@@ -282,8 +282,8 @@ __global__ void __launch_bounds__(kThreads, MINB) k_stream(const StreamArgs a) {
         int nr = 0;
         if (windowed) {
           while (nr < R && p < p_hi) {
-            const int row = clarans ? a.draws[p] : (int)(p % n);
-            if (row >= 0 && row < n && !a.is_med[row]) {
+            const int row = clarans ? a.draws[p] : (int)(p % m);
+            if (row >= 0 && row < m && !a.is_med[row]) {
               rows[nr] = row;
               outs[nr] = (int)(p - base);
               ++nr;
@@ -297,7 +297,7 @@ __global__ void __launch_bounds__(kThreads, MINB) k_stream(const StreamArgs a) {
             const unsigned tile = atomicAdd(&st->tile_next, 1u);
             if (tile >= ntiles) break;
             const int r0 = (int)tile * R;
-            const int r1 = (r0 + R < n) ? r0 + R : n;
+            const int r1 = (r0 + R < m) ? r0 + R : m;
             for (int row = r0; row < r1; ++row)
               if (!a.is_med[row]) {
                 rows[nr] = row;
@@ -626,7 +626,7 @@ __global__ void __launch_bounds__(kThreads, MINB) k_stream(const StreamArgs a) {
     KM_CSYNC();
     for (long long w = t; w < wlen; w += kConsThreads) {
       const int row = a.draws[base + w];
-      if (row < 0 || row >= n || a.is_med[row]) continue;
+      if (row < 0 || row >= m || a.is_med[row]) continue;
       if (__ldcg(a.cand_slot + w) >= 0 && __ldcg(a.cand_delta + w) < -a.tol)
         atomicMin(firstw, (int)w);
     }
@@ -635,7 +635,7 @@ __global__ void __launch_bounds__(kThreads, MINB) k_stream(const StreamArgs a) {
     int cnt = 0;  // evaluated draws before the first improving one
     for (long long w = t; w < wlen && w < fw; w += kConsThreads) {
       const int row = a.draws[base + w];
-      if (row >= 0 && row < n && !a.is_med[row]) ++cnt;
+      if (row >= 0 && row < m && !a.is_med[row]) ++cnt;
     }
     if (cnt) atomicAdd(nfail, cnt);
     KM_CSYNC();
@@ -647,7 +647,7 @@ __global__ void __launch_bounds__(kThreads, MINB) k_stream(const StreamArgs a) {
         long long seen = 0, w = 0;
         for (; w < wlen; ++w) {
           const int row = a.draws[base + w];
-          if (row >= 0 && row < n && !a.is_med[row] && ++seen == need) break;
+          if (row >= 0 && row < m && !a.is_med[row] && ++seen == need) break;
         }
         st->accept = 0;
         st->done = 1;
@@ -688,7 +688,7 @@ __global__ void __launch_bounds__(kThreads, MINB) k_stream(const StreamArgs a) {
   // evaluated again against the new state.
   if (a.flavour == kFasterPAM) {
     // first improving candidate of the window, in scan order
-    const long long stop = (st->last < 0) ? (long long)n : st->last + n;
+    const long long stop = (st->last < 0) ? (long long)m : st->last + m;
     long long wlen = wl;
     if (base + wlen > stop) wlen = stop - base;
     int* firstw = scratch_int;
@@ -699,7 +699,7 @@ __global__ void __launch_bounds__(kThreads, MINB) k_stream(const StreamArgs a) {
     }
     KM_CSYNC();
     for (long long w = t; w < wlen; w += kConsThreads) {
-      const int row = (int)((base + w) % n);
+      const int row = (int)((base + w) % m);
       if (a.is_med[row]) continue;
       if (__ldcg(a.cand_slot + w) >= 0 && __ldcg(a.cand_delta + w) < -a.tol)
         atomicMin(firstw, (int)w);
@@ -711,7 +711,7 @@ __global__ void __launch_bounds__(kThreads, MINB) k_stream(const StreamArgs a) {
       const int fw0 = *firstw;
       int cnt = 0;
       for (long long w = t; w < wlen && w <= fw0; w += kConsThreads)
-        if (!a.is_med[(int)((base + w) % n)]) ++cnt;
+        if (!a.is_med[(int)((base + w) % m)]) ++cnt;
       if (cnt) atomicAdd(nev, cnt);
     }
     KM_CSYNC();
@@ -724,7 +724,7 @@ __global__ void __launch_bounds__(kThreads, MINB) k_stream(const StreamArgs a) {
         st->best_d = dw;
         st->best_i = (long long)dw;
         st->best_slot = __ldcg(a.cand_slot + w);
-        st->best_cand = (int)((base + w) % n);
+        st->best_cand = (int)((base + w) % m);
         st->last = base + w;
         st->pos = base + w + 1;
         st->win_len = gridDim.x;

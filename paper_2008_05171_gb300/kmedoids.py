@@ -34,7 +34,9 @@ EXPORTS = ["km_default_options", "kmedoids_workspace_size", "kmedoids_build",
            "kmedoids_init_lab", "kmedoids_wait_selftest", "kmedoids_build_features",
            "kmedoids_batched_geometry_info", "kmedoids_batched_autotune",
            "kmedoids_batched_clara_workspace_size", "kmedoids_run_batched_clara",
-           "kmedoids_upload_matrix", "kmedoids_bounds_checked"]
+           "kmedoids_upload_matrix", "kmedoids_bounds_checked",
+           "kmedoids_bichromatic_workspace_size", "kmedoids_run_bichromatic",
+           "kmedoids_swap_bichromatic"]
 
 
 class KmError(RuntimeError):
@@ -156,6 +158,12 @@ def load(path: str = LIB_PATH):
         lib.kmedoids_wait_selftest.restype = i32
         lib.kmedoids_upload_matrix.argtypes = [P, i64, i32, i64, P, i64, P]
         lib.kmedoids_upload_matrix.restype = i32
+        lib.kmedoids_bichromatic_workspace_size.argtypes = [i64, i64, i32, i32, opt_p]
+        lib.kmedoids_bichromatic_workspace_size.restype = sz
+        for name in ("kmedoids_run_bichromatic", "kmedoids_swap_bichromatic"):
+            f = getattr(lib, name)
+            f.argtypes = [P, i32, i64, i64, i64, i32, P, P, opt_p, res_p, P, sz, P]
+            f.restype = i32
         lib.kmedoids_bounds_checked.argtypes = []
         lib.kmedoids_bounds_checked.restype = i32
         lib.kmedoids_last_error.restype = ctypes.c_char_p
@@ -709,6 +717,56 @@ def geometry_info(geometry):
 
 def version() -> str:
     return load().kmedoids_version().decode()
+
+
+def _bi_call(fn_name, D, k, n, medoids, labels, ws, kw):
+    torch = _torch()
+    lib = load()
+    if D.dim() != 2 or not D.is_cuda or D.stride(1) != 1:
+        raise ValueError("D must be a 2-D CUDA tensor with unit column stride")
+    m, ld = D.shape[0], D.stride(0)
+    code = _dtype_code(D)
+    o = options(**kw)
+    tr = _Trace(o, o.trace_capacity, k, True)
+    if ws is None:
+        nbytes = int(lib.kmedoids_bichromatic_workspace_size(m, int(n), int(k), code, ctypes.byref(o)))
+        if nbytes == 0:
+            raise KmError(1, "invalid sizes for a workspace")
+        ws = torch.empty(nbytes, dtype=torch.uint8, device=D.device)
+    res = km_result()
+    st = getattr(lib, fn_name)(
+        ctypes.c_void_p(D.data_ptr()), code, m, int(n), ld, int(k),
+        ctypes.c_void_p(medoids.data_ptr()),
+        ctypes.c_void_p(labels.data_ptr() if labels is not None else 0),
+        ctypes.byref(o), ctypes.byref(res), ctypes.c_void_p(ws.data_ptr()), ws.numel(), _stream())
+    if st not in (0, 4):
+        _check(st)
+    out = _result(res, o, k)
+    out["status_name"] = STATUS.get(st, st)
+    out["converged"] = st == 0
+    out["medoids"] = medoids
+    out["labels"] = labels
+    out["trace"] = tr.items(res.swaps) if o.trace_capacity > 0 else []
+    out["build_gains"] = tr.g[:k].copy()
+    return out
+
+
+def run_bichromatic(D, k, n, labels=True, ws=None, **kw):
+    """Bichromatic BUILD + SWAP (kmedoids_run_bichromatic): D holds m
+    location rows of the distances to n consumers (columns); the medoids are
+    location indices, the labels one slot per consumer."""
+    torch = _torch()
+    med = torch.empty(k, dtype=torch.int32, device=D.device)
+    lab = torch.empty(int(n), dtype=torch.int32, device=D.device) if labels else None
+    return _bi_call("kmedoids_run_bichromatic", D, k, n, med, lab, ws, kw)
+
+
+def swap_bichromatic(D, medoids, n, labels=True, ws=None, **kw):
+    """Bichromatic SWAP from the given locations (kmedoids_swap_bichromatic)."""
+    torch = _torch()
+    med = torch.as_tensor(medoids, dtype=torch.int32).to(D.device).clone()
+    lab = torch.empty(int(n), dtype=torch.int32, device=D.device) if labels else None
+    return _bi_call("kmedoids_swap_bichromatic", D, med.numel(), n, med, lab, ws, kw)
 
 
 def upload(H, n=None, D=None, ld=None, device=None):

@@ -162,6 +162,17 @@ def test_invalid_arguments_of_the_newer_entry_points(lib):
     assert lib.kmedoids_wait_selftest(0, 1000, P(fake), 256, None) == 1
     assert lib.kmedoids_wait_selftest(0, 1000, P(fake + 8), 512, None) == 1
     assert lib.kmedoids_wait_selftest(0, 1000, None, 512, None) == 1
+    # bichromatic form: sizes checked before any launch
+    ws_bi = lib.kmedoids_bichromatic_workspace_size
+    assert ws_bi(0, 10, 2, km.KM_F32, None) == 0
+    assert ws_bi(10, 20, 11, km.KM_F32, None) == 0          # k > m
+    assert ws_bi(10, 20, 3, 7, None) == 0                   # dtype
+    assert ws_bi(10, 20, 3, km.KM_F32, None) > 0
+    assert ws_bi(3000, 20, 3, km.KM_F32, None) > ws_bi(10, 20, 3, km.KM_F32, None)
+    for m_, n_, k_, ld_ in ((0, 20, 2, 20), (10, 0, 2, 20), (10, 20, 11, 20), (10, 20, 2, 18)):
+        assert lib.kmedoids_run_bichromatic(P(fake), km.KM_F32, m_, n_, ld_, k_, P(fake), None,
+                                            None, ctypes.byref(res), P(fake), 1 << 30,
+                                            None) == 1, (m_, n_, k_, ld_)
     # matrix upload: dtype, pointers and sizes checked before any CUDA call
     up = lib.kmedoids_upload_matrix
     assert up(P(fake), 100, 7, 100, P(fake), 100, None) == 1          # dtype
