@@ -20,6 +20,7 @@ method's passes are one sequential chain; each rank runs its own instance).
 from __future__ import annotations
 
 import argparse
+import ctypes
 import json
 import os
 import subprocess
@@ -66,6 +67,14 @@ WORKLOADS = {
                            "[0,1000)^2, exact Manhattan distances (<= 2000) stored as uint16 "
                            "(20000x20000, 0.8 GB), k=100, BUILD + FastPAM1 SWAP to convergence; "
                            "the same matrix as int32 timed beside it"),
+    "bichromatic_100000": dict(n=100000, m=20000, d=2, centers=200, k=100,
+                               recipe="bichromatic_100000",
+                               desc="facility placement (the paper's Outlook): n=100000 "
+                                    "consumers around 200 towns (2-D Gaussian mixture), "
+                                    "m=20000 candidate locations uniform over the square, "
+                                    "Euclidean f32 20000x100000 location-by-consumer matrix "
+                                    "(8 GB), k=100 locations, BUILD (plain pass) + FastPAM1 "
+                                    "SWAP over the consumers to convergence"),
     "gmm_50000": dict(n=50000, d=32, centers=200, k=200, recipe="gmm_50000_points",
                       desc="n=50000 d=32 f32 GMM (200 clusters, centres U[-10,10]^32, "
                            "sigma U[0.5,2], Dirichlet(1) weights), Euclidean f32 "
@@ -712,6 +721,132 @@ def run_clarans(args, rank, world, local_rank):
     return line
 
 
+def run_bichromatic(args, rank, world, local_rank):
+    """Bichromatic BUILD + FastPAM1 per step on the m x n location-by-consumer
+    matrix; value = (m - k) n point-evals per SWAP pass / median pass."""
+    import torch
+    import paper_2008_05171_gb300.kmedoids as km
+    from paper_2008_05171_gb300 import workloads as wl
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    spec = WORKLOADS[args.workload]
+    m, n, k = spec["m"], spec["n"], spec["k"]
+    L, C = getattr(wl, spec["recipe"])()
+    D = wl.cross_euclidean_f32_torch(L, C, dev)
+    stream = torch.cuda.current_stream()
+    opts = km.options(profile=True)
+    ws = torch.empty(int(km.load().kmedoids_bichromatic_workspace_size(m, n, k, km.KM_F32,
+                                                                        ctypes.byref(opts))),
+                     dtype=torch.uint8, device=dev)
+    torch.cuda.synchronize()
+
+    def step():
+        return km.run_bichromatic(D, k, n, ws=ws, profile=True, tune=args.tune)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    barrier(world)
+    clocks = Clocks(local_rank)
+    clocks.start()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    results = []
+    for i in range(args.steps):
+        ev[i][0].record(stream)
+        results.append(step())
+        ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    ck = clocks.stop()
+    total_ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in ev), world, dev)
+    med_ms = max_over_ranks(float(np.median([r["eval_ms_median"] for r in results])), world, dev)
+    mean_ms = sum(r["eval_ms"] for r in results) / max(1, sum(r["eval_launches"] for r in results))
+    evals = (m - k) * n
+    value = world * evals / (med_ms / 1e3)
+    peak, peak_kind = peaks()
+    r0 = results[-1]
+    ach = evals * 4 / (mean_ms / 1e3) / 1e9
+    roofline = {"bound": "hbm", "achieved": round(ach, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(ach / peak, 4), "traffic": None,
+                "peak_source": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)"
+                if peak_kind == "measured" else "fallback 6.8 TB/s",
+                "kernel": "k_stream<float,SWAP> over the location rows",
+                "algorithmic_bytes_per_launch": evals * 4, "avg_launch_ms": round(mean_ms, 5)}
+    e2e = None
+    if not args.no_e2e:
+        Dh = torch.empty(D.shape, dtype=D.dtype, pin_memory=True)
+        Dh.copy_(D)
+        Dd = torch.empty_like(D)
+        med_h = torch.empty(k, dtype=torch.int32, pin_memory=True)
+        lab_h = torch.empty(n, dtype=torch.int32, pin_memory=True)
+        torch.cuda.synchronize()
+        e_ms, e_evals = 0.0, 0
+        for i in range(-1, args.steps):  # one untimed warm-up step
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            km.upload(Dh, n=n, D=Dd)
+            r = km.run_bichromatic(Dd, k, n, ws=ws, tune=args.tune)
+            med_h.copy_(r["medoids"], non_blocking=True)
+            lab_h.copy_(r["labels"], non_blocking=True)
+            b.record(stream)
+            torch.cuda.synchronize()
+            if i >= 0:
+                e_ms += a.elapsed_time(b)
+                e_evals += r["iterations"] * evals
+        e_ms = max_over_ranks(e_ms, world, dev)
+        e2e = {"value": world * e_evals / (e_ms / 1e3), "unit": "point-evals/s",
+               "steps": args.steps, "ms_per_step": e_ms / args.steps,
+               "h2d_bytes_per_step": int(D.numel() * 4), "d2h_bytes_per_step": int(4 * k + 4 * n),
+               "note": "SWAP point-evals / (matrix upload from pinned host memory + BUILD + "
+                       "SWAP + medoids and labels read back)"}
+        del Dh, Dd
+    line = {
+        "metric": METRIC, "value": value, "unit": "point-evals/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32 (exact 64-bit fixed-point dTD sums, FP64 TD)", "data": "synthetic",
+        "config": {"workload": args.workload + ": " + spec["desc"], "m": m, "n": n, "k": k,
+                   "matrix_bytes": int(D.numel() * 4),
+                   "l2": "matrix larger than L2 (129 MB): no flush needed",
+                   "parallelism": "single GPU" if world == 1 else "replicas"},
+        "value_definition": "(m-k)*n point-evals per FastPAM1 SWAP evaluation pass / median "
+                            "pass time; ms_per_step = the whole BUILD + SWAP run",
+        "swap_pass": {"median_ms": med_ms, "mean_ms": mean_ms,
+                      "passes_per_run": int(r0["iterations"]), "point_evals_per_pass": evals},
+        "full_run_ms": total_ms / args.steps, "swap_iterations": r0["iterations"],
+        "swaps": r0["swaps"], "td": r0["td"],
+        "kernel_ms_per_step": {"build_eval": r0["build_eval_ms"], "swap_eval": r0["eval_ms"],
+                               "build_total": r0["build_ms"], "swap_total": r0["swap_ms"]},
+        "roofline": roofline,
+        "gpu_launches": int(sum(r["kernel_launches"] for r in results)),
+        "clocks": ck, "e2e": e2e,
+    }
+    if rank == 0 and not args.no_cpu_baseline and world == 1:
+        line["cpu_baseline"] = cpu_baseline_bichromatic(D, spec, args.cpu_seconds)
+    return line
+
+
+def cpu_baseline_bichromatic(D, spec, budget_s, m_sample=1000):
+    """The FP64 bichromatic oracle on the host cores: FastPAM1 evaluation
+    passes (Eq. (7) over every consumer) of the first m_sample locations,
+    from a fixed medoid set among them, as many as fit in about budget_s."""
+    import oracle
+    n, k = spec["n"], spec["k"]
+    Dh = D[:m_sample].cpu().numpy() if hasattr(D, "cpu") else np.asarray(D)[:m_sample]
+    med = np.arange(0, m_sample, m_sample // k, dtype=np.int32)[:k]
+    t0 = time.perf_counter()
+    passes = 0
+    while time.perf_counter() - t0 < budget_s or passes == 0:
+        oracle.bi_eval_swaps(Dh, med, n=n)
+        passes += 1
+    dt = time.perf_counter() - t0
+    return {"value": passes * (m_sample - k) * n / dt, "unit": "point-evals/s",
+            "cores": oracle.num_threads(), "kind": "oracle", "seconds": dt,
+            "sample": "%d FastPAM1 evaluation passes of the first %d locations against all "
+                      "n=%d consumers (k=%d evenly spaced medoids among them; FP64 C oracle, "
+                      "OpenMP over locations), %.1f s" % (passes, m_sample, n, k, dt)}
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
     import paper_2008_05171_gb300.kmedoids as km
@@ -723,6 +858,8 @@ def run_ours(args, rank, world, local_rank):
         return run_features(args, rank, world, local_rank)
     if args.workload.startswith("batched"):
         return run_batched(args, rank, world, local_rank)
+    if args.workload.startswith("bichromatic"):
+        return run_bichromatic(args, rank, world, local_rank)
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
     D, spec = make_input(args.workload, dev)
@@ -1195,6 +1332,30 @@ def run_reference(args, rank, world):
     import torch
     spec = WORKLOADS[args.workload]
     from paper_2008_05171_gb300 import workloads as wl
+    if args.workload.startswith("bichromatic"):
+        m, n, k = spec["m"], spec["n"], spec["k"]
+        L, C = getattr(wl, spec["recipe"])()
+        Ds = wl.cross_euclidean_f32(L[:1000], C)  # the sample's location rows
+        vals, secs, cb = [], [], None
+        for _ in range(args.warmup + args.steps):
+            cb = cpu_baseline_bichromatic(Ds, spec, min(8.0, args.cpu_seconds))
+            vals.append(cb["value"])
+            secs.append(cb.pop("seconds"))
+        v = float(np.mean(vals[args.warmup:]))
+        cb["value"] = v
+        ld = (n + 3) // 4 * 4
+        return {"impl": "reference", "metric": METRIC, "value": v, "unit": "point-evals/s",
+                "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": 1e3 * float(np.mean(secs[args.warmup:])),
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f64", "data": "synthetic",
+                "config": {"workload": args.workload + ": " + spec["desc"], "m": m, "n": n,
+                           "k": k, "matrix_bytes": int(m * ld * 4),
+                           "l2": "matrix larger than L2 (129 MB): no flush needed",
+                           "parallelism": "single GPU" if world == 1 else "replicas"},
+                "cpu_baseline": cb,
+                "e2e": {"value": v, "unit": "point-evals/s", "h2d_bytes_per_step": 0,
+                        "d2h_bytes_per_step": 0}}
     if args.workload.startswith("batched"):
         # the oracle on the first instances of the batch (bounded sample)
         vals, secs, cb = [], [], None

@@ -638,6 +638,12 @@ km_status kmedoids_upload_matrix(const void *host, int64_t host_ld,
                                  int32_t dtype, int64_t n, void *D,
                                  int64_t ld, void *stream);
 
+/* kmedoids_upload_matrix for a matrix of `rows` rows of n elements (the m
+ * location rows of the bichromatic form): D holds rows * ld elements. */
+km_status kmedoids_upload_rows(const void *host, int64_t host_ld,
+                               int32_t dtype, int64_t rows, int64_t n,
+                               void *D, int64_t ld, void *stream);
+
 /* Self-test of the bounded device waits (failure detection; the paper has
  * no counterpart).  Launches a kernel whose wait can never be satisfied,
  * built on the same wait routines the pipelined kernels use:

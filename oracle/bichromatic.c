@@ -139,52 +139,62 @@ void oracle_bi_eval_swaps(const void *D, int dtype, int64_t m, int64_t n,
   int32_t *near = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
   double *dn = (double *)malloc(sizeof(double) * (size_t)n);
   double *ds = (double *)malloc(sizeof(double) * (size_t)n);
-  double *acc = (double *)malloc(sizeof(double) * (size_t)k);
-  int32_t *trial = (int32_t *)malloc(sizeof(int32_t) * (size_t)k);
   double *rl = (double *)malloc(sizeof(double) * (size_t)k);
   bi_cache(D, dtype, n, ld, med, k, near, dn, ds);
   /* removal loss, Eq. (7): Delta^{-m_i} = sum_{nearest(c) = i} (d_s - d_n) */
   for (int i = 0; i < k; i++) rl[i] = 0.0;
   for (int64_t c = 0; c < n; c++) rl[near[c]] += ds[c] - dn[c];
   const double td0 = (method == 0) ? oracle_bi_td(D, dtype, m, n, ld, med, k, NULL) : 0.0;
+#pragma omp parallel
+  {
+    double *acc = (double *)malloc(sizeof(double) * (size_t)k);
+    int32_t *trial = (int32_t *)malloc(sizeof(int32_t) * (size_t)k);
+#pragma omp for schedule(dynamic, 16)
+    for (int64_t l = 0; l < m; l++) {
+      if (is_med[l]) {
+        cand_delta[l] = BI_INF;
+        cand_slot[l] = -1;
+        continue;
+      }
+      if (method == 0) {
+        for (int i = 0; i < k; i++) {
+          memcpy(trial, med, sizeof(int32_t) * (size_t)k);
+          trial[i] = (int32_t)l;
+          acc[i] = oracle_bi_td(D, dtype, m, n, ld, trial, k, NULL) - td0;
+        }
+      } else {
+        for (int i = 0; i < k; i++) acc[i] = rl[i];
+        double plus = 0.0; /* shared term Delta^{+x_l} */
+        for (int64_t c = 0; c < n; c++) {
+          double v = bd(D, dtype, ld, l, c);
+          if (v < dn[c]) { /* x_l becomes the nearest medoid of x_c */
+            plus += v - dn[c];
+            acc[near[c]] += dn[c] - ds[c];
+          } else if (v < ds[c]) { /* x_l would be the second nearest */
+            acc[near[c]] += v - ds[c];
+          }
+        }
+        for (int i = 0; i < k; i++) acc[i] += plus;
+      }
+      int bi = 0;
+      for (int i = 1; i < k; i++)
+        if (acc[i] < acc[bi]) bi = i;
+      cand_delta[l] = acc[bi];
+      cand_slot[l] = bi;
+    }
+    free(acc);
+    free(trial);
+  }
+  /* the least (Delta, slot, location) */
   *best_delta = BI_INF;
   *best_slot = -1;
   *best_cand = -1;
   for (int64_t l = 0; l < m; l++) {
-    if (is_med[l]) {
-      cand_delta[l] = BI_INF;
-      cand_slot[l] = -1;
-      continue;
-    }
-    if (method == 0) {
-      for (int i = 0; i < k; i++) {
-        memcpy(trial, med, sizeof(int32_t) * (size_t)k);
-        trial[i] = (int32_t)l;
-        acc[i] = oracle_bi_td(D, dtype, m, n, ld, trial, k, NULL) - td0;
-      }
-    } else {
-      for (int i = 0; i < k; i++) acc[i] = rl[i];
-      double plus = 0.0; /* shared term Delta^{+x_l} */
-      for (int64_t c = 0; c < n; c++) {
-        double v = bd(D, dtype, ld, l, c);
-        if (v < dn[c]) { /* x_l becomes the nearest medoid of x_c */
-          plus += v - dn[c];
-          acc[near[c]] += dn[c] - ds[c];
-        } else if (v < ds[c]) { /* x_l would be the second nearest */
-          acc[near[c]] += v - ds[c];
-        }
-      }
-      for (int i = 0; i < k; i++) acc[i] += plus;
-    }
-    int bi = 0;
-    for (int i = 1; i < k; i++)
-      if (acc[i] < acc[bi]) bi = i;
-    cand_delta[l] = acc[bi];
-    cand_slot[l] = bi;
-    if (acc[bi] < *best_delta ||
-        (acc[bi] == *best_delta && (bi < *best_slot))) {
-      *best_delta = acc[bi];
-      *best_slot = bi;
+    if (is_med[l]) continue;
+    if (cand_delta[l] < *best_delta ||
+        (cand_delta[l] == *best_delta && cand_slot[l] < *best_slot)) {
+      *best_delta = cand_delta[l];
+      *best_slot = cand_slot[l];
       *best_cand = l;
     }
   }
@@ -192,8 +202,6 @@ void oracle_bi_eval_swaps(const void *D, int dtype, int64_t m, int64_t n,
   free(near);
   free(dn);
   free(ds);
-  free(acc);
-  free(trial);
   free(rl);
 }
 

@@ -1,6 +1,6 @@
-// km_upload.cu -- kmedoids_upload_matrix: the dissimilarity matrix from host
-// memory into the caller's device buffer, row by row from one row pitch to
-// another, padding columns cleared.
+// km_upload.cu -- kmedoids_upload_matrix / kmedoids_upload_rows: the
+// dissimilarity matrix from host memory into the caller's device buffer, row
+// by row from one row pitch to another, padding columns cleared.
 //
 // From page-locked (pinned or registered) host memory the rows are read by
 // the SMs themselves, 16-byte loads over the CPU-GPU link into the device
@@ -66,16 +66,17 @@ km_status up_fail(km_status s, const char* msg) {
 
 using namespace km;
 
-extern "C" km_status kmedoids_upload_matrix(const void* host, int64_t host_ld, int32_t dtype,
-                                            int64_t n, void* D, int64_t ld, void* stream) {
+extern "C" km_status kmedoids_upload_rows(const void* host, int64_t host_ld, int32_t dtype,
+                                          int64_t rows, int64_t n, void* D, int64_t ld,
+                                          void* stream) {
   set_last_error("");
   if (dtype != KM_I32 && dtype != KM_F32 && dtype != KM_U16)
     return up_fail(KM_E_INVALID, "dtype must be KM_I32, KM_F32 or KM_U16");
   if (!host || !D) return up_fail(KM_E_INVALID, "host and D must be non-NULL");
-  if (n <= 0 || host_ld < n || ld < n)
-    return up_fail(KM_E_INVALID, "need n > 0, host_ld >= n and ld >= n");
+  if (rows <= 0 || n <= 0 || host_ld < n || ld < n)
+    return up_fail(KM_E_INVALID, "need rows > 0, n > 0, host_ld >= n and ld >= n");
   const size_t es = dtype == KM_U16 ? 2 : 4;
-  if ((double)n * (double)(ld > host_ld ? ld : host_ld) * (double)es > 0x1p60)
+  if ((double)rows * (double)(ld > host_ld ? ld : host_ld) * (double)es > 0x1p60)
     return up_fail(KM_E_INVALID, "matrix too large");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const size_t row = (size_t)n * es, sp = (size_t)host_ld * es, dp = (size_t)ld * es;
@@ -94,7 +95,7 @@ extern "C" km_status kmedoids_upload_matrix(const void* host, int64_t host_ld, i
   if (pa.type == cudaMemoryTypeHost && src) {
     // the last byte read must lie in page-locked memory too, at the same
     // offset of the device mapping
-    const size_t last = (size_t)(n - 1) * sp + row - 1;
+    const size_t last = (size_t)(rows - 1) * sp + row - 1;
     cudaPointerAttributes pb;
     memset(&pb, 0, sizeof(pb));
     if (cudaPointerGetAttributes(&pb, static_cast<const unsigned char*>(host) + last) != cudaSuccess) {
@@ -107,8 +108,9 @@ extern "C" km_status kmedoids_upload_matrix(const void* host, int64_t host_ld, i
   }
   if (pa.type != cudaMemoryTypeHost || !src) {
     // not addressable by the device: the copy engines, then the pad columns
-    e = cudaMemcpy2DAsync(D, dp, host, sp, row, (size_t)n, cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess && dp > row) e = cudaMemset2DAsync(static_cast<char*>(D) + row, dp, 0, dp - row, (size_t)n, s);
+    e = cudaMemcpy2DAsync(D, dp, host, sp, row, (size_t)rows, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess && dp > row)
+      e = cudaMemset2DAsync(static_cast<char*>(D) + row, dp, 0, dp - row, (size_t)rows, s);
   } else {
     int dev = 0, sms = 0;
     e = cudaGetDevice(&dev);
@@ -116,19 +118,19 @@ extern "C" km_status kmedoids_upload_matrix(const void* host, int64_t host_ld, i
     if (e == cudaSuccess) {
       unsigned char* dst = static_cast<unsigned char*>(D);
       const uintptr_t al = reinterpret_cast<uintptr_t>(src) | reinterpret_cast<uintptr_t>(dst);
-      if (sp == row && dp == row && (al % 16) == 0 && ((size_t)n * row) % 16 == 0) {
-        const size_t n16 = (size_t)n * row / 16;
+      if (sp == row && dp == row && (al % 16) == 0 && ((size_t)rows * row) % 16 == 0) {
+        const size_t n16 = (size_t)rows * row / 16;
         k_upload_flat<<<sms * 4, kUpThreads, 0, s>>>(reinterpret_cast<const uint4*>(src),
                                                       reinterpret_cast<uint4*>(dst), n16);
       } else {
-        const int grid = (int)(n < (int64_t)sms * 8 ? n : (int64_t)sms * 8);
+        const int grid = (int)(rows < (int64_t)sms * 8 ? rows : (int64_t)sms * 8);
         const size_t mix = al | sp | dp | row;
         if (mix % 16 == 0)
-          k_upload_rows<uint4><<<grid, kUpThreads, 0, s>>>(src, sp, dst, dp, row, n);
+          k_upload_rows<uint4><<<grid, kUpThreads, 0, s>>>(src, sp, dst, dp, row, rows);
         else if (mix % 4 == 0)
-          k_upload_rows<uint32_t><<<grid, kUpThreads, 0, s>>>(src, sp, dst, dp, row, n);
+          k_upload_rows<uint32_t><<<grid, kUpThreads, 0, s>>>(src, sp, dst, dp, row, rows);
         else
-          k_upload_rows<uint16_t><<<grid, kUpThreads, 0, s>>>(src, sp, dst, dp, row, n);
+          k_upload_rows<uint16_t><<<grid, kUpThreads, 0, s>>>(src, sp, dst, dp, row, rows);
       }
       e = cudaGetLastError();
     }
@@ -140,4 +142,9 @@ extern "C" km_status kmedoids_upload_matrix(const void* host, int64_t host_ld, i
     return KM_E_CUDA;
   }
   return KM_OK;
+}
+
+extern "C" km_status kmedoids_upload_matrix(const void* host, int64_t host_ld, int32_t dtype,
+                                            int64_t n, void* D, int64_t ld, void* stream) {
+  return kmedoids_upload_rows(host, host_ld, dtype, n, n, D, ld, stream);
 }

@@ -36,7 +36,7 @@ EXPORTS = ["km_default_options", "kmedoids_workspace_size", "kmedoids_build",
            "kmedoids_batched_clara_workspace_size", "kmedoids_run_batched_clara",
            "kmedoids_upload_matrix", "kmedoids_bounds_checked",
            "kmedoids_bichromatic_workspace_size", "kmedoids_run_bichromatic",
-           "kmedoids_swap_bichromatic"]
+           "kmedoids_swap_bichromatic", "kmedoids_upload_rows"]
 
 
 class KmError(RuntimeError):
@@ -158,6 +158,8 @@ def load(path: str = LIB_PATH):
         lib.kmedoids_wait_selftest.restype = i32
         lib.kmedoids_upload_matrix.argtypes = [P, i64, i32, i64, P, i64, P]
         lib.kmedoids_upload_matrix.restype = i32
+        lib.kmedoids_upload_rows.argtypes = [P, i64, i32, i64, i64, P, i64, P]
+        lib.kmedoids_upload_rows.restype = i32
         lib.kmedoids_bichromatic_workspace_size.argtypes = [i64, i64, i32, i32, opt_p]
         lib.kmedoids_bichromatic_workspace_size.restype = sz
         for name in ("kmedoids_run_bichromatic", "kmedoids_swap_bichromatic"):
@@ -770,26 +772,30 @@ def swap_bichromatic(D, medoids, n, labels=True, ws=None, **kw):
 
 
 def upload(H, n=None, D=None, ld=None, device=None):
-    """kmedoids_upload_matrix: the n x n matrix H (a CPU tensor with unit
-    column stride, int32 / float32 / 16-bit; pinned memory is read by the
-    SMs over the CPU-GPU link) into the device tensor D (allocated with ld
-    columns when None, ld defaulting to n rounded up to the library's
-    alignment: 4 elements, 8 for 16-bit).  Columns n .. ld-1 of D are set to
-    zero.  Returns D."""
+    """kmedoids_upload_rows: the rows of H (a CPU tensor with unit column
+    stride, int32 / float32 / 16-bit; pinned memory is read by the SMs over
+    the CPU-GPU link), n elements each (default: as many as H has rows, the
+    square matrix), into the device tensor D (allocated with ld columns
+    when None, ld defaulting to n rounded up to the library's alignment: 4
+    elements, 8 for 16-bit).  Columns n .. ld-1 of D are set to zero.
+    Returns D."""
     torch = _torch()
     if H.dim() != 2 or H.is_cuda or H.stride(1) != 1:
         raise ValueError("H must be a 2-D CPU tensor with unit column stride")
     code = _dtype_code(H)
-    n = H.shape[0] if n is None else int(n)
+    rows = H.shape[0]
+    n = rows if n is None else int(n)
     if D is None:
         a = 8 if code == KM_U16 else 4
         ld = (n + a - 1) // a * a if ld is None else int(ld)
-        D = torch.empty((n, ld), dtype=H.dtype, device=device or "cuda")
-    if D.dim() != 2 or not D.is_cuda or D.stride(1) != 1 or D.dtype != H.dtype:
-        raise ValueError("D must be a 2-D CUDA tensor of H's dtype with unit column stride")
+        D = torch.empty((rows, ld), dtype=H.dtype, device=device or "cuda")
+    if D.dim() != 2 or not D.is_cuda or D.stride(1) != 1 or D.dtype != H.dtype or \
+            D.shape[0] < rows:
+        raise ValueError("D must be a 2-D CUDA tensor of H's dtype with unit column stride "
+                         "and at least H's rows")
     with torch.cuda.device(D.device):
-        _check(load().kmedoids_upload_matrix(
-            ctypes.c_void_p(H.data_ptr()), H.stride(0), code, n,
+        _check(load().kmedoids_upload_rows(
+            ctypes.c_void_p(H.data_ptr()), H.stride(0), code, rows, n,
             ctypes.c_void_p(D.data_ptr()), D.stride(0), _stream()))
     return D
 

@@ -173,6 +173,23 @@ def cross_euclidean_f32(L: np.ndarray, C: np.ndarray, ld: int | None = None) -> 
     return D
 
 
+def cross_euclidean_f32_torch(L: np.ndarray, C: np.ndarray, device, ld: int | None = None,
+                              block: int = 512):
+    """cross_euclidean_f32 evaluated with torch on ``device``: FP64 direct
+    differences, one rounding to FP32, shape (len(L), ld)."""
+    import torch
+    Lt = torch.as_tensor(np.asarray(L, dtype=np.float64), device=device)
+    Ct = torch.as_tensor(np.asarray(C, dtype=np.float64), device=device)
+    m, n = Lt.shape[0], Ct.shape[0]
+    ld = round_up(n, 4) if ld is None else ld
+    D = torch.zeros((m, ld), dtype=torch.float32, device=device)
+    for i0 in range(0, m, block):
+        diff = Lt[i0:i0 + block, None, :] - Ct[None, :, :]
+        D[i0:i0 + block, :n] = torch.sqrt((diff * diff).sum(-1)).float()
+        del diff
+    return D
+
+
 def bichromatic_points(m: int, n: int, *, towns: int = 40, seed=11, integer: bool = False):
     """(locations (m, 2), consumers (n, 2)): consumers from a mixture of
     ``towns`` Gaussian clusters (centres uniform in [0, 1000)^2, sigma
@@ -190,6 +207,12 @@ def bichromatic_points(m: int, n: int, *, towns: int = 40, seed=11, integer: boo
 
 
 # -------------------------------------------------------------- workloads --
+
+def bichromatic_100000(m: int = 20000, n: int = 100000):
+    """Facility placement: n = 100000 consumers around 200 towns, m = 20000
+    candidate locations uniform over the square (float coordinates)."""
+    return bichromatic_points(m, n, towns=200, seed=100000)
+
 
 def manhattan_1000(n: int = 1000):
     """Integer workload: (D int32 (n, ld), k=10)."""

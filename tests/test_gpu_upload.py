@@ -50,6 +50,19 @@ def test_upload_is_byte_exact_and_clears_padding(n, host_ld, ld, dtype, pinned):
     assert bool((Dc[:, n:] == 0).all())
 
 
+@pytest.mark.parametrize("pinned", [True, False])
+def test_upload_of_a_rectangular_matrix(pinned):
+    """kmedoids_upload_rows: m location rows of n consumer columns (the
+    bichromatic form), into a padded device buffer."""
+    H = torch.from_numpy(np.random.default_rng(9).random((300, 1001), np.float32))
+    if pinned:
+        H = H.pin_memory()
+    D = torch.full((300, 1004), -1.0, dtype=torch.float32, device="cuda")
+    km.upload(H, n=1001, D=D)
+    Dc = D.cpu()
+    assert torch.equal(Dc[:, :1001], H[:, :1001]) and bool((Dc[:, 1001:] == 0).all())
+
+
 def test_upload_rejects_a_device_source():
     lib = km.load()
     import ctypes
