@@ -23,7 +23,8 @@
 //               funnel-shifted into a 16-bit lane mask (one shift a pair);
 //               the pairs that pass (rare) are walked lane by lane (or, in
 //               a group where some lane has many, with predication) and
-//               take d = sqrt(|x_c|^2 + |x_o|^2 - 2 g):
+//               take d = sqrt(|x_c|^2 + |x_o|^2 - 2 g) (hardware square
+//               root):
 //               SWAP:  Eq. (7) per-slot terms into per-candidate slot
 //                      accumulators in shared memory, the shared term into
 //                      a register sum;
@@ -214,6 +215,15 @@ __device__ __forceinline__ float sel16(const float* v, int j) {
 // case comparison of Eq. (7) keeps its sign in fixed point.
 __device__ __forceinline__ int fxq(float x, float scale) {
   return __float2int_rn(fminf(x * scale, 67108864.f));
+}
+
+// Distance of a Gram pair in the pass: the hardware square root (relative
+// error a few ulp, far below the error of the bf16 Gram entry itself), so a
+// hit costs one instruction instead of the correctly rounded sequence.
+__device__ __forceinline__ float pair_dist(float d2) {
+  float r;
+  asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(fmaxf(d2, 0.f)));
+  return r;
 }
 
 // ------------------------------------------------------------ pass kernel
@@ -462,7 +472,7 @@ __global__ void __launch_bounds__(kFeatThreads, 1) k_feat_pass(const FeatArgs a)
         auto hit = [&](int col, float v) {
           const float g = (hc + m_thr[col]) - v;
           const float d2 = fmaf(-2.f, g, nc + m_no[col]);
-          const float dd = sqrtf(fmaxf(d2, 0.f));
+          const float dd = pair_dist(d2);
           const float dn_ = m_dn[col];
           const int ddq = fxq(dd, scale), dnq = fxq(dn_, scale);
           if (MODE == kModeSwap) {
@@ -489,7 +499,7 @@ __global__ void __launch_bounds__(kFeatThreads, 1) k_feat_pass(const FeatArgs a)
           for (int j = 0; j < 32; ++j) {
             const float g = (hc + m_thr[col0 + j]) - v[j];
             const float d2 = fmaf(-2.f, g, nc + m_no[col0 + j]);
-            sh += (colg + j < n) ? fxq(sqrtf(fmaxf(d2, 0.f)), scale) : 0;
+            sh += (colg + j < n) ? fxq(pair_dist(d2), scale) : 0;
           }
         } else {
 #pragma unroll
