@@ -107,7 +107,27 @@ struct FeatArgs {
   int mode;             // kModeSwap / kModeBuild
   int build_first;
   double tol;
+  // Incremental BUILD (steps >= 1): the points whose d_n the last commit
+  // lowered (every point after step 0), listed by that commit in any order:
+  // their B-operand rows (XpL, the threshold columns zero during BUILD so
+  // that every Gram entry is the same in every pass), |x_o|^2, a threshold
+  // on the MMA output below which the pair may change the gain, and d_n
+  // before and after the commit in fixed point (0 before step 0's commit);
+  // bgain holds every candidate's gain sum_o min(d - d_n, 0) in fixed point.
+  int incremental;
+  uint16_t* XpL;
+  float* lno;
+  float* lthr;
+  int* lqo;
+  int* lqn;
+  unsigned* lcnt;       // [0] entries in the list (cleared by the pass that reads
+                        // it); as u64 [1] the rows every update pass streamed
+  long long* bgain;
 };
+
+// Pass of the incremental BUILD: the gain change of every candidate from
+// the listed points (k_feat_pass with the list as the point blocks).
+constexpr int kModeBuildUpd = 2;
 
 constexpr int kFeatAccBufs = 4;     // TMEM accumulators of kTileN columns
 constexpr int kFeatMetaStages = 4;  // ring of per-block point caches
@@ -262,7 +282,11 @@ __global__ void __launch_bounds__(kFeatThreads, 1) k_feat_pass(const FeatArgs a)
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int rb = st->rb;
   const int ntiles = a.n_pad / kTileM;
-  const int nblocks = a.n_pad / kTileN;
+  // the update pass streams the listed points only (read before any block
+  // moves; the commit that wrote the list finished before this launch)
+  const int nlist = (MODE == kModeBuildUpd) ? (int)min(__ldcg(a.lcnt), (unsigned)a.n) : 0;
+  const int nblocks = (MODE == kModeBuildUpd) ? (nlist + kTileN - 1) / kTileN : a.n_pad / kTileN;
+  const uint16_t* Bsrc = (MODE == kModeBuildUpd) ? a.XpL : a.XpB;
   const uint32_t tile_bytes = (uint32_t)(kTileM * d * 2);
 
   if (MODE == kModeSwap && blockIdx.x == 0) {
@@ -270,7 +294,7 @@ __global__ void __launch_bounds__(kFeatThreads, 1) k_feat_pass(const FeatArgs a)
     for (int i = tid; i < k; i += blockDim.x) rnext[i] = 0;
     if (tid == 0) a.td2[rb ^ 1] = 0.0;
   }
-  if (MODE == kModeBuild && blockIdx.x == 0 && tid == 0) st->build_td_d = 0.0;
+  if (MODE != kModeSwap && blockIdx.x == 0 && tid == 0) st->build_td_d = 0.0;
   if (tid == 0) {
     mbar_init(a_full, 1);
     mbar_init(tile_done, kFeatEpiWarps);
@@ -343,7 +367,7 @@ __global__ void __launch_bounds__(kFeatThreads, 1) k_feat_pass(const FeatArgs a)
           mbar_arrive_expect_tx(&b_full[s], tile_bytes);
           bused |= 1u << s;
           bph = (bph & ~(1u << s)) | (ph << s);
-          bulk_g2s(stages + (size_t)s * L.stage_bytes, a.XpB + (size_t)b * kTileN * d, tile_bytes,
+          bulk_g2s(stages + (size_t)s * L.stage_bytes, Bsrc + (size_t)b * kTileN * d, tile_bytes,
                    &b_full[s]);
           const int ms = (int)(gb % kFeatMetaStages);
           const uint32_t mp = (uint32_t)((gb / kFeatMetaStages) & 1);
@@ -356,11 +380,19 @@ __global__ void __launch_bounds__(kFeatThreads, 1) k_feat_pass(const FeatArgs a)
           mused |= 1u << ms;
           mph = (mph & ~(1u << ms)) | (mp << ms);
           const size_t o0 = (size_t)b * kTileN;
-          bulk_g2s(meta, a.norms + o0, 4 * kTileN, &m_full[ms]);
-          bulk_g2s(meta + 512, a.thr + o0, 4 * kTileN, &m_full[ms]);
-          bulk_g2s(meta + 1024, a.dn + o0, 4 * kTileN, &m_full[ms]);
-          bulk_g2s(meta + 1536, a.ds + o0, 4 * kTileN, &m_full[ms]);
-          bulk_g2s(meta + 2048, a.near + o0, 4 * kTileN, &m_full[ms]);
+          if (MODE == kModeBuildUpd) {
+            bulk_g2s(meta, a.lno + o0, 4 * kTileN, &m_full[ms]);
+            bulk_g2s(meta + 512, a.lthr + o0, 4 * kTileN, &m_full[ms]);
+            bulk_g2s(meta + 1024, a.lqo + o0, 4 * kTileN, &m_full[ms]);
+            bulk_g2s(meta + 1536, a.lqn + o0, 4 * kTileN, &m_full[ms]);
+            bulk_g2s(meta + 2048, a.lqn + o0, 4 * kTileN, &m_full[ms]);  // keeps the byte count
+          } else {
+            bulk_g2s(meta, a.norms + o0, 4 * kTileN, &m_full[ms]);
+            bulk_g2s(meta + 512, a.thr + o0, 4 * kTileN, &m_full[ms]);
+            bulk_g2s(meta + 1024, a.dn + o0, 4 * kTileN, &m_full[ms]);
+            bulk_g2s(meta + 1536, a.ds + o0, 4 * kTileN, &m_full[ms]);
+            bulk_g2s(meta + 2048, a.near + o0, 4 * kTileN, &m_full[ms]);
+          }
         }
       }
       if (!ok) {
@@ -492,7 +524,26 @@ __global__ void __launch_bounds__(kFeatThreads, 1) k_feat_pass(const FeatArgs a)
             sh += dnq - ddq;
           }
         };
-        if (MODE == kModeBuild && a.build_first) {
+        if (MODE == kModeBuildUpd) {
+          // listed point o (column col): v = |x_c|^2/2 - x_c.x_o (zero
+          // threshold columns), so d^2 = |x_o|^2 + 2 v; the pair can change
+          // the gain only when d is below the larger of its old and new d_n
+          // (lthr is that bound with a margin, so the test lets through a
+          // superset); the change min(d - dn_new, 0) - min(d - dn_old, 0) is
+          // exact in fixed point, and zero for the pairs the margin adds
+          const int* m_qo = reinterpret_cast<const int*>(meta + 1024);
+          const int* m_qn = reinterpret_cast<const int*>(meta + 1536);
+          const int colg = b * kTileN + col0;
+          if (cvalid) {
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+              if (v[j] < m_thr[col0 + j] && colg + j < nlist) {
+                const int ddq = fxq(pair_dist(fmaf(2.f, v[j], m_no[col0 + j])), scale);
+                sh += (long long)(min(ddq - m_qn[col0 + j], 0) - min(ddq - m_qo[col0 + j], 0));
+              }
+            }
+          }
+        } else if (MODE == kModeBuild && a.build_first) {
           // every pair (thr = 0 before the first BUILD step)
           const int colg = b * kTileN + col0;
 #pragma unroll
@@ -571,6 +622,18 @@ __global__ void __launch_bounds__(kFeatThreads, 1) k_feat_pass(const FeatArgs a)
             for (int i = 0; i < k; ++i) __stcg(crow + i, 0u);
             rowc[r] = 0;
           }
+        } else if (MODE == kModeBuildUpd) {
+          if (c < n) {
+            const long long g = a.bgain[c] + shared_part;  // one CTA owns the tile
+            a.bgain[c] = g;
+            if (cvalid) {
+              Key<double> ck;
+              ck.d = (double)g * unit;
+              ck.slot = 0;
+              ck.cand = c;
+              if (key_less(ck, wbest)) wbest = ck;
+            }
+          }
         } else {
           if (cvalid) {
             Key<double> ck;
@@ -622,9 +685,15 @@ __global__ void __launch_bounds__(kFeatThreads, 1) k_feat_pass(const FeatArgs a)
     }
     b = warp_min_key(b);
     if (lane == 0) {
-      if (MODE == kModeBuild) {
+      if (MODE != kModeSwap) {
         st->build_gain_d = b.d;
         st->build_cand = b.cand;
+        if (MODE == kModeBuildUpd) {
+          // rows streamed by the update passes, then an empty list for the
+          // next commit
+          reinterpret_cast<unsigned long long*>(a.lcnt)[1] += (unsigned long long)nlist;
+          *a.lcnt = 0u;
+        }
       } else {
         st->best_d = b.d;
         st->best_i = 0;
@@ -840,6 +909,9 @@ __global__ void __launch_bounds__(256) k_feat_apply(const FeatArgs a) {
 }
 
 // BUILD commit: add the chosen point and lower d_n (exact FP32 distances).
+// Incremental BUILD: every point whose d_n this commit lowered (every point
+// at step 0) is appended to the list for the next update pass, its B row
+// copied into XpL; the plain pass instead gets the new threshold columns.
 __global__ void __launch_bounds__(256) k_feat_build_commit(const FeatArgs a) {
   __shared__ double scratch[8];
   KmState* st = a.st;
@@ -847,27 +919,67 @@ __global__ void __launch_bounds__(256) k_feat_build_commit(const FeatArgs a) {
   const int n = a.n, d = a.d;
   const int c = st->build_cand;
   const int o = blockIdx.x * blockDim.x + threadIdx.x;
+  const int lane = threadIdx.x & 31;
+  const float scale = __int_as_float((127 + a.fq) << 23);  // 2^q
   double local = 0.0;
   if (c >= 0 && c < n) {
+    bool listed = false;
+    float old_dn = 0.f, new_dn = 0.f;
     if (o < n) {
       const float q = dist2_rows(a.X + (size_t)o * a.ldx, a.X + (size_t)c * a.ldx, d);
       float cur = q;
       if (!a.build_first && !(q < a.dn2[o])) cur = a.dn2[o];
+      listed = a.build_first || q < a.dn2[o];
+      old_dn = a.build_first ? 0.f : a.dn[o];
       a.dn2[o] = cur;
       a.dn[o] = sqrtf(cur);
-      a.thr[o] = 0.5f * (a.norms[o] - cur);
-      write_thr_cols(a, o, a.thr[o]);
+      new_dn = a.dn[o];
+      if (!a.incremental) {
+        a.thr[o] = 0.5f * (a.norms[o] - cur);
+        write_thr_cols(a, o, a.thr[o]);
+      }
       local = sqrtf(cur);
     } else if (o < a.n_pad) {
       a.dn2[o] = Tr<float>::low();
       a.dn[o] = 0.f;
-      a.thr[o] = Tr<float>::high();
-      write_thr_cols(a, o, Tr<float>::high());
+      if (!a.incremental) {
+        a.thr[o] = Tr<float>::high();
+        write_thr_cols(a, o, Tr<float>::high());
+      }
+    }
+    if (a.incremental) {
+      // warp-aggregated append
+      const unsigned m = __ballot_sync(0xffffffffu, listed);
+      if (m) {
+        unsigned base = 0;
+        if (lane == __ffs(m) - 1) base = atomicAdd(a.lcnt, (unsigned)__popc(m));
+        base = __shfl_sync(0xffffffffu, base, __ffs(m) - 1);
+        if (listed) {
+          unsigned lt;
+          asm("mov.u32 %0, %%lanemask_lt;" : "=r"(lt));
+          const unsigned p = base + (unsigned)__popc(m & lt);
+          if (KM_INB(st, p, a.n_pad)) {
+            const float no = a.norms[o];
+            const float dmax = fmaxf(old_dn, new_dn);
+            a.lno[p] = no;
+            // v = (d^2 - |x_o|^2) / 2 below this bound: d below dmax with a
+            // relative margin of 2^-10 on d^2 that covers every rounding
+            a.lthr[p] = 0.5f * (dmax * dmax * (1.f + 0x1p-10f) + 0x1p-100f - no);
+            a.lqo[p] = a.build_first ? 0 : fxq(old_dn, scale);
+            a.lqn[p] = fxq(new_dn, scale);
+            const int kcs = a.dk >> 3;
+            for (int kc = 0; kc < kcs; ++kc)
+              *reinterpret_cast<uint4*>(a.XpL + chunk_off((int)p, kc, a.dk)) =
+                  *reinterpret_cast<const uint4*>(a.XpB + chunk_off(o, kc, a.dk));
+          }
+        }
+      }
     }
   }
   const double bs = fblock_sum(local, scratch);
   if (threadIdx.x == 0) atomicAdd(&st->build_td_d, bs);
-  if (blockIdx.x == 0 && threadIdx.x == 0 && c >= 0 && c < n) {
+  if (blockIdx.x == 0 && threadIdx.x == 0 && c >= 0 && c < n &&
+      KM_INB(st, st->build_step, a.k)) {
     const int step = st->build_step;
     a.med[step] = c;
     a.is_med[c] = 1;
@@ -954,7 +1066,7 @@ namespace {
 
 struct FeatWs {
   size_t st, med, is_med, near, sec, dn, ds, dn2, ds2, thr, norms, removal, td2, partials, trace,
-      gains, xpa, xpb, carry, range, total;
+      gains, xpa, xpb, carry, range, xpl, lno, lthr, lqo, lqn, lcnt, bgain, total;
   int n_pad, k_pad, cap;
 };
 
@@ -991,6 +1103,14 @@ bool feat_ws(int64_t n, int d, int k, const km_options* o, FeatWs* L) {
   L->xpb = take((size_t)n_pad * (d + 16) * 2);
   L->carry = take(4 * (size_t)kFeatMaxGrid * kTileM * k_pad);
   L->range = take(8 * (size_t)d);
+  // incremental BUILD: the list of changed points and every candidate's gain
+  L->xpl = take((size_t)n_pad * (d + 16) * 2);
+  L->lno = take(4 * (size_t)n_pad);
+  L->lthr = take(4 * (size_t)n_pad);
+  L->lqo = take(4 * (size_t)n_pad);
+  L->lqn = take(4 * (size_t)n_pad);
+  L->lcnt = take(16);
+  L->bgain = take(8 * (size_t)n_pad);
   L->total = off;
   L->n_pad = n_pad;
   L->k_pad = k_pad;
@@ -1059,13 +1179,18 @@ km_status f_pass(FCtx& c, int mode, int first, cudaEvent_t ev0 = nullptr,
   if (grid > kFeatMaxGrid) grid = kFeatMaxGrid;
   if (mode == kModeSwap)
     FK(cudaFuncSetAttribute(k_feat_pass<kModeSwap>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total));
-  else
+  else if (mode == kModeBuild)
     FK(cudaFuncSetAttribute(k_feat_pass<kModeBuild>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total));
+  else
+    FK(cudaFuncSetAttribute(k_feat_pass<kModeBuildUpd>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                            (int)L.total));
   if (ev0) FK(cudaEventRecord(ev0, c.s));
   if (mode == kModeSwap)
     k_feat_pass<kModeSwap><<<grid, kFeatThreads, L.total, c.s>>>(a);
-  else
+  else if (mode == kModeBuild)
     k_feat_pass<kModeBuild><<<grid, kFeatThreads, L.total, c.s>>>(a);
+  else
+    k_feat_pass<kModeBuildUpd><<<grid, kFeatThreads, L.total, c.s>>>(a);
   FK(cudaGetLastError());
   if (ev1) FK(cudaEventRecord(ev1, c.s));
   ++c.launches;
@@ -1145,6 +1270,14 @@ km_status run_features(bool do_build, bool do_swap, const void* X, int64_t n, in
   a.trace = c.ws + c.L.trace;
   a.trace_cap = c.L.cap;
   a.tol = c.opt.tol;
+  a.incremental = c.opt.build_full ? 0 : 1;
+  a.XpL = reinterpret_cast<uint16_t*>(c.ws + c.L.xpl);
+  a.lno = reinterpret_cast<float*>(c.ws + c.L.lno);
+  a.lthr = reinterpret_cast<float*>(c.ws + c.L.lthr);
+  a.lqo = reinterpret_cast<int*>(c.ws + c.L.lqo);
+  a.lqn = reinterpret_cast<int*>(c.ws + c.L.lqn);
+  a.lcnt = reinterpret_cast<unsigned*>(c.ws + c.L.lcnt);
+  a.bgain = reinterpret_cast<long long*>(c.ws + c.L.bgain);
   if (res) memset(res, 0, sizeof(*res));
 
   cudaEvent_t e0 = nullptr, e1 = nullptr, e2 = nullptr;
@@ -1202,6 +1335,13 @@ km_status run_features(bool do_build, bool do_swap, const void* X, int64_t n, in
   memset(&h, 0, sizeof(h));
   if (do_build) {
     FK(cudaMemsetAsync(a.is_med, 0, (size_t)c.L.n_pad, c.s));
+    if (a.incremental) {
+      // rows of the list past its length are streamed but never counted;
+      // zeros keep them finite
+      FK(cudaMemsetAsync(a.XpL, 0, (size_t)c.L.n_pad * a.dk * 2, c.s));
+      FK(cudaMemsetAsync(a.lcnt, 0, 16, c.s));
+      FK(cudaMemsetAsync(a.bgain, 0, 8 * (size_t)c.L.n_pad, c.s));
+    }
     for (int step = 0; step < k; ++step) {
       cudaEvent_t x0 = nullptr, x1 = nullptr;
       if (prof) {
@@ -1209,7 +1349,7 @@ km_status run_features(bool do_build, bool do_swap, const void* X, int64_t n, in
         FK(cudaEventCreate(&x1));
         bev.push_back({x0, x1});
       }
-      r = f_pass(c, kModeBuild, step == 0, x0, x1);
+      r = f_pass(c, (step > 0 && a.incremental) ? kModeBuildUpd : kModeBuild, step == 0, x0, x1);
       if (r != KM_OK) return r;
       FeatArgs b = a;
       b.build_first = (step == 0);
@@ -1222,6 +1362,13 @@ km_status run_features(bool do_build, bool do_swap, const void* X, int64_t n, in
     if (res) {
       res->build_steps = h.build_step;
       res->td_initial = h.td_book_d;
+      // point rows the BUILD passes streamed: every point in the dense step
+      // 0 (and in every step of the plain pass), the lists after that
+      unsigned long long upd = 0;
+      if (a.incremental)
+        FK(cudaMemcpy(&upd, reinterpret_cast<unsigned long long*>(a.lcnt) + 1, 8,
+                      cudaMemcpyDeviceToHost));
+      res->build_rows = a.incremental ? (long long)n + (long long)upd : (long long)n * k;
     }
     if (c.opt.build_gains)
       FK(cudaMemcpy(c.opt.build_gains, a.gains, 8 * (size_t)k, cudaMemcpyDeviceToHost));

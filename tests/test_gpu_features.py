@@ -81,6 +81,23 @@ def test_build_features_steps():
     assert start["iterations"] >= 1
 
 
+@pytest.mark.parametrize("n,d,k", [(20000, 64, 40), (6001, 128, 25)])
+def test_incremental_build_equals_the_plain_pass(n, d, k):
+    """The incremental BUILD (a dense pass for step 0, then each step updates
+    every candidate's gain from the points the last commit moved) against
+    the plain pass of every step: the same medoids in the same order, gains
+    within 1e-6 of TD, and far fewer point rows streamed."""
+    X = wl.features_200000(n=n, d=d, n_centers=k)
+    Xt = torch.from_numpy(X).to(torch.bfloat16).cuda()
+    a = km.build_features(Xt, k)
+    b = km.build_features(Xt, k, build_full=True)
+    assert a["medoids"].cpu().tolist() == b["medoids"].cpu().tolist()
+    assert np.all(np.abs(a["build_gains"] - b["build_gains"]) <= 1e-6 * b["td"])
+    assert abs(a["td"] - b["td"]) <= 1e-9 * b["td"]
+    assert b["build_rows"] == n * k
+    assert n <= a["build_rows"] < n * k // 4, a["build_rows"]
+
+
 def test_run_features_many_tiles_per_cta():
     """n = 20000 gives 157 candidate tiles, more than there are SMs, so CTAs
     take several tiles each through the dynamic tile counter (and the tile
