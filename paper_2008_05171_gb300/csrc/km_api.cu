@@ -1,11 +1,14 @@
-// km_api.cu -- the C ABI of libkmedoids for the matrix form (declared in
-// include/kmedoids.h): argument checks, workspace carving and the host-side
-// enqueue loops of BUILD (Alg. 1) and SWAP (Alg. 3 FastPAM1, Sec. 3.2
-// FastPAM2, Alg. 4 FasterPAM, Sec. 3.4 FastCLARANS), plus the
-// initialisations of Sec. 3.3.  All arithmetic of the method runs in the
-// kernels of km_stream.cu, km_points.cu, km_eager.cu and km_init.cu; this
-// file only orders launches and reads the device state record between
-// batches of passes.
+// km_api.cu -- the C ABI of libkmedoids for the matrix form and its
+// bichromatic variant (declared in include/kmedoids.h): argument checks,
+// workspace carving and the enqueue of BUILD (Alg. 1) and SWAP (Alg. 3
+// FastPAM1, Sec. 3.2 FastPAM2, Alg. 4 FasterPAM, Sec. 3.4 FastCLARANS),
+// plus the initialisations of Sec. 3.3.  All arithmetic of the method runs
+// in the kernels of km_stream.cu, km_points.cu, km_build.cu, km_eager.cu and
+// km_init.cu; this file orders launches.  FastPAM1 without per-pass timing
+// runs its loop as one cached CUDA graph (a conditional WHILE node) and a
+// run reads its results once at the end; with per-pass timing and for
+// FastPAM2 the host reads the device state record between batches of
+// passes.
 #define KM_SRC_ID 10  // names this file in bounds-check reports
 #include <cmath>
 #include <algorithm>

@@ -398,6 +398,20 @@ def test_swap_loop_graph_equals_host_driven_loop(kind):
     assert g2["kernel_launches"] == g["kernel_launches"]
 
 
+def test_swap_loop_graph_cache_evicts_and_rebuilds():
+    """More distinct argument sets than the graph cache keeps (8): every run
+    still equals the oracle, including a repeat of the first after it was
+    evicted."""
+    Dh = int_instance(900, "graph-cache")
+    D = dev(Dh)
+    ks = list(range(3, 14))
+    for k in ks + [ks[0]]:
+        out = km.run(D, k, trace=500)
+        ref = oracle.run(Dh, k, variant="fastpam1")
+        assert out["medoids"].cpu().tolist() == ref["medoids"].tolist(), k
+        assert out["td_i64"] == int(ref["td"]), k
+
+
 @pytest.mark.parametrize("fill", [0x00, 0xA5, 0xFF])
 def test_workspace_contents_do_not_matter(fill):
     """Every call initialises what it reads of the caller's workspace: the
