@@ -772,8 +772,12 @@ def run_bichromatic(args, rank, world, local_rank):
     peak, peak_kind = peaks()
     r0 = results[-1]
     ach = evals * 4 / (mean_ms / 1e3) / 1e9
+    ent = (load_json(os.path.join(ROOT, "profiles", "traffic.json")) or {}).get(
+        "swap_eval@" + args.workload)
+    traffic = ent.get("dram_bytes_per_launch") if ent and \
+        ent.get("source_hash") == source_hash(("km_stream.cu", "km_device.cuh")) else None
     roofline = {"bound": "hbm", "achieved": round(ach, 1), "peak": peak, "unit": "GB/s",
-                "frac": round(ach / peak, 4), "traffic": None,
+                "frac": round(ach / peak, 4), "traffic": traffic,
                 "peak_source": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)"
                 if peak_kind == "measured" else "fallback 6.8 TB/s",
                 "kernel": "k_stream<float,SWAP> over the location rows",
