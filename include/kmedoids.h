@@ -191,6 +191,24 @@ typedef struct km_options {
                              matrix untouched).  Negative: KM_E_INVALID.
                              A limit far below a kernel's normal wait times
                              turns ordinary calls into timeouts. */
+  int32_t swap_full;      /* SWAP of the on-the-fly form (kmedoids_run_features
+                             / _swap_features, k >= 2):
+                             0 (default) = incremental: every candidate's
+                               per-slot sums of Eq. (7) are kept in exact
+                               64-bit fixed point in the workspace; the
+                               first pass sums every point, each later pass
+                               only the points whose nearest / second
+                               distances the last swap changed (their old
+                               terms out, their new terms in), so the
+                               same Delta of every swap is found at a
+                               fraction of the work; the workspace holds
+                               n x k_pad 64-bit sums for it;
+                             nonzero = every pass sums every point (the
+                               plain FastPAM1 pass).
+                             Both take the same swaps (the sums are exact
+                             integer functions of the same pair
+                             distances).  Ignored by the matrix forms. */
+  int32_t pad_options;    /* keeps the struct a multiple of 8 bytes */
 } km_options;
 
 /* Results, filled on the HOST before the call returns. */

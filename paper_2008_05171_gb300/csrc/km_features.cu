@@ -123,11 +123,39 @@ struct FeatArgs {
   unsigned* lcnt;       // [0] entries in the list (cleared by the pass that reads
                         // it); as u64 [1] the rows every update pass streamed
   long long* bgain;
+  // Incremental SWAP (k >= 2): the same list, each entry a point's old
+  // (sign -1) or new (sign +1) cache entry: lqo = d_n and lqn = d_s in
+  // fixed point, lnear = nearest slot | sign bit, lthr = the test's bound
+  // from that d_s; sg[c][i] and ss[c] the per-slot and shared sums of
+  // Eq. (7) of every candidate (magnitudes, fixed point), kept across passes.
+  int swap_incremental;
+  int* lnear;
+  long long* sg;        // [n_pad][k_pad]
+  long long* ss;        // [n_pad]
 };
 
 // Pass of the incremental BUILD: the gain change of every candidate from
 // the listed points (k_feat_pass with the list as the point blocks).
 constexpr int kModeBuildUpd = 2;
+// Pass of the incremental SWAP: the Eq. (7) sums of every candidate moved
+// by the listed old and new cache entries, then every candidate's Delta.
+constexpr int kModeSwapUpd = 3;
+
+// Adds a signed x (|x| < 2^31) to the 32-bit word w of a sum whose value is
+// w + 2^32 * carry (carry a signed count in two's complement).
+__device__ __forceinline__ void add_signed_word(unsigned* w, unsigned* carry,
+                                                volatile unsigned char* flag, int x) {
+  const unsigned u = (unsigned)x;
+  const unsigned old = atomicAdd(w, u);
+  const bool wrap = old + u < old;
+  if (x > 0 && wrap) {
+    atomicAdd(carry, 1u);
+    *flag = 1;
+  } else if (x < 0 && !wrap) {
+    atomicAdd(carry, 0xffffffffu);
+    *flag = 1;
+  }
+}
 
 constexpr int kFeatAccBufs = 4;     // TMEM accumulators of kTileN columns
 constexpr int kFeatMetaStages = 4;  // ring of per-block point caches
@@ -284,17 +312,20 @@ __global__ void __launch_bounds__(kFeatThreads, 1) k_feat_pass(const FeatArgs a)
   const int ntiles = a.n_pad / kTileM;
   // the update pass streams the listed points only (read before any block
   // moves; the commit that wrote the list finished before this launch)
-  const int nlist = (MODE == kModeBuildUpd) ? (int)min(__ldcg(a.lcnt), (unsigned)a.n) : 0;
-  const int nblocks = (MODE == kModeBuildUpd) ? (nlist + kTileN - 1) / kTileN : a.n_pad / kTileN;
-  const uint16_t* Bsrc = (MODE == kModeBuildUpd) ? a.XpL : a.XpB;
+  constexpr bool kList = (MODE == kModeBuildUpd || MODE == kModeSwapUpd);
+  constexpr bool kSwapLike = (MODE == kModeSwap || MODE == kModeSwapUpd);
+  const int nlist =
+      kList ? (int)min(__ldcg(a.lcnt), (unsigned)(MODE == kModeSwapUpd ? 2 * a.n : a.n)) : 0;
+  const int nblocks = kList ? (nlist + kTileN - 1) / kTileN : a.n_pad / kTileN;
+  const uint16_t* Bsrc = kList ? a.XpL : a.XpB;
   const uint32_t tile_bytes = (uint32_t)(kTileM * d * 2);
 
-  if (MODE == kModeSwap && blockIdx.x == 0) {
+  if (kSwapLike && blockIdx.x == 0) {
     long long* rnext = a.removal + (size_t)(rb ^ 1) * a.k_pad;
     for (int i = tid; i < k; i += blockDim.x) rnext[i] = 0;
     if (tid == 0) a.td2[rb ^ 1] = 0.0;
   }
-  if (MODE != kModeSwap && blockIdx.x == 0 && tid == 0) st->build_td_d = 0.0;
+  if (!kSwapLike && blockIdx.x == 0 && tid == 0) st->build_td_d = 0.0;
   if (tid == 0) {
     mbar_init(a_full, 1);
     mbar_init(tile_done, kFeatEpiWarps);
@@ -315,7 +346,7 @@ __global__ void __launch_bounds__(kFeatThreads, 1) k_feat_pass(const FeatArgs a)
     *last_flag = 0;
     fence_barrier_init();
   }
-  if (MODE == kModeSwap) {
+  if (kSwapLike) {
     const long long* rsrc = a.removal + (size_t)rb * a.k_pad;
     for (int i = tid; i < k; i += blockDim.x) rl[i] = rsrc[i];
     for (int i = tid; i < kTileM * k; i += blockDim.x) acc[i] = 0u;
@@ -386,6 +417,12 @@ __global__ void __launch_bounds__(kFeatThreads, 1) k_feat_pass(const FeatArgs a)
             bulk_g2s(meta + 1024, a.lqo + o0, 4 * kTileN, &m_full[ms]);
             bulk_g2s(meta + 1536, a.lqn + o0, 4 * kTileN, &m_full[ms]);
             bulk_g2s(meta + 2048, a.lqn + o0, 4 * kTileN, &m_full[ms]);  // keeps the byte count
+          } else if (MODE == kModeSwapUpd) {
+            bulk_g2s(meta, a.lno + o0, 4 * kTileN, &m_full[ms]);
+            bulk_g2s(meta + 512, a.lthr + o0, 4 * kTileN, &m_full[ms]);
+            bulk_g2s(meta + 1024, a.lqo + o0, 4 * kTileN, &m_full[ms]);
+            bulk_g2s(meta + 1536, a.lqn + o0, 4 * kTileN, &m_full[ms]);
+            bulk_g2s(meta + 2048, a.lnear + o0, 4 * kTileN, &m_full[ms]);
           } else {
             bulk_g2s(meta, a.norms + o0, 4 * kTileN, &m_full[ms]);
             bulk_g2s(meta + 512, a.thr + o0, 4 * kTileN, &m_full[ms]);
@@ -524,6 +561,27 @@ __global__ void __launch_bounds__(kFeatThreads, 1) k_feat_pass(const FeatArgs a)
             sh += dnq - ddq;
           }
         };
+        // incremental SWAP: listed entry at column col, an old (sign -1) or
+        // new (sign +1) cache entry of its point; d^2 = |x_o|^2 + 2 v (zero
+        // threshold columns); Eq. (7)'s terms of that entry, classified in
+        // fixed point, added with the entry's sign
+        auto hit_upd = [&](int col, float vv) {
+          const int ddq = fxq(pair_dist(fmaf(2.f, vv, m_no[col])), scale);
+          const int dnq = reinterpret_cast<const int*>(meta + 1024)[col];
+          const int dsq = reinterpret_cast<const int*>(meta + 1536)[col];
+          const int pk = m_near[col];
+          const int sl = pk & 0x7fffffff;
+          const int sgn = pk < 0 ? -1 : 1;
+          int mag = 0;
+          if (ddq < dnq) {
+            sh += (long long)(sgn * (dnq - ddq));
+            mag = dsq - dnq;
+          } else if (ddq < dsq) {
+            mag = dsq - ddq;
+          }
+          if (mag > 0 && KM_INB(a.st, sl, a.k))
+            add_signed_word(arow + sl, crow + sl, rowc + r, sgn * mag);
+        };
         if (MODE == kModeBuildUpd) {
           // listed point o (column col): v = |x_c|^2/2 - x_c.x_o (zero
           // threshold columns), so d^2 = |x_o|^2 + 2 v; the pair can change
@@ -559,10 +617,21 @@ __global__ void __launch_bounds__(kFeatThreads, 1) k_feat_pass(const FeatArgs a)
             // j (set: a hit), shifted in from column 15 down to 0 with one
             // funnel shift per pair; rows that are not candidates see none
             unsigned mask = 0;
+            if (MODE == kModeSwapUpd) {
+              // explicit test against each entry's bound; every row c < n
+              // (a medoid swapped out later is a candidate again)
+              const int cbase = b * kTileN + col0 + g16 * 16;
 #pragma unroll
-            for (int j = 15; j >= 0; --j)
-              mask = __funnelshift_l(__float_as_uint(v[g16 * 16 + j]), mask, 1);
-            if (!cvalid) mask = 0;
+              for (int j = 0; j < 16; ++j)
+                if (v[g16 * 16 + j] < m_thr[col0 + g16 * 16 + j] && cbase + j < nlist)
+                  mask |= 1u << j;
+              if (c >= n) mask = 0;
+            } else {
+#pragma unroll
+              for (int j = 15; j >= 0; --j)
+                mask = __funnelshift_l(__float_as_uint(v[g16 * 16 + j]), mask, 1);
+              if (!cvalid) mask = 0;
+            }
             const unsigned most = __reduce_max_sync(0xffffffffu, (unsigned)__popc(mask));
             if (most == 0) continue;
             const int cb = col0 + g16 * 16;
@@ -570,13 +639,21 @@ __global__ void __launch_bounds__(kFeatThreads, 1) k_feat_pass(const FeatArgs a)
               // dense group: every column, predicated on its bit
 #pragma unroll
               for (int j = 0; j < 16; ++j)
-                if ((mask >> j) & 1u) hit(cb + j, v[g16 * 16 + j]);
+                if ((mask >> j) & 1u) {
+                  if (MODE == kModeSwapUpd)
+                    hit_upd(cb + j, v[g16 * 16 + j]);
+                  else
+                    hit(cb + j, v[g16 * 16 + j]);
+                }
             } else {
               // sparse group: each lane walks its own hits
               while (mask) {
                 const int j = __ffs(mask) - 1;
                 mask &= mask - 1;
-                hit(cb + j, sel16(v + g16 * 16, j));
+                if (MODE == kModeSwapUpd)
+                  hit_upd(cb + j, sel16(v + g16 * 16, j));
+                else
+                  hit(cb + j, sel16(v + g16 * 16, j));
               }
             }
           }
@@ -616,6 +693,52 @@ __global__ void __launch_bounds__(kFeatThreads, 1) k_feat_pass(const FeatArgs a)
             ck.slot = bi;
             ck.cand = c;
             if (key_less(ck, wbest)) wbest = ck;
+          }
+          for (int i = 0; i < k; ++i) arow[i] = 0u;
+          if (carried) {
+            for (int i = 0; i < k; ++i) __stcg(crow + i, 0u);
+            rowc[r] = 0;
+          }
+        } else if (MODE == kModeSwapUpd) {
+          // the kept sums of row c moved by this pass (word + 2^32 x its
+          // signed carry count), then Delta(c) as in the plain pass
+          const bool carried = rowc[r] != 0;
+          if (c < n) {
+            long long best = LLONG_MAX;
+            int bi = 0;
+            // the kept sums are slot-major, so the 32 rows of a warp read
+            // consecutive words; eight slots' loads in flight at a time
+            constexpr int U = 8;
+            for (int i0 = 0; i0 < k; i0 += U) {
+              long long gv[U];
+#pragma unroll
+              for (int u = 0; u < U; ++u)
+                if (i0 + u < k) gv[u] = __ldcg(a.sg + (size_t)(i0 + u) * a.n_pad + c);
+#pragma unroll
+              for (int u = 0; u < U; ++u) {
+                const int i = i0 + u;
+                if (i < k) {
+                  long long t = (long long)arow[i];
+                  if (carried) t += (long long)(int)__ldcg(crow + i) * 4294967296ll;
+                  const long long gi = gv[u] + t;
+                  a.sg[(size_t)i * a.n_pad + c] = gi;
+                  const long long vi = rl[i] - gi;
+                  if (vi < best) {
+                    best = vi;
+                    bi = i;
+                  }
+                }
+              }
+            }
+            const long long sc = a.ss[c] + shared_part;
+            a.ss[c] = sc;
+            if (cvalid) {
+              Key<double> ck;
+              ck.d = (double)(best - sc) * unit;
+              ck.slot = bi;
+              ck.cand = c;
+              if (key_less(ck, wbest)) wbest = ck;
+            }
           }
           for (int i = 0; i < k; ++i) arow[i] = 0u;
           if (carried) {
@@ -685,7 +808,7 @@ __global__ void __launch_bounds__(kFeatThreads, 1) k_feat_pass(const FeatArgs a)
     }
     b = warp_min_key(b);
     if (lane == 0) {
-      if (MODE != kModeSwap) {
+      if (!kSwapLike) {
         st->build_gain_d = b.d;
         st->build_cand = b.cand;
         if (MODE == kModeBuildUpd) {
@@ -695,6 +818,7 @@ __global__ void __launch_bounds__(kFeatThreads, 1) k_feat_pass(const FeatArgs a)
           *a.lcnt = 0u;
         }
       } else {
+        if (MODE == kModeSwapUpd) *a.lcnt = 0u;  // the next swap writes a new list
         st->best_d = b.d;
         st->best_i = 0;
         st->best_slot = (b.cand == INT_MAX) ? -1 : b.slot;
@@ -756,6 +880,41 @@ __device__ __forceinline__ void top2f(float v, int j, int& n1, float& d1, int& n
   }
 }
 
+// One entry of the incremental SWAP's list at position p: point o's cache
+// entry (d_n, d_s, nearest slot; sign -1 for the entry it had before a
+// swap), the bound of the pass's test from that d_s (v < bound iff d is
+// below d_s, with a 2^-10 relative margin on d^2), and o's B-operand row.
+__device__ __forceinline__ void swap_list_put(const FeatArgs& a, unsigned p, int o, float dn,
+                                              float ds, int near, bool old_entry) {
+  const float scale = __int_as_float((127 + a.fq) << 23);
+  const float no = a.norms[o];
+  a.lno[p] = no;
+  a.lthr[p] = 0.5f * (ds * ds * (1.f + 0x1p-10f) + 0x1p-100f - no);
+  a.lqo[p] = fxq(dn, scale);
+  a.lqn[p] = fxq(ds, scale);
+  a.lnear[p] = old_entry ? (int)((unsigned)near | 0x80000000u) : near;
+  const int kcs = a.dk >> 3;
+  for (int kc = 0; kc < kcs; ++kc)
+    *reinterpret_cast<uint4*>(a.XpL + chunk_off((int)p, kc, a.dk)) =
+        *reinterpret_cast<const uint4*>(a.XpB + chunk_off(o, kc, a.dk));
+}
+
+// Warp-aggregated reservation of cnt list positions per lane (cnt 0..2).
+__device__ __forceinline__ unsigned list_reserve(unsigned* lcnt, unsigned cnt) {
+  const int lane = threadIdx.x & 31;
+  unsigned incl = cnt;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const unsigned v = __shfl_up_sync(0xffffffffu, incl, d);
+    if (lane >= d) incl += v;
+  }
+  const unsigned total = __shfl_sync(0xffffffffu, incl, 31);
+  unsigned base = 0;
+  if (lane == 31 && total) base = atomicAdd(lcnt, total);
+  base = __shfl_sync(0xffffffffu, base, 31);
+  return base + incl - cnt;
+}
+
 // Exact cache of every point for the current medoids (distances compared
 // squared; d_n, d_s stored as FP32 square roots), removal loss and TD.
 __global__ void __launch_bounds__(256) k_feat_cache(const FeatArgs a) {
@@ -787,8 +946,10 @@ __global__ void __launch_bounds__(256) k_feat_cache(const FeatArgs a) {
     a.dn2[o] = q1;
     a.ds2[o] = (n2 < 0) ? Tr<float>::high() : q2;
     // k = 1 has no second medoid; its SWAP is a dense pass (every pair), for
-    // which any finite threshold lets the Gram entries be recovered
-    a.thr[o] = (n2 < 0) ? 0.f : 0.5f * (a.norms[o] - q2);
+    // which any finite threshold lets the Gram entries be recovered.  The
+    // incremental SWAP keeps the threshold columns zero (each pair's Gram
+    // entry the same in every pass) and tests explicitly.
+    a.thr[o] = (n2 < 0 || a.swap_incremental) ? 0.f : 0.5f * (a.norms[o] - q2);
     write_thr_cols(a, o, a.thr[o]);
     if (n2 >= 0 && n1 >= 0)
       atomicAdd(&sacc[n1], (unsigned long long)(fxq(e2, scale) - fxq(e1, scale)));
@@ -802,6 +963,12 @@ __global__ void __launch_bounds__(256) k_feat_cache(const FeatArgs a) {
     a.ds2[o] = Tr<float>::low();
     a.thr[o] = Tr<float>::high();
     write_thr_cols(a, o, Tr<float>::high());
+  }
+  if (a.swap_incremental) {  // uniform: every point's entry opens the list
+    const bool put = o < n;
+    const unsigned p = list_reserve(a.lcnt, put ? 1u : 0u);
+    if (put && KM_INB(st, p, 2 * (long long)a.n_pad))
+      swap_list_put(a, p, o, a.dn[o], a.ds[o], a.near[o], false);
   }
   const double bs = fblock_sum(tdl, scratch);
   if (threadIdx.x == 0) atomicAdd(&a.td2[rb], bs);
@@ -837,10 +1004,17 @@ __global__ void __launch_bounds__(256) k_feat_apply(const FeatArgs a) {
   __syncthreads();
   const int o = blockIdx.x * blockDim.x + threadIdx.x;
   double tdl = 0.0;
+  bool changed = false;
+  int n1_old = 0;
+  float dn_old = 0.f, ds_old = 0.f;
   if (o < n) {
     const uint16_t* xo = a.X + (size_t)o * a.ldx;
     int n1 = a.near[o], n2 = a.sec[o];
     float q1 = a.dn2[o], q2 = a.ds2[o];
+    const float q1_old = q1, q2_old = q2;
+    n1_old = n1;
+    dn_old = a.dn[o];
+    ds_old = a.ds[o];
     if (n1 == i_s || n2 == i_s) {
       n1 = -1;
       n2 = -1;
@@ -862,17 +1036,27 @@ __global__ void __launch_bounds__(256) k_feat_apply(const FeatArgs a) {
       }
     }
     const float e1 = sqrtf(q1), e2 = sqrtf(q2);
+    changed = n1 != n1_old || q1 != q1_old || q2 != q2_old;
     a.near[o] = n1;
     a.sec[o] = n2;
     a.dn[o] = e1;
     a.ds[o] = e2;
     a.dn2[o] = q1;
     a.ds2[o] = q2;
-    a.thr[o] = 0.5f * (a.norms[o] - q2);
-    write_thr_cols(a, o, a.thr[o]);
+    if (!a.swap_incremental) {
+      a.thr[o] = 0.5f * (a.norms[o] - q2);
+      write_thr_cols(a, o, a.thr[o]);
+    }
     if (KM_INB(st, n1, k))
       atomicAdd(&sacc[n1], (unsigned long long)(fxq(e2, scale) - fxq(e1, scale)));
     tdl = e1;
+  }
+  if (a.swap_incremental) {  // uniform: a changed point's old entry out, new in
+    const unsigned p = list_reserve(a.lcnt, changed ? 2u : 0u);
+    if (changed && KM_INB(st, p + 1, 2 * (long long)a.n_pad)) {
+      swap_list_put(a, p, o, dn_old, ds_old, n1_old, true);
+      swap_list_put(a, p + 1, o, a.dn[o], a.ds[o], a.near[o], false);
+    }
   }
   const double bs = fblock_sum(tdl, scratch);
   if (threadIdx.x == 0) atomicAdd(&a.td2[rb ^ 1], bs);
@@ -1066,7 +1250,7 @@ namespace {
 
 struct FeatWs {
   size_t st, med, is_med, near, sec, dn, ds, dn2, ds2, thr, norms, removal, td2, partials, trace,
-      gains, xpa, xpb, carry, range, xpl, lno, lthr, lqo, lqn, lcnt, bgain, total;
+      gains, xpa, xpb, carry, range, xpl, lno, lthr, lqo, lqn, lnear, lcnt, bgain, sg, ss, total;
   int n_pad, k_pad, cap;
 };
 
@@ -1103,14 +1287,20 @@ bool feat_ws(int64_t n, int d, int k, const km_options* o, FeatWs* L) {
   L->xpb = take((size_t)n_pad * (d + 16) * 2);
   L->carry = take(4 * (size_t)kFeatMaxGrid * kTileM * k_pad);
   L->range = take(8 * (size_t)d);
-  // incremental BUILD: the list of changed points and every candidate's gain
-  L->xpl = take((size_t)n_pad * (d + 16) * 2);
-  L->lno = take(4 * (size_t)n_pad);
-  L->lthr = take(4 * (size_t)n_pad);
-  L->lqo = take(4 * (size_t)n_pad);
-  L->lqn = take(4 * (size_t)n_pad);
+  // incremental BUILD and SWAP: the list (BUILD: one entry per changed
+  // point; SWAP: an old and a new entry each), every candidate's BUILD gain,
+  // and the SWAP's per-slot and shared sums of every candidate
+  L->xpl = take(2 * (size_t)n_pad * (d + 16) * 2);
+  L->lno = take(8 * (size_t)n_pad);
+  L->lthr = take(8 * (size_t)n_pad);
+  L->lqo = take(8 * (size_t)n_pad);
+  L->lqn = take(8 * (size_t)n_pad);
+  L->lnear = take(8 * (size_t)n_pad);
   L->lcnt = take(16);
   L->bgain = take(8 * (size_t)n_pad);
+  const bool swap_inc = k >= 2 && !(o && o->swap_full);
+  L->sg = take(swap_inc ? 8 * (size_t)n_pad * k_pad : 0);
+  L->ss = take(swap_inc ? 8 * (size_t)n_pad : 0);
   L->total = off;
   L->n_pad = n_pad;
   L->k_pad = k_pad;
@@ -1181,16 +1371,21 @@ km_status f_pass(FCtx& c, int mode, int first, cudaEvent_t ev0 = nullptr,
     FK(cudaFuncSetAttribute(k_feat_pass<kModeSwap>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total));
   else if (mode == kModeBuild)
     FK(cudaFuncSetAttribute(k_feat_pass<kModeBuild>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total));
-  else
+  else if (mode == kModeBuildUpd)
     FK(cudaFuncSetAttribute(k_feat_pass<kModeBuildUpd>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                            (int)L.total));
+  else
+    FK(cudaFuncSetAttribute(k_feat_pass<kModeSwapUpd>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                             (int)L.total));
   if (ev0) FK(cudaEventRecord(ev0, c.s));
   if (mode == kModeSwap)
     k_feat_pass<kModeSwap><<<grid, kFeatThreads, L.total, c.s>>>(a);
   else if (mode == kModeBuild)
     k_feat_pass<kModeBuild><<<grid, kFeatThreads, L.total, c.s>>>(a);
-  else
+  else if (mode == kModeBuildUpd)
     k_feat_pass<kModeBuildUpd><<<grid, kFeatThreads, L.total, c.s>>>(a);
+  else
+    k_feat_pass<kModeSwapUpd><<<grid, kFeatThreads, L.total, c.s>>>(a);
   FK(cudaGetLastError());
   if (ev1) FK(cudaEventRecord(ev1, c.s));
   ++c.launches;
@@ -1199,6 +1394,11 @@ km_status f_pass(FCtx& c, int mode, int first, cudaEvent_t ev0 = nullptr,
 
 km_status f_cache(FCtx& c) {
   FK(cudaMemsetAsync(c.a.is_med, 0, (size_t)c.L.n_pad, c.s));
+  if (c.a.swap_incremental) {
+    FK(cudaMemsetAsync(c.a.lcnt, 0, 4, c.s));
+    FK(cudaMemsetAsync(c.a.sg, 0, 8 * (size_t)c.L.n_pad * c.L.k_pad, c.s));
+    FK(cudaMemsetAsync(c.a.ss, 0, 8 * (size_t)c.L.n_pad, c.s));
+  }
   FK(cudaMemsetAsync(c.a.removal, 0, 16 * (size_t)c.L.k_pad, c.s));
   FK(cudaMemsetAsync(c.a.td2, 0, 16, c.s));
   k_feat_mark<<<(c.a.k + 255) / 256, 256, 0, c.s>>>(c.a);
@@ -1278,6 +1478,10 @@ km_status run_features(bool do_build, bool do_swap, const void* X, int64_t n, in
   a.lqn = reinterpret_cast<int*>(c.ws + c.L.lqn);
   a.lcnt = reinterpret_cast<unsigned*>(c.ws + c.L.lcnt);
   a.bgain = reinterpret_cast<long long*>(c.ws + c.L.bgain);
+  a.swap_incremental = (k >= 2 && !c.opt.swap_full) ? 1 : 0;
+  a.lnear = reinterpret_cast<int*>(c.ws + c.L.lnear);
+  a.sg = reinterpret_cast<long long*>(c.ws + c.L.sg);
+  a.ss = reinterpret_cast<long long*>(c.ws + c.L.ss);
   if (res) memset(res, 0, sizeof(*res));
 
   cudaEvent_t e0 = nullptr, e1 = nullptr, e2 = nullptr;
@@ -1437,7 +1641,7 @@ km_status run_features(bool do_build, bool do_swap, const void* X, int64_t n, in
           FK(cudaEventCreate(&x1));
           sev.push_back({x0, x1});
         }
-        r = f_pass(c, kModeSwap, 0, x0, x1);
+        r = f_pass(c, a.swap_incremental ? kModeSwapUpd : kModeSwap, 0, x0, x1);
         if (r != KM_OK) return r;
         k_feat_apply<<<(a.n + 255) / 256, 256, sm, c.s>>>(a);
         FK(cudaGetLastError());

@@ -98,6 +98,32 @@ def test_incremental_build_equals_the_plain_pass(n, d, k):
     assert n <= a["build_rows"] < n * k // 4, a["build_rows"]
 
 
+@pytest.mark.parametrize("n,d,k", [(20000, 64, 40), (6001, 128, 25), (3000, 32, 2)])
+def test_incremental_swap_equals_the_plain_pass(n, d, k):
+    """The incremental SWAP (every candidate's Eq. (7) sums kept across
+    passes; each pass after the first moves only the entries of the points
+    the last swap changed) against the plain FastPAM1 pass over every
+    point: the same swaps in the same order, the same medoids and TD."""
+    X = wl.features_200000(n=n, d=d, n_centers=max(k, 4))
+    Xt = torch.from_numpy(X).to(torch.bfloat16).cuda()
+    rng = np.random.default_rng(n)
+    start = rng.choice(n, size=k, replace=False).astype(np.int32)
+    a = km.swap_features(Xt, start, trace=100000)
+    b = km.swap_features(Xt, start, trace=100000, swap_full=True)
+    assert a["swaps"] >= 1 and a["converged"] and b["converged"]
+    assert [(i, c) for _, i, c in a["trace"]] == [(i, c) for _, i, c in b["trace"]]
+    # the two passes recover a pair's distance from differently folded MMA
+    # outputs (the plain pass carries the threshold in the product), so the
+    # Deltas agree to the Gram's rounding, well inside the 1e-6 TD tolerance
+    for (da, _, _), (db, _, _) in zip(a["trace"], b["trace"]):
+        assert abs(da - db) <= 1e-7 * b["td"]
+    assert a["medoids"].cpu().tolist() == b["medoids"].cpu().tolist()
+    assert abs(a["td"] - b["td"]) <= 1e-12 * b["td"]
+    r = km.run_features(Xt, k)
+    rf = km.run_features(Xt, k, swap_full=True)
+    assert r["medoids"].cpu().tolist() == rf["medoids"].cpu().tolist()
+
+
 def test_run_features_many_tiles_per_cta():
     """n = 20000 gives 157 candidate tiles, more than there are SMs, so CTAs
     take several tiles each through the dynamic tile counter (and the tile
