@@ -252,7 +252,15 @@ def run_features(args, rank, world, local_rank):
     ck = clocks.stop()
     total_ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in ev), world, dev)
     sw = swap_pass_figures(n, k, None, results)
-    pass_ms = max_over_ranks(sw["median_ms"], world, dev)
+    # the SWAP is incremental: its first pass sums every point (the full
+    # FastPAM1 evaluation of every pair), each later one only the entries of
+    # the points the last swap changed; value is the full pass's throughput
+    first_ms = float(np.median([r["eval_ms_first"] for r in results]))
+    sw["first_pass_ms"] = first_ms
+    sw["later_passes_median_ms"] = sw.pop("median_ms")
+    sw["kind"] = ("incremental: pass 1 over every point, later passes over the points the "
+                  "last swap changed (old entry out, new entry in)")
+    pass_ms = max_over_ranks(first_ms, world, dev)
     value = world * (n - k) * n / (pass_ms / 1e3)
     r0 = results[-1]
     peak, pk = tensor_peak()
@@ -262,7 +270,7 @@ def run_features(args, rank, world, local_rank):
     b_rows = int(r0.get("build_rows") or n * k)
     b_flops = 2.0 * n * d * b_rows / max(1, r0["build_launches"])
     b_ms = r0["build_eval_ms"] / max(1, r0["build_launches"])
-    s_ms = r0["eval_ms"] / max(1, r0["eval_launches"])
+    s_ms = first_ms
 
     def roof(ms, name, share, fl):
         ach = fl / (ms / 1e3) / 1e12
@@ -274,7 +282,7 @@ def run_features(args, rank, world, local_rank):
     rb = roof(b_ms, "k_feat_pass<BUILD> (step 0 dense, then incremental updates)",
               r0["build_eval_ms"], b_flops)
     rb["build_rows_streamed"] = b_rows
-    rs = roof(s_ms, "k_feat_pass<SWAP>", r0["eval_ms"], flops)
+    rs = roof(s_ms, "k_feat_pass<SWAP> (the first pass: every point)", r0["eval_ms"], flops)
     dom, other = (rb, rs) if r0["build_eval_ms"] >= r0["eval_ms"] else (rs, rb)
     e2e = None
     if not args.no_e2e:
@@ -303,8 +311,9 @@ def run_features(args, rank, world, local_rank):
         "scaling": "weak", "vs_baseline": None, "dtype": "bf16 Gram / f32 (FP64 TD)",
         "data": "synthetic",
         "config": features_config(args.workload, spec, world),
-        "value_definition": "(n-k)*n point-evals per FastPAM1 SWAP pass / median pass time; "
-                            "ms_per_step = the whole BUILD + SWAP run",
+        "value_definition": "(n-k)*n point-evals of the first FastPAM1 SWAP pass (every point) "
+                            "/ its median time over the steps; ms_per_step = the whole BUILD + "
+                            "SWAP run (later passes incremental)",
         "swap_pass": sw,
         "full_run_ms": total_ms / args.steps, "swap_iterations": r0["iterations"],
         "swaps": r0["swaps"], "swap_iter_ms": s_ms, "build_step_ms": b_ms, "td": r0["td"],

@@ -250,6 +250,10 @@ typedef struct km_result {
                               evaluation kernels streamed */
   double eval_ms_median;   /* profile != 0: median over the SWAP evaluation
                               launches of their device time */
+  double eval_ms_first;    /* profile != 0: device time of the first SWAP
+                              evaluation launch (the on-the-fly form's
+                              incremental SWAP: the pass over every point;
+                              the later ones move the changed points only) */
 } km_result;
 
 /* Parameters of a matrix-form geometry table entry (1..16, as reported in

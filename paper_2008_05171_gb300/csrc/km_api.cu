@@ -905,6 +905,7 @@ void eval_times(const Timer& tm, const std::vector<std::pair<int, int>>& ev_swap
   res->eval_ms = sum;
   res->eval_launches = (int)per.size();
   if (!per.empty()) {
+    res->eval_ms_first = per[0];
     std::sort(per.begin(), per.end());
     const size_t m = per.size() / 2;
     res->eval_ms_median = (per.size() % 2) ? per[m] : 0.5 * (per[m - 1] + per[m]);

@@ -618,13 +618,18 @@ __global__ void __launch_bounds__(kFeatThreads, 1) k_feat_pass(const FeatArgs a)
             // funnel shift per pair; rows that are not candidates see none
             unsigned mask = 0;
             if (MODE == kModeSwapUpd) {
-              // explicit test against each entry's bound; every row c < n
-              // (a medoid swapped out later is a candidate again)
+              // explicit test against each entry's bound: the sign of
+              // v - bound (negative exactly when v < bound), funnel-shifted
+              // as in the plain pass; entries past the list's end and rows
+              // c >= n see none (every row c < n counts: a medoid swapped
+              // out later is a candidate again)
               const int cbase = b * kTileN + col0 + g16 * 16;
 #pragma unroll
-              for (int j = 0; j < 16; ++j)
-                if (v[g16 * 16 + j] < m_thr[col0 + g16 * 16 + j] && cbase + j < nlist)
-                  mask |= 1u << j;
+              for (int j = 15; j >= 0; --j)
+                mask = __funnelshift_l(
+                    __float_as_uint(v[g16 * 16 + j] - m_thr[col0 + g16 * 16 + j]), mask, 1);
+              const int left = nlist - cbase;
+              if (left < 16) mask &= (left > 0) ? ((1u << left) - 1u) : 0u;
               if (c >= n) mask = 0;
             } else {
 #pragma unroll
@@ -1704,6 +1709,7 @@ km_status run_features(bool do_build, bool do_swap, const void* X, int64_t n, in
       res->eval_ms = ss;
       res->eval_launches = cnt;
       if (!per.empty()) {
+        res->eval_ms_first = per[0];
         std::sort(per.begin(), per.end());
         const size_t m = per.size() / 2;
         res->eval_ms_median = (per.size() % 2) ? per[m] : 0.5 * (per[m - 1] + per[m]);

@@ -76,7 +76,8 @@ class km_result(ctypes.Structure):
                 ("kernel_launches", ctypes.c_int64),
                 ("best_sample", ctypes.c_int32), ("swap_geometry", ctypes.c_int16),
                 ("build_geometry", ctypes.c_int16), ("evaluated", ctypes.c_int64),
-                ("build_rows", ctypes.c_int64), ("eval_ms_median", ctypes.c_double)]
+                ("build_rows", ctypes.c_int64), ("eval_ms_median", ctypes.c_double),
+                ("eval_ms_first", ctypes.c_double)]
 
 
 _LOCK = threading.Lock()
