@@ -279,6 +279,13 @@ def run_features(args, rank, world, local_rank):
                 "kernel": name, "algorithmic_flops_per_launch": fl,
                 "avg_launch_ms": round(ms, 4), "share_ms": share, "traffic": None}
 
+    # the plain FastPAM1 pass over every point (swap_full) beside it, untimed
+    rp = km.run_features(X, k, profile=True, swap_full=True)
+    torch.cuda.synchronize()
+    plain = {"ms_per_step": rp["build_ms"] + rp["swap_ms"], "swap_pass_median_ms": rp["eval_ms_median"],
+             "swap_passes": rp["eval_launches"],
+             "same_medoids": rp["medoids"].cpu().tolist() == r0["medoids"].cpu().tolist(),
+             "frac_of_sustained_bf16": round(flops / (rp["eval_ms_median"] / 1e3) / 1e12 / peak, 4)}
     rb = roof(b_ms, "k_feat_pass<BUILD> (step 0 dense, then incremental updates)",
               r0["build_eval_ms"], b_flops)
     rb["build_rows_streamed"] = b_rows
@@ -315,6 +322,7 @@ def run_features(args, rank, world, local_rank):
                             "/ its median time over the steps; ms_per_step = the whole BUILD + "
                             "SWAP run (later passes incremental)",
         "swap_pass": sw,
+        "plain_swap_run": plain,
         "full_run_ms": total_ms / args.steps, "swap_iterations": r0["iterations"],
         "swaps": r0["swaps"], "swap_iter_ms": s_ms, "build_step_ms": b_ms, "td": r0["td"],
         "kernel_ms_per_step": {"build_eval": r0["build_eval_ms"], "swap_eval": r0["eval_ms"],
