@@ -392,10 +392,17 @@ km_status kmedoids_gram_bf16(const void *X, int64_t n, int32_t d, int64_t ldx,
  * aligned, d a multiple of 16 up to 240); d(o,c) is the Euclidean distance.
  * Every BUILD step and SWAP pass recomputes the distances it needs from a
  * tensor-core Gram product (tcgen05, BF16 inputs, FP32 accumulation):
- * d^2 = |x_o|^2 + |x_c|^2 - 2 x_o.x_c.  The pair test against each point's
- * threshold is folded into the product: the operands carry 16 more
- * columns holding |x_c|^2 / 2 and the point's threshold as exact sums of
- * three bf16 pieces, so the sign of one MMA output decides a pair.  The per-point cache (nearest, d_n,
+ * d^2 = |x_o|^2 + |x_c|^2 - 2 x_o.x_c, the operands carrying 16 more
+ * columns for |x_c|^2 / 2 and a per-point threshold (exact sums of three
+ * bf16 pieces).  By default (build_full = swap_full = 0) both phases are
+ * incremental: BUILD's step 0 and SWAP's first pass take every point, and
+ * each later step or pass only the points the last commit or swap changed,
+ * the candidates' gains and Eq. (7) sums being kept in the workspace; the
+ * threshold columns are then zero, so a pair's Gram entry is the same in
+ * every pass, and the kept sums equal a full recomputation's.  With
+ * build_full / swap_full every step or pass takes every point and the
+ * threshold test is folded into the product (the sign of one MMA output
+ * decides a pair).  The per-point cache (nearest, d_n,
  * d_s) and the TD are computed exactly from FP32 differences sum (x - y)^2,
  * so the Gram form's rounding (relative error ~1e-5 on d^2 for well
  * separated points) only affects which candidates see a hit and the Delta
@@ -405,7 +412,8 @@ km_status kmedoids_gram_bf16(const void *X, int64_t n, int32_t d, int64_t ldx,
  * units), so they do not depend on the order of the GPU's additions.
  * FastPAM1 only; k <= 224.
  * Workspace (DEVICE, 256-byte aligned): kmedoids_features_workspace_size()
- * bytes, which includes the features rearranged for the tensor cores. */
+ * bytes, which includes the features rearranged for the tensor cores and,
+ * unless opts->swap_full, the kept SWAP sums (8 n k_pad bytes). */
 size_t kmedoids_features_workspace_size(int64_t n, int32_t d, int32_t k,
                                         const km_options *opts);
 
