@@ -126,11 +126,11 @@ struct FeatArgs {
   // Incremental SWAP (k >= 2): the same list, each entry a point's old
   // (sign -1) or new (sign +1) cache entry: lqo = d_n and lqn = d_s in
   // fixed point, lnear = nearest slot | sign bit, lthr = the test's bound
-  // from that d_s; sg[c][i] and ss[c] the per-slot and shared sums of
+  // from that d_s; sg[i][c] and ss[c] the per-slot and shared sums of
   // Eq. (7) of every candidate (magnitudes, fixed point), kept across passes.
   int swap_incremental;
   int* lnear;
-  long long* sg;        // [n_pad][k_pad]
+  long long* sg;        // [k_pad][n_pad], slot-major
   long long* ss;        // [n_pad]
 };
 
