@@ -208,7 +208,20 @@ typedef struct km_options {
                              Both take the same swaps (the sums are exact
                              integer functions of the same pair
                              distances).  Ignored by the matrix forms. */
-  int32_t pad_options;    /* keeps the struct a multiple of 8 bytes */
+  int32_t gram_full;      /* dense passes of the on-the-fly form (its first
+                             BUILD step, and the swap of k = 1), which sum
+                             every pair's distance for every candidate:
+                             0 (default) = each 128 x 128 Gram tile pair is
+                               computed once and used for both roles
+                               (d(c, o) = d(o, c)): candidate tile t takes
+                               the point blocks b >= t, adds each distance
+                               to its row's candidate and, off the
+                               diagonal, to its column's point as a
+                               candidate (half the tensor-core work);
+                             nonzero = every tile in both orientations.
+                             The two differ only by FP32 rounding of a
+                             pair's distance from the other orientation's
+                             Gram entry.  Ignored by the matrix forms. */
 } km_options;
 
 /* Results, filled on the HOST before the call returns. */

@@ -132,6 +132,9 @@ struct FeatArgs {
   int* lnear;
   long long* sg;        // [k_pad][n_pad], slot-major
   long long* ss;        // [n_pad]
+  // Symmetric dense pass: every candidate's distance sum (fixed point),
+  // from its own tile's rows and the column sums of the tiles before it.
+  unsigned long long* gsym;  // [n_pad]
 };
 
 // Pass of the incremental BUILD: the gain change of every candidate from
@@ -140,6 +143,13 @@ constexpr int kModeBuildUpd = 2;
 // Pass of the incremental SWAP: the Eq. (7) sums of every candidate moved
 // by the listed old and new cache entries, then every candidate's Delta.
 constexpr int kModeSwapUpd = 3;
+// Dense pass (first BUILD step, the k = 1 swap) with each Gram tile pair
+// computed once: candidate tile t streams only the point blocks b >= t;
+// every pair's distance goes to its row's sum (candidate c, point o) and,
+// for b > t, to its column's sum (candidate o, point c), d being
+// symmetric.  The totals meet in a global array; the last CTA takes the
+// least.
+constexpr int kModeBuildSym = 4;
 
 // Adds a signed x (|x| < 2^31) to the 32-bit word w of a sum whose value is
 // w + 2^32 * carry (carry a signed count in two's complement).
@@ -183,8 +193,10 @@ __host__ __device__ inline FeatLayout feat_layout(int d, int k) {
   o += 16 * 16;
   L.rl = o;
   o += 8 * (size_t)k;
-  L.acc = o;
-  o += 4 * (size_t)kTileM * k;
+  L.acc = o;  // SWAP: slot table; symmetric pass: column partials + counters
+  const size_t sym_bytes = 8 * (size_t)kFeatMetaStages * kTileN + 4 * kFeatMetaStages;
+  o += (4 * (size_t)kTileM * k > sym_bytes) ? 4 * (size_t)kTileM * k : sym_bytes;
+  o = (o + 7) / 8 * 8;
   L.red = o;
   o += 8 * (size_t)kTileM * (kFeatEpiWarps / 4 - 1);
   o = (o + 127) / 128 * 128;
@@ -314,6 +326,7 @@ __global__ void __launch_bounds__(kFeatThreads, 1) k_feat_pass(const FeatArgs a)
   // moves; the commit that wrote the list finished before this launch)
   constexpr bool kList = (MODE == kModeBuildUpd || MODE == kModeSwapUpd);
   constexpr bool kSwapLike = (MODE == kModeSwap || MODE == kModeSwapUpd);
+  constexpr bool kSym = (MODE == kModeBuildSym);
   const int nlist =
       kList ? (int)min(__ldcg(a.lcnt), (unsigned)(MODE == kModeSwapUpd ? 2 * a.n : a.n)) : 0;
   const int nblocks = kList ? (nlist + kTileN - 1) / kTileN : a.n_pad / kTileN;
@@ -352,6 +365,14 @@ __global__ void __launch_bounds__(kFeatThreads, 1) k_feat_pass(const FeatArgs a)
     for (int i = tid; i < kTileM * k; i += blockDim.x) acc[i] = 0u;
   }
   for (int i = tid; i < kTileM; i += blockDim.x) rowc[i] = 0;
+  // symmetric pass: per meta stage, the block's 128 column sums and the
+  // count of epilogue warps that added theirs (the last one flushes)
+  unsigned long long* colp = reinterpret_cast<unsigned long long*>(smem + L.acc);
+  unsigned* colc = reinterpret_cast<unsigned*>(colp + kFeatMetaStages * kTileN);
+  if (kSym) {
+    for (int i = tid; i < kFeatMetaStages * kTileN; i += blockDim.x) colp[i] = 0ull;
+    if (tid < kFeatMetaStages) colc[tid] = 0u;
+  }
   if (warp == 1) {
     tmem_alloc(tmem_slot, kFeatAccBufs * kTileN);
     tmem_relinquish();
@@ -388,7 +409,7 @@ __global__ void __launch_bounds__(kFeatThreads, 1) k_feat_pass(const FeatArgs a)
         }
         mbar_arrive_expect_tx(a_full, tile_bytes);
         bulk_g2s(sA, a.XpA + (size_t)t * kTileM * d, tile_bytes, a_full);
-        for (int b = 0; b < nblocks; ++b, ++gb) {
+        for (int b = kSym ? t : 0; b < nblocks; ++b, ++gb) {
           const int s = (int)(gb % bst);
           const uint32_t ph = (uint32_t)((gb / bst) & 1);
           if (!mbar_wait(&b_empty[s], ph ^ 1u, abort_flag, wlim)) {
@@ -456,7 +477,7 @@ __global__ void __launch_bounds__(kFeatThreads, 1) k_feat_pass(const FeatArgs a)
         if (t < 0) break;
         tc_fence_after();
         bool ok = true;
-        for (int b = 0; b < nblocks; ++b, ++gb) {
+        for (int b = kSym ? t : 0; b < nblocks; ++b, ++gb) {
           const int s = (int)(gb % bst);
           const int buf = (int)(gb % kFeatAccBufs);
           if (!mbar_wait(&b_full[s], (uint32_t)((gb / bst) & 1), abort_flag, wlim) ||
@@ -511,7 +532,7 @@ __global__ void __launch_bounds__(kFeatThreads, 1) k_feat_pass(const FeatArgs a)
       // <=>  v = |x_c|^2/2 + thr[o] - g < 0, and v is what the MMA produced
       const float hc = 0.5f * nc;
       long long sh = 0;  // fixed point: the BUILD gain's sum or the SWAP shared term
-      for (int b = 0; b < nblocks; ++b, ++gb) {
+      for (int b = kSym ? t : 0; b < nblocks; ++b, ++gb) {
         const int buf = (int)(gb % kFeatAccBufs);
         const int ms = (int)(gb % kFeatMetaStages);
         if (!mbar_wait(&acc_full[buf], (uint32_t)((gb / kFeatAccBufs) & 1), abort_flag, wlim) ||
@@ -599,6 +620,56 @@ __global__ void __launch_bounds__(kFeatThreads, 1) k_feat_pass(const FeatArgs a)
                 const int ddq = fxq(pair_dist(fmaf(2.f, v[j], m_no[col0 + j])), scale);
                 sh += (long long)(min(ddq - m_qn[col0 + j], 0) - min(ddq - m_qo[col0 + j], 0));
               }
+            }
+          }
+        } else if (kSym) {
+          // every pair once: x[j] = d(c, o_j) in fixed point (0 where the
+          // row or the column is padding) into this row's sum
+          const int colg = b * kTileN + col0;
+          unsigned x[32];
+#pragma unroll
+          for (int j = 0; j < 32; ++j) {
+            const float g = (hc + m_thr[col0 + j]) - v[j];
+            const float d2 = fmaf(-2.f, g, nc + m_no[col0 + j]);
+            x[j] = (c < n && colg + j < n) ? (unsigned)fxq(pair_dist(d2), scale) : 0u;
+            sh += x[j];
+          }
+          if (b != t) {
+            // column sums over the warp's 32 rows (each below 2^31: 32
+            // terms below 2^26): at every halving step a lane keeps the
+            // half of its columns selected by its lane bit and adds the
+            // partner's copy of that half, so lane j ends with column j
+#pragma unroll
+            for (int h = 16; h >= 1; h >>= 1) {
+              const bool up = (lane & h) != 0;
+#pragma unroll
+              for (int i = 0; i < h; ++i) {
+                const unsigned keep = up ? x[i + h] : x[i];
+                const unsigned send = up ? x[i] : x[i + h];
+                x[i] = keep + __shfl_xor_sync(0xffffffffu, send, h);
+              }
+            }
+            unsigned long long* cp = colp + (size_t)ms * kTileN;
+            atomicAdd(cp + col0 + lane, (unsigned long long)x[0]);
+            __syncwarp();
+            unsigned last = 0;
+            if (lane == 0) {
+              __threadfence_block();
+              last = (atomicAdd(colc + ms, 1u) == (unsigned)kFeatEpiWarps - 1u) ? 1u : 0u;
+            }
+            last = __shfl_sync(0xffffffffu, last, 0);
+            if (last) {
+              // every warp's sums of this block are in: add the block's
+              // columns to those points' totals as candidates, clear the
+              // stage's partials (reused after the stage is released)
+              __threadfence_block();
+#pragma unroll
+              for (int q = 0; q < kTileN / 32; ++q) {
+                const int col = q * 32 + lane;
+                const unsigned long long vsum = atomicExch(cp + col, 0ull);
+                if (vsum) atomicAdd(a.gsym + (size_t)b * kTileN + col, vsum);
+              }
+              if (lane == 0) atomicExch(colc + ms, 0u);
             }
           }
         } else if (MODE == kModeBuild && a.build_first) {
@@ -762,6 +833,8 @@ __global__ void __launch_bounds__(kFeatThreads, 1) k_feat_pass(const FeatArgs a)
               if (key_less(ck, wbest)) wbest = ck;
             }
           }
+        } else if (kSym) {
+          if (c < n) atomicAdd(a.gsym + c, (unsigned long long)shared_part);
         } else {
           if (cvalid) {
             Key<double> ck;
@@ -782,6 +855,7 @@ __global__ void __launch_bounds__(kFeatThreads, 1) k_feat_pass(const FeatArgs a)
       abort_flag[0] = 1;
       atomicExch(&st->error, kErrTimeout);
     }
+    if (kSym) __threadfence();  // this thread's totals before the CTA's ticket
     wbest = warp_min_key(wbest);
     if (lane == 0) wkeys[ew] = wbest;
   }
@@ -802,6 +876,49 @@ __global__ void __launch_bounds__(kFeatThreads, 1) k_feat_pass(const FeatArgs a)
   __syncthreads();
   if (!*last_flag) return;
   __threadfence();
+  if (kSym) {
+    // every CTA's totals are in: the least over the non-medoid candidates,
+    // eight of each thread's loads in flight
+    const double unit = __longlong_as_double((long long)(1023 - a.fq) << 52);
+    Key<double> b;
+    b.d = Tr<float>::g_high();
+    b.slot = INT_MAX;
+    b.cand = INT_MAX;
+    constexpr int U = 8;
+    for (int c0 = tid; c0 < n; c0 += U * kFeatThreads) {
+      unsigned long long tv[U];
+      unsigned char mv[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int c = c0 + u * kFeatThreads;
+        tv[u] = (c < n) ? __ldcg(a.gsym + c) : 0ull;
+        mv[u] = (c < n) ? a.is_med[c] : (unsigned char)1;
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+        if (!mv[u]) {
+          Key<double> ck;
+          ck.d = (double)(long long)tv[u] * unit;
+          ck.slot = 0;
+          ck.cand = c0 + u * kFeatThreads;
+          if (key_less(ck, b)) b = ck;
+        }
+    }
+    b = warp_min_key(b);
+    Key<double>* kk = reinterpret_cast<Key<double>*>(red);  // free after the tiles
+    if (lane == 0) kk[warp] = b;
+    __syncthreads();
+    if (tid == 0) {
+      Key<double> bb = kk[0];
+      for (int w = 1; w < kFeatThreads / 32; ++w)
+        if (key_less(kk[w], bb)) bb = kk[w];
+      st->build_gain_d = bb.d;
+      st->build_cand = bb.cand;
+      st->tile_next = 0;
+      st->ticket = 0;
+    }
+    return;
+  }
   if (warp == 0) {
     Key<double> b;
     b.d = Tr<float>::g_high();
@@ -1255,7 +1372,8 @@ namespace {
 
 struct FeatWs {
   size_t st, med, is_med, near, sec, dn, ds, dn2, ds2, thr, norms, removal, td2, partials, trace,
-      gains, xpa, xpb, carry, range, xpl, lno, lthr, lqo, lqn, lnear, lcnt, bgain, sg, ss, total;
+      gains, xpa, xpb, carry, range, xpl, lno, lthr, lqo, lqn, lnear, lcnt, bgain, sg, ss, gsym,
+      total;
   int n_pad, k_pad, cap;
 };
 
@@ -1306,6 +1424,7 @@ bool feat_ws(int64_t n, int d, int k, const km_options* o, FeatWs* L) {
   const bool swap_inc = k >= 2 && !(o && o->swap_full);
   L->sg = take(swap_inc ? 8 * (size_t)n_pad * k_pad : 0);
   L->ss = take(swap_inc ? 8 * (size_t)n_pad : 0);
+  L->gsym = take(8 * (size_t)n_pad);  // totals of the symmetric dense pass
   L->total = off;
   L->n_pad = n_pad;
   L->k_pad = k_pad;
@@ -1379,9 +1498,14 @@ km_status f_pass(FCtx& c, int mode, int first, cudaEvent_t ev0 = nullptr,
   else if (mode == kModeBuildUpd)
     FK(cudaFuncSetAttribute(k_feat_pass<kModeBuildUpd>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                             (int)L.total));
+  else if (mode == kModeBuildSym)
+    FK(cudaFuncSetAttribute(k_feat_pass<kModeBuildSym>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                            (int)L.total));
   else
     FK(cudaFuncSetAttribute(k_feat_pass<kModeSwapUpd>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                             (int)L.total));
+  // the symmetric pass adds into zeroed totals
+  if (mode == kModeBuildSym) FK(cudaMemsetAsync(a.gsym, 0, 8 * (size_t)a.n_pad, c.s));
   if (ev0) FK(cudaEventRecord(ev0, c.s));
   if (mode == kModeSwap)
     k_feat_pass<kModeSwap><<<grid, kFeatThreads, L.total, c.s>>>(a);
@@ -1389,6 +1513,8 @@ km_status f_pass(FCtx& c, int mode, int first, cudaEvent_t ev0 = nullptr,
     k_feat_pass<kModeBuild><<<grid, kFeatThreads, L.total, c.s>>>(a);
   else if (mode == kModeBuildUpd)
     k_feat_pass<kModeBuildUpd><<<grid, kFeatThreads, L.total, c.s>>>(a);
+  else if (mode == kModeBuildSym)
+    k_feat_pass<kModeBuildSym><<<grid, kFeatThreads, L.total, c.s>>>(a);
   else
     k_feat_pass<kModeSwapUpd><<<grid, kFeatThreads, L.total, c.s>>>(a);
   FK(cudaGetLastError());
@@ -1487,6 +1613,7 @@ km_status run_features(bool do_build, bool do_swap, const void* X, int64_t n, in
   a.lnear = reinterpret_cast<int*>(c.ws + c.L.lnear);
   a.sg = reinterpret_cast<long long*>(c.ws + c.L.sg);
   a.ss = reinterpret_cast<long long*>(c.ws + c.L.ss);
+  a.gsym = reinterpret_cast<unsigned long long*>(c.ws + c.L.gsym);
   if (res) memset(res, 0, sizeof(*res));
 
   cudaEvent_t e0 = nullptr, e1 = nullptr, e2 = nullptr;
@@ -1558,7 +1685,11 @@ km_status run_features(bool do_build, bool do_swap, const void* X, int64_t n, in
         FK(cudaEventCreate(&x1));
         bev.push_back({x0, x1});
       }
-      r = f_pass(c, (step > 0 && a.incremental) ? kModeBuildUpd : kModeBuild, step == 0, x0, x1);
+      // step 0: every pair (each Gram tile pair once unless gram_full);
+      // later steps: the listed points, or every candidate row again
+      const int mode = (step == 0) ? (c.opt.gram_full ? kModeBuild : kModeBuildSym)
+                                   : (a.incremental ? kModeBuildUpd : kModeBuild);
+      r = f_pass(c, mode, step == 0, x0, x1);
       if (r != KM_OK) return r;
       FeatArgs b = a;
       b.build_first = (step == 0);
@@ -1596,7 +1727,7 @@ km_status run_features(bool do_build, bool do_swap, const void* X, int64_t n, in
     KmState h0;
     r = f_read(c, &h0);
     if (r != KM_OK) return r;
-    r = f_pass(c, kModeBuild, 1);
+    r = f_pass(c, c.opt.gram_full ? kModeBuild : kModeBuildSym, 1);
     if (r != KM_OK) return r;
     KmState h1;
     r = f_read(c, &h1);

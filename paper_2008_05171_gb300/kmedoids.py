@@ -59,7 +59,7 @@ class km_options(ctypes.Structure):
                 ("draws", ctypes.c_void_p), ("draws_len", ctypes.c_int64),
                 ("maxneighbor", ctypes.c_int64), ("check_input", ctypes.c_int32),
                 ("build_full", ctypes.c_int32), ("wait_limit_ns", ctypes.c_int64),
-                ("swap_full", ctypes.c_int32), ("pad_options", ctypes.c_int32)]
+                ("swap_full", ctypes.c_int32), ("gram_full", ctypes.c_int32)]
 
 
 class km_result(ctypes.Structure):
@@ -215,15 +215,18 @@ def _stream():
 def options(variant="fastpam1", max_iter=0, tol=0.0, fastpam2_tol=0.0,
             rows_per_tile=0, profile=False, trace=0, tune=0, draws=None,
             maxneighbor=0, check_input=False, build_full=False, wait_limit_ns=0,
-            swap_full=False):
+            swap_full=False, gram_full=False):
     """km_options.  draws: int32 CUDA tensor of candidate draws (FastCLARANS);
     the caller keeps it alive for the call.  build_full: every BUILD step
     streams all candidate rows instead of updating the gains
-    incrementally.  wait_limit_ns: limit of the device waits (0 = 4 s)."""
+    incrementally.  wait_limit_ns: limit of the device waits (0 = 4 s).
+    swap_full / gram_full (on-the-fly form): plain SWAP passes / every
+    Gram tile in both orientations in the dense passes."""
     o = km_options()
     load().km_default_options(ctypes.byref(o))
     o.wait_limit_ns = int(wait_limit_ns)
     o.swap_full = 1 if swap_full else 0
+    o.gram_full = 1 if gram_full else 0
     if draws is not None:
         o.draws = ctypes.c_void_p(draws.data_ptr())
         o.draws_len = int(draws.numel())

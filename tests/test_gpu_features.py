@@ -124,6 +124,43 @@ def test_incremental_swap_equals_the_plain_pass(n, d, k):
     assert r["medoids"].cpu().tolist() == rf["medoids"].cpu().tolist()
 
 
+@pytest.mark.parametrize("n,d", [(6001, 128), (3000, 64), (129, 16), (100, 32)])
+def test_symmetric_gram_dense_pass(n, d):
+    """The dense pass of the first BUILD step with each Gram tile pair
+    computed once (default: candidate tile t takes the point blocks b >= t
+    and sums the off-diagonal tiles along rows and columns) and with every
+    tile in both orientations (gram_full), against the oracle's exact
+    distance sums of step 0 (Alg. 1): the step's gain within 1e-6 of the
+    least sum plus the error of the candidate's distance to itself (the
+    Gram form gives d(c, c) as the square root of the rounding residue of
+    |x_c|^2 + |x_c|^2 - 2 x_c.x_c, up to sqrt(2^-19 max |x|^2)), and the
+    oracle's medoid (on these inputs the best sum leads the next by 0.18 %
+    or more).  The points are taken in three orders so
+    that the best candidate sits in different tiles (a dropped or doubled
+    column sum moves the choice or the gain); 3-medoid runs of both forms
+    take the same medoids."""
+    X, Dh = _feat_case(n, d, 5, ("sym", n, d))
+    self_pair = float(np.sqrt(2.0 ** -19 * (X.astype(np.float64) ** 2).sum(axis=1).max()))
+    rng = np.random.default_rng(n + d)
+    for perm in (np.arange(n), np.arange(n)[::-1], rng.permutation(n)):
+        Xp = np.ascontiguousarray(X[perm])
+        Dp = np.ascontiguousarray(Dh[:n, :n][np.ix_(perm, perm)])
+        sums = oracle.build_gains(Dp, [])
+        order = np.argsort(sums, kind="stable")
+        best = float(sums[order[0]])
+        assert sums[order[1]] - best > 1e-3 * best
+        Xt = torch.from_numpy(Xp).to(torch.bfloat16).cuda()
+        for full in (False, True):
+            out = km.build_features(Xt, 1, gram_full=full)
+            assert out["status_name"] == "KM_OK"
+            assert abs(out["build_gains"][0] - best) <= 1e-6 * best + self_pair
+            assert out["medoids"].cpu().tolist() == [int(order[0])]
+        a = km.run_features(Xt, 3)
+        b = km.run_features(Xt, 3, gram_full=True)
+        assert a["medoids"].cpu().tolist() == b["medoids"].cpu().tolist()
+        assert abs(a["td"] - b["td"]) <= 1e-9 * b["td"]
+
+
 def test_run_features_many_tiles_per_cta():
     """n = 20000 gives 157 candidate tiles, more than there are SMs, so CTAs
     take several tiles each through the dynamic tile counter (and the tile
