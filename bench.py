@@ -286,6 +286,22 @@ def run_features(args, rank, world, local_rank):
              "swap_passes": rp["eval_launches"],
              "same_medoids": rp["medoids"].cpu().tolist() == r0["medoids"].cpu().tolist(),
              "frac_of_sustained_bf16": round(flops / (rp["eval_ms_median"] / 1e3) / 1e12 / peak, 4)}
+    # the dense pass of BUILD step 0 (every candidate's distance sum) with
+    # each Gram tile pair computed once, against every tile (gram_full)
+    def step0(full):
+        t, med = [], None
+        for _ in range(3):
+            r1 = km.build_features(X, 1, labels=False, profile=True, gram_full=full)
+            t.append(r1["build_eval_ms"])
+            med = r1["medoids"].cpu().tolist()
+        return float(np.median(t)), med
+    s0_ms, s0_med = step0(False)
+    f0_ms, f0_med = step0(True)
+    sym = {"step0_ms": s0_ms, "step0_gram_full_ms": f0_ms, "speedup": round(f0_ms / s0_ms, 3),
+           "same_medoid": s0_med == f0_med,
+           "pairs_per_s": n * n / (s0_ms / 1e3),
+           "kind": "each 128x128 Gram tile pair once (tiles b >= t), distances summed along "
+                   "rows and columns; gram_full = every tile in both orientations"}
     rb = roof(b_ms, "k_feat_pass<BUILD> (step 0 dense, then incremental updates)",
               r0["build_eval_ms"], b_flops)
     rb["build_rows_streamed"] = b_rows
@@ -323,6 +339,7 @@ def run_features(args, rank, world, local_rank):
                             "SWAP run (later passes incremental)",
         "swap_pass": sw,
         "plain_swap_run": plain,
+        "symmetric_gram": sym,
         "full_run_ms": total_ms / args.steps, "swap_iterations": r0["iterations"],
         "swaps": r0["swaps"], "swap_iter_ms": s_ms, "build_step_ms": b_ms, "td": r0["td"],
         "kernel_ms_per_step": {"build_eval": r0["build_eval_ms"], "swap_eval": r0["eval_ms"],
