@@ -415,7 +415,10 @@ km_status kmedoids_gram_bf16(const void *X, int64_t n, int32_t d, int64_t ldx,
  * every pass, and the kept sums equal a full recomputation's.  With
  * build_full / swap_full every step or pass takes every point and the
  * threshold test is folded into the product (the sign of one MMA output
- * decides a pair).  The per-point cache (nearest, d_n,
+ * decides a pair).  BUILD's step 0 (and the swap of k = 1), where every
+ * pair counts for both of its points, computes each Gram tile pair once
+ * and sums its distances along rows and columns (unless opts->gram_full).
+ * The per-point cache (nearest, d_n,
  * d_s) and the TD are computed exactly from FP32 differences sum (x - y)^2,
  * so the Gram form's rounding (relative error ~1e-5 on d^2 for well
  * separated points) only affects which candidates see a hit and the Delta
@@ -425,8 +428,9 @@ km_status kmedoids_gram_bf16(const void *X, int64_t n, int32_t d, int64_t ldx,
  * units), so they do not depend on the order of the GPU's additions.
  * FastPAM1 only; k <= 224.
  * Workspace (DEVICE, 256-byte aligned): kmedoids_features_workspace_size()
- * bytes, which includes the features rearranged for the tensor cores and,
- * unless opts->swap_full, the kept SWAP sums (8 n k_pad bytes). */
+ * bytes, which includes the features rearranged for the tensor cores, the
+ * totals of the symmetric step 0 (8 n bytes) and, unless opts->swap_full,
+ * the kept SWAP sums (8 n k_pad bytes). */
 size_t kmedoids_features_workspace_size(int64_t n, int32_t d, int32_t k,
                                         const km_options *opts);
 
