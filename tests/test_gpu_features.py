@@ -183,8 +183,9 @@ def test_run_features_many_tiles_per_cta():
 
 def test_features_k1_and_k_equals_n():
     """k = 1: SWAP from any single medoid reaches the 1-medoid (Eq. (3)) by a
-    dense pass (TD within 1e-5 of the exact 1-medoid's); BUILD + SWAP with
-    k = 1 as well.  k = n: every point a medoid, TD 0."""
+    dense pass (TD within 1e-5 of the exact 1-medoid's; the same medoid with
+    each Gram tile pair once and with every tile); BUILD + SWAP with k = 1
+    as well.  k = n: every point a medoid, TD 0."""
     X, Dh = _feat_case(900, 64, 4, "feat-k1")
     Xt = torch.from_numpy(X).to(torch.bfloat16).cuda()
     best = float(Dh[:900, :900].astype(np.float64).sum(axis=0).min())
@@ -195,6 +196,12 @@ def test_features_k1_and_k_equals_n():
         assert out["swaps"] <= 1
     r = km.run_features(Xt, 1)
     assert abs(r["td"] - best) <= 1e-5 * best
+    # the dense pass with every Gram tile (gram_full) reaches the same medoid
+    for start in ([0], [899]):
+        a = km.swap_features(Xt, start)
+        b = km.swap_features(Xt, start, gram_full=True)
+        assert a["medoids"].cpu().tolist() == b["medoids"].cpu().tolist()
+        assert abs(a["td"] - b["td"]) <= 1e-12 * b["td"]
     small = torch.from_numpy(X[:40]).to(torch.bfloat16).cuda()
     z = km.run_features(small, 40)
     assert z["td"] == 0.0 and sorted(z["medoids"].cpu().tolist()) == list(range(40))
