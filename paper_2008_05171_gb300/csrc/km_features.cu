@@ -123,13 +123,19 @@ struct FeatArgs {
   unsigned* lcnt;       // [0] entries in the list (cleared by the pass that reads
                         // it); as u64 [1] the rows every update pass streamed
   long long* bgain;
-  // Incremental SWAP (k >= 2): the same list, each entry a point's old
-  // (sign -1) or new (sign +1) cache entry: lqo = d_n and lqn = d_s in
-  // fixed point, lnear = nearest slot | sign bit, lthr = the test's bound
-  // from that d_s; sg[i][c] and ss[c] the per-slot and shared sums of
+  // Incremental SWAP (k >= 2): the same list, one entry per point whose
+  // cache entry a swap changed (every point for the first pass), holding
+  // the new entry (lqo = d_n, lqn = d_s in fixed point) and, after a swap,
+  // the old one (lqo2, lqn2; lqo2 shares lno's storage), lnear = new
+  // nearest slot | old nearest slot << 16 | 1 << 31 when the old entry is
+  // there, lthr = the test's bound on the MMA output from the larger d_s;
+  // the list rows' threshold columns carry |x_o|^2 / 2, so the output is
+  // d^2 / 2.  sg[i][c] and ss[c] are the per-slot and shared sums of
   // Eq. (7) of every candidate (magnitudes, fixed point), kept across passes.
   int swap_incremental;
   int* lnear;
+  int* lqo2;
+  int* lqn2;
   long long* sg;        // [k_pad][n_pad], slot-major
   long long* ss;        // [n_pad]
   // Symmetric dense pass: every candidate's distance sum (fixed point),
@@ -201,7 +207,7 @@ __host__ __device__ inline FeatLayout feat_layout(int d, int k) {
   o += 8 * (size_t)kTileM * (kFeatEpiWarps / 4 - 1);
   o = (o + 127) / 128 * 128;
   L.meta = o;
-  L.meta_bytes = 5 * 4 * kTileN;
+  L.meta_bytes = 6 * 4 * kTileN;  // per-block point data: up to six 4-byte arrays
   o += L.meta_bytes * kFeatMetaStages;
   o = (o + 1023) / 1024 * 1024;
   L.a = o;
@@ -428,7 +434,7 @@ __global__ void __launch_bounds__(kFeatThreads, 1) k_feat_pass(const FeatArgs a)
             break;
           }
           unsigned char* meta = metas + (size_t)ms * L.meta_bytes;
-          mbar_arrive_expect_tx(&m_full[ms], (uint32_t)L.meta_bytes);
+          mbar_arrive_expect_tx(&m_full[ms], (uint32_t)((MODE == kModeSwapUpd ? 6 : 5) * 4 * kTileN));
           mused |= 1u << ms;
           mph = (mph & ~(1u << ms)) | (mp << ms);
           const size_t o0 = (size_t)b * kTileN;
@@ -439,11 +445,12 @@ __global__ void __launch_bounds__(kFeatThreads, 1) k_feat_pass(const FeatArgs a)
             bulk_g2s(meta + 1536, a.lqn + o0, 4 * kTileN, &m_full[ms]);
             bulk_g2s(meta + 2048, a.lqn + o0, 4 * kTileN, &m_full[ms]);  // keeps the byte count
           } else if (MODE == kModeSwapUpd) {
-            bulk_g2s(meta, a.lno + o0, 4 * kTileN, &m_full[ms]);
+            bulk_g2s(meta, a.lqo2 + o0, 4 * kTileN, &m_full[ms]);
             bulk_g2s(meta + 512, a.lthr + o0, 4 * kTileN, &m_full[ms]);
             bulk_g2s(meta + 1024, a.lqo + o0, 4 * kTileN, &m_full[ms]);
             bulk_g2s(meta + 1536, a.lqn + o0, 4 * kTileN, &m_full[ms]);
             bulk_g2s(meta + 2048, a.lnear + o0, 4 * kTileN, &m_full[ms]);
+            bulk_g2s(meta + 2560, a.lqn2 + o0, 4 * kTileN, &m_full[ms]);
           } else {
             bulk_g2s(meta, a.norms + o0, 4 * kTileN, &m_full[ms]);
             bulk_g2s(meta + 512, a.thr + o0, 4 * kTileN, &m_full[ms]);
@@ -582,26 +589,42 @@ __global__ void __launch_bounds__(kFeatThreads, 1) k_feat_pass(const FeatArgs a)
             sh += dnq - ddq;
           }
         };
-        // incremental SWAP: listed entry at column col, an old (sign -1) or
-        // new (sign +1) cache entry of its point; d^2 = |x_o|^2 + 2 v (zero
-        // threshold columns); Eq. (7)'s terms of that entry, classified in
-        // fixed point, added with the entry's sign
+        // incremental SWAP: listed point at column col, d^2 = 2 v (its
+        // threshold columns carry |x_o|^2 / 2); Eq. (7)'s terms of its new
+        // cache entry added and, after a swap, those of its old entry
+        // subtracted, each classified in fixed point from the same d
         auto hit_upd = [&](int col, float vv) {
-          const int ddq = fxq(pair_dist(fmaf(2.f, vv, m_no[col])), scale);
-          const int dnq = reinterpret_cast<const int*>(meta + 1024)[col];
-          const int dsq = reinterpret_cast<const int*>(meta + 1536)[col];
-          const int pk = m_near[col];
-          const int sl = pk & 0x7fffffff;
-          const int sgn = pk < 0 ? -1 : 1;
+          const int* mq = reinterpret_cast<const int*>(meta);
+          const int ddq = fxq(pair_dist(2.f * vv), scale);
+          const unsigned pk = (unsigned)m_near[col];
+          const int dnq = mq[256 + col], dsq = mq[384 + col];
+          const int sl = (int)(pk & 0xffffu);
+          long long dsh = 0;
           int mag = 0;
           if (ddq < dnq) {
-            sh += (long long)(sgn * (dnq - ddq));
+            dsh = dnq - ddq;
             mag = dsq - dnq;
           } else if (ddq < dsq) {
             mag = dsq - ddq;
           }
-          if (mag > 0 && KM_INB(a.st, sl, a.k))
-            add_signed_word(arow + sl, crow + sl, rowc + r, sgn * mag);
+          if (pk >> 31) {
+            const int sl2 = (int)((pk >> 16) & 0x7fffu);
+            const int dnq2 = mq[col], dsq2 = mq[640 + col];
+            int mag2 = 0;
+            if (ddq < dnq2) {
+              dsh -= dnq2 - ddq;
+              mag2 = dsq2 - dnq2;
+            } else if (ddq < dsq2) {
+              mag2 = dsq2 - ddq;
+            }
+            if (sl2 == sl) {
+              mag -= mag2;
+            } else if (mag2 > 0 && KM_INB(a.st, sl2, a.k)) {
+              add_signed_word(arow + sl2, crow + sl2, rowc + r, -mag2);
+            }
+          }
+          sh += dsh;
+          if (mag != 0 && KM_INB(a.st, sl, a.k)) add_signed_word(arow + sl, crow + sl, rowc + r, mag);
         };
         if (MODE == kModeBuildUpd) {
           // listed point o (column col): v = |x_c|^2/2 - x_c.x_o (zero
@@ -1002,23 +1025,37 @@ __device__ __forceinline__ void top2f(float v, int j, int& n1, float& d1, int& n
   }
 }
 
-// One entry of the incremental SWAP's list at position p: point o's cache
-// entry (d_n, d_s, nearest slot; sign -1 for the entry it had before a
-// swap), the bound of the pass's test from that d_s (v < bound iff d is
-// below d_s, with a 2^-10 relative margin on d^2), and o's B-operand row.
+// One entry of the incremental SWAP's list at position p: point o's new
+// cache entry (d_n, d_s, nearest slot) and, when has_old, the entry it had
+// before the swap; the bound of the pass's test from the larger d_s (the
+// MMA output v = d^2 / 2 is below it iff d is below that d_s, with a 2^-10
+// relative margin on d^2); o's B-operand row with |x_o|^2 / 2 in its
+// threshold columns.
 __device__ __forceinline__ void swap_list_put(const FeatArgs& a, unsigned p, int o, float dn,
-                                              float ds, int near, bool old_entry) {
+                                              float ds, int near, bool has_old, float dn_old,
+                                              float ds_old, int near_old) {
   const float scale = __int_as_float((127 + a.fq) << 23);
-  const float no = a.norms[o];
-  a.lno[p] = no;
-  a.lthr[p] = 0.5f * (ds * ds * (1.f + 0x1p-10f) + 0x1p-100f - no);
+  const float dsm = has_old ? fmaxf(ds, ds_old) : ds;
+  a.lthr[p] = 0.5f * (dsm * dsm * (1.f + 0x1p-10f) + 0x1p-100f);
   a.lqo[p] = fxq(dn, scale);
   a.lqn[p] = fxq(ds, scale);
-  a.lnear[p] = old_entry ? (int)((unsigned)near | 0x80000000u) : near;
+  a.lqo2[p] = has_old ? fxq(dn_old, scale) : 0;
+  a.lqn2[p] = has_old ? fxq(ds_old, scale) : 0;
+  a.lnear[p] = (int)(((unsigned)near & 0xffffu) |
+                     (has_old ? ((((unsigned)near_old & 0x7fffu) << 16) | 0x80000000u) : 0u));
   const int kcs = a.dk >> 3;
   for (int kc = 0; kc < kcs; ++kc)
     *reinterpret_cast<uint4*>(a.XpL + chunk_off((int)p, kc, a.dk)) =
         *reinterpret_cast<const uint4*>(a.XpB + chunk_off(o, kc, a.dk));
+  uint16_t t[3];
+  split3_bf16(0.5f * a.norms[o], t);
+  const uint16_t one = 0x3F80u;  // bf16 1.0
+  uint4 c;
+  c.x = (uint32_t)one | ((uint32_t)one << 16);
+  c.y = (uint32_t)one | ((uint32_t)t[0] << 16);
+  c.z = (uint32_t)t[1] | ((uint32_t)t[2] << 16);
+  c.w = 0u;
+  *reinterpret_cast<uint4*>(a.XpL + chunk_off((int)p, a.d >> 3, a.dk)) = c;
 }
 
 // Warp-aggregated reservation of cnt list positions per lane (cnt 0..2).
@@ -1090,7 +1127,7 @@ __global__ void __launch_bounds__(256) k_feat_cache(const FeatArgs a) {
     const bool put = o < n;
     const unsigned p = list_reserve(a.lcnt, put ? 1u : 0u);
     if (put && KM_INB(st, p, 2 * (long long)a.n_pad))
-      swap_list_put(a, p, o, a.dn[o], a.ds[o], a.near[o], false);
+      swap_list_put(a, p, o, a.dn[o], a.ds[o], a.near[o], false, 0.f, 0.f, 0);
   }
   const double bs = fblock_sum(tdl, scratch);
   if (threadIdx.x == 0) atomicAdd(&a.td2[rb], bs);
@@ -1173,12 +1210,10 @@ __global__ void __launch_bounds__(256) k_feat_apply(const FeatArgs a) {
       atomicAdd(&sacc[n1], (unsigned long long)(fxq(e2, scale) - fxq(e1, scale)));
     tdl = e1;
   }
-  if (a.swap_incremental) {  // uniform: a changed point's old entry out, new in
-    const unsigned p = list_reserve(a.lcnt, changed ? 2u : 0u);
-    if (changed && KM_INB(st, p + 1, 2 * (long long)a.n_pad)) {
-      swap_list_put(a, p, o, dn_old, ds_old, n1_old, true);
-      swap_list_put(a, p + 1, o, a.dn[o], a.ds[o], a.near[o], false);
-    }
+  if (a.swap_incremental) {  // uniform: a changed point's new entry in, old one out
+    const unsigned p = list_reserve(a.lcnt, changed ? 1u : 0u);
+    if (changed && KM_INB(st, p, 2 * (long long)a.n_pad))
+      swap_list_put(a, p, o, a.dn[o], a.ds[o], a.near[o], true, dn_old, ds_old, n1_old);
   }
   const double bs = fblock_sum(tdl, scratch);
   if (threadIdx.x == 0) atomicAdd(&a.td2[rb ^ 1], bs);
@@ -1372,7 +1407,7 @@ namespace {
 
 struct FeatWs {
   size_t st, med, is_med, near, sec, dn, ds, dn2, ds2, thr, norms, removal, td2, partials, trace,
-      gains, xpa, xpb, carry, range, xpl, lno, lthr, lqo, lqn, lnear, lcnt, bgain, sg, ss, gsym,
+      gains, xpa, xpb, carry, range, xpl, lno, lthr, lqo, lqn, lnear, lqn2, lcnt, bgain, sg, ss, gsym,
       total;
   int n_pad, k_pad, cap;
 };
@@ -1419,6 +1454,7 @@ bool feat_ws(int64_t n, int d, int k, const km_options* o, FeatWs* L) {
   L->lqo = take(8 * (size_t)n_pad);
   L->lqn = take(8 * (size_t)n_pad);
   L->lnear = take(8 * (size_t)n_pad);
+  L->lqn2 = take(8 * (size_t)n_pad);
   L->lcnt = take(16);
   L->bgain = take(8 * (size_t)n_pad);
   const bool swap_inc = k >= 2 && !(o && o->swap_full);
@@ -1611,6 +1647,8 @@ km_status run_features(bool do_build, bool do_swap, const void* X, int64_t n, in
   a.bgain = reinterpret_cast<long long*>(c.ws + c.L.bgain);
   a.swap_incremental = (k >= 2 && !c.opt.swap_full) ? 1 : 0;
   a.lnear = reinterpret_cast<int*>(c.ws + c.L.lnear);
+  a.lqo2 = reinterpret_cast<int*>(c.ws + c.L.lno);  // the BUILD list is done by then
+  a.lqn2 = reinterpret_cast<int*>(c.ws + c.L.lqn2);
   a.sg = reinterpret_cast<long long*>(c.ws + c.L.sg);
   a.ss = reinterpret_cast<long long*>(c.ws + c.L.ss);
   a.gsym = reinterpret_cast<unsigned long long*>(c.ws + c.L.gsym);
