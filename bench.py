@@ -259,7 +259,7 @@ def run_features(args, rank, world, local_rank):
     sw["first_pass_ms"] = first_ms
     sw["later_passes_median_ms"] = sw.pop("median_ms")
     sw["kind"] = ("incremental: pass 1 over every point, later passes over the points the "
-                  "last swap changed (old entry out, new entry in)")
+                  "last swap changed (one entry per point: its old terms out, its new terms in)")
     pass_ms = max_over_ranks(first_ms, world, dev)
     value = world * (n - k) * n / (pass_ms / 1e3)
     r0 = results[-1]
