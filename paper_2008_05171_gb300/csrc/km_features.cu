@@ -626,26 +626,18 @@ __global__ void __launch_bounds__(kFeatThreads, 1) k_feat_pass(const FeatArgs a)
           sh += dsh;
           if (mag != 0 && KM_INB(a.st, sl, a.k)) add_signed_word(arow + sl, crow + sl, rowc + r, mag);
         };
-        if (MODE == kModeBuildUpd) {
-          // listed point o (column col): v = |x_c|^2/2 - x_c.x_o (zero
-          // threshold columns), so d^2 = |x_o|^2 + 2 v; the pair can change
-          // the gain only when d is below the larger of its old and new d_n
-          // (lthr is that bound with a margin, so the test lets through a
-          // superset); the change min(d - dn_new, 0) - min(d - dn_old, 0) is
-          // exact in fixed point, and zero for the pairs the margin adds
-          const int* m_qo = reinterpret_cast<const int*>(meta + 1024);
-          const int* m_qn = reinterpret_cast<const int*>(meta + 1536);
-          const int colg = b * kTileN + col0;
-          if (cvalid) {
-#pragma unroll
-            for (int j = 0; j < 32; ++j) {
-              if (v[j] < m_thr[col0 + j] && colg + j < nlist) {
-                const int ddq = fxq(pair_dist(fmaf(2.f, v[j], m_no[col0 + j])), scale);
-                sh += (long long)(min(ddq - m_qn[col0 + j], 0) - min(ddq - m_qo[col0 + j], 0));
-              }
-            }
-          }
-        } else if (kSym) {
+        // incremental BUILD: listed point o (column col), v = |x_c|^2/2 -
+        // x_c.x_o (zero threshold columns), so d^2 = |x_o|^2 + 2 v; the pair
+        // can change the gain only when d is below the larger of its old and
+        // new d_n (lthr is that bound with a margin, so the test lets through
+        // a superset); the change min(d - dn_new, 0) - min(d - dn_old, 0) is
+        // exact in fixed point, and zero for the pairs the margin adds
+        auto hit_b = [&](int col, float vv) {
+          const int* mq = reinterpret_cast<const int*>(meta);
+          const int ddq = fxq(pair_dist(fmaf(2.f, vv, m_no[col])), scale);
+          sh += (long long)(min(ddq - mq[384 + col], 0) - min(ddq - mq[256 + col], 0));
+        };
+        if (kSym) {
           // every pair once: x[j] = d(c, o_j) in fixed point (0 where the
           // row or the column is padding) into this row's sum
           const int colg = b * kTileN + col0;
@@ -711,12 +703,12 @@ __global__ void __launch_bounds__(kFeatThreads, 1) k_feat_pass(const FeatArgs a)
             // j (set: a hit), shifted in from column 15 down to 0 with one
             // funnel shift per pair; rows that are not candidates see none
             unsigned mask = 0;
-            if (MODE == kModeSwapUpd) {
+            if (MODE == kModeSwapUpd || MODE == kModeBuildUpd) {
               // explicit test against each entry's bound: the sign of
               // v - bound (negative exactly when v < bound), funnel-shifted
-              // as in the plain pass; entries past the list's end and rows
-              // c >= n see none (every row c < n counts: a medoid swapped
-              // out later is a candidate again)
+              // as in the plain pass; entries past the list's end see none,
+              // and in SWAP rows c >= n (every row c < n counts: a medoid
+              // swapped out later is a candidate again)
               const int cbase = b * kTileN + col0 + g16 * 16;
 #pragma unroll
               for (int j = 15; j >= 0; --j)
@@ -724,7 +716,8 @@ __global__ void __launch_bounds__(kFeatThreads, 1) k_feat_pass(const FeatArgs a)
                     __float_as_uint(v[g16 * 16 + j] - m_thr[col0 + g16 * 16 + j]), mask, 1);
               const int left = nlist - cbase;
               if (left < 16) mask &= (left > 0) ? ((1u << left) - 1u) : 0u;
-              if (c >= n) mask = 0;
+              // BUILD: only candidates (a medoid's gain is never used again)
+              if (MODE == kModeSwapUpd ? c >= n : !cvalid) mask = 0;
             } else {
 #pragma unroll
               for (int j = 15; j >= 0; --j)
@@ -741,6 +734,8 @@ __global__ void __launch_bounds__(kFeatThreads, 1) k_feat_pass(const FeatArgs a)
                 if ((mask >> j) & 1u) {
                   if (MODE == kModeSwapUpd)
                     hit_upd(cb + j, v[g16 * 16 + j]);
+                  else if (MODE == kModeBuildUpd)
+                    hit_b(cb + j, v[g16 * 16 + j]);
                   else
                     hit(cb + j, v[g16 * 16 + j]);
                 }
@@ -751,6 +746,8 @@ __global__ void __launch_bounds__(kFeatThreads, 1) k_feat_pass(const FeatArgs a)
                 mask &= mask - 1;
                 if (MODE == kModeSwapUpd)
                   hit_upd(cb + j, sel16(v + g16 * 16, j));
+                else if (MODE == kModeBuildUpd)
+                  hit_b(cb + j, sel16(v + g16 * 16, j));
                 else
                   hit(cb + j, sel16(v + g16 * 16, j));
               }
